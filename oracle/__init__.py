@@ -1,0 +1,22 @@
+"""CPU oracle of the ADHA layout method.  TEST INFRASTRUCTURE ONLY.
+
+Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may import
+this package.  It shares no code with the CUDA path and never imports it.
+
+  * adha_oracle.c  -- layouts, scalar remap, sections, project tanh, chain gradient
+                      (plain scalar C, every float operation rounded on its own).
+  * planner.py     -- affinity graph, greedy grouping (ODS), candidate set, and the
+                      program layout choice (PDL) by dynamic programming and by
+                      exhaustive enumeration.
+  * program.py     -- runs a workload's sections on field arrays, whole or for a
+                      sample of records.
+
+Paper: Majeti, Meel, Barik, Sarkar, "ADHA: Automatic Data layout framework for
+Heterogeneous Architectures", PACT 2014, Section 2 and Tables 2-4.
+"""
+from .core import (  # noqa: F401
+    build, group_layout, layout_info, remap, to_fields, from_fields, tanhf, tanh_coeffs, section,
+    chain_grad, aos, soa, canon,
+)
+from .planner import affinity, ods, candidates, pdl_dp, pdl_exhaustive, program_cost  # noqa: F401
+from .program import run_program_fields, sample_program, initial_fields  # noqa: F401

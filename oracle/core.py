@@ -1,0 +1,192 @@
+"""ctypes front end of adha_oracle.c (TEST INFRASTRUCTURE ONLY; see the package docstring)."""
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "adha_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+SIZE = {0: 4, 1: 8, 2: 4, 3: 2}
+NP = {0: np.float32, 1: np.float64, 2: np.int32, 3: np.uint16}
+OPS = dict(madd3=1, xorshift=2, add=3, mix=4, drift=5, bin=6, ke=7, flags=8, gather=9, kick=10,
+           axpb=11, mul=12, tanh=13)
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_I64 = ctypes.c_int64
+
+
+def build(force=False):
+    """Compile liboracle.so (plain C, no FMA contraction, no fast math)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + ".%d.tmp" % os.getpid()
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+                           "-fno-fast-math", "-Wall", "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _get():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            lib.oracle_group_layout.argtypes = [_P, _P, _I, _P]
+            lib.oracle_layout_info.argtypes = [_I, _P, _I, _P, _P, _P, _P, _P]
+            lib.oracle_remap.argtypes = [_I64, _I, _P, _I, _P, _P, _P, _I, _P, _P, _P]
+            lib.oracle_tanhf.restype = ctypes.c_float
+            lib.oracle_tanhf.argtypes = [ctypes.c_float]
+            lib.oracle_tanhf_n.argtypes = [_P, _P, _I64]
+            lib.oracle_tanh_coeffs.argtypes = [_P, _P]
+            lib.oracle_section.argtypes = [_I, _P, _P, ctypes.c_uint64, ctypes.c_uint64, _I, _P, _P, _I64, _P]
+            lib.oracle_chain_grad.argtypes = [_I, _P, _P, _P, _I, _P, _P, _P, _I64]
+            _lib = lib
+    return _lib
+
+
+def _i32(xs):
+    return np.ascontiguousarray(np.asarray(xs, dtype=np.int32))
+
+
+def aos(F):
+    return [list(range(F))]
+
+
+def soa(F):
+    return [[f] for f in range(F)]
+
+
+def canon(groups):
+    """Canonical form of a grouping: fields ascending in a group, groups ordered by their first field."""
+    return sorted((sorted(g) for g in groups), key=lambda g: g[0])
+
+
+def group_layout(dtypes, fields):
+    """(offsets, struct size) of one group: natural alignment, size rounded to the largest alignment."""
+    f = _i32(fields)
+    off = np.zeros(len(fields), dtype=np.int32)
+    s = _get().oracle_group_layout(_i32(dtypes).ctypes.data, f.ctypes.data, len(fields), off.ctypes.data)
+    return off.tolist(), int(s)
+
+
+def layout_info(dtypes, groups):
+    """(strides per group, group of each field, offset of each field) of a layout."""
+    F = len(dtypes)
+    lens = _i32([len(g) for g in groups])
+    flat = _i32([f for g in groups for f in g])
+    stride = np.zeros(len(groups), dtype=np.int32)
+    gof = np.zeros(F, dtype=np.int32)
+    oof = np.zeros(F, dtype=np.int32)
+    d = _i32(dtypes)
+    rc = _get().oracle_layout_info(F, d.ctypes.data, len(groups), lens.ctypes.data, flat.ctypes.data,
+                                   stride.ctypes.data, gof.ctypes.data, oof.ctypes.data)
+    if rc != 0:
+        raise ValueError("not a layout of %d fields: %r" % (F, groups))
+    return stride.tolist(), gof.tolist(), oof.tolist()
+
+
+def _ptrs(bufs):
+    arr = (ctypes.c_void_p * max(1, len(bufs)))()
+    for k, b in enumerate(bufs):
+        assert b.flags.c_contiguous
+        arr[k] = b.ctypes.data
+    return arr
+
+
+def remap(n, dtypes, src_groups, src_bufs, dst_groups):
+    """Byte remap of n records from src_groups (buffers src_bufs) to new buffers in dst_groups."""
+    F = len(dtypes)
+    d_stride, _, _ = layout_info(dtypes, dst_groups)
+    dst = [np.empty(n * s, dtype=np.uint8) for s in d_stride]
+    sl, sf = _i32([len(g) for g in src_groups]), _i32([f for g in src_groups for f in g])
+    dl, df = _i32([len(g) for g in dst_groups]), _i32([f for g in dst_groups for f in g])
+    srcb = [np.ascontiguousarray(b).view(np.uint8).reshape(-1) for b in src_bufs]
+    rc = _get().oracle_remap(n, F, _i32(dtypes).ctypes.data, len(src_groups), sl.ctypes.data, sf.ctypes.data,
+                             _ptrs(srcb), len(dst_groups), dl.ctypes.data, df.ctypes.data, _ptrs(dst))
+    if rc != 0:
+        raise ValueError("bad layout")
+    return dst
+
+
+def to_fields(n, dtypes, groups, bufs):
+    """Decode a layout's group buffers into one numpy array per field (via a remap to SoA)."""
+    F = len(dtypes)
+    out = remap(n, dtypes, groups, bufs, soa(F))
+    return [out[f].view(NP[dtypes[f]]) for f in range(F)]
+
+
+def from_fields(n, dtypes, groups, fields):
+    """Encode field arrays into the group buffers of a layout (via a remap from SoA)."""
+    F = len(dtypes)
+    src = [np.ascontiguousarray(fields[f], dtype=NP[dtypes[f]]).view(np.uint8) for f in range(F)]
+    return remap(n, dtypes, soa(F), src, groups)
+
+
+def tanhf(x):
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    y = np.empty_like(x)
+    _get().oracle_tanhf_n(x.ctypes.data, y.ctypes.data, x.size)
+    return y
+
+
+def tanh_coeffs():
+    p = np.zeros(13, dtype=np.float32)
+    q = np.zeros(13, dtype=np.float32)
+    k = _get().oracle_tanh_coeffs(p.ctypes.data, q.ctypes.data)
+    return k, p, q
+
+
+def _mask(s):
+    m = 0
+    for f in s:
+        m |= 1 << f
+    return m
+
+
+def section(sec, dtypes, fields, perm=None):
+    """Run one section (a synth.Section) in place on field arrays (list of numpy arrays)."""
+    n = fields[0].shape[0]
+    args = _i32(list(sec.args) + [0] * (8 - len(sec.args)))
+    par = np.ascontiguousarray(np.asarray(list(sec.params) + [0.0] * (4 - len(sec.params)), dtype=np.float32))
+    for a in fields:
+        assert a.flags.c_contiguous and a.shape[0] == n
+    pp = None
+    if sec.op == "gather":
+        pp = np.ascontiguousarray(perm, dtype=np.int32)
+        assert pp.shape[0] == n and (n == 0 or (pp.min() >= 0 and pp.max() < n))
+        pp = pp.ctypes.data
+    rc = _get().oracle_section(OPS[sec.op], args.ctypes.data, par.ctypes.data, _mask(sec.read),
+                               _mask(sec.write), len(dtypes), _i32(dtypes).ctypes.data, _ptrs(fields), n, pp)
+    if rc != 0:
+        raise ValueError("unknown op %r" % sec.op)
+
+
+def chain_grad(sections, fields, c):
+    """Final state (in place in `fields`, fp32 arrays) and dL/d(input) of an axpb/mul/tanh chain."""
+    n = fields[0].shape[0]
+    F = len(fields)
+    ops = _i32([OPS[s.op] for s in sections])
+    args = []
+    par = []
+    for s in sections:
+        if s.op == "mul":
+            args += [s.args[0], s.args[1], s.args[2]]
+        else:
+            args += [s.args[0], 0, s.args[1]]
+        par += list(s.params) if s.op == "axpb" else [0.0, 0.0]
+    args = _i32(args)
+    par = np.ascontiguousarray(np.asarray(par, dtype=np.float32))
+    cc = np.ascontiguousarray(np.asarray(c, dtype=np.float32))
+    grads = [np.empty(n, dtype=np.float32) for _ in range(F)]
+    rc = _get().oracle_chain_grad(len(sections), ops.ctypes.data, args.ctypes.data, par.ctypes.data, F,
+                                  _ptrs(fields), cc.ctypes.data, _ptrs(grads), n)
+    if rc != 0:
+        raise ValueError("chain_grad failed")
+    return grads

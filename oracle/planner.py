@@ -1,0 +1,129 @@
+"""Planner of the oracle (TEST INFRASTRUCTURE ONLY): ODS and PDL written out plainly.
+
+Paper, Section 2 ("Overall Framework"):
+  * ODS: an affinity graph whose nodes are the fields a section accesses and whose
+    edge weights count the two fields' common occurrences; a greedy clustering
+    under an architecture-dependent size limit; each cluster becomes a structure.
+  * PDL: a rooted DAG over the sections with "combine" and "remap" edges; a
+    shortest path through it, weighted by measured execution times, picks one
+    layout per section.
+Readings taken where the paper is silent (each one is listed in the design notes):
+  * the weight of edge (a, b) is the number of sections of the window whose
+    accessed fields (read, written, or read through the permutation) hold both;
+  * greedy: edges in order (weight descending, smaller id ascending, larger id
+    ascending); two clusters merge when the weight is positive and the merged
+    struct (fields ascending, natural alignment) is at most `cap` bytes
+    (cap <= 0: no limit); fields outside the window stay alone;
+  * a layout is canonical: fields ascending within a group, groups ordered by
+    their first field;
+  * candidates = AoS and SoA, then the ODS layout of every window of 1..W
+    consecutive sections under every cap, first occurrence kept;
+  * a "combine" is two consecutive sections keeping one layout (remap cost 0);
+  * the DAG is layered (input -> section 1 -> ... -> section S), so its shortest
+    path is a dynamic program over the layers; among equal costs the
+    lexicographically smallest sequence of layout indices wins.
+"""
+import itertools
+
+from .core import group_layout, aos, soa, canon
+
+
+def affinity(sections, F):
+    """Edge weights {(a, b): w}, a < b: sections whose accessed fields include both a and b."""
+    w = {}
+    for s in sections:
+        t = sorted(s.touched)
+        for i in range(len(t)):
+            for j in range(i + 1, len(t)):
+                w[(t[i], t[j])] = w.get((t[i], t[j]), 0) + 1
+    return w
+
+
+def ods(sections, dtypes, cap):
+    """Greedy clustering of the window's affinity graph under a struct-size cap (bytes)."""
+    F = len(dtypes)
+    w = affinity(sections, F)
+    cluster = {f: frozenset([f]) for f in range(F)}
+    for (a, b), wt in sorted(w.items(), key=lambda e: (-e[1], e[0][0], e[0][1])):
+        if wt <= 0 or cluster[a] is cluster[b]:
+            continue
+        merged = cluster[a] | cluster[b]
+        _, size = group_layout(dtypes, sorted(merged))
+        if cap is not None and cap > 0 and size > cap:
+            continue
+        for f in merged:
+            cluster[f] = merged
+    groups = {c for c in cluster.values()}
+    return canon([sorted(c) for c in groups])
+
+
+def candidates(sections, dtypes, caps, max_window=0, include_aos_soa=True, max_candidates=0):
+    """Deduplicated candidate layouts in generation order."""
+    F = len(dtypes)
+    S = len(sections)
+    out, seen = [], set()
+
+    def add(layout):
+        key = tuple(tuple(g) for g in layout)
+        if key not in seen:
+            seen.add(key)
+            out.append(layout)
+
+    if include_aos_soa:
+        add(aos(F))
+        add(soa(F))
+    W = S if max_window <= 0 else min(max_window, S)
+    for w in range(1, W + 1):
+        for k in range(0, S - w + 1):
+            for cap in caps:
+                add(ods(sections[k:k + w], dtypes, cap))
+    if max_candidates > 0:
+        out = out[:max_candidates]
+    return out
+
+
+def program_cost(seq, sec_cost, remap_cost, return_to_input=False):
+    """Model cost of one layout assignment: sum of section and remap costs (input layout = index L)."""
+    L = len(sec_cost[0])
+    total = remap_cost[L][seq[0]]
+    for k, l in enumerate(seq):
+        if k > 0:
+            total += remap_cost[seq[k - 1]][l]
+        total += sec_cost[k][l]
+    if return_to_input:
+        total += remap_cost[seq[-1]][L]
+    return total
+
+
+def pdl_exhaustive(sec_cost, remap_cost, return_to_input=False):
+    """Brute force over all L^S assignments: (min cost, lexicographically smallest argmin)."""
+    S, L = len(sec_cost), len(sec_cost[0])
+    return min((program_cost(seq, sec_cost, remap_cost, return_to_input), list(seq))
+               for seq in itertools.product(range(L), repeat=S))
+
+
+def pdl_dp(sec_cost, remap_cost, return_to_input=False):
+    """Shortest path through the layered DAG: (min cost, lexicographically smallest argmin).
+
+    rest[k][l] = cheapest cost of sections k..S-1 (and the final remap) when section k
+    runs in layout l; the path is then read forwards, taking the smallest index
+    among the layouts that reach the minimum.
+    """
+    S, L = len(sec_cost), len(sec_cost[0])
+    rest = [[0] * L for _ in range(S)]
+    for l in range(L):
+        rest[S - 1][l] = sec_cost[S - 1][l] + (remap_cost[l][L] if return_to_input else 0)
+    for k in range(S - 2, -1, -1):
+        for l in range(L):
+            rest[k][l] = sec_cost[k][l] + min(remap_cost[l][m] + rest[k + 1][m] for m in range(L))
+    seq = []
+    prev = L
+    for k in range(S):
+        vals = [remap_cost[prev][m] + rest[k][m] for m in range(L)]
+        best = min(vals)
+        m = vals.index(best)
+        if k == 0:
+            total = best
+        seq.append(m)
+        prev = m
+    return total, seq

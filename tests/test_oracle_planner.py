@@ -1,0 +1,103 @@
+"""Oracle pins: affinity graph, greedy grouping (ODS) and program layout choice (PDL), CPU only.
+
+ODS is pinned by hand-worked cases (tests/golden/ods_cases.txt, two of them the
+groupings printed in Tables 2 and 3 of the paper); the DP by brute-force
+enumeration of every assignment on small programs.
+"""
+import os
+import random
+
+import pytest
+
+import oracle
+from synth.workloads import Section
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "ods_cases.txt")
+DT = {"f32": 0, "f64": 1, "i32": 2, "bf16": 3}
+
+
+def _parse_list(spec):
+    out = []
+    for part in spec.split(","):
+        part = part.strip()
+        if "-" in part:
+            a, b = part.split("-")
+            out += list(range(int(a), int(b) + 1))
+        elif part:
+            out.append(int(part))
+    return out
+
+
+def _dtypes(spec):
+    out = []
+    for part in spec.split(","):
+        name, _, rep = part.strip().partition("*")
+        out += [DT[name]] * (int(rep) if rep else 1)
+    return out
+
+
+def golden_cases():
+    cases = []
+    for line in open(GOLDEN):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        name, dts, secs, cap, want = [x.strip() for x in line.split("|")]
+        sections = [Section("mix", (), frozenset(_parse_list(s)), frozenset(_parse_list(s)))
+                    for s in secs.split(";")]
+        layout = [_parse_list(g) for g in want.split("/")]
+        cases.append(pytest.param(_dtypes(dts), sections, int(cap), layout, id=name))
+    return cases
+
+
+@pytest.mark.parametrize("dtypes,sections,cap,want", golden_cases())
+def test_ods_golden(dtypes, sections, cap, want):
+    assert oracle.ods(sections, dtypes, cap) == want
+
+
+def test_affinity_counts_common_occurrences():
+    secs = [Section("mix", (), frozenset([0, 1, 2]), frozenset([0])),
+            Section("gather", (), frozenset([1]), frozenset([1]), frozenset([2, 3])),
+            Section("mix", (), frozenset([3]), frozenset([3]))]
+    w = oracle.affinity(secs, 4)
+    assert w == {(0, 1): 1, (0, 2): 1, (1, 2): 2, (1, 3): 1, (2, 3): 1}
+
+
+def test_untouched_fields_stay_alone_and_no_cap_gives_one_cluster():
+    secs = [Section("mix", (), frozenset([1, 3]), frozenset([3]))]
+    assert oracle.ods(secs, [0, 1, 2, 0, 3], 0) == [[0], [1, 3], [2], [4]]
+
+
+def test_candidates_order_and_dedup():
+    secs = [Section("mix", (), frozenset([0, 1]), frozenset([0])),
+            Section("mix", (), frozenset([2, 3]), frozenset([2]))]
+    c = oracle.candidates(secs, [0, 0, 0, 0], caps=[0, 4], max_window=0)
+    assert c[0] == [[0, 1, 2, 3]] and c[1] == [[0], [1], [2], [3]]
+    assert c[2:] == [[[0, 1], [2], [3]], [[0], [1], [2, 3]], [[0, 1], [2, 3]]]
+    assert len({tuple(map(tuple, x)) for x in c}) == len(c)
+
+
+def _random_costs(rng, S, L):
+    sec = [[rng.randrange(0, 20) for _ in range(L)] for _ in range(S)]
+    rem = [[0 if a == b else rng.randrange(0, 15) for b in range(L + 1)] for a in range(L + 1)]
+    return sec, rem
+
+
+@pytest.mark.parametrize("seed", range(60))
+def test_dp_equals_exhaustive(seed):
+    rng = random.Random(seed)
+    S, L = rng.randrange(1, 6), rng.randrange(1, 5)
+    sec, rem = _random_costs(rng, S, L)
+    back = bool(seed % 2)
+    assert oracle.pdl_dp(sec, rem, back) == oracle.pdl_exhaustive(sec, rem, back)
+
+
+def test_dp_hand_worked():
+    # two layouts: A is 1 per section, B is 10; moving A->B costs 5.  Section 2 costs 100 in A, 1 in B.
+    sec = [[1, 10], [100, 1], [1, 10]]
+    rem = [[0, 5, 0], [5, 0, 0], [0, 0, 0]]               # index 2 = the input layout (free to leave)
+    assert oracle.pdl_dp(sec, rem) == (1 + 5 + 1 + 5 + 1, [0, 1, 0])
+    # ties: every path costs 3 -> lexicographically smallest
+    assert oracle.pdl_dp([[1, 1], [1, 1], [1, 1]], [[0, 0, 0]] * 3) == (3, [0, 0, 0])
+    # returning to the input layout adds its remap
+    assert oracle.pdl_dp([[1, 0]], [[0, 0, 7], [0, 0, 1], [0, 0, 0]], True) == (1, [1])
