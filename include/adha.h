@@ -1,0 +1,194 @@
+/*
+ * adha.h -- C ABI of libadha.so, a GB300 (sm_103a) implementation of the data
+ * path of ADHA, the automatic data-layout framework of Majeti, Meel, Barik and
+ * Sarkar ("ADHA: Automatic Data layout framework for Heterogeneous
+ * Architectures", PACT 2014).
+ *
+ * Model (paper, Section 2 "Overall Framework"; Table 2):
+ *   - A record array holds n records of F fields (F <= 64), each field of one
+ *     of four types.  A *layout* splits the fields into ordered *groups*; each
+ *     group is stored as its own array of C structs (fields in listed order,
+ *     each at its natural alignment, struct size rounded up to the largest
+ *     alignment).  AoS is one group of all fields; SoA is one group per field.
+ *     Record i of group g starts at byte i * stride(g) of that group's buffer.
+ *     Padding bytes written by this library are zero.
+ *   - A *section* is one data-parallel loop over the records that reads and
+ *     writes some fields of each record (the paper's section).
+ *   - ODS picks a layout for a run of sections (affinity graph + greedy
+ *     grouping); PDL picks one layout per section for the whole program by a
+ *     shortest path whose edge weights are measured run and remap times.
+ *
+ * Conventions, for every entry point:
+ *   - Return 0 (ADHA_OK) on success, a negative ADHA_E* code on failure; the
+ *     calling thread's message is then in adha_last_error().  No C++ exception
+ *     crosses this boundary.  Arguments are validated before anything is
+ *     launched; a call that fails validation launches nothing.
+ *   - "device pointer" means memory the GPU can read/write (cudaMalloc,
+ *     PyTorch tensors); buffers are owned by the caller, must start on a
+ *     16-byte boundary, and must not overlap unless stated.  The library
+ *     allocates no device memory of its own: scratch comes from a caller
+ *     workspace whose size a *_workspace_bytes call returns.
+ *   - adha_stream is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *     that launch work are asynchronous on that stream unless stated.
+ *   - Result objects the library returns (layout sets, cost tables) are
+ *     allocated on the host and freed with adha_free.
+ */
+#ifndef ADHA_H_
+#define ADHA_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef void* adha_stream;
+
+enum {
+  ADHA_OK = 0,
+  ADHA_EINVAL = -1,   /* bad argument: the message names it                      */
+  ADHA_ENOMEM = -2,   /* workspace too small, or host allocation failed          */
+  ADHA_ECUDA = -3,    /* a CUDA runtime call failed: the message has its text    */
+  ADHA_ETIMEOUT = -4, /* a kernel gave up waiting for its copies (see adha_device_status) */
+  ADHA_ENOTIMPL = -5  /* not supported on this build or device                   */
+};
+
+#define ADHA_MAX_FIELDS 64
+#define ADHA_MAX_SECTIONS 256
+
+typedef enum { ADHA_F32 = 0, ADHA_F64 = 1, ADHA_I32 = 2, ADHA_BF16 = 3 } adha_dtype;
+
+/* n_fields fields; dtype[f] is an adha_dtype.  Host pointer, read during the call only. */
+typedef struct {
+  int32_t n_fields;
+  const int32_t* dtype;
+} adha_schema;
+
+/* Groups in order; group g lists group_len[g] field ids, concatenated in `fields`.
+ * Every field of the schema appears exactly once.  Host pointers. */
+typedef struct {
+  int32_t n_groups;
+  const int32_t* group_len;
+  const int32_t* fields;
+} adha_layout;
+
+/*
+ * Section ops.  arg[] holds operand field ids and fparam[] fp32 constants.
+ * Every floating-point operation is rounded to nearest on its own (no fused
+ * multiply-add), in the order written:
+ *   MADD3   (x,y,z):            z = x*y + z                                 fp32
+ *   XORSHIFT(x,z):              z = x ^ (x >> 3), logical shift              int32
+ *   ADD     (x,y,z):            z = x + y                                   fp32
+ *   MIX     (masks only):       over the read set in ascending field order,
+ *                               s = sum of fp32 fields, h = xor of int32 fields,
+ *                               of both 32-bit halves of fp64 fields and of
+ *                               bf16 bits; t = s + (h & 255) * 2^-8; then each
+ *                               written field w: fp32 w*0.5 + t, fp64
+ *                               w*0.5 + (double)t, int32 w ^ ((h ^ bits(t)) >> 3),
+ *                               bf16 bits w ^ low16 of the same
+ *   DRIFT   (px,py,pz,vx,vy,vz; dt):  p = p + dt*v, then p -= 1 if p >= 1, p += 1 if p < 0
+ *   BIN     (px,py,pz,cell; G):  c = clamp((int)(p*G), 0, G-1) per axis,
+ *                               cell = cx + G*(cy + G*cz)
+ *   KE      (vx,vy,vz,m,e):     e = (double)((0.5*m) * ((vx*vx + vy*vy) + vz*vz))   (fp32 arithmetic)
+ *   FLAGS   (fl,e; thr):         fl = ((fl << 1) | (e > thr)) & 255
+ *   GATHER  (vx,vy,vz,px,py,pz,q; dt): j = perm[i]; v[i] = v[i] + (dt*q[j]) * (p[j] - 0.5)
+ *   KICK    (vx,vy,vz,q; dt,Ex,Ey,Ez): v = v + (dt*q) * E
+ *   AXPB    (x,z; a,b):          z = a*x + b          MUL (x,y,z): z = x*y
+ *   TANH    (x,z):               z = adha tanh of x: Lambert's continued fraction
+ *                               x/(1 + x^2/(3 + x^2/(5 + ...))) cut after the
+ *                               partial denominator 25, written as x*Q(x^2)/P(x^2)
+ *                               with P, Q its exact integer polynomials rounded
+ *                               once to fp32 and evaluated by Horner's rule;
+ *                               copysign(1, x) for |x| >= 9
+ */
+typedef enum {
+  ADHA_OP_MADD3 = 1, ADHA_OP_XORSHIFT = 2, ADHA_OP_ADD = 3, ADHA_OP_MIX = 4, ADHA_OP_DRIFT = 5,
+  ADHA_OP_BIN = 6, ADHA_OP_KE = 7, ADHA_OP_FLAGS = 8, ADHA_OP_GATHER = 9, ADHA_OP_KICK = 10,
+  ADHA_OP_AXPB = 11, ADHA_OP_MUL = 12, ADHA_OP_TANH = 13
+} adha_op;
+
+/*
+ * One section (paper Section 2: a data-parallel loop with per-field accesses).
+ * read_mask / write_mask: fields read / written at record i (bit f = field f);
+ * read_at_perm_mask: fields read at record perm[i] (GATHER only).  The masks
+ * must contain the op's operands; extra read bits declare reads the op does
+ * not use (they still shape the affinity graph and what a section loads).
+ * perm: device pointer to n int32 record ids in [0,n) (GATHER only, else NULL);
+ * fields read through perm must not be written by the same section.
+ */
+typedef struct {
+  int32_t op;
+  int32_t arg[8];
+  float fparam[4];
+  uint64_t read_mask;
+  uint64_t write_mask;
+  uint64_t read_at_perm_mask;
+  const int32_t* perm;
+} adha_section;
+
+/* ---------------------------------------------------------------- layouts */
+
+/*
+ * Byte stride of every group and byte offset of every field in its group
+ * (the struct rule above).  stride[n_groups], offset[n_fields] are host
+ * arrays the caller provides.  Host only.
+ */
+int adha_layout_strides(const adha_schema* schema, const adha_layout* layout, int32_t* stride,
+                        int32_t* offset);
+
+/*
+ * Remap n records from layout src (group buffers src_ptrs[g], device) to
+ * layout dst (dst_ptrs[g], device): the byte permutation that moves every
+ * field of every record to its place in dst (paper Section 2, the remap edge;
+ * Table 4, "remap").  A dst group identical to a src group (same fields in the
+ * same order) whose pointer equals that src group's pointer is left alone (an
+ * alias); otherwise dst buffers must not overlap src buffers.  Buffer g holds
+ * n * stride(g) bytes.  Async on `stream`.
+ */
+int adha_remap(const adha_schema* schema, int64_t n, const adha_layout* src, const void* const* src_ptrs,
+               const adha_layout* dst, void* const* dst_ptrs, adha_stream stream);
+
+/*
+ * Run one section in place on n records stored in `layout` (group buffers
+ * ptrs[g], device).  save: NULL, or a device buffer of n elements of the
+ * written field's type that receives the values the section overwrites
+ * (AXPB, MUL, TANH only; used by adha_section_backward).  Async.
+ */
+int adha_run_section(const adha_schema* schema, int64_t n, const adha_layout* layout, void* const* ptrs,
+                     const adha_section* section, void* save, adha_stream stream);
+
+/*
+ * Reverse of one AXPB, MUL or TANH section for the chain gradient: restores
+ * the overwritten field z from `save` (written by adha_run_section) in the
+ * state buffers, then updates the adjoint buffers `grad_ptrs` (same layout,
+ * fp32 fields, one adjoint per field):
+ *   gz = g[z]; g[z] = 0;  AXPB: g[x] += a*gz;  MUL: g[x] += gz*y, then g[y] += gz*x;
+ *   TANH: t = tanh(x); g[x] += gz*(1 - t*t)      (x, y: values before the section)
+ * each operation rounded to nearest in fp32.  All fields must be fp32.  Async.
+ */
+int adha_section_backward(const adha_schema* schema, int64_t n, const adha_layout* layout,
+                          void* const* state_ptrs, void* const* grad_ptrs, const adha_section* section,
+                          const void* save, adha_stream stream);
+
+/*
+ * Reads and clears the device status word that kernels set when a bounded
+ * wait for their own copies ran out (then they stop early and their output is
+ * incomplete).  Synchronizes `stream`.  *status = 0 when nothing happened.
+ */
+int adha_device_status(adha_stream stream, int32_t* status);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char* adha_last_error(void);
+
+/* Frees a host object returned by this library (NULL is ignored). */
+void adha_free(void* p);
+
+/* Library version string. */
+const char* adha_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ADHA_H_ */

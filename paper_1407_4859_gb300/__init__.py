@@ -1,0 +1,10 @@
+"""GB300 (sm_103a) implementation of the ADHA data-layout path (Majeti et al., PACT 2014).
+
+The compute lives in libadha.so (hand-written CUDA, C ABI in include/adha.h); this package is
+its thin ctypes binding.  Importing it does not load the library; the first call does, and
+raises if the library has not been built.
+"""
+from .api import (  # noqa: F401
+    Schema, Layout, alloc_layout, c_section, adha_version, adha_layout_strides, adha_remap, adha_run_section,
+    adha_section_backward, adha_device_status, remap,
+)

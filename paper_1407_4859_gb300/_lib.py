@@ -1,0 +1,76 @@
+"""ctypes declarations of libadha.so (include/adha.h).  Loading fails loudly if the library is missing."""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libadha.so")
+
+ADHA_OK, ADHA_EINVAL, ADHA_ENOMEM, ADHA_ECUDA, ADHA_ETIMEOUT, ADHA_ENOTIMPL = 0, -1, -2, -3, -4, -5
+CODES = {-1: "ADHA_EINVAL", -2: "ADHA_ENOMEM", -3: "ADHA_ECUDA", -4: "ADHA_ETIMEOUT", -5: "ADHA_ENOTIMPL"}
+OPS = dict(madd3=1, xorshift=2, add=3, mix=4, drift=5, bin=6, ke=7, flags=8, gather=9, kick=10,
+           axpb=11, mul=12, tanh=13)
+
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+_PP = ctypes.POINTER(ctypes.c_void_p)
+
+
+class adha_schema(ctypes.Structure):
+    _fields_ = [("n_fields", _I32), ("dtype", ctypes.POINTER(_I32))]
+
+
+class adha_layout(ctypes.Structure):
+    _fields_ = [("n_groups", _I32), ("group_len", ctypes.POINTER(_I32)), ("fields", ctypes.POINTER(_I32))]
+
+
+class adha_section(ctypes.Structure):
+    _fields_ = [("op", _I32), ("arg", _I32 * 8), ("fparam", ctypes.c_float * 4), ("read_mask", ctypes.c_uint64),
+                ("write_mask", ctypes.c_uint64), ("read_at_perm_mask", ctypes.c_uint64), ("perm", _P)]
+
+
+class AdhaError(RuntimeError):
+    def __init__(self, code, fn, msg):
+        super().__init__("%s failed with %s: %s" % (fn, CODES.get(code, code), msg))
+        self.code = code
+
+
+_lib = None
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "adha_version": (ctypes.c_char_p, []),
+    "adha_last_error": (ctypes.c_char_p, []),
+    "adha_free": (None, [_P]),
+    "adha_layout_strides": (ctypes.c_int, [ctypes.POINTER(adha_schema), ctypes.POINTER(adha_layout),
+                                           ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
+    "adha_remap": (ctypes.c_int, [ctypes.POINTER(adha_schema), _I64, ctypes.POINTER(adha_layout), _PP,
+                                  ctypes.POINTER(adha_layout), _PP, _P]),
+    "adha_run_section": (ctypes.c_int, [ctypes.POINTER(adha_schema), _I64, ctypes.POINTER(adha_layout), _PP,
+                                        ctypes.POINTER(adha_section), _P, _P]),
+    "adha_section_backward": (ctypes.c_int, [ctypes.POINTER(adha_schema), _I64, ctypes.POINTER(adha_layout), _PP,
+                                             _PP, ctypes.POINTER(adha_section), _P, _P]),
+    "adha_device_status": (ctypes.c_int, [_P, ctypes.POINTER(_I32)]),
+}
+
+
+def load():
+    """The loaded libadha.so; raises if it has not been built (no fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libadha.so is not built (%s): run __graft_entry__.build() or "
+                              "python -m paper_1407_4859_gb300.build" % LIB_PATH)
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def check(rc, fn):
+    if rc != 0:
+        raise AdhaError(rc, fn, load().adha_last_error().decode())
+    return rc

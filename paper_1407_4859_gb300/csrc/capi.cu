@@ -1,0 +1,542 @@
+// capi.cu -- validation, layout model, launch planning and the extern "C" entry points of
+// libadha.so for the remap and section kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstring>
+#include <mutex>
+#include <set>
+
+#include "internal.h"
+
+namespace adha {
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string t_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  t_err = buf;
+  return code;
+}
+
+int cuda_fail(int err, const char* what) {
+  return fail(ADHA_ECUDA, "%s: %s", what, cudaGetErrorString((cudaError_t)err));
+}
+
+void clear_error() { t_err.clear(); }
+
+// ------------------------------------------------------------------ device state
+// Status word set by kernels whose bounded waits ran out (one per device, module memory).
+__device__ int g_status_word;
+
+static std::mutex g_mu;
+static int* g_status_ptr[256];
+static int g_sms[256];
+
+static int current_device(int* dev) {
+  cudaError_t e = cudaGetDevice(dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (*dev < 0 || *dev >= 256) return fail(ADHA_ENOTIMPL, "device ordinal %d out of range", *dev);
+  return 0;
+}
+
+int status_word(int** ptr) {
+  int dev;
+  if (int rc = current_device(&dev)) return rc;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_status_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_status_word);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(status)");
+    g_status_ptr[dev] = static_cast<int*>(p);
+  }
+  *ptr = g_status_ptr[dev];
+  return 0;
+}
+
+int sm_count(int* count) {
+  int dev;
+  if (int rc = current_device(&dev)) return rc;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_sms[dev]) {
+    cudaError_t e = cudaDeviceGetAttribute(&g_sms[dev], cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute(SM count)");
+  }
+  *count = g_sms[dev];
+  return 0;
+}
+
+// ------------------------------------------------------------------ layouts
+int group_struct(const int* dtype, const std::vector<int>& fields, std::vector<int>* offsets) {
+  int pos = 0, align = 1;
+  if (offsets) offsets->resize(fields.size());
+  for (size_t k = 0; k < fields.size(); ++k) {
+    const int sz = dtype_size(dtype[fields[k]]);
+    pos = (pos + sz - 1) / sz * sz;
+    if (offsets) (*offsets)[k] = pos;
+    pos += sz;
+    align = std::max(align, sz);
+  }
+  return (pos + align - 1) / align * align;
+}
+
+int check_schema(const adha_schema* schema) {
+  if (!schema) return fail(ADHA_EINVAL, "schema is NULL");
+  if (schema->n_fields < 1 || schema->n_fields > kMaxFields)
+    return fail(ADHA_EINVAL, "schema has %d fields (1..%d allowed)", schema->n_fields, kMaxFields);
+  if (!schema->dtype) return fail(ADHA_EINVAL, "schema dtype array is NULL");
+  for (int f = 0; f < schema->n_fields; ++f)
+    if (schema->dtype[f] < ADHA_F32 || schema->dtype[f] > ADHA_BF16)
+      return fail(ADHA_EINVAL, "field %d has unknown dtype %d", f, schema->dtype[f]);
+  return 0;
+}
+
+int make_layout(const adha_schema* schema, const adha_layout* layout, Layout* out, const char* what) {
+  if (int rc = check_schema(schema)) return rc;
+  const int F = schema->n_fields;
+  if (!layout) return fail(ADHA_EINVAL, "%s layout is NULL", what);
+  if (layout->n_groups < 1 || layout->n_groups > F)
+    return fail(ADHA_EINVAL, "%s layout has %d groups for %d fields", what, layout->n_groups, F);
+  if (!layout->group_len || !layout->fields) return fail(ADHA_EINVAL, "%s layout arrays are NULL", what);
+  out->F = F;
+  for (int f = 0; f < F; ++f) out->dtype[f] = schema->dtype[f];
+  out->n_groups = layout->n_groups;
+  out->groups.assign(layout->n_groups, {});
+  bool seen[kMaxFields] = {};
+  int p = 0;
+  for (int g = 0; g < layout->n_groups; ++g) {
+    const int len = layout->group_len[g];
+    if (len < 1 || p + len > F) return fail(ADHA_EINVAL, "%s layout group %d has bad length %d", what, g, len);
+    for (int k = 0; k < len; ++k) {
+      const int f = layout->fields[p + k];
+      if (f < 0 || f >= F) return fail(ADHA_EINVAL, "%s layout names field %d (schema has %d)", what, f, F);
+      if (seen[f]) return fail(ADHA_EINVAL, "%s layout lists field %d twice", what, f);
+      seen[f] = true;
+      out->groups[g].push_back(f);
+    }
+    p += len;
+  }
+  if (p != F) return fail(ADHA_EINVAL, "%s layout covers %d of %d fields", what, p, F);
+  for (int g = 0; g < out->n_groups; ++g) {
+    std::vector<int> off;
+    out->stride[g] = group_struct(out->dtype, out->groups[g], &off);
+    if (out->stride[g] > kMaxStride)
+      return fail(ADHA_EINVAL, "%s layout group %d is %d bytes (max %d)", what, g, out->stride[g], kMaxStride);
+    for (size_t k = 0; k < off.size(); ++k) {
+      out->group_of[out->groups[g][k]] = g;
+      out->offset_of[out->groups[g][k]] = off[k];
+    }
+  }
+  return 0;
+}
+
+bool same_group(const Layout& a, int ga, const Layout& b, int gb) { return a.groups[ga] == b.groups[gb]; }
+
+static int check_ptrs(const void* const* ptrs, int count, const char* what) {
+  if (!ptrs) return fail(ADHA_EINVAL, "%s pointer array is NULL", what);
+  for (int g = 0; g < count; ++g) {
+    if (!ptrs[g]) return fail(ADHA_EINVAL, "%s buffer %d is NULL", what, g);
+    if (reinterpret_cast<uintptr_t>(ptrs[g]) % 16 != 0)
+      return fail(ADHA_EINVAL, "%s buffer %d is not 16-byte aligned", what, g);
+  }
+  return 0;
+}
+
+static bool overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  return na && nb && x < y + nb && y < x + na;
+}
+
+// Records per tile so that one stage of `rec_bytes`-byte records is about `target` bytes.
+static int pick_tile(int rec_bytes, int target, int tmax) {
+  int T = rec_bytes > 0 ? target / rec_bytes : tmax;
+  T = T / 32 * 32;
+  return std::max(32, std::min(T, tmax));
+}
+
+static inline int align128(int64_t x) { return (int)((x + 127) / 128 * 128); }
+
+void tanh_coefficients(float p[8], float q[8]) {
+  // P_k = (2k+1) P_{k-1} + a P_{k-2}, Q_k likewise; P_{-1} = 1, P_0 = 1, Q_{-1} = 0, Q_0 = 1; k up to 12.
+  int64_t pm[8] = {1}, pc[8] = {1}, qm[8] = {0}, qc[8] = {1};
+  for (int k = 1; k <= 12; ++k) {
+    int64_t pn[8], qn[8];
+    for (int j = 0; j < 8; ++j) {
+      pn[j] = (2 * k + 1) * pc[j] + (j ? pm[j - 1] : 0);
+      qn[j] = (2 * k + 1) * qc[j] + (j ? qm[j - 1] : 0);
+    }
+    std::memcpy(pm, pc, sizeof pc);
+    std::memcpy(pc, pn, sizeof pc);
+    std::memcpy(qm, qc, sizeof qc);
+    std::memcpy(qc, qn, sizeof qc);
+  }
+  for (int j = 0; j < 8; ++j) {
+    p[j] = (float)pc[j];
+    q[j] = (float)qc[j];
+  }
+}
+
+// ------------------------------------------------------------------ remap planning
+struct RemapPlan {
+  RemapArgs args;
+  int unit = 4;
+  size_t smem = 0;
+  int grid = 1;
+  bool empty = true;
+};
+
+// Tile / stage override for the autotuner (0 = default rule).
+static thread_local int t_tile_override = 0, t_stage_override = 0;
+
+static int plan_remap(const Layout& S, const void* const* src_ptrs, const Layout& D, void* const* dst_ptrs, int64_t n,
+                      RemapPlan* plan) {
+  std::memset(&plan->args, 0, sizeof plan->args);
+  RemapArgs& a = plan->args;
+  std::vector<int> build;
+  for (int d = 0; d < D.n_groups; ++d) {
+    bool alias = false;
+    for (int j = 0; j < S.n_groups; ++j)
+      if (same_group(D, d, S, j) && dst_ptrs[d] == src_ptrs[j]) alias = true;
+    if (!alias) build.push_back(d);
+  }
+  plan->empty = build.empty() || n == 0;
+  if (plan->empty) return 0;
+  std::set<int> need_set;
+  int unit = 8;
+  for (int d : build)
+    for (int f : D.groups[d]) {
+      need_set.insert(S.group_of[f]);
+      unit = std::min(unit, dtype_size(D.dtype[f]));
+    }
+  std::vector<int> need(need_set.begin(), need_set.end());
+  // overlap: built dst vs needed src, built dst vs each other
+  for (size_t x = 0; x < build.size(); ++x) {
+    const size_t nd = (size_t)n * D.stride[build[x]];
+    for (int j : need)
+      if (overlap(dst_ptrs[build[x]], nd, src_ptrs[j], (size_t)n * S.stride[j]))
+        return fail(ADHA_EINVAL, "destination group %d overlaps source group %d", build[x], j);
+    for (size_t y = x + 1; y < build.size(); ++y)
+      if (overlap(dst_ptrs[build[x]], nd, dst_ptrs[build[y]], (size_t)n * D.stride[build[y]]))
+        return fail(ADHA_EINVAL, "destination groups %d and %d overlap", build[x], build[y]);
+  }
+  int src_rec = 0, dst_rec = 0;
+  for (int j : need) src_rec += S.stride[j];
+  for (int d : build) dst_rec += D.stride[d];
+  int T = t_tile_override ? t_tile_override : pick_tile(src_rec, 16384, 1024);
+  const int stages = t_stage_override ? t_stage_override : 4;
+  int n_slots = 0;
+  for (int d : build) n_slots += D.stride[d] / unit;
+  if (n_slots > kMaxSlots) return fail(ADHA_EINVAL, "destination records too wide (%d slots)", n_slots);
+  for (;;) {
+    a.n = n;
+    a.T = T;
+    a.S = stages;
+    a.n_full = n / T;
+    a.n_src = (int)need.size();
+    a.n_dst = (int)build.size();
+    int off = 0;
+    for (int k = 0; k < a.n_src; ++k) {
+      a.src[k] = static_cast<const uint8_t*>(src_ptrs[need[k]]);
+      a.s_stride[k] = S.stride[need[k]];
+      a.s_smem[k] = off;
+      off += align128((int64_t)T * a.s_stride[k]);
+    }
+    a.stage_bytes = off;
+    off = 0;
+    int slot0 = 0;
+    for (int k = 0; k < a.n_dst; ++k) {
+      const int d = build[k];
+      a.dst[k] = static_cast<uint8_t*>(dst_ptrs[d]);
+      a.d_stride[k] = D.stride[d];
+      a.d_smem[k] = off;
+      off += align128((int64_t)T * a.d_stride[k]);
+      a.d_nslot[k] = D.stride[d] / unit;
+      a.d_slot0[k] = slot0;
+      a.d_q[k] = kThreads / a.d_nslot[k];
+      a.d_rem[k] = kThreads % a.d_nslot[k];
+      for (int s = 0; s < a.d_nslot[k]; ++s) a.slot[slot0 + s] = kPadSlot;
+      for (int f : D.groups[d]) {
+        const int sg = S.group_of[f];
+        const int k_src = (int)(std::lower_bound(need.begin(), need.end(), sg) - need.begin());
+        for (int b = 0; b < dtype_size(D.dtype[f]); b += unit) {
+          const uint32_t addr = (uint32_t)(a.s_smem[k_src] + S.offset_of[f] + b);
+          a.slot[slot0 + (D.offset_of[f] + b) / unit] = addr | ((uint32_t)S.stride[sg] << 20);
+        }
+      }
+      slot0 += a.d_nslot[k];
+    }
+    a.out_bytes = off;
+    a.n_slots = slot0;
+    const size_t smem = remap_smem_bytes(a);
+    if (smem <= (size_t)kSmemLimit && (a.stage_bytes < (1 << 20))) {
+      plan->smem = smem;
+      break;
+    }
+    if (T <= 32) return fail(ADHA_EINVAL, "records too wide for a 32-record tile (%zu bytes)", smem);
+    T = std::max(32, T / 2 / 32 * 32);
+  }
+  plan->unit = unit;
+  int sms = 0, blocks = 0;
+  if (int rc = sm_count(&sms)) return rc;
+  if (int rc = remap_occupancy(unit, plan->smem, &blocks)) return rc;
+  if (blocks < 1) return fail(ADHA_ENOTIMPL, "remap kernel does not fit on an SM (%zu bytes smem)", plan->smem);
+  const int64_t slots = (int64_t)sms * blocks;
+  plan->grid = (int)std::max<int64_t>(1, std::min<int64_t>(a.n_full, slots));
+  return 0;
+}
+
+// ------------------------------------------------------------------ section planning
+static bool has(uint64_t m, int f) { return (m >> f) & 1ull; }
+
+static int check_section(const Layout& L, const adha_section* s, int64_t n, bool has_save) {
+  if (!s) return fail(ADHA_EINVAL, "section is NULL");
+  const int F = L.F;
+  const uint64_t all = F == 64 ? ~0ull : ((1ull << F) - 1);
+  if ((s->read_mask | s->write_mask | s->read_at_perm_mask) & ~all)
+    return fail(ADHA_EINVAL, "section masks name fields beyond %d", F);
+  struct Need {
+    int n;
+    int dt[8];
+    char role[8];   // 'r' read, 'w' written, 'b' both, 'p' read at perm
+  };
+  Need need{};
+  switch (s->op) {
+    case ADHA_OP_MADD3: need = {3, {ADHA_F32, ADHA_F32, ADHA_F32}, {'r', 'r', 'b'}}; break;
+    case ADHA_OP_XORSHIFT: need = {2, {ADHA_I32, ADHA_I32}, {'r', 'w'}}; break;
+    case ADHA_OP_ADD: need = {3, {ADHA_F32, ADHA_F32, ADHA_F32}, {'r', 'r', 'w'}}; break;
+    case ADHA_OP_MIX: need = {0, {}, {}}; break;
+    case ADHA_OP_DRIFT: need = {6, {0, 0, 0, 0, 0, 0}, {'b', 'b', 'b', 'r', 'r', 'r'}}; break;
+    case ADHA_OP_BIN: need = {4, {0, 0, 0, ADHA_I32}, {'r', 'r', 'r', 'w'}}; break;
+    case ADHA_OP_KE: need = {5, {0, 0, 0, 0, ADHA_F64}, {'r', 'r', 'r', 'r', 'w'}}; break;
+    case ADHA_OP_FLAGS: need = {2, {ADHA_I32, ADHA_F64}, {'b', 'r'}}; break;
+    case ADHA_OP_GATHER: need = {7, {0, 0, 0, 0, 0, 0, 0}, {'b', 'b', 'b', 'p', 'p', 'p', 'p'}}; break;
+    case ADHA_OP_KICK: need = {4, {0, 0, 0, 0}, {'b', 'b', 'b', 'r'}}; break;
+    case ADHA_OP_AXPB: need = {2, {0, 0}, {'r', 'w'}}; break;
+    case ADHA_OP_MUL: need = {3, {0, 0, 0}, {'r', 'r', 'w'}}; break;
+    case ADHA_OP_TANH: need = {2, {0, 0}, {'r', 'w'}}; break;
+    default: return fail(ADHA_EINVAL, "unknown section op %d", s->op);
+  }
+  for (int k = 0; k < need.n; ++k) {
+    const int f = s->arg[k];
+    if (f < 0 || f >= F) return fail(ADHA_EINVAL, "op %d operand %d is field %d (schema has %d)", s->op, k, f, F);
+    if (L.dtype[f] != need.dt[k])
+      return fail(ADHA_EINVAL, "op %d operand %d (field %d) has dtype %d, needs %d", s->op, k, f, L.dtype[f], need.dt[k]);
+    const char r = need.role[k];
+    if ((r == 'r' || r == 'b') && !has(s->read_mask, f))
+      return fail(ADHA_EINVAL, "op %d reads field %d but read_mask lacks it", s->op, f);
+    if ((r == 'w' || r == 'b') && !has(s->write_mask, f))
+      return fail(ADHA_EINVAL, "op %d writes field %d but write_mask lacks it", s->op, f);
+    if (r == 'p' && !has(s->read_at_perm_mask, f))
+      return fail(ADHA_EINVAL, "op %d reads field %d at perm[i] but read_at_perm_mask lacks it", s->op, f);
+  }
+  if (s->op == ADHA_OP_MIX && (s->write_mask & ~s->read_mask))
+    return fail(ADHA_EINVAL, "mix section writes fields it does not read");
+  if (s->op == ADHA_OP_GATHER) {
+    if (s->read_at_perm_mask & s->write_mask)
+      return fail(ADHA_EINVAL, "gather section writes a field it reads through perm");
+    if (n > 0 && !s->perm) return fail(ADHA_EINVAL, "gather section has no perm");
+  } else if (s->read_at_perm_mask) {
+    return fail(ADHA_EINVAL, "only gather sections read through perm");
+  }
+  if (has_save && s->op != ADHA_OP_AXPB && s->op != ADHA_OP_MUL && s->op != ADHA_OP_TANH)
+    return fail(ADHA_EINVAL, "save is only defined for axpb, mul and tanh sections");
+  return 0;
+}
+
+struct SectionPlan {
+  SectionArgs args;
+  size_t smem = 0;
+  int grid = 1;
+};
+
+static int plan_section(const Layout& L, void* const* ptrs, const adha_section* s, int64_t n, void* save,
+                        SectionPlan* plan) {
+  SectionArgs& a = plan->args;
+  std::memset(&a, 0, sizeof a);
+  uint64_t staged = s->read_mask;
+  if (s->op == ADHA_OP_MIX) staged |= s->write_mask;
+  if (save) staged |= 1ull << (s->op == ADHA_OP_MUL ? s->arg[2] : s->arg[1]);
+  std::vector<int> groups;
+  for (int g = 0; g < L.n_groups; ++g) {
+    bool any = false;
+    for (int f : L.groups[g]) any = any || has(staged, f);
+    if (any) groups.push_back(g);
+  }
+  int rec = 0;
+  for (int g : groups) rec += L.stride[g];
+  if (s->op == ADHA_OP_GATHER) rec += 4;
+  int T = t_tile_override ? t_tile_override : pick_tile(rec, 16384, 4096);
+  const int stages = t_stage_override ? t_stage_override : 4;
+  for (;;) {
+    a.n = n;
+    a.T = T;
+    a.S = stages;
+    a.n_full = n / T;
+    a.F = L.F;
+    a.op = s->op;
+    a.R = s->read_mask;
+    a.W = s->write_mask;
+    a.n_load = (int)groups.size();
+    int off = 0;
+    for (int f = 0; f < L.F; ++f) {
+      const int g = L.group_of[f];
+      a.f[f].g = static_cast<uint8_t*>(ptrs[g]) + L.offset_of[f];
+      a.f[f].gs = L.stride[g];
+      a.f[f].s0 = -1;
+      a.f[f].ss = 0;
+      a.f[f].dtype = L.dtype[f];
+    }
+    for (int k = 0; k < a.n_load; ++k) {
+      const int g = groups[k];
+      a.lsrc[k] = static_cast<const uint8_t*>(ptrs[g]);
+      a.l_stride[k] = L.stride[g];
+      a.l_smem[k] = off;
+      for (int f : L.groups[g]) {
+        a.f[f].s0 = off + L.offset_of[f];
+        a.f[f].ss = L.stride[g];
+      }
+      off += align128((int64_t)T * L.stride[g]);
+    }
+    if (s->op == ADHA_OP_GATHER) {
+      a.lsrc[a.n_load] = reinterpret_cast<const uint8_t*>(s->perm);
+      a.l_stride[a.n_load] = 4;
+      a.l_smem[a.n_load] = off;
+      off += align128((int64_t)T * 4);
+    }
+    a.stage_bytes = off;
+    plan->smem = section_smem_bytes(a);
+    if (plan->smem <= (size_t)kSmemLimit) break;
+    if (T <= 32) return fail(ADHA_EINVAL, "section records too wide for a 32-record tile");
+    T = std::max(32, T / 2 / 32 * 32);
+  }
+  for (int k = 0; k < 8; ++k) a.arg[k] = s->arg[k];
+  for (int k = 0; k < 4; ++k) a.par[k] = s->fparam[k];
+  tanh_coefficients(a.tanh_p, a.tanh_q);
+  a.perm = s->perm;
+  a.save = static_cast<uint8_t*>(save);
+  int sms = 0, blocks = 0;
+  if (int rc = sm_count(&sms)) return rc;
+  if (int rc = section_occupancy(s->op, plan->smem, &blocks)) return rc;
+  if (blocks < 1) return fail(ADHA_ENOTIMPL, "section kernel does not fit on an SM");
+  plan->grid = (int)std::max<int64_t>(1, std::min<int64_t>(a.n_full, (int64_t)sms * blocks));
+  return 0;
+}
+
+}  // namespace adha
+
+using namespace adha;
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char* adha_version(void) { return "adha-gb300 0.1 (sm_103a)"; }
+
+const char* adha_last_error(void) { return t_err.c_str(); }
+
+void adha_free(void* p) { std::free(p); }
+
+int adha_layout_strides(const adha_schema* schema, const adha_layout* layout, int32_t* stride, int32_t* offset) {
+  clear_error();
+  Layout L;
+  if (int rc = make_layout(schema, layout, &L, "")) return rc;
+  if (!stride || !offset) return fail(ADHA_EINVAL, "output arrays are NULL");
+  for (int g = 0; g < L.n_groups; ++g) stride[g] = L.stride[g];
+  for (int f = 0; f < L.F; ++f) offset[f] = L.offset_of[f];
+  return 0;
+}
+
+int adha_remap(const adha_schema* schema, int64_t n, const adha_layout* src, const void* const* src_ptrs,
+               const adha_layout* dst, void* const* dst_ptrs, adha_stream stream) {
+  clear_error();
+  Layout S, D;
+  if (int rc = make_layout(schema, src, &S, "source")) return rc;
+  if (int rc = make_layout(schema, dst, &D, "destination")) return rc;
+  if (n < 0) return fail(ADHA_EINVAL, "n = %lld is negative", (long long)n);
+  if (n == 0) return 0;
+  if (int rc = check_ptrs(src_ptrs, S.n_groups, "source")) return rc;
+  if (int rc = check_ptrs(reinterpret_cast<const void* const*>(dst_ptrs), D.n_groups, "destination")) return rc;
+  RemapPlan plan;
+  if (int rc = plan_remap(S, src_ptrs, D, dst_ptrs, n, &plan)) return rc;
+  if (plan.empty) return 0;
+  return launch_remap(plan.args, plan.unit, plan.grid, plan.smem, stream);
+}
+
+int adha_run_section(const adha_schema* schema, int64_t n, const adha_layout* layout, void* const* ptrs,
+                     const adha_section* section, void* save, adha_stream stream) {
+  clear_error();
+  Layout L;
+  if (int rc = make_layout(schema, layout, &L, "")) return rc;
+  if (n < 0) return fail(ADHA_EINVAL, "n = %lld is negative", (long long)n);
+  if (int rc = check_section(L, section, n, save != nullptr)) return rc;
+  if (n == 0) return 0;
+  if (int rc = check_ptrs(reinterpret_cast<const void* const*>(ptrs), L.n_groups, "layout")) return rc;
+  if (save && reinterpret_cast<uintptr_t>(save) % 4) return fail(ADHA_EINVAL, "save buffer is not 4-byte aligned");
+  if (section->op == ADHA_OP_GATHER && reinterpret_cast<uintptr_t>(section->perm) % 16)
+    return fail(ADHA_EINVAL, "perm is not 16-byte aligned");
+  SectionPlan plan;
+  if (int rc = plan_section(L, ptrs, section, n, save, &plan)) return rc;
+  return launch_section(plan.args, plan.grid, plan.smem, stream);
+}
+
+int adha_section_backward(const adha_schema* schema, int64_t n, const adha_layout* layout, void* const* state_ptrs,
+                          void* const* grad_ptrs, const adha_section* section, const void* save, adha_stream stream) {
+  clear_error();
+  Layout L;
+  if (int rc = make_layout(schema, layout, &L, "")) return rc;
+  for (int f = 0; f < L.F; ++f)
+    if (L.dtype[f] != ADHA_F32) return fail(ADHA_EINVAL, "backward needs fp32 fields (field %d is not)", f);
+  if (n < 0) return fail(ADHA_EINVAL, "n = %lld is negative", (long long)n);
+  if (!section) return fail(ADHA_EINVAL, "section is NULL");
+  if (section->op != ADHA_OP_AXPB && section->op != ADHA_OP_MUL && section->op != ADHA_OP_TANH)
+    return fail(ADHA_EINVAL, "backward is defined for axpb, mul and tanh sections only");
+  if (int rc = check_section(L, section, n, true)) return rc;
+  if (n == 0) return 0;
+  if (!save) return fail(ADHA_EINVAL, "save buffer is NULL");
+  if (int rc = check_ptrs(reinterpret_cast<const void* const*>(state_ptrs), L.n_groups, "state")) return rc;
+  if (int rc = check_ptrs(reinterpret_cast<const void* const*>(grad_ptrs), L.n_groups, "gradient")) return rc;
+  BackwardArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.n = n;
+  a.op = section->op;
+  const int x = section->arg[0];
+  const int y = section->op == ADHA_OP_MUL ? section->arg[1] : section->arg[0];
+  const int z = section->op == ADHA_OP_MUL ? section->arg[2] : section->arg[1];
+  a.x = x;
+  a.y = y;
+  a.z = z;
+  a.a = section->fparam[0];
+  const int fl[3] = {x, y, z};
+  for (int k = 0; k < 3; ++k) {
+    const int g = L.group_of[fl[k]];
+    a.s[k] = static_cast<uint8_t*>(state_ptrs[g]) + L.offset_of[fl[k]];
+    a.g[k] = static_cast<uint8_t*>(grad_ptrs[g]) + L.offset_of[fl[k]];
+    a.ss[k] = a.gs[k] = L.stride[g];
+  }
+  a.save = static_cast<const float*>(save);
+  tanh_coefficients(a.tanh_p, a.tanh_q);
+  return launch_backward(a, stream);
+}
+
+int adha_device_status(adha_stream stream, int32_t* status) {
+  clear_error();
+  if (!status) return fail(ADHA_EINVAL, "status is NULL");
+  int* word = nullptr;
+  if (int rc = status_word(&word)) return rc;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  int v = 0;
+  e = cudaMemcpy(&v, word, sizeof v, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "read status word");
+  e = cudaMemset(word, 0, sizeof v);
+  if (e != cudaSuccess) return cuda_fail(e, "clear status word");
+  *status = v;
+  return 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,127 @@
+"""GPU parity of the section kernels and the chain-section backward: bit-exact against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_util import to_device, from_device, assert_fields_equal, random_layout
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_1407_4859_gb300 import build
+    build.build()
+    import paper_1407_4859_gb300 as P
+    return P
+
+
+def _layouts(F, seed):
+    rng = np.random.default_rng(seed)
+    return [oracle.aos(F), oracle.soa(F), random_layout(rng, F), random_layout(rng, F)]
+
+
+def _check_section(P, wl, sec, groups, perm=None, save=False):
+    n = wl.n
+    fields = oracle.initial_fields(wl)
+    bufs = to_device(n, wl.dtypes, groups, fields)
+    dperm = torch.from_numpy(perm).cuda() if perm is not None else None
+    zf = None
+    sbuf = None
+    if save:
+        zf = sec.args[2] if sec.op == "mul" else sec.args[1]
+        sbuf = torch.empty(n, dtype=torch.float32, device="cuda")
+    P.adha_run_section(P.Schema(wl.dtypes), n, P.Layout(groups), bufs, P.c_section(sec, dperm), save=sbuf)
+    torch.cuda.synchronize()
+    assert P.adha_device_status() == 0
+    want = [a.copy() for a in fields]
+    oracle.section(sec, wl.dtypes, want, perm)
+    assert_fields_equal(from_device(n, wl.dtypes, groups, bufs), want, "%s in %r" % (sec.op, groups))
+    if save:
+        assert np.array_equal(sbuf.cpu().numpy(), fields[zf])
+
+
+@pytest.mark.parametrize("k", range(3))
+@pytest.mark.parametrize("n", [1, 33, 70001])
+def test_tiny_program_sections(P, k, n):
+    wl = synth.config1(n=n)
+    for groups in _layouts(wl.F, k):
+        _check_section(P, wl, wl.sections[k], groups)
+
+
+@pytest.mark.parametrize("k", range(9))
+def test_stress_sections(P, k):
+    wl = synth.config2(n=50021)
+    for groups in _layouts(wl.F, 10 + k):
+        _check_section(P, wl, wl.sections[k], groups)
+
+
+@pytest.mark.parametrize("k", range(10))
+def test_particle_sections(P, k):
+    wl = synth.config3(n=60013)
+    perm = wl.perm()
+    for groups in _layouts(wl.F, 20 + k):
+        _check_section(P, wl, wl.sections[k], groups, perm)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_mix_on_mixed_dtypes_with_bf16(P, seed):
+    wl = synth.tiny_workload(seed, F_max=12, n=9001)
+    flds = list(wl.fields)
+    flds[0] = synth.Field("b", synth.workloads.BF16, "RAW16")   # one bf16 field in every case
+    wl.fields = flds
+    for groups in _layouts(wl.F, 40 + seed):
+        for sec in wl.sections:
+            _check_section(P, wl, sec, groups)
+
+
+@pytest.mark.parametrize("k", range(12))
+def test_chain_sections_with_save(P, k):
+    wl = synth.config5(n=30011, n_sections=12)
+    for groups in _layouts(wl.F, 60 + k):
+        _check_section(P, wl, wl.sections[k], groups, save=True)
+
+
+@pytest.mark.parametrize("k", range(16))
+def test_chain_backward_single_section(P, k):
+    wl = synth.config5(n=20011, n_sections=16)
+    sec = wl.sections[k]
+    n = wl.n
+    fields = oracle.initial_fields(wl)
+    for groups in _layouts(wl.F, 80 + k):
+        S, L = P.Schema(wl.dtypes), P.Layout(groups)
+        state = to_device(n, wl.dtypes, groups, fields)
+        save = torch.empty(n, dtype=torch.float32, device="cuda")
+        cs = P.c_section(sec)
+        P.adha_run_section(S, n, L, state, cs, save=save)
+        c = [np.full(n, w, np.float32) for w in wl.loss_weights]
+        grads = to_device(n, wl.dtypes, groups, c)
+        P.adha_section_backward(S, n, L, state, grads, cs, save)
+        torch.cuda.synchronize()
+        st = [a.copy() for a in fields]
+        want_g = oracle.chain_grad([sec], st, wl.loss_weights)
+        assert_fields_equal(from_device(n, wl.dtypes, groups, grads), want_g, "grad %s" % sec.op)
+        assert_fields_equal(from_device(n, wl.dtypes, groups, state), fields, "restored state")
+
+
+def test_python_driven_tiny_program_every_assignment(P):
+    """All 2^3 AoS/SoA assignments of the 3-section tiny program, remaps included."""
+    import itertools
+    wl = synth.config1()
+    n = wl.n
+    fields = oracle.initial_fields(wl)
+    want = oracle.run_program_fields(wl, [a.copy() for a in fields])
+    S = P.Schema(wl.dtypes)
+    for seq in itertools.product([0, 1], repeat=3):
+        lay = [P.Layout.aos(6), P.Layout.soa(6)]
+        cur = P.Layout.aos(6)
+        bufs = to_device(n, wl.dtypes, oracle.aos(6), fields)
+        for k, l in enumerate(seq):
+            if lay[l] != cur:
+                bufs = P.remap(S, n, cur, bufs, lay[l])
+                cur = lay[l]
+            P.adha_run_section(S, n, cur, bufs, P.c_section(wl.sections[k]))
+        torch.cuda.synchronize()
+        assert_fields_equal(from_device(n, wl.dtypes, cur.groups, bufs), want, "assignment %r" % (seq,))
