@@ -171,6 +171,145 @@ int adha_section_backward(const adha_schema* schema, int64_t n, const adha_layou
                           void* const* state_ptrs, void* const* grad_ptrs, const adha_section* section,
                           const void* save, adha_stream stream);
 
+/* ----------------------------------------------------------- planning (host) */
+
+/* Options of candidate generation (ODS) and layout choice (PDL). */
+typedef struct {
+  int32_t n_caps;           /* struct-size limits (bytes) tried by ODS; a limit <= 0 means none    */
+  const int32_t* caps;      /* n_caps limits (host); n_caps = 0 runs ODS once without a limit       */
+  int32_t max_window;       /* ODS runs on every window of 1..max_window consecutive sections
+                               (0 = every window length)                                            */
+  int32_t include_aos_soa;  /* 1: the candidate list starts with AoS and SoA                        */
+  int32_t max_candidates;   /* keep the first this many candidates (0 = all)                        */
+  int32_t return_to_input;  /* PDL adds the remap back to the input layout after the last section  */
+} adha_plan_opts;
+
+/* A list of layouts over n_fields fields: layout l has n_groups[l] groups; its group
+ * lengths are group_len[l*n_fields ...] and its fields, group after group,
+ * fields[l*n_fields ...].  Host memory; library-made sets are freed with adha_free. */
+typedef struct {
+  int32_t n_fields;
+  int32_t n_layouts;
+  int32_t* n_groups;
+  int32_t* group_len;
+  int32_t* fields;
+} adha_layout_set;
+
+/* Measured costs in whole nanoseconds (stored as doubles, so sums are exact):
+ * section_ns[k*n_layouts + l] = time of section k in candidate l;
+ * remap_ns[a*(n_layouts+1) + b] = time of the remap from a to b, where index
+ * n_layouts stands for the input layout and identical groups cost nothing.
+ * Host memory, freed with adha_free. */
+typedef struct {
+  int32_t n_sections;
+  int32_t n_layouts;
+  double* section_ns;
+  double* remap_ns;
+} adha_cost_table;
+
+/*
+ * ODS of one run of sections (paper Section 2, "optimal data-layout of a
+ * section"): builds the affinity graph whose nodes are the fields and whose
+ * edge (a,b) weighs the number of sections accessing both (read, written or
+ * read through perm), then merges clusters greedily along edges in order of
+ * weight (descending; ties: smaller field id, then larger) while the merged
+ * struct (fields ascending, natural alignment) is at most cap_bytes (<= 0: no
+ * limit).  Fields the sections do not touch stay alone.  The result is
+ * canonical: fields ascending in a group, groups ordered by their first field.
+ * Outputs: *n_groups, group_len[<= n_fields], fields[n_fields] (host).  Host only.
+ */
+int adha_ods(const adha_schema* schema, const adha_section* sections, int32_t n_sec, int32_t cap_bytes,
+             int32_t* n_groups, int32_t* group_len, int32_t* fields);
+
+/*
+ * Candidate layouts of a program: AoS and SoA (if asked), then the ODS layout
+ * of every window of 1..max_window consecutive sections under every cap, in
+ * that order (window length, start, cap), first occurrence kept.  *out is a
+ * library-owned set (adha_free).  Host only.
+ */
+int adha_plan_sections(const adha_schema* schema, const adha_section* sections, int32_t n_sec,
+                       const adha_plan_opts* opts, adha_layout_set** out);
+
+/* A library-owned copy of n_layouts caller layouts (for example AoS and SoA only). */
+int adha_layout_set_create(int32_t n_fields, int32_t n_layouts, const adha_layout* layouts, adha_layout_set** out);
+
+/* A zeroed library-owned cost table of the given size (to fill by hand or in tests). */
+int adha_cost_table_create(int32_t n_sections, int32_t n_layouts, adha_cost_table** out);
+
+/*
+ * PDL (paper Section 2, "program data-layout"): the shortest path through the
+ * layered DAG input -> (section 1, l) -> ... -> (section S, l), node weight
+ * section_ns, edge weight remap_ns (zero when the layout stays: the paper's
+ * combine edge), plus the remap back to the input layout if return_to_input.
+ * Ties go to the lexicographically smallest sequence of candidate indices.
+ * Writes layout_of_section[n_sections] and the path cost.  Host only.
+ */
+int adha_pdl_solve(const adha_cost_table* costs, int32_t return_to_input, int32_t* layout_of_section,
+                   double* total_ns);
+
+/* ----------------------------------------------------------- measure and run */
+
+/* A program's layout plan and where its result ended up. */
+typedef struct {
+  int32_t fixed;                                  /* in: 1 = run layout_of_section as given; 0 = solve PDL */
+  int32_t n_sections;                             /* out */
+  int32_t layout_of_section[ADHA_MAX_SECTIONS];   /* in when fixed, else out: candidate per section */
+  double model_ns;                                /* out: sum of the cost-table entries on the path (0 without a table) */
+  int32_t n_remaps;                               /* out: layout changes performed */
+  int32_t n_launches;                             /* out: kernels launched */
+  int32_t final_layout;                           /* out: candidate equal to the result's layout, -1 if none */
+  int32_t final_n_groups;                         /* out: groups of the result's layout */
+  void* final_ptrs[ADHA_MAX_FIELDS];              /* out: device buffers of the result's groups */
+} adha_plan;
+
+/* Workspace bytes adha_measure needs: two copies of the widest candidate (or input) layout. */
+size_t adha_measure_workspace_bytes(const adha_schema* schema, int64_t n, const adha_layout* in_layout,
+                                    const adha_layout_set* candidates);
+
+/*
+ * The tuning profile of PDL (paper Section 2: execution times measured per
+ * section and device): times every section in every candidate layout and every
+ * remap between two candidates (and from / to the input layout) on the
+ * caller's data: the input (layout in_layout, device buffers in_ptrs) is first
+ * copied into the workspace, so it is not modified.  Each entry is one warm-up
+ * call, then the faster of two batches of `reps` calls timed with CUDA events
+ * on `stream`, in whole nanoseconds.  A remap between layouts sharing a group
+ * leaves that group in place, as the executor does.  Synchronizes `stream`;
+ * *out is a library-owned table (adha_free).
+ */
+int adha_measure(const adha_schema* schema, int64_t n, const adha_layout* in_layout, void* const* in_ptrs,
+                 const adha_section* sections, int32_t n_sec, const adha_layout_set* candidates, int32_t reps,
+                 void* workspace, size_t ws_bytes, adha_stream stream, adha_cost_table** out);
+
+/* Workspace bytes adha_run_program needs: three copies of the widest candidate layout. */
+size_t adha_program_workspace_bytes(const adha_schema* schema, int64_t n, const adha_layout* in_layout,
+                                    const adha_layout_set* candidates);
+
+/*
+ * Runs a program (paper Section 2 and Table 4): picks one candidate layout per
+ * section by PDL on `costs` (unless plan->fixed), then enqueues on `stream`, in
+ * order, the remap into each section's layout when it differs from the current
+ * one and the section itself, in place.  The data start in in_layout / in_ptrs
+ * (device); groups shared by consecutive layouts stay where they are (so input
+ * buffers are updated in place while their group survives); other groups are
+ * placed in the workspace (device, ws_bytes from adha_program_workspace_bytes).
+ * With opts->return_to_input the result is remapped back into in_ptrs.  The
+ * result's buffers are listed in plan->final_ptrs.  Asynchronous; no device
+ * memory is allocated and nothing synchronizes, so the call can be captured in
+ * a CUDA graph.
+ */
+int adha_run_program(const adha_schema* schema, int64_t n, const adha_layout* in_layout, void* const* in_ptrs,
+                     const adha_section* sections, int32_t n_sec, const adha_layout_set* candidates,
+                     const adha_cost_table* costs, const adha_plan_opts* opts, void* workspace, size_t ws_bytes,
+                     adha_stream stream, adha_plan* plan);
+
+/*
+ * Records per warp chunk (a multiple of 32 up to 1024; 0 = automatic) that the
+ * remap and section kernels launched later by the calling thread use.  The
+ * autotuner sets it while it times candidates.  Host only.
+ */
+int adha_tune_override(int32_t chunk_records);
+
 /*
  * Reads and clears the device status word that kernels set when a bounded
  * wait for their own copies ran out (then they stop early and their output is

@@ -29,6 +29,31 @@ class adha_section(ctypes.Structure):
                 ("write_mask", ctypes.c_uint64), ("read_at_perm_mask", ctypes.c_uint64), ("perm", _P)]
 
 
+class adha_plan_opts(ctypes.Structure):
+    _fields_ = [("n_caps", _I32), ("caps", ctypes.POINTER(_I32)), ("max_window", _I32), ("include_aos_soa", _I32),
+                ("max_candidates", _I32), ("return_to_input", _I32)]
+
+
+class adha_layout_set(ctypes.Structure):
+    _fields_ = [("n_fields", _I32), ("n_layouts", _I32), ("n_groups", ctypes.POINTER(_I32)),
+                ("group_len", ctypes.POINTER(_I32)), ("fields", ctypes.POINTER(_I32))]
+
+
+class adha_cost_table(ctypes.Structure):
+    _fields_ = [("n_sections", _I32), ("n_layouts", _I32), ("section_ns", ctypes.POINTER(ctypes.c_double)),
+                ("remap_ns", ctypes.POINTER(ctypes.c_double))]
+
+
+MAX_SECTIONS = 256
+MAX_FIELDS = 64
+
+
+class adha_plan(ctypes.Structure):
+    _fields_ = [("fixed", _I32), ("n_sections", _I32), ("layout_of_section", _I32 * MAX_SECTIONS),
+                ("model_ns", ctypes.c_double), ("n_remaps", _I32), ("n_launches", _I32), ("final_layout", _I32),
+                ("final_n_groups", _I32), ("final_ptrs", _P * MAX_FIELDS)]
+
+
 class AdhaError(RuntimeError):
     def __init__(self, code, fn, msg):
         super().__init__("%s failed with %s: %s" % (fn, CODES.get(code, code), msg))
@@ -51,6 +76,27 @@ SIGNATURES = {
     "adha_section_backward": (ctypes.c_int, [ctypes.POINTER(adha_schema), _I64, ctypes.POINTER(adha_layout), _PP,
                                              _PP, ctypes.POINTER(adha_section), _P, _P]),
     "adha_device_status": (ctypes.c_int, [_P, ctypes.POINTER(_I32)]),
+    "adha_tune_override": (ctypes.c_int, [_I32]),
+    "adha_ods": (ctypes.c_int, [ctypes.POINTER(adha_schema), ctypes.POINTER(adha_section), _I32, _I32,
+                                ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
+    "adha_plan_sections": (ctypes.c_int, [ctypes.POINTER(adha_schema), ctypes.POINTER(adha_section), _I32,
+                                          ctypes.POINTER(adha_plan_opts), ctypes.POINTER(ctypes.POINTER(adha_layout_set))]),
+    "adha_layout_set_create": (ctypes.c_int, [_I32, _I32, ctypes.POINTER(adha_layout),
+                                              ctypes.POINTER(ctypes.POINTER(adha_layout_set))]),
+    "adha_cost_table_create": (ctypes.c_int, [_I32, _I32, ctypes.POINTER(ctypes.POINTER(adha_cost_table))]),
+    "adha_pdl_solve": (ctypes.c_int, [ctypes.POINTER(adha_cost_table), _I32, ctypes.POINTER(_I32),
+                                      ctypes.POINTER(ctypes.c_double)]),
+    "adha_measure_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(adha_schema), _I64, ctypes.POINTER(adha_layout),
+                                                       ctypes.POINTER(adha_layout_set)]),
+    "adha_measure": (ctypes.c_int, [ctypes.POINTER(adha_schema), _I64, ctypes.POINTER(adha_layout), _PP,
+                                    ctypes.POINTER(adha_section), _I32, ctypes.POINTER(adha_layout_set), _I32, _P,
+                                    ctypes.c_size_t, _P, ctypes.POINTER(ctypes.POINTER(adha_cost_table))]),
+    "adha_program_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(adha_schema), _I64, ctypes.POINTER(adha_layout),
+                                                       ctypes.POINTER(adha_layout_set)]),
+    "adha_run_program": (ctypes.c_int, [ctypes.POINTER(adha_schema), _I64, ctypes.POINTER(adha_layout), _PP,
+                                        ctypes.POINTER(adha_section), _I32, ctypes.POINTER(adha_layout_set),
+                                        ctypes.POINTER(adha_cost_table), ctypes.POINTER(adha_plan_opts), _P,
+                                        ctypes.c_size_t, _P, ctypes.POINTER(adha_plan)]),
 }
 
 

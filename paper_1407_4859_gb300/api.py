@@ -8,7 +8,8 @@ import ctypes
 import torch
 
 from . import _lib
-from ._lib import adha_schema, adha_layout, adha_section, OPS, check
+from ._lib import (adha_schema, adha_layout, adha_section, adha_plan_opts, adha_layout_set, adha_cost_table,
+                   adha_plan, OPS, check)
 
 DTYPE_SIZE = {0: 4, 1: 8, 2: 4, 3: 2}
 
@@ -125,6 +126,10 @@ def adha_section_backward(schema, n, layout, state_bufs, grad_bufs, section, sav
                                             save.data_ptr(), _stream_ptr(stream)), "adha_section_backward")
 
 
+def adha_tune_override(chunk_records=0):
+    check(_lib.load().adha_tune_override(int(chunk_records)), "adha_tune_override")
+
+
 def adha_device_status(stream=None):
     v = ctypes.c_int32(0)
     check(_lib.load().adha_device_status(_stream_ptr(stream), ctypes.byref(v)), "adha_device_status")
@@ -136,3 +141,195 @@ def remap(schema, n, src_layout, src_bufs, dst_layout, stream=None):
     dst = alloc_layout(schema, dst_layout, n, device=src_bufs[0].device)
     adha_remap(schema, n, src_layout, src_bufs, dst_layout, dst, stream)
     return dst
+
+
+# ------------------------------------------------------------------ planning, measuring, running
+
+class PlanOpts:
+    """adha_plan_opts: ODS struct-size limits, window length, candidate cap, return to input."""
+
+    def __init__(self, caps=(16, 32, 64, 128, 256, 0), max_window=0, include_aos_soa=True, max_candidates=0,
+                 return_to_input=False):
+        self._caps = _i32_array(list(caps))
+        self.c = adha_plan_opts(len(caps), self._caps, int(max_window), int(bool(include_aos_soa)),
+                                int(max_candidates), int(bool(return_to_input)))
+
+
+class Sections:
+    """A contiguous adha_section array (keeps the perm tensors it points to alive)."""
+
+    def __init__(self, secs, perm=None):
+        self.src = list(secs)
+        self.perm = perm
+        self.arr = (adha_section * len(self.src))()
+        for k, s in enumerate(self.src):
+            self.arr[k] = c_section(s, perm) if not isinstance(s, adha_section) else s
+
+    def __len__(self):
+        return len(self.src)
+
+
+class LayoutSet:
+    """A library-owned adha_layout_set (freed with adha_free)."""
+
+    def __init__(self, ptr):
+        self.ptr = ptr
+
+    @property
+    def layouts(self):
+        s = self.ptr.contents
+        F = s.n_fields
+        out = []
+        for l in range(s.n_layouts):
+            groups, p = [], 0
+            for g in range(s.n_groups[l]):
+                n = s.group_len[l * F + g]
+                groups.append([s.fields[l * F + p + j] for j in range(n)])
+                p += n
+            out.append(Layout(groups))
+        return out
+
+    def __len__(self):
+        return self.ptr.contents.n_layouts
+
+    def __del__(self):
+        if getattr(self, "ptr", None) is not None and _lib._lib is not None:
+            _lib._lib.adha_free(ctypes.cast(self.ptr, ctypes.c_void_p))
+            self.ptr = None
+
+
+class CostTable:
+    """A library-owned adha_cost_table; section_ns[k][l] and remap_ns[a][b] in nanoseconds."""
+
+    def __init__(self, ptr):
+        self.ptr = ptr
+
+    @property
+    def section_ns(self):
+        t = self.ptr.contents
+        return [[t.section_ns[k * t.n_layouts + l] for l in range(t.n_layouts)] for k in range(t.n_sections)]
+
+    @property
+    def remap_ns(self):
+        t = self.ptr.contents
+        L = t.n_layouts + 1
+        return [[t.remap_ns[a * L + b] for b in range(L)] for a in range(L)]
+
+    def set(self, section_ns, remap_ns):
+        t = self.ptr.contents
+        for k, row in enumerate(section_ns):
+            for l, v in enumerate(row):
+                t.section_ns[k * t.n_layouts + l] = float(v)
+        for a, row in enumerate(remap_ns):
+            for b, v in enumerate(row):
+                t.remap_ns[a * (t.n_layouts + 1) + b] = float(v)
+
+    def __del__(self):
+        if getattr(self, "ptr", None) is not None and _lib._lib is not None:
+            _lib._lib.adha_free(ctypes.cast(self.ptr, ctypes.c_void_p))
+            self.ptr = None
+
+
+def adha_ods(schema, sections, cap_bytes=0):
+    secs = sections if isinstance(sections, Sections) else Sections(sections)
+    ng = ctypes.c_int32(0)
+    gl = (ctypes.c_int32 * schema.F)()
+    fl = (ctypes.c_int32 * schema.F)()
+    check(_lib.load().adha_ods(ctypes.byref(schema.c), secs.arr, len(secs), int(cap_bytes), ctypes.byref(ng), gl, fl),
+          "adha_ods")
+    groups, p = [], 0
+    for g in range(ng.value):
+        groups.append([fl[p + j] for j in range(gl[g])])
+        p += gl[g]
+    return Layout(groups)
+
+
+def adha_plan_sections(schema, sections, opts=None):
+    secs = sections if isinstance(sections, Sections) else Sections(sections)
+    opts = opts or PlanOpts()
+    out = ctypes.POINTER(adha_layout_set)()
+    check(_lib.load().adha_plan_sections(ctypes.byref(schema.c), secs.arr, len(secs), ctypes.byref(opts.c),
+                                         ctypes.byref(out)), "adha_plan_sections")
+    return LayoutSet(out)
+
+
+def adha_layout_set_create(F, layouts):
+    arr = (adha_layout * len(layouts))(*[l.c for l in layouts])
+    out = ctypes.POINTER(adha_layout_set)()
+    check(_lib.load().adha_layout_set_create(F, len(layouts), arr, ctypes.byref(out)), "adha_layout_set_create")
+    return LayoutSet(out)
+
+
+def adha_cost_table_create(n_sections, n_layouts):
+    out = ctypes.POINTER(adha_cost_table)()
+    check(_lib.load().adha_cost_table_create(n_sections, n_layouts, ctypes.byref(out)), "adha_cost_table_create")
+    return CostTable(out)
+
+
+def adha_pdl_solve(costs, return_to_input=False):
+    S = costs.ptr.contents.n_sections
+    seq = (ctypes.c_int32 * S)()
+    tot = ctypes.c_double(0)
+    check(_lib.load().adha_pdl_solve(costs.ptr, int(bool(return_to_input)), seq, ctypes.byref(tot)), "adha_pdl_solve")
+    return tot.value, list(seq)
+
+
+def adha_measure_workspace_bytes(schema, n, in_layout, candidates):
+    return _lib.load().adha_measure_workspace_bytes(ctypes.byref(schema.c), int(n), ctypes.byref(in_layout.c),
+                                                    candidates.ptr)
+
+
+def adha_measure(schema, n, in_layout, in_bufs, sections, candidates, reps=2, workspace=None, stream=None):
+    """Cost table of every section in every candidate and every remap between candidates."""
+    secs = sections if isinstance(sections, Sections) else Sections(sections)
+    need = adha_measure_workspace_bytes(schema, n, in_layout, candidates)
+    ws = workspace if workspace is not None else torch.empty(need, dtype=torch.uint8, device=in_bufs[0].device)
+    out = ctypes.POINTER(adha_cost_table)()
+    check(_lib.load().adha_measure(ctypes.byref(schema.c), int(n), ctypes.byref(in_layout.c), _ptrs(in_bufs),
+                                   secs.arr, len(secs), candidates.ptr, int(reps), ws.data_ptr(), ws.numel(),
+                                   _stream_ptr(stream), ctypes.byref(out)), "adha_measure")
+    return CostTable(out)
+
+
+def adha_program_workspace_bytes(schema, n, in_layout, candidates):
+    return _lib.load().adha_program_workspace_bytes(ctypes.byref(schema.c), int(n), ctypes.byref(in_layout.c),
+                                                    candidates.ptr)
+
+
+def adha_run_program(schema, n, in_layout, in_bufs, sections, candidates, costs=None, opts=None, workspace=None,
+                     fixed=None, stream=None, plan=None):
+    """Runs the program; returns the adha_plan (layout per section, final buffers' pointers)."""
+    secs = sections if isinstance(sections, Sections) else Sections(sections)
+    opts = opts or PlanOpts()
+    if plan is None:
+        plan = adha_plan()
+    plan.fixed = 0
+    if fixed is not None:
+        plan.fixed = 1
+        for k, l in enumerate(fixed):
+            plan.layout_of_section[k] = int(l)
+    check(_lib.load().adha_run_program(ctypes.byref(schema.c), int(n), ctypes.byref(in_layout.c), _ptrs(in_bufs),
+                                       secs.arr, len(secs), candidates.ptr, costs.ptr if costs is not None else None,
+                                       ctypes.byref(opts.c), workspace.data_ptr() if workspace is not None else None,
+                                       workspace.numel() if workspace is not None else 0, _stream_ptr(stream),
+                                       ctypes.byref(plan)), "adha_run_program")
+    return plan
+
+
+def final_buffers(plan, schema, n, candidates, in_layout, workspace_views=None):
+    """(layout, list of uint8 device tensors viewing the result's groups) of a finished program."""
+    layouts = candidates.layouts
+    lay = layouts[plan.final_layout] if plan.final_layout >= 0 else in_layout
+    strides, _ = adha_layout_strides(schema, lay)
+    out = []
+    for g, st in enumerate(strides):
+        out.append(_view_device(plan.final_ptrs[g], n * st))
+    return lay, out
+
+
+def _view_device(ptr, nbytes):
+    """A uint8 CUDA tensor aliasing nbytes at ptr (memory owned elsewhere)."""
+    class _Cuda:
+        __cuda_array_interface__ = {"shape": (int(nbytes),), "typestr": "|u1", "data": (int(ptr), False),
+                                    "version": 3, "strides": None}
+    return torch.as_tensor(_Cuda(), device="cuda")

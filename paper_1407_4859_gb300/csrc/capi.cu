@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cstdarg>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <set>
 
@@ -153,14 +154,6 @@ static bool overlap(const void* a, size_t na, const void* b, size_t nb) {
   return na && nb && x < y + nb && y < x + na;
 }
 
-// Records per tile so that one stage of `rec_bytes`-byte records is about `target` bytes.
-static int pick_tile(int rec_bytes, int target, int tmax) {
-  int T = rec_bytes > 0 ? target / rec_bytes : tmax;
-  T = T / 32 * 32;
-  return std::max(32, std::min(T, tmax));
-}
-
-static inline int align128(int64_t x) { return (int)((x + 127) / 128 * 128); }
 
 void tanh_coefficients(float p[8], float q[8]) {
   // P_k = (2k+1) P_{k-1} + a P_{k-2}, Q_k likewise; P_{-1} = 1, P_0 = 1, Q_{-1} = 0, Q_0 = 1; k up to 12.
@@ -185,14 +178,116 @@ void tanh_coefficients(float p[8], float q[8]) {
 // ------------------------------------------------------------------ remap planning
 struct RemapPlan {
   RemapArgs args;
-  int unit = 4;
   size_t smem = 0;
   int grid = 1;
   bool empty = true;
 };
 
-// Tile / stage override for the autotuner (0 = default rule).
-static thread_local int t_tile_override = 0, t_stage_override = 0;
+// Chunk / pipeline override for the autotuner (0 = default rule).
+static thread_local int t_tile_override = 0;
+
+// Records per warp chunk: a multiple of 32 with about `target` bytes of the widest side.
+static int pick_chunk(int rec_bytes, int target, int rmax) {
+  int m = rec_bytes > 0 ? target / (32 * rec_bytes) : rmax / 32;
+  m = std::max(1, std::min(m, rmax / 32));
+  return 32 * m;
+}
+
+static int finish_grid(int64_t n_chunks, int blocks, int* grid) {
+  int sms = 0;
+  if (int rc = sm_count(&sms)) return rc;
+  if (blocks < 1) return fail(ADHA_ENOTIMPL, "kernel does not fit on an SM");
+  const int64_t need = (n_chunks + 1 + kWarps - 1) / kWarps;   // +1: the tail's owner
+  *grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * blocks, need));
+  return 0;
+}
+
+// Shared-memory wavefronts of one chunk's element moves in schedule order `order` (the kernel's
+// table): per warp step of 32 elements, the largest number of distinct 4-byte words that fall
+// in one bank, on the read side plus the write side.
+static int step_wavefronts(const uint32_t* bytes, int cnt, int u) {
+  uint32_t words[64];
+  int m = 0;
+  for (int l = 0; l < cnt; ++l) {
+    if (bytes[l] == 0xFFFFFFFFu) continue;
+    for (int w = 0; w < (u + 3) / 4; ++w) words[m++] = bytes[l] / 4 + w;
+  }
+  std::sort(words, words + m);
+  m = (int)(std::unique(words, words + m) - words);
+  int per_bank[32] = {};
+  int worst = 1;
+  for (int k = 0; k < m; ++k) worst = std::max(worst, ++per_bank[words[k] % 32]);
+  return worst;
+}
+
+static long remap_conflict_cost(const RemapArgs& a, int order) {
+  const int u = a.unit;
+  long cost = 0;
+  uint32_t rd[32], wr[32];
+  int dd = 0, ee = 0;
+  for (int t = 0; t < a.n_elems; t += 32) {
+    const int cnt = std::min(32, a.n_elems - t);
+    for (int l = 0; l < cnt; ++l) {
+      const int tt = t + l;
+      while (tt >= ee + a.R * a.d_nslot[dd]) ee += a.R * a.d_nslot[dd++];
+      const int S = a.d_nslot[dd];
+      int r, k;
+      if (order == 0) {
+        r = (tt - ee) / S;
+        k = (tt - ee) - r * S;
+      } else {
+        k = (tt - ee) / a.R;
+        r = (tt - ee) - k * a.R;
+      }
+      const uint32_t code = a.slot[a.d_slot0[dd] + k];
+      rd[l] = code == kPadSlot ? 0xFFFFFFFFu
+                               : (uint32_t)(a.src[code >> 16].start + r * a.src[code >> 16].stride + (int)(code & 0xFFFFu));
+      wr[l] = (uint32_t)((ee + r * S + k) * u);
+    }
+    cost += step_wavefronts(rd, cnt, u) + step_wavefronts(wr, cnt, u);
+  }
+  return cost;
+}
+
+// The schedule order depends only on the two layouts' moved groups and the chunk size.
+static std::mutex g_order_mu;
+static std::map<std::vector<int32_t>, int> g_order_cache;
+
+static int choose_order(const RemapArgs& a) {
+  std::vector<int32_t> key = {a.R, a.unit, a.n_src, a.n_dst};
+  for (int k = 0; k < a.n_src; ++k) key.push_back(a.src[k].stride);
+  for (int k = 0; k < a.n_dst; ++k) key.push_back(a.d_nslot[k]);
+  key.insert(key.end(), a.slot, a.slot + a.n_slots);
+  {
+    std::lock_guard<std::mutex> lk(g_order_mu);
+    auto it = g_order_cache.find(key);
+    if (it != g_order_cache.end()) return it->second;
+  }
+  const int order = remap_conflict_cost(a, 0) <= remap_conflict_cost(a, 1) ? 0 : 1;
+  std::lock_guard<std::mutex> lk(g_order_mu);
+  g_order_cache[key] = order;
+  return order;
+}
+
+// Occupancy per (kernel, shared bytes), queried once.
+static std::mutex g_occ_mu;
+static std::map<std::pair<int, size_t>, int> g_occ_cache;
+
+static int cached_occupancy(int kind, size_t smem, int* blocks) {
+  {
+    std::lock_guard<std::mutex> lk(g_occ_mu);
+    auto it = g_occ_cache.find({kind, smem});
+    if (it != g_occ_cache.end()) {
+      *blocks = it->second;
+      return 0;
+    }
+  }
+  const int rc = kind < 100 ? remap_occupancy(kind, smem, blocks) : section_occupancy(kind - 100, smem, blocks);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(g_occ_mu);
+  g_occ_cache[{kind, smem}] = *blocks;
+  return 0;
+}
 
 static int plan_remap(const Layout& S, const void* const* src_ptrs, const Layout& D, void* const* dst_ptrs, int64_t n,
                       RemapPlan* plan) {
@@ -215,7 +310,6 @@ static int plan_remap(const Layout& S, const void* const* src_ptrs, const Layout
       unit = std::min(unit, dtype_size(D.dtype[f]));
     }
   std::vector<int> need(need_set.begin(), need_set.end());
-  // overlap: built dst vs needed src, built dst vs each other
   for (size_t x = 0; x < build.size(); ++x) {
     const size_t nd = (size_t)n * D.stride[build[x]];
     for (int j : need)
@@ -225,70 +319,59 @@ static int plan_remap(const Layout& S, const void* const* src_ptrs, const Layout
       if (overlap(dst_ptrs[build[x]], nd, dst_ptrs[build[y]], (size_t)n * D.stride[build[y]]))
         return fail(ADHA_EINVAL, "destination groups %d and %d overlap", build[x], build[y]);
   }
-  int src_rec = 0, dst_rec = 0;
+  int src_rec = 0, dst_rec = 0, n_slots = 0;
   for (int j : need) src_rec += S.stride[j];
-  for (int d : build) dst_rec += D.stride[d];
-  int T = t_tile_override ? t_tile_override : pick_tile(src_rec, 16384, 1024);
-  const int stages = t_stage_override ? t_stage_override : 4;
-  int n_slots = 0;
-  for (int d : build) n_slots += D.stride[d] / unit;
+  for (int d : build) {
+    dst_rec += D.stride[d];
+    n_slots += D.stride[d] / unit;
+  }
   if (n_slots > kMaxSlots) return fail(ADHA_EINVAL, "destination records too wide (%d slots)", n_slots);
+  int R = t_tile_override ? t_tile_override : pick_chunk(std::max(src_rec, dst_rec), 2560, 512);
   for (;;) {
     a.n = n;
-    a.T = T;
-    a.S = stages;
-    a.n_full = n / T;
+    a.R = R;
+    a.n_chunks = n / R;
+    a.unit = unit;
     a.n_src = (int)need.size();
     a.n_dst = (int)build.size();
     int off = 0;
     for (int k = 0; k < a.n_src; ++k) {
-      a.src[k] = static_cast<const uint8_t*>(src_ptrs[need[k]]);
-      a.s_stride[k] = S.stride[need[k]];
-      a.s_smem[k] = off;
-      off += align128((int64_t)T * a.s_stride[k]);
+      a.src[k].ptr = static_cast<const uint8_t*>(src_ptrs[need[k]]);
+      a.src[k].stride = S.stride[need[k]];
+      a.src[k].start = off;
+      off += R * a.src[k].stride;
     }
-    a.stage_bytes = off;
+    a.in_bytes = off;
     off = 0;
     int slot0 = 0;
     for (int k = 0; k < a.n_dst; ++k) {
       const int d = build[k];
-      a.dst[k] = static_cast<uint8_t*>(dst_ptrs[d]);
-      a.d_stride[k] = D.stride[d];
-      a.d_smem[k] = off;
-      off += align128((int64_t)T * a.d_stride[k]);
+      a.dst[k].ptr = static_cast<const uint8_t*>(dst_ptrs[d]);
+      a.dst[k].stride = D.stride[d];
+      a.dst[k].start = off;
+      off += R * a.dst[k].stride;
       a.d_nslot[k] = D.stride[d] / unit;
       a.d_slot0[k] = slot0;
-      a.d_q[k] = kThreads / a.d_nslot[k];
-      a.d_rem[k] = kThreads % a.d_nslot[k];
       for (int s = 0; s < a.d_nslot[k]; ++s) a.slot[slot0 + s] = kPadSlot;
       for (int f : D.groups[d]) {
-        const int sg = S.group_of[f];
-        const int k_src = (int)(std::lower_bound(need.begin(), need.end(), sg) - need.begin());
-        for (int b = 0; b < dtype_size(D.dtype[f]); b += unit) {
-          const uint32_t addr = (uint32_t)(a.s_smem[k_src] + S.offset_of[f] + b);
-          a.slot[slot0 + (D.offset_of[f] + b) / unit] = addr | ((uint32_t)S.stride[sg] << 20);
-        }
+        const int k_src = (int)(std::lower_bound(need.begin(), need.end(), S.group_of[f]) - need.begin());
+        for (int b = 0; b < dtype_size(D.dtype[f]); b += unit)
+          a.slot[slot0 + (D.offset_of[f] + b) / unit] = ((uint32_t)k_src << 16) | (uint32_t)(S.offset_of[f] + b);
       }
       slot0 += a.d_nslot[k];
     }
     a.out_bytes = off;
     a.n_slots = slot0;
-    const size_t smem = remap_smem_bytes(a);
-    if (smem <= (size_t)kSmemLimit && (a.stage_bytes < (1 << 20))) {
-      plan->smem = smem;
-      break;
-    }
-    if (T <= 32) return fail(ADHA_EINVAL, "records too wide for a 32-record tile (%zu bytes)", smem);
-    T = std::max(32, T / 2 / 32 * 32);
+    a.n_elems = a.out_bytes / unit;
+    plan->smem = remap_smem_bytes(a);
+    if (plan->smem <= (size_t)kSmemLimit && a.in_bytes / unit < 0xFFFF && a.n_elems <= 0x10000) break;
+    if (R <= 32) return fail(ADHA_EINVAL, "records too wide for a 32-record chunk (%zu bytes smem)", plan->smem);
+    R = std::max(32, R / 2 / 32 * 32);
   }
-  plan->unit = unit;
-  int sms = 0, blocks = 0;
-  if (int rc = sm_count(&sms)) return rc;
-  if (int rc = remap_occupancy(unit, plan->smem, &blocks)) return rc;
-  if (blocks < 1) return fail(ADHA_ENOTIMPL, "remap kernel does not fit on an SM (%zu bytes smem)", plan->smem);
-  const int64_t slots = (int64_t)sms * blocks;
-  plan->grid = (int)std::max<int64_t>(1, std::min<int64_t>(a.n_full, slots));
-  return 0;
+  a.order = choose_order(a);
+  int blocks = 0;
+  if (int rc = cached_occupancy(unit, plan->smem, &blocks)) return rc;
+  return finish_grid(a.n_chunks, blocks, &plan->grid);
 }
 
 // ------------------------------------------------------------------ section planning
@@ -371,19 +454,17 @@ static int plan_section(const Layout& L, void* const* ptrs, const adha_section* 
   int rec = 0;
   for (int g : groups) rec += L.stride[g];
   if (s->op == ADHA_OP_GATHER) rec += 4;
-  int T = t_tile_override ? t_tile_override : pick_tile(rec, 16384, 4096);
-  const int stages = t_stage_override ? t_stage_override : 4;
+  int R = t_tile_override ? t_tile_override : pick_chunk(rec, 2048, 1024);
   for (;;) {
     a.n = n;
-    a.T = T;
-    a.S = stages;
-    a.n_full = n / T;
+    a.R = R;
+    a.n_chunks = n / R;
     a.F = L.F;
     a.op = s->op;
-    a.R = s->read_mask;
-    a.W = s->write_mask;
+    a.R_mask = s->read_mask;
+    a.W_mask = s->write_mask;
     a.n_load = (int)groups.size();
-    int off = 0;
+    a.perm_slot = -1;
     for (int f = 0; f < L.F; ++f) {
       const int g = L.group_of[f];
       a.f[f].g = static_cast<uint8_t*>(ptrs[g]) + L.offset_of[f];
@@ -392,40 +473,61 @@ static int plan_section(const Layout& L, void* const* ptrs, const adha_section* 
       a.f[f].ss = 0;
       a.f[f].dtype = L.dtype[f];
     }
+    int off = 0;
     for (int k = 0; k < a.n_load; ++k) {
       const int g = groups[k];
-      a.lsrc[k] = static_cast<const uint8_t*>(ptrs[g]);
-      a.l_stride[k] = L.stride[g];
-      a.l_smem[k] = off;
+      a.load[k].ptr = static_cast<const uint8_t*>(ptrs[g]);
+      a.load[k].stride = L.stride[g];
+      a.load[k].start = off;
       for (int f : L.groups[g]) {
         a.f[f].s0 = off + L.offset_of[f];
         a.f[f].ss = L.stride[g];
       }
-      off += align128((int64_t)T * L.stride[g]);
+      off += R * L.stride[g];
     }
     if (s->op == ADHA_OP_GATHER) {
-      a.lsrc[a.n_load] = reinterpret_cast<const uint8_t*>(s->perm);
-      a.l_stride[a.n_load] = 4;
-      a.l_smem[a.n_load] = off;
-      off += align128((int64_t)T * 4);
+      a.perm_slot = a.n_load;
+      a.load[a.n_load].ptr = reinterpret_cast<const uint8_t*>(s->perm);
+      a.load[a.n_load].stride = 4;
+      a.load[a.n_load].start = off;
+      off += R * 4;
     }
-    a.stage_bytes = off;
+    a.in_bytes = off;
     plan->smem = section_smem_bytes(a);
     if (plan->smem <= (size_t)kSmemLimit) break;
-    if (T <= 32) return fail(ADHA_EINVAL, "section records too wide for a 32-record tile");
-    T = std::max(32, T / 2 / 32 * 32);
+    if (R <= 32) return fail(ADHA_EINVAL, "section records too wide for a 32-record chunk");
+    R = std::max(32, R / 2 / 32 * 32);
   }
   for (int k = 0; k < 8; ++k) a.arg[k] = s->arg[k];
   for (int k = 0; k < 4; ++k) a.par[k] = s->fparam[k];
+  for (int f = 0; f < L.F; ++f) {
+    const int d = L.dtype[f];
+    if (has(s->read_mask, f)) a.rd[d][a.n_rd[d]++] = (int8_t)f;
+    if (has(s->write_mask, f)) a.wr[d][a.n_wr[d]++] = (int8_t)f;
+  }
   tanh_coefficients(a.tanh_p, a.tanh_q);
   a.perm = s->perm;
   a.save = static_cast<uint8_t*>(save);
-  int sms = 0, blocks = 0;
-  if (int rc = sm_count(&sms)) return rc;
-  if (int rc = section_occupancy(s->op, plan->smem, &blocks)) return rc;
-  if (blocks < 1) return fail(ADHA_ENOTIMPL, "section kernel does not fit on an SM");
-  plan->grid = (int)std::max<int64_t>(1, std::min<int64_t>(a.n_full, (int64_t)sms * blocks));
-  return 0;
+  int blocks = 0;
+  if (int rc = cached_occupancy(100 + s->op, plan->smem, &blocks)) return rc;
+  return finish_grid(a.n_chunks, blocks, &plan->grid);
+}
+
+int remap_layouts(const Layout& S, const void* const* src_ptrs, const Layout& D, void* const* dst_ptrs, int64_t n,
+                  void* stream, int* launched) {
+  RemapPlan plan;
+  if (int rc = plan_remap(S, src_ptrs, D, dst_ptrs, n, &plan)) return rc;
+  if (launched) *launched = plan.empty ? 0 : 1;
+  if (plan.empty) return 0;
+  return launch_remap(plan.args, plan.grid, plan.smem, stream);
+}
+
+int run_section_layout(const Layout& L, void* const* ptrs, const adha_section* s, int64_t n, void* save, void* stream) {
+  if (int rc = check_section(L, s, n, save != nullptr)) return rc;
+  if (n == 0) return 0;
+  SectionPlan plan;
+  if (int rc = plan_section(L, ptrs, s, n, save, &plan)) return rc;
+  return launch_section(plan.args, plan.grid, plan.smem, stream);
 }
 
 }  // namespace adha
@@ -464,7 +566,7 @@ int adha_remap(const adha_schema* schema, int64_t n, const adha_layout* src, con
   RemapPlan plan;
   if (int rc = plan_remap(S, src_ptrs, D, dst_ptrs, n, &plan)) return rc;
   if (plan.empty) return 0;
-  return launch_remap(plan.args, plan.unit, plan.grid, plan.smem, stream);
+  return launch_remap(plan.args, plan.grid, plan.smem, stream);
 }
 
 int adha_run_section(const adha_schema* schema, int64_t n, const adha_layout* layout, void* const* ptrs,
@@ -521,6 +623,14 @@ int adha_section_backward(const adha_schema* schema, int64_t n, const adha_layou
   a.save = static_cast<const float*>(save);
   tanh_coefficients(a.tanh_p, a.tanh_q);
   return launch_backward(a, stream);
+}
+
+int adha_tune_override(int32_t chunk_records) {
+  clear_error();
+  if (chunk_records < 0 || chunk_records % 32 != 0 || chunk_records > 1024)
+    return fail(ADHA_EINVAL, "chunk %d is not a multiple of 32 in [0, 1024]", chunk_records);
+  t_tile_override = chunk_records;
+  return 0;
 }
 
 int adha_device_status(adha_stream stream, int32_t* status) {

@@ -19,7 +19,7 @@ constexpr int kMaxGroups = ADHA_MAX_FIELDS;
 constexpr int kMaxSlots = 512;         // u-sized slots over all built destination records
 constexpr int kMaxStride = 4095;       // bytes; fits the 12-bit stride field of a slot code
 constexpr uint32_t kPadSlot = 0xFFFFFFFFu;
-constexpr int kThreads = 256;          // threads per CTA of the staged kernels
+constexpr int kThreads = 256;          // threads per CTA of the staged kernels (8 warps)
 constexpr int kSmemLimit = 227 * 1024; // dynamic shared memory one CTA may use
 
 inline int dtype_size(int d) { return d == ADHA_F64 ? 8 : (d == ADHA_BF16 ? 2 : 4); }
@@ -53,58 +53,74 @@ int status_word(int** ptr);
 int sm_count(int* count);
 
 // ------------------------------------------------------------------ kernel argument blocks
-// Remap of one record array: every built destination group is assembled in shared memory from
-// the source groups' tiles, one u-sized slot at a time.
+// Both staged kernels work per warp: a warp copies R consecutive records of every group it needs
+// ("a chunk", R a multiple of 32) into its own shared buffer with 16-byte cp.async, double
+// buffered, then works on the chunk.  Inside a buffer the groups' slices follow one another in
+// the listed order; slice k starts at byte start[k] (16-byte aligned) and holds R*stride[k] bytes.
+struct GroupRef {
+  const uint8_t* ptr;     // group buffer
+  int32_t stride;         // struct size
+  int32_t start;          // slice offset within a chunk buffer
+};
+
+// Remap of one record array: every built destination group is assembled from the source groups'
+// slices, one u-sized slot at a time.
 struct RemapArgs {
   int64_t n;              // records
-  int64_t n_full;         // whole tiles
-  int32_t T;              // records per tile (multiple of 32)
-  int32_t S;              // pipeline stages
+  int64_t n_chunks;       // whole chunks of R records
+  int32_t R;              // records per chunk
   int32_t n_src, n_dst;
-  int32_t stage_bytes;    // one stage: the source tiles, each region 128-byte aligned
-  int32_t out_bytes;      // one output buffer: the destination tiles
+  int32_t in_bytes;       // one chunk of the source slices
+  int32_t out_bytes;      // one chunk of the destination slices
+  int32_t n_elems;        // u-sized elements in one destination chunk (R * total slots)
   int32_t n_slots;
-  int32_t pad_;
-  const uint8_t* src[kMaxGroups];
-  uint8_t* dst[kMaxGroups];
-  int32_t s_stride[kMaxGroups];
-  int32_t s_smem[kMaxGroups];
-  int32_t d_stride[kMaxGroups];
-  int32_t d_smem[kMaxGroups];
+  int32_t unit;
+  int32_t order;          // element schedule: 0 destination-major, 1 record-major (lane = record)
+  GroupRef src[kMaxGroups];
+  GroupRef dst[kMaxGroups];
   int32_t d_nslot[kMaxGroups];
   int32_t d_slot0[kMaxGroups];
-  int32_t d_q[kMaxGroups];     // kThreads / nslot
-  int32_t d_rem[kMaxGroups];   // kThreads % nslot
-  // slot code: (byte offset of the slot's source bytes for tile record 0 within a stage) |
-  //            (source stride << 20); kPadSlot for padding
+  // per destination slot: (source group index << 16) | byte offset in the source struct;
+  // kPadSlot for padding bytes
   uint32_t slot[kMaxSlots];
 };
 
 struct FieldRef {
   uint8_t* g;       // global address of the field in record 0
   int32_t gs;       // global stride (the group's struct size)
-  int32_t s0;       // byte offset within a stage of the field in tile record 0, -1 if not staged
-  int32_t ss;       // stride within the stage
+  int32_t s0;       // byte offset within a chunk buffer of the field in chunk record 0, -1 if not staged
+  int32_t ss;       // stride within the chunk buffer
   int32_t dtype;
 };
 
 struct SectionArgs {
   int64_t n;
-  int64_t n_full;
-  int32_t T, S;
-  int32_t n_load, stage_bytes;
+  int64_t n_chunks;
+  int32_t R;
+  int32_t n_load, in_bytes;
   int32_t F;
   int32_t op;
-  uint64_t R, W;
-  const uint8_t* lsrc[kMaxGroups];
-  int32_t l_stride[kMaxGroups];
-  int32_t l_smem[kMaxGroups];
+  int32_t perm_slot;            // index of the staged perm slice (GATHER), else -1
+  uint64_t R_mask, W_mask;
+  GroupRef load[kMaxGroups + 1];
   FieldRef f[kMaxFields];
   int32_t arg[8];
   float par[4];
-  float tanh_p[8], tanh_q[8];   // tanh polynomial coefficients (7 used each)
+  float tanh_p[8], tanh_q[8];   // Plan + launch helpers shared by the entry points, the measurer and the executor.
+int remap_layouts(const Layout& S, const void* const* src_ptrs, const Layout& D, void* const* dst_ptrs, int64_t n,
+                  void* stream, int* launched);
+int run_section_layout(const Layout& L, void* const* ptrs, const adha_section* s, int64_t n, void* save,
+                       void* stream);
+adha_layout set_layout(const adha_layout_set* s, int l);
+int pdl_solve(const adha_cost_table* c, int return_to_input, int32_t* seq, double* total);
+
+// tanh polynomial coefficients (7 used each)
   const int32_t* perm;
   uint8_t* save;                // NULL or n elements of the written field's type
+  // MIX: field ids of the read set by type (ascending) and of the write set by type
+  int8_t n_rd[4], n_wr[4];      // indexed by adha_dtype
+  int8_t rd[4][kMaxFields];
+  int8_t wr[4][kMaxFields];
 };
 
 struct BackwardArgs {
@@ -120,16 +136,25 @@ struct BackwardArgs {
   float tanh_p[8], tanh_q[8];
 };
 
+// Plan + launch helpers shared by the entry points, the measurer and the executor.
+int remap_layouts(const Layout& S, const void* const* src_ptrs, const Layout& D, void* const* dst_ptrs, int64_t n,
+                  void* stream, int* launched);
+int run_section_layout(const Layout& L, void* const* ptrs, const adha_section* s, int64_t n, void* save,
+                       void* stream);
+adha_layout set_layout(const adha_layout_set* s, int l);
+int pdl_solve(const adha_cost_table* c, int return_to_input, int32_t* seq, double* total);
+
 // tanh polynomial coefficients (Lambert's continued fraction cut after 25): 7 each, rounded once.
 void tanh_coefficients(float p[8], float q[8]);
 
 // Launchers (defined in the .cu files); all arguments already validated.
-int launch_remap(const RemapArgs& a, int unit, int grid, size_t smem, void* stream);
+int launch_remap(const RemapArgs& a, int grid, size_t smem, void* stream);
 size_t remap_smem_bytes(const RemapArgs& a);
 int launch_section(const SectionArgs& a, int grid, size_t smem, void* stream);
 size_t section_smem_bytes(const SectionArgs& a);
 int launch_backward(const BackwardArgs& a, void* stream);
 int remap_occupancy(int unit, size_t smem, int* blocks);
 int section_occupancy(int op, size_t smem, int* blocks);
+constexpr int kWarps = kThreads / 32;
 
 }  // namespace adha

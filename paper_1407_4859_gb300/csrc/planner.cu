@@ -1,0 +1,252 @@
+// planner.cu -- host side of ADHA's two levels (paper Section 2):
+//   ODS: an affinity graph over the fields a run of sections accesses, edge weight = the number
+//        of sections accessing both fields; greedy clustering of fields into structures under a
+//        struct-size limit ("determined based on the underlying architecture");
+//   PDL: one layout per section for the whole program: the shortest path through the layered
+//        DAG input -> section 1 -> ... -> section S whose nodes are (section, candidate layout),
+//        node weight = measured section time, edge weight = measured remap time (0 when the
+//        layout stays: the paper's "combine" edge).
+// Readings where the paper is silent: ties in the greedy order go to the smaller field id, then
+// the larger; a cluster merge must keep the struct (fields ascending, natural alignment) within
+// the limit; candidates are AoS, SoA and the ODS layout of every window of consecutive
+// sections under every limit; among equally short paths the lexicographically smallest
+// sequence of candidate indices wins.
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "internal.h"
+
+namespace adha {
+
+using Groups = std::vector<std::vector<int>>;
+
+static uint64_t touched(const adha_section& s) { return s.read_mask | s.write_mask | s.read_at_perm_mask; }
+
+// Canonical order: fields ascending inside a group, groups by their first field.
+static Groups canonical(Groups g) {
+  for (auto& x : g) std::sort(x.begin(), x.end());
+  std::sort(g.begin(), g.end(), [](const std::vector<int>& a, const std::vector<int>& b) { return a[0] < b[0]; });
+  return g;
+}
+
+Groups ods_groups(int F, const int* dtype, const adha_section* secs, int n_sec, int cap) {
+  // affinity weights
+  std::vector<int> w(F * F, 0);
+  for (int k = 0; k < n_sec; ++k) {
+    const uint64_t m = touched(secs[k]);
+    for (int a = 0; a < F; ++a)
+      if ((m >> a) & 1ull)
+        for (int b = a + 1; b < F; ++b)
+          if ((m >> b) & 1ull) ++w[a * F + b];
+  }
+  struct Edge { int w, a, b; };
+  std::vector<Edge> edges;
+  for (int a = 0; a < F; ++a)
+    for (int b = a + 1; b < F; ++b)
+      if (w[a * F + b] > 0) edges.push_back({w[a * F + b], a, b});
+  std::sort(edges.begin(), edges.end(), [](const Edge& x, const Edge& y) {
+    if (x.w != y.w) return x.w > y.w;
+    if (x.a != y.a) return x.a < y.a;
+    return x.b < y.b;
+  });
+  // clusters as field lists; owner[f] = cluster id
+  std::vector<int> owner(F);
+  std::vector<std::vector<int>> members(F);
+  for (int f = 0; f < F; ++f) {
+    owner[f] = f;
+    members[f] = {f};
+  }
+  for (const Edge& e : edges) {
+    const int ca = owner[e.a], cb = owner[e.b];
+    if (ca == cb) continue;
+    std::vector<int> merged = members[ca];
+    merged.insert(merged.end(), members[cb].begin(), members[cb].end());
+    std::sort(merged.begin(), merged.end());
+    if (cap > 0 && group_struct(dtype, merged, nullptr) > cap) continue;
+    for (int f : members[cb]) owner[f] = ca;
+    members[ca] = merged;
+    members[cb].clear();
+  }
+  Groups out;
+  for (int c = 0; c < F; ++c)
+    if (!members[c].empty()) out.push_back(members[c]);
+  return canonical(out);
+}
+
+static int validate_sections(int F, const adha_section* secs, int n_sec) {
+  if (n_sec < 1 || n_sec > ADHA_MAX_SECTIONS) return fail(ADHA_EINVAL, "%d sections (1..%d allowed)", n_sec, ADHA_MAX_SECTIONS);
+  if (!secs) return fail(ADHA_EINVAL, "sections are NULL");
+  const uint64_t all = F == 64 ? ~0ull : ((1ull << F) - 1);
+  for (int k = 0; k < n_sec; ++k)
+    if (touched(secs[k]) & ~all) return fail(ADHA_EINVAL, "section %d names fields beyond %d", k, F);
+  return 0;
+}
+
+// One malloc'd block holding the struct and its arrays, freed with adha_free.
+static adha_layout_set* pack_set(int F, const std::vector<Groups>& layouts) {
+  const size_t L = layouts.size();
+  const size_t bytes = sizeof(adha_layout_set) + sizeof(int32_t) * (L + 2 * L * F);
+  auto* s = static_cast<adha_layout_set*>(std::malloc(bytes));
+  if (!s) return nullptr;
+  int32_t* base = reinterpret_cast<int32_t*>(s + 1);
+  s->n_fields = F;
+  s->n_layouts = (int32_t)L;
+  s->n_groups = base;
+  s->group_len = base + L;
+  s->fields = base + L + L * F;
+  for (size_t l = 0; l < L; ++l) {
+    s->n_groups[l] = (int32_t)layouts[l].size();
+    int p = 0;
+    for (size_t g = 0; g < layouts[l].size(); ++g) {
+      s->group_len[l * F + g] = (int32_t)layouts[l][g].size();
+      for (int f : layouts[l][g]) s->fields[l * F + p++] = f;
+    }
+    for (size_t g = layouts[l].size(); g < (size_t)F; ++g) s->group_len[l * F + g] = 0;
+  }
+  return s;
+}
+
+adha_layout set_layout(const adha_layout_set* s, int l) {
+  adha_layout x;
+  x.n_groups = s->n_groups[l];
+  x.group_len = s->group_len + (size_t)l * s->n_fields;
+  x.fields = s->fields + (size_t)l * s->n_fields;
+  return x;
+}
+
+// Layered-DAG shortest path with lexicographic tie-break; costs are whole nanoseconds held in
+// doubles, so every sum is exact and ties compare exactly.
+int pdl_solve(const adha_cost_table* c, int return_to_input, int32_t* seq, double* total) {
+  const int S = c->n_sections, L = c->n_layouts, In = L;
+  auto sec = [&](int k, int l) { return c->section_ns[(size_t)k * L + l]; };
+  auto rem = [&](int a, int b) { return c->remap_ns[(size_t)a * (L + 1) + b]; };
+  std::vector<double> rest((size_t)S * L);
+  for (int l = 0; l < L; ++l) rest[(size_t)(S - 1) * L + l] = sec(S - 1, l) + (return_to_input ? rem(l, In) : 0.0);
+  for (int k = S - 2; k >= 0; --k)
+    for (int l = 0; l < L; ++l) {
+      double best = 0;
+      for (int m = 0; m < L; ++m) {
+        const double v = rem(l, m) + rest[(size_t)(k + 1) * L + m];
+        if (m == 0 || v < best) best = v;
+      }
+      rest[(size_t)k * L + l] = sec(k, l) + best;
+    }
+  int prev = In;
+  for (int k = 0; k < S; ++k) {
+    int arg = 0;
+    double best = 0;
+    for (int m = 0; m < L; ++m) {
+      const double v = rem(prev, m) + rest[(size_t)k * L + m];
+      if (m == 0 || v < best) {
+        best = v;
+        arg = m;
+      }
+    }
+    if (k == 0) *total = best;
+    seq[k] = arg;
+    prev = arg;
+  }
+  return 0;
+}
+
+}  // namespace adha
+
+using namespace adha;
+
+extern "C" {
+
+int adha_ods(const adha_schema* schema, const adha_section* sections, int32_t n_sec, int32_t cap_bytes,
+             int32_t* n_groups, int32_t* group_len, int32_t* fields) {
+  clear_error();
+  if (int rc = check_schema(schema)) return rc;
+  const int F = schema->n_fields;
+  if (int rc = validate_sections(F, sections, n_sec)) return rc;
+  if (!n_groups || !group_len || !fields) return fail(ADHA_EINVAL, "output arrays are NULL");
+  const Groups g = ods_groups(F, schema->dtype, sections, n_sec, cap_bytes);
+  *n_groups = (int32_t)g.size();
+  int p = 0;
+  for (size_t k = 0; k < g.size(); ++k) {
+    group_len[k] = (int32_t)g[k].size();
+    for (int f : g[k]) fields[p++] = f;
+  }
+  return 0;
+}
+
+int adha_plan_sections(const adha_schema* schema, const adha_section* sections, int32_t n_sec,
+                       const adha_plan_opts* opts, adha_layout_set** out) {
+  clear_error();
+  if (int rc = check_schema(schema)) return rc;
+  const int F = schema->n_fields;
+  if (int rc = validate_sections(F, sections, n_sec)) return rc;
+  if (!opts || !out) return fail(ADHA_EINVAL, "opts or out is NULL");
+  if (opts->n_caps < 0 || (opts->n_caps > 0 && !opts->caps)) return fail(ADHA_EINVAL, "bad caps array");
+  std::vector<Groups> layouts;
+  std::map<Groups, int> seen;
+  auto add = [&](const Groups& g) {
+    if (seen.count(g)) return;
+    seen[g] = (int)layouts.size();
+    layouts.push_back(g);
+  };
+  if (opts->include_aos_soa) {
+    Groups aos(1), soa;
+    for (int f = 0; f < F; ++f) {
+      aos[0].push_back(f);
+      soa.push_back({f});
+    }
+    add(aos);
+    add(soa);
+  }
+  const int W = opts->max_window <= 0 ? n_sec : std::min<int>(opts->max_window, n_sec);
+  const int n_caps = opts->n_caps > 0 ? opts->n_caps : 1;
+  for (int w = 1; w <= W; ++w)
+    for (int k = 0; k + w <= n_sec; ++k)
+      for (int c = 0; c < n_caps; ++c) add(ods_groups(F, schema->dtype, sections + k, w, opts->n_caps > 0 ? opts->caps[c] : 0));
+  if (opts->max_candidates > 0 && (int)layouts.size() > opts->max_candidates) layouts.resize(opts->max_candidates);
+  *out = pack_set(F, layouts);
+  if (!*out) return fail(ADHA_ENOMEM, "host allocation of the layout set failed");
+  return 0;
+}
+
+int adha_layout_set_create(int32_t n_fields, int32_t n_layouts, const adha_layout* layouts, adha_layout_set** out) {
+  clear_error();
+  if (!out || !layouts || n_layouts < 1 || n_fields < 1 || n_fields > kMaxFields)
+    return fail(ADHA_EINVAL, "bad layout set arguments");
+  std::vector<Groups> v;
+  std::vector<int32_t> dummy(n_fields, ADHA_F32);
+  adha_schema sc{n_fields, dummy.data()};
+  for (int l = 0; l < n_layouts; ++l) {
+    Layout L;
+    if (int rc = make_layout(&sc, &layouts[l], &L, "candidate")) return rc;
+    v.push_back(L.groups);
+  }
+  *out = pack_set(n_fields, v);
+  if (!*out) return fail(ADHA_ENOMEM, "host allocation of the layout set failed");
+  return 0;
+}
+
+int adha_pdl_solve(const adha_cost_table* costs, int32_t return_to_input, int32_t* layout_of_section, double* total_ns) {
+  clear_error();
+  if (!costs || !layout_of_section || !total_ns) return fail(ADHA_EINVAL, "NULL argument");
+  if (costs->n_sections < 1 || costs->n_layouts < 1 || !costs->section_ns || !costs->remap_ns)
+    return fail(ADHA_EINVAL, "empty cost table");
+  return pdl_solve(costs, return_to_input, layout_of_section, total_ns);
+}
+
+int adha_cost_table_create(int32_t n_sections, int32_t n_layouts, adha_cost_table** out) {
+  clear_error();
+  if (!out || n_sections < 1 || n_layouts < 1) return fail(ADHA_EINVAL, "bad cost table size");
+  const size_t ns = (size_t)n_sections * n_layouts, nr = (size_t)(n_layouts + 1) * (n_layouts + 1);
+  auto* t = static_cast<adha_cost_table*>(std::calloc(1, sizeof(adha_cost_table) + sizeof(double) * (ns + nr)));
+  if (!t) return fail(ADHA_ENOMEM, "host allocation of the cost table failed");
+  t->n_sections = n_sections;
+  t->n_layouts = n_layouts;
+  t->section_ns = reinterpret_cast<double*>(t + 1);
+  t->remap_ns = t->section_ns + ns;
+  *out = t;
+  return 0;
+}
+
+}  // extern "C"

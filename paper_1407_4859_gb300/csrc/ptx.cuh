@@ -1,9 +1,10 @@
-// ptx.cuh -- inline PTX for the staged kernels: mbarriers and bulk (TMA, non-tensor) copies.
+// ptx.cuh -- inline PTX for the staged kernels: 16-byte cp.async copies, and mbarriers with bulk
+// (TMA, non-tensor) copies.
 //
-// Tiles move between global and shared memory with cp.async.bulk: one thread issues a
-// contiguous copy of a whole group tile, the transaction count lands on an mbarrier, and every
-// consumer waits on the mbarrier's phase.  Waits are bounded: after kWaitBudget clock cycles the
-// caller stops and reports ADHA_ETIMEOUT through the status word instead of spinning forever.
+// Bulk copies move a contiguous slice with one instruction; the transaction count lands on an
+// mbarrier whose phase the consumers wait for.  Every mbarrier wait is bounded: after
+// kWaitBudget clock cycles the caller stops and reports ADHA_ETIMEOUT through the status word
+// instead of spinning forever.
 #pragma once
 
 #include <cstdint>
@@ -87,5 +88,18 @@ __device__ __forceinline__ void fence_proxy_async() {
 }
 
 __device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(status, 0, code); }
+
+// 16-byte asynchronous copy global -> shared (LDGSTS), completion tracked per thread in groups.
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(sdst)), "l"(gsrc) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+// Wait until at most N of this thread's committed cp.async groups are pending.
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 }  // namespace adha

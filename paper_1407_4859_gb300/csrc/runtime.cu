@@ -1,0 +1,312 @@
+// runtime.cu -- the measured side of PDL and the program executor.
+//
+// adha_measure is ADHA's "tuning profile" (paper Section 2: the PDL pass takes execution times
+// measured on the device): it times every section in every candidate layout and every remap
+// between candidates on the caller's own data (copied into a workspace first, so the input is
+// not changed), with CUDA events on the caller's stream.  adha_run_program solves PDL on such a
+// table and enqueues the chosen chain of remaps and sections on one stream; groups that two
+// consecutive layouts share are kept in place (aliased), new groups are carved from a caller
+// workspace by a first-fit allocator.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+
+namespace adha {
+
+static size_t round256(size_t x) { return (x + 255) / 256 * 256; }
+
+static size_t layout_bytes(const Layout& L, int64_t n) {
+  size_t b = 0;
+  for (int g = 0; g < L.n_groups; ++g) b += round256((size_t)n * L.stride[g]);
+  return b;
+}
+
+static bool same_layout(const Layout& a, const Layout& b) { return a.groups == b.groups; }
+
+static int load_set(const adha_schema* schema, const adha_layout_set* set, std::vector<Layout>* out) {
+  if (!set || set->n_layouts < 1 || set->n_fields != schema->n_fields)
+    return fail(ADHA_EINVAL, "candidate set is empty or has another field count");
+  out->resize(set->n_layouts);
+  for (int l = 0; l < set->n_layouts; ++l) {
+    const adha_layout x = set_layout(set, l);
+    if (int rc = make_layout(schema, &x, &(*out)[l], "candidate")) return rc;
+  }
+  return 0;
+}
+
+// ------------------------------------------------------------------ workspace allocator
+struct Arena {
+  uint8_t* base = nullptr;
+  size_t size = 0;
+  std::vector<std::pair<size_t, size_t>> used;   // (offset, bytes), sorted by offset
+
+  void* alloc(size_t bytes) {
+    bytes = round256(std::max<size_t>(bytes, 1));
+    size_t at = 0;
+    for (size_t k = 0; k <= used.size(); ++k) {
+      const size_t end = k < used.size() ? used[k].first : size;
+      if (at + bytes <= end) {
+        used.insert(used.begin() + k, {at, bytes});
+        return base + at;
+      }
+      if (k < used.size()) at = used[k].first + used[k].second;
+    }
+    return nullptr;
+  }
+  void release(const void* p) {
+    const size_t off = static_cast<const uint8_t*>(p) - base;
+    for (size_t k = 0; k < used.size(); ++k)
+      if (used[k].first == off) {
+        used.erase(used.begin() + k);
+        return;
+      }
+  }
+  bool owns(const void* p) const {
+    const uint8_t* q = static_cast<const uint8_t*>(p);
+    return q >= base && q < base + size;
+  }
+};
+
+// ------------------------------------------------------------------ timing
+struct Timer {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ~Timer() {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  }
+  int init() {
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    return e == cudaSuccess ? 0 : cuda_fail(e, "cudaEventCreate");
+  }
+};
+
+// Whole nanoseconds of one call of `fn`: one warm-up call, then the faster of two batches of
+// `reps` back-to-back calls timed with events on `stream`.
+template <class Fn>
+static int time_ns(Timer& t, void* stream, int reps, Fn fn, double* ns) {
+  if (int rc = fn()) return rc;
+  double best = -1;
+  for (int b = 0; b < 2; ++b) {
+    cudaError_t e = cudaEventRecord(t.e0, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    for (int r = 0; r < reps; ++r)
+      if (int rc = fn()) return rc;
+    e = cudaEventRecord(t.e1, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(t.e1);
+    if (e != cudaSuccess) return cuda_fail(e, "timing event");
+    float ms = 0;
+    e = cudaEventElapsedTime(&ms, t.e0, t.e1);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+    const double v = (double)ms * 1e6 / reps;
+    if (best < 0 || v < best) best = v;
+  }
+  *ns = (double)(long long)(best + 0.5);
+  return 0;
+}
+
+static void carve(const Layout& L, int64_t n, uint8_t* base, std::vector<void*>* ptrs) {
+  ptrs->assign(L.n_groups, nullptr);
+  size_t off = 0;
+  for (int g = 0; g < L.n_groups; ++g) {
+    (*ptrs)[g] = base + off;
+    off += round256((size_t)n * L.stride[g]);
+  }
+}
+
+// Destination pointers of layout D after S (pointers sp): groups identical to a group of S alias
+// it, the others are carved from `base`.
+static void carve_after(const Layout& S, const std::vector<void*>& sp, const Layout& D, int64_t n, uint8_t* base,
+                        std::vector<void*>* dp) {
+  carve(D, n, base, dp);
+  for (int g = 0; g < D.n_groups; ++g)
+    for (int j = 0; j < S.n_groups; ++j)
+      if (same_group(D, g, S, j)) (*dp)[g] = sp[j];
+}
+
+}  // namespace adha
+
+using namespace adha;
+
+extern "C" {
+
+size_t adha_measure_workspace_bytes(const adha_schema* schema, int64_t n, const adha_layout* in_layout,
+                                    const adha_layout_set* candidates) {
+  clear_error();
+  Layout in;
+  std::vector<Layout> cand;
+  if (make_layout(schema, in_layout, &in, "input") || load_set(schema, candidates, &cand)) return 0;
+  size_t m = layout_bytes(in, n);
+  for (const Layout& L : cand) m = std::max(m, layout_bytes(L, n));
+  return 2 * m;
+}
+
+int adha_measure(const adha_schema* schema, int64_t n, const adha_layout* in_layout, void* const* in_ptrs,
+                 const adha_section* sections, int32_t n_sec, const adha_layout_set* candidates, int32_t reps,
+                 void* workspace, size_t ws_bytes, adha_stream stream, adha_cost_table** out) {
+  clear_error();
+  Layout in;
+  std::vector<Layout> cand;
+  if (int rc = make_layout(schema, in_layout, &in, "input")) return rc;
+  if (int rc = load_set(schema, candidates, &cand)) return rc;
+  if (n < 1) return fail(ADHA_EINVAL, "n = %lld: nothing to measure", (long long)n);
+  if (!in_ptrs || !sections || n_sec < 1 || n_sec > ADHA_MAX_SECTIONS || !out)
+    return fail(ADHA_EINVAL, "bad arguments to adha_measure");
+  if (reps < 1) reps = 2;
+  size_t m = layout_bytes(in, n);
+  for (const Layout& L : cand) m = std::max(m, layout_bytes(L, n));
+  if (!workspace || ws_bytes < 2 * m)
+    return fail(ADHA_ENOMEM, "measure workspace has %zu bytes, needs %zu", ws_bytes, 2 * m);
+  const int L = (int)cand.size();
+  adha_cost_table* t = nullptr;
+  if (int rc = adha_cost_table_create(n_sec, L, &t)) return rc;
+  uint8_t* A = static_cast<uint8_t*>(workspace);
+  uint8_t* B = A + m;
+  std::vector<void*> in_p(in_ptrs, in_ptrs + in.n_groups), pa, pb;
+  Timer timer;
+  int rc = timer.init();
+  auto done = [&](int code) {
+    if (code) std::free(t);
+    else *out = t;
+    return code;
+  };
+  if (rc) return done(rc);
+  for (int a = 0; a < L && !rc; ++a) {
+    // input -> a (identical groups stay where they are)
+    carve_after(in, in_p, cand[a], n, B, &pb);
+    double ns = 0;
+    rc = time_ns(timer, stream, reps, [&] { return remap_layouts(in, in_p.data(), cand[a], pb.data(), n, stream, nullptr); }, &ns);
+    if (rc) break;
+    t->remap_ns[(size_t)L * (L + 1) + a] = ns;
+    // a full private copy of the input in layout a, for the section and remap timings
+    carve(cand[a], n, A, &pa);
+    rc = remap_layouts(in, in_p.data(), cand[a], pa.data(), n, stream, nullptr);
+    for (int k = 0; k < n_sec && !rc; ++k) {
+      rc = time_ns(timer, stream, reps, [&] { return run_section_layout(cand[a], pa.data(), &sections[k], n, nullptr, stream); }, &ns);
+      t->section_ns[(size_t)k * L + a] = ns;
+    }
+    for (int b = 0; b <= L && !rc; ++b) {
+      if (b == a) continue;
+      const Layout& D = b < L ? cand[b] : in;
+      if (same_layout(cand[a], D)) continue;
+      carve_after(cand[a], pa, D, n, B, &pb);
+      rc = time_ns(timer, stream, reps, [&] { return remap_layouts(cand[a], pa.data(), D, pb.data(), n, stream, nullptr); }, &ns);
+      t->remap_ns[(size_t)a * (L + 1) + b] = ns;
+    }
+  }
+  if (!rc) {
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cudaStreamSynchronize(measure)");
+  }
+  return done(rc);
+}
+
+size_t adha_program_workspace_bytes(const adha_schema* schema, int64_t n, const adha_layout* in_layout,
+                                    const adha_layout_set* candidates) {
+  clear_error();
+  Layout in;
+  std::vector<Layout> cand;
+  if (make_layout(schema, in_layout, &in, "input") || load_set(schema, candidates, &cand)) return 0;
+  size_t m = layout_bytes(in, n);
+  for (const Layout& L : cand) m = std::max(m, layout_bytes(L, n));
+  return 3 * m;
+}
+
+int adha_run_program(const adha_schema* schema, int64_t n, const adha_layout* in_layout, void* const* in_ptrs,
+                     const adha_section* sections, int32_t n_sec, const adha_layout_set* candidates,
+                     const adha_cost_table* costs, const adha_plan_opts* opts, void* workspace, size_t ws_bytes,
+                     adha_stream stream, adha_plan* plan) {
+  clear_error();
+  Layout in;
+  std::vector<Layout> cand;
+  if (int rc = make_layout(schema, in_layout, &in, "input")) return rc;
+  if (int rc = load_set(schema, candidates, &cand)) return rc;
+  if (!plan || !sections || n_sec < 1 || n_sec > ADHA_MAX_SECTIONS) return fail(ADHA_EINVAL, "bad program arguments");
+  if (n < 0) return fail(ADHA_EINVAL, "n = %lld is negative", (long long)n);
+  const int L = (int)cand.size();
+  const int back = opts ? opts->return_to_input : 0;
+  if (costs && (costs->n_sections != n_sec || costs->n_layouts != L))
+    return fail(ADHA_EINVAL, "cost table is %dx%d, program is %dx%d", costs->n_sections, costs->n_layouts, n_sec, L);
+  if (!plan->fixed) {
+    if (!costs) return fail(ADHA_EINVAL, "no cost table: run adha_measure first or pass a fixed plan");
+    pdl_solve(costs, back, plan->layout_of_section, &plan->model_ns);
+  } else {
+    for (int k = 0; k < n_sec; ++k)
+      if (plan->layout_of_section[k] < 0 || plan->layout_of_section[k] >= L)
+        return fail(ADHA_EINVAL, "fixed plan names candidate %d for section %d", plan->layout_of_section[k], k);
+    plan->model_ns = 0;
+    if (costs) {
+      int prev = L;
+      for (int k = 0; k < n_sec; ++k) {
+        const int l = plan->layout_of_section[k];
+        plan->model_ns += costs->remap_ns[(size_t)prev * (L + 1) + l] + costs->section_ns[(size_t)k * L + l];
+        prev = l;
+      }
+      if (back) plan->model_ns += costs->remap_ns[(size_t)prev * (L + 1) + L];
+    }
+  }
+  plan->n_sections = n_sec;
+  plan->n_remaps = 0;
+  plan->n_launches = 0;
+  if (n > 0) {
+    if (!in_ptrs) return fail(ADHA_EINVAL, "input pointers are NULL");
+    for (int g = 0; g < in.n_groups; ++g)
+      if (!in_ptrs[g] || reinterpret_cast<uintptr_t>(in_ptrs[g]) % 16)
+        return fail(ADHA_EINVAL, "input buffer %d is NULL or not 16-byte aligned", g);
+  }
+  Arena arena;
+  arena.base = static_cast<uint8_t*>(workspace);
+  arena.size = workspace ? ws_bytes : 0;
+  Layout cur = in;
+  std::vector<void*> cur_p(in_ptrs, in_ptrs + in.n_groups);
+  for (int k = 0; k < n_sec; ++k) {
+    const int l = plan->layout_of_section[k];
+    const Layout& D = cand[l];
+    if (!same_layout(cur, D)) {
+      std::vector<void*> dp(D.n_groups, nullptr);
+      std::vector<bool> kept(cur.n_groups, false);
+      for (int g = 0; g < D.n_groups; ++g) {
+        for (int j = 0; j < cur.n_groups; ++j)
+          if (same_group(D, g, cur, j)) {
+            dp[g] = cur_p[j];
+            kept[j] = true;
+          }
+        if (!dp[g]) {
+          dp[g] = arena.alloc((size_t)n * D.stride[g]);
+          if (!dp[g]) return fail(ADHA_ENOMEM, "program workspace of %zu bytes is too small", ws_bytes);
+        }
+      }
+      int launched = 0;
+      if (int rc = remap_layouts(cur, cur_p.data(), D, dp.data(), n, stream, &launched)) return rc;
+      plan->n_remaps += 1;
+      plan->n_launches += launched;
+      for (int j = 0; j < cur.n_groups; ++j)
+        if (!kept[j] && arena.owns(cur_p[j])) arena.release(cur_p[j]);
+      cur = D;
+      cur_p = dp;
+    }
+    if (int rc = run_section_layout(cur, cur_p.data(), &sections[k], n, nullptr, stream)) return rc;
+    plan->n_launches += n > 0 ? 1 : 0;
+  }
+  if (back && !same_layout(cur, in)) {
+    std::vector<void*> dp(in_ptrs, in_ptrs + in.n_groups);
+    int launched = 0;
+    if (int rc = remap_layouts(cur, cur_p.data(), in, dp.data(), n, stream, &launched)) return rc;
+    plan->n_remaps += 1;
+    plan->n_launches += launched;
+    cur = in;
+    cur_p = dp;
+  }
+  plan->final_layout = -1;
+  for (int l = 0; l < L && plan->final_layout < 0; ++l)
+    if (same_layout(cur, cand[l])) plan->final_layout = l;
+  plan->final_n_groups = cur.n_groups;
+  for (int g = 0; g < cur.n_groups; ++g) plan->final_ptrs[g] = cur_p[g];
+  return 0;
+}
+
+}  // extern "C"

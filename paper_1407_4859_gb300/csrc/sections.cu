@@ -2,10 +2,11 @@
 // data-parallel loop; its layout decides which bytes it drags through memory) and the reverse
 // (adjoint) kernel of the fp32 chain sections.
 //
-// The forward kernel stages, per tile of T records, every group that holds a field the section
-// reads (bulk copies into an mbarrier pipeline, as in remap.cu), computes each record from the
-// staged bytes, and stores the written fields straight to global memory (a partial-record store
-// touches only the sectors of the written field).  The op is a template parameter; the layout is
+// The forward kernel works per warp on chunks of R records, like remap.cu: it copies the chunk's
+// slice of every group that holds a field the section reads into its own shared buffer (16-byte
+// cp.async, one chunk ahead), computes each record from the staged bytes, and stores the
+// written fields straight to global memory (a partial-record store touches only the sectors of
+// the written field).  The op is a template parameter; the layout is
 // the FieldRef table (where each field sits in the stage and in global memory).  Every floating
 // operation is an explicitly rounded-to-nearest intrinsic, so no contraction can change a bit.
 #include <cuda_runtime.h>
@@ -74,31 +75,33 @@ __device__ __forceinline__ void run_record(const SectionArgs& a, const Rec& rec,
   } else if (OP == ADHA_OP_MIX) {
     float s = 0.0f;
     uint32_t h = 0u;
-    for (int f = 0; f < a.F; ++f) {
-      if (!((a.R >> f) & 1ull)) continue;
-      switch (a.f[f].dtype) {
-        case ADHA_F32: s = __fadd_rn(s, rec.template ld<float>(f)); break;
-        case ADHA_F64: {
-          const unsigned long long b = rec.template ld<unsigned long long>(f);
-          h ^= (uint32_t)b ^ (uint32_t)(b >> 32);
-          break;
-        }
-        case ADHA_I32: h ^= rec.template ld<uint32_t>(f); break;
-        default: h ^= (uint32_t)rec.template ld<uint16_t>(f); break;
-      }
+    for (int j = 0; j < a.n_rd[ADHA_F32]; ++j) s = __fadd_rn(s, rec.template ld<float>(a.rd[ADHA_F32][j]));
+    for (int j = 0; j < a.n_rd[ADHA_F64]; ++j) {
+      const unsigned long long b = rec.template ld<unsigned long long>(a.rd[ADHA_F64][j]);
+      h ^= (uint32_t)b ^ (uint32_t)(b >> 32);
     }
+    for (int j = 0; j < a.n_rd[ADHA_I32]; ++j) h ^= rec.template ld<uint32_t>(a.rd[ADHA_I32][j]);
+    for (int j = 0; j < a.n_rd[ADHA_BF16]; ++j) h ^= (uint32_t)rec.template ld<uint16_t>(a.rd[ADHA_BF16][j]);
     const float t = __fadd_rn(s, __fmul_rn(__uint2float_rn(h & 255u), 0.00390625f));
     const uint32_t k = (h ^ __float_as_uint(t)) >> 3;
-    for (int f = 0; f < a.F; ++f) {
-      if (!((a.W >> f) & 1ull)) continue;
-      switch (a.f[f].dtype) {
-        case ADHA_F32: gst<float>(a, f, i, __fadd_rn(__fmul_rn(rec.template ld<float>(f), 0.5f), t)); break;
-        case ADHA_F64:
-          gst<double>(a, f, i, __dadd_rn(__dmul_rn(rec.template ld<double>(f), 0.5), (double)t));
-          break;
-        case ADHA_I32: gst<uint32_t>(a, f, i, rec.template ld<uint32_t>(f) ^ k); break;
-        default: gst<uint16_t>(a, f, i, (uint16_t)(rec.template ld<uint16_t>(f) ^ (uint16_t)(k & 0xFFFFu))); break;
+    for (int j = 0; j < a.n_wr[ADHA_F32]; ++j) {
+      const int f = a.wr[ADHA_F32][j];
+      gst<float>(a, f, i, __fadd_rn(__fmul_rn(rec.template ld<float>(f), 0.5f), t));
+    }
+    if (a.n_wr[ADHA_F64]) {
+      const double td = (double)t;
+      for (int j = 0; j < a.n_wr[ADHA_F64]; ++j) {
+        const int f = a.wr[ADHA_F64][j];
+        gst<double>(a, f, i, __dadd_rn(__dmul_rn(rec.template ld<double>(f), 0.5), td));
       }
+    }
+    for (int j = 0; j < a.n_wr[ADHA_I32]; ++j) {
+      const int f = a.wr[ADHA_I32][j];
+      gst<uint32_t>(a, f, i, rec.template ld<uint32_t>(f) ^ k);
+    }
+    for (int j = 0; j < a.n_wr[ADHA_BF16]; ++j) {
+      const int f = a.wr[ADHA_BF16][j];
+      gst<uint16_t>(a, f, i, (uint16_t)(rec.template ld<uint16_t>(f) ^ (uint16_t)(k & 0xFFFFu)));
     }
   } else if (OP == ADHA_OP_DRIFT) {
 #pragma unroll
@@ -156,64 +159,46 @@ __device__ __forceinline__ void run_record(const SectionArgs& a, const Rec& rec,
 }
 
 template <int OP>
-__global__ void __launch_bounds__(kThreads) section_kernel(const __grid_constant__ SectionArgs a, int* status) {
-  extern __shared__ __align__(128) uint8_t smem[];
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
-  uint8_t* stages = smem + 128;
-  const int tid = threadIdx.x;
-  if (tid == 0) {
-    for (int s = 0; s < a.S; ++s) mbar_init(&bars[s], 1);
-    fence_mbar_init();
-  }
+__global__ void __launch_bounds__(kThreads, 4) section_kernel(const __grid_constant__ SectionArgs a) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  GroupRef* tl = reinterpret_cast<GroupRef*>(smem);
+  const int n_slices = a.n_load + (a.perm_slot >= 0 ? 1 : 0);
+  uint8_t* wbase = smem + ((n_slices * (int)sizeof(GroupRef) + 15) & ~15);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  uint8_t* buf0 = wbase + (size_t)warp * 2 * a.in_bytes;
+  uint8_t* buf1 = buf0 + a.in_bytes;
+  for (int k = tid; k < n_slices; k += kThreads) tl[k] = a.load[k];
   __syncthreads();
 
-  const int64_t G = gridDim.x;
-  const int64_t my_n = (int64_t)blockIdx.x < a.n_full ? (a.n_full - 1 - blockIdx.x) / G + 1 : 0;
-  // staged group n_load (if present) is the permutation (GATHER): int32 per record
-  const bool perm_staged = OP == ADHA_OP_GATHER;
-  const int n_groups = a.n_load + (perm_staged ? 1 : 0);
-
-  auto issue = [&](int64_t j) {
-    const int st = (int)(j % a.S);
-    const int64_t t = blockIdx.x + j * G;
-    uint8_t* dst = stages + (size_t)st * a.stage_bytes;
-    uint32_t bytes = 0;
-    for (int k = 0; k < n_groups; ++k) bytes += (uint32_t)a.T * a.l_stride[k];
-    mbar_expect_tx(&bars[st], bytes);
-    for (int k = 0; k < n_groups; ++k)
-      bulk_load(dst + a.l_smem[k], a.lsrc[k] + t * a.T * a.l_stride[k], (uint32_t)a.T * a.l_stride[k], &bars[st]);
+  const int64_t W = (int64_t)gridDim.x * kWarps;
+  const int64_t R = a.R;
+  auto stage = [&](int64_t ch, uint8_t* buf) {
+    int g = 0;
+    for (int p = lane * 16; p < a.in_bytes; p += 512) {
+      while (p >= tl[g].start + a.R * tl[g].stride) ++g;
+      cp_async16(buf + p, tl[g].ptr + ch * R * tl[g].stride + (p - tl[g].start));
+    }
   };
-  if (tid == 0)
-    for (int64_t j = 0; j < my_n && j < a.S; ++j) issue(j);
 
-  int64_t j = 0;
-  for (; j < my_n; ++j) {
-    const int st = (int)(j % a.S);
-    const bool ok = mbar_wait(&bars[st], (uint32_t)((j / a.S) & 1));
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) {
-        set_status(status, ADHA_ETIMEOUT);
-        for (int64_t k = j; k < my_n && k < j + a.S; ++k) (void)mbar_wait(&bars[k % a.S], (uint32_t)((k / a.S) & 1));
-      }
-      return;
-    }
-    const uint8_t* stage = stages + (size_t)st * a.stage_bytes;
-    const int64_t i0 = (blockIdx.x + j * G) * a.T;
-    for (int r = tid; r < a.T; r += kThreads) {
-      const int32_t pj = perm_staged ? reinterpret_cast<const int32_t*>(stage + a.l_smem[a.n_load])[r] : 0;
-      run_record<OP>(a, StagedRec{&a, stage, r}, i0 + r, pj);
-    }
-    __syncthreads();
-    if (tid == 0 && j + a.S < my_n) issue(j + a.S);
+  int64_t c = (int64_t)blockIdx.x * kWarps + warp;
+  if (c < a.n_chunks) stage(c, buf0);
+  cp_async_commit();
+  for (int i = 0; c < a.n_chunks; c += W, ++i) {
+    const uint8_t* cur = (i & 1) ? buf1 : buf0;
+    if (c + W < a.n_chunks) stage(c + W, (i & 1) ? buf0 : buf1);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncwarp();
+    const int32_t* ps = a.perm_slot >= 0 ? reinterpret_cast<const int32_t*>(cur + tl[a.perm_slot].start) : nullptr;
+    for (int r = lane; r < a.R; r += 32) run_record<OP>(a, StagedRec{&a, cur, r}, c * R + r, ps ? ps[r] : 0);
+    __syncwarp();
   }
+  cp_async_wait<0>();
 
-  // ragged tail: the CTA that would own tile n_full
-  const int64_t t0 = a.n_full * a.T;
-  if (t0 < a.n && (int64_t)blockIdx.x == a.n_full % G) {
-    for (int64_t i = t0 + tid; i < a.n; i += kThreads) {
-      const int32_t pj = perm_staged ? a.perm[i] : 0;
-      run_record<OP>(a, GlobalRec{&a, i}, i, pj);
-    }
+  // ragged tail: the warp whose next chunk would be n_chunks
+  const int64_t t0 = a.n_chunks * R;
+  if (c == a.n_chunks && t0 < a.n) {
+    for (int64_t i = t0 + lane; i < a.n; i += 32) run_record<OP>(a, GlobalRec{&a, i}, i, a.perm_slot >= 0 ? a.perm[i] : 0);
   }
 }
 
@@ -243,13 +228,16 @@ __global__ void __launch_bounds__(kThreads) backward_kernel(const __grid_constan
   }
 }
 
-size_t section_smem_bytes(const SectionArgs& a) { return 128 + (size_t)a.S * a.stage_bytes; }
+size_t section_smem_bytes(const SectionArgs& a) {
+  const int n_slices = a.n_load + (a.perm_slot >= 0 ? 1 : 0);
+  return (size_t)((n_slices * (int)sizeof(GroupRef) + 15) & ~15) + (size_t)kWarps * 2 * a.in_bytes;
+}
 
 template <int OP>
-static int launch_op(const SectionArgs& a, int grid, size_t smem, void* stream, int* status) {
+static int launch_op(const SectionArgs& a, int grid, size_t smem, void* stream) {
   cudaError_t e = cudaFuncSetAttribute(section_kernel<OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(section)");
-  section_kernel<OP><<<grid, kThreads, smem, (cudaStream_t)stream>>>(a, status);
+  section_kernel<OP><<<grid, kThreads, smem, (cudaStream_t)stream>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "section kernel launch");
   return 0;
@@ -270,10 +258,8 @@ static int occ_op(size_t smem, int* blocks) {
   X(ADHA_OP_TANH)
 
 int launch_section(const SectionArgs& a, int grid, size_t smem, void* stream) {
-  int* status = nullptr;
-  if (int rc = status_word(&status)) return rc;
   switch (a.op) {
-#define X(op) case op: return launch_op<op>(a, grid, smem, stream, status);
+#define X(op) case op: return launch_op<op>(a, grid, smem, stream);
     ADHA_FOR_EACH_OP(X)
 #undef X
     default: return fail(ADHA_EINVAL, "unknown section op %d", a.op);

@@ -1,0 +1,124 @@
+"""GPU parity of the whole hot path: candidates (ODS) -> measured costs -> PDL -> executed
+program of remaps and sections, bit-exact against the oracle; the plan itself equal to the
+oracle's exhaustive / DP choice on the same measured cost table."""
+import itertools
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_util import to_device, from_device, assert_fields_equal
+
+pytestmark = pytest.mark.gpu
+CAPS = [16, 32, 64, 128, 256, 0]
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_1407_4859_gb300 import build
+    build.build()
+    import paper_1407_4859_gb300 as P
+    return P
+
+
+def _setup(P, wl, perm=None):
+    S = P.Schema(wl.dtypes)
+    AOS = P.Layout.aos(wl.F)
+    if wl.candidates == "aos_soa":
+        cand = P.adha_layout_set_create(wl.F, [AOS, P.Layout.soa(wl.F)])
+    else:
+        cand = P.adha_plan_sections(S, wl.sections, P.PlanOpts(CAPS, max_window=3))
+    secs = P.Sections(wl.sections, perm)
+    return S, AOS, cand, secs
+
+
+def _run(P, wl, S, AOS, cand, secs, in_bufs, costs=None, fixed=None, back=False):
+    ws = torch.empty(P.adha_program_workspace_bytes(S, wl.n, AOS, cand), dtype=torch.uint8, device="cuda")
+    plan = P.adha_run_program(S, wl.n, AOS, in_bufs, secs, cand, costs=costs, fixed=fixed, workspace=ws,
+                              opts=P.PlanOpts(CAPS, return_to_input=back))
+    torch.cuda.synchronize()
+    lay, bufs = P.final_buffers(plan, S, wl.n, cand, AOS)
+    host = [b.cpu().numpy().copy() for b in bufs]
+    del ws
+    return plan, lay, host
+
+
+def test_tiny_program_pdl_matches_exhaustive_on_measured_costs(P):
+    wl = synth.config1()
+    S, AOS, cand, secs = _setup(P, wl)
+    fields = oracle.initial_fields(wl)
+    want = oracle.run_program_fields(wl, [a.copy() for a in fields])
+    in_bufs = to_device(wl.n, wl.dtypes, AOS.groups, fields)
+    costs = P.adha_measure(S, wl.n, AOS, in_bufs, secs, cand)
+    # measuring leaves the input untouched
+    assert_fields_equal(from_device(wl.n, wl.dtypes, AOS.groups, in_bufs), fields, "input after measure")
+    sec_ns, rem_ns = costs.section_ns, costs.remap_ns
+    assert all(v > 0 for row in sec_ns for v in row)
+    best_cost, best_seq = oracle.pdl_exhaustive(sec_ns, rem_ns)
+    plan, lay, host = _run(P, wl, S, AOS, cand, secs, in_bufs, costs=costs)
+    assert list(plan.layout_of_section[:3]) == best_seq and plan.model_ns == best_cost
+    assert_fields_equal(oracle.to_fields(wl.n, wl.dtypes, lay.groups, host), want, "pdl program")
+
+
+def test_tiny_program_every_fixed_assignment(P):
+    wl = synth.config1()
+    S, AOS, cand, secs = _setup(P, wl)
+    fields = oracle.initial_fields(wl)
+    want = oracle.run_program_fields(wl, [a.copy() for a in fields])
+    for seq in itertools.product([0, 1], repeat=3):
+        in_bufs = to_device(wl.n, wl.dtypes, AOS.groups, fields)
+        plan, lay, host = _run(P, wl, S, AOS, cand, secs, in_bufs, fixed=seq)
+        assert plan.n_remaps == sum(1 for k in range(3) if seq[k] != (seq[k - 1] if k else 0))
+        assert_fields_equal(oracle.to_fields(wl.n, wl.dtypes, lay.groups, host), want, "assignment %r" % (seq,))
+
+
+@pytest.mark.parametrize("make,n", [(synth.config2, (1 << 16) + 7), (synth.config3, (1 << 16) + 3)])
+@pytest.mark.parametrize("back", [False, True])
+def test_program_with_ods_candidates(P, make, n, back):
+    wl = make(n=n)
+    perm = wl.perm() if wl.has_perm else None
+    dperm = torch.from_numpy(perm).cuda() if perm is not None else None
+    S, AOS, cand, secs = _setup(P, wl, dperm)
+    fields = oracle.initial_fields(wl)
+    want = oracle.run_program_fields(wl, [a.copy() for a in fields], perm)
+    in_bufs = to_device(n, wl.dtypes, AOS.groups, fields)
+    costs = P.adha_measure(S, n, AOS, in_bufs, secs, cand)
+    cost, seq = oracle.pdl_dp(costs.section_ns, costs.remap_ns, back)
+    plan, lay, host = _run(P, wl, S, AOS, cand, secs, in_bufs, costs=costs, back=back)
+    assert list(plan.layout_of_section[:len(wl.sections)]) == seq and plan.model_ns == cost
+    if back:
+        assert lay == AOS
+        host = [b.cpu().numpy() for b in in_bufs]
+    assert_fields_equal(oracle.to_fields(n, wl.dtypes, lay.groups, host), want, "program")
+
+
+@pytest.mark.parametrize("make", [synth.config2, synth.config3])
+def test_full_size_program_sampled(P, make):
+    """The full-size stress (2^24 x 80 B) and particle (2^25 x 56 B) programs, planned on costs
+    measured at 2^20 records, checked on 4096 sampled records plus both ends."""
+    wl = make()
+    n = wl.n
+    perm = wl.perm() if wl.has_perm else None
+    dperm = torch.from_numpy(perm).cuda() if perm is not None else None
+    S, AOS, cand, secs = _setup(P, wl, dperm)
+    small = wl.with_n(1 << 20)
+    sfields = oracle.initial_fields(small)
+    sperm = torch.from_numpy(small.perm()).cuda() if wl.has_perm else None
+    ssecs = P.Sections(small.sections, sperm)
+    costs = P.adha_measure(S, small.n, AOS, to_device(small.n, wl.dtypes, AOS.groups, sfields), ssecs, cand)
+    fields = oracle.initial_fields(wl)
+    in_bufs = to_device(n, wl.dtypes, AOS.groups, fields)
+    del fields
+    plan, lay, host = _run(P, wl, S, AOS, cand, secs, in_bufs, costs=costs)
+    rng = np.random.default_rng(11)
+    sample = np.concatenate([[0, 1, n - 2, n - 1], rng.integers(0, n, 4096)])
+    want = oracle.sample_program(wl, sample, perm)
+    st, gof, off = oracle.layout_info(wl.dtypes, lay.groups)
+    for f in range(wl.F):
+        g = gof[f]
+        sz = oracle.core.SIZE[wl.dtypes[f]]
+        rows = host[g].reshape(n, st[g])[sample, off[f]:off[f] + sz]
+        got = np.ascontiguousarray(rows).view(oracle.core.NP[wl.dtypes[f]]).reshape(-1)
+        assert np.array_equal(got.view(np.uint8), np.ascontiguousarray(want[f]).view(np.uint8)), "field %d" % f

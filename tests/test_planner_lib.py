@@ -1,0 +1,89 @@
+"""The library's host planner (ODS, candidates, PDL) against the oracle's, CPU only."""
+import random
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from test_oracle_planner import golden_cases
+
+CAPS = [16, 32, 64, 128, 256, 0]
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_1407_4859_gb300 import build
+    build.build()
+    import paper_1407_4859_gb300 as P
+    return P
+
+
+@pytest.mark.parametrize("dtypes,sections,cap,want", golden_cases())
+def test_library_ods_golden(P, dtypes, sections, cap, want):
+    assert P.adha_ods(P.Schema(dtypes), sections, cap).groups == want
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_library_ods_random(P, seed):
+    wl = synth.tiny_workload(seed, F_max=20, n=1, n_sections=5)
+    rng = np.random.default_rng(seed)
+    for cap in [0, 8, 12, 16, 24, 40]:
+        k = int(rng.integers(0, len(wl.sections)))
+        secs = wl.sections[k:k + 3]
+        assert P.adha_ods(P.Schema(wl.dtypes), secs, cap).groups == oracle.ods(secs, wl.dtypes, cap)
+
+
+@pytest.mark.parametrize("make,window", [(synth.config1, 0), (synth.config2, 0), (synth.config3, 4),
+                                         (synth.config5, 3)])
+def test_library_candidates_match_oracle(P, make, window):
+    wl = make(n=16)
+    lib = P.adha_plan_sections(P.Schema(wl.dtypes), wl.sections, P.PlanOpts(CAPS, max_window=window))
+    assert [l.groups for l in lib.layouts] == oracle.candidates(wl.sections, wl.dtypes, CAPS, window)
+
+
+def test_candidate_cap_and_no_aos_soa(P):
+    wl = synth.config2(n=16)
+    lib = P.adha_plan_sections(P.Schema(wl.dtypes), wl.sections,
+                               P.PlanOpts(CAPS, max_window=2, include_aos_soa=False, max_candidates=5))
+    want = oracle.candidates(wl.sections, wl.dtypes, CAPS, 2, include_aos_soa=False, max_candidates=5)
+    assert [l.groups for l in lib.layouts] == want and len(want) == 5
+
+
+def _table(P, sec, rem):
+    t = P.adha_cost_table_create(len(sec), len(sec[0]))
+    t.set(sec, rem)
+    return t
+
+
+@pytest.mark.parametrize("seed", range(80))
+def test_library_pdl_equals_exhaustive(P, seed):
+    rng = random.Random(seed)
+    S, L = rng.randrange(1, 7), rng.randrange(1, 5)
+    sec = [[rng.randrange(0, 30) for _ in range(L)] for _ in range(S)]
+    rem = [[0 if a == b else rng.randrange(0, 25) for b in range(L + 1)] for a in range(L + 1)]
+    back = bool(seed % 3 == 0)
+    cost, seq = oracle.pdl_exhaustive(sec, rem, back)
+    got_cost, got_seq = P.adha_pdl_solve(_table(P, sec, rem), back)
+    assert (got_cost, got_seq) == (cost, seq)
+
+
+def test_library_pdl_large_matches_oracle_dp(P):
+    rng = random.Random(7)
+    S, L = 64, 40
+    sec = [[rng.randrange(1000, 50000) for _ in range(L)] for _ in range(S)]
+    rem = [[0 if a == b else rng.randrange(0, 90000) for b in range(L + 1)] for a in range(L + 1)]
+    assert P.adha_pdl_solve(_table(P, sec, rem)) == tuple(oracle.pdl_dp(sec, rem))
+
+
+def test_run_program_rejects_bad_fixed_plan_without_gpu(P):
+    from paper_1407_4859_gb300._lib import AdhaError, ADHA_EINVAL
+    wl = synth.config1(n=64)
+    S = P.Schema(wl.dtypes)
+    cand = P.adha_layout_set_create(6, [P.Layout.aos(6), P.Layout.soa(6)])
+    with pytest.raises(AdhaError) as e:
+        P.adha_run_program(S, 64, P.Layout.aos(6), [256], wl.sections, cand, fixed=[0, 5, 1], stream=0)
+    assert e.value.code == ADHA_EINVAL
+    with pytest.raises(AdhaError) as e:     # neither a table nor a fixed plan
+        P.adha_run_program(S, 64, P.Layout.aos(6), [256], wl.sections, cand, stream=0)
+    assert e.value.code == ADHA_EINVAL and "measure" in str(e.value)
