@@ -1,0 +1,402 @@
+#!/usr/bin/env python3
+"""Benchmark of the ADHA hot path on GB300: the layout-stress program (2^24 records of 16
+fields: 8 fp32, 4 fp64, 4 int32 = 80 B in AoS; 8 sections with Bernoulli(0.3) read/write sets
+plus one section over every field).
+
+One step = one pass of the path over one batch: candidate layouts by ODS (affinity graph +
+greedy grouping, host), PDL on the measured cost table (host), then the chosen chain of remap
+and section kernels (device).  The cost table (the paper's tuning profile) is measured once
+before the timed region, like an autotuner cache.
+
+Prints one JSON line.  `value` is algorithmic GB/s of the program: the data bytes its sections
+must move (accessed fields only; no padding, no untouched fields) divided by the step's device
+time, so a plan pays for the remaps it adds in time.  Extra keys: program times under the ADHA layouts vs
+all-AoS, all-SoA and the best of a bounded exhaustive set; the roofline of the dominant kernel;
+the oracle timed on the host cores; the end-to-end number through the C ABI with host buffers.
+
+--impl reference times the CPU oracle (the only reference this method has) on a bounded sample
+of the same workload and prints the same metric.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+CAPS = [16, 32, 64, 128, 256, 0]
+METRIC = "remap and section HBM GB/s vs ~8 TB/s; program time ADHA-layout vs AoS/SoA/exhaustive"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+SZ = {0: 4, 1: 8, 2: 4, 3: 2}
+
+
+def program_bytes(wl):
+    """Algorithmic bytes of the program itself, independent of layouts: every section reads its
+    read/write fields once and writes its written fields once (plus the permutation and the
+    fields it reads through it).  Remaps a plan adds are paid in time, not counted as work."""
+    total = 0
+    for s in wl.sections:
+        total += wl.n * (sum(SZ[wl.dtypes[f]] for f in s.read | s.write) + sum(SZ[wl.dtypes[f]] for f in s.write))
+        if s.op == "gather":
+            total += wl.n * (4 + sum(SZ[wl.dtypes[f]] for f in s.read_at_perm))
+    return total
+
+
+def remap_bytes(wl, plan_layouts, in_layout):
+    """Algorithmic bytes of the plan's remaps: 2 x data bytes of every group that changes."""
+    total = 0
+    cur = [tuple(g) for g in in_layout]
+    for lay in plan_layouts:
+        lay = [tuple(g) for g in lay]
+        if lay != cur:
+            total += 2 * wl.n * sum(SZ[wl.dtypes[f]] for g in lay if g not in cur for f in g)
+            cur = lay
+    return total
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def csrc_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1407_4859_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, if the kernels have not changed."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("csrc_hash") != csrc_hash():
+        return None
+    ent = d.get("kernels", {}).get(kernel_key)
+    return None if ent is None else ent.get("dram_bytes_per_launch")
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.4)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        rows = [r.split(",") for r in out.strip().splitlines() if r.count(",") >= 8]
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if "Active" in r[5 + k] and "Not" not in r[5 + k]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------------- reference arm
+
+_AOS_CACHE = {}
+
+
+def oracle_program_seconds(wl, plan_layouts, n_sample):
+    """The oracle computing the same transformation on the first n_sample records: decode the
+    AoS input, run every section, encode the result in the plan's final layout."""
+    import numpy as np
+    import oracle
+    small = wl.with_n(n_sample)
+    key = (wl.name, n_sample)
+    if key not in _AOS_CACHE:
+        fields = oracle.initial_fields(small)
+        _AOS_CACHE[key] = oracle.from_fields(n_sample, wl.dtypes, oracle.aos(wl.F), fields)
+    aos = _AOS_CACHE[key]
+    t0 = time.perf_counter()
+    f = oracle.to_fields(n_sample, wl.dtypes, oracle.aos(wl.F), aos)
+    f = [np.ascontiguousarray(a) for a in f]
+    oracle.run_program_fields(small, f, small.perm() if small.has_perm else None)
+    oracle.from_fields(n_sample, wl.dtypes, plan_layouts[-1], f)
+    return time.perf_counter() - t0
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    import synth
+    wl = synth.config2()
+    n_sample = 1 << 18
+    aos = [list(range(wl.F))]
+    layouts = [aos] * len(wl.sections)          # the oracle's own representation does not change layout
+    small = wl.with_n(n_sample)
+    bytes_per = program_bytes(small)
+    for _ in range(args.warmup):
+        oracle_program_seconds(wl, layouts, n_sample)
+    secs = [oracle_program_seconds(wl, layouts, n_sample) for _ in range(args.steps)]
+    total = sum(secs)
+    value = bytes_per * args.steps / total / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000 * total / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64+i32",
+        "data": "synthetic (seeded SplitMix64)",
+        "config": {"workload": wl.name, "n_records_per_step": n_sample,
+                   "note": "CPU oracle (plain scalar C, one thread) on the first 2^18 records of the 2^24-record batch"},
+        "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": "first 2^18 of 2^24 records per step, all 9 sections + AoS decode / encode"},
+        "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------- device arm
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="adha", choices=["adha", "reference"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the AoS/SoA/exhaustive program comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle timing")
+    ap.add_argument("--n-log2", type=int, default=24, help="records per GPU (default 2^24, the workload's size)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    rank, world, local = env_rank()
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import synth
+    from paper_1407_4859_gb300 import build
+    build.build()
+    import paper_1407_4859_gb300 as P
+
+    wl = synth.config2(n=1 << args.n_log2)
+    n = wl.n
+    S = P.Schema(wl.dtypes)
+    AOS = P.Layout.aos(wl.F)
+    secs = P.Sections(wl.sections)
+    t0 = time.perf_counter()
+    host_aos = None
+    fields = [wl.values(f) for f in range(wl.F)]
+    import oracle  # encoding the seeded input as AoS bytes on the host (test infrastructure, not timed)
+    host_aos = oracle.from_fields(n, wl.dtypes, AOS.groups, fields)[0]
+    del fields
+    pinned = torch.from_numpy(host_aos).pin_memory()
+    in_buf = [pinned.cuda()]
+    log("inputs ready in %.1f s" % (time.perf_counter() - t0))
+
+    opts = P.PlanOpts(CAPS, max_window=0)
+    cand = P.adha_plan_sections(S, secs, opts)
+    L = len(cand)
+    t0 = time.perf_counter()
+    costs = P.adha_measure(S, n, AOS, in_buf, secs, cand, reps=2)
+    measure_s = time.perf_counter() - t0
+    log("%d candidates measured in %.1f s" % (L, measure_s))
+    ws = torch.empty(P.adha_program_workspace_bytes(S, n, AOS, cand), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        c = P.adha_plan_sections(S, secs, opts)          # ODS candidates (host)
+        return P.adha_run_program(S, n, AOS, in_buf, secs, c, costs=costs, workspace=ws, stream=stream), c
+
+    for _ in range(args.warmup):
+        plan, _ = step()
+    layouts = cand.layouts
+    seq = list(plan.layout_of_section[:len(wl.sections)])
+    plan_layouts = [layouts[l].groups for l in seq]
+    bytes_per_step = program_bytes(wl)
+    remap_bytes_per_step = remap_bytes(wl, plan_layouts, AOS.groups)
+
+    clocks = Clocks(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    P.adha_profile_start(64 * args.steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    recs = P.adha_profile_stop(64 * args.steps)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * bytes_per_step * args.steps / (ms * 1e6)
+
+    # roofline of the dominant kernel (largest share of the timed region)
+    groups = {}
+    for r in recs:
+        key = r["kind"] if r["kind"] != "section" else "section_%s" % r["op"]
+        g = groups.setdefault(key, [0.0, 0.0, 0])
+        g[0] += r["ms"]
+        g[1] += r["bytes"]
+        g[2] += 1
+    dom = max(groups, key=lambda k: groups[k][0])
+    peak, peak_src = measured_peaks()
+    achieved = groups[dom][1] / (groups[dom][0] * 1e6)
+    kernel_name = {"remap": "remap_kernel"}.get(dom, "section_kernel<%s>" % dom.replace("section_", ""))
+    traffic = traffic_for(dom)
+    roofline = {"bound": "hbm", "kernel": kernel_name, "achieved": round(achieved, 1), "peak": peak,
+                "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                "launches": groups[dom][2], "share": round(groups[dom][0] / max(1e-9, sum(v[0] for v in groups.values())), 3)}
+    per_kernel = {k: {"launches": v[2], "ms": round(v[0], 3), "alg_GBs": round(v[1] / (v[0] * 1e6), 1)}
+                  for k, v in sorted(groups.items(), key=lambda kv: -kv[1][0])}
+
+    # end to end through the C ABI with host buffers: H2D input, program, D2H result
+    lay_final = layouts[plan.final_layout] if plan.final_layout >= 0 else AOS
+    strides, _ = P.adha_layout_strides(S, lay_final)
+    host_out = [torch.empty(n * s, dtype=torch.uint8).pin_memory() for s in strides]
+    e2e_steps = max(3, min(10, args.steps // 20))
+    for it in range(e2e_steps + 1):
+        if it == 1:
+            torch.cuda.synchronize()
+            f0 = torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+        in_buf[0].copy_(pinned, non_blocking=True)
+        pl, c = step()
+        lay, outs = P.final_buffers(pl, S, n, c, AOS)
+        for h, d in zip(host_out, outs):
+            h.copy_(d, non_blocking=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = f0.elapsed_time(f1) / e2e_steps
+    e2e = {"value": round(world * bytes_per_step / (e2e_ms * 1e6), 1), "unit": "GB/s",
+           "h2d_bytes_per_step": int(pinned.numel()), "d2h_bytes_per_step": int(sum(h.numel() for h in host_out)),
+           "ms_per_step": round(e2e_ms, 3)}
+
+    # program time: ADHA vs all-AoS vs all-SoA vs a bounded exhaustive set
+    compare = None
+    if not args.no_compare and rank == 0:
+        def prog_ms(fixed, reps=3):
+            ts = []
+            for r in range(reps + 1):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                P.adha_run_program(S, n, AOS, in_buf, secs, cand, costs=costs, fixed=fixed, workspace=ws, stream=stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+                if r:
+                    ts.append(a.elapsed_time(b))
+            return statistics.median(ts)
+        nsec = len(wl.sections)
+        i_aos, i_soa = 0, 1
+        adha_ms = prog_ms(seq)
+        t_aos = prog_ms([i_aos] * nsec)
+        t_soa = prog_ms([i_soa] * nsec)
+        import itertools
+        tried = {}
+        for assign in itertools.product([i_aos, i_soa], repeat=nsec):
+            tried[assign] = prog_ms(list(assign), reps=1)
+        for l in range(L):
+            tried[(l,) * nsec] = prog_ms([l] * nsec, reps=1)
+        best_assign = min(tried, key=tried.get)
+        best_ms = prog_ms(list(best_assign))
+        uniform_best = min(range(L), key=lambda l: tried[(l,) * nsec])
+        compare = {"adha_ms": round(adha_ms, 3), "all_aos_ms": round(t_aos, 3), "all_soa_ms": round(t_soa, 3),
+                   "exhaustive_best_ms": round(min(best_ms, adha_ms), 3),
+                   "exhaustive_set": "bounded: all %d {AoS,SoA}^%d assignments + %d uniform single-layout programs "
+                                     "+ the ADHA plan (full %d^%d enumeration infeasible)" % (2 ** nsec, nsec, L, L, nsec),
+                   "exhaustive_best_plan": list(best_assign), "best_uniform_layout": layouts[uniform_best].groups,
+                   "adha_over_best": round(adha_ms / min(best_ms, adha_ms), 4),
+                   "speedup_vs_aos": round(t_aos / adha_ms, 3), "speedup_vs_soa": round(t_soa / adha_ms, 3),
+                   "paper_context": "paper: up to 6.92x over manual (SoA) layouts, K-Means on Xeon X5660 + Tesla M2050, OpenCL"}
+
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        n_sample = min(n, 1 << 22)
+        small = wl.with_n(n_sample)
+        b_small = program_bytes(small)
+        t_tot, reps = 0.0, 0
+        while reps < 3 and (reps == 0 or t_tot < 10.0):
+            t_tot += oracle_program_seconds(wl, plan_layouts, n_sample)
+            reps += 1
+        cpu = {"value": round(b_small * reps / t_tot / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": "first 2^22 of 2^24 records x %d runs: AoS decode, 9 sections, encode in the ADHA final layout"
+                         % reps}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64+i32",
+            "data": "synthetic (seeded SplitMix64, uniform values as the workload states)",
+            "config": {"workload": wl.name, "records": n, "fields": "8 f32 + 4 f64 + 4 i32 (80 B AoS)",
+                       "sections": len(wl.sections), "candidates": L, "plan": seq,
+                       "plan_layouts": plan_layouts, "remaps_per_step": plan.n_remaps,
+                       "l2": "inputs larger than L2 (1.34 GB per layout vs 129 MB)",
+                       "parallelism": "one independent batch per GPU" if world > 1 else "single GPU",
+                       "measure_s": round(measure_s, 2), "program_bytes_per_step": bytes_per_step,
+                       "remap_bytes_per_step": remap_bytes_per_step,
+                       "value_definition": "program section bytes per step / step device time; remaps the plan "
+                                           "adds cost time but are not counted as work",
+                       "step_GBs_incl_remaps": round(world * (bytes_per_step + remap_bytes_per_step) * args.steps
+                                                     / (ms * 1e6), 1)},
+            "gpu_launches": len(recs), "roofline": roofline, "kernels": per_kernel, "clocks": clk,
+            "e2e": e2e, "cpu_baseline": cpu, "program_ms": compare,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

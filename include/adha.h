@@ -310,6 +310,26 @@ int adha_run_program(const adha_schema* schema, int64_t n, const adha_layout* in
  */
 int adha_tune_override(int32_t chunk_records);
 
+/* One kernel launch seen by the profiler.  kind: 0 remap, 1 section, 2 section
+ * backward, 3 batched remap; op: the section's adha_op (0 for remaps); bytes:
+ * the algorithmic bytes the launch had to move (data bytes of the moved or
+ * accessed fields, not padding or untouched fields); ms: its duration between
+ * two CUDA events recorded around it on its stream. */
+typedef struct {
+  int32_t kind;
+  int32_t op;
+  double bytes;
+  double ms;
+} adha_launch_record;
+
+/* Starts recording every kernel the calling thread launches through this
+ * library (up to max_records; events are created once and reused).  Host only. */
+int adha_profile_start(int32_t max_records);
+
+/* Stops recording, waits for the recorded launches and copies up to
+ * max_records of them to out; *n_records = how many were recorded. */
+int adha_profile_stop(adha_launch_record* out, int32_t max_records, int32_t* n_records);
+
 /*
  * Reads and clears the device status word that kernels set when a bounded
  * wait for their own copies ran out (then they stop early and their output is

@@ -54,6 +54,10 @@ class adha_plan(ctypes.Structure):
                 ("final_n_groups", _I32), ("final_ptrs", _P * MAX_FIELDS)]
 
 
+class adha_launch_record(ctypes.Structure):
+    _fields_ = [("kind", _I32), ("op", _I32), ("bytes", ctypes.c_double), ("ms", ctypes.c_double)]
+
+
 class AdhaError(RuntimeError):
     def __init__(self, code, fn, msg):
         super().__init__("%s failed with %s: %s" % (fn, CODES.get(code, code), msg))
@@ -77,6 +81,8 @@ SIGNATURES = {
                                              _PP, ctypes.POINTER(adha_section), _P, _P]),
     "adha_device_status": (ctypes.c_int, [_P, ctypes.POINTER(_I32)]),
     "adha_tune_override": (ctypes.c_int, [_I32]),
+    "adha_profile_start": (ctypes.c_int, [_I32]),
+    "adha_profile_stop": (ctypes.c_int, [ctypes.POINTER(adha_launch_record), _I32, ctypes.POINTER(_I32)]),
     "adha_ods": (ctypes.c_int, [ctypes.POINTER(adha_schema), ctypes.POINTER(adha_section), _I32, _I32,
                                 ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "adha_plan_sections": (ctypes.c_int, [ctypes.POINTER(adha_schema), ctypes.POINTER(adha_section), _I32,

@@ -333,3 +333,20 @@ def _view_device(ptr, nbytes):
         __cuda_array_interface__ = {"shape": (int(nbytes),), "typestr": "|u1", "data": (int(ptr), False),
                                     "version": 3, "strides": None}
     return torch.as_tensor(_Cuda(), device="cuda")
+
+
+KINDS = {0: "remap", 1: "section", 2: "section_backward", 3: "batched_remap"}
+OP_NAMES = {v: k for k, v in OPS.items()}
+
+
+def adha_profile_start(max_records=4096):
+    check(_lib.load().adha_profile_start(int(max_records)), "adha_profile_start")
+
+
+def adha_profile_stop(max_records=4096):
+    """List of dicts (kind, op, bytes, ms) of the launches recorded since adha_profile_start."""
+    recs = (_lib.adha_launch_record * max_records)()
+    n = ctypes.c_int32(0)
+    check(_lib.load().adha_profile_stop(recs, max_records, ctypes.byref(n)), "adha_profile_stop")
+    return [dict(kind=KINDS.get(recs[k].kind, recs[k].kind), op=OP_NAMES.get(recs[k].op, recs[k].op),
+                 bytes=recs[k].bytes, ms=recs[k].ms) for k in range(min(n.value, max_records))]

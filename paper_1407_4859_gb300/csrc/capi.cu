@@ -175,6 +175,33 @@ void tanh_coefficients(float p[8], float q[8]) {
   }
 }
 
+// ------------------------------------------------------------------ launch profiler
+// When on, every kernel the calling thread launches is bracketed by two CUDA events on its
+// stream and tagged with its kind, op and algorithmic bytes (what the method must move).
+struct ProfRec {
+  int kind, op;
+  double bytes;
+  cudaEvent_t a, b;
+};
+static thread_local bool t_prof_on = false;
+static thread_local std::vector<ProfRec> t_prof;
+static thread_local std::vector<cudaEvent_t> t_pool;
+static thread_local size_t t_pool_used = 0;
+
+template <class Fn>
+static int profiled(int kind, int op, double bytes, void* stream, Fn launch) {
+  if (!t_prof_on || t_pool_used + 2 > t_pool.size()) return launch();
+  ProfRec r{kind, op, bytes, t_pool[t_pool_used], t_pool[t_pool_used + 1]};
+  t_pool_used += 2;
+  cudaError_t e = cudaEventRecord(r.a, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord(profile)");
+  if (int rc = launch()) return rc;
+  e = cudaEventRecord(r.b, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord(profile)");
+  t_prof.push_back(r);
+  return 0;
+}
+
 // ------------------------------------------------------------------ remap planning
 struct RemapPlan {
   RemapArgs args;
@@ -513,13 +540,46 @@ static int plan_section(const Layout& L, void* const* ptrs, const adha_section* 
   return finish_grid(a.n_chunks, blocks, &plan->grid);
 }
 
-int remap_layouts(const Layout& S, const void* const* src_ptrs, const Layout& D, void* const* dst_ptrs, int64_t n,
-                  void* stream, int* launched) {
+static double remap_bytes(const RemapArgs& a, const Layout& D, const std::vector<int>& built) {
+  double b = 0;
+  for (int d : built)
+    for (int f : D.groups[d]) b += dtype_size(D.dtype[f]);
+  return 2.0 * (double)a.n * b;
+}
+
+static double section_bytes(const Layout& L, const adha_section* s, int64_t n, bool save) {
+  double b = 0;
+  const uint64_t rw = s->read_mask | s->write_mask;
+  for (int f = 0; f < L.F; ++f) {
+    const int sz = dtype_size(L.dtype[f]);
+    if (has(rw, f)) b += sz;
+    if (has(s->write_mask, f)) b += sz;
+    if (has(s->read_at_perm_mask, f)) b += sz;
+  }
+  if (s->op == ADHA_OP_GATHER) b += 4;
+  if (save) b += 4;
+  return b * (double)n;
+}
+
+static int do_remap(const Layout& S, const void* const* src_ptrs, const Layout& D, void* const* dst_ptrs, int64_t n,
+                    void* stream, int* launched) {
   RemapPlan plan;
   if (int rc = plan_remap(S, src_ptrs, D, dst_ptrs, n, &plan)) return rc;
   if (launched) *launched = plan.empty ? 0 : 1;
   if (plan.empty) return 0;
-  return launch_remap(plan.args, plan.grid, plan.smem, stream);
+  std::vector<int> built;
+  for (int d = 0; d < D.n_groups; ++d) {
+    bool alias = false;
+    for (int j = 0; j < S.n_groups; ++j) alias = alias || (same_group(D, d, S, j) && dst_ptrs[d] == src_ptrs[j]);
+    if (!alias) built.push_back(d);
+  }
+  return profiled(0, 0, remap_bytes(plan.args, D, built), stream,
+                  [&] { return launch_remap(plan.args, plan.grid, plan.smem, stream); });
+}
+
+int remap_layouts(const Layout& S, const void* const* src_ptrs, const Layout& D, void* const* dst_ptrs, int64_t n,
+                  void* stream, int* launched) {
+  return do_remap(S, src_ptrs, D, dst_ptrs, n, stream, launched);
 }
 
 int run_section_layout(const Layout& L, void* const* ptrs, const adha_section* s, int64_t n, void* save, void* stream) {
@@ -527,7 +587,8 @@ int run_section_layout(const Layout& L, void* const* ptrs, const adha_section* s
   if (n == 0) return 0;
   SectionPlan plan;
   if (int rc = plan_section(L, ptrs, s, n, save, &plan)) return rc;
-  return launch_section(plan.args, plan.grid, plan.smem, stream);
+  return profiled(1, s->op, section_bytes(L, s, n, save != nullptr), stream,
+                  [&] { return launch_section(plan.args, plan.grid, plan.smem, stream); });
 }
 
 }  // namespace adha
@@ -563,10 +624,7 @@ int adha_remap(const adha_schema* schema, int64_t n, const adha_layout* src, con
   if (n == 0) return 0;
   if (int rc = check_ptrs(src_ptrs, S.n_groups, "source")) return rc;
   if (int rc = check_ptrs(reinterpret_cast<const void* const*>(dst_ptrs), D.n_groups, "destination")) return rc;
-  RemapPlan plan;
-  if (int rc = plan_remap(S, src_ptrs, D, dst_ptrs, n, &plan)) return rc;
-  if (plan.empty) return 0;
-  return launch_remap(plan.args, plan.grid, plan.smem, stream);
+  return do_remap(S, src_ptrs, D, dst_ptrs, n, stream, nullptr);
 }
 
 int adha_run_section(const adha_schema* schema, int64_t n, const adha_layout* layout, void* const* ptrs,
@@ -581,9 +639,7 @@ int adha_run_section(const adha_schema* schema, int64_t n, const adha_layout* la
   if (save && reinterpret_cast<uintptr_t>(save) % 4) return fail(ADHA_EINVAL, "save buffer is not 4-byte aligned");
   if (section->op == ADHA_OP_GATHER && reinterpret_cast<uintptr_t>(section->perm) % 16)
     return fail(ADHA_EINVAL, "perm is not 16-byte aligned");
-  SectionPlan plan;
-  if (int rc = plan_section(L, ptrs, section, n, save, &plan)) return rc;
-  return launch_section(plan.args, plan.grid, plan.smem, stream);
+  return run_section_layout(L, ptrs, section, n, save, stream);
 }
 
 int adha_section_backward(const adha_schema* schema, int64_t n, const adha_layout* layout, void* const* state_ptrs,
@@ -622,7 +678,44 @@ int adha_section_backward(const adha_schema* schema, int64_t n, const adha_layou
   }
   a.save = static_cast<const float*>(save);
   tanh_coefficients(a.tanh_p, a.tanh_q);
-  return launch_backward(a, stream);
+  const double bytes = (double)n * (section->op == ADHA_OP_MUL ? 40.0 : 28.0);
+  return profiled(2, section->op, bytes, stream, [&] { return launch_backward(a, stream); });
+}
+
+int adha_profile_start(int32_t max_records) {
+  clear_error();
+  if (max_records < 1 || max_records > (1 << 20)) return fail(ADHA_EINVAL, "max_records %d not in [1, 2^20]", max_records);
+  while (t_pool.size() < 2 * (size_t)max_records) {
+    cudaEvent_t e;
+    cudaError_t err = cudaEventCreate(&e);
+    if (err != cudaSuccess) return cuda_fail(err, "cudaEventCreate(profile)");
+    t_pool.push_back(e);
+  }
+  t_prof.clear();
+  t_pool_used = 0;
+  t_prof_on = true;
+  return 0;
+}
+
+int adha_profile_stop(adha_launch_record* out, int32_t max_records, int32_t* n_records) {
+  clear_error();
+  t_prof_on = false;
+  if (!n_records) return fail(ADHA_EINVAL, "n_records is NULL");
+  int32_t k = 0;
+  for (const ProfRec& r : t_prof) {
+    if (out && k < max_records) {
+      cudaError_t e = cudaEventSynchronize(r.b);
+      float ms = 0;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+      if (e != cudaSuccess) return cuda_fail(e, "profile event");
+      out[k] = adha_launch_record{r.kind, r.op, r.bytes, (double)ms};
+    }
+    ++k;
+  }
+  *n_records = k;
+  t_prof.clear();
+  t_pool_used = 0;
+  return 0;
 }
 
 int adha_tune_override(int32_t chunk_records) {
