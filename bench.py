@@ -198,6 +198,9 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the AoS/SoA/exhaustive program comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle timing")
     ap.add_argument("--n-log2", type=int, default=24, help="records per GPU (default 2^24, the workload's size)")
+    ap.add_argument("--cost-cache", default=None,
+                    help="JSON file holding the measured cost table: loaded when it matches the GPU, workload and "
+                         "candidates, written after measuring otherwise")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -236,9 +239,23 @@ def main():
     cand = P.adha_plan_sections(S, secs, opts)
     L = len(cand)
     t0 = time.perf_counter()
-    costs = P.adha_measure(S, n, AOS, in_buf, secs, cand, reps=2)
+    cache_key = {"gpu": torch.cuda.get_device_name(local), "workload": wl.name, "n": n,
+                 "candidates": [l.groups for l in cand.layouts], "csrc": csrc_hash()}
+    costs = None
+    if args.cost_cache and os.path.exists(args.cost_cache):
+        d = json.load(open(args.cost_cache))
+        if d.get("key") == cache_key:
+            costs = P.adha_cost_table_create(len(wl.sections), L)
+            costs.set(d["section_ns"], d["remap_ns"])
+            P.adha_tune_import(d.get("tuning", ""))
+            log("cost table and tuning loaded from %s" % args.cost_cache)
+    if costs is None:
+        costs = P.adha_measure(S, n, AOS, in_buf, secs, cand, reps=2, autotune=True)
+        if args.cost_cache:
+            json.dump({"key": cache_key, "section_ns": costs.section_ns, "remap_ns": costs.remap_ns,
+                       "tuning": P.adha_tune_export()}, open(args.cost_cache, "w"))
     measure_s = time.perf_counter() - t0
-    log("%d candidates measured in %.1f s" % (L, measure_s))
+    log("%d candidates, cost table ready in %.1f s" % (L, measure_s))
     ws = torch.empty(P.adha_program_workspace_bytes(S, n, AOS, cand), dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -262,11 +279,13 @@ def main():
     torch.cuda.synchronize()
     P.adha_profile_start(64 * args.steps)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
     e0.record(stream)
     for _ in range(args.steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     recs = P.adha_profile_stop(64 * args.steps)
     if dist:
         dist.barrier()

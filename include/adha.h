@@ -262,6 +262,9 @@ typedef struct {
   void* final_ptrs[ADHA_MAX_FIELDS];              /* out: device buffers of the result's groups */
 } adha_plan;
 
+/* adha_measure flags. */
+#define ADHA_MEASURE_AUTOTUNE 1   /* time every section launch shape, keep the fastest for later launches */
+
 /* Workspace bytes adha_measure needs: two copies of the widest candidate (or input) layout. */
 size_t adha_measure_workspace_bytes(const adha_schema* schema, int64_t n, const adha_layout* in_layout,
                                     const adha_layout_set* candidates);
@@ -274,12 +277,16 @@ size_t adha_measure_workspace_bytes(const adha_schema* schema, int64_t n, const 
  * copied into the workspace, so it is not modified.  Each entry is one warm-up
  * call, then the faster of two batches of `reps` calls timed with CUDA events
  * on `stream`, in whole nanoseconds.  A remap between layouts sharing a group
- * leaves that group in place, as the executor does.  Synchronizes `stream`;
- * *out is a library-owned table (adha_free).
+ * leaves that group in place, as the executor does.  With ADHA_MEASURE_AUTOTUNE
+ * in flags each section is timed under every launch shape (records per chunk
+ * 32, 64, 128 x field-wise or whole-group stores); the fastest enters the table
+ * and the library's tuning cache, which later launches of the same section,
+ * layout and size class use.  Synchronizes `stream`; *out is a library-owned
+ * table (adha_free).
  */
 int adha_measure(const adha_schema* schema, int64_t n, const adha_layout* in_layout, void* const* in_ptrs,
                  const adha_section* sections, int32_t n_sec, const adha_layout_set* candidates, int32_t reps,
-                 void* workspace, size_t ws_bytes, adha_stream stream, adha_cost_table** out);
+                 int32_t flags, void* workspace, size_t ws_bytes, adha_stream stream, adha_cost_table** out);
 
 /* Workspace bytes adha_run_program needs: three copies of the widest candidate layout. */
 size_t adha_program_workspace_bytes(const adha_schema* schema, int64_t n, const adha_layout* in_layout,
@@ -309,6 +316,26 @@ int adha_run_program(const adha_schema* schema, int64_t n, const adha_layout* in
  * autotuner sets it while it times candidates.  Host only.
  */
 int adha_tune_override(int32_t chunk_records);
+
+/*
+ * How section kernels launched later by the calling thread store into staged
+ * groups wider than 8 bytes: 0 = automatic (a group whose written fields make
+ * up at least a quarter of its struct is updated in shared memory and written
+ * back whole with 16-byte stores; other written fields are stored one by one),
+ * 1 = always field by field, 2 = always whole.  Host only.
+ */
+int adha_tune_writeback(int32_t mode);
+
+/* Empties the library's tuning cache (process-wide).  Host only. */
+int adha_tune_clear(void);
+
+/* Writes the tuning cache as text ("key<TAB>records<TAB>mode" lines) into buf
+ * (len bytes, NUL-terminated); *needed = bytes required.  buf may be NULL to
+ * ask for the size.  Host only. */
+int adha_tune_export(char* buf, size_t len, size_t* needed);
+
+/* Adds the entries of a text made by adha_tune_export to the cache.  Host only. */
+int adha_tune_import(const char* text);
 
 /* One kernel launch seen by the profiler.  kind: 0 remap, 1 section, 2 section
  * backward, 3 batched remap; op: the section's adha_op (0 for remaps); bytes:

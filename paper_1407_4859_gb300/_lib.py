@@ -81,6 +81,10 @@ SIGNATURES = {
                                              _PP, ctypes.POINTER(adha_section), _P, _P]),
     "adha_device_status": (ctypes.c_int, [_P, ctypes.POINTER(_I32)]),
     "adha_tune_override": (ctypes.c_int, [_I32]),
+    "adha_tune_writeback": (ctypes.c_int, [_I32]),
+    "adha_tune_clear": (ctypes.c_int, []),
+    "adha_tune_export": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+    "adha_tune_import": (ctypes.c_int, [ctypes.c_char_p]),
     "adha_profile_start": (ctypes.c_int, [_I32]),
     "adha_profile_stop": (ctypes.c_int, [ctypes.POINTER(adha_launch_record), _I32, ctypes.POINTER(_I32)]),
     "adha_ods": (ctypes.c_int, [ctypes.POINTER(adha_schema), ctypes.POINTER(adha_section), _I32, _I32,
@@ -95,8 +99,8 @@ SIGNATURES = {
     "adha_measure_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(adha_schema), _I64, ctypes.POINTER(adha_layout),
                                                        ctypes.POINTER(adha_layout_set)]),
     "adha_measure": (ctypes.c_int, [ctypes.POINTER(adha_schema), _I64, ctypes.POINTER(adha_layout), _PP,
-                                    ctypes.POINTER(adha_section), _I32, ctypes.POINTER(adha_layout_set), _I32, _P,
-                                    ctypes.c_size_t, _P, ctypes.POINTER(ctypes.POINTER(adha_cost_table))]),
+                                    ctypes.POINTER(adha_section), _I32, ctypes.POINTER(adha_layout_set), _I32, _I32,
+                                    _P, ctypes.c_size_t, _P, ctypes.POINTER(ctypes.POINTER(adha_cost_table))]),
     "adha_program_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(adha_schema), _I64, ctypes.POINTER(adha_layout),
                                                        ctypes.POINTER(adha_layout_set)]),
     "adha_run_program": (ctypes.c_int, [ctypes.POINTER(adha_schema), _I64, ctypes.POINTER(adha_layout), _PP,

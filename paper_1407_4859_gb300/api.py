@@ -130,6 +130,26 @@ def adha_tune_override(chunk_records=0):
     check(_lib.load().adha_tune_override(int(chunk_records)), "adha_tune_override")
 
 
+def adha_tune_writeback(mode=0):
+    check(_lib.load().adha_tune_writeback(int(mode)), "adha_tune_writeback")
+
+
+def adha_tune_clear():
+    check(_lib.load().adha_tune_clear(), "adha_tune_clear")
+
+
+def adha_tune_export():
+    need = ctypes.c_size_t(0)
+    check(_lib.load().adha_tune_export(None, 0, ctypes.byref(need)), "adha_tune_export")
+    buf = ctypes.create_string_buffer(need.value)
+    check(_lib.load().adha_tune_export(buf, need.value, ctypes.byref(need)), "adha_tune_export")
+    return buf.value.decode()
+
+
+def adha_tune_import(text):
+    check(_lib.load().adha_tune_import(text.encode()), "adha_tune_import")
+
+
 def adha_device_status(stream=None):
     v = ctypes.c_int32(0)
     check(_lib.load().adha_device_status(_stream_ptr(stream), ctypes.byref(v)), "adha_device_status")
@@ -279,14 +299,19 @@ def adha_measure_workspace_bytes(schema, n, in_layout, candidates):
                                                     candidates.ptr)
 
 
-def adha_measure(schema, n, in_layout, in_bufs, sections, candidates, reps=2, workspace=None, stream=None):
+ADHA_MEASURE_AUTOTUNE = 1
+
+
+def adha_measure(schema, n, in_layout, in_bufs, sections, candidates, reps=2, workspace=None, stream=None,
+                 autotune=False):
     """Cost table of every section in every candidate and every remap between candidates."""
     secs = sections if isinstance(sections, Sections) else Sections(sections)
     need = adha_measure_workspace_bytes(schema, n, in_layout, candidates)
     ws = workspace if workspace is not None else torch.empty(need, dtype=torch.uint8, device=in_bufs[0].device)
     out = ctypes.POINTER(adha_cost_table)()
     check(_lib.load().adha_measure(ctypes.byref(schema.c), int(n), ctypes.byref(in_layout.c), _ptrs(in_bufs),
-                                   secs.arr, len(secs), candidates.ptr, int(reps), ws.data_ptr(), ws.numel(),
+                                   secs.arr, len(secs), candidates.ptr, int(reps),
+                                   ADHA_MEASURE_AUTOTUNE if autotune else 0, ws.data_ptr(), ws.numel(),
                                    _stream_ptr(stream), ctypes.byref(out)), "adha_measure")
     return CostTable(out)
 

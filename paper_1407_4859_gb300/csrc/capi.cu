@@ -212,6 +212,38 @@ struct RemapPlan {
 
 // Chunk / pipeline override for the autotuner (0 = default rule).
 static thread_local int t_tile_override = 0;
+static thread_local int t_writeback_mode = 0;   // 0 automatic, 1 never, 2 every wide written group
+
+// Autotuned launch shapes: section key -> (records per chunk, writeback mode).
+static std::mutex g_tune_mu;
+static std::map<std::string, std::pair<int, int>> g_tune;
+
+static std::string section_key(const Layout& L, const adha_section* s, int64_t n, bool save) {
+  std::string k = "S" + std::to_string(s->op) + ":" + std::to_string(s->read_mask) + ":" +
+                  std::to_string(s->write_mask) + ":" + std::to_string(s->read_at_perm_mask) + ":" +
+                  std::to_string(save ? 1 : 0) + ":";
+  for (int a = 0; a < 8; ++a) k += std::to_string(s->arg[a]) + ",";
+  k += ":L";
+  for (const auto& g : L.groups) {
+    for (int f : g) k += std::to_string(f) + "." + std::to_string(L.dtype[f]) + ",";
+    k += "|";
+  }
+  int lg = 0;
+  while (lg < 62 && (int64_t(1) << (lg + 1)) <= n) ++lg;
+  return k + ":n" + std::to_string(lg);
+}
+
+std::string tuning_key(const Layout& L, const adha_section* s, int64_t n, bool save) { return section_key(L, s, n, save); }
+
+void tuning_store(const std::string& key, int R, int wb) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = {R, wb};
+}
+
+void set_overrides(int R, int wb) {
+  t_tile_override = R;
+  t_writeback_mode = wb;
+}
 
 // Records per warp chunk: a multiple of 32 with about `target` bytes of the widest side.
 static int pick_chunk(int rec_bytes, int target, int rmax) {
@@ -469,9 +501,20 @@ static int plan_section(const Layout& L, void* const* ptrs, const adha_section* 
                         SectionPlan* plan) {
   SectionArgs& a = plan->args;
   std::memset(&a, 0, sizeof a);
+  int tuned_R = t_tile_override, wb_mode = t_writeback_mode;
+  if (!tuned_R && !wb_mode) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(section_key(L, s, n, save != nullptr));
+    if (it != g_tune.end()) {
+      tuned_R = it->second.first;
+      wb_mode = it->second.second;
+    }
+  }
   uint64_t staged = s->read_mask;
   if (s->op == ADHA_OP_MIX) staged |= s->write_mask;
   if (save) staged |= 1ull << (s->op == ADHA_OP_MUL ? s->arg[2] : s->arg[1]);
+  // Every group the section reads is staged through shared memory: the double-buffered copies
+  // keep a chunk in flight per warp while the previous one is computed.
   std::vector<int> groups;
   for (int g = 0; g < L.n_groups; ++g) {
     bool any = false;
@@ -481,7 +524,8 @@ static int plan_section(const Layout& L, void* const* ptrs, const adha_section* 
   int rec = 0;
   for (int g : groups) rec += L.stride[g];
   if (s->op == ADHA_OP_GATHER) rec += 4;
-  int R = t_tile_override ? t_tile_override : pick_chunk(rec, 2048, 1024);
+  int R = tuned_R ? std::min(tuned_R, 128) : (rec > 0 ? pick_chunk(rec, 4096, 128) : 128);
+  if (R == 96) R = 64;
   for (;;) {
     a.n = n;
     a.R = R;
@@ -498,22 +542,33 @@ static int plan_section(const Layout& L, void* const* ptrs, const adha_section* 
       a.f[f].gs = L.stride[g];
       a.f[f].s0 = -1;
       a.f[f].ss = 0;
+      a.f[f].wsm = 0;
       a.f[f].dtype = L.dtype[f];
     }
     int off = 0;
+    a.n_writeback = 0;
     for (int k = 0; k < a.n_load; ++k) {
       const int g = groups[k];
       a.load[k].ptr = static_cast<const uint8_t*>(ptrs[g]);
       a.load[k].stride = L.stride[g];
       a.load[k].start = off;
+      // A wide group with written fields is updated in the chunk buffer and written back whole:
+      // one coalesced store stream instead of scattered partial-record stores.
+      int written = 0;
+      for (int f : L.groups[g]) written += has(s->write_mask, f) ? dtype_size(L.dtype[f]) : 0;
+      const bool wide = L.stride[g] > 8 && written > 0;
+      a.writeback[k] = (int8_t)(wb_mode == 1 ? 0 : wb_mode == 2 ? wide : (wide && 4 * written >= L.stride[g]));
+      a.n_writeback += a.writeback[k];
       for (int f : L.groups[g]) {
         a.f[f].s0 = off + L.offset_of[f];
         a.f[f].ss = L.stride[g];
+        a.f[f].wsm = a.writeback[k];
       }
       off += R * L.stride[g];
     }
     if (s->op == ADHA_OP_GATHER) {
       a.perm_slot = a.n_load;
+      a.writeback[a.n_load] = 0;
       a.load[a.n_load].ptr = reinterpret_cast<const uint8_t*>(s->perm);
       a.load[a.n_load].stride = 4;
       a.load[a.n_load].start = off;
@@ -523,7 +578,7 @@ static int plan_section(const Layout& L, void* const* ptrs, const adha_section* 
     plan->smem = section_smem_bytes(a);
     if (plan->smem <= (size_t)kSmemLimit) break;
     if (R <= 32) return fail(ADHA_EINVAL, "section records too wide for a 32-record chunk");
-    R = std::max(32, R / 2 / 32 * 32);
+    R /= 2;
   }
   for (int k = 0; k < 8; ++k) a.arg[k] = s->arg[k];
   for (int k = 0; k < 4; ++k) a.par[k] = s->fparam[k];
@@ -723,6 +778,55 @@ int adha_tune_override(int32_t chunk_records) {
   if (chunk_records < 0 || chunk_records % 32 != 0 || chunk_records > 1024)
     return fail(ADHA_EINVAL, "chunk %d is not a multiple of 32 in [0, 1024]", chunk_records);
   t_tile_override = chunk_records;
+  return 0;
+}
+
+int adha_tune_clear(void) {
+  clear_error();
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune.clear();
+  return 0;
+}
+
+int adha_tune_export(char* buf, size_t len, size_t* needed) {
+  clear_error();
+  std::string text;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (const auto& kv : g_tune)
+      text += kv.first + "\t" + std::to_string(kv.second.first) + "\t" + std::to_string(kv.second.second) + "\n";
+  }
+  if (needed) *needed = text.size() + 1;
+  if (buf && len > text.size()) std::memcpy(buf, text.c_str(), text.size() + 1);
+  else if (buf && len) return fail(ADHA_ENOMEM, "export buffer of %zu bytes is too small (%zu needed)", len, text.size() + 1);
+  return 0;
+}
+
+int adha_tune_import(const char* text) {
+  clear_error();
+  if (!text) return fail(ADHA_EINVAL, "text is NULL");
+  std::map<std::string, std::pair<int, int>> parsed;
+  const char* p = text;
+  while (*p) {
+    const char* eol = std::strchr(p, '\n');
+    std::string line(p, eol ? (size_t)(eol - p) : std::strlen(p));
+    p = eol ? eol + 1 : p + line.size();
+    if (line.empty()) continue;
+    const size_t t1 = line.find('\t'), t2 = line.find('\t', t1 == std::string::npos ? 0 : t1 + 1);
+    if (t1 == std::string::npos || t2 == std::string::npos) return fail(ADHA_EINVAL, "bad tuning line: %s", line.c_str());
+    const int R = std::atoi(line.c_str() + t1 + 1), wb = std::atoi(line.c_str() + t2 + 1);
+    if (R < 0 || R > 128 || R % 32 || wb < 0 || wb > 2) return fail(ADHA_EINVAL, "bad tuning values: %s", line.c_str());
+    parsed[line.substr(0, t1)] = {R, wb};
+  }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (const auto& kv : parsed) g_tune[kv.first] = kv.second;
+  return 0;
+}
+
+int adha_tune_writeback(int32_t mode) {
+  clear_error();
+  if (mode < 0 || mode > 2) return fail(ADHA_EINVAL, "writeback mode %d not in [0, 2]", mode);
+  t_writeback_mode = mode;
   return 0;
 }
 

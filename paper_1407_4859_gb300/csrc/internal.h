@@ -91,6 +91,7 @@ struct FieldRef {
   int32_t s0;       // byte offset within a chunk buffer of the field in chunk record 0, -1 if not staged
   int32_t ss;       // stride within the chunk buffer
   int32_t dtype;
+  int32_t wsm;      // 1: writes go into the chunk buffer and the whole slice is written back
 };
 
 struct SectionArgs {
@@ -103,6 +104,8 @@ struct SectionArgs {
   int32_t perm_slot;            // index of the staged perm slice (GATHER), else -1
   uint64_t R_mask, W_mask;
   GroupRef load[kMaxGroups + 1];
+  int8_t writeback[kMaxGroups + 1];   // staged slice k is written back whole after the chunk
+  int32_t n_writeback;
   FieldRef f[kMaxFields];
   int32_t arg[8];
   float par[4];
@@ -112,6 +115,10 @@ int remap_layouts(const Layout& S, const void* const* src_ptrs, const Layout& D,
 int run_section_layout(const Layout& L, void* const* ptrs, const adha_section* s, int64_t n, void* save,
                        void* stream);
 adha_layout set_layout(const adha_layout_set* s, int l);
+// Autotuning: the key of a section launch, storing its best shape, thread-local overrides.
+std::string tuning_key(const Layout& L, const adha_section* s, int64_t n, bool save);
+void tuning_store(const std::string& key, int R, int wb);
+void set_overrides(int R, int wb);
 int pdl_solve(const adha_cost_table* c, int return_to_input, int32_t* seq, double* total);
 
 // tanh polynomial coefficients (7 used each)
@@ -142,6 +149,10 @@ int remap_layouts(const Layout& S, const void* const* src_ptrs, const Layout& D,
 int run_section_layout(const Layout& L, void* const* ptrs, const adha_section* s, int64_t n, void* save,
                        void* stream);
 adha_layout set_layout(const adha_layout_set* s, int l);
+// Autotuning: the key of a section launch, storing its best shape, thread-local overrides.
+std::string tuning_key(const Layout& L, const adha_section* s, int64_t n, bool save);
+void tuning_store(const std::string& key, int R, int wb);
+void set_overrides(int R, int wb);
 int pdl_solve(const adha_cost_table* c, int return_to_input, int32_t* seq, double* total);
 
 // tanh polynomial coefficients (Lambert's continued fraction cut after 25): 7 each, rounded once.

@@ -147,7 +147,7 @@ size_t adha_measure_workspace_bytes(const adha_schema* schema, int64_t n, const 
 
 int adha_measure(const adha_schema* schema, int64_t n, const adha_layout* in_layout, void* const* in_ptrs,
                  const adha_section* sections, int32_t n_sec, const adha_layout_set* candidates, int32_t reps,
-                 void* workspace, size_t ws_bytes, adha_stream stream, adha_cost_table** out) {
+                 int32_t flags, void* workspace, size_t ws_bytes, adha_stream stream, adha_cost_table** out) {
   clear_error();
   Layout in;
   std::vector<Layout> cand;
@@ -186,7 +186,28 @@ int adha_measure(const adha_schema* schema, int64_t n, const adha_layout* in_lay
     carve(cand[a], n, A, &pa);
     rc = remap_layouts(in, in_p.data(), cand[a], pa.data(), n, stream, nullptr);
     for (int k = 0; k < n_sec && !rc; ++k) {
-      rc = time_ns(timer, stream, reps, [&] { return run_section_layout(cand[a], pa.data(), &sections[k], n, nullptr, stream); }, &ns);
+      auto run = [&] { return run_section_layout(cand[a], pa.data(), &sections[k], n, nullptr, stream); };
+      if (flags & ADHA_MEASURE_AUTOTUNE) {
+        // every chunk size x store mode; the fastest is kept for the executor
+        double best = -1;
+        int bR = 0, bW = 0;
+        for (int R = 32; R <= 128 && !rc; R *= 2)
+          for (int wb = 1; wb <= 2 && !rc; ++wb) {
+            set_overrides(R, wb);
+            rc = time_ns(timer, stream, reps, run, &ns);
+            if (!rc && (best < 0 || ns < best)) {
+              best = ns;
+              bR = R;
+              bW = wb;
+            }
+          }
+        set_overrides(0, 0);
+        if (rc) break;
+        tuning_store(tuning_key(cand[a], &sections[k], n, false), bR, bW);
+        ns = best;
+      } else {
+        rc = time_ns(timer, stream, reps, run, &ns);
+      }
       t->section_ns[(size_t)k * L + a] = ns;
     }
     for (int b = 0; b <= L && !rc; ++b) {

@@ -2,11 +2,11 @@
 // data-parallel loop; its layout decides which bytes it drags through memory) and the reverse
 // (adjoint) kernel of the fp32 chain sections.
 //
-// The forward kernel works per warp on chunks of R records, like remap.cu: it copies the chunk's
-// slice of every group that holds a field the section reads into its own shared buffer (16-byte
-// cp.async, one chunk ahead), computes each record from the staged bytes, and stores the
-// written fields straight to global memory (a partial-record store touches only the sectors of
-// the written field).  The op is a template parameter; the layout is
+// The forward kernel works per warp on chunks of R = 32*M records, like remap.cu: it copies the
+// chunk's slice of every group that holds a field the section reads into its own shared buffer
+// (16-byte cp.async, one chunk ahead), computes the M records of each lane from the staged
+// bytes, and stores the written fields straight to global memory (a partial-record store
+// touches only the sectors of the written field).  The op is a template parameter; the layout is
 // the FieldRef table (where each field sits in the stage and in global memory).  Every floating
 // operation is an explicitly rounded-to-nearest intrinsic, so no contraction can change a bit.
 #include <cuda_runtime.h>
@@ -16,18 +16,29 @@
 
 namespace adha {
 
-struct StagedRec {      // loads from the stage tile
+// per-CTA slice table at the start of shared memory: pointers, slice ends, write-back flags
+constexpr int kSectionTable = (16 * (kMaxGroups + 1) + 15) / 16 * 16;
+
+struct StagedRec {      // record r of a staged chunk (global record i)
   const SectionArgs* a;
-  const uint8_t* stage;
+  uint8_t* stage;
   int r;
+  int64_t i;
   template <class V>
   __device__ __forceinline__ V ld(int f) const {
     const FieldRef& F = a->f[f];
-    return *reinterpret_cast<const V*>(stage + F.s0 + r * F.ss);
+    if (F.s0 >= 0) return *reinterpret_cast<const V*>(stage + F.s0 + r * F.ss);
+    return *reinterpret_cast<const V*>(F.g + i * F.gs);
+  }
+  template <class V>
+  __device__ __forceinline__ void st(int f, V v) const {
+    const FieldRef& F = a->f[f];
+    if (F.wsm) *reinterpret_cast<V*>(stage + F.s0 + r * F.ss) = v;
+    else *reinterpret_cast<V*>(F.g + i * F.gs) = v;
   }
 };
 
-struct GlobalRec {      // loads from global memory (ragged tail)
+struct GlobalRec {      // record i in global memory (ragged tail)
   const SectionArgs* a;
   int64_t i;
   template <class V>
@@ -35,12 +46,12 @@ struct GlobalRec {      // loads from global memory (ragged tail)
     const FieldRef& F = a->f[f];
     return *reinterpret_cast<const V*>(F.g + i * F.gs);
   }
+  template <class V>
+  __device__ __forceinline__ void st(int f, V v) const {
+    const FieldRef& F = a->f[f];
+    *reinterpret_cast<V*>(F.g + i * F.gs) = v;
+  }
 };
-
-template <class V>
-__device__ __forceinline__ void gst(const SectionArgs& a, int f, int64_t i, V v) {
-  *reinterpret_cast<V*>(a.f[f].g + i * a.f[f].gs) = v;
-}
 
 template <class V>
 __device__ __forceinline__ V gld(const SectionArgs& a, int f, int64_t i) {
@@ -61,17 +72,84 @@ __device__ __forceinline__ float tanh_cf(float x, const float* P, const float* Q
   return __fdiv_rn(__fmul_rn(x, q), p);
 }
 
+// MIX over the M records r = lane + 32m of a staged chunk, field-major: every field's shared
+// and global addresses are computed once for the M records.
+template <int M>
+__device__ __forceinline__ void mix_chunk(const SectionArgs& a, uint8_t* stage, int64_t i0, int lane) {
+  float s[M];
+  uint32_t h[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    s[m] = 0.0f;
+    h[m] = 0u;
+  }
+  // V value of field F for the lane's record m: from the chunk buffer if staged, else global
+#define ADHA_MIX_READ(V, LIST, BODY)                                                        \
+  for (int j = 0; j < a.n_rd[LIST]; ++j) {                                                  \
+    const FieldRef& F = a.f[a.rd[LIST][j]];                                                 \
+    if (F.s0 >= 0) {                                                                        \
+      const uint8_t* p = stage + F.s0 + lane * F.ss;                                        \
+      _Pragma("unroll") for (int m = 0; m < M; ++m) {                                       \
+        const V v = *reinterpret_cast<const V*>(p + m * 32 * F.ss);                         \
+        BODY;                                                                               \
+      }                                                                                     \
+    } else {                                                                                \
+      const uint8_t* p = F.g + (i0 + lane) * F.gs;                                          \
+      _Pragma("unroll") for (int m = 0; m < M; ++m) {                                       \
+        const V v = *reinterpret_cast<const V*>(p + (int64_t)m * 32 * F.gs);                \
+        BODY;                                                                               \
+      }                                                                                     \
+    }                                                                                       \
+  }
+  ADHA_MIX_READ(float, ADHA_F32, s[m] = __fadd_rn(s[m], v))
+  ADHA_MIX_READ(unsigned long long, ADHA_F64, h[m] ^= (uint32_t)v ^ (uint32_t)(v >> 32))
+  ADHA_MIX_READ(uint32_t, ADHA_I32, h[m] ^= v)
+  ADHA_MIX_READ(uint16_t, ADHA_BF16, h[m] ^= (uint32_t)v)
+#undef ADHA_MIX_READ
+  float t[M];
+  uint32_t k[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    t[m] = __fadd_rn(s[m], __fmul_rn(__uint2float_rn(h[m] & 255u), 0.00390625f));
+    k[m] = (h[m] ^ __float_as_uint(t[m])) >> 3;
+  }
+  // written fields: old value from the chunk buffer if staged, else global; new value to global
+#define ADHA_MIX_WRITE(V, LIST, EXPR)                                                       \
+  for (int j = 0; j < a.n_wr[LIST]; ++j) {                                                  \
+    const FieldRef& F = a.f[a.wr[LIST][j]];                                                 \
+    uint8_t* p = stage + F.s0 + lane * F.ss;                                                \
+    if (F.wsm) {                                                                            \
+      _Pragma("unroll") for (int m = 0; m < M; ++m) {                                       \
+        V* x = reinterpret_cast<V*>(p + m * 32 * F.ss);                                     \
+        const V old = *x;                                                                   \
+        *x = EXPR;                                                                          \
+      }                                                                                     \
+    } else {                                                                                \
+      uint8_t* q = F.g + (i0 + lane) * F.gs;                                                \
+      _Pragma("unroll") for (int m = 0; m < M; ++m) {                                       \
+        const V old = *reinterpret_cast<const V*>(p + m * 32 * F.ss);                       \
+        *reinterpret_cast<V*>(q + (int64_t)m * 32 * F.gs) = EXPR;                           \
+      }                                                                                     \
+    }                                                                                       \
+  }
+  ADHA_MIX_WRITE(float, ADHA_F32, __fadd_rn(__fmul_rn(old, 0.5f), t[m]))
+  ADHA_MIX_WRITE(double, ADHA_F64, __dadd_rn(__dmul_rn(old, 0.5), (double)t[m]))
+  ADHA_MIX_WRITE(uint32_t, ADHA_I32, old ^ k[m])
+  ADHA_MIX_WRITE(uint16_t, ADHA_BF16, (uint16_t)(old ^ (uint16_t)(k[m] & 0xFFFFu)))
+#undef ADHA_MIX_WRITE
+}
+
 template <int OP, class Rec>
 __device__ __forceinline__ void run_record(const SectionArgs& a, const Rec& rec, int64_t i, int32_t pj) {
   const int* g = a.arg;
   if (OP == ADHA_OP_MADD3) {
     const float m = __fmul_rn(rec.template ld<float>(g[0]), rec.template ld<float>(g[1]));
-    gst<float>(a, g[2], i, __fadd_rn(m, rec.template ld<float>(g[2])));
+    rec.template st<float>(g[2], __fadd_rn(m, rec.template ld<float>(g[2])));
   } else if (OP == ADHA_OP_XORSHIFT) {
     const uint32_t u = rec.template ld<uint32_t>(g[0]);
-    gst<uint32_t>(a, g[1], i, u ^ (u >> 3));
+    rec.template st<uint32_t>(g[1], u ^ (u >> 3));
   } else if (OP == ADHA_OP_ADD) {
-    gst<float>(a, g[2], i, __fadd_rn(rec.template ld<float>(g[0]), rec.template ld<float>(g[1])));
+    rec.template st<float>(g[2], __fadd_rn(rec.template ld<float>(g[0]), rec.template ld<float>(g[1])));
   } else if (OP == ADHA_OP_MIX) {
     float s = 0.0f;
     uint32_t h = 0u;
@@ -86,22 +164,22 @@ __device__ __forceinline__ void run_record(const SectionArgs& a, const Rec& rec,
     const uint32_t k = (h ^ __float_as_uint(t)) >> 3;
     for (int j = 0; j < a.n_wr[ADHA_F32]; ++j) {
       const int f = a.wr[ADHA_F32][j];
-      gst<float>(a, f, i, __fadd_rn(__fmul_rn(rec.template ld<float>(f), 0.5f), t));
+      rec.template st<float>(f, __fadd_rn(__fmul_rn(rec.template ld<float>(f), 0.5f), t));
     }
     if (a.n_wr[ADHA_F64]) {
       const double td = (double)t;
       for (int j = 0; j < a.n_wr[ADHA_F64]; ++j) {
         const int f = a.wr[ADHA_F64][j];
-        gst<double>(a, f, i, __dadd_rn(__dmul_rn(rec.template ld<double>(f), 0.5), td));
+        rec.template st<double>(f, __dadd_rn(__dmul_rn(rec.template ld<double>(f), 0.5), td));
       }
     }
     for (int j = 0; j < a.n_wr[ADHA_I32]; ++j) {
       const int f = a.wr[ADHA_I32][j];
-      gst<uint32_t>(a, f, i, rec.template ld<uint32_t>(f) ^ k);
+      rec.template st<uint32_t>(f, rec.template ld<uint32_t>(f) ^ k);
     }
     for (int j = 0; j < a.n_wr[ADHA_BF16]; ++j) {
       const int f = a.wr[ADHA_BF16][j];
-      gst<uint16_t>(a, f, i, (uint16_t)(rec.template ld<uint16_t>(f) ^ (uint16_t)(k & 0xFFFFu)));
+      rec.template st<uint16_t>(f, (uint16_t)(rec.template ld<uint16_t>(f) ^ (uint16_t)(k & 0xFFFFu)));
     }
   } else if (OP == ADHA_OP_DRIFT) {
 #pragma unroll
@@ -110,7 +188,7 @@ __device__ __forceinline__ void run_record(const SectionArgs& a, const Rec& rec,
       float q = __fadd_rn(rec.template ld<float>(g[ax]), d);
       if (q >= 1.0f) q = __fsub_rn(q, 1.0f);
       else if (q < 0.0f) q = __fadd_rn(q, 1.0f);
-      gst<float>(a, g[ax], i, q);
+      rec.template st<float>(g[ax], q);
     }
   } else if (OP == ADHA_OP_BIN) {
     const int G = (int)a.par[0];
@@ -121,31 +199,31 @@ __device__ __forceinline__ void run_record(const SectionArgs& a, const Rec& rec,
       k = k < 0 ? 0 : (k > G - 1 ? G - 1 : k);
       c[ax] = k;
     }
-    gst<int32_t>(a, g[3], i, c[0] + G * (c[1] + G * c[2]));
+    rec.template st<int32_t>(g[3], c[0] + G * (c[1] + G * c[2]));
   } else if (OP == ADHA_OP_KE) {
     const float vx = rec.template ld<float>(g[0]), vy = rec.template ld<float>(g[1]),
                 vz = rec.template ld<float>(g[2]);
     float s = __fadd_rn(__fmul_rn(vx, vx), __fmul_rn(vy, vy));
     s = __fadd_rn(s, __fmul_rn(vz, vz));
     const float e = __fmul_rn(__fmul_rn(0.5f, rec.template ld<float>(g[3])), s);
-    gst<double>(a, g[4], i, (double)e);
+    rec.template st<double>(g[4], (double)e);
   } else if (OP == ADHA_OP_FLAGS) {
     const uint32_t fl = rec.template ld<uint32_t>(g[0]);
     const uint32_t bit = rec.template ld<double>(g[1]) > (double)a.par[0] ? 1u : 0u;
-    gst<uint32_t>(a, g[0], i, ((fl << 1) | bit) & 255u);
+    rec.template st<uint32_t>(g[0], ((fl << 1) | bit) & 255u);
   } else if (OP == ADHA_OP_GATHER) {
     const int64_t j = pj;
     const float c = __fmul_rn(a.par[0], gld<float>(a, g[6], j));
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
       const float d = __fsub_rn(gld<float>(a, g[3 + ax], j), 0.5f);
-      gst<float>(a, g[ax], i, __fadd_rn(rec.template ld<float>(g[ax]), __fmul_rn(c, d)));
+      rec.template st<float>(g[ax], __fadd_rn(rec.template ld<float>(g[ax]), __fmul_rn(c, d)));
     }
   } else if (OP == ADHA_OP_KICK) {
     const float c = __fmul_rn(a.par[0], rec.template ld<float>(g[3]));
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax)
-      gst<float>(a, g[ax], i, __fadd_rn(rec.template ld<float>(g[ax]), __fmul_rn(c, a.par[1 + ax])));
+      rec.template st<float>(g[ax], __fadd_rn(rec.template ld<float>(g[ax]), __fmul_rn(c, a.par[1 + ax])));
   } else {   // AXPB, MUL, TANH: z = op(x[, y]); the old z goes to `save` when asked
     const int z = OP == ADHA_OP_MUL ? g[2] : g[1];
     if (a.save) reinterpret_cast<float*>(a.save)[i] = rec.template ld<float>(z);
@@ -154,29 +232,39 @@ __device__ __forceinline__ void run_record(const SectionArgs& a, const Rec& rec,
     if (OP == ADHA_OP_AXPB) v = __fadd_rn(__fmul_rn(a.par[0], x), a.par[1]);
     else if (OP == ADHA_OP_MUL) v = __fmul_rn(x, rec.template ld<float>(g[1]));
     else v = tanh_cf(x, a.tanh_p, a.tanh_q);
-    gst<float>(a, z, i, v);
+    rec.template st<float>(z, v);
   }
 }
 
-template <int OP>
-__global__ void __launch_bounds__(kThreads, 4) section_kernel(const __grid_constant__ SectionArgs a) {
+template <int OP, int M>
+__global__ void __launch_bounds__(kThreads) section_kernel(const __grid_constant__ SectionArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
-  GroupRef* tl = reinterpret_cast<GroupRef*>(smem);
   const int n_slices = a.n_load + (a.perm_slot >= 0 ? 1 : 0);
-  uint8_t* wbase = smem + ((n_slices * (int)sizeof(GroupRef) + 15) & ~15);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  uint8_t* buf0 = wbase + (size_t)warp * 2 * a.in_bytes;
+  // slice table: base pointer and byte range of each staged slice within a chunk buffer
+  const uint8_t** sp = reinterpret_cast<const uint8_t**>(smem);
+  int* send = reinterpret_cast<int*>(smem + 8 * (kMaxGroups + 1));
+  int* wback = send + (kMaxGroups + 1);
+  uint8_t* buf0 = smem + kSectionTable + (size_t)warp * 2 * a.in_bytes;
   uint8_t* buf1 = buf0 + a.in_bytes;
-  for (int k = tid; k < n_slices; k += kThreads) tl[k] = a.load[k];
+  constexpr int R = 32 * M;
+  for (int k = tid; k < n_slices; k += kThreads) {
+    sp[k] = a.load[k].ptr;
+    send[k] = a.load[k].start + R * a.load[k].stride;
+    wback[k] = a.writeback[k];
+  }
   __syncthreads();
 
   const int64_t W = (int64_t)gridDim.x * kWarps;
-  const int64_t R = a.R;
+  // The chunk's slices are contiguous in the buffer and each a multiple of 64 bytes, so the
+  // warp walks the whole buffer in 16-byte pieces (512 bytes per step, every lane busy); piece
+  // p of slice g comes from byte (ch*R*stride_g + p - start_g) of group g.
   auto stage = [&](int64_t ch, uint8_t* buf) {
-    int g = 0;
+    int g = 0, start = 0;
     for (int p = lane * 16; p < a.in_bytes; p += 512) {
-      while (p >= tl[g].start + a.R * tl[g].stride) ++g;
-      cp_async16(buf + p, tl[g].ptr + ch * R * tl[g].stride + (p - tl[g].start));
+      while (p >= send[g]) start = send[g++];
+      const int64_t stride = (send[g] - start) / R;
+      cp_async16(buf + p, sp[g] + ch * (R * stride) + (p - start));
     }
   };
 
@@ -184,13 +272,34 @@ __global__ void __launch_bounds__(kThreads, 4) section_kernel(const __grid_const
   if (c < a.n_chunks) stage(c, buf0);
   cp_async_commit();
   for (int i = 0; c < a.n_chunks; c += W, ++i) {
-    const uint8_t* cur = (i & 1) ? buf1 : buf0;
+    uint8_t* cur = (i & 1) ? buf1 : buf0;
     if (c + W < a.n_chunks) stage(c + W, (i & 1) ? buf0 : buf1);
     cp_async_commit();
     cp_async_wait<1>();
     __syncwarp();
-    const int32_t* ps = a.perm_slot >= 0 ? reinterpret_cast<const int32_t*>(cur + tl[a.perm_slot].start) : nullptr;
-    for (int r = lane; r < a.R; r += 32) run_record<OP>(a, StagedRec{&a, cur, r}, c * R + r, ps ? ps[r] : 0);
+    const int64_t i0 = c * R;
+    if (OP == ADHA_OP_MIX) {
+      mix_chunk<M>(a, cur, i0, lane);
+    } else {
+      const int32_t* ps = a.perm_slot >= 0 ? reinterpret_cast<const int32_t*>(cur + a.load[a.perm_slot].start) : nullptr;
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        const int r = lane + 32 * m;
+        run_record<OP>(a, StagedRec{&a, cur, r, i0 + r}, i0 + r, ps ? ps[r] : 0);
+      }
+    }
+    if (a.n_writeback) {   // wide written groups go back whole, 16 bytes per lane per step
+      __syncwarp();
+      int g = 0, start = 0;
+      for (int p = lane * 16; p < a.in_bytes; p += 512) {
+        while (p >= send[g]) start = send[g++];
+        if (wback[g]) {
+          const int64_t stride = (send[g] - start) / R;
+          *reinterpret_cast<uint4*>(const_cast<uint8_t*>(sp[g]) + c * (R * stride) + (p - start)) =
+              *reinterpret_cast<const uint4*>(cur + p);
+        }
+      }
+    }
     __syncwarp();
   }
   cp_async_wait<0>();
@@ -228,26 +337,32 @@ __global__ void __launch_bounds__(kThreads) backward_kernel(const __grid_constan
   }
 }
 
-size_t section_smem_bytes(const SectionArgs& a) {
-  const int n_slices = a.n_load + (a.perm_slot >= 0 ? 1 : 0);
-  return (size_t)((n_slices * (int)sizeof(GroupRef) + 15) & ~15) + (size_t)kWarps * 2 * a.in_bytes;
-}
+size_t section_smem_bytes(const SectionArgs& a) { return kSectionTable + (size_t)kWarps * 2 * a.in_bytes; }
 
-template <int OP>
-static int launch_op(const SectionArgs& a, int grid, size_t smem, void* stream) {
-  cudaError_t e = cudaFuncSetAttribute(section_kernel<OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <int OP, int M>
+static int launch_om(const SectionArgs& a, int grid, size_t smem, void* stream) {
+  cudaError_t e = cudaFuncSetAttribute(section_kernel<OP, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(section)");
-  section_kernel<OP><<<grid, kThreads, smem, (cudaStream_t)stream>>>(a);
+  section_kernel<OP, M><<<grid, kThreads, smem, (cudaStream_t)stream>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "section kernel launch");
   return 0;
 }
 
 template <int OP>
+static int launch_op(const SectionArgs& a, int grid, size_t smem, void* stream) {
+  switch (a.R) {
+    case 32: return launch_om<OP, 1>(a, grid, smem, stream);
+    case 64: return launch_om<OP, 2>(a, grid, smem, stream);
+    default: return launch_om<OP, 4>(a, grid, smem, stream);
+  }
+}
+
+template <int OP>
 static int occ_op(size_t smem, int* blocks) {
-  cudaError_t e = cudaFuncSetAttribute(section_kernel<OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(section_kernel<OP, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(section)");
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, section_kernel<OP>, kThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, section_kernel<OP, 1>, kThreads, smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(section)");
   return 0;
 }

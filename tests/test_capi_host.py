@@ -112,3 +112,25 @@ def test_remap_overlap_and_negative_n_rejected(P):
     assert e.value.code == ADHA_EINVAL and "overlap" in str(e.value)
     # n == 0 is a no-op that touches nothing
     P.adha_remap(s, 0, P.Layout.aos(2), [0], P.Layout.soa(2), [0, 0], stream=0)
+
+
+def test_tuning_cache_text_round_trip(P):
+    from paper_1407_4859_gb300._lib import AdhaError, ADHA_EINVAL
+    P.adha_tune_clear()
+    assert P.adha_tune_export() == ""
+    text = "S4:3:2:0:0:0,0,0,0,0,0,0,0,:L0.0,|1.0,|:n10\t64\t2\nS1:7:4:0:0:0,1,2,0,0,0,0,0,:L0.0,1.0,2.0,|:n20\t32\t1\n"
+    P.adha_tune_import(text)
+    assert sorted(P.adha_tune_export().splitlines()) == sorted(text.splitlines())
+    for bad in ["no tabs here\n", "k\t48\t1\n", "k\t32\t7\n"]:
+        with pytest.raises(AdhaError) as e:
+            P.adha_tune_import(bad)
+        assert e.value.code == ADHA_EINVAL
+    P.adha_tune_clear()
+    assert P.adha_tune_export() == ""
+    for bad in [-32, 33, 2048]:
+        with pytest.raises(AdhaError):
+            P.adha_tune_override(bad)
+    with pytest.raises(AdhaError):
+        P.adha_tune_writeback(3)
+    P.adha_tune_override(0)
+    P.adha_tune_writeback(0)

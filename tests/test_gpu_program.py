@@ -75,8 +75,8 @@ def test_tiny_program_every_fixed_assignment(P):
 
 
 @pytest.mark.parametrize("make,n", [(synth.config2, (1 << 16) + 7), (synth.config3, (1 << 16) + 3)])
-@pytest.mark.parametrize("back", [False, True])
-def test_program_with_ods_candidates(P, make, n, back):
+@pytest.mark.parametrize("back,autotune", [(False, False), (True, False), (False, True)])
+def test_program_with_ods_candidates(P, make, n, back, autotune):
     wl = make(n=n)
     perm = wl.perm() if wl.has_perm else None
     dperm = torch.from_numpy(perm).cuda() if perm is not None else None
@@ -84,7 +84,10 @@ def test_program_with_ods_candidates(P, make, n, back):
     fields = oracle.initial_fields(wl)
     want = oracle.run_program_fields(wl, [a.copy() for a in fields], perm)
     in_bufs = to_device(n, wl.dtypes, AOS.groups, fields)
-    costs = P.adha_measure(S, n, AOS, in_bufs, secs, cand)
+    P.adha_tune_clear()
+    costs = P.adha_measure(S, n, AOS, in_bufs, secs, cand, autotune=autotune)
+    if autotune:
+        assert len(P.adha_tune_export().splitlines()) == len(cand) * len(set(wl.sections))
     cost, seq = oracle.pdl_dp(costs.section_ns, costs.remap_ns, back)
     plan, lay, host = _run(P, wl, S, AOS, cand, secs, in_bufs, costs=costs, back=back)
     assert list(plan.layout_of_section[:len(wl.sections)]) == seq and plan.model_ns == cost
