@@ -575,6 +575,10 @@ static int plan_section(const Layout& L, void* const* ptrs, const adha_section* 
       off += R * 4;
     }
     a.in_bytes = off;
+    // vector mapping: every staged group and every written field's group is one field wide
+    a.vec = (s->op == ADHA_OP_MIX && R >= 64 && a.n_writeback == 0) ? 1 : 0;
+    for (int f = 0; f < L.F && a.vec; ++f)
+      if ((has(staged, f) || has(s->write_mask, f)) && L.groups[L.group_of[f]].size() != 1) a.vec = 0;
     plan->smem = section_smem_bytes(a);
     if (plan->smem <= (size_t)kSmemLimit) break;
     if (R <= 32) return fail(ADHA_EINVAL, "section records too wide for a 32-record chunk");

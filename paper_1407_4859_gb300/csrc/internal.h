@@ -106,6 +106,7 @@ struct SectionArgs {
   GroupRef load[kMaxGroups + 1];
   int8_t writeback[kMaxGroups + 1];   // staged slice k is written back whole after the chunk
   int32_t n_writeback;
+  int32_t vec;                        // 1: every accessed group is one field wide; lane = M consecutive records
   FieldRef f[kMaxFields];
   int32_t arg[8];
   float par[4];

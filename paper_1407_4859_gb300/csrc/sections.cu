@@ -139,6 +139,123 @@ __device__ __forceinline__ void mix_chunk(const SectionArgs& a, uint8_t* stage, 
 #undef ADHA_MIX_WRITE
 }
 
+// M consecutive values of one field for records lane*M .. lane*M+M-1 of a one-field slice
+// (contiguous, M*sizeof(V)-byte aligned): moved with 8- or 16-byte accesses.
+template <class V, int M>
+__device__ __forceinline__ void ld_vec(const uint8_t* p, V (&v)[M]) {
+  constexpr int B = M * (int)sizeof(V);
+  if constexpr (B % 16 == 0) {
+#pragma unroll
+    for (int k = 0; k < B / 16; ++k) {
+      const uint4 x = reinterpret_cast<const uint4*>(p)[k];
+      memcpy(reinterpret_cast<uint8_t*>(v) + 16 * k, &x, 16);
+    }
+  } else if constexpr (B == 8) {
+    const uint2 x = *reinterpret_cast<const uint2*>(p);
+    memcpy(v, &x, 8);
+  } else {
+#pragma unroll
+    for (int m = 0; m < M; ++m) v[m] = reinterpret_cast<const V*>(p)[m];
+  }
+}
+
+template <class V, int M>
+__device__ __forceinline__ void st_vec(uint8_t* p, const V (&v)[M]) {
+  constexpr int B = M * (int)sizeof(V);
+  if constexpr (B % 16 == 0) {
+#pragma unroll
+    for (int k = 0; k < B / 16; ++k) {
+      uint4 x;
+      memcpy(&x, reinterpret_cast<const uint8_t*>(v) + 16 * k, 16);
+      reinterpret_cast<uint4*>(p)[k] = x;
+    }
+  } else if constexpr (B == 8) {
+    uint2 x;
+    memcpy(&x, v, 8);
+    *reinterpret_cast<uint2*>(p) = x;
+  } else {
+#pragma unroll
+    for (int m = 0; m < M; ++m) reinterpret_cast<V*>(p)[m] = v[m];
+  }
+}
+
+// MIX when every accessed group holds one field (SoA-like): lane takes records lane*M + m, so
+// each field is one vector load from the chunk buffer and one vector store to global memory.
+template <int M>
+__device__ __forceinline__ void mix_chunk_vec(const SectionArgs& a, const uint8_t* stage, int64_t i0, int lane) {
+  float s[M];
+  uint32_t h[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    s[m] = 0.0f;
+    h[m] = 0u;
+  }
+  for (int j = 0; j < a.n_rd[ADHA_F32]; ++j) {
+    float v[M];
+    ld_vec<float, M>(stage + a.f[a.rd[ADHA_F32][j]].s0 + lane * M * 4, v);
+#pragma unroll
+    for (int m = 0; m < M; ++m) s[m] = __fadd_rn(s[m], v[m]);
+  }
+  for (int j = 0; j < a.n_rd[ADHA_F64]; ++j) {
+    unsigned long long v[M];
+    ld_vec<unsigned long long, M>(stage + a.f[a.rd[ADHA_F64][j]].s0 + lane * M * 8, v);
+#pragma unroll
+    for (int m = 0; m < M; ++m) h[m] ^= (uint32_t)v[m] ^ (uint32_t)(v[m] >> 32);
+  }
+  for (int j = 0; j < a.n_rd[ADHA_I32]; ++j) {
+    uint32_t v[M];
+    ld_vec<uint32_t, M>(stage + a.f[a.rd[ADHA_I32][j]].s0 + lane * M * 4, v);
+#pragma unroll
+    for (int m = 0; m < M; ++m) h[m] ^= v[m];
+  }
+  for (int j = 0; j < a.n_rd[ADHA_BF16]; ++j) {
+    uint16_t v[M];
+    ld_vec<uint16_t, M>(stage + a.f[a.rd[ADHA_BF16][j]].s0 + lane * M * 2, v);
+#pragma unroll
+    for (int m = 0; m < M; ++m) h[m] ^= (uint32_t)v[m];
+  }
+  float t[M];
+  uint32_t k[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    t[m] = __fadd_rn(s[m], __fmul_rn(__uint2float_rn(h[m] & 255u), 0.00390625f));
+    k[m] = (h[m] ^ __float_as_uint(t[m])) >> 3;
+  }
+  const int64_t r0 = i0 + (int64_t)lane * M;
+  for (int j = 0; j < a.n_wr[ADHA_F32]; ++j) {
+    const FieldRef& F = a.f[a.wr[ADHA_F32][j]];
+    float v[M];
+    ld_vec<float, M>(stage + F.s0 + lane * M * 4, v);
+#pragma unroll
+    for (int m = 0; m < M; ++m) v[m] = __fadd_rn(__fmul_rn(v[m], 0.5f), t[m]);
+    st_vec<float, M>(F.g + r0 * 4, v);
+  }
+  for (int j = 0; j < a.n_wr[ADHA_F64]; ++j) {
+    const FieldRef& F = a.f[a.wr[ADHA_F64][j]];
+    double v[M];
+    ld_vec<double, M>(stage + F.s0 + lane * M * 8, v);
+#pragma unroll
+    for (int m = 0; m < M; ++m) v[m] = __dadd_rn(__dmul_rn(v[m], 0.5), (double)t[m]);
+    st_vec<double, M>(F.g + r0 * 8, v);
+  }
+  for (int j = 0; j < a.n_wr[ADHA_I32]; ++j) {
+    const FieldRef& F = a.f[a.wr[ADHA_I32][j]];
+    uint32_t v[M];
+    ld_vec<uint32_t, M>(stage + F.s0 + lane * M * 4, v);
+#pragma unroll
+    for (int m = 0; m < M; ++m) v[m] ^= k[m];
+    st_vec<uint32_t, M>(F.g + r0 * 4, v);
+  }
+  for (int j = 0; j < a.n_wr[ADHA_BF16]; ++j) {
+    const FieldRef& F = a.f[a.wr[ADHA_BF16][j]];
+    uint16_t v[M];
+    ld_vec<uint16_t, M>(stage + F.s0 + lane * M * 2, v);
+#pragma unroll
+    for (int m = 0; m < M; ++m) v[m] = (uint16_t)(v[m] ^ (uint16_t)(k[m] & 0xFFFFu));
+    st_vec<uint16_t, M>(F.g + r0 * 2, v);
+  }
+}
+
 template <int OP, class Rec>
 __device__ __forceinline__ void run_record(const SectionArgs& a, const Rec& rec, int64_t i, int32_t pj) {
   const int* g = a.arg;
@@ -236,7 +353,7 @@ __device__ __forceinline__ void run_record(const SectionArgs& a, const Rec& rec,
   }
 }
 
-template <int OP, int M>
+template <int OP, int M, bool VEC>
 __global__ void __launch_bounds__(kThreads) section_kernel(const __grid_constant__ SectionArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int n_slices = a.n_load + (a.perm_slot >= 0 ? 1 : 0);
@@ -278,7 +395,9 @@ __global__ void __launch_bounds__(kThreads) section_kernel(const __grid_constant
     cp_async_wait<1>();
     __syncwarp();
     const int64_t i0 = c * R;
-    if (OP == ADHA_OP_MIX) {
+    if (OP == ADHA_OP_MIX && VEC) {
+      mix_chunk_vec<M>(a, cur, i0, lane);
+    } else if (OP == ADHA_OP_MIX) {
       mix_chunk<M>(a, cur, i0, lane);
     } else {
       const int32_t* ps = a.perm_slot >= 0 ? reinterpret_cast<const int32_t*>(cur + a.load[a.perm_slot].start) : nullptr;
@@ -339,11 +458,11 @@ __global__ void __launch_bounds__(kThreads) backward_kernel(const __grid_constan
 
 size_t section_smem_bytes(const SectionArgs& a) { return kSectionTable + (size_t)kWarps * 2 * a.in_bytes; }
 
-template <int OP, int M>
+template <int OP, int M, bool VEC>
 static int launch_om(const SectionArgs& a, int grid, size_t smem, void* stream) {
-  cudaError_t e = cudaFuncSetAttribute(section_kernel<OP, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(section_kernel<OP, M, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(section)");
-  section_kernel<OP, M><<<grid, kThreads, smem, (cudaStream_t)stream>>>(a);
+  section_kernel<OP, M, VEC><<<grid, kThreads, smem, (cudaStream_t)stream>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "section kernel launch");
   return 0;
@@ -351,18 +470,22 @@ static int launch_om(const SectionArgs& a, int grid, size_t smem, void* stream) 
 
 template <int OP>
 static int launch_op(const SectionArgs& a, int grid, size_t smem, void* stream) {
+  if (OP == ADHA_OP_MIX && a.vec) {
+    if (a.R == 64) return launch_om<OP, 2, true>(a, grid, smem, stream);
+    if (a.R == 128) return launch_om<OP, 4, true>(a, grid, smem, stream);
+  }
   switch (a.R) {
-    case 32: return launch_om<OP, 1>(a, grid, smem, stream);
-    case 64: return launch_om<OP, 2>(a, grid, smem, stream);
-    default: return launch_om<OP, 4>(a, grid, smem, stream);
+    case 32: return launch_om<OP, 1, false>(a, grid, smem, stream);
+    case 64: return launch_om<OP, 2, false>(a, grid, smem, stream);
+    default: return launch_om<OP, 4, false>(a, grid, smem, stream);
   }
 }
 
 template <int OP>
 static int occ_op(size_t smem, int* blocks) {
-  cudaError_t e = cudaFuncSetAttribute(section_kernel<OP, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(section_kernel<OP, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(section)");
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, section_kernel<OP, 1>, kThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, section_kernel<OP, 1, false>, kThreads, smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(section)");
   return 0;
 }
