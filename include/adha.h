@@ -310,6 +310,64 @@ int adha_run_program(const adha_schema* schema, int64_t n, const adha_layout* in
                      const adha_cost_table* costs, const adha_plan_opts* opts, void* workspace, size_t ws_bytes,
                      adha_stream stream, adha_plan* plan);
 
+/* ----------------------------------------------------------- batched remap */
+
+/* One record array of a batched remap: its own schema, record count, and
+ * source / destination layouts with their group buffers (device).  Host structs,
+ * read during adha_batched_create only. */
+typedef struct {
+  const adha_schema* schema;
+  int64_t n;
+  const adha_layout* src;
+  const void* const* src_ptrs;
+  const adha_layout* dst;
+  void* const* dst_ptrs;
+} adha_remap_desc;
+
+/* A prepared batched remap (host object). */
+typedef struct adha_batched adha_batched;
+
+#define ADHA_BATCHED_AUTOTUNE 1   /* pick each array's chunk size by timing it (synchronizes `stream`) */
+
+/*
+ * Prepares the remap of n_arrays record arrays in one persistent launch (the
+ * batching form of the paper's remap, Section 2): validates every array (rules
+ * of adha_remap), plans each one (chunk size, element schedule) and lays out
+ * the descriptors the kernel reads.  With ADHA_BATCHED_AUTOTUNE each array's
+ * chunk size is the fastest of 32..256 records, timed with the single-array
+ * kernel on the array's own buffers (their contents are overwritten with the
+ * remap's result).  *out is freed with adha_batched_destroy.
+ */
+int adha_batched_create(int32_t n_arrays, const adha_remap_desc* descs, int32_t flags, adha_stream stream,
+                        adha_batched** out);
+
+/* Device workspace bytes the batched remap needs (descriptors + its work ticket). */
+size_t adha_batched_workspace_bytes(const adha_batched* b);
+
+/* Copies the descriptors into `workspace` (device, 256-byte aligned) and
+ * synchronizes `stream`.  Needed once per workspace before launches. */
+int adha_batched_upload(const adha_batched* b, void* workspace, size_t ws_bytes, adha_stream stream);
+
+/* Enqueues the batched remap: zeroes the work ticket, then one persistent
+ * kernel in which CTAs take blocks of chunks by atomic ticket.  Async; no
+ * allocation or synchronization, so it can be captured in a CUDA graph.  The
+ * workspace must hold uploaded descriptors and not be shared by overlapping
+ * launches. */
+int adha_batched_launch(const adha_batched* b, void* workspace, adha_stream stream);
+
+/* Captures adha_batched_launch into a CUDA graph owned by b (on a private
+ * stream; `stream` is synchronized first).  Replaces an earlier graph of b. */
+int adha_batched_graph(adha_batched* b, void* workspace, adha_stream stream);
+
+/* Launches the captured graph on `stream` (async). */
+int adha_batched_graph_launch(const adha_batched* b, adha_stream stream);
+
+/* Algorithmic bytes one launch moves: 2 x data bytes of every field in a changed group. */
+double adha_batched_bytes(const adha_batched* b);
+
+/* Frees b and its graph (NULL is ignored). */
+void adha_batched_destroy(adha_batched* b);
+
 /*
  * Records per warp chunk (a multiple of 32 up to 1024; 0 = automatic) that the
  * remap and section kernels launched later by the calling thread use.  The

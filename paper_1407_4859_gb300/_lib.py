@@ -58,6 +58,11 @@ class adha_launch_record(ctypes.Structure):
     _fields_ = [("kind", _I32), ("op", _I32), ("bytes", ctypes.c_double), ("ms", ctypes.c_double)]
 
 
+class adha_remap_desc(ctypes.Structure):
+    _fields_ = [("schema", ctypes.POINTER(adha_schema)), ("n", _I64), ("src", ctypes.POINTER(adha_layout)),
+                ("src_ptrs", _PP), ("dst", ctypes.POINTER(adha_layout)), ("dst_ptrs", _PP)]
+
+
 class AdhaError(RuntimeError):
     def __init__(self, code, fn, msg):
         super().__init__("%s failed with %s: %s" % (fn, CODES.get(code, code), msg))
@@ -81,6 +86,14 @@ SIGNATURES = {
                                              _PP, ctypes.POINTER(adha_section), _P, _P]),
     "adha_device_status": (ctypes.c_int, [_P, ctypes.POINTER(_I32)]),
     "adha_tune_override": (ctypes.c_int, [_I32]),
+    "adha_batched_create": (ctypes.c_int, [_I32, ctypes.POINTER(adha_remap_desc), _I32, _P, ctypes.POINTER(_P)]),
+    "adha_batched_workspace_bytes": (ctypes.c_size_t, [_P]),
+    "adha_batched_upload": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P]),
+    "adha_batched_launch": (ctypes.c_int, [_P, _P, _P]),
+    "adha_batched_graph": (ctypes.c_int, [_P, _P, _P]),
+    "adha_batched_graph_launch": (ctypes.c_int, [_P, _P]),
+    "adha_batched_bytes": (ctypes.c_double, [_P]),
+    "adha_batched_destroy": (None, [_P]),
     "adha_tune_writeback": (ctypes.c_int, [_I32]),
     "adha_tune_clear": (ctypes.c_int, []),
     "adha_tune_export": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),

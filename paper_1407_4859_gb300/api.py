@@ -375,3 +375,58 @@ def adha_profile_stop(max_records=4096):
     check(_lib.load().adha_profile_stop(recs, max_records, ctypes.byref(n)), "adha_profile_stop")
     return [dict(kind=KINDS.get(recs[k].kind, recs[k].kind), op=OP_NAMES.get(recs[k].op, recs[k].op),
                  bytes=recs[k].bytes, ms=recs[k].ms) for k in range(min(n.value, max_records))]
+
+
+# ------------------------------------------------------------------ batched remap
+
+ADHA_BATCHED_AUTOTUNE = 1
+
+
+class Batched:
+    """A prepared batched remap (adha_batched_create); arrays: list of dicts with keys
+    schema (Schema), n, src (Layout), src_bufs, dst (Layout), dst_bufs."""
+
+    def __init__(self, arrays, autotune=False, stream=None):
+        self._keep = []
+        descs = (_lib.adha_remap_desc * len(arrays))()
+        for k, a in enumerate(arrays):
+            sp, dp = _ptrs(a["src_bufs"]), _ptrs(a["dst_bufs"])
+            self._keep += [a["schema"], a["src"], a["dst"], sp, dp]
+            descs[k] = _lib.adha_remap_desc(ctypes.pointer(a["schema"].c), int(a["n"]), ctypes.pointer(a["src"].c),
+                                            sp, ctypes.pointer(a["dst"].c), dp)
+        self.ptr = ctypes.c_void_p()
+        check(_lib.load().adha_batched_create(len(arrays), descs, ADHA_BATCHED_AUTOTUNE if autotune else 0,
+                                              _stream_ptr(stream), ctypes.byref(self.ptr)), "adha_batched_create")
+        self.workspace = None
+
+    @property
+    def workspace_bytes(self):
+        return _lib.load().adha_batched_workspace_bytes(self.ptr)
+
+    @property
+    def bytes(self):
+        return _lib.load().adha_batched_bytes(self.ptr)
+
+    def upload(self, workspace=None, stream=None):
+        if workspace is None:
+            workspace = torch.empty(self.workspace_bytes, dtype=torch.uint8, device="cuda")
+        self.workspace = workspace
+        check(_lib.load().adha_batched_upload(self.ptr, workspace.data_ptr(), workspace.numel(), _stream_ptr(stream)),
+              "adha_batched_upload")
+        return workspace
+
+    def launch(self, stream=None):
+        check(_lib.load().adha_batched_launch(self.ptr, self.workspace.data_ptr(), _stream_ptr(stream)),
+              "adha_batched_launch")
+
+    def capture(self, stream=None):
+        check(_lib.load().adha_batched_graph(self.ptr, self.workspace.data_ptr(), _stream_ptr(stream)),
+              "adha_batched_graph")
+
+    def graph_launch(self, stream=None):
+        check(_lib.load().adha_batched_graph_launch(self.ptr, _stream_ptr(stream)), "adha_batched_graph_launch")
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _lib._lib is not None:
+            _lib._lib.adha_batched_destroy(self.ptr)
+            self.ptr = None

@@ -1,0 +1,470 @@
+// batched.cu -- many record arrays remapped in one persistent launch.
+//
+// Each array (its own schema, record count and source/destination layouts) is cut into chunks
+// of R_a records, and its chunks into work blocks of kBlockChunks.  A CTA takes the next block
+// with one atomic ticket (a 64-bit counter in the caller's workspace, zeroed by a memset node
+// before every launch), builds the block's array's element schedule in shared memory when the
+// array changes, and its warps run the same double-buffered cp.async pipeline as remap.cu on
+// the block's chunks.  Blocks of small arrays and of large arrays are interleaved by the ticket
+// order, so uneven sizes balance across SMs without any waiting between CTAs.  The descriptors
+// live in the workspace; the launch (memset + kernel) can be captured in a CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+#include "ptx.cuh"
+
+namespace adha {
+
+constexpr int kBlockChunksPerWarp = 16;
+constexpr int kBlockChunks = kWarps * kBlockChunksPerWarp;
+
+struct BatchHeader {
+  int64_t n, n_full, n_chunks, block0;
+  int32_t R, unit, n_src, n_dst, in_bytes, out_bytes, n_elems, order;
+  int32_t group0, slot0, nslot0, n_slots;
+};
+
+struct BatchParams {
+  unsigned long long* ticket;
+  const BatchHeader* headers;
+  const GroupRef* groups;
+  const uint32_t* slots;
+  const int32_t* nslots;
+  const int64_t* prefix;     // first block of each array, n_arrays + 1 entries
+  int32_t n_arrays;
+  int64_t total_blocks;
+  int32_t max_elems, max_in, max_out;
+};
+
+template <typename U>
+__device__ __forceinline__ void gather_elems(const uint32_t* sched, int n_elems, const uint8_t* in, uint8_t* out, int lane) {
+  const U* src = reinterpret_cast<const U*>(in);
+  U* dst = reinterpret_cast<U*>(out);
+#pragma unroll 4
+  for (int t = lane; t < n_elems; t += 32) {
+    const uint32_t p = sched[t];
+    const uint32_t x = p & 0xFFFFu;
+    dst[p >> 16] = x != 0xFFFFu ? src[x] : U(0);
+  }
+}
+
+template <typename U>
+__device__ __forceinline__ void tail_elems(const BatchHeader& h, const GroupRef* tin, const GroupRef* tout,
+                                           const int32_t* nslot, const uint32_t* slots, int lane) {
+  const int64_t t0 = h.n_full * h.R;
+  const int Tt = (int)(h.n - t0);
+  int s0 = 0;
+  for (int d = 0; d < h.n_dst; ++d) {
+    const int S = nslot[d];
+    for (int e = lane; e < Tt * S; e += 32) {
+      const int r = e / S, k = e - r * S;
+      const uint32_t code = slots[s0 + k];
+      U v = U(0);
+      if (code != kPadSlot) {
+        const GroupRef& sg = tin[code >> 16];
+        v = *reinterpret_cast<const U*>(sg.ptr + (t0 + r) * sg.stride + (code & 0xFFFFu));
+      }
+      *reinterpret_cast<U*>(const_cast<uint8_t*>(tout[d].ptr) + (t0 + r) * tout[d].stride + k * (int)sizeof(U)) = v;
+    }
+    s0 += S;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) batched_kernel(const __grid_constant__ BatchParams p) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ BatchHeader h;
+  __shared__ unsigned long long s_blk;
+  __shared__ int s_arr;
+  GroupRef* tin = reinterpret_cast<GroupRef*>(smem);
+  GroupRef* tout = tin + kMaxGroups;
+  int32_t* nslot = reinterpret_cast<int32_t*>(tout + kMaxGroups);
+  uint32_t* slots = reinterpret_cast<uint32_t*>(nslot + kMaxGroups);
+  uint32_t* sched = slots + kMaxSlots;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  uint8_t* buf0 = reinterpret_cast<uint8_t*>(sched + p.max_elems) + (size_t)warp * (2 * p.max_in + p.max_out);
+  uint8_t* buf1 = buf0 + p.max_in;
+  uint8_t* outb = buf1 + p.max_in;
+  int cur = -1;
+
+  for (;;) {
+    if (tid == 0) {
+      s_blk = atomicAdd(p.ticket, 1ull);
+      int lo = 0, hi = p.n_arrays - 1;   // last array whose first block is <= s_blk
+      const int64_t b = (int64_t)s_blk;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (p.prefix[mid] <= b) lo = mid;
+        else hi = mid - 1;
+      }
+      s_arr = lo;
+    }
+    __syncthreads();
+    const int64_t blk = (int64_t)s_blk;
+    if (blk >= p.total_blocks) break;
+    const int arr = s_arr;
+    if (arr != cur) {
+      if (tid == 0) h = p.headers[arr];
+      __syncthreads();
+      for (int k = tid; k < h.n_src; k += kThreads) tin[k] = p.groups[h.group0 + k];
+      for (int k = tid; k < h.n_dst; k += kThreads) tout[k] = p.groups[h.group0 + h.n_src + k];
+      for (int k = tid; k < h.n_dst; k += kThreads) nslot[k] = p.nslots[h.nslot0 + k];
+      for (int k = tid; k < h.n_slots; k += kThreads) slots[k] = p.slots[h.slot0 + k];
+      __syncthreads();
+      for (int t = tid; t < h.n_elems; t += kThreads) {
+        int d = 0, e0 = 0, sl0 = 0;
+        while (t >= e0 + h.R * nslot[d]) {
+          e0 += h.R * nslot[d];
+          sl0 += nslot[d++];
+        }
+        const int S = nslot[d];
+        int r, k;
+        if (h.order == 0) {
+          r = (t - e0) / S;
+          k = (t - e0) - r * S;
+        } else {
+          k = (t - e0) / h.R;
+          r = (t - e0) - k * h.R;
+        }
+        const uint32_t code = slots[sl0 + k];
+        uint32_t x = 0xFFFFu;
+        if (code != kPadSlot) {
+          const int j = (int)(code >> 16);
+          x = (uint32_t)((tin[j].start + r * tin[j].stride + (int)(code & 0xFFFFu)) / h.unit);
+        }
+        sched[t] = x | ((uint32_t)(e0 + r * S + k) << 16);
+      }
+      __syncthreads();
+      cur = arr;
+    }
+    const int64_t c_begin = (blk - h.block0) * kBlockChunks;
+    const int64_t c_end = c_begin + kBlockChunks < h.n_chunks ? c_begin + kBlockChunks : h.n_chunks;
+    const int64_t full_end = c_end < h.n_full ? c_end : h.n_full;
+    const int64_t R = h.R;
+    auto stage = [&](int64_t ch, uint8_t* buf) {
+      int g = 0;
+      for (int q = lane * 16; q < h.in_bytes; q += 512) {
+        while (q >= tin[g].start + h.R * tin[g].stride) ++g;
+        cp_async16(buf + q, tin[g].ptr + ch * R * tin[g].stride + (q - tin[g].start));
+      }
+    };
+    int64_t c = c_begin + warp;
+    if (c < full_end) stage(c, buf0);
+    cp_async_commit();
+    for (int i = 0; c < full_end; c += kWarps, ++i) {
+      uint8_t* curb = (i & 1) ? buf1 : buf0;
+      if (c + kWarps < full_end) stage(c + kWarps, (i & 1) ? buf0 : buf1);
+      cp_async_commit();
+      cp_async_wait<1>();
+      __syncwarp();
+      if (h.unit == 2) gather_elems<uint16_t>(sched, h.n_elems, curb, outb, lane);
+      else if (h.unit == 4) gather_elems<uint32_t>(sched, h.n_elems, curb, outb, lane);
+      else gather_elems<unsigned long long>(sched, h.n_elems, curb, outb, lane);
+      __syncwarp();
+      int g = 0;
+      for (int q = lane * 16; q < h.out_bytes; q += 512) {
+        while (q >= tout[g].start + h.R * tout[g].stride) ++g;
+        *reinterpret_cast<uint4*>(const_cast<uint8_t*>(tout[g].ptr) + c * R * tout[g].stride + (q - tout[g].start)) =
+            *reinterpret_cast<const uint4*>(outb + q);
+      }
+      __syncwarp();
+    }
+    cp_async_wait<0>();
+    // the array's ragged tail chunk, by the warp it falls to
+    if (h.n_full < h.n_chunks && h.n_full >= c_begin && h.n_full < c_end && (h.n_full - c_begin) % kWarps == warp) {
+      if (h.unit == 2) tail_elems<uint16_t>(h, tin, tout, nslot, slots, lane);
+      else if (h.unit == 4) tail_elems<uint32_t>(h, tin, tout, nslot, slots, lane);
+      else tail_elems<unsigned long long>(h, tin, tout, nslot, slots, lane);
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace adha
+
+using namespace adha;
+
+struct adha_batched {
+  int32_t n_arrays = 0;
+  std::vector<uint8_t> image;      // descriptor region as it is copied to the workspace
+  size_t off_headers = 0, off_groups = 0, off_slots = 0, off_nslots = 0, off_prefix = 0;
+  int64_t total_blocks = 0;
+  int32_t max_elems = 0, max_in = 0, max_out = 0;
+  size_t smem = 0;
+  int grid = 1;
+  double bytes = 0;
+  cudaGraphExec_t graph = nullptr;
+  void* graph_ws = nullptr;
+};
+
+namespace adha {
+
+static size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+
+static BatchParams params_for(const adha_batched* b, void* ws) {
+  uint8_t* base = static_cast<uint8_t*>(ws);
+  BatchParams p;
+  p.ticket = reinterpret_cast<unsigned long long*>(base);
+  p.headers = reinterpret_cast<const BatchHeader*>(base + b->off_headers);
+  p.groups = reinterpret_cast<const GroupRef*>(base + b->off_groups);
+  p.slots = reinterpret_cast<const uint32_t*>(base + b->off_slots);
+  p.nslots = reinterpret_cast<const int32_t*>(base + b->off_nslots);
+  p.prefix = reinterpret_cast<const int64_t*>(base + b->off_prefix);
+  p.n_arrays = b->n_arrays;
+  p.total_blocks = b->total_blocks;
+  p.max_elems = b->max_elems;
+  p.max_in = b->max_in;
+  p.max_out = b->max_out;
+  return p;
+}
+
+static int launch_batched(const adha_batched* b, void* ws, void* stream) {
+  cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(unsigned long long), (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(ticket)");
+  if (b->total_blocks == 0) return 0;
+  e = cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(batched)");
+  batched_kernel<<<b->grid, kThreads, b->smem, (cudaStream_t)stream>>>(params_for(b, ws));
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "batched kernel launch");
+  return 0;
+}
+
+// Chooses each array's chunk size: the default rule, or (autotune) the fastest of 32..256
+// records measured with the single-array remap kernel on the array's own buffers.
+static int tune_chunk(const Layout& S, const void* const* sp, const Layout& D, void* const* dp, int64_t n, void* stream,
+                      int* best_R) {
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return fail(ADHA_ECUDA, "cudaEventCreate");
+  float best = -1;
+  int rc = 0;
+  for (int R = 32; R <= 256 && !rc; R *= 2) {
+    RemapArgs a;
+    bool empty = false;
+    rc = remap_plan_args(S, sp, D, dp, n, R, &a, &empty);
+    if (rc || empty) break;
+    if (2 * a.in_bytes + a.out_bytes > 24 * 1024) continue;   // keep the batched kernel's buffers small
+    adha_tune_override(R);
+    for (int w = 0; w < 2 && !rc; ++w) rc = remap_layouts(S, sp, D, dp, n, stream, nullptr);
+    cudaEventRecord(e0, (cudaStream_t)stream);
+    for (int w = 0; w < 3 && !rc; ++w) rc = remap_layouts(S, sp, D, dp, n, stream, nullptr);
+    cudaEventRecord(e1, (cudaStream_t)stream);
+    adha_tune_override(0);
+    if (rc) break;
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (best < 0 || ms < best) {
+      best = ms;
+      *best_R = R;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
+}
+
+}  // namespace adha
+
+extern "C" {
+
+int adha_batched_create(int32_t n_arrays, const adha_remap_desc* descs, int32_t flags, adha_stream stream,
+                        adha_batched** out) {
+  clear_error();
+  if (!out || !descs || n_arrays < 1) return fail(ADHA_EINVAL, "bad batched arguments");
+  auto* b = new (std::nothrow) adha_batched();
+  if (!b) return fail(ADHA_ENOMEM, "host allocation failed");
+  std::vector<BatchHeader> headers;
+  std::vector<GroupRef> groups;
+  std::vector<uint32_t> slots;
+  std::vector<int32_t> nslots;
+  std::vector<int64_t> prefix;
+  int64_t blocks = 0;
+  for (int k = 0; k < n_arrays; ++k) {
+    const adha_remap_desc& d = descs[k];
+    Layout S, D;
+    int rc = make_layout(d.schema, d.src, &S, "source");
+    if (!rc) rc = make_layout(d.schema, d.dst, &D, "destination");
+    if (!rc && d.n < 0) rc = fail(ADHA_EINVAL, "array %d has n = %lld", k, (long long)d.n);
+    if (!rc && d.n > 0) {
+      for (int g = 0; g < S.n_groups && !rc; ++g)
+        if (!d.src_ptrs || !d.src_ptrs[g] || reinterpret_cast<uintptr_t>(d.src_ptrs[g]) % 16)
+          rc = fail(ADHA_EINVAL, "array %d source buffer %d is NULL or misaligned", k, g);
+      for (int g = 0; g < D.n_groups && !rc; ++g)
+        if (!d.dst_ptrs || !d.dst_ptrs[g] || reinterpret_cast<uintptr_t>(d.dst_ptrs[g]) % 16)
+          rc = fail(ADHA_EINVAL, "array %d destination buffer %d is NULL or misaligned", k, g);
+    }
+    int R = 0;
+    if (!rc && d.n > 0 && (flags & ADHA_BATCHED_AUTOTUNE))
+      rc = tune_chunk(S, d.src_ptrs, D, d.dst_ptrs, d.n, stream, &R);
+    RemapArgs a;
+    bool empty = true;
+    if (!rc && d.n > 0) rc = remap_plan_args(S, d.src_ptrs, D, d.dst_ptrs, d.n, R, &a, &empty);
+    if (rc) {
+      delete b;
+      return rc;
+    }
+    BatchHeader h;
+    std::memset(&h, 0, sizeof h);
+    h.block0 = blocks;
+    prefix.push_back(blocks);
+    if (!empty) {
+      h.n = a.n;
+      h.R = a.R;
+      h.n_full = a.n_chunks;
+      h.n_chunks = a.n_chunks + (a.n % a.R ? 1 : 0);
+      h.unit = a.unit;
+      h.n_src = a.n_src;
+      h.n_dst = a.n_dst;
+      h.in_bytes = a.in_bytes;
+      h.out_bytes = a.out_bytes;
+      h.n_elems = a.n_elems;
+      h.order = a.order;
+      h.group0 = (int32_t)groups.size();
+      h.slot0 = (int32_t)slots.size();
+      h.nslot0 = (int32_t)nslots.size();
+      h.n_slots = a.n_slots;
+      for (int g = 0; g < a.n_src; ++g) groups.push_back(a.src[g]);
+      for (int g = 0; g < a.n_dst; ++g) groups.push_back(a.dst[g]);
+      for (int g = 0; g < a.n_dst; ++g) nslots.push_back(a.d_nslot[g]);
+      slots.insert(slots.end(), a.slot, a.slot + a.n_slots);
+      blocks += (h.n_chunks + kBlockChunks - 1) / kBlockChunks;
+      b->max_elems = std::max(b->max_elems, a.n_elems);
+      b->max_in = std::max(b->max_in, a.in_bytes);
+      b->max_out = std::max(b->max_out, a.out_bytes);
+      double moved = 0;
+      for (int g = 0; g < D.n_groups; ++g) {
+        bool alias = false;
+        for (int j = 0; j < S.n_groups; ++j) alias = alias || (same_group(D, g, S, j) && d.dst_ptrs[g] == d.src_ptrs[j]);
+        if (!alias)
+          for (int f : D.groups[g]) moved += dtype_size(D.dtype[f]);
+      }
+      b->bytes += 2.0 * moved * (double)d.n;
+    }
+    headers.push_back(h);
+  }
+  prefix.push_back(blocks);
+  b->n_arrays = n_arrays;
+  b->total_blocks = blocks;
+  b->off_headers = al256(sizeof(unsigned long long));
+  b->off_groups = b->off_headers + al256(headers.size() * sizeof(BatchHeader));
+  b->off_slots = b->off_groups + al256(std::max<size_t>(1, groups.size()) * sizeof(GroupRef));
+  b->off_nslots = b->off_slots + al256(std::max<size_t>(1, slots.size()) * sizeof(uint32_t));
+  b->off_prefix = b->off_nslots + al256(std::max<size_t>(1, nslots.size()) * sizeof(int32_t));
+  b->image.assign(b->off_prefix + al256(prefix.size() * sizeof(int64_t)), 0);
+  std::memcpy(b->image.data() + b->off_headers, headers.data(), headers.size() * sizeof(BatchHeader));
+  if (!groups.empty()) std::memcpy(b->image.data() + b->off_groups, groups.data(), groups.size() * sizeof(GroupRef));
+  if (!slots.empty()) std::memcpy(b->image.data() + b->off_slots, slots.data(), slots.size() * sizeof(uint32_t));
+  if (!nslots.empty()) std::memcpy(b->image.data() + b->off_nslots, nslots.data(), nslots.size() * sizeof(int32_t));
+  std::memcpy(b->image.data() + b->off_prefix, prefix.data(), prefix.size() * sizeof(int64_t));
+  b->smem = (size_t)2 * kMaxGroups * sizeof(GroupRef) + kMaxGroups * 4 + kMaxSlots * 4 + (size_t)b->max_elems * 4 +
+            (size_t)kWarps * (2 * b->max_in + b->max_out);
+  if (b->smem > (size_t)kSmemLimit - 1024) {
+    const size_t need = b->smem;
+    delete b;
+    return fail(ADHA_ENOTIMPL, "batched remap needs %zu bytes of shared memory per CTA (limit %d): an array is too wide",
+                need, kSmemLimit);
+  }
+  int sms = 0, per_sm = 0;
+  if (int rc = sm_count(&sms)) {
+    delete b;
+    return rc;
+  }
+  cudaError_t e = cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel, kThreads, b->smem);
+  if (e != cudaSuccess) {
+    delete b;
+    return cuda_fail(e, "batched occupancy");
+  }
+  b->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * std::max(1, per_sm), blocks));
+  *out = b;
+  return 0;
+}
+
+size_t adha_batched_workspace_bytes(const adha_batched* b) { return b ? b->image.size() : 0; }
+
+int adha_batched_upload(const adha_batched* b, void* workspace, size_t ws_bytes, adha_stream stream) {
+  clear_error();
+  if (!b || !workspace) return fail(ADHA_EINVAL, "NULL batched plan or workspace");
+  if (ws_bytes < b->image.size()) return fail(ADHA_ENOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, b->image.size());
+  if (reinterpret_cast<uintptr_t>(workspace) % 256) return fail(ADHA_EINVAL, "workspace is not 256-byte aligned");
+  cudaError_t e = cudaMemcpyAsync(workspace, b->image.data(), b->image.size(), cudaMemcpyHostToDevice, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "upload of the batched descriptors");
+  e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize(upload)");
+  return 0;
+}
+
+static int batched_fn(const void* ctx) {
+  const auto* c = static_cast<const std::pair<const adha_batched*, std::pair<void*, void*>>*>(ctx);
+  return launch_batched(c->first, c->second.first, c->second.second);
+}
+
+int adha_batched_launch(const adha_batched* b, void* workspace, adha_stream stream) {
+  clear_error();
+  if (!b || !workspace) return fail(ADHA_EINVAL, "NULL batched plan or workspace");
+  const std::pair<const adha_batched*, std::pair<void*, void*>> ctx{b, {workspace, stream}};
+  return profiled_launch(3, 0, b->bytes, stream, batched_fn, &ctx);
+}
+
+int adha_batched_graph(adha_batched* b, void* workspace, adha_stream stream) {
+  clear_error();
+  if (!b || !workspace) return fail(ADHA_EINVAL, "NULL batched plan or workspace");
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  // Capture on a private stream (the legacy default stream cannot be captured); the graph is
+  // later launched on the caller's stream.  `stream` is synchronized first so that the capture
+  // does not race with work already queued there.
+  (void)stream;
+  cudaStream_t s = nullptr;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e, "capture stream");
+  e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(s);
+    return cuda_fail(e, "cudaStreamBeginCapture");
+  }
+  const int rc = launch_batched(b, workspace, s);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(s, &g);
+  cudaStreamDestroy(s);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&b->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  b->graph_ws = workspace;
+  return 0;
+}
+
+static int graph_fn(const void* ctx) {
+  const auto* c = static_cast<const std::pair<const adha_batched*, void*>*>(ctx);
+  cudaError_t e = cudaGraphLaunch(c->first->graph, (cudaStream_t)c->second);
+  return e == cudaSuccess ? 0 : cuda_fail(e, "cudaGraphLaunch");
+}
+
+int adha_batched_graph_launch(const adha_batched* b, adha_stream stream) {
+  clear_error();
+  if (!b || !b->graph) return fail(ADHA_EINVAL, "no captured graph: call adha_batched_graph first");
+  const std::pair<const adha_batched*, void*> ctx{b, stream};
+  return profiled_launch(3, 1, b->bytes, stream, graph_fn, &ctx);
+}
+
+void adha_batched_destroy(adha_batched* b) {
+  if (!b) return;
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  delete b;
+}
+
+double adha_batched_bytes(const adha_batched* b) { return b ? b->bytes : 0.0; }
+
+}  // extern "C"

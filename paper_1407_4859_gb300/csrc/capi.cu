@@ -599,6 +599,19 @@ static int plan_section(const Layout& L, void* const* ptrs, const adha_section* 
   return finish_grid(a.n_chunks, blocks, &plan->grid);
 }
 
+int remap_plan_args(const Layout& S, const void* const* src_ptrs, const Layout& D, void* const* dst_ptrs, int64_t n,
+                    int chunk_override, RemapArgs* out, bool* empty) {
+  const int saved = t_tile_override;
+  t_tile_override = chunk_override;
+  RemapPlan plan;
+  const int rc = plan_remap(S, src_ptrs, D, dst_ptrs, n, &plan);
+  t_tile_override = saved;
+  if (rc) return rc;
+  *out = plan.args;
+  *empty = plan.empty;
+  return 0;
+}
+
 static double remap_bytes(const RemapArgs& a, const Layout& D, const std::vector<int>& built) {
   double b = 0;
   for (int d : built)
@@ -639,6 +652,10 @@ static int do_remap(const Layout& S, const void* const* src_ptrs, const Layout& 
 int remap_layouts(const Layout& S, const void* const* src_ptrs, const Layout& D, void* const* dst_ptrs, int64_t n,
                   void* stream, int* launched) {
   return do_remap(S, src_ptrs, D, dst_ptrs, n, stream, launched);
+}
+
+int profiled_launch(int kind, int op, double bytes, void* stream, int (*fn)(const void*), const void* ctx) {
+  return profiled(kind, op, bytes, stream, [&] { return fn(ctx); });
 }
 
 int run_section_layout(const Layout& L, void* const* ptrs, const adha_section* s, int64_t n, void* save, void* stream) {

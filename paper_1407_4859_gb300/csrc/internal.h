@@ -116,6 +116,11 @@ int remap_layouts(const Layout& S, const void* const* src_ptrs, const Layout& D,
 int run_section_layout(const Layout& L, void* const* ptrs, const adha_section* s, int64_t n, void* save,
                        void* stream);
 adha_layout set_layout(const adha_layout_set* s, int l);
+// Remap launch arguments for one array (chunk_override 0 = the default chunk rule).
+int remap_plan_args(const Layout& S, const void* const* src_ptrs, const Layout& D, void* const* dst_ptrs, int64_t n,
+                    int chunk_override, RemapArgs* out, bool* empty);
+// Runs fn(ctx) bracketed by the launch profiler's events when profiling is on.
+int profiled_launch(int kind, int op, double bytes, void* stream, int (*fn)(const void*), const void* ctx);
 // Autotuning: the key of a section launch, storing its best shape, thread-local overrides.
 std::string tuning_key(const Layout& L, const adha_section* s, int64_t n, bool save);
 void tuning_store(const std::string& key, int R, int wb);
@@ -150,6 +155,11 @@ int remap_layouts(const Layout& S, const void* const* src_ptrs, const Layout& D,
 int run_section_layout(const Layout& L, void* const* ptrs, const adha_section* s, int64_t n, void* save,
                        void* stream);
 adha_layout set_layout(const adha_layout_set* s, int l);
+// Remap launch arguments for one array (chunk_override 0 = the default chunk rule).
+int remap_plan_args(const Layout& S, const void* const* src_ptrs, const Layout& D, void* const* dst_ptrs, int64_t n,
+                    int chunk_override, RemapArgs* out, bool* empty);
+// Runs fn(ctx) bracketed by the launch profiler's events when profiling is on.
+int profiled_launch(int kind, int op, double bytes, void* stream, int (*fn)(const void*), const void* ctx);
 // Autotuning: the key of a section launch, storing its best shape, thread-local overrides.
 std::string tuning_key(const Layout& L, const adha_section* s, int64_t n, bool save);
 void tuning_store(const std::string& key, int R, int wb);
