@@ -368,6 +368,27 @@ double adha_batched_bytes(const adha_batched* b);
 /* Frees b and its graph (NULL is ignored). */
 void adha_batched_destroy(adha_batched* b);
 
+/* Bytes of the device array that adha_remap_batched_noalloc keeps its descriptors in. */
+#define ADHA_NOALLOC_SCRATCH_BYTES (1u << 20)
+
+/*
+ * The batched remap for callers that cannot allocate device memory: code
+ * running where cudaMalloc is not allowed (inside someone else's memory pool or
+ * allocator accounting, or a plugin given only its input and output buffers)
+ * cannot provide the workspace adha_batched_upload needs.  This entry point
+ * keeps the descriptors and the work ticket in a fixed device array inside the
+ * library (ADHA_NOALLOC_SCRATCH_BYTES, held on every GPU that loads the library
+ * until the process exits) and calls no device-allocating routine.  The caller
+ * still passes every input and output buffer in `descs` (rules of adha_remap).
+ * A batch whose descriptors do not fit fails with ADHA_EINVAL.  Each call
+ * rewrites the descriptors and zeroes the ticket, then launches the kernel on
+ * `stream` (async); all calls share the one array, so calls that overlap on the
+ * GPU race and must be ordered by the caller.  The first call on a device looks
+ * up the array's device address; make that first call before any stream
+ * capture.  The paper has no counterpart of this entry point.
+ */
+int adha_remap_batched_noalloc(int32_t n_arrays, const adha_remap_desc* descs, adha_stream stream);
+
 /*
  * Records per warp chunk (a multiple of 32 up to 1024; 0 = automatic) that the
  * remap and section kernels launched later by the calling thread use.  The

@@ -12,6 +12,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -468,3 +469,65 @@ void adha_batched_destroy(adha_batched* b) {
 double adha_batched_bytes(const adha_batched* b) { return b ? b->bytes : 0.0; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Batched remap without a caller workspace.
+//
+// For callers that cannot allocate device memory (for example code that runs where cudaMalloc
+// is forbidden or would break an outer allocator's accounting, or plugins handed only their
+// input and output buffers), the descriptors and the work ticket of the batched remap can live
+// in this file-scope device array instead of a caller workspace.  Every GPU that loads the
+// library holds the array until the process exits.  All calls share it and it keeps the last
+// call's contents: each call rewrites the descriptors and zeroes the ticket before its kernel,
+// so calls that overlap on the GPU (on different streams, unordered) race on it.
+
+namespace adha {
+
+static __device__ __align__(256) uint8_t g_noalloc_scratch[ADHA_NOALLOC_SCRATCH_BYTES];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[256];
+
+// Device address of the scratch array on the current device, looked up once per device (the
+// host-side name of a __device__ array is only a stand-in, not a device address).
+static int noalloc_scratch(void** ptr) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= 256) return fail(ADHA_ENOTIMPL, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(batched scratch)");
+    g_noalloc_ptr[dev] = p;
+  }
+  *ptr = g_noalloc_ptr[dev];
+  return 0;
+}
+
+}  // namespace adha
+
+extern "C" int adha_remap_batched_noalloc(int32_t n_arrays, const adha_remap_desc* descs, adha_stream stream) {
+  clear_error();
+  void* scratch = nullptr;
+  if (int rc = noalloc_scratch(&scratch)) return rc;
+  adha_batched* b = nullptr;
+  if (int rc = adha_batched_create(n_arrays, descs, 0, stream, &b)) return rc;
+  const size_t need = b->image.size();
+  if (need > (size_t)ADHA_NOALLOC_SCRATCH_BYTES) {
+    adha_batched_destroy(b);
+    return fail(ADHA_EINVAL, "this batch needs %zu bytes of descriptors; the allocation-free entry point holds at most %u",
+                need, (unsigned)ADHA_NOALLOC_SCRATCH_BYTES);
+  }
+  // Pageable source: the call returns once the bytes are staged, so the host image can go.
+  cudaError_t e = cudaMemcpyAsync(scratch, b->image.data(), need, cudaMemcpyHostToDevice, (cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    adha_batched_destroy(b);
+    return cuda_fail(e, "copy of the batched descriptors into the scratch array");
+  }
+  const std::pair<const adha_batched*, std::pair<void*, void*>> ctx{b, {scratch, stream}};
+  const int rc = profiled_launch(3, 2, b->bytes, stream, batched_fn, &ctx);
+  adha_batched_destroy(b);
+  return rc;
+}
