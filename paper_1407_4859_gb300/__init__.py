@@ -1,7 +1,7 @@
 """GB300 (sm_103a) implementation of the ADHA data-layout path (Majeti et al., PACT 2014).
 
 The compute lives in libadha.so (hand-written CUDA, C ABI in include/adha.h); this package is
-its thin ctypes binding.  Importing it does not load the library; the first call does, and
+its thin ctypes binding; autograd.py makes remaps and chain sections differentiable.  Importing it does not load the library; the first call does, and
 raises if the library has not been built.
 """
 from .api import (  # noqa: F401
