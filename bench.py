@@ -197,7 +197,11 @@ def main():
     ap.add_argument("--impl", default="adha", choices=["adha", "reference"])
     ap.add_argument("--no-compare", action="store_true", help="skip the AoS/SoA/exhaustive program comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle timing")
-    ap.add_argument("--n-log2", type=int, default=24, help="records per GPU (default 2^24, the workload's size)")
+    ap.add_argument("--workload", default="stress", choices=["stress", "particles", "batched", "differentiable"],
+                    help="stress: the 2^24-record layout-stress program (the headline); particles: the 2^25-record "
+                         "particle program with a gather; batched: 256 uneven arrays remapped in one launch; "
+                         "differentiable: the 2^26-record chain of 64 sections, forward + backward")
+    ap.add_argument("--n-log2", type=int, default=0, help="records per GPU (default: the workload's size)")
     ap.add_argument("--cost-cache", default=None,
                     help="JSON file holding the measured cost table: loaded when it matches the GPU, workload and "
                          "candidates, written after measuring otherwise")
@@ -220,11 +224,19 @@ def main():
     build.build()
     import paper_1407_4859_gb300 as P
 
-    wl = synth.config2(n=1 << args.n_log2)
+    if args.workload == "batched":
+        return batched_bench(args, rank, world, local, dist)
+    if args.workload == "differentiable":
+        return differentiable_bench(args, rank, world, local, dist)
+    if args.workload == "particles":
+        wl = synth.config3(n=1 << (args.n_log2 or 25))
+    else:
+        wl = synth.config2(n=1 << (args.n_log2 or 24))
     n = wl.n
     S = P.Schema(wl.dtypes)
     AOS = P.Layout.aos(wl.F)
-    secs = P.Sections(wl.sections)
+    perm_dev = torch.from_numpy(wl.perm()).cuda() if wl.has_perm else None
+    secs = P.Sections(wl.sections, perm_dev)
     t0 = time.perf_counter()
     host_aos = None
     fields = [wl.values(f) for f in range(wl.F)]
@@ -388,19 +400,21 @@ def main():
             t_tot += oracle_program_seconds(wl, plan_layouts, n_sample)
             reps += 1
         cpu = {"value": round(b_small * reps / t_tot / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
-               "sample": "first 2^22 of 2^24 records x %d runs: AoS decode, 9 sections, encode in the ADHA final layout"
-                         % reps}
+               "sample": "first 2^22 of %d records x %d runs: AoS decode, %d sections, encode in the ADHA final layout"
+                         % (n, reps, len(wl.sections))}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64+i32",
-            "data": "synthetic (seeded SplitMix64, uniform values as the workload states)",
-            "config": {"workload": wl.name, "records": n, "fields": "8 f32 + 4 f64 + 4 i32 (80 B AoS)",
+            "data": "synthetic (seeded SplitMix64, values as the workload states)",
+            "config": {"workload": wl.name, "records": n,
+                       "fields": ("8 f32 + 4 f64 + 4 i32 (80 B AoS)" if args.workload == "stress"
+                                  else "pos, vel, mass, charge f32; id, cell, flags i32; energy f64 (56 B AoS)"),
                        "sections": len(wl.sections), "candidates": L, "plan": seq,
                        "plan_layouts": plan_layouts, "remaps_per_step": plan.n_remaps,
-                       "l2": "inputs larger than L2 (1.34 GB per layout vs 129 MB)",
+                       "l2": "inputs larger than L2 (%.2f GB per AoS copy vs 129 MB)" % (pinned.numel() / 1e9),
                        "parallelism": "one independent batch per GPU" if world > 1 else "single GPU",
                        "measure_s": round(measure_s, 2), "program_bytes_per_step": bytes_per_step,
                        "remap_bytes_per_step": remap_bytes_per_step,
@@ -412,6 +426,257 @@ def main():
             "e2e": e2e, "cpu_baseline": cpu, "program_ms": compare,
         }
         print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+# ---------------------------------------------------------------------------------- other workloads
+
+def _timed(torch, stream, steps, fn):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def _max_ms(torch, dist, ms):
+    if not dist:
+        return ms
+    t = torch.tensor([ms], device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _roofline(recs):
+    groups = {}
+    for r in recs:
+        key = r["kind"] if r["kind"] != "section" else "section_%s" % r["op"]
+        g = groups.setdefault(key, [0.0, 0.0, 0])
+        g[0] += r["ms"]
+        g[1] += r["bytes"]
+        g[2] += 1
+    dom = max(groups, key=lambda k: groups[k][0])
+    peak, src = measured_peaks()
+    achieved = groups[dom][1] / (groups[dom][0] * 1e6)
+    total = sum(v[0] for v in groups.values())
+    roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback",
+            "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic_for(dom),
+            "launches": groups[dom][2], "share": round(groups[dom][0] / max(1e-9, total), 3)}
+    kernels = {k: {"launches": v[2], "ms": round(v[0], 3), "alg_GBs": round(v[1] / (v[0] * 1e6), 1)}
+               for k, v in sorted(groups.items(), key=lambda kv: -kv[1][0])}
+    return roof, kernels
+
+
+def batched_bench(args, rank, world, local, dist):
+    """256 record arrays (N log-uniform in [2^10, 2^22), F in [4, 32], mixed dtypes) remapped
+    AoS -> their own random groupings: one graph-captured persistent launch per step, against one
+    adha_remap launch per array."""
+    import numpy as np
+    import torch
+    import synth
+    import oracle
+    import paper_1407_4859_gb300 as P
+    stream = torch.cuda.current_stream()
+    specs = synth.config4_arrays(n_scale=2.0 ** ((args.n_log2 or 22) - 22))
+    arrays, host_in = [], []
+    t0 = time.perf_counter()
+    for a in specs:
+        S = P.Schema(a["dtypes"])
+        src, dst = P.Layout(a["src"]), P.Layout(a["dst"])
+        (sst,), _ = P.adha_layout_strides(S, src)
+        dst_st, _ = P.adha_layout_strides(S, dst)
+        words = (a["n"] * sst + 7) // 8
+        raw = synth.fill("RAW64", synth.key(3, 200000 + len(arrays)), n=words).view(np.uint8)[: a["n"] * sst]
+        h = torch.from_numpy(np.ascontiguousarray(raw)).pin_memory()
+        host_in.append(h)
+        arrays.append(dict(schema=S, n=a["n"], src=src, dst=dst, src_bufs=[h.cuda()],
+                           dst_bufs=[torch.empty(max(1, a["n"] * s), dtype=torch.uint8, device="cuda") for s in dst_st]))
+    log("batched inputs ready in %.1f s" % (time.perf_counter() - t0))
+    t0 = time.perf_counter()
+    b = P.Batched(arrays, autotune=True)
+    b.upload()
+    b.capture()
+    tune_s = time.perf_counter() - t0
+    bytes_per = b.bytes
+    for _ in range(args.warmup):
+        b.graph_launch()
+    clocks = Clocks(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    P.adha_profile_start(4 * args.steps + 16)
+    torch.cuda.nvtx.range_push("timed")
+    ms = _timed(torch, stream, args.steps, b.graph_launch)
+    torch.cuda.nvtx.range_pop()
+    recs = P.adha_profile_stop(4 * args.steps + 16)
+    clk = clocks.stop()
+    ms = _max_ms(torch, dist, ms)
+    value = world * bytes_per * args.steps / (ms * 1e6)
+    roof, kernels = _roofline(recs)
+
+    def per_array():
+        for a in arrays:
+            P.adha_remap(a["schema"], a["n"], a["src"], a["src_bufs"], a["dst"], a["dst_bufs"], stream=stream)
+    for _ in range(3):
+        per_array()
+    k2 = max(3, args.steps // 10)
+    per_ms = _timed(torch, stream, k2, per_array) / k2
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            for a in arrays:
+                P.adha_remap(a["schema"], a["n"], a["src"], a["src_bufs"], a["dst"], a["dst_bufs"],
+                             stream=torch.cuda.current_stream())
+    stream.wait_stream(side)
+    for _ in range(3):
+        g.replay()
+    graph_ms = _timed(torch, stream, k2, g.replay) / k2
+    # end to end: host inputs in, one batched launch, results out
+    host_out = [[torch.empty(d.numel(), dtype=torch.uint8).pin_memory() for d in a["dst_bufs"]] for a in arrays]
+    e2e_steps = 3
+
+    def e2e_step():
+        for a, h in zip(arrays, host_in):
+            a["src_bufs"][0].copy_(h, non_blocking=True)
+        b.graph_launch()
+        for a, ho in zip(arrays, host_out):
+            for d, hh in zip(a["dst_bufs"], ho):
+                hh.copy_(d, non_blocking=True)
+    e2e_step()
+    e2e_ms = _timed(torch, stream, e2e_steps, e2e_step) / e2e_steps
+    h2d = sum(h.numel() for h in host_in)
+    d2h = sum(hh.numel() for ho in host_out for hh in ho)
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        t_tot, moved = 0.0, 0.0
+        for a, h in list(zip(specs, host_in))[:64]:
+            ns = min(a["n"], 1 << 16)
+            S = a["dtypes"]
+            (sst,), _ = P.adha_layout_strides(P.Schema(S), P.Layout(a["src"]))
+            src_bytes = h[: ns * sst].numpy()
+            t1 = time.perf_counter()
+            oracle.remap(ns, S, a["src"], [src_bytes], a["dst"])
+            t_tot += time.perf_counter() - t1
+            moved += 2 * ns * sum(SZ[d] for d in S)
+        cpu = {"value": round(moved / t_tot / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": "first min(N, 2^16) records of the first 64 arrays, scalar oracle remap"}
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bytes (f32/f64/i32/bf16 fields)",
+            "data": "synthetic (seeded SplitMix64 bytes)",
+            "config": {"workload": "config4_batched_remap_256_arrays", "arrays": len(arrays),
+                       "records": int(sum(a["n"] for a in arrays)), "moved_bytes_per_step": bytes_per,
+                       "l2": "inputs larger than L2 (%.1f GB)" % (h2d / 1e9), "autotune_and_capture_s": round(tune_s, 2),
+                       "value_definition": "2 x data bytes of all moved fields of all arrays / step time"},
+            "gpu_launches": len(recs), "roofline": roof, "kernels": kernels, "clocks": clk,
+            "per_array_launches": {"ms_per_step": round(per_ms, 4), "GBs": round(bytes_per / (per_ms * 1e6), 1),
+                                   "graph_of_256_launches_ms": round(graph_ms, 4),
+                                   "graph_of_256_launches_GBs": round(bytes_per / (graph_ms * 1e6), 1)},
+            "e2e": {"value": round(world * bytes_per / (e2e_ms * 1e6), 1), "unit": "GB/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3)},
+            "cpu_baseline": cpu}), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def differentiable_bench(args, rank, world, local, dist):
+    """The 2^26-record chain of 64 fp32 sections: forward (remaps + in-place sections with saves)
+    and backward (inverse remaps + adjoint kernels) under the PDL plan, against all-AoS / all-SoA."""
+    import numpy as np
+    import torch
+    import synth
+    import oracle
+    import paper_1407_4859_gb300 as P
+    from paper_1407_4859_gb300.autograd import DifferentiableProgram
+    wl = synth.config5(n=1 << (args.n_log2 or 26))
+    n, F = wl.n, wl.F
+    S = P.Schema(wl.dtypes)
+    AOS = P.Layout.aos(F)
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    host = np.empty((n, F), dtype=np.float32)
+    for f in range(F):
+        host[:, f] = wl.values(f)
+    pinned = torch.from_numpy(host).pin_memory()
+    del host
+    x0 = pinned.cuda()
+    log("inputs ready in %.1f s" % (time.perf_counter() - t0))
+    secs = P.Sections(wl.sections)
+    cand = P.adha_plan_sections(S, secs, P.PlanOpts(CAPS, max_window=2, max_candidates=16))
+    t0 = time.perf_counter()
+    costs = P.adha_measure(S, n, AOS, [x0], secs, cand, reps=2, autotune=True)
+    measure_s = time.perf_counter() - t0
+    _, seq = P.adha_pdl_solve(costs)
+    layouts = cand.layouts
+    c = torch.tensor(wl.loss_weights, dtype=torch.float32, device="cuda")
+
+    def run(plan_layouts):
+        x = x0.detach().requires_grad_(True)
+        prog = DifferentiableProgram(S, n, AOS, wl.sections, plan_layouts)
+        lay, out = prog.forward([x])
+        loss = None
+        for g, t in zip(lay.groups, out):
+            term = (t * c[torch.tensor(g, device="cuda")]).sum()
+            loss = term if loss is None else loss + term
+        loss.backward()
+        return x.grad
+
+    plan = [layouts[l] for l in seq]
+    for _ in range(args.warmup):
+        run(plan)
+    clocks = Clocks(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    P.adha_profile_start(512 * args.steps + 64)
+    torch.cuda.nvtx.range_push("timed")
+    ms = _timed(torch, stream, args.steps, lambda: run(plan))
+    torch.cuda.nvtx.range_pop()
+    recs = P.adha_profile_stop(512 * args.steps + 64)
+    clk = clocks.stop()
+    ms = _max_ms(torch, dist, ms)
+    fwd = sum(r["bytes"] for r in recs if r["kind"] in ("section", "remap")) / args.steps
+    bwd = sum(r["bytes"] for r in recs if r["kind"] == "section_backward") / args.steps
+    # program work only (sections and their adjoints), like the stress bench's value
+    work = sum(r["bytes"] for r in recs if r["kind"] in ("section", "section_backward")) / args.steps
+    value = world * work * args.steps / (ms * 1e6)
+    roof, kernels = _roofline(recs)
+    k2 = max(3, args.steps // 2)
+    t_aos = _timed(torch, stream, k2, lambda: run([AOS] * len(wl.sections))) / k2
+    t_soa = _timed(torch, stream, k2, lambda: run([P.Layout.soa(F)] * len(wl.sections))) / k2
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        ns = 1 << 18
+        st = [wl.values(f, n=ns) for f in range(F)]
+        t1 = time.perf_counter()
+        oracle.chain_grad(wl.sections, st, wl.loss_weights)
+        dt = time.perf_counter() - t1
+        cpu = {"value": round(work * ns / n / dt / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": "first 2^18 of 2^26 records: forward + reverse pass per record"}
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded N(0,1))",
+            "config": {"workload": wl.name, "records": n, "fields": "24 f32 (96 B AoS)", "sections": len(wl.sections),
+                       "candidates": len(cand), "plan": seq, "measure_s": round(measure_s, 1),
+                       "forward_bytes_per_step": fwd, "backward_bytes_per_step": bwd,
+                       "value_definition": "section + adjoint algorithmic bytes per forward+backward step / step time",
+                       "l2": "inputs larger than L2 (6.4 GB)"},
+            "gpu_launches": len(recs), "roofline": roof, "kernels": kernels, "clocks": clk,
+            "step_ms": {"adha": round(ms / args.steps, 3), "all_aos": round(t_aos, 3), "all_soa": round(t_soa, 3)},
+            "cpu_baseline": cpu}), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0

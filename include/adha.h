@@ -428,8 +428,9 @@ typedef struct {
   double ms;
 } adha_launch_record;
 
-/* Starts recording every kernel the calling thread launches through this
- * library (up to max_records; events are created once and reused).  Host only. */
+/* Starts recording every kernel launched through this library by any host
+ * thread of the process (up to max_records; events are created once and
+ * reused).  Host only. */
 int adha_profile_start(int32_t max_records);
 
 /* Stops recording, waits for the recorded launches and copies up to

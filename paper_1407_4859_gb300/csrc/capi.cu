@@ -178,26 +178,37 @@ void tanh_coefficients(float p[8], float q[8]) {
 // ------------------------------------------------------------------ launch profiler
 // When on, every kernel the calling thread launches is bracketed by two CUDA events on its
 // stream and tagged with its kind, op and algorithmic bytes (what the method must move).
+// Process-wide, so launches from other host threads (an autograd engine's, for example) are seen.
 struct ProfRec {
   int kind, op;
   double bytes;
   cudaEvent_t a, b;
 };
-static thread_local bool t_prof_on = false;
-static thread_local std::vector<ProfRec> t_prof;
-static thread_local std::vector<cudaEvent_t> t_pool;
-static thread_local size_t t_pool_used = 0;
+static std::mutex g_prof_mu;
+static bool t_prof_on = false;
+static std::vector<ProfRec> t_prof;
+static std::vector<cudaEvent_t> t_pool;
+static size_t t_pool_used = 0;
 
 template <class Fn>
 static int profiled(int kind, int op, double bytes, void* stream, Fn launch) {
-  if (!t_prof_on || t_pool_used + 2 > t_pool.size()) return launch();
-  ProfRec r{kind, op, bytes, t_pool[t_pool_used], t_pool[t_pool_used + 1]};
-  t_pool_used += 2;
+  ProfRec r{kind, op, bytes, nullptr, nullptr};
+  {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!t_prof_on || t_pool_used + 2 > t_pool.size()) r.a = nullptr;
+    else {
+      r.a = t_pool[t_pool_used];
+      r.b = t_pool[t_pool_used + 1];
+      t_pool_used += 2;
+    }
+  }
+  if (!r.a) return launch();
   cudaError_t e = cudaEventRecord(r.a, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord(profile)");
   if (int rc = launch()) return rc;
   e = cudaEventRecord(r.b, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord(profile)");
+  std::lock_guard<std::mutex> lk(g_prof_mu);
   t_prof.push_back(r);
   return 0;
 }
@@ -761,6 +772,7 @@ int adha_section_backward(const adha_schema* schema, int64_t n, const adha_layou
 int adha_profile_start(int32_t max_records) {
   clear_error();
   if (max_records < 1 || max_records > (1 << 20)) return fail(ADHA_EINVAL, "max_records %d not in [1, 2^20]", max_records);
+  std::lock_guard<std::mutex> lk(g_prof_mu);
   while (t_pool.size() < 2 * (size_t)max_records) {
     cudaEvent_t e;
     cudaError_t err = cudaEventCreate(&e);
@@ -775,6 +787,7 @@ int adha_profile_start(int32_t max_records) {
 
 int adha_profile_stop(adha_launch_record* out, int32_t max_records, int32_t* n_records) {
   clear_error();
+  std::lock_guard<std::mutex> lk(g_prof_mu);
   t_prof_on = false;
   if (!n_records) return fail(ADHA_EINVAL, "n_records is NULL");
   int32_t k = 0;

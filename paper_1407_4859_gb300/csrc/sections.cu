@@ -430,28 +430,61 @@ __global__ void __launch_bounds__(kThreads) section_kernel(const __grid_constant
   }
 }
 
-// Reverse of one fp32 chain section (AXPB, MUL, TANH) on one record per thread: restore the
-// overwritten field, then propagate the adjoint in the oracle's operation order.
+// Reverse of one fp32 chain section (AXPB, MUL, TANH).  Every value a record needs is loaded
+// first (4 records per thread, independent loads), the oracle's sequential update
+//   restore z; gz = g[z]; g[z] = 0; then g[x] (and g[y]) += ...
+// is carried out in registers with the aliasing of x, y, z resolved explicitly (they are
+// launch-uniform), and the results are stored last.
+template <int OP>
+__device__ __forceinline__ void backward_record(const BackwardArgs& a, int64_t i, float sv, float xs, float ys,
+                                                float gz, float gx, float gy) {
+  const bool xz = a.x == a.z, yz = a.y == a.z, xy = a.x == a.y;
+  const float xo = xz ? sv : xs;                   // x before the section
+  const float yo = yz ? sv : ys;
+  float gxn = xz ? 0.0f : gx;                      // after g[z] = 0
+  if (OP == ADHA_OP_AXPB) {
+    gxn = __fadd_rn(gxn, __fmul_rn(a.a, gz));
+  } else if (OP == ADHA_OP_TANH) {
+    const float t = tanh_cf(xo, a.tanh_p, a.tanh_q);
+    gxn = __fadd_rn(gxn, __fmul_rn(gz, __fsub_rn(1.0f, __fmul_rn(t, t))));
+  } else {
+    gxn = __fadd_rn(gxn, __fmul_rn(gz, yo));
+    float gyn = xy ? gxn : (yz ? 0.0f : gy);
+    gyn = __fadd_rn(gyn, __fmul_rn(gz, xo));
+    *reinterpret_cast<float*>(a.g[1] + i * a.gs[1]) = gyn;
+    if (!xy) *reinterpret_cast<float*>(a.g[0] + i * a.gs[0]) = gxn;
+    if (!xz && !yz) *reinterpret_cast<float*>(a.g[2] + i * a.gs[2]) = 0.0f;
+    *reinterpret_cast<float*>(a.s[2] + i * a.ss[2]) = sv;
+    return;
+  }
+  *reinterpret_cast<float*>(a.g[0] + i * a.gs[0]) = gxn;
+  if (!xz) *reinterpret_cast<float*>(a.g[2] + i * a.gs[2]) = 0.0f;
+  *reinterpret_cast<float*>(a.s[2] + i * a.ss[2]) = sv;
+}
+
+template <int OP>
 __global__ void __launch_bounds__(kThreads) backward_kernel(const __grid_constant__ BackwardArgs a) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
-    *reinterpret_cast<float*>(a.s[2] + i * a.ss[2]) = a.save[i];
-    const float xo = *reinterpret_cast<const float*>(a.s[0] + i * a.ss[0]);
-    float* gz_p = reinterpret_cast<float*>(a.g[2] + i * a.gs[2]);
-    const float gz = *gz_p;
-    *gz_p = 0.0f;
-    float* gx_p = reinterpret_cast<float*>(a.g[0] + i * a.gs[0]);
-    if (a.op == ADHA_OP_AXPB) {
-      *gx_p = __fadd_rn(*gx_p, __fmul_rn(a.a, gz));
-    } else if (a.op == ADHA_OP_MUL) {
-      const float yo = *reinterpret_cast<const float*>(a.s[1] + i * a.ss[1]);
-      *gx_p = __fadd_rn(*gx_p, __fmul_rn(gz, yo));
-      float* gy_p = reinterpret_cast<float*>(a.g[1] + i * a.gs[1]);
-      *gy_p = __fadd_rn(*gy_p, __fmul_rn(gz, xo));
-    } else {
-      const float t = tanh_cf(xo, a.tanh_p, a.tanh_q);
-      const float d = __fsub_rn(1.0f, __fmul_rn(t, t));
-      *gx_p = __fadd_rn(*gx_p, __fmul_rn(gz, d));
+  constexpr int K = 4;
+  const int64_t T = (int64_t)gridDim.x * blockDim.x;
+  const bool need_y = OP == ADHA_OP_MUL;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; base < a.n; base += K * T) {
+    float sv[K], xs[K], ys[K], gz[K], gx[K], gy[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int64_t i = base + k * T;
+      if (i < a.n) {
+        sv[k] = a.save[i];
+        xs[k] = *reinterpret_cast<const float*>(a.s[0] + i * a.ss[0]);
+        ys[k] = need_y ? *reinterpret_cast<const float*>(a.s[1] + i * a.ss[1]) : 0.0f;
+        gz[k] = *reinterpret_cast<const float*>(a.g[2] + i * a.gs[2]);
+        gx[k] = *reinterpret_cast<const float*>(a.g[0] + i * a.gs[0]);
+        gy[k] = need_y ? *reinterpret_cast<const float*>(a.g[1] + i * a.gs[1]) : 0.0f;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int64_t i = base + k * T;
+      if (i < a.n) backward_record<OP>(a, i, sv[k], xs[k], ys[k], gz[k], gx[k], gy[k]);
     }
   }
 }
@@ -516,10 +549,12 @@ int section_occupancy(int op, size_t smem, int* blocks) {
 int launch_backward(const BackwardArgs& a, void* stream) {
   int sms = 0;
   if (int rc = sm_count(&sms)) return rc;
-  int64_t blocks = (a.n + kThreads - 1) / kThreads;
+  int64_t blocks = (a.n + 4 * kThreads - 1) / (4 * kThreads);
   if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
   if (blocks < 1) blocks = 1;
-  backward_kernel<<<(int)blocks, kThreads, 0, (cudaStream_t)stream>>>(a);
+  if (a.op == ADHA_OP_AXPB) backward_kernel<ADHA_OP_AXPB><<<(int)blocks, kThreads, 0, (cudaStream_t)stream>>>(a);
+  else if (a.op == ADHA_OP_MUL) backward_kernel<ADHA_OP_MUL><<<(int)blocks, kThreads, 0, (cudaStream_t)stream>>>(a);
+  else backward_kernel<ADHA_OP_TANH><<<(int)blocks, kThreads, 0, (cudaStream_t)stream>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "backward kernel launch");
   return 0;
