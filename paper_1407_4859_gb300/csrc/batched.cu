@@ -1,7 +1,9 @@
 // batched.cu -- many record arrays remapped in one persistent launch.
 //
 // Each array (its own schema, record count and source/destination layouts) is cut into chunks
-// of R_a records, and its chunks into work blocks of kBlockChunks.  A CTA takes the next block
+// of R_a records, and its chunks into work blocks (16 chunks per working warp).  A CTA holds a
+// fixed budget of shared memory for its warps' buffers; an array whose records are too wide for
+// eight warps' buffers in that budget is worked on by fewer warps of the CTA.  A CTA takes the next block
 // with one atomic ticket (a 64-bit counter in the caller's workspace, zeroed by a memset node
 // before every launch), builds the block's array's element schedule in shared memory when the
 // array changes, and its warps run the same double-buffered cp.async pipeline as remap.cu on
@@ -17,63 +19,34 @@
 
 #include "internal.h"
 #include "ptx.cuh"
+#include "remap_common.cuh"
 
 namespace adha {
 
 constexpr int kBlockChunksPerWarp = 16;
-constexpr int kBlockChunks = kWarps * kBlockChunksPerWarp;
 
 struct BatchHeader {
   int64_t n, n_full, n_chunks, block0;
-  int32_t R, unit, n_src, n_dst, in_bytes, out_bytes, n_elems, order;
-  int32_t group0, slot0, nslot0, n_slots;
+  int32_t R, n_src, n_dst, in_bytes, out_bytes, n_moves;
+  int32_t cls_count[3], cls_order[3];
+  int32_t group0, move0;
+  int32_t warps;        // warps of a CTA that work on this array (the others idle for its blocks)
+  int32_t warp_bytes;   // shared bytes of one working warp: two input buffers and an output buffer
 };
+
+// Shared bytes for the warps' buffers in one CTA: an array whose warp needs more uses fewer warps.
+constexpr int kWarpBufferBudget = 80 * 1024;
 
 struct BatchParams {
   unsigned long long* ticket;
   const BatchHeader* headers;
   const GroupRef* groups;
-  const uint32_t* slots;
-  const int32_t* nslots;
+  const Move* moves;
   const int64_t* prefix;     // first block of each array, n_arrays + 1 entries
   int32_t n_arrays;
   int64_t total_blocks;
-  int32_t max_elems, max_in, max_out;
+  int32_t max_entries;
 };
-
-template <typename U>
-__device__ __forceinline__ void gather_elems(const uint32_t* sched, int n_elems, const uint8_t* in, uint8_t* out, int lane) {
-  const U* src = reinterpret_cast<const U*>(in);
-  U* dst = reinterpret_cast<U*>(out);
-#pragma unroll 4
-  for (int t = lane; t < n_elems; t += 32) {
-    const uint32_t p = sched[t];
-    const uint32_t x = p & 0xFFFFu;
-    dst[p >> 16] = x != 0xFFFFu ? src[x] : U(0);
-  }
-}
-
-template <typename U>
-__device__ __forceinline__ void tail_elems(const BatchHeader& h, const GroupRef* tin, const GroupRef* tout,
-                                           const int32_t* nslot, const uint32_t* slots, int lane) {
-  const int64_t t0 = h.n_full * h.R;
-  const int Tt = (int)(h.n - t0);
-  int s0 = 0;
-  for (int d = 0; d < h.n_dst; ++d) {
-    const int S = nslot[d];
-    for (int e = lane; e < Tt * S; e += 32) {
-      const int r = e / S, k = e - r * S;
-      const uint32_t code = slots[s0 + k];
-      U v = U(0);
-      if (code != kPadSlot) {
-        const GroupRef& sg = tin[code >> 16];
-        v = *reinterpret_cast<const U*>(sg.ptr + (t0 + r) * sg.stride + (code & 0xFFFFu));
-      }
-      *reinterpret_cast<U*>(const_cast<uint8_t*>(tout[d].ptr) + (t0 + r) * tout[d].stride + k * (int)sizeof(U)) = v;
-    }
-    s0 += S;
-  }
-}
 
 __global__ void __launch_bounds__(kThreads) batched_kernel(const __grid_constant__ BatchParams p) {
   extern __shared__ __align__(16) uint8_t smem[];
@@ -82,13 +55,10 @@ __global__ void __launch_bounds__(kThreads) batched_kernel(const __grid_constant
   __shared__ int s_arr;
   GroupRef* tin = reinterpret_cast<GroupRef*>(smem);
   GroupRef* tout = tin + kMaxGroups;
-  int32_t* nslot = reinterpret_cast<int32_t*>(tout + kMaxGroups);
-  uint32_t* slots = reinterpret_cast<uint32_t*>(nslot + kMaxGroups);
-  uint32_t* sched = slots + kMaxSlots;
+  Move* moves = reinterpret_cast<Move*>(tout + kMaxGroups);
+  uint32_t* sched = reinterpret_cast<uint32_t*>(moves + kMaxMoves);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  uint8_t* buf0 = reinterpret_cast<uint8_t*>(sched + p.max_elems) + (size_t)warp * (2 * p.max_in + p.max_out);
-  uint8_t* buf1 = buf0 + p.max_in;
-  uint8_t* outb = buf1 + p.max_in;
+  uint8_t* wbase = reinterpret_cast<uint8_t*>(sched + p.max_entries);
   int cur = -1;
 
   for (;;) {
@@ -112,37 +82,20 @@ __global__ void __launch_bounds__(kThreads) batched_kernel(const __grid_constant
       __syncthreads();
       for (int k = tid; k < h.n_src; k += kThreads) tin[k] = p.groups[h.group0 + k];
       for (int k = tid; k < h.n_dst; k += kThreads) tout[k] = p.groups[h.group0 + h.n_src + k];
-      for (int k = tid; k < h.n_dst; k += kThreads) nslot[k] = p.nslots[h.nslot0 + k];
-      for (int k = tid; k < h.n_slots; k += kThreads) slots[k] = p.slots[h.slot0 + k];
+      for (int k = tid; k < h.n_moves; k += kThreads) moves[k] = p.moves[h.move0 + k];
       __syncthreads();
-      for (int t = tid; t < h.n_elems; t += kThreads) {
-        int d = 0, e0 = 0, sl0 = 0;
-        while (t >= e0 + h.R * nslot[d]) {
-          e0 += h.R * nslot[d];
-          sl0 += nslot[d++];
-        }
-        const int S = nslot[d];
-        int r, k;
-        if (h.order == 0) {
-          r = (t - e0) / S;
-          k = (t - e0) - r * S;
-        } else {
-          k = (t - e0) / h.R;
-          r = (t - e0) - k * h.R;
-        }
-        const uint32_t code = slots[sl0 + k];
-        uint32_t x = 0xFFFFu;
-        if (code != kPadSlot) {
-          const int j = (int)(code >> 16);
-          x = (uint32_t)((tin[j].start + r * tin[j].stride + (int)(code & 0xFFFFu)) / h.unit);
-        }
-        sched[t] = x | ((uint32_t)(e0 + r * S + k) << 16);
-      }
+      for (int t = tid; t < h.R * h.n_moves; t += kThreads)
+        sched[t] = schedule_entry(t, h.R, h.cls_count, h.cls_order, moves, tin, tout);
       __syncthreads();
       cur = arr;
     }
-    const int64_t c_begin = (blk - h.block0) * kBlockChunks;
-    const int64_t c_end = c_begin + kBlockChunks < h.n_chunks ? c_begin + kBlockChunks : h.n_chunks;
+    const int nw = h.warps;
+    const int64_t per_block = (int64_t)kBlockChunksPerWarp * nw;
+    const int64_t c_begin = (blk - h.block0) * per_block;
+    const int64_t c_end = c_begin + per_block < h.n_chunks ? c_begin + per_block : h.n_chunks;
+    uint8_t* buf0 = wbase + (size_t)warp * h.warp_bytes;
+    uint8_t* buf1 = buf0 + h.in_bytes;
+    uint8_t* outb = buf1 + h.in_bytes;
     const int64_t full_end = c_end < h.n_full ? c_end : h.n_full;
     const int64_t R = h.R;
     auto stage = [&](int64_t ch, uint8_t* buf) {
@@ -152,18 +105,16 @@ __global__ void __launch_bounds__(kThreads) batched_kernel(const __grid_constant
         cp_async16(buf + q, tin[g].ptr + ch * R * tin[g].stride + (q - tin[g].start));
       }
     };
-    int64_t c = c_begin + warp;
+    int64_t c = warp < nw ? c_begin + warp : full_end;
     if (c < full_end) stage(c, buf0);
     cp_async_commit();
-    for (int i = 0; c < full_end; c += kWarps, ++i) {
+    for (int i = 0; c < full_end; c += nw, ++i) {
       uint8_t* curb = (i & 1) ? buf1 : buf0;
-      if (c + kWarps < full_end) stage(c + kWarps, (i & 1) ? buf0 : buf1);
+      if (c + nw < full_end) stage(c + nw, (i & 1) ? buf0 : buf1);
       cp_async_commit();
       cp_async_wait<1>();
       __syncwarp();
-      if (h.unit == 2) gather_elems<uint16_t>(sched, h.n_elems, curb, outb, lane);
-      else if (h.unit == 4) gather_elems<uint32_t>(sched, h.n_elems, curb, outb, lane);
-      else gather_elems<unsigned long long>(sched, h.n_elems, curb, outb, lane);
+      move_chunk(sched, h.R, h.cls_count, curb, outb, lane);
       __syncwarp();
       int g = 0;
       for (int q = lane * 16; q < h.out_bytes; q += 512) {
@@ -175,11 +126,8 @@ __global__ void __launch_bounds__(kThreads) batched_kernel(const __grid_constant
     }
     cp_async_wait<0>();
     // the array's ragged tail chunk, by the warp it falls to
-    if (h.n_full < h.n_chunks && h.n_full >= c_begin && h.n_full < c_end && (h.n_full - c_begin) % kWarps == warp) {
-      if (h.unit == 2) tail_elems<uint16_t>(h, tin, tout, nslot, slots, lane);
-      else if (h.unit == 4) tail_elems<uint32_t>(h, tin, tout, nslot, slots, lane);
-      else tail_elems<unsigned long long>(h, tin, tout, nslot, slots, lane);
-    }
+    if (warp < nw && h.n_full < h.n_chunks && h.n_full >= c_begin && h.n_full < c_end && (h.n_full - c_begin) % nw == warp)
+      tail_moves(h.n_full * h.R, h.n, h.n_moves, h.cls_count, moves, tin, tout, lane);
     __syncthreads();
   }
 }
@@ -191,9 +139,9 @@ using namespace adha;
 struct adha_batched {
   int32_t n_arrays = 0;
   std::vector<uint8_t> image;      // descriptor region as it is copied to the workspace
-  size_t off_headers = 0, off_groups = 0, off_slots = 0, off_nslots = 0, off_prefix = 0;
+  size_t off_headers = 0, off_groups = 0, off_moves = 0, off_prefix = 0;
   int64_t total_blocks = 0;
-  int32_t max_elems = 0, max_in = 0, max_out = 0;
+  int32_t max_entries = 0, warp_budget = kWarpBufferBudget;
   size_t smem = 0;
   int grid = 1;
   double bytes = 0;
@@ -211,14 +159,11 @@ static BatchParams params_for(const adha_batched* b, void* ws) {
   p.ticket = reinterpret_cast<unsigned long long*>(base);
   p.headers = reinterpret_cast<const BatchHeader*>(base + b->off_headers);
   p.groups = reinterpret_cast<const GroupRef*>(base + b->off_groups);
-  p.slots = reinterpret_cast<const uint32_t*>(base + b->off_slots);
-  p.nslots = reinterpret_cast<const int32_t*>(base + b->off_nslots);
+  p.moves = reinterpret_cast<const Move*>(base + b->off_moves);
   p.prefix = reinterpret_cast<const int64_t*>(base + b->off_prefix);
   p.n_arrays = b->n_arrays;
   p.total_blocks = b->total_blocks;
-  p.max_elems = b->max_elems;
-  p.max_in = b->max_in;
-  p.max_out = b->max_out;
+  p.max_entries = b->max_entries;
   return p;
 }
 
@@ -247,7 +192,7 @@ static int tune_chunk(const Layout& S, const void* const* sp, const Layout& D, v
     bool empty = false;
     rc = remap_plan_args(S, sp, D, dp, n, R, &a, &empty);
     if (rc || empty) break;
-    if (2 * a.in_bytes + a.out_bytes > 24 * 1024) continue;   // keep the batched kernel's buffers small
+    if (2 * a.in_bytes + a.out_bytes > kWarpBufferBudget / kWarps && R > 32) continue;   // keep 8 warps busy
     adha_tune_override(R);
     for (int w = 0; w < 2 && !rc; ++w) rc = remap_layouts(S, sp, D, dp, n, stream, nullptr);
     cudaEventRecord(e0, (cudaStream_t)stream);
@@ -280,8 +225,7 @@ int adha_batched_create(int32_t n_arrays, const adha_remap_desc* descs, int32_t 
   if (!b) return fail(ADHA_ENOMEM, "host allocation failed");
   std::vector<BatchHeader> headers;
   std::vector<GroupRef> groups;
-  std::vector<uint32_t> slots;
-  std::vector<int32_t> nslots;
+  std::vector<Move> moves;
   std::vector<int64_t> prefix;
   int64_t blocks = 0;
   for (int k = 0; k < n_arrays; ++k) {
@@ -317,25 +261,26 @@ int adha_batched_create(int32_t n_arrays, const adha_remap_desc* descs, int32_t 
       h.R = a.R;
       h.n_full = a.n_chunks;
       h.n_chunks = a.n_chunks + (a.n % a.R ? 1 : 0);
-      h.unit = a.unit;
       h.n_src = a.n_src;
       h.n_dst = a.n_dst;
       h.in_bytes = a.in_bytes;
       h.out_bytes = a.out_bytes;
-      h.n_elems = a.n_elems;
-      h.order = a.order;
+      h.n_moves = a.n_moves;
+      for (int c = 0; c < 3; ++c) {
+        h.cls_count[c] = a.cls_count[c];
+        h.cls_order[c] = a.cls_order[c];
+      }
       h.group0 = (int32_t)groups.size();
-      h.slot0 = (int32_t)slots.size();
-      h.nslot0 = (int32_t)nslots.size();
-      h.n_slots = a.n_slots;
+      h.move0 = (int32_t)moves.size();
+      h.warp_bytes = 2 * a.in_bytes + a.out_bytes;
+      h.warps = std::max(1, std::min(kWarps, kWarpBufferBudget / h.warp_bytes));
+      b->warp_budget = std::max(b->warp_budget, h.warps * h.warp_bytes);
       for (int g = 0; g < a.n_src; ++g) groups.push_back(a.src[g]);
       for (int g = 0; g < a.n_dst; ++g) groups.push_back(a.dst[g]);
-      for (int g = 0; g < a.n_dst; ++g) nslots.push_back(a.d_nslot[g]);
-      slots.insert(slots.end(), a.slot, a.slot + a.n_slots);
-      blocks += (h.n_chunks + kBlockChunks - 1) / kBlockChunks;
-      b->max_elems = std::max(b->max_elems, a.n_elems);
-      b->max_in = std::max(b->max_in, a.in_bytes);
-      b->max_out = std::max(b->max_out, a.out_bytes);
+      moves.insert(moves.end(), a.move, a.move + a.n_moves);
+      const int64_t per_block = (int64_t)kBlockChunksPerWarp * h.warps;
+      blocks += (h.n_chunks + per_block - 1) / per_block;
+      b->max_entries = std::max(b->max_entries, a.R * a.n_moves);
       double moved = 0;
       for (int g = 0; g < D.n_groups; ++g) {
         bool alias = false;
@@ -352,17 +297,16 @@ int adha_batched_create(int32_t n_arrays, const adha_remap_desc* descs, int32_t 
   b->total_blocks = blocks;
   b->off_headers = al256(sizeof(unsigned long long));
   b->off_groups = b->off_headers + al256(headers.size() * sizeof(BatchHeader));
-  b->off_slots = b->off_groups + al256(std::max<size_t>(1, groups.size()) * sizeof(GroupRef));
-  b->off_nslots = b->off_slots + al256(std::max<size_t>(1, slots.size()) * sizeof(uint32_t));
-  b->off_prefix = b->off_nslots + al256(std::max<size_t>(1, nslots.size()) * sizeof(int32_t));
+  b->off_moves = b->off_groups + al256(std::max<size_t>(1, groups.size()) * sizeof(GroupRef));
+  b->off_prefix = b->off_moves + al256(std::max<size_t>(1, moves.size()) * sizeof(Move));
   b->image.assign(b->off_prefix + al256(prefix.size() * sizeof(int64_t)), 0);
   std::memcpy(b->image.data() + b->off_headers, headers.data(), headers.size() * sizeof(BatchHeader));
   if (!groups.empty()) std::memcpy(b->image.data() + b->off_groups, groups.data(), groups.size() * sizeof(GroupRef));
-  if (!slots.empty()) std::memcpy(b->image.data() + b->off_slots, slots.data(), slots.size() * sizeof(uint32_t));
-  if (!nslots.empty()) std::memcpy(b->image.data() + b->off_nslots, nslots.data(), nslots.size() * sizeof(int32_t));
+  if (!moves.empty()) std::memcpy(b->image.data() + b->off_moves, moves.data(), moves.size() * sizeof(Move));
   std::memcpy(b->image.data() + b->off_prefix, prefix.data(), prefix.size() * sizeof(int64_t));
-  b->smem = (size_t)2 * kMaxGroups * sizeof(GroupRef) + kMaxGroups * 4 + kMaxSlots * 4 + (size_t)b->max_elems * 4 +
-            (size_t)kWarps * (2 * b->max_in + b->max_out);
+  b->max_entries = (b->max_entries + 3) / 4 * 4;
+  b->smem = (size_t)2 * kMaxGroups * sizeof(GroupRef) + kMaxMoves * sizeof(Move) + (size_t)b->max_entries * 4 +
+            (size_t)b->warp_budget;
   if (b->smem > (size_t)kSmemLimit - 1024) {
     const size_t need = b->smem;
     delete b;

@@ -272,15 +272,14 @@ static int finish_grid(int64_t n_chunks, int blocks, int* grid) {
   return 0;
 }
 
-// Shared-memory wavefronts of one chunk's element moves in schedule order `order` (the kernel's
-// table): per warp step of 32 elements, the largest number of distinct 4-byte words that fall
-// in one bank, on the read side plus the write side.
-static int step_wavefronts(const uint32_t* bytes, int cnt, int u) {
+// Shared-memory wavefronts of one warp step (32 schedule entries of one move class): the
+// largest number of distinct 4-byte words that fall in one bank, for the given byte addresses.
+static int step_wavefronts(const uint32_t* bytes, int cnt, int width) {
   uint32_t words[64];
   int m = 0;
   for (int l = 0; l < cnt; ++l) {
     if (bytes[l] == 0xFFFFFFFFu) continue;
-    for (int w = 0; w < (u + 3) / 4; ++w) words[m++] = bytes[l] / 4 + w;
+    for (int w = 0; w < (width + 3) / 4; ++w) words[m++] = bytes[l] / 4 + w;
   }
   std::sort(words, words + m);
   m = (int)(std::unique(words, words + m) - words);
@@ -290,53 +289,63 @@ static int step_wavefronts(const uint32_t* bytes, int cnt, int u) {
   return worst;
 }
 
-static long remap_conflict_cost(const RemapArgs& a, int order) {
-  const int u = a.unit;
+// Wavefronts of one chunk's moves of class c under schedule order `order` (as the kernel's
+// schedule_entry lays them out), read side plus write side.
+static long class_conflict_cost(const RemapArgs& a, int c, int order) {
+  int first = 0;
+  for (int k = 0; k < c; ++k) first += a.cls_count[k];
+  const int cnt = a.cls_count[c], n = a.R * cnt, width = 8 >> c;
   long cost = 0;
   uint32_t rd[32], wr[32];
-  int dd = 0, ee = 0;
-  for (int t = 0; t < a.n_elems; t += 32) {
-    const int cnt = std::min(32, a.n_elems - t);
-    for (int l = 0; l < cnt; ++l) {
-      const int tt = t + l;
-      while (tt >= ee + a.R * a.d_nslot[dd]) ee += a.R * a.d_nslot[dd++];
-      const int S = a.d_nslot[dd];
+  for (int t = 0; t < n; t += 32) {
+    const int w = std::min(32, n - t);
+    for (int l = 0; l < w; ++l) {
+      const int u = t + l;
       int r, k;
       if (order == 0) {
-        r = (tt - ee) / S;
-        k = (tt - ee) - r * S;
+        r = u / cnt;
+        k = u - r * cnt;
       } else {
-        k = (tt - ee) / a.R;
-        r = (tt - ee) - k * a.R;
+        k = u / a.R;
+        r = u - k * a.R;
       }
-      const uint32_t code = a.slot[a.d_slot0[dd] + k];
-      rd[l] = code == kPadSlot ? 0xFFFFFFFFu
-                               : (uint32_t)(a.src[code >> 16].start + r * a.src[code >> 16].stride + (int)(code & 0xFFFFu));
-      wr[l] = (uint32_t)((ee + r * S + k) * u);
+      const Move& m = a.move[first + k];
+      rd[l] = m.src_group < 0 ? 0xFFFFFFFFu
+                              : (uint32_t)(a.src[m.src_group].start + r * a.src[m.src_group].stride + m.src_off);
+      wr[l] = (uint32_t)(a.dst[m.dst_group].start + r * a.dst[m.dst_group].stride + m.dst_off);
     }
-    cost += step_wavefronts(rd, cnt, u) + step_wavefronts(wr, cnt, u);
+    cost += step_wavefronts(rd, w, width) + step_wavefronts(wr, w, width);
   }
   return cost;
 }
 
-// The schedule order depends only on the two layouts' moved groups and the chunk size.
+// The schedule orders depend only on the moves, strides and chunk size: cached per shape.
 static std::mutex g_order_mu;
-static std::map<std::vector<int32_t>, int> g_order_cache;
+static std::map<std::vector<int32_t>, std::vector<int32_t>> g_order_cache;
 
-static int choose_order(const RemapArgs& a) {
-  std::vector<int32_t> key = {a.R, a.unit, a.n_src, a.n_dst};
-  for (int k = 0; k < a.n_src; ++k) key.push_back(a.src[k].stride);
-  for (int k = 0; k < a.n_dst; ++k) key.push_back(a.d_nslot[k]);
-  key.insert(key.end(), a.slot, a.slot + a.n_slots);
+static void choose_orders(RemapArgs* a) {
+  std::vector<int32_t> key = {a->R, a->n_src, a->n_dst, a->n_moves};
+  for (int k = 0; k < a->n_src; ++k) key.push_back(a->src[k].stride);
+  for (int k = 0; k < a->n_dst; ++k) key.push_back(a->dst[k].stride);
+  for (int k = 0; k < a->n_moves; ++k) {
+    const Move& m = a->move[k];
+    key.insert(key.end(), {m.dst_group, m.dst_off, m.src_group, m.src_off});
+  }
+  for (int c = 0; c < 3; ++c) key.push_back(a->cls_count[c]);
   {
     std::lock_guard<std::mutex> lk(g_order_mu);
     auto it = g_order_cache.find(key);
-    if (it != g_order_cache.end()) return it->second;
+    if (it != g_order_cache.end()) {
+      for (int c = 0; c < 3; ++c) a->cls_order[c] = it->second[c];
+      return;
+    }
   }
-  const int order = remap_conflict_cost(a, 0) <= remap_conflict_cost(a, 1) ? 0 : 1;
+  std::vector<int32_t> orders(3, 0);
+  for (int c = 0; c < 3; ++c)
+    if (a->cls_count[c]) orders[c] = class_conflict_cost(*a, c, 0) <= class_conflict_cost(*a, c, 1) ? 0 : 1;
+  for (int c = 0; c < 3; ++c) a->cls_order[c] = orders[c];
   std::lock_guard<std::mutex> lk(g_order_mu);
-  g_order_cache[key] = order;
-  return order;
+  g_order_cache[key] = orders;
 }
 
 // Occupancy per (kernel, shared bytes), queried once.
@@ -352,7 +361,7 @@ static int cached_occupancy(int kind, size_t smem, int* blocks) {
       return 0;
     }
   }
-  const int rc = kind < 100 ? remap_occupancy(kind, smem, blocks) : section_occupancy(kind - 100, smem, blocks);
+  const int rc = kind < 100 ? remap_occupancy(0, smem, blocks) : section_occupancy(kind - 100, smem, blocks);
   if (rc) return rc;
   std::lock_guard<std::mutex> lk(g_occ_mu);
   g_occ_cache[{kind, smem}] = *blocks;
@@ -373,12 +382,8 @@ static int plan_remap(const Layout& S, const void* const* src_ptrs, const Layout
   plan->empty = build.empty() || n == 0;
   if (plan->empty) return 0;
   std::set<int> need_set;
-  int unit = 8;
   for (int d : build)
-    for (int f : D.groups[d]) {
-      need_set.insert(S.group_of[f]);
-      unit = std::min(unit, dtype_size(D.dtype[f]));
-    }
+    for (int f : D.groups[d]) need_set.insert(S.group_of[f]);
   std::vector<int> need(need_set.begin(), need_set.end());
   for (size_t x = 0; x < build.size(); ++x) {
     const size_t nd = (size_t)n * D.stride[build[x]];
@@ -389,19 +394,48 @@ static int plan_remap(const Layout& S, const void* const* src_ptrs, const Layout
       if (overlap(dst_ptrs[build[x]], nd, dst_ptrs[build[y]], (size_t)n * D.stride[build[y]]))
         return fail(ADHA_EINVAL, "destination groups %d and %d overlap", build[x], build[y]);
   }
-  int src_rec = 0, dst_rec = 0, n_slots = 0;
-  for (int j : need) src_rec += S.stride[j];
-  for (int d : build) {
-    dst_rec += D.stride[d];
-    n_slots += D.stride[d] / unit;
+  // moves: every field of every built destination struct, and its padding in aligned pieces
+  std::vector<Move> moves;
+  std::vector<int> widths;
+  for (size_t k = 0; k < build.size(); ++k) {
+    const int d = build[k];
+    std::vector<std::pair<int, int>> spans;   // (offset, size) of the fields
+    for (int f : D.groups[d]) {
+      const int k_src = (int)(std::lower_bound(need.begin(), need.end(), S.group_of[f]) - need.begin());
+      moves.push_back(Move{(int16_t)k, (int16_t)D.offset_of[f], (int16_t)k_src, (int16_t)S.offset_of[f]});
+      widths.push_back(dtype_size(D.dtype[f]));
+      spans.push_back({D.offset_of[f], dtype_size(D.dtype[f])});
+    }
+    std::sort(spans.begin(), spans.end());
+    spans.push_back({D.stride[d], 0});
+    int pos = 0;
+    for (const auto& sp : spans) {
+      while (pos < sp.first) {   // zero padding, in the widest aligned pieces
+        int w = 8;
+        while (w > 2 && (pos % w != 0 || pos + w > sp.first)) w /= 2;
+        moves.push_back(Move{(int16_t)k, (int16_t)pos, (int16_t)-1, (int16_t)0});
+        widths.push_back(w);
+        pos += w;
+      }
+      pos = sp.first + sp.second;
+    }
   }
-  if (n_slots > kMaxSlots) return fail(ADHA_EINVAL, "destination records too wide (%d slots)", n_slots);
+  if ((int)moves.size() > kMaxMoves) return fail(ADHA_EINVAL, "destination records too wide (%zu moves)", moves.size());
+  std::vector<size_t> idx(moves.size());
+  for (size_t k = 0; k < idx.size(); ++k) idx[k] = k;
+  std::stable_sort(idx.begin(), idx.end(), [&](size_t x, size_t y) {
+    if (widths[x] != widths[y]) return widths[x] > widths[y];
+    if (moves[x].dst_group != moves[y].dst_group) return moves[x].dst_group < moves[y].dst_group;
+    return moves[x].dst_off < moves[y].dst_off;
+  });
+  int src_rec = 0, dst_rec = 0;
+  for (int j : need) src_rec += S.stride[j];
+  for (int d : build) dst_rec += D.stride[d];
   int R = t_tile_override ? t_tile_override : pick_chunk(std::max(src_rec, dst_rec), 2560, 512);
   for (;;) {
     a.n = n;
     a.R = R;
     a.n_chunks = n / R;
-    a.unit = unit;
     a.n_src = (int)need.size();
     a.n_dst = (int)build.size();
     int off = 0;
@@ -413,34 +447,27 @@ static int plan_remap(const Layout& S, const void* const* src_ptrs, const Layout
     }
     a.in_bytes = off;
     off = 0;
-    int slot0 = 0;
     for (int k = 0; k < a.n_dst; ++k) {
-      const int d = build[k];
-      a.dst[k].ptr = static_cast<const uint8_t*>(dst_ptrs[d]);
-      a.dst[k].stride = D.stride[d];
+      a.dst[k].ptr = static_cast<const uint8_t*>(dst_ptrs[build[k]]);
+      a.dst[k].stride = D.stride[build[k]];
       a.dst[k].start = off;
       off += R * a.dst[k].stride;
-      a.d_nslot[k] = D.stride[d] / unit;
-      a.d_slot0[k] = slot0;
-      for (int s = 0; s < a.d_nslot[k]; ++s) a.slot[slot0 + s] = kPadSlot;
-      for (int f : D.groups[d]) {
-        const int k_src = (int)(std::lower_bound(need.begin(), need.end(), S.group_of[f]) - need.begin());
-        for (int b = 0; b < dtype_size(D.dtype[f]); b += unit)
-          a.slot[slot0 + (D.offset_of[f] + b) / unit] = ((uint32_t)k_src << 16) | (uint32_t)(S.offset_of[f] + b);
-      }
-      slot0 += a.d_nslot[k];
     }
     a.out_bytes = off;
-    a.n_slots = slot0;
-    a.n_elems = a.out_bytes / unit;
+    a.n_moves = (int)moves.size();
+    for (int c = 0; c < 3; ++c) a.cls_count[c] = 0;
+    for (size_t k = 0; k < idx.size(); ++k) {
+      a.move[k] = moves[idx[k]];
+      a.cls_count[widths[idx[k]] == 8 ? 0 : widths[idx[k]] == 4 ? 1 : 2]++;
+    }
     plan->smem = remap_smem_bytes(a);
-    if (plan->smem <= (size_t)kSmemLimit && a.in_bytes / unit < 0xFFFF && a.n_elems <= 0x10000) break;
+    if (plan->smem <= (size_t)kSmemLimit && a.in_bytes < 0xFFFF && a.out_bytes <= 0xFFFF) break;
     if (R <= 32) return fail(ADHA_EINVAL, "records too wide for a 32-record chunk (%zu bytes smem)", plan->smem);
     R = std::max(32, R / 2 / 32 * 32);
   }
-  a.order = choose_order(a);
+  choose_orders(&a);
   int blocks = 0;
-  if (int rc = cached_occupancy(unit, plan->smem, &blocks)) return rc;
+  if (int rc = cached_occupancy(0, plan->smem, &blocks)) return rc;
   return finish_grid(a.n_chunks, blocks, &plan->grid);
 }
 

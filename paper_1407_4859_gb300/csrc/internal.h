@@ -16,9 +16,8 @@ namespace adha {
 
 constexpr int kMaxFields = ADHA_MAX_FIELDS;
 constexpr int kMaxGroups = ADHA_MAX_FIELDS;
-constexpr int kMaxSlots = 512;         // u-sized slots over all built destination records
-constexpr int kMaxStride = 4095;       // bytes; fits the 12-bit stride field of a slot code
-constexpr uint32_t kPadSlot = 0xFFFFFFFFu;
+constexpr int kMaxMoves = 256;         // moves (fields + padding pieces) over all built destination records
+constexpr int kMaxStride = 4095;       // bytes per struct
 constexpr int kThreads = 256;          // threads per CTA of the staged kernels (8 warps)
 constexpr int kSmemLimit = 227 * 1024; // dynamic shared memory one CTA may use
 
@@ -63,8 +62,19 @@ struct GroupRef {
   int32_t start;          // slice offset within a chunk buffer
 };
 
+// One field of a destination record (or one aligned zero piece of its padding) and where its
+// bytes come from.  Moves are 8, 4 or 2 bytes wide: a field moves whole, whatever the other
+// fields' sizes.
+struct Move {
+  int16_t dst_group;    // index into RemapArgs::dst
+  int16_t dst_off;      // byte offset in the destination struct
+  int16_t src_group;    // index into RemapArgs::src; -1 for padding
+  int16_t src_off;      // byte offset in the source struct
+};
+
 // Remap of one record array: every built destination group is assembled from the source groups'
-// slices, one u-sized slot at a time.
+// slices, one move per lane per step; the moves are sorted by width into three classes
+// (8, 4 and 2 bytes), each with its own schedule order.
 struct RemapArgs {
   int64_t n;              // records
   int64_t n_chunks;       // whole chunks of R records
@@ -72,17 +82,12 @@ struct RemapArgs {
   int32_t n_src, n_dst;
   int32_t in_bytes;       // one chunk of the source slices
   int32_t out_bytes;      // one chunk of the destination slices
-  int32_t n_elems;        // u-sized elements in one destination chunk (R * total slots)
-  int32_t n_slots;
-  int32_t unit;
-  int32_t order;          // element schedule: 0 destination-major, 1 record-major (lane = record)
+  int32_t n_moves;
+  int32_t cls_count[3];   // moves of 8, 4, 2 bytes, in that order in `move`
+  int32_t cls_order[3];   // per class: 0 destination-major, 1 record-major (lane = record)
   GroupRef src[kMaxGroups];
   GroupRef dst[kMaxGroups];
-  int32_t d_nslot[kMaxGroups];
-  int32_t d_slot0[kMaxGroups];
-  // per destination slot: (source group index << 16) | byte offset in the source struct;
-  // kPadSlot for padding bytes
-  uint32_t slot[kMaxSlots];
+  Move move[kMaxMoves];
 };
 
 struct FieldRef {

@@ -6,32 +6,33 @@
 //   1. the warp copies the chunk's slice of every source group into its own shared buffer with
 //      16-byte cp.async (coalesced: lane l moves bytes 16l, 16l+512, ...), one chunk ahead of
 //      the one it works on (double buffering);
-//   2. it assembles the destination slices in a second buffer, one u-sized element per lane
-//      per step (u = the smallest moved field size), through a schedule table built once per CTA
-//      that pairs every destination element of a chunk with its source element: this is the
-//      tile transpose between the source and destination record strides.  The host picks the
-//      order of the pairs (destination-major or record-major) with fewer shared-memory bank
-//      conflicts for the two strides;
+//   2. it assembles the destination slices in a second buffer, one move per lane per step: a
+//      move is one field of one destination record (8, 4 or 2 bytes, whole) or an aligned piece
+//      of its zero padding, taken from a schedule table built once per CTA.  This is the tile
+//      transpose between the source and destination record strides; the host picks, per move
+//      width, the schedule order (destination-major or record-major) with fewer shared-memory
+//      bank conflicts;
 //   3. it writes the destination slices back with 16-byte stores.
 // Global traffic is one contiguous read stream per source group and one write stream per
-// destination group.  The ragged tail (fewer than R records) goes element by element through
-// the warp that would own the next chunk.
+// destination group.  The ragged tail (fewer than R records) goes move by move through the warp
+// that would own the next chunk.
 #include <cuda_runtime.h>
 
 #include "internal.h"
 #include "ptx.cuh"
+#include "remap_common.cuh"
 
 namespace adha {
 
 __device__ __forceinline__ int align16(int x) { return (x + 15) & ~15; }
 
-template <typename U>
 __global__ void __launch_bounds__(kThreads) remap_kernel(const __grid_constant__ RemapArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   GroupRef* tin = reinterpret_cast<GroupRef*>(smem);
   GroupRef* tout = tin + a.n_src;
+  const int n_entries = a.R * a.n_moves;
   uint32_t* sched = reinterpret_cast<uint32_t*>(smem + align16((a.n_src + a.n_dst) * (int)sizeof(GroupRef)));
-  uint8_t* wbase = reinterpret_cast<uint8_t*>(sched) + align16(a.n_elems * 4);
+  uint8_t* wbase = reinterpret_cast<uint8_t*>(sched) + align16(n_entries * 4);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   uint8_t* buf0 = wbase + (size_t)warp * (2 * a.in_bytes + a.out_bytes);
   uint8_t* buf1 = buf0 + a.in_bytes;
@@ -39,30 +40,8 @@ __global__ void __launch_bounds__(kThreads) remap_kernel(const __grid_constant__
 
   for (int k = tid; k < a.n_src; k += kThreads) tin[k] = a.src[k];
   for (int k = tid; k < a.n_dst; k += kThreads) tout[k] = a.dst[k];
-  // schedule table: entry t = (source element << 16 | destination element) of the t-th element
-  // the warp moves; lanes take consecutive entries.  Order 0 walks destination elements in
-  // order (conflict-free writes); order 1 walks, per destination slot, 32 consecutive records
-  // (conflict-free reads from narrow source slices).
-  for (int t = tid; t < a.n_elems; t += kThreads) {
-    int d = 0, e0 = 0;
-    while (t >= e0 + a.R * a.d_nslot[d]) e0 += a.R * a.d_nslot[d++];
-    const int S = a.d_nslot[d];
-    int r, k;
-    if (a.order == 0) {
-      r = (t - e0) / S;
-      k = (t - e0) - r * S;
-    } else {
-      k = (t - e0) / a.R;
-      r = (t - e0) - k * a.R;
-    }
-    const uint32_t code = a.slot[a.d_slot0[d] + k];
-    uint32_t x = 0xFFFFu;
-    if (code != kPadSlot) {
-      const int j = (int)(code >> 16);
-      x = (uint32_t)((a.src[j].start + r * a.src[j].stride + (int)(code & 0xFFFFu)) / (int)sizeof(U));
-    }
-    sched[t] = x | ((uint32_t)(e0 + r * S + k) << 16);
-  }
+  for (int t = tid; t < n_entries; t += kThreads)
+    sched[t] = schedule_entry(t, a.R, a.cls_count, a.cls_order, a.move, a.src, a.dst);
   __syncthreads();
 
   const int64_t W = (int64_t)gridDim.x * kWarps;
@@ -84,14 +63,7 @@ __global__ void __launch_bounds__(kThreads) remap_kernel(const __grid_constant__
     cp_async_commit();
     cp_async_wait<1>();
     __syncwarp();
-    const U* src = reinterpret_cast<const U*>(cur);
-    U* dst = reinterpret_cast<U*>(outb);
-#pragma unroll 4
-    for (int t = lane; t < a.n_elems; t += 32) {
-      const uint32_t p = sched[t];
-      const uint32_t x = p & 0xFFFFu;
-      dst[p >> 16] = x != 0xFFFFu ? src[x] : U(0);
-    }
+    move_chunk(sched, a.R, a.cls_count, cur, outb, lane);
     __syncwarp();
     int g = 0;
     for (int p = lane * 16; p < a.out_bytes; p += 512) {
@@ -105,63 +77,30 @@ __global__ void __launch_bounds__(kThreads) remap_kernel(const __grid_constant__
 
   // ragged tail: the warp whose next chunk would be n_chunks
   const int64_t t0 = a.n_chunks * R;
-  if (c == a.n_chunks && t0 < a.n) {
-    const int Tt = (int)(a.n - t0);
-    for (int d = 0; d < a.n_dst; ++d) {
-      const int S = a.d_nslot[d];
-      for (int e = lane; e < Tt * S; e += 32) {
-        const int r = e / S, k = e - r * S;
-        const uint32_t code = a.slot[a.d_slot0[d] + k];
-        U v = U(0);
-        if (code != kPadSlot) {
-          const GroupRef& sg = tin[code >> 16];
-          v = *reinterpret_cast<const U*>(sg.ptr + (t0 + r) * sg.stride + (code & 0xFFFFu));
-        }
-        *reinterpret_cast<U*>(const_cast<uint8_t*>(tout[d].ptr) + (t0 + r) * tout[d].stride + k * (int)sizeof(U)) = v;
-      }
-    }
-  }
+  if (c == a.n_chunks && t0 < a.n) tail_moves(t0, a.n, a.n_moves, a.cls_count, a.move, tin, tout, lane);
 }
 
 size_t remap_smem_bytes(const RemapArgs& a) {
   auto al = [](size_t x) { return (x + 15) / 16 * 16; };
-  return al((size_t)(a.n_src + a.n_dst) * sizeof(GroupRef)) + al((size_t)a.n_elems * 4) +
+  return al((size_t)(a.n_src + a.n_dst) * sizeof(GroupRef)) + al((size_t)a.R * a.n_moves * 4) +
          (size_t)kWarps * (2 * (size_t)a.in_bytes + a.out_bytes);
 }
 
-template <typename U>
-static int launch_t(const RemapArgs& a, int grid, size_t smem, void* stream) {
-  cudaError_t e = cudaFuncSetAttribute(remap_kernel<U>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+int launch_remap(const RemapArgs& a, int grid, size_t smem, void* stream) {
+  cudaError_t e = cudaFuncSetAttribute(remap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(remap)");
-  remap_kernel<U><<<grid, kThreads, smem, (cudaStream_t)stream>>>(a);
+  remap_kernel<<<grid, kThreads, smem, (cudaStream_t)stream>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "remap kernel launch");
   return 0;
 }
 
-int launch_remap(const RemapArgs& a, int grid, size_t smem, void* stream) {
-  switch (a.unit) {
-    case 2: return launch_t<uint16_t>(a, grid, smem, stream);
-    case 4: return launch_t<uint32_t>(a, grid, smem, stream);
-    default: return launch_t<unsigned long long>(a, grid, smem, stream);
-  }
-}
-
-template <typename U>
-static int occ_t(size_t smem, int* blocks) {
-  cudaError_t e = cudaFuncSetAttribute(remap_kernel<U>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+int remap_occupancy(int, size_t smem, int* blocks) {
+  cudaError_t e = cudaFuncSetAttribute(remap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(remap)");
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, remap_kernel<U>, kThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, remap_kernel, kThreads, smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(remap)");
   return 0;
-}
-
-int remap_occupancy(int unit, size_t smem, int* blocks) {
-  switch (unit) {
-    case 2: return occ_t<uint16_t>(smem, blocks);
-    case 4: return occ_t<uint32_t>(smem, blocks);
-    default: return occ_t<unsigned long long>(smem, blocks);
-  }
 }
 
 }  // namespace adha
