@@ -70,6 +70,21 @@ def remap_bytes(wl, plan_layouts, in_layout):
     return total
 
 
+def reduce_max_ms(dist, ms, device="cuda"):
+    """The slowest rank's time (the job's time under weak scaling); ms unchanged without dist."""
+    if not dist:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(world, bytes_per_step, steps, ms):
+    """Whole-job GB/s: every rank processed its own batch of bytes_per_step per step in ms (max)."""
+    return world * bytes_per_step * steps / (ms * 1e6)
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -303,12 +318,8 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * bytes_per_step * args.steps / (ms * 1e6)
+    ms = reduce_max_ms(dist, e0.elapsed_time(e1))
+    value = weak_scaling_value(world, bytes_per_step, args.steps, ms)
 
     # roofline of the dominant kernel (largest share of the timed region)
     groups = {}
@@ -444,14 +455,6 @@ def _timed(torch, stream, steps, fn):
     return e0.elapsed_time(e1)
 
 
-def _max_ms(torch, dist, ms):
-    if not dist:
-        return ms
-    t = torch.tensor([ms], device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
-
-
 def _roofline(recs):
     groups = {}
     for r in recs:
@@ -516,8 +519,8 @@ def batched_bench(args, rank, world, local, dist):
     torch.cuda.nvtx.range_pop()
     recs = P.adha_profile_stop(4 * args.steps + 16)
     clk = clocks.stop()
-    ms = _max_ms(torch, dist, ms)
-    value = world * bytes_per * args.steps / (ms * 1e6)
+    ms = reduce_max_ms(dist, ms)
+    value = weak_scaling_value(world, bytes_per, args.steps, ms)
     roof, kernels = _roofline(recs)
 
     def per_array():
@@ -645,12 +648,12 @@ def differentiable_bench(args, rank, world, local, dist):
     torch.cuda.nvtx.range_pop()
     recs = P.adha_profile_stop(512 * args.steps + 64)
     clk = clocks.stop()
-    ms = _max_ms(torch, dist, ms)
+    ms = reduce_max_ms(dist, ms)
     fwd = sum(r["bytes"] for r in recs if r["kind"] in ("section", "remap")) / args.steps
     bwd = sum(r["bytes"] for r in recs if r["kind"] == "section_backward") / args.steps
     # program work only (sections and their adjoints), like the stress bench's value
     work = sum(r["bytes"] for r in recs if r["kind"] in ("section", "section_backward")) / args.steps
-    value = world * work * args.steps / (ms * 1e6)
+    value = weak_scaling_value(world, work, args.steps, ms)
     roof, kernels = _roofline(recs)
     k2 = max(3, args.steps // 2)
     t_aos = _timed(torch, stream, k2, lambda: run([AOS] * len(wl.sections))) / k2
