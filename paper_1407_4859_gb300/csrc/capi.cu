@@ -10,6 +10,7 @@
 #include <set>
 
 #include "internal.h"
+#include "remap_common.cuh"
 
 namespace adha {
 
@@ -302,13 +303,7 @@ static long class_conflict_cost(const RemapArgs& a, int c, int order) {
     for (int l = 0; l < w; ++l) {
       const int u = t + l;
       int r, k;
-      if (order == 0) {
-        r = u / cnt;
-        k = u - r * cnt;
-      } else {
-        k = u / a.R;
-        r = u - k * a.R;
-      }
+      schedule_pair(u, a.R, cnt, order, &r, &k);
       const Move& m = a.move[first + k];
       rd[l] = m.src_group < 0 ? 0xFFFFFFFFu
                               : (uint32_t)(a.src[m.src_group].start + r * a.src[m.src_group].stride + m.src_off);
@@ -341,8 +336,17 @@ static void choose_orders(RemapArgs* a) {
     }
   }
   std::vector<int32_t> orders(3, 0);
-  for (int c = 0; c < 3; ++c)
-    if (a->cls_count[c]) orders[c] = class_conflict_cost(*a, c, 0) <= class_conflict_cost(*a, c, 1) ? 0 : 1;
+  for (int c = 0; c < 3; ++c) {
+    if (!a->cls_count[c]) continue;
+    long best = -1;
+    for (int o = 0; o <= 6; ++o) {   // destination-major, record-major, skewed record-major (5 skews)
+      const long cost = class_conflict_cost(*a, c, o);
+      if (best < 0 || cost < best) {
+        best = cost;
+        orders[c] = o;
+      }
+    }
+  }
   for (int c = 0; c < 3; ++c) a->cls_order[c] = orders[c];
   std::lock_guard<std::mutex> lk(g_order_mu);
   g_order_cache[key] = orders;

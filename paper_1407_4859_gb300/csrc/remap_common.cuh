@@ -8,23 +8,37 @@
 
 namespace adha {
 
+// (record, move) of entry u of a class of cnt moves in a chunk of R records under `order`:
+//   0: destination-major (record by record, its moves in turn);
+//   1: record-major (per move, 32 consecutive records per warp step);
+//   2 + s (s = 0..4): skewed record-major: warp step j covers records 32*(j / cnt) + lane, lane l
+//      taking move (j + l / 2^s) mod cnt, which spreads a strided read over more banks while the
+//      records (and so the writes of a one-field slice) stay consecutive.
+__host__ __device__ __forceinline__ void schedule_pair(int u, int R, int cnt, int order, int* r, int* k) {
+  if (order == 0) {
+    *r = u / cnt;
+    *k = u - *r * cnt;
+  } else if (order == 1) {
+    *k = u / R;
+    *r = u - *k * R;
+  } else {
+    const int step = u >> 5, lane = u & 31;
+    const int block = step / cnt, j = step - block * cnt;
+    *r = 32 * block + lane;
+    *k = (j + (lane >> (order - 2))) % cnt;
+  }
+}
+
 // Schedule entry t of a chunk (R records, n_moves moves sorted into classes of 8/4/2 bytes):
 // (source byte in the chunk buffer | destination byte in the output buffer << 16), source
-// 0xFFFF for padding.  Within class c, order 0 walks destination records then their moves,
-// order 1 walks moves then 32 consecutive records per warp step.
+// 0xFFFF for padding.
 __device__ __forceinline__ uint32_t schedule_entry(int t, int R, const int32_t* cls_count, const int32_t* cls_order,
                                                    const Move* moves, const GroupRef* src, const GroupRef* dst) {
   int c = 0, first = 0;
   while (t >= R * (first + cls_count[c])) first += cls_count[c++];
   const int u = t - R * first, cnt = cls_count[c];
   int r, k;
-  if (cls_order[c] == 0) {
-    r = u / cnt;
-    k = u - r * cnt;
-  } else {
-    k = u / R;
-    r = u - k * R;
-  }
+  schedule_pair(u, R, cnt, cls_order[c], &r, &k);
   const Move m = moves[first + k];
   const uint32_t s = m.src_group < 0 ? 0xFFFFu : (uint32_t)(src[m.src_group].start + r * src[m.src_group].stride + m.src_off);
   const uint32_t d = (uint32_t)(dst[m.dst_group].start + r * dst[m.dst_group].stride + m.dst_off);
