@@ -334,7 +334,8 @@ typedef struct adha_batched adha_batched;
  * batching form of the paper's remap, Section 2): validates every array (rules
  * of adha_remap), plans each one (chunk size, element schedule) and lays out
  * the descriptors the kernel reads.  With ADHA_BATCHED_AUTOTUNE each array's
- * chunk size is the fastest of 32..256 records, timed with the single-array
+ * chunk size (32..256 records) and store mode for one-field destination groups
+ * (see adha_tune_remap_direct) are the fastest pair, timed with the single-array
  * kernel on the array's own buffers (their contents are overwritten with the
  * remap's result).  *out is freed with adha_batched_destroy.
  */
@@ -390,9 +391,10 @@ void adha_batched_destroy(adha_batched* b);
 int adha_remap_batched_noalloc(int32_t n_arrays, const adha_remap_desc* descs, adha_stream stream);
 
 /*
- * Records per warp chunk (a multiple of 32 up to 1024; 0 = automatic) that the
- * remap and section kernels launched later by the calling thread use.  The
- * autotuner sets it while it times candidates.  Host only.
+ * Records per warp chunk (a multiple of 8 up to 1024; 0 = automatic) that the
+ * remap kernels launched later by the calling thread use; section kernels take
+ * it rounded to 32, 64 or 128.  The autotuner sets it while it times
+ * candidates.  Host only.
  */
 int adha_tune_override(int32_t chunk_records);
 
@@ -404,6 +406,14 @@ int adha_tune_override(int32_t chunk_records);
  * 1 = always field by field, 2 = always whole.  Host only.
  */
 int adha_tune_writeback(int32_t mode);
+
+/*
+ * How remaps launched later by the calling thread store one-field destination
+ * groups: 0 = through the warp's output buffer with 16-byte stores (default),
+ * 1 = straight from the move loop to global memory (less shared memory, more
+ * store instructions).  The batched autotuner tries both per array.  Host only.
+ */
+int adha_tune_remap_direct(int32_t mode);
 
 /* Empties the library's tuning cache (process-wide).  Host only. */
 int adha_tune_clear(void);

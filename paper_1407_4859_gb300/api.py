@@ -134,6 +134,10 @@ def adha_tune_writeback(mode=0):
     check(_lib.load().adha_tune_writeback(int(mode)), "adha_tune_writeback")
 
 
+def adha_tune_remap_direct(mode=0):
+    check(_lib.load().adha_tune_remap_direct(int(mode)), "adha_tune_remap_direct")
+
+
 def adha_tune_clear():
     check(_lib.load().adha_tune_clear(), "adha_tune_clear")
 

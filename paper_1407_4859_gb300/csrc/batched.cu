@@ -1,7 +1,7 @@
 // batched.cu -- many record arrays remapped in one persistent launch.
 //
 // Each array (its own schema, record count and source/destination layouts) is cut into chunks
-// of R_a records, and its chunks into work blocks (16 chunks per working warp).  A CTA holds a
+// of R_a records, and its chunks into work blocks (about 2048 records per working warp).  A CTA holds a
 // fixed budget of shared memory for its warps' buffers; an array whose records are too wide for
 // eight warps' buffers in that budget is worked on by fewer warps of the CTA.  A CTA takes the next block
 // with one atomic ticket (a 64-bit counter in the caller's workspace, zeroed by a memset node
@@ -23,14 +23,15 @@
 
 namespace adha {
 
-constexpr int kBlockChunksPerWarp = 16;
+constexpr int kBlockRecordsPerWarp = 2048;   // a work block gives each working warp about this many records
 
 struct BatchHeader {
   int64_t n, n_full, n_chunks, block0;
   int32_t R, n_src, n_dst, in_bytes, out_bytes, n_moves;
-  int32_t cls_count[3], cls_order[3];
+  int32_t cls_count[6], cls_order[6];
   int32_t group0, move0;
   int32_t warps;        // warps of a CTA that work on this array (the others idle for its blocks)
+  int32_t chunks_per_warp;   // chunks of one working warp in one work block
   int32_t warp_bytes;   // shared bytes of one working warp: two input buffers and an output buffer
 };
 
@@ -48,6 +49,7 @@ struct BatchParams {
   int32_t max_entries;
 };
 
+template <bool DIRECT>
 __global__ void __launch_bounds__(kThreads) batched_kernel(const __grid_constant__ BatchParams p) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ BatchHeader h;
@@ -90,7 +92,7 @@ __global__ void __launch_bounds__(kThreads) batched_kernel(const __grid_constant
       cur = arr;
     }
     const int nw = h.warps;
-    const int64_t per_block = (int64_t)kBlockChunksPerWarp * nw;
+    const int64_t per_block = (int64_t)h.chunks_per_warp * nw;
     const int64_t c_begin = (blk - h.block0) * per_block;
     const int64_t c_end = c_begin + per_block < h.n_chunks ? c_begin + per_block : h.n_chunks;
     uint8_t* buf0 = wbase + (size_t)warp * h.warp_bytes;
@@ -114,14 +116,9 @@ __global__ void __launch_bounds__(kThreads) batched_kernel(const __grid_constant
       cp_async_commit();
       cp_async_wait<1>();
       __syncwarp();
-      move_chunk(sched, h.R, h.cls_count, curb, outb, lane);
+      move_chunk<DIRECT>(sched, h.R, h.cls_count, curb, outb, tout, c * R, lane);
       __syncwarp();
-      int g = 0;
-      for (int q = lane * 16; q < h.out_bytes; q += 512) {
-        while (q >= tout[g].start + h.R * tout[g].stride) ++g;
-        *reinterpret_cast<uint4*>(const_cast<uint8_t*>(tout[g].ptr) + c * R * tout[g].stride + (q - tout[g].start)) =
-            *reinterpret_cast<const uint4*>(outb + q);
-      }
+      write_back(tout, h.n_dst, h.R, h.out_bytes, outb, c, lane);
       __syncwarp();
     }
     cp_async_wait<0>();
@@ -145,6 +142,7 @@ struct adha_batched {
   size_t smem = 0;
   int grid = 1;
   double bytes = 0;
+  bool direct = false;          // some array stores one-field destination groups directly
   cudaGraphExec_t graph = nullptr;
   void* graph_ws = nullptr;
 };
@@ -171,34 +169,50 @@ static int launch_batched(const adha_batched* b, void* ws, void* stream) {
   cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(unsigned long long), (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(ticket)");
   if (b->total_blocks == 0) return 0;
-  e = cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+  auto* k = b->direct ? batched_kernel<true> : batched_kernel<false>;
+  e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(batched)");
-  batched_kernel<<<b->grid, kThreads, b->smem, (cudaStream_t)stream>>>(params_for(b, ws));
+  k<<<b->grid, kThreads, b->smem, (cudaStream_t)stream>>>(params_for(b, ws));
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "batched kernel launch");
   return 0;
 }
 
+// Default chunk of an array in the batched kernel: the single-array rule, but at least 32 records.
+static int batch_chunk(const Layout& S, const Layout& D) {
+  int src = 0, dst = 0;
+  for (int g = 0; g < S.n_groups; ++g) src += S.stride[g];
+  for (int g = 0; g < D.n_groups; ++g) dst += D.stride[g];
+  int R = 32;
+  while (R < 512 && 2 * R * std::max(src, dst) <= 4096) R *= 2;
+  return R;
+}
+
 // Chooses each array's chunk size: the default rule, or (autotune) the fastest of 32..256
 // records measured with the single-array remap kernel on the array's own buffers.
 static int tune_chunk(const Layout& S, const void* const* sp, const Layout& D, void* const* dp, int64_t n, void* stream,
-                      int* best_R) {
+                      int* best_R, int* best_direct) {
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return fail(ADHA_ECUDA, "cudaEventCreate");
   float best = -1;
   int rc = 0;
-  for (int R = 32; R <= 256 && !rc; R *= 2) {
+  // 32..256 records: in the batched kernel occupancy is fixed by the buffer budget, so shorter
+  // chunks only add per-chunk overhead
+  for (int trial = 0; trial < 8 && !rc; ++trial) {
+    const int R = 32 << (trial >> 1), direct = trial & 1;
     RemapArgs a;
     bool empty = false;
-    rc = remap_plan_args(S, sp, D, dp, n, R, &a, &empty);
+    rc = remap_plan_args(S, sp, D, dp, n, R, direct, &a, &empty);
     if (rc || empty) break;
     if (2 * a.in_bytes + a.out_bytes > kWarpBufferBudget / kWarps && R > 32) continue;   // keep 8 warps busy
     adha_tune_override(R);
+    adha_tune_remap_direct(direct);
     for (int w = 0; w < 2 && !rc; ++w) rc = remap_layouts(S, sp, D, dp, n, stream, nullptr);
     cudaEventRecord(e0, (cudaStream_t)stream);
     for (int w = 0; w < 3 && !rc; ++w) rc = remap_layouts(S, sp, D, dp, n, stream, nullptr);
     cudaEventRecord(e1, (cudaStream_t)stream);
     adha_tune_override(0);
+    adha_tune_remap_direct(0);
     if (rc) break;
     cudaEventSynchronize(e1);
     float ms = 0;
@@ -206,6 +220,7 @@ static int tune_chunk(const Layout& S, const void* const* sp, const Layout& D, v
     if (best < 0 || ms < best) {
       best = ms;
       *best_R = R;
+      *best_direct = direct;
     }
   }
   cudaEventDestroy(e0);
@@ -242,12 +257,12 @@ int adha_batched_create(int32_t n_arrays, const adha_remap_desc* descs, int32_t 
         if (!d.dst_ptrs || !d.dst_ptrs[g] || reinterpret_cast<uintptr_t>(d.dst_ptrs[g]) % 16)
           rc = fail(ADHA_EINVAL, "array %d destination buffer %d is NULL or misaligned", k, g);
     }
-    int R = 0;
+    int R = 0, direct = 0;
     if (!rc && d.n > 0 && (flags & ADHA_BATCHED_AUTOTUNE))
-      rc = tune_chunk(S, d.src_ptrs, D, d.dst_ptrs, d.n, stream, &R);
+      rc = tune_chunk(S, d.src_ptrs, D, d.dst_ptrs, d.n, stream, &R, &direct);
     RemapArgs a;
     bool empty = true;
-    if (!rc && d.n > 0) rc = remap_plan_args(S, d.src_ptrs, D, d.dst_ptrs, d.n, R, &a, &empty);
+    if (!rc && d.n > 0) rc = remap_plan_args(S, d.src_ptrs, D, d.dst_ptrs, d.n, R ? R : batch_chunk(S, D), direct, &a, &empty);
     if (rc) {
       delete b;
       return rc;
@@ -266,10 +281,11 @@ int adha_batched_create(int32_t n_arrays, const adha_remap_desc* descs, int32_t 
       h.in_bytes = a.in_bytes;
       h.out_bytes = a.out_bytes;
       h.n_moves = a.n_moves;
-      for (int c = 0; c < 3; ++c) {
+      for (int c = 0; c < 6; ++c) {
         h.cls_count[c] = a.cls_count[c];
         h.cls_order[c] = a.cls_order[c];
       }
+      b->direct = b->direct || (a.cls_count[0] + a.cls_count[1] + a.cls_count[2] > 0);
       h.group0 = (int32_t)groups.size();
       h.move0 = (int32_t)moves.size();
       h.warp_bytes = 2 * a.in_bytes + a.out_bytes;
@@ -278,7 +294,8 @@ int adha_batched_create(int32_t n_arrays, const adha_remap_desc* descs, int32_t 
       for (int g = 0; g < a.n_src; ++g) groups.push_back(a.src[g]);
       for (int g = 0; g < a.n_dst; ++g) groups.push_back(a.dst[g]);
       moves.insert(moves.end(), a.move, a.move + a.n_moves);
-      const int64_t per_block = (int64_t)kBlockChunksPerWarp * h.warps;
+      h.chunks_per_warp = std::max(1, kBlockRecordsPerWarp / h.R);
+      const int64_t per_block = (int64_t)h.chunks_per_warp * h.warps;
       blocks += (h.n_chunks + per_block - 1) / per_block;
       b->max_entries = std::max(b->max_entries, a.R * a.n_moves);
       double moved = 0;
@@ -318,8 +335,9 @@ int adha_batched_create(int32_t n_arrays, const adha_remap_desc* descs, int32_t 
     delete b;
     return rc;
   }
-  cudaError_t e = cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel, kThreads, b->smem);
+  auto* kern = b->direct ? batched_kernel<true> : batched_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, b->smem);
   if (e != cudaSuccess) {
     delete b;
     return cuda_fail(e, "batched occupancy");

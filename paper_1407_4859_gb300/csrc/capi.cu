@@ -225,6 +225,7 @@ struct RemapPlan {
 // Chunk / pipeline override for the autotuner (0 = default rule).
 static thread_local int t_tile_override = 0;
 static thread_local int t_writeback_mode = 0;   // 0 automatic, 1 never, 2 every wide written group
+static thread_local int t_remap_direct = 0;     // 1: remaps store one-field destination groups directly
 
 // Autotuned launch shapes: section key -> (records per chunk, writeback mode).
 static std::mutex g_tune_mu;
@@ -264,6 +265,14 @@ static int pick_chunk(int rec_bytes, int target, int rmax) {
   return 32 * m;
 }
 
+// Records per remap chunk: a power of two from 8 to 512 with about 4 KB of the widest side, so
+// wide records use short chunks and keep more warps resident.
+static int pick_remap_chunk(int rec_bytes) {
+  int R = 8;
+  while (R < 512 && 2 * R * rec_bytes <= 4096) R *= 2;
+  return R;
+}
+
 static int finish_grid(int64_t n_chunks, int blocks, int* grid) {
   int sms = 0;
   if (int rc = sm_count(&sms)) return rc;
@@ -291,11 +300,13 @@ static int step_wavefronts(const uint32_t* bytes, int cnt, int width) {
 }
 
 // Wavefronts of one chunk's moves of class c under schedule order `order` (as the kernel's
-// schedule_entry lays them out), read side plus write side.
+// schedule_entry lays them out): read side, plus write side for staged classes (direct classes
+// store to global memory).
 static long class_conflict_cost(const RemapArgs& a, int c, int order) {
   int first = 0;
   for (int k = 0; k < c; ++k) first += a.cls_count[k];
-  const int cnt = a.cls_count[c], n = a.R * cnt, width = 8 >> c;
+  const int cnt = a.cls_count[c], n = a.R * cnt, width = class_width(c);
+  const bool direct = c < 3;
   long cost = 0;
   uint32_t rd[32], wr[32];
   for (int t = 0; t < n; t += 32) {
@@ -307,9 +318,9 @@ static long class_conflict_cost(const RemapArgs& a, int c, int order) {
       const Move& m = a.move[first + k];
       rd[l] = m.src_group < 0 ? 0xFFFFFFFFu
                               : (uint32_t)(a.src[m.src_group].start + r * a.src[m.src_group].stride + m.src_off);
-      wr[l] = (uint32_t)(a.dst[m.dst_group].start + r * a.dst[m.dst_group].stride + m.dst_off);
+      wr[l] = direct ? 0xFFFFFFFFu : (uint32_t)(a.dst[m.dst_group].start + r * a.dst[m.dst_group].stride + m.dst_off);
     }
-    cost += step_wavefronts(rd, w, width) + step_wavefronts(wr, w, width);
+    cost += step_wavefronts(rd, w, width) + (direct ? 0 : step_wavefronts(wr, w, width));
   }
   return cost;
 }
@@ -326,20 +337,24 @@ static void choose_orders(RemapArgs* a) {
     const Move& m = a->move[k];
     key.insert(key.end(), {m.dst_group, m.dst_off, m.src_group, m.src_off});
   }
-  for (int c = 0; c < 3; ++c) key.push_back(a->cls_count[c]);
+  for (int c = 0; c < kMoveClasses; ++c) key.push_back(a->cls_count[c]);
   {
     std::lock_guard<std::mutex> lk(g_order_mu);
     auto it = g_order_cache.find(key);
     if (it != g_order_cache.end()) {
-      for (int c = 0; c < 3; ++c) a->cls_order[c] = it->second[c];
+      for (int c = 0; c < kMoveClasses; ++c) a->cls_order[c] = it->second[c];
       return;
     }
   }
-  std::vector<int32_t> orders(3, 0);
-  for (int c = 0; c < 3; ++c) {
+  std::vector<int32_t> orders(kMoveClasses, 1);
+  for (int c = 0; c < kMoveClasses; ++c) {
     if (!a->cls_count[c]) continue;
     long best = -1;
     for (int o = 0; o <= 6; ++o) {   // destination-major, record-major, skewed record-major (5 skews)
+      // direct classes store to global memory: keep each run of lanes on one field at least
+      // 32 bytes long (order 1, or a skew of at least 32/width lanes) so the stores stay coalesced
+      if (c < 3 && (o == 0 || (o >= 2 && (1 << (o - 2)) * class_width(c) < 32))) continue;
+      if (o >= 2 && a->R % 32) continue;   // skewed orders walk whole 32-record blocks
       const long cost = class_conflict_cost(*a, c, o);
       if (best < 0 || cost < best) {
         best = cost;
@@ -347,7 +362,7 @@ static void choose_orders(RemapArgs* a) {
       }
     }
   }
-  for (int c = 0; c < 3; ++c) a->cls_order[c] = orders[c];
+  for (int c = 0; c < kMoveClasses; ++c) a->cls_order[c] = orders[c];
   std::lock_guard<std::mutex> lk(g_order_mu);
   g_order_cache[key] = orders;
 }
@@ -365,7 +380,7 @@ static int cached_occupancy(int kind, size_t smem, int* blocks) {
       return 0;
     }
   }
-  const int rc = kind < 100 ? remap_occupancy(0, smem, blocks) : section_occupancy(kind - 100, smem, blocks);
+  const int rc = kind < 100 ? remap_occupancy(kind, smem, blocks) : section_occupancy(kind - 100, smem, blocks);
   if (rc) return rc;
   std::lock_guard<std::mutex> lk(g_occ_mu);
   g_occ_cache[{kind, smem}] = *blocks;
@@ -425,17 +440,23 @@ static int plan_remap(const Layout& S, const void* const* src_ptrs, const Layout
     }
   }
   if ((int)moves.size() > kMaxMoves) return fail(ADHA_EINVAL, "destination records too wide (%zu moves)", moves.size());
+  // class of a move: direct (its destination group holds one field) or staged, then its width
+  const bool allow_direct = t_remap_direct != 0;
+  auto move_class = [&](size_t k) {
+    const bool direct = allow_direct && D.groups[build[moves[k].dst_group]].size() == 1;
+    return (direct ? 0 : 3) + (widths[k] == 8 ? 0 : widths[k] == 4 ? 1 : 2);
+  };
   std::vector<size_t> idx(moves.size());
   for (size_t k = 0; k < idx.size(); ++k) idx[k] = k;
   std::stable_sort(idx.begin(), idx.end(), [&](size_t x, size_t y) {
-    if (widths[x] != widths[y]) return widths[x] > widths[y];
+    if (move_class(x) != move_class(y)) return move_class(x) < move_class(y);
     if (moves[x].dst_group != moves[y].dst_group) return moves[x].dst_group < moves[y].dst_group;
     return moves[x].dst_off < moves[y].dst_off;
   });
   int src_rec = 0, dst_rec = 0;
   for (int j : need) src_rec += S.stride[j];
   for (int d : build) dst_rec += D.stride[d];
-  int R = t_tile_override ? t_tile_override : pick_chunk(std::max(src_rec, dst_rec), 2560, 512);
+  int R = t_tile_override ? t_tile_override : pick_remap_chunk(std::max(src_rec, dst_rec));
   for (;;) {
     a.n = n;
     a.R = R;
@@ -454,24 +475,28 @@ static int plan_remap(const Layout& S, const void* const* src_ptrs, const Layout
     for (int k = 0; k < a.n_dst; ++k) {
       a.dst[k].ptr = static_cast<const uint8_t*>(dst_ptrs[build[k]]);
       a.dst[k].stride = D.stride[build[k]];
-      a.dst[k].start = off;
-      off += R * a.dst[k].stride;
+      if (allow_direct && D.groups[build[k]].size() == 1) {
+        a.dst[k].start = -1;          // direct: stored straight to global memory
+      } else {
+        a.dst[k].start = off;
+        off += R * a.dst[k].stride;
+      }
     }
     a.out_bytes = off;
     a.n_moves = (int)moves.size();
-    for (int c = 0; c < 3; ++c) a.cls_count[c] = 0;
+    for (int c = 0; c < kMoveClasses; ++c) a.cls_count[c] = 0;
     for (size_t k = 0; k < idx.size(); ++k) {
       a.move[k] = moves[idx[k]];
-      a.cls_count[widths[idx[k]] == 8 ? 0 : widths[idx[k]] == 4 ? 1 : 2]++;
+      a.cls_count[move_class(idx[k])]++;
     }
     plan->smem = remap_smem_bytes(a);
-    if (plan->smem <= (size_t)kSmemLimit && a.in_bytes < 0xFFFF && a.out_bytes <= 0xFFFF) break;
-    if (R <= 32) return fail(ADHA_EINVAL, "records too wide for a 32-record chunk (%zu bytes smem)", plan->smem);
-    R = std::max(32, R / 2 / 32 * 32);
+    if (plan->smem <= (size_t)kSmemLimit && a.in_bytes < 0xFFFF && a.out_bytes <= 0xFFFF && R <= 1024) break;
+    if (R <= 8) return fail(ADHA_EINVAL, "records too wide for an 8-record chunk (%zu bytes smem)", plan->smem);
+    R = std::max(8, R / 2 / 8 * 8);
   }
   choose_orders(&a);
   int blocks = 0;
-  if (int rc = cached_occupancy(0, plan->smem, &blocks)) return rc;
+  if (int rc = cached_occupancy(allow_direct ? 1 : 0, plan->smem, &blocks)) return rc;
   return finish_grid(a.n_chunks, blocks, &plan->grid);
 }
 
@@ -566,7 +591,8 @@ static int plan_section(const Layout& L, void* const* ptrs, const adha_section* 
   int rec = 0;
   for (int g : groups) rec += L.stride[g];
   if (s->op == ADHA_OP_GATHER) rec += 4;
-  int R = tuned_R ? std::min(tuned_R, 128) : (rec > 0 ? pick_chunk(rec, 4096, 128) : 128);
+  int R = tuned_R ? std::max(32, std::min(tuned_R, 128)) : (rec > 0 ? pick_chunk(rec, 4096, 128) : 128);
+  if (R != 32 && R != 64 && R != 128) R = R < 64 ? 32 : 64;
   if (R == 96) R = 64;
   for (;;) {
     a.n = n;
@@ -642,12 +668,14 @@ static int plan_section(const Layout& L, void* const* ptrs, const adha_section* 
 }
 
 int remap_plan_args(const Layout& S, const void* const* src_ptrs, const Layout& D, void* const* dst_ptrs, int64_t n,
-                    int chunk_override, RemapArgs* out, bool* empty) {
-  const int saved = t_tile_override;
+                    int chunk_override, int direct, RemapArgs* out, bool* empty) {
+  const int saved = t_tile_override, saved_direct = t_remap_direct;
   t_tile_override = chunk_override;
+  t_remap_direct = direct;
   RemapPlan plan;
   const int rc = plan_remap(S, src_ptrs, D, dst_ptrs, n, &plan);
   t_tile_override = saved;
+  t_remap_direct = saved_direct;
   if (rc) return rc;
   *out = plan.args;
   *empty = plan.empty;
@@ -840,8 +868,8 @@ int adha_profile_stop(adha_launch_record* out, int32_t max_records, int32_t* n_r
 
 int adha_tune_override(int32_t chunk_records) {
   clear_error();
-  if (chunk_records < 0 || chunk_records % 32 != 0 || chunk_records > 1024)
-    return fail(ADHA_EINVAL, "chunk %d is not a multiple of 32 in [0, 1024]", chunk_records);
+  if (chunk_records < 0 || chunk_records % 8 != 0 || chunk_records > 1024)
+    return fail(ADHA_EINVAL, "chunk %d is not a multiple of 8 in [0, 1024]", chunk_records);
   t_tile_override = chunk_records;
   return 0;
 }
@@ -885,6 +913,13 @@ int adha_tune_import(const char* text) {
   }
   std::lock_guard<std::mutex> lk(g_tune_mu);
   for (const auto& kv : parsed) g_tune[kv.first] = kv.second;
+  return 0;
+}
+
+int adha_tune_remap_direct(int32_t mode) {
+  clear_error();
+  if (mode < 0 || mode > 1) return fail(ADHA_EINVAL, "remap direct mode %d not in [0, 1]", mode);
+  t_remap_direct = mode;
   return 0;
 }
 

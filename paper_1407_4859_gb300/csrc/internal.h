@@ -73,8 +73,11 @@ struct Move {
 };
 
 // Remap of one record array: every built destination group is assembled from the source groups'
-// slices, one move per lane per step; the moves are sorted by width into three classes
-// (8, 4 and 2 bytes), each with its own schedule order.
+// slices, one move per lane per step.  Moves fall into six classes: moves into one-field
+// destination groups ("direct": stored straight to global memory, consecutive lanes on
+// consecutive records) of 8, 4 and 2 bytes, then moves into wider groups ("staged": assembled in
+// the warp's output buffer, written back with 16-byte stores) of 8, 4 and 2 bytes.  A direct
+// destination group has start = -1 in `dst`; the staged ones have their output-buffer offset.
 struct RemapArgs {
   int64_t n;              // records
   int64_t n_chunks;       // whole chunks of R records
@@ -83,8 +86,8 @@ struct RemapArgs {
   int32_t in_bytes;       // one chunk of the source slices
   int32_t out_bytes;      // one chunk of the destination slices
   int32_t n_moves;
-  int32_t cls_count[3];   // moves of 8, 4, 2 bytes, in that order in `move`
-  int32_t cls_order[3];   // per class: 0 destination-major, 1 record-major (lane = record)
+  int32_t cls_count[6];   // moves per class, in that order in `move`
+  int32_t cls_order[6];   // per class: schedule order (see schedule_pair)
   GroupRef src[kMaxGroups];
   GroupRef dst[kMaxGroups];
   Move move[kMaxMoves];
@@ -123,7 +126,7 @@ int run_section_layout(const Layout& L, void* const* ptrs, const adha_section* s
 adha_layout set_layout(const adha_layout_set* s, int l);
 // Remap launch arguments for one array (chunk_override 0 = the default chunk rule).
 int remap_plan_args(const Layout& S, const void* const* src_ptrs, const Layout& D, void* const* dst_ptrs, int64_t n,
-                    int chunk_override, RemapArgs* out, bool* empty);
+                    int chunk_override, int direct, RemapArgs* out, bool* empty);
 // Runs fn(ctx) bracketed by the launch profiler's events when profiling is on.
 int profiled_launch(int kind, int op, double bytes, void* stream, int (*fn)(const void*), const void* ctx);
 // Autotuning: the key of a section launch, storing its best shape, thread-local overrides.
@@ -162,7 +165,7 @@ int run_section_layout(const Layout& L, void* const* ptrs, const adha_section* s
 adha_layout set_layout(const adha_layout_set* s, int l);
 // Remap launch arguments for one array (chunk_override 0 = the default chunk rule).
 int remap_plan_args(const Layout& S, const void* const* src_ptrs, const Layout& D, void* const* dst_ptrs, int64_t n,
-                    int chunk_override, RemapArgs* out, bool* empty);
+                    int chunk_override, int direct, RemapArgs* out, bool* empty);
 // Runs fn(ctx) bracketed by the launch profiler's events when profiling is on.
 int profiled_launch(int kind, int op, double bytes, void* stream, int (*fn)(const void*), const void* ctx);
 // Autotuning: the key of a section launch, storing its best shape, thread-local overrides.

@@ -6,13 +6,14 @@
 //   1. the warp copies the chunk's slice of every source group into its own shared buffer with
 //      16-byte cp.async (coalesced: lane l moves bytes 16l, 16l+512, ...), one chunk ahead of
 //      the one it works on (double buffering);
-//   2. it assembles the destination slices in a second buffer, one move per lane per step: a
-//      move is one field of one destination record (8, 4 or 2 bytes, whole) or an aligned piece
-//      of its zero padding, taken from a schedule table built once per CTA.  This is the tile
+//   2. it moves every field of every destination record, one move per lane per step: a move is
+//      one field (8, 4 or 2 bytes, whole) or an aligned piece of zero padding, taken from a
+//      schedule table built once per CTA.  Moves into one-field destination groups are stored
+//      straight to global memory (consecutive lanes on consecutive records, so the stores are
+//      coalesced); moves into wider groups are assembled in a second buffer.  This is the tile
 //      transpose between the source and destination record strides; the host picks, per move
-//      width, the schedule order (destination-major or record-major) with fewer shared-memory
-//      bank conflicts;
-//   3. it writes the destination slices back with 16-byte stores.
+//      class, the schedule order with the fewest shared-memory bank conflicts;
+//   3. it writes the assembled wider destination slices back with 16-byte stores.
 // Global traffic is one contiguous read stream per source group and one write stream per
 // destination group.  The ragged tail (fewer than R records) goes move by move through the warp
 // that would own the next chunk.
@@ -26,6 +27,7 @@ namespace adha {
 
 __device__ __forceinline__ int align16(int x) { return (x + 15) & ~15; }
 
+template <bool DIRECT>
 __global__ void __launch_bounds__(kThreads) remap_kernel(const __grid_constant__ RemapArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   GroupRef* tin = reinterpret_cast<GroupRef*>(smem);
@@ -63,14 +65,9 @@ __global__ void __launch_bounds__(kThreads) remap_kernel(const __grid_constant__
     cp_async_commit();
     cp_async_wait<1>();
     __syncwarp();
-    move_chunk(sched, a.R, a.cls_count, cur, outb, lane);
+    move_chunk<DIRECT>(sched, a.R, a.cls_count, cur, outb, tout, c * R, lane);
     __syncwarp();
-    int g = 0;
-    for (int p = lane * 16; p < a.out_bytes; p += 512) {
-      while (p >= tout[g].start + a.R * tout[g].stride) ++g;
-      const uint4 v = *reinterpret_cast<const uint4*>(outb + p);
-      *reinterpret_cast<uint4*>(const_cast<uint8_t*>(tout[g].ptr) + c * R * tout[g].stride + (p - tout[g].start)) = v;
-    }
+    write_back(tout, a.n_dst, a.R, a.out_bytes, outb, c, lane);
     __syncwarp();
   }
   cp_async_wait<0>();
@@ -86,21 +83,32 @@ size_t remap_smem_bytes(const RemapArgs& a) {
          (size_t)kWarps * (2 * (size_t)a.in_bytes + a.out_bytes);
 }
 
-int launch_remap(const RemapArgs& a, int grid, size_t smem, void* stream) {
-  cudaError_t e = cudaFuncSetAttribute(remap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <bool DIRECT>
+static int launch_d(const RemapArgs& a, int grid, size_t smem, void* stream) {
+  cudaError_t e = cudaFuncSetAttribute(remap_kernel<DIRECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(remap)");
-  remap_kernel<<<grid, kThreads, smem, (cudaStream_t)stream>>>(a);
+  remap_kernel<DIRECT><<<grid, kThreads, smem, (cudaStream_t)stream>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "remap kernel launch");
   return 0;
 }
 
-int remap_occupancy(int, size_t smem, int* blocks) {
-  cudaError_t e = cudaFuncSetAttribute(remap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+int launch_remap(const RemapArgs& a, int grid, size_t smem, void* stream) {
+  const bool direct = a.cls_count[0] + a.cls_count[1] + a.cls_count[2] > 0;
+  return direct ? launch_d<true>(a, grid, smem, stream) : launch_d<false>(a, grid, smem, stream);
+}
+
+template <bool DIRECT>
+static int occ_d(size_t smem, int* blocks) {
+  cudaError_t e = cudaFuncSetAttribute(remap_kernel<DIRECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(remap)");
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, remap_kernel, kThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, remap_kernel<DIRECT>, kThreads, smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(remap)");
   return 0;
+}
+
+int remap_occupancy(int direct, size_t smem, int* blocks) {
+  return direct ? occ_d<true>(smem, blocks) : occ_d<false>(smem, blocks);
 }
 
 }  // namespace adha

@@ -29,9 +29,13 @@ __host__ __device__ __forceinline__ void schedule_pair(int u, int R, int cnt, in
   }
 }
 
-// Schedule entry t of a chunk (R records, n_moves moves sorted into classes of 8/4/2 bytes):
-// (source byte in the chunk buffer | destination byte in the output buffer << 16), source
-// 0xFFFF for padding.
+constexpr int kMoveClasses = 6;
+
+__host__ __device__ __forceinline__ int class_width(int c) { return 8 >> (c % 3); }
+
+// Schedule entry t of a chunk (R records, n_moves moves sorted into the six classes):
+// source byte in the chunk buffer (0xFFFF for padding) | destination << 16, where the
+// destination is (group << 10 | record) for direct classes and the output-buffer byte otherwise.
 __device__ __forceinline__ uint32_t schedule_entry(int t, int R, const int32_t* cls_count, const int32_t* cls_order,
                                                    const Move* moves, const GroupRef* src, const GroupRef* dst) {
   int c = 0, first = 0;
@@ -41,13 +45,14 @@ __device__ __forceinline__ uint32_t schedule_entry(int t, int R, const int32_t* 
   schedule_pair(u, R, cnt, cls_order[c], &r, &k);
   const Move m = moves[first + k];
   const uint32_t s = m.src_group < 0 ? 0xFFFFu : (uint32_t)(src[m.src_group].start + r * src[m.src_group].stride + m.src_off);
-  const uint32_t d = (uint32_t)(dst[m.dst_group].start + r * dst[m.dst_group].stride + m.dst_off);
+  const uint32_t d = c < 3 ? (((uint32_t)m.dst_group << 10) | (uint32_t)r)
+                           : (uint32_t)(dst[m.dst_group].start + r * dst[m.dst_group].stride + m.dst_off);
   return s | (d << 16);
 }
 
 template <typename V>
-__device__ __forceinline__ void move_class(const uint32_t* sched, int begin, int end, const uint8_t* in, uint8_t* out,
-                                           int lane) {
+__device__ __forceinline__ void move_class_staged(const uint32_t* sched, int begin, int end, const uint8_t* in,
+                                                  uint8_t* out, int lane) {
 #pragma unroll 4
   for (int t = begin + lane; t < end; t += 32) {
     const uint32_t p = sched[t];
@@ -56,13 +61,34 @@ __device__ __forceinline__ void move_class(const uint32_t* sched, int begin, int
   }
 }
 
-// All moves of a chunk: the 8-, 4- and 2-byte classes in turn.
+// Moves into one-field destination groups go straight to global memory: record rec0 + r.
+template <typename V>
+__device__ __forceinline__ void move_class_direct(const uint32_t* sched, int begin, int end, const uint8_t* in,
+                                                  const GroupRef* dst, int64_t rec0, int lane) {
+#pragma unroll 4
+  for (int t = begin + lane; t < end; t += 32) {
+    const uint32_t p = sched[t];
+    const uint32_t s = p & 0xFFFFu, d = p >> 16;
+    const GroupRef& g = dst[d >> 10];
+    *reinterpret_cast<V*>(const_cast<uint8_t*>(g.ptr) + (rec0 + (int64_t)(d & 1023u)) * g.stride) =
+        s != 0xFFFFu ? *reinterpret_cast<const V*>(in + s) : V(0);
+  }
+}
+
+// All moves of a chunk whose first record is rec0 (DIRECT: the plan has direct classes).
+template <bool DIRECT>
 __device__ __forceinline__ void move_chunk(const uint32_t* sched, int R, const int32_t* cls_count, const uint8_t* in,
-                                           uint8_t* out, int lane) {
-  const int e8 = R * cls_count[0], e4 = e8 + R * cls_count[1], e2 = e4 + R * cls_count[2];
-  move_class<unsigned long long>(sched, 0, e8, in, out, lane);
-  move_class<uint32_t>(sched, e8, e4, in, out, lane);
-  move_class<uint16_t>(sched, e4, e2, in, out, lane);
+                                           uint8_t* out, const GroupRef* dst, int64_t rec0, int lane) {
+  int e = R * (cls_count[0] + cls_count[1] + cls_count[2]), b;
+  if (DIRECT) {
+    e = 0;
+    b = e; e += R * cls_count[0]; move_class_direct<unsigned long long>(sched, b, e, in, dst, rec0, lane);
+    b = e; e += R * cls_count[1]; move_class_direct<uint32_t>(sched, b, e, in, dst, rec0, lane);
+    b = e; e += R * cls_count[2]; move_class_direct<uint16_t>(sched, b, e, in, dst, rec0, lane);
+  }
+  b = e; e += R * cls_count[3]; move_class_staged<unsigned long long>(sched, b, e, in, out, lane);
+  b = e; e += R * cls_count[4]; move_class_staged<uint32_t>(sched, b, e, in, out, lane);
+  b = e; e += R * cls_count[5]; move_class_staged<uint16_t>(sched, b, e, in, out, lane);
 }
 
 template <typename V>
@@ -78,11 +104,26 @@ __device__ __forceinline__ void tail_moves(int64_t t0, int64_t n, int n_moves, c
   const int Tt = (int)(n - t0);
   for (int e = lane; e < Tt * n_moves; e += 32) {
     const int r = e / n_moves, k = e - r * n_moves;
-    const Move m = moves[k];
-    if (k < cls_count[0]) tail_move<unsigned long long>(m, t0 + r, src, dst);
-    else if (k < cls_count[0] + cls_count[1]) tail_move<uint32_t>(m, t0 + r, src, dst);
-    else tail_move<uint16_t>(m, t0 + r, src, dst);
+    int c = 0, first = 0;
+    while (k >= first + cls_count[c]) first += cls_count[c++];
+    const int w = class_width(c);
+    if (w == 8) tail_move<unsigned long long>(moves[k], t0 + r, src, dst);
+    else if (w == 4) tail_move<uint32_t>(moves[k], t0 + r, src, dst);
+    else tail_move<uint16_t>(moves[k], t0 + r, src, dst);
   }
+}
+
+// Writes the staged (start >= 0) destination slices of chunk `ch` from the output buffer with
+// 16-byte stores; the staged slices follow one another in the buffer in destination order.
+__device__ __forceinline__ void write_back(const GroupRef* dst, int n_dst, int R, int out_bytes, const uint8_t* out,
+                                           int64_t ch, int lane) {
+  int g = 0;
+  for (int p = lane * 16; p < out_bytes; p += 512) {
+    while (dst[g].start < 0 || p >= dst[g].start + R * dst[g].stride) ++g;
+    *reinterpret_cast<uint4*>(const_cast<uint8_t*>(dst[g].ptr) + ch * R * dst[g].stride + (p - dst[g].start)) =
+        *reinterpret_cast<const uint4*>(out + p);
+  }
+  (void)n_dst;
 }
 
 }  // namespace adha

@@ -127,7 +127,7 @@ def test_tuning_cache_text_round_trip(P):
         assert e.value.code == ADHA_EINVAL
     P.adha_tune_clear()
     assert P.adha_tune_export() == ""
-    for bad in [-32, 33, 2048]:
+    for bad in [-32, 33, 12, 2048]:
         with pytest.raises(AdhaError):
             P.adha_tune_override(bad)
     with pytest.raises(AdhaError):

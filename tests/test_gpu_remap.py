@@ -34,19 +34,31 @@ def _check_remap(P, n, dtypes, src, dst, fields):
 
 @pytest.mark.parametrize("seed", range(24))
 @pytest.mark.parametrize("n", [1, 17, 1000, 4099])
-def test_random_layouts(P, seed, n):
+@pytest.mark.parametrize("direct", [0, 1])
+def test_random_layouts(P, seed, n, direct):
     rng = np.random.default_rng(1000 + seed)
     F = int(rng.integers(1, 24))
     dtypes = [int(x) for x in rng.integers(0, 4, F)]
-    _check_remap(P, n, dtypes, random_layout(rng, F), random_layout(rng, F), _random_bytes(rng, n, dtypes))
+    P.adha_tune_remap_direct(direct)
+    try:
+        _check_remap(P, n, dtypes, random_layout(rng, F), random_layout(rng, F), _random_bytes(rng, n, dtypes))
+    finally:
+        P.adha_tune_remap_direct(0)
 
 
 @pytest.mark.parametrize("n", [1, 15, 16, 31, 32, 33, 191, 192, 193, 100003])
-def test_aos_soa_stress_record(P, n):
+@pytest.mark.parametrize("chunk,direct", [(0, 0), (64, 1), (128, 0), (8, 0), (16, 1), (24, 0)])
+def test_aos_soa_stress_record(P, n, chunk, direct):
     wl = synth.config2(n=n)
     fields = oracle.initial_fields(wl)
-    _check_remap(P, n, wl.dtypes, oracle.aos(16), oracle.soa(16), fields)
-    _check_remap(P, n, wl.dtypes, oracle.soa(16), oracle.aos(16), fields)
+    P.adha_tune_override(chunk)
+    P.adha_tune_remap_direct(direct)
+    try:
+        _check_remap(P, n, wl.dtypes, oracle.aos(16), oracle.soa(16), fields)
+        _check_remap(P, n, wl.dtypes, oracle.soa(16), oracle.aos(16), fields)
+    finally:
+        P.adha_tune_override(0)
+        P.adha_tune_remap_direct(0)
 
 
 @pytest.mark.parametrize("dt", [0, 1, 2, 3])
