@@ -310,6 +310,32 @@ int adha_run_program(const adha_schema* schema, int64_t n, const adha_layout* in
                      const adha_cost_table* costs, const adha_plan_opts* opts, void* workspace, size_t ws_bytes,
                      adha_stream stream, adha_plan* plan);
 
+/* Device workspace bytes adha_run_program_host needs for n records cut into n_slices slices:
+ * three buffer sets, each an input slice plus three copies of the widest candidate layout. */
+size_t adha_program_host_workspace_bytes(const adha_schema* schema, int64_t n, const adha_layout* in_layout,
+                                         const adha_layout_set* candidates, int32_t n_slices);
+
+/*
+ * adha_run_program on host-resident records: host_in (n records in in_layout;
+ * pinned host memory lets the copies run asynchronously) is processed in
+ * n_slices slices of consecutive records that flow through three streams of
+ * the library's own (upload, program, download; chained by events over three
+ * buffer sets), so copies in both directions and kernels overlap.  The plan is solved once (or taken as fixed) before any data
+ * moves; the result is written in the plan's final layout (the last section's
+ * candidate, or in_layout with opts->return_to_input), host_out[g] holding
+ * n * stride(g) bytes.  Sections that read through a permutation need every
+ * record: with one of those n_slices must be 1.  The workspace (device,
+ * adha_program_host_workspace_bytes) must not be used by anything else until
+ * the work is done.  Asynchronous with respect to `stream`: the pipelines wait
+ * for work queued on `stream` before they start, and `stream` waits for them
+ * to finish.  plan->final_ptrs lists host_out.
+ */
+int adha_run_program_host(const adha_schema* schema, int64_t n, const adha_layout* in_layout,
+                          const void* const* host_in, const adha_section* sections, int32_t n_sec,
+                          const adha_layout_set* candidates, const adha_cost_table* costs, const adha_plan_opts* opts,
+                          void* const* host_out, int32_t n_slices, void* workspace, size_t ws_bytes, adha_stream stream,
+                          adha_plan* plan);
+
 /* ----------------------------------------------------------- batched remap */
 
 /* One record array of a batched remap: its own schema, record count, and

@@ -11,4 +11,5 @@ from .api import (  # noqa: F401
     PlanOpts, Sections, LayoutSet, CostTable, adha_ods, adha_plan_sections, adha_layout_set_create,
     adha_cost_table_create, adha_pdl_solve, adha_measure_workspace_bytes, adha_measure, adha_program_workspace_bytes,
     adha_run_program, final_buffers, adha_profile_start, adha_profile_stop, Batched,
+    adha_program_host_workspace_bytes, adha_run_program_host,
 )

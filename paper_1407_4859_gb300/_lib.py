@@ -118,6 +118,12 @@ SIGNATURES = {
                                     _P, ctypes.c_size_t, _P, ctypes.POINTER(ctypes.POINTER(adha_cost_table))]),
     "adha_program_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(adha_schema), _I64, ctypes.POINTER(adha_layout),
                                                        ctypes.POINTER(adha_layout_set)]),
+    "adha_program_host_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(adha_schema), _I64, ctypes.POINTER(adha_layout),
+                                                            ctypes.POINTER(adha_layout_set), _I32]),
+    "adha_run_program_host": (ctypes.c_int, [ctypes.POINTER(adha_schema), _I64, ctypes.POINTER(adha_layout), _PP,
+                                             ctypes.POINTER(adha_section), _I32, ctypes.POINTER(adha_layout_set),
+                                             ctypes.POINTER(adha_cost_table), ctypes.POINTER(adha_plan_opts), _PP, _I32,
+                                             _P, ctypes.c_size_t, _P, ctypes.POINTER(adha_plan)]),
     "adha_run_program": (ctypes.c_int, [ctypes.POINTER(adha_schema), _I64, ctypes.POINTER(adha_layout), _PP,
                                         ctypes.POINTER(adha_section), _I32, ctypes.POINTER(adha_layout_set),
                                         ctypes.POINTER(adha_cost_table), ctypes.POINTER(adha_plan_opts), _P,

@@ -345,6 +345,32 @@ def adha_run_program(schema, n, in_layout, in_bufs, sections, candidates, costs=
     return plan
 
 
+def adha_program_host_workspace_bytes(schema, n, in_layout, candidates, n_slices):
+    return _lib.load().adha_program_host_workspace_bytes(ctypes.byref(schema.c), int(n), ctypes.byref(in_layout.c),
+                                                         candidates.ptr, int(n_slices))
+
+
+def adha_run_program_host(schema, n, in_layout, host_in, sections, candidates, host_out, costs=None, opts=None,
+                          workspace=None, n_slices=8, fixed=None, stream=None, plan=None):
+    """Runs the program on host buffers (pinned CPU tensors), writing the result into host_out
+    (CPU tensors in the plan's final layout); returns the adha_plan."""
+    secs = sections if isinstance(sections, Sections) else Sections(sections)
+    opts = opts or PlanOpts()
+    if plan is None:
+        plan = adha_plan()
+    plan.fixed = 0
+    if fixed is not None:
+        plan.fixed = 1
+        for k, l in enumerate(fixed):
+            plan.layout_of_section[k] = int(l)
+    check(_lib.load().adha_run_program_host(ctypes.byref(schema.c), int(n), ctypes.byref(in_layout.c), _ptrs(host_in),
+                                            secs.arr, len(secs), candidates.ptr,
+                                            costs.ptr if costs is not None else None, ctypes.byref(opts.c),
+                                            _ptrs(host_out), int(n_slices), workspace.data_ptr(), workspace.numel(),
+                                            _stream_ptr(stream), ctypes.byref(plan)), "adha_run_program_host")
+    return plan
+
+
 def final_buffers(plan, schema, n, candidates, in_layout, workspace_views=None):
     """(layout, list of uint8 device tensors viewing the result's groups) of a finished program."""
     layouts = candidates.layouts

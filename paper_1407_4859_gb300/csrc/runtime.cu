@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -327,6 +328,151 @@ int adha_run_program(const adha_schema* schema, int64_t n, const adha_layout* in
     if (same_layout(cur, cand[l])) plan->final_layout = l;
   plan->final_n_groups = cur.n_groups;
   for (int g = 0; g < cur.n_groups; ++g) plan->final_ptrs[g] = cur_p[g];
+  return 0;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Programs on host-resident data: the record array is cut into slices that flow through three
+// streams (upload, compute, download) chained by events over three buffer sets, so the upload of
+// one slice, the program on the one before and the download of the one before that overlap.
+// Sections are per record, so slices are independent; a section that reads through a
+// permutation needs every record and forces one slice.
+
+namespace adha {
+
+constexpr int kPipeSets = 3;
+
+struct HostPipe {
+  cudaStream_t up = nullptr, comp = nullptr, down = nullptr;
+  cudaEvent_t start = nullptr, end_comp = nullptr, end_down = nullptr;
+  cudaEvent_t uploaded[kPipeSets] = {}, computed[kPipeSets] = {}, freed[kPipeSets] = {};
+};
+
+static std::mutex g_pipe_mu;
+static HostPipe g_pipes[256];
+
+static int host_pipe(HostPipe** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= 256) return fail(ADHA_ENOTIMPL, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lk(g_pipe_mu);
+  HostPipe& p = g_pipes[dev];
+  if (!p.up) {
+    cudaStream_t* ss[3] = {&p.up, &p.comp, &p.down};
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaStreamCreateWithFlags(ss[k], cudaStreamNonBlocking);
+    cudaEvent_t* ev[3] = {&p.start, &p.end_comp, &p.end_down};
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(ev[k], cudaEventDisableTiming);
+    for (int k = 0; k < kPipeSets && e == cudaSuccess; ++k) {
+      e = cudaEventCreateWithFlags(&p.uploaded[k], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p.computed[k], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p.freed[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "pipeline streams");
+  }
+  *out = &p;
+  return 0;
+}
+
+static int64_t slice_records(int64_t n, int n_slices) { return (n + n_slices - 1) / n_slices; }
+
+}  // namespace adha
+
+extern "C" {
+
+size_t adha_program_host_workspace_bytes(const adha_schema* schema, int64_t n, const adha_layout* in_layout,
+                                         const adha_layout_set* candidates, int32_t n_slices) {
+  clear_error();
+  Layout in;
+  std::vector<Layout> cand;
+  if (n_slices < 1 || make_layout(schema, in_layout, &in, "input") || load_set(schema, candidates, &cand)) return 0;
+  const int64_t ns = slice_records(n, n_slices);
+  size_t m = layout_bytes(in, ns);
+  for (const Layout& L : cand) m = std::max(m, layout_bytes(L, ns));
+  return kPipeSets * (layout_bytes(in, ns) + 3 * m);
+}
+
+int adha_run_program_host(const adha_schema* schema, int64_t n, const adha_layout* in_layout,
+                          const void* const* host_in, const adha_section* sections, int32_t n_sec,
+                          const adha_layout_set* candidates, const adha_cost_table* costs, const adha_plan_opts* opts,
+                          void* const* host_out, int32_t n_slices, void* workspace, size_t ws_bytes, adha_stream stream,
+                          adha_plan* plan) {
+  clear_error();
+  Layout in;
+  std::vector<Layout> cand;
+  if (int rc = make_layout(schema, in_layout, &in, "input")) return rc;
+  if (int rc = load_set(schema, candidates, &cand)) return rc;
+  if (!plan || !sections || n_sec < 1 || n_sec > ADHA_MAX_SECTIONS || n < 0 || n_slices < 1)
+    return fail(ADHA_EINVAL, "bad host-program arguments");
+  for (int k = 0; k < n_sec; ++k)
+    if (sections[k].read_at_perm_mask && n_slices > 1)
+      return fail(ADHA_EINVAL, "section %d reads through a permutation: it needs every record, use one slice", k);
+  const int L = (int)cand.size();
+  // the plan (and with it the result's layout) is fixed before any data moves
+  if (!plan->fixed) {
+    if (!costs) return fail(ADHA_EINVAL, "no cost table: run adha_measure first or pass a fixed plan");
+    if (costs->n_sections != n_sec || costs->n_layouts != L) return fail(ADHA_EINVAL, "cost table does not match");
+    pdl_solve(costs, opts ? opts->return_to_input : 0, plan->layout_of_section, &plan->model_ns);
+  } else {
+    for (int k = 0; k < n_sec; ++k)
+      if (plan->layout_of_section[k] < 0 || plan->layout_of_section[k] >= L)
+        return fail(ADHA_EINVAL, "fixed plan names candidate %d for section %d", plan->layout_of_section[k], k);
+  }
+  const bool back = opts && opts->return_to_input;
+  const Layout& out_layout = back ? in : cand[plan->layout_of_section[n_sec - 1]];
+  if (!host_in || !host_out) return fail(ADHA_EINVAL, "host buffers are NULL");
+  if (n == 0) return 0;
+  const int64_t ns = slice_records(n, n_slices);
+  const size_t need = adha_program_host_workspace_bytes(schema, n, in_layout, candidates, n_slices);
+  if (!workspace || ws_bytes < need) return fail(ADHA_ENOMEM, "host-program workspace has %zu bytes, needs %zu", ws_bytes, need);
+  HostPipe* pipe = nullptr;
+  if (int rc = host_pipe(&pipe)) return rc;
+  const size_t in_b = layout_bytes(in, ns), set_b = need / kPipeSets;
+  cudaError_t e = cudaEventRecord(pipe->start, (cudaStream_t)stream);
+  cudaStream_t ss[3] = {pipe->up, pipe->comp, pipe->down};
+  for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(ss[k], pipe->start, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "pipeline start");
+  adha_plan slice_plan;
+  for (int64_t k = 0, i0 = 0; i0 < n; ++k, i0 += ns) {
+    const int b = (int)(k % kPipeSets);
+    const int64_t cnt = std::min(ns, n - i0);
+    uint8_t* base = static_cast<uint8_t*>(workspace) + b * set_b;
+    std::vector<void*> dev_in;
+    carve(in, ns, base, &dev_in);
+    // upload: once the download that last used this buffer set is done
+    if (k >= kPipeSets) e = cudaStreamWaitEvent(pipe->up, pipe->freed[b], 0);
+    for (int g = 0; g < in.n_groups && e == cudaSuccess; ++g)
+      e = cudaMemcpyAsync(dev_in[g], static_cast<const uint8_t*>(host_in[g]) + i0 * in.stride[g],
+                          (size_t)cnt * in.stride[g], cudaMemcpyHostToDevice, pipe->up);
+    if (e == cudaSuccess) e = cudaEventRecord(pipe->uploaded[b], pipe->up);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(pipe->comp, pipe->uploaded[b], 0);
+    if (e != cudaSuccess) return cuda_fail(e, "slice upload");
+    slice_plan = *plan;
+    slice_plan.fixed = 1;
+    if (int rc = adha_run_program(schema, cnt, in_layout, dev_in.data(), sections, n_sec, candidates, costs, opts,
+                                  base + in_b, set_b - in_b, pipe->comp, &slice_plan))
+      return rc;
+    e = cudaEventRecord(pipe->computed[b], pipe->comp);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(pipe->down, pipe->computed[b], 0);
+    for (int g = 0; g < slice_plan.final_n_groups && e == cudaSuccess; ++g)
+      e = cudaMemcpyAsync(static_cast<uint8_t*>(host_out[g]) + i0 * out_layout.stride[g], slice_plan.final_ptrs[g],
+                          (size_t)cnt * out_layout.stride[g], cudaMemcpyDeviceToHost, pipe->down);
+    if (e == cudaSuccess) e = cudaEventRecord(pipe->freed[b], pipe->down);
+    if (e != cudaSuccess) return cuda_fail(e, "slice download");
+  }
+  e = cudaEventRecord(pipe->end_comp, pipe->comp);
+  if (e == cudaSuccess) e = cudaEventRecord(pipe->end_down, pipe->down);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent((cudaStream_t)stream, pipe->end_comp, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent((cudaStream_t)stream, pipe->end_down, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "pipeline join");
+  const double model = plan->model_ns;
+  *plan = slice_plan;
+  plan->fixed = 0;
+  plan->model_ns = model;
+  plan->final_n_groups = out_layout.n_groups;
+  for (int g = 0; g < out_layout.n_groups; ++g) plan->final_ptrs[g] = host_out[g];
   return 0;
 }
 

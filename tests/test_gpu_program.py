@@ -125,3 +125,41 @@ def test_full_size_program_sampled(P, make):
         rows = host[g].reshape(n, st[g])[sample, off[f]:off[f] + sz]
         got = np.ascontiguousarray(rows).view(oracle.core.NP[wl.dtypes[f]]).reshape(-1)
         assert np.array_equal(got.view(np.uint8), np.ascontiguousarray(want[f]).view(np.uint8)), "field %d" % f
+
+
+@pytest.mark.parametrize("slices", [1, 3, 8])
+def test_host_program_pipeline(P, slices):
+    """adha_run_program_host: host buffers in, host buffers out, slices pipelined on two streams."""
+    wl = synth.config2(n=200003)
+    n = wl.n
+    S, AOS, cand, secs = _setup(P, wl)
+    fields = oracle.initial_fields(wl)
+    want = oracle.run_program_fields(wl, [a.copy() for a in fields])
+    host_in = [torch.from_numpy(b).pin_memory() for b in oracle.from_fields(n, wl.dtypes, AOS.groups, fields)]
+    costs = P.adha_measure(S, n, AOS, [h.cuda() for h in host_in], secs, cand)
+    _, seq = P.adha_pdl_solve(costs)
+    out_layout = cand.layouts[seq[-1]]
+    strides, _ = P.adha_layout_strides(S, out_layout)
+    host_out = [torch.zeros(n * s, dtype=torch.uint8).pin_memory() for s in strides]
+    ws = torch.empty(P.adha_program_host_workspace_bytes(S, n, AOS, cand, slices), dtype=torch.uint8, device="cuda")
+    plan = P.adha_run_program_host(S, n, AOS, host_in, secs, cand, host_out, costs=costs, workspace=ws, n_slices=slices)
+    torch.cuda.synchronize()
+    assert list(plan.layout_of_section[:len(wl.sections)]) == seq
+    assert_fields_equal(oracle.to_fields(n, wl.dtypes, out_layout.groups, [h.numpy() for h in host_out]), want,
+                        "host program, %d slices" % slices)
+    # the inputs are host data: untouched
+    assert np.array_equal(host_in[0].numpy(), oracle.from_fields(n, wl.dtypes, AOS.groups, fields)[0])
+
+
+def test_host_program_gather_needs_one_slice(P):
+    from paper_1407_4859_gb300._lib import AdhaError, ADHA_EINVAL
+    wl = synth.config3(n=4096)
+    perm = torch.from_numpy(wl.perm()).cuda()
+    S, AOS, cand, secs = _setup(P, wl, perm)
+    host_in = [torch.zeros(wl.n * 56, dtype=torch.uint8).pin_memory()]
+    host_out = [torch.zeros(wl.n * 56, dtype=torch.uint8).pin_memory()]
+    ws = torch.empty(P.adha_program_host_workspace_bytes(S, wl.n, AOS, cand, 2), dtype=torch.uint8, device="cuda")
+    with pytest.raises(AdhaError) as e:
+        P.adha_run_program_host(S, wl.n, AOS, host_in, secs, cand, host_out, workspace=ws, n_slices=2,
+                                fixed=[0] * len(wl.sections))
+    assert e.value.code == ADHA_EINVAL and "permutation" in str(e.value)
