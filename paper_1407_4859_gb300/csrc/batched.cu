@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kThreads) batched_kernel(const __grid_constant
       __syncwarp();
       move_chunk<DIRECT>(sched, h.R, h.cls_count, curb, outb, tout, c * R, lane);
       __syncwarp();
-      write_back(tout, h.n_dst, h.R, h.out_bytes, outb, c, lane);
+      write_back<DIRECT>(tout, h.n_dst, h.R, h.out_bytes, outb, c, lane);
       __syncwarp();
     }
     cp_async_wait<0>();

@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(kThreads) remap_kernel(const __grid_constant__
     __syncwarp();
     move_chunk<DIRECT>(sched, a.R, a.cls_count, cur, outb, tout, c * R, lane);
     __syncwarp();
-    write_back(tout, a.n_dst, a.R, a.out_bytes, outb, c, lane);
+    write_back<DIRECT>(tout, a.n_dst, a.R, a.out_bytes, outb, c, lane);
     __syncwarp();
   }
   cp_async_wait<0>();
