@@ -101,15 +101,16 @@ def csrc_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_for(kernel_key):
-    """DRAM bytes per launch from the committed ncu summary, if the kernels have not changed."""
+def traffic_for(workload, kernel_key):
+    """DRAM bytes per launch of one kernel in one bench workload, from the committed ncu summary,
+    if the kernel sources have not changed since it was taken."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
     if d.get("csrc_hash") != csrc_hash():
         return None
-    ent = d.get("kernels", {}).get(kernel_key)
+    ent = d.get("workloads", {}).get(workload, {}).get(kernel_key)
     return None if ent is None else ent.get("dram_bytes_per_launch")
 
 
@@ -333,7 +334,7 @@ def main():
     peak, peak_src = measured_peaks()
     achieved = groups[dom][1] / (groups[dom][0] * 1e6)
     kernel_name = {"remap": "remap_kernel"}.get(dom, "section_kernel<%s>" % dom.replace("section_", ""))
-    traffic = traffic_for(dom)
+    traffic = traffic_for(args.workload, dom)
     roofline = {"bound": "hbm", "kernel": kernel_name, "achieved": round(achieved, 1), "peak": peak,
                 "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
@@ -454,7 +455,7 @@ def _timed(torch, stream, steps, fn):
     return e0.elapsed_time(e1)
 
 
-def _roofline(recs):
+def _roofline(recs, workload):
     groups = {}
     for r in recs:
         key = r["kind"] if r["kind"] != "section" else "section_%s" % r["op"]
@@ -468,7 +469,7 @@ def _roofline(recs):
     total = sum(v[0] for v in groups.values())
     roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback",
-            "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic_for(dom),
+            "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic_for(workload, dom),
             "launches": groups[dom][2], "share": round(groups[dom][0] / max(1e-9, total), 3)}
     kernels = {k: {"launches": v[2], "ms": round(v[0], 3), "alg_GBs": round(v[1] / (v[0] * 1e6), 1)}
                for k, v in sorted(groups.items(), key=lambda kv: -kv[1][0])}
@@ -520,7 +521,7 @@ def batched_bench(args, rank, world, local, dist):
     clk = clocks.stop()
     ms = reduce_max_ms(dist, ms)
     value = weak_scaling_value(world, bytes_per, args.steps, ms)
-    roof, kernels = _roofline(recs)
+    roof, kernels = _roofline(recs, args.workload)
 
     def per_array():
         for a in arrays:
@@ -653,7 +654,7 @@ def differentiable_bench(args, rank, world, local, dist):
     # program work only (sections and their adjoints), like the stress bench's value
     work = sum(r["bytes"] for r in recs if r["kind"] in ("section", "section_backward")) / args.steps
     value = weak_scaling_value(world, work, args.steps, ms)
-    roof, kernels = _roofline(recs)
+    roof, kernels = _roofline(recs, args.workload)
     k2 = max(3, args.steps // 2)
     t_aos = _timed(torch, stream, k2, lambda: run([AOS] * len(wl.sections))) / k2
     t_soa = _timed(torch, stream, k2, lambda: run([P.Layout.soa(F)] * len(wl.sections))) / k2
