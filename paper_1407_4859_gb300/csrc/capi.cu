@@ -644,7 +644,9 @@ static int plan_section(const Layout& L, void* const* ptrs, const adha_section* 
     }
     a.in_bytes = off;
     // vector mapping: every staged group and every written field's group is one field wide
-    a.vec = (s->op == ADHA_OP_MIX && R >= 64 && a.n_writeback == 0) ? 1 : 0;
+    // (and `save`, if any, aligned for the chunk's vector stores)
+    const bool vec_op = s->op == ADHA_OP_MIX || s->op == ADHA_OP_AXPB || s->op == ADHA_OP_MUL || s->op == ADHA_OP_TANH;
+    a.vec = (vec_op && R >= 64 && a.n_writeback == 0 && reinterpret_cast<uintptr_t>(save) % (R / 8) == 0) ? 1 : 0;
     for (int f = 0; f < L.F && a.vec; ++f)
       if ((has(staged, f) || has(s->write_mask, f)) && L.groups[L.group_of[f]].size() != 1) a.vec = 0;
     plan->smem = section_smem_bytes(a);

@@ -256,6 +256,39 @@ __device__ __forceinline__ void mix_chunk_vec(const SectionArgs& a, const uint8_
   }
 }
 
+// AXPB, MUL, TANH under the vector mapping (x, y, z each a one-field group): lane takes records
+// lane*M + m; x, y and the old z come from the chunk buffer (the values before the section, so
+// any aliasing of x, y, z reads what the per-record rule reads), z and `save` get vector stores.
+template <int OP, int M>
+__device__ __forceinline__ void chain_chunk_vec(const SectionArgs& a, const uint8_t* stage, int64_t i0, int lane) {
+  const int* g = a.arg;
+  const int z = OP == ADHA_OP_MUL ? g[2] : g[1];
+  const int64_t r0 = i0 + (int64_t)lane * M;
+  float x[M], v[M];
+  ld_vec<float, M>(stage + a.f[g[0]].s0 + lane * M * 4, x);
+  if (a.save) {
+    float old[M];
+    ld_vec<float, M>(stage + a.f[z].s0 + lane * M * 4, old);
+    st_vec<float, M>(a.save + r0 * 4, old);
+  }
+  if (OP == ADHA_OP_MUL) {
+    float y[M];
+    ld_vec<float, M>(stage + a.f[g[1]].s0 + lane * M * 4, y);
+#pragma unroll
+    for (int m = 0; m < M; ++m) v[m] = __fmul_rn(x[m], y[m]);
+  } else if (OP == ADHA_OP_AXPB) {
+#pragma unroll
+    for (int m = 0; m < M; ++m) v[m] = __fadd_rn(__fmul_rn(a.par[0], x[m]), a.par[1]);
+  } else {
+#pragma unroll
+    for (int m = 0; m < M; ++m) v[m] = tanh_cf(x[m], a.tanh_p, a.tanh_q);
+  }
+  st_vec<float, M>(a.f[z].g + r0 * 4, v);
+}
+
+template <int OP>
+constexpr bool kVectorOp = OP == ADHA_OP_MIX || OP == ADHA_OP_AXPB || OP == ADHA_OP_MUL || OP == ADHA_OP_TANH;
+
 template <int OP, class Rec>
 __device__ __forceinline__ void run_record(const SectionArgs& a, const Rec& rec, int64_t i, int32_t pj) {
   const int* g = a.arg;
@@ -397,6 +430,8 @@ __global__ void __launch_bounds__(kThreads) section_kernel(const __grid_constant
     const int64_t i0 = c * R;
     if (OP == ADHA_OP_MIX && VEC) {
       mix_chunk_vec<M>(a, cur, i0, lane);
+    } else if (VEC) {
+      chain_chunk_vec<OP, M>(a, cur, i0, lane);
     } else if (OP == ADHA_OP_MIX) {
       mix_chunk<M>(a, cur, i0, lane);
     } else {
@@ -503,9 +538,9 @@ static int launch_om(const SectionArgs& a, int grid, size_t smem, void* stream) 
 
 template <int OP>
 static int launch_op(const SectionArgs& a, int grid, size_t smem, void* stream) {
-  if (OP == ADHA_OP_MIX && a.vec) {
-    if (a.R == 64) return launch_om<OP, 2, true>(a, grid, smem, stream);
-    if (a.R == 128) return launch_om<OP, 4, true>(a, grid, smem, stream);
+  if constexpr (kVectorOp<OP>) {
+    if (a.vec && a.R == 64) return launch_om<OP, 2, true>(a, grid, smem, stream);
+    if (a.vec && a.R == 128) return launch_om<OP, 4, true>(a, grid, smem, stream);
   }
   switch (a.R) {
     case 32: return launch_om<OP, 1, false>(a, grid, smem, stream);

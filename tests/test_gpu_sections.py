@@ -125,3 +125,49 @@ def test_python_driven_tiny_program_every_assignment(P):
             P.adha_run_section(S, n, cur, bufs, P.c_section(wl.sections[k]))
         torch.cuda.synchronize()
         assert_fields_equal(from_device(n, wl.dtypes, cur.groups, bufs), want, "assignment %r" % (seq,))
+
+
+def _aliased_chain_sections():
+    """axpb, mul and tanh with every aliasing of x, y, z (fields of a 6-field fp32 schema)."""
+    S = synth.Section
+    fs = synth.workloads._fs
+    out = []
+    for x, z in [(0, 1), (2, 2)]:
+        out.append(S("axpb", (x, z), fs(x), fs(z), params=(0.75, -0.125)))
+        out.append(S("tanh", (x, z), fs(x), fs(z)))
+    for x, y, z in [(0, 1, 2), (3, 3, 4), (1, 2, 1), (2, 4, 4), (5, 5, 5)]:
+        out.append(S("mul", (x, y, z), fs(x, y), fs(z)))
+    return out
+
+
+@pytest.mark.parametrize("R", [32, 64, 128])
+@pytest.mark.parametrize("save_offset", [None, 0, 1, 2])
+def test_chain_sections_vector_mapping(P, R, save_offset):
+    """One-field groups take the vector mapping at 64 and 128 records per chunk; a save buffer that
+    is not aligned for the chunk's vector stores (offset by 1 or 2 floats) takes the per-record
+    path.  Both match the oracle bit for bit, aliasing of x, y, z included, with a ragged tail."""
+    n = 3 * 128 * 152 + 77
+    wl = synth.config5(n=n, n_sections=1)
+    wl.fields = wl.fields[:6]
+    groups = oracle.soa(6)
+    S, L = P.Schema(wl.dtypes), P.Layout(groups)
+    fields = oracle.initial_fields(wl)
+    P.adha_tune_override(R)
+    try:
+        for sec in _aliased_chain_sections():
+            bufs = to_device(n, wl.dtypes, groups, fields)
+            sbuf = None
+            if save_offset is not None:
+                base = torch.empty(n + 4, dtype=torch.float32, device="cuda")
+                sbuf = base[save_offset:save_offset + n]
+            P.adha_run_section(S, n, L, bufs, P.c_section(sec), save=sbuf)
+            torch.cuda.synchronize()
+            assert P.adha_device_status() == 0
+            want = [a.copy() for a in fields]
+            oracle.section(sec, wl.dtypes, want, None)
+            assert_fields_equal(from_device(n, wl.dtypes, groups, bufs), want, "%s %r R=%d" % (sec.op, sec.args, R))
+            if sbuf is not None:
+                z = sec.args[2] if sec.op == "mul" else sec.args[1]
+                assert np.array_equal(sbuf.cpu().numpy(), fields[z])
+    finally:
+        P.adha_tune_override(0)
