@@ -279,10 +279,11 @@ size_t adha_measure_workspace_bytes(const adha_schema* schema, int64_t n, const 
  * on `stream`, in whole nanoseconds.  A remap between layouts sharing a group
  * leaves that group in place, as the executor does.  With ADHA_MEASURE_AUTOTUNE
  * in flags each section is timed under every launch shape (records per chunk
- * 32, 64, 128 x field-wise or whole-group stores); the fastest enters the table
- * and the library's tuning cache, which later launches of the same section,
- * layout and size class use.  Synchronizes `stream`; *out is a library-owned
- * table (adha_free).
+ * 32, 64, 128 x field-wise or whole-group stores), and each remap from or to
+ * the input layout under every choice of piece tables (adha_tune_remap_pieces);
+ * the fastest enters the table and the library's tuning cache, which later
+ * launches of the same section (or pair of layouts), layout and size class use.
+ * Synchronizes `stream`; *out is a library-owned table (adha_free).
  */
 int adha_measure(const adha_schema* schema, int64_t n, const adha_layout* in_layout, void* const* in_ptrs,
                  const adha_section* sections, int32_t n_sec, const adha_layout_set* candidates, int32_t reps,
@@ -441,10 +442,24 @@ int adha_tune_writeback(int32_t mode);
  */
 int adha_tune_remap_direct(int32_t mode);
 
+/*
+ * How remaps launched later by the calling thread find where each 16-byte piece
+ * of a chunk buffer lives in global memory: through a per-block table of the
+ * pieces, or by a search over the groups.  0 = as tuned for the pair of layouts
+ * (adha_measure with ADHA_MEASURE_AUTOTUNE), else automatic (the table for a
+ * buffer whose slices average under 256 bytes); 1..4 = forced, with bits
+ * mode - 1: bit 0 = stage the source buffer through the table, bit 1 = write the
+ * destination buffer back through it.  Every mode moves the same bytes.  Host
+ * only; EINVAL for another mode.
+ */
+int adha_tune_remap_pieces(int32_t mode);
+
 /* Empties the library's tuning cache (process-wide).  Host only. */
 int adha_tune_clear(void);
 
-/* Writes the tuning cache as text ("key<TAB>records<TAB>mode" lines) into buf
+/* Writes the tuning cache as text ("key<TAB>records<TAB>mode" lines; section
+ * keys start with S, remap keys with M and carry records 0 and the piece-table
+ * bits as mode) into buf
  * (len bytes, NUL-terminated); *needed = bytes required.  buf may be NULL to
  * ask for the size.  Host only. */
 int adha_tune_export(char* buf, size_t len, size_t* needed);

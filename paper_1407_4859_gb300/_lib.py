@@ -97,6 +97,7 @@ SIGNATURES = {
     "adha_remap_batched_noalloc": (ctypes.c_int, [_I32, ctypes.POINTER(adha_remap_desc), _P]),
     "adha_tune_writeback": (ctypes.c_int, [_I32]),
     "adha_tune_remap_direct": (ctypes.c_int, [_I32]),
+    "adha_tune_remap_pieces": (ctypes.c_int, [_I32]),
     "adha_tune_clear": (ctypes.c_int, []),
     "adha_tune_export": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     "adha_tune_import": (ctypes.c_int, [ctypes.c_char_p]),

@@ -138,6 +138,10 @@ def adha_tune_remap_direct(mode=0):
     check(_lib.load().adha_tune_remap_direct(int(mode)), "adha_tune_remap_direct")
 
 
+def adha_tune_remap_pieces(mode=0):
+    check(_lib.load().adha_tune_remap_pieces(int(mode)), "adha_tune_remap_pieces")
+
+
 def adha_tune_clear():
     check(_lib.load().adha_tune_clear(), "adha_tune_clear")
 

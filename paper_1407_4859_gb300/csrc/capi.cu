@@ -226,27 +226,44 @@ struct RemapPlan {
 static thread_local int t_tile_override = 0;
 static thread_local int t_writeback_mode = 0;   // 0 automatic, 1 never, 2 every wide written group
 static thread_local int t_remap_direct = 0;     // 1: remaps store one-field destination groups directly
+static thread_local int t_remap_pieces = 0;     // 0: tuned or automatic, 1 + piece-table bits otherwise
 
-// Autotuned launch shapes: section key -> (records per chunk, writeback mode).
+// Autotuned launch shapes: section key -> (records per chunk, writeback mode); remap key ->
+// (0, piece-table bits).
 static std::mutex g_tune_mu;
 static std::map<std::string, std::pair<int, int>> g_tune;
+
+static std::string layout_code(const Layout& L) {
+  std::string k;
+  for (const auto& g : L.groups) {
+    for (int f : g) k += std::to_string(f) + "." + std::to_string(L.dtype[f]) + ",";
+    k += "|";
+  }
+  return k;
+}
+
+static std::string size_class(int64_t n) {
+  int lg = 0;
+  while (lg < 62 && (int64_t(1) << (lg + 1)) <= n) ++lg;
+  return ":n" + std::to_string(lg);
+}
 
 static std::string section_key(const Layout& L, const adha_section* s, int64_t n, bool save) {
   std::string k = "S" + std::to_string(s->op) + ":" + std::to_string(s->read_mask) + ":" +
                   std::to_string(s->write_mask) + ":" + std::to_string(s->read_at_perm_mask) + ":" +
                   std::to_string(save ? 1 : 0) + ":";
   for (int a = 0; a < 8; ++a) k += std::to_string(s->arg[a]) + ",";
-  k += ":L";
-  for (const auto& g : L.groups) {
-    for (int f : g) k += std::to_string(f) + "." + std::to_string(L.dtype[f]) + ",";
-    k += "|";
-  }
-  int lg = 0;
-  while (lg < 62 && (int64_t(1) << (lg + 1)) <= n) ++lg;
-  return k + ":n" + std::to_string(lg);
+  return k + ":L" + layout_code(L) + size_class(n);
+}
+
+static std::string remap_key(const Layout& S, const Layout& D, int64_t n) {
+  return "M" + layout_code(S) + ">" + layout_code(D) + size_class(n);
 }
 
 std::string tuning_key(const Layout& L, const adha_section* s, int64_t n, bool save) { return section_key(L, s, n, save); }
+std::string remap_tuning_key(const Layout& S, const Layout& D, int64_t n) { return remap_key(S, D, n); }
+
+void set_remap_pieces(int mode) { t_remap_pieces = mode; }
 
 void tuning_store(const std::string& key, int R, int wb) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -457,6 +474,12 @@ static int plan_remap(const Layout& S, const void* const* src_ptrs, const Layout
   for (int j : need) src_rec += S.stride[j];
   for (int d : build) dst_rec += D.stride[d];
   int R = t_tile_override ? t_tile_override : pick_remap_chunk(std::max(src_rec, dst_rec));
+  int tuned_pieces = -1;
+  if (!t_remap_pieces) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(remap_key(S, D, n));
+    if (it != g_tune.end()) tuned_pieces = it->second.second;
+  }
   for (;;) {
     a.n = n;
     a.R = R;
@@ -483,6 +506,14 @@ static int plan_remap(const Layout& S, const void* const* src_ptrs, const Layout
       }
     }
     a.out_bytes = off;
+    // piece tables: as forced or tuned for this pair of layouts, else for a buffer whose slices
+    // average under 256 bytes (two or more groups in each 512-byte warp step)
+    int staged_dst = 0;
+    for (int k = 0; k < a.n_dst; ++k) staged_dst += a.dst[k].start >= 0;
+    const bool narrow_in = a.in_bytes < 256 * a.n_src, narrow_out = staged_dst > 0 && a.out_bytes < 256 * staged_dst;
+    a.pieces = (narrow_in ? 1 : 0) | (narrow_out ? 2 : 0);
+    if (t_remap_pieces) a.pieces = t_remap_pieces - 1;
+    else if (tuned_pieces >= 0) a.pieces = tuned_pieces;
     a.n_moves = (int)moves.size();
     for (int c = 0; c < kMoveClasses; ++c) a.cls_count[c] = 0;
     for (size_t k = 0; k < idx.size(); ++k) {
@@ -910,7 +941,9 @@ int adha_tune_import(const char* text) {
     const size_t t1 = line.find('\t'), t2 = line.find('\t', t1 == std::string::npos ? 0 : t1 + 1);
     if (t1 == std::string::npos || t2 == std::string::npos) return fail(ADHA_EINVAL, "bad tuning line: %s", line.c_str());
     const int R = std::atoi(line.c_str() + t1 + 1), wb = std::atoi(line.c_str() + t2 + 1);
-    if (R < 0 || R > 128 || R % 32 || wb < 0 || wb > 2) return fail(ADHA_EINVAL, "bad tuning values: %s", line.c_str());
+    const bool remap = line[0] == 'M';
+    if (remap ? (R != 0 || wb < 0 || wb > 3) : (R < 0 || R > 128 || R % 32 || wb < 0 || wb > 2))
+      return fail(ADHA_EINVAL, "bad tuning values: %s", line.c_str());
     parsed[line.substr(0, t1)] = {R, wb};
   }
   std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -922,6 +955,13 @@ int adha_tune_remap_direct(int32_t mode) {
   clear_error();
   if (mode < 0 || mode > 1) return fail(ADHA_EINVAL, "remap direct mode %d not in [0, 1]", mode);
   t_remap_direct = mode;
+  return 0;
+}
+
+int adha_tune_remap_pieces(int32_t mode) {
+  clear_error();
+  if (mode < 0 || mode > 4) return fail(ADHA_EINVAL, "remap piece-table mode %d not in [0, 4]", mode);
+  t_remap_pieces = mode;
   return 0;
 }
 

@@ -88,6 +88,7 @@ struct RemapArgs {
   int32_t n_moves;
   int32_t cls_count[6];   // moves per class, in that order in `move`
   int32_t cls_order[6];   // per class: schedule order (see schedule_pair)
+  int32_t pieces;         // bit 0: stage through the per-CTA piece table, bit 1: write back through it
   GroupRef src[kMaxGroups];
   GroupRef dst[kMaxGroups];
   Move move[kMaxMoves];
@@ -118,24 +119,7 @@ struct SectionArgs {
   FieldRef f[kMaxFields];
   int32_t arg[8];
   float par[4];
-  float tanh_p[8], tanh_q[8];   // Plan + launch helpers shared by the entry points, the measurer and the executor.
-int remap_layouts(const Layout& S, const void* const* src_ptrs, const Layout& D, void* const* dst_ptrs, int64_t n,
-                  void* stream, int* launched);
-int run_section_layout(const Layout& L, void* const* ptrs, const adha_section* s, int64_t n, void* save,
-                       void* stream);
-adha_layout set_layout(const adha_layout_set* s, int l);
-// Remap launch arguments for one array (chunk_override 0 = the default chunk rule).
-int remap_plan_args(const Layout& S, const void* const* src_ptrs, const Layout& D, void* const* dst_ptrs, int64_t n,
-                    int chunk_override, int direct, RemapArgs* out, bool* empty);
-// Runs fn(ctx) bracketed by the launch profiler's events when profiling is on.
-int profiled_launch(int kind, int op, double bytes, void* stream, int (*fn)(const void*), const void* ctx);
-// Autotuning: the key of a section launch, storing its best shape, thread-local overrides.
-std::string tuning_key(const Layout& L, const adha_section* s, int64_t n, bool save);
-void tuning_store(const std::string& key, int R, int wb);
-void set_overrides(int R, int wb);
-int pdl_solve(const adha_cost_table* c, int return_to_input, int32_t* seq, double* total);
-
-// tanh polynomial coefficients (7 used each)
+  float tanh_p[8], tanh_q[8];   // tanh polynomial coefficients (7 used each)
   const int32_t* perm;
   uint8_t* save;                // NULL or n elements of the written field's type
   // MIX: field ids of the read set by type (ascending) and of the write set by type
@@ -172,6 +156,8 @@ int profiled_launch(int kind, int op, double bytes, void* stream, int (*fn)(cons
 std::string tuning_key(const Layout& L, const adha_section* s, int64_t n, bool save);
 void tuning_store(const std::string& key, int R, int wb);
 void set_overrides(int R, int wb);
+std::string remap_tuning_key(const Layout& S, const Layout& D, int64_t n);
+void set_remap_pieces(int mode);
 int pdl_solve(const adha_cost_table* c, int return_to_input, int32_t* seq, double* total);
 
 // tanh polynomial coefficients (Lambert's continued fraction cut after 25): 7 each, rounded once.

@@ -14,6 +14,9 @@
 //      transpose between the source and destination record strides; the host picks, per move
 //      class, the schedule order with the fewest shared-memory bank conflicts;
 //   3. it writes the assembled wider destination slices back with 16-byte stores.
+// Where each 16-byte piece of the two buffers lives in global memory is the same for every chunk
+// up to the chunk's offset; when a buffer's slices are narrower than a warp step (many groups
+// per step), a per-CTA table of the pieces replaces the search over the groups.
 // Global traffic is one contiguous read stream per source group and one write stream per
 // destination group.  The ragged tail (fewer than R records) goes move by move through the warp
 // that would own the next chunk.
@@ -27,19 +30,38 @@ namespace adha {
 
 __device__ __forceinline__ int align16(int x) { return (x + 15) & ~15; }
 
+// Where a 16-byte piece of a chunk buffer lives in global memory: base + chunk * step.
+struct Piece {
+  const uint8_t* base;
+  int64_t step;
+};
+
+// Piece q of a buffer holding the slices `grp` (staged ones, start >= 0) in buffer order.
+__device__ __forceinline__ Piece piece_of(int q, const GroupRef* grp, int R) {
+  const int p = q * 16;
+  int g = 0;
+  while (grp[g].start < 0 || p >= grp[g].start + R * grp[g].stride) ++g;
+  return Piece{grp[g].ptr + (p - grp[g].start), (int64_t)R * grp[g].stride};
+}
+
 template <bool DIRECT>
 __global__ void __launch_bounds__(kThreads) remap_kernel(const __grid_constant__ RemapArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
-  GroupRef* tin = reinterpret_cast<GroupRef*>(smem);
+  const int in_pieces = (a.pieces & 1) ? a.in_bytes / 16 : 0, out_pieces = (a.pieces & 2) ? a.out_bytes / 16 : 0;
+  Piece* pin = reinterpret_cast<Piece*>(smem);
+  Piece* pout = pin + in_pieces;
+  GroupRef* tin = reinterpret_cast<GroupRef*>(pout + out_pieces);
   GroupRef* tout = tin + a.n_src;
   const int n_entries = a.R * a.n_moves;
-  uint32_t* sched = reinterpret_cast<uint32_t*>(smem + align16((a.n_src + a.n_dst) * (int)sizeof(GroupRef)));
+  uint32_t* sched = reinterpret_cast<uint32_t*>(tout + a.n_dst);
   uint8_t* wbase = reinterpret_cast<uint8_t*>(sched) + align16(n_entries * 4);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   uint8_t* buf0 = wbase + (size_t)warp * (2 * a.in_bytes + a.out_bytes);
   uint8_t* buf1 = buf0 + a.in_bytes;
   uint8_t* outb = buf1 + a.in_bytes;
 
+  for (int q = tid; q < in_pieces; q += kThreads) pin[q] = piece_of(q, a.src, a.R);
+  for (int q = tid; q < out_pieces; q += kThreads) pout[q] = piece_of(q, a.dst, a.R);
   for (int k = tid; k < a.n_src; k += kThreads) tin[k] = a.src[k];
   for (int k = tid; k < a.n_dst; k += kThreads) tout[k] = a.dst[k];
   for (int t = tid; t < n_entries; t += kThreads)
@@ -48,11 +70,21 @@ __global__ void __launch_bounds__(kThreads) remap_kernel(const __grid_constant__
 
   const int64_t W = (int64_t)gridDim.x * kWarps;
   const int64_t R = a.R;
+  // lane l moves pieces l, l + 32, ... (16 bytes each: coalesced within every slice), finding
+  // each piece's group by a search that resumes where the last piece's ended, or in the table
   auto stage = [&](int64_t ch, uint8_t* buf) {
-    int g = 0;
-    for (int p = lane * 16; p < a.in_bytes; p += 512) {
-      while (p >= tin[g].start + a.R * tin[g].stride) ++g;
-      cp_async16(buf + p, tin[g].ptr + ch * R * tin[g].stride + (p - tin[g].start));
+    if (a.pieces & 1) {
+#pragma unroll 1
+      for (int q = lane; q < in_pieces; q += 32) {
+        const Piece pc = pin[q];
+        cp_async16(buf + q * 16, pc.base + ch * pc.step);
+      }
+    } else {
+      int g = 0;
+      for (int p = lane * 16; p < a.in_bytes; p += 512) {
+        while (p >= tin[g].start + a.R * tin[g].stride) ++g;
+        cp_async16(buf + p, tin[g].ptr + ch * R * tin[g].stride + (p - tin[g].start));
+      }
     }
   };
 
@@ -67,7 +99,16 @@ __global__ void __launch_bounds__(kThreads) remap_kernel(const __grid_constant__
     __syncwarp();
     move_chunk<DIRECT>(sched, a.R, a.cls_count, cur, outb, tout, c * R, lane);
     __syncwarp();
-    write_back<DIRECT>(tout, a.n_dst, a.R, a.out_bytes, outb, c, lane);
+    if (a.pieces & 2) {
+#pragma unroll 1
+      for (int q = lane; q < out_pieces; q += 32) {
+        const Piece pc = pout[q];
+        *reinterpret_cast<uint4*>(const_cast<uint8_t*>(pc.base) + c * pc.step) =
+            *reinterpret_cast<const uint4*>(outb + q * 16);
+      }
+    } else {
+      write_back<DIRECT>(tout, a.n_dst, a.R, a.out_bytes, outb, c, lane);
+    }
     __syncwarp();
   }
   cp_async_wait<0>();
@@ -79,7 +120,8 @@ __global__ void __launch_bounds__(kThreads) remap_kernel(const __grid_constant__
 
 size_t remap_smem_bytes(const RemapArgs& a) {
   auto al = [](size_t x) { return (x + 15) / 16 * 16; };
-  return al((size_t)(a.n_src + a.n_dst) * sizeof(GroupRef)) + al((size_t)a.R * a.n_moves * 4) +
+  const size_t pieces = ((a.pieces & 1) ? a.in_bytes / 16 : 0) + ((a.pieces & 2) ? a.out_bytes / 16 : 0);
+  return pieces * sizeof(Piece) + (size_t)(a.n_src + a.n_dst) * sizeof(GroupRef) + al((size_t)a.R * a.n_moves * 4) +
          (size_t)kWarps * (2 * (size_t)a.in_bytes + a.out_bytes);
 }
 

@@ -176,11 +176,33 @@ int adha_measure(const adha_schema* schema, int64_t n, const adha_layout* in_lay
     return code;
   };
   if (rc) return done(rc);
+  // A remap into or out of the input layout (every plan starts there, and may return there):
+  // under autotuning, timed with each choice of piece tables and the fastest kept.
+  auto time_remap = [&](const Layout& S, const std::vector<void*>& sp, const Layout& D, const std::vector<void*>& dp,
+                        bool tune, double* ns) {
+    auto run = [&] { return remap_layouts(S, sp.data(), D, const_cast<void**>(dp.data()), n, stream, nullptr); };
+    if (!tune || !(flags & ADHA_MEASURE_AUTOTUNE)) return time_ns(timer, stream, reps, run, ns);
+    double best = -1, t = 0;
+    int bits = 0;
+    for (int m = 1; m <= 4; ++m) {
+      set_remap_pieces(m);
+      const int e = time_ns(timer, stream, reps, run, &t);
+      set_remap_pieces(0);
+      if (e) return e;
+      if (best < 0 || t < best) {
+        best = t;
+        bits = m - 1;
+      }
+    }
+    tuning_store(remap_tuning_key(S, D, n), 0, bits);
+    *ns = best;
+    return 0;
+  };
   for (int a = 0; a < L && !rc; ++a) {
     // input -> a (identical groups stay where they are)
     carve_after(in, in_p, cand[a], n, B, &pb);
     double ns = 0;
-    rc = time_ns(timer, stream, reps, [&] { return remap_layouts(in, in_p.data(), cand[a], pb.data(), n, stream, nullptr); }, &ns);
+    rc = time_remap(in, in_p, cand[a], pb, true, &ns);
     if (rc) break;
     t->remap_ns[(size_t)L * (L + 1) + a] = ns;
     // a full private copy of the input in layout a, for the section and remap timings
@@ -216,7 +238,7 @@ int adha_measure(const adha_schema* schema, int64_t n, const adha_layout* in_lay
       const Layout& D = b < L ? cand[b] : in;
       if (same_layout(cand[a], D)) continue;
       carve_after(cand[a], pa, D, n, B, &pb);
-      rc = time_ns(timer, stream, reps, [&] { return remap_layouts(cand[a], pa.data(), D, pb.data(), n, stream, nullptr); }, &ns);
+      rc = time_remap(cand[a], pa, D, pb, b == L, &ns);
       t->remap_ns[(size_t)a * (L + 1) + b] = ns;
     }
   }

@@ -86,8 +86,10 @@ def test_program_with_ods_candidates(P, make, n, back, autotune):
     in_bufs = to_device(n, wl.dtypes, AOS.groups, fields)
     P.adha_tune_clear()
     costs = P.adha_measure(S, n, AOS, in_bufs, secs, cand, autotune=autotune)
-    if autotune:
-        assert len(P.adha_tune_export().splitlines()) == len(cand) * len(set(wl.sections))
+    if autotune:   # one entry per (section, candidate) and per remap from or to the input layout
+        lines = P.adha_tune_export().splitlines()
+        assert sum(1 for x in lines if x.startswith("S")) == len(cand) * len(set(wl.sections))
+        assert sum(1 for x in lines if x.startswith("M")) == len(cand) + sum(1 for l in cand.layouts if l != AOS)
     cost, seq = oracle.pdl_dp(costs.section_ns, costs.remap_ns, back)
     plan, lay, host = _run(P, wl, S, AOS, cand, secs, in_bufs, costs=costs, back=back)
     assert list(plan.layout_of_section[:len(wl.sections)]) == seq and plan.model_ns == cost

@@ -34,16 +34,37 @@ def _check_remap(P, n, dtypes, src, dst, fields):
 
 @pytest.mark.parametrize("seed", range(24))
 @pytest.mark.parametrize("n", [1, 17, 1000, 4099])
-@pytest.mark.parametrize("direct", [0, 1])
-def test_random_layouts(P, seed, n, direct):
+@pytest.mark.parametrize("direct,pieces", [(0, 0), (1, 0), (0, 2), (1, 1)])
+def test_random_layouts(P, seed, n, direct, pieces):
     rng = np.random.default_rng(1000 + seed)
     F = int(rng.integers(1, 24))
     dtypes = [int(x) for x in rng.integers(0, 4, F)]
     P.adha_tune_remap_direct(direct)
+    P.adha_tune_remap_pieces(pieces)
     try:
         _check_remap(P, n, dtypes, random_layout(rng, F), random_layout(rng, F), _random_bytes(rng, n, dtypes))
     finally:
         P.adha_tune_remap_direct(0)
+        P.adha_tune_remap_pieces(0)
+
+
+@pytest.mark.parametrize("n", [33, 4099, 100003])
+@pytest.mark.parametrize("pieces", [0, 1, 2])
+@pytest.mark.parametrize("chunk", [0, 8, 64])
+def test_aos_soa_many_narrow_fields(P, n, pieces, chunk):
+    """24 fp32 fields: 24 slices of 4 * chunk bytes per buffer, the case the piece tables are for."""
+    rng = np.random.default_rng(n + chunk)
+    dtypes = [0] * 24
+    f = _random_bytes(rng, n, dtypes)
+    P.adha_tune_remap_pieces(pieces)
+    P.adha_tune_override(chunk)
+    try:
+        _check_remap(P, n, dtypes, oracle.aos(24), oracle.soa(24), f)
+        _check_remap(P, n, dtypes, oracle.soa(24), oracle.aos(24), f)
+        _check_remap(P, n, dtypes, oracle.soa(24), [list(range(k, k + 3)) for k in range(0, 24, 3)], f)
+    finally:
+        P.adha_tune_remap_pieces(0)
+        P.adha_tune_override(0)
 
 
 @pytest.mark.parametrize("n", [1, 15, 16, 31, 32, 33, 191, 192, 193, 100003])
