@@ -2,12 +2,14 @@
 //
 // Each array (its own schema, record count and source/destination layouts) is cut into chunks
 // of R_a records, and its chunks into work blocks (about 2048 records per working warp).  A CTA holds a
-// fixed budget of shared memory for its warps' buffers; an array whose records are too wide for
-// eight warps' buffers in that budget is worked on by fewer warps of the CTA.  A CTA takes the next block
-// with one atomic ticket (a 64-bit counter in the caller's workspace, zeroed by a memset node
-// before every launch), builds the block's array's element schedule in shared memory when the
-// array changes, and its warps run the same double-buffered cp.async pipeline as remap.cu on
-// the block's chunks.  Blocks of small arrays and of large arrays are interleaved by the ticket
+// budget of shared memory for its warps' buffers, set when the batch is created from the number of
+// CTAs per SM (1 to 4) that gives the most working warps weighted by the arrays' bytes; an array
+// whose records are too wide for eight warps' buffers in that budget is worked on by fewer warps
+// of the CTA.  A CTA takes the next block with one atomic ticket (a 64-bit counter in the caller's
+// workspace, zeroed by a memset node before every launch), builds the block's array's element
+// schedule (and, where the array uses them, its piece tables) in shared memory when the array
+// changes, and its warps run the same double-buffered cp.async pipeline as remap.cu on the
+// block's chunks.  Blocks of small arrays and of large arrays are interleaved by the ticket
 // order, so uneven sizes balance across SMs without any waiting between CTAs.  The descriptors
 // live in the workspace; the launch (memset + kernel) can be captured in a CUDA graph.
 #include <cuda_runtime.h>
@@ -33,10 +35,11 @@ struct BatchHeader {
   int32_t warps;        // warps of a CTA that work on this array (the others idle for its blocks)
   int32_t chunks_per_warp;   // chunks of one working warp in one work block
   int32_t warp_bytes;   // shared bytes of one working warp: two input buffers and an output buffer
+  int32_t pieces;       // bit 0: stage through the piece table, bit 1: write back through it
 };
 
-// Shared bytes for the warps' buffers in one CTA: an array whose warp needs more uses fewer warps.
-constexpr int kWarpBufferBudget = 80 * 1024;
+// Warp bytes up to which the autotuner considers chunks longer than 32 records.
+constexpr int kTuneWarpBytes = 8 * 1024;
 
 struct BatchParams {
   unsigned long long* ticket;
@@ -47,6 +50,7 @@ struct BatchParams {
   int32_t n_arrays;
   int64_t total_blocks;
   int32_t max_entries;
+  int32_t max_pieces;        // piece-table entries of the array that needs the most
 };
 
 template <bool DIRECT>
@@ -59,9 +63,12 @@ __global__ void __launch_bounds__(kThreads) batched_kernel(const __grid_constant
   GroupRef* tout = tin + kMaxGroups;
   Move* moves = reinterpret_cast<Move*>(tout + kMaxGroups);
   uint32_t* sched = reinterpret_cast<uint32_t*>(moves + kMaxMoves);
+  Piece* pin = reinterpret_cast<Piece*>(sched + p.max_entries);   // max_entries is a multiple of 4
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  uint8_t* wbase = reinterpret_cast<uint8_t*>(sched + p.max_entries);
+  uint8_t* wbase = reinterpret_cast<uint8_t*>(pin + p.max_pieces);
   int cur = -1;
+  int in_pieces = 0, out_pieces = 0;
+  Piece* pout = pin;
 
   for (;;) {
     if (tid == 0) {
@@ -88,6 +95,11 @@ __global__ void __launch_bounds__(kThreads) batched_kernel(const __grid_constant
       __syncthreads();
       for (int t = tid; t < h.R * h.n_moves; t += kThreads)
         sched[t] = schedule_entry(t, h.R, h.cls_count, h.cls_order, moves, tin, tout);
+      in_pieces = (h.pieces & 1) ? h.in_bytes / 16 : 0;
+      out_pieces = (h.pieces & 2) ? h.out_bytes / 16 : 0;
+      pout = pin + in_pieces;
+      for (int q = tid; q < in_pieces; q += kThreads) pin[q] = piece_of(q, tin, h.R);
+      for (int q = tid; q < out_pieces; q += kThreads) pout[q] = piece_of(q, tout, h.R);
       __syncthreads();
       cur = arr;
     }
@@ -100,11 +112,20 @@ __global__ void __launch_bounds__(kThreads) batched_kernel(const __grid_constant
     uint8_t* outb = buf1 + h.in_bytes;
     const int64_t full_end = c_end < h.n_full ? c_end : h.n_full;
     const int64_t R = h.R;
+    const int in_bytes = h.in_bytes, pieces = h.pieces;
     auto stage = [&](int64_t ch, uint8_t* buf) {
-      int g = 0;
-      for (int q = lane * 16; q < h.in_bytes; q += 512) {
-        while (q >= tin[g].start + h.R * tin[g].stride) ++g;
-        cp_async16(buf + q, tin[g].ptr + ch * R * tin[g].stride + (q - tin[g].start));
+      if (pieces & 1) {
+#pragma unroll 1
+        for (int q = lane; q < in_pieces; q += 32) {
+          const Piece pc = pin[q];
+          cp_async16(buf + q * 16, pc.base + ch * pc.step);
+        }
+      } else {
+        int g = 0;
+        for (int q = lane * 16; q < in_bytes; q += 512) {
+          while (q >= tin[g].start + (int)R * tin[g].stride) ++g;
+          cp_async16(buf + q, tin[g].ptr + ch * R * tin[g].stride + (q - tin[g].start));
+        }
       }
     };
     int64_t c = warp < nw ? c_begin + warp : full_end;
@@ -118,7 +139,16 @@ __global__ void __launch_bounds__(kThreads) batched_kernel(const __grid_constant
       __syncwarp();
       move_chunk<DIRECT>(sched, h.R, h.cls_count, curb, outb, tout, c * R, lane);
       __syncwarp();
-      write_back<DIRECT>(tout, h.n_dst, h.R, h.out_bytes, outb, c, lane);
+      if (pieces & 2) {
+#pragma unroll 1
+        for (int q = lane; q < out_pieces; q += 32) {
+          const Piece pc = pout[q];
+          *reinterpret_cast<uint4*>(const_cast<uint8_t*>(pc.base) + c * pc.step) =
+              *reinterpret_cast<const uint4*>(outb + q * 16);
+        }
+      } else {
+        write_back<DIRECT>(tout, h.n_dst, h.R, h.out_bytes, outb, c, lane);
+      }
       __syncwarp();
     }
     cp_async_wait<0>();
@@ -138,7 +168,7 @@ struct adha_batched {
   std::vector<uint8_t> image;      // descriptor region as it is copied to the workspace
   size_t off_headers = 0, off_groups = 0, off_moves = 0, off_prefix = 0;
   int64_t total_blocks = 0;
-  int32_t max_entries = 0, warp_budget = kWarpBufferBudget;
+  int32_t max_entries = 0, max_pieces = 0, warp_budget = 0;
   size_t smem = 0;
   int grid = 1;
   double bytes = 0;
@@ -162,6 +192,7 @@ static BatchParams params_for(const adha_batched* b, void* ws) {
   p.n_arrays = b->n_arrays;
   p.total_blocks = b->total_blocks;
   p.max_entries = b->max_entries;
+  p.max_pieces = b->max_pieces;
   return p;
 }
 
@@ -188,39 +219,54 @@ static int batch_chunk(const Layout& S, const Layout& D) {
   return R;
 }
 
-// Chooses each array's chunk size: the default rule, or (autotune) the fastest of 32..256
-// records measured with the single-array remap kernel on the array's own buffers.
+// Chooses each array's chunk size, direct stores and piece tables: the default rules, or
+// (autotune) the fastest measured with the single-array remap kernel on the array's own buffers:
+// first 32..256 records x direct stores, then the four piece-table choices for the best of those.
 static int tune_chunk(const Layout& S, const void* const* sp, const Layout& D, void* const* dp, int64_t n, void* stream,
-                      int* best_R, int* best_direct) {
+                      int* best_R, int* best_direct, int* best_pieces) {
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return fail(ADHA_ECUDA, "cudaEventCreate");
-  float best = -1;
-  int rc = 0;
-  // 32..256 records: in the batched kernel occupancy is fixed by the buffer budget, so shorter
-  // chunks only add per-chunk overhead
-  for (int trial = 0; trial < 8 && !rc; ++trial) {
-    const int R = 32 << (trial >> 1), direct = trial & 1;
-    RemapArgs a;
-    bool empty = false;
-    rc = remap_plan_args(S, sp, D, dp, n, R, direct, &a, &empty);
-    if (rc || empty) break;
-    if (2 * a.in_bytes + a.out_bytes > kWarpBufferBudget / kWarps && R > 32) continue;   // keep 8 warps busy
+  auto time_ms = [&](int R, int direct, int pieces, float* ms) {
     adha_tune_override(R);
     adha_tune_remap_direct(direct);
+    adha_tune_remap_pieces(pieces);
+    int rc = 0;
     for (int w = 0; w < 2 && !rc; ++w) rc = remap_layouts(S, sp, D, dp, n, stream, nullptr);
     cudaEventRecord(e0, (cudaStream_t)stream);
     for (int w = 0; w < 3 && !rc; ++w) rc = remap_layouts(S, sp, D, dp, n, stream, nullptr);
     cudaEventRecord(e1, (cudaStream_t)stream);
     adha_tune_override(0);
     adha_tune_remap_direct(0);
-    if (rc) break;
+    adha_tune_remap_pieces(0);
+    if (rc) return rc;
     cudaEventSynchronize(e1);
-    float ms = 0;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (best < 0 || ms < best) {
+    cudaEventElapsedTime(ms, e0, e1);
+    return 0;
+  };
+  float best = -1, ms = 0;
+  int rc = 0;
+  // 32..256 records (shorter chunks only add per-chunk work); longer ones only while a warp's
+  // buffers stay small enough for a CTA's eight warps
+  for (int trial = 0; trial < 8 && !rc; ++trial) {
+    const int R = 32 << (trial >> 1), direct = trial & 1;
+    RemapArgs a;
+    bool empty = false;
+    rc = remap_plan_args(S, sp, D, dp, n, R, direct, &a, &empty);
+    if (rc || empty) break;
+    if (2 * a.in_bytes + a.out_bytes > kTuneWarpBytes && R > 32) continue;
+    rc = time_ms(R, direct, 0, &ms);
+    if (!rc && (best < 0 || ms < best)) {
       best = ms;
       *best_R = R;
       *best_direct = direct;
+      *best_pieces = a.pieces;
+    }
+  }
+  for (int m = 1; m <= 4 && !rc && best >= 0; ++m) {
+    rc = time_ms(*best_R, *best_direct, m, &ms);
+    if (!rc && ms < best) {
+      best = ms;
+      *best_pieces = m - 1;
     }
   }
   cudaEventDestroy(e0);
@@ -241,8 +287,8 @@ int adha_batched_create(int32_t n_arrays, const adha_remap_desc* descs, int32_t 
   std::vector<BatchHeader> headers;
   std::vector<GroupRef> groups;
   std::vector<Move> moves;
-  std::vector<int64_t> prefix;
-  int64_t blocks = 0;
+  std::vector<double> moved_bytes;   // per array, for the choice of CTAs per SM
+  int max_pieces = 0, max_warp = 0;
   for (int k = 0; k < n_arrays; ++k) {
     const adha_remap_desc& d = descs[k];
     Layout S, D;
@@ -257,9 +303,9 @@ int adha_batched_create(int32_t n_arrays, const adha_remap_desc* descs, int32_t 
         if (!d.dst_ptrs || !d.dst_ptrs[g] || reinterpret_cast<uintptr_t>(d.dst_ptrs[g]) % 16)
           rc = fail(ADHA_EINVAL, "array %d destination buffer %d is NULL or misaligned", k, g);
     }
-    int R = 0, direct = 0;
+    int R = 0, direct = 0, pieces = -1;
     if (!rc && d.n > 0 && (flags & ADHA_BATCHED_AUTOTUNE))
-      rc = tune_chunk(S, d.src_ptrs, D, d.dst_ptrs, d.n, stream, &R, &direct);
+      rc = tune_chunk(S, d.src_ptrs, D, d.dst_ptrs, d.n, stream, &R, &direct, &pieces);
     RemapArgs a;
     bool empty = true;
     if (!rc && d.n > 0) rc = remap_plan_args(S, d.src_ptrs, D, d.dst_ptrs, d.n, R ? R : batch_chunk(S, D), direct, &a, &empty);
@@ -269,8 +315,7 @@ int adha_batched_create(int32_t n_arrays, const adha_remap_desc* descs, int32_t 
     }
     BatchHeader h;
     std::memset(&h, 0, sizeof h);
-    h.block0 = blocks;
-    prefix.push_back(blocks);
+    double moved = 0;
     if (!empty) {
       h.n = a.n;
       h.R = a.R;
@@ -285,20 +330,18 @@ int adha_batched_create(int32_t n_arrays, const adha_remap_desc* descs, int32_t 
         h.cls_count[c] = a.cls_count[c];
         h.cls_order[c] = a.cls_order[c];
       }
+      h.pieces = pieces >= 0 ? pieces : a.pieces;
       b->direct = b->direct || (a.cls_count[0] + a.cls_count[1] + a.cls_count[2] > 0);
       h.group0 = (int32_t)groups.size();
       h.move0 = (int32_t)moves.size();
       h.warp_bytes = 2 * a.in_bytes + a.out_bytes;
-      h.warps = std::max(1, std::min(kWarps, kWarpBufferBudget / h.warp_bytes));
-      b->warp_budget = std::max(b->warp_budget, h.warps * h.warp_bytes);
+      max_warp = std::max(max_warp, h.warp_bytes);
+      max_pieces = std::max(max_pieces, ((h.pieces & 1) ? a.in_bytes / 16 : 0) + ((h.pieces & 2) ? a.out_bytes / 16 : 0));
       for (int g = 0; g < a.n_src; ++g) groups.push_back(a.src[g]);
       for (int g = 0; g < a.n_dst; ++g) groups.push_back(a.dst[g]);
       moves.insert(moves.end(), a.move, a.move + a.n_moves);
       h.chunks_per_warp = std::max(1, kBlockRecordsPerWarp / h.R);
-      const int64_t per_block = (int64_t)h.chunks_per_warp * h.warps;
-      blocks += (h.n_chunks + per_block - 1) / per_block;
       b->max_entries = std::max(b->max_entries, a.R * a.n_moves);
-      double moved = 0;
       for (int g = 0; g < D.n_groups; ++g) {
         bool alias = false;
         for (int j = 0; j < S.n_groups; ++j) alias = alias || (same_group(D, g, S, j) && d.dst_ptrs[g] == d.src_ptrs[j]);
@@ -307,7 +350,62 @@ int adha_batched_create(int32_t n_arrays, const adha_remap_desc* descs, int32_t 
       }
       b->bytes += 2.0 * moved * (double)d.n;
     }
+    moved_bytes.push_back(2.0 * moved * (double)d.n);
     headers.push_back(h);
+  }
+  b->max_entries = (b->max_entries + 3) / 4 * 4;
+  b->max_pieces = max_pieces;
+
+  // CTAs per SM: 1..4, each with the shared memory left by the others; the warp-buffer budget is
+  // what remains after the tables.  The choice maximises the working warps per SM weighted by
+  // each array's bytes (an array gets as many warps of a CTA as its buffers fit, at most 8).
+  int sms = 0, dev = 0, sm_smem = 0, reserved = 0, optin = 0;
+  if (int rc = sm_count(&sms)) {
+    delete b;
+    return rc;
+  }
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  auto* kern = b->direct ? batched_kernel<true> : batched_kernel<false>;
+  cudaFuncAttributes fa;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
+  if (e != cudaSuccess) {
+    delete b;
+    return cuda_fail(e, "device attributes for the batched kernel");
+  }
+  const size_t fixed = (size_t)2 * kMaxGroups * sizeof(GroupRef) + kMaxMoves * sizeof(Move) +
+                       (size_t)b->max_entries * 4 + (size_t)max_pieces * sizeof(Piece);
+  double best_score = -1;
+  for (int k = 1; k <= 4; ++k) {
+    const int64_t dyn = std::min<int64_t>(optin, (int64_t)sm_smem / k - reserved - (int64_t)fa.sharedSizeBytes) / 16 * 16;
+    const int64_t budget = dyn - (int64_t)fixed;
+    if (budget < std::max(max_warp, 1)) continue;
+    double score = 0;
+    for (size_t a = 0; a < headers.size(); ++a)
+      if (headers[a].warp_bytes > 0)
+        score += moved_bytes[a] * k * std::min<int64_t>(kWarps, budget / headers[a].warp_bytes);
+    if (score > best_score) {
+      best_score = score;
+      b->warp_budget = (int32_t)budget;
+    }
+  }
+  if (best_score < 0) {
+    const size_t need = fixed + (size_t)max_warp;
+    delete b;
+    return fail(ADHA_ENOTIMPL, "batched remap needs %zu bytes of shared memory per CTA (limit %d): an array is too wide",
+                need, optin);
+  }
+  std::vector<int64_t> prefix;
+  int64_t blocks = 0;
+  for (BatchHeader& h : headers) {
+    h.block0 = blocks;
+    prefix.push_back(blocks);
+    if (h.warp_bytes == 0) continue;
+    h.warps = (int32_t)std::max(1, std::min(kWarps, b->warp_budget / h.warp_bytes));
+    const int64_t per_block = (int64_t)h.chunks_per_warp * h.warps;
+    blocks += (h.n_chunks + per_block - 1) / per_block;
   }
   prefix.push_back(blocks);
   b->n_arrays = n_arrays;
@@ -321,22 +419,9 @@ int adha_batched_create(int32_t n_arrays, const adha_remap_desc* descs, int32_t 
   if (!groups.empty()) std::memcpy(b->image.data() + b->off_groups, groups.data(), groups.size() * sizeof(GroupRef));
   if (!moves.empty()) std::memcpy(b->image.data() + b->off_moves, moves.data(), moves.size() * sizeof(Move));
   std::memcpy(b->image.data() + b->off_prefix, prefix.data(), prefix.size() * sizeof(int64_t));
-  b->max_entries = (b->max_entries + 3) / 4 * 4;
-  b->smem = (size_t)2 * kMaxGroups * sizeof(GroupRef) + kMaxMoves * sizeof(Move) + (size_t)b->max_entries * 4 +
-            (size_t)b->warp_budget;
-  if (b->smem > (size_t)kSmemLimit - 1024) {
-    const size_t need = b->smem;
-    delete b;
-    return fail(ADHA_ENOTIMPL, "batched remap needs %zu bytes of shared memory per CTA (limit %d): an array is too wide",
-                need, kSmemLimit);
-  }
-  int sms = 0, per_sm = 0;
-  if (int rc = sm_count(&sms)) {
-    delete b;
-    return rc;
-  }
-  auto* kern = b->direct ? batched_kernel<true> : batched_kernel<false>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+  b->smem = fixed + (size_t)b->warp_budget;
+  int per_sm = 0;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, b->smem);
   if (e != cudaSuccess) {
     delete b;

@@ -30,20 +30,6 @@ namespace adha {
 
 __device__ __forceinline__ int align16(int x) { return (x + 15) & ~15; }
 
-// Where a 16-byte piece of a chunk buffer lives in global memory: base + chunk * step.
-struct Piece {
-  const uint8_t* base;
-  int64_t step;
-};
-
-// Piece q of a buffer holding the slices `grp` (staged ones, start >= 0) in buffer order.
-__device__ __forceinline__ Piece piece_of(int q, const GroupRef* grp, int R) {
-  const int p = q * 16;
-  int g = 0;
-  while (grp[g].start < 0 || p >= grp[g].start + R * grp[g].stride) ++g;
-  return Piece{grp[g].ptr + (p - grp[g].start), (int64_t)R * grp[g].stride};
-}
-
 template <bool DIRECT>
 __global__ void __launch_bounds__(kThreads) remap_kernel(const __grid_constant__ RemapArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];

@@ -128,4 +128,18 @@ __device__ __forceinline__ void write_back(const GroupRef* dst, int n_dst, int R
   (void)n_dst;
 }
 
+// Where a 16-byte piece of a chunk buffer lives in global memory: base + chunk * step.
+struct Piece {
+  const uint8_t* base;
+  int64_t step;
+};
+
+// Piece q of a buffer holding the slices `grp` (staged ones, start >= 0) in buffer order.
+__device__ __forceinline__ Piece piece_of(int q, const GroupRef* grp, int R) {
+  const int p = q * 16;
+  int g = 0;
+  while (grp[g].start < 0 || p >= grp[g].start + R * grp[g].stride) ++g;
+  return Piece{grp[g].ptr + (p - grp[g].start), (int64_t)R * grp[g].stride};
+}
+
 }  // namespace adha
