@@ -56,6 +56,7 @@ enum {
 
 #define ADHA_MAX_FIELDS 64
 #define ADHA_MAX_SECTIONS 256
+#define ADHA_MAX_FUSED 16      /* sections in one fused run (adha_run_sections_fused) */
 
 typedef enum { ADHA_F32 = 0, ADHA_F64 = 1, ADHA_I32 = 2, ADHA_BF16 = 3 } adha_dtype;
 
@@ -159,6 +160,20 @@ int adha_run_section(const adha_schema* schema, int64_t n, const adha_layout* la
                      const adha_section* section, void* save, adha_stream stream);
 
 /*
+ * Run sections[0..n_sec) in place on n records stored in `layout`, in one pass
+ * (paper Section 2: the combine edge joins consecutive sections into one node):
+ * per chunk of records, every group holding a field some section reads or
+ * writes is staged once, the sections are applied in order, and groups with
+ * written fields are written back whole.  The result equals running the
+ * sections one after another with adha_run_section.  Requirements (EINVAL
+ * otherwise): 1 <= n_sec <= ADHA_MAX_FUSED, each section valid alone, all
+ * gathers of the run use the same perm, and no section of the run writes a
+ * field that a gather of the run reads through perm.  Async on `stream`.
+ */
+int adha_run_sections_fused(const adha_schema* schema, int64_t n, const adha_layout* layout, void* const* ptrs,
+                            const adha_section* sections, int32_t n_sec, adha_stream stream);
+
+/*
  * Reverse of one AXPB, MUL or TANH section for the chain gradient: restores
  * the overwritten field z from `save` (written by adha_run_section) in the
  * state buffers, then updates the adjoint buffers `grad_ptrs` (same layout,
@@ -182,6 +197,9 @@ typedef struct {
   int32_t include_aos_soa;  /* 1: the candidate list starts with AoS and SoA                        */
   int32_t max_candidates;   /* keep the first this many candidates (0 = all)                        */
   int32_t return_to_input;  /* PDL adds the remap back to the input layout after the last section  */
+  int32_t fuse_window;      /* PDL may also run up to this many consecutive sections fused in one
+                               layout (the combine node; needs a cost table measured with
+                               ADHA_MEASURE_FUSE); <= 1: every section alone                         */
 } adha_plan_opts;
 
 /* A list of layouts over n_fields fields: layout l has n_groups[l] groups; its group
@@ -198,13 +216,18 @@ typedef struct {
 /* Measured costs in whole nanoseconds (stored as doubles, so sums are exact):
  * section_ns[k*n_layouts + l] = time of section k in candidate l;
  * remap_ns[a*(n_layouts+1) + b] = time of the remap from a to b, where index
- * n_layouts stands for the input layout and identical groups cost nothing.
+ * n_layouts stands for the input layout and identical groups cost nothing;
+ * with max_window >= 2, fused_ns[(k*max_window + m-1)*n_layouts + l] = time of
+ * sections k..k+m-1 run fused in candidate l (2 <= m <= max_window; +inf where
+ * the run may not be fused or was not measured; the m = 1 entries are unused).
  * Host memory, freed with adha_free. */
 typedef struct {
   int32_t n_sections;
   int32_t n_layouts;
   double* section_ns;
   double* remap_ns;
+  int32_t max_window;   /* 0: no fused runs (fused_ns NULL) */
+  double* fused_ns;
 } adha_cost_table;
 
 /*
@@ -236,6 +259,10 @@ int adha_layout_set_create(int32_t n_fields, int32_t n_layouts, const adha_layou
 /* A zeroed library-owned cost table of the given size (to fill by hand or in tests). */
 int adha_cost_table_create(int32_t n_sections, int32_t n_layouts, adha_cost_table** out);
 
+/* The same with room for fused runs of up to max_window (0, or 2..ADHA_MAX_FUSED)
+ * sections, all +inf.  Host only. */
+int adha_cost_table_create_fused(int32_t n_sections, int32_t n_layouts, int32_t max_window, adha_cost_table** out);
+
 /*
  * PDL (paper Section 2, "program data-layout"): the shortest path through the
  * layered DAG input -> (section 1, l) -> ... -> (section S, l), node weight
@@ -246,6 +273,22 @@ int adha_cost_table_create(int32_t n_sections, int32_t n_layouts, adha_cost_tabl
  */
 int adha_pdl_solve(const adha_cost_table* costs, int32_t return_to_input, int32_t* layout_of_section,
                    double* total_ns);
+
+/*
+ * PDL with combine nodes (paper Section 2: consecutive sections joined into one
+ * node of the DAG): besides every section alone, any run of 2..max_window
+ * consecutive sections may be one node, run fused in one layout at the cost
+ * fused_ns.  A path is a sequence of windows, each with a layout; its cost is
+ * the sum of the remaps between consecutive windows' layouts (zero when the
+ * layout stays), the windows' costs, and the remap back if return_to_input.
+ * Ties go to the smaller layout index, then the longer window, window by window
+ * from the first.  Writes layout_of_section[n_sections] (every section of a
+ * window gets the window's layout), window_len[n_sections] (the window length at
+ * the window's first section, 0 at the others) and the path cost.  max_window
+ * <= 1 gives adha_pdl_solve's path with every window_len 1.  Host only.
+ */
+int adha_pdl_solve_fused(const adha_cost_table* costs, int32_t return_to_input, int32_t max_window,
+                         int32_t* layout_of_section, int32_t* window_len, double* total_ns);
 
 /* ----------------------------------------------------------- measure and run */
 
@@ -260,10 +303,13 @@ typedef struct {
   int32_t final_layout;                           /* out: candidate equal to the result's layout, -1 if none */
   int32_t final_n_groups;                         /* out: groups of the result's layout */
   void* final_ptrs[ADHA_MAX_FIELDS];              /* out: device buffers of the result's groups */
+  int32_t window_len[ADHA_MAX_SECTIONS];          /* out (in when fixed): sections run fused from section k
+                                                     (0 inside a window); all 0 when fixed = each alone */
 } adha_plan;
 
 /* adha_measure flags. */
 #define ADHA_MEASURE_AUTOTUNE 1   /* time every section launch shape, keep the fastest for later launches */
+#define ADHA_MEASURE_FUSE(w) ((int32_t)(w) << 8)   /* also time every fusable run of 2..w sections (w <= 16) */
 
 /* Workspace bytes adha_measure needs: two copies of the widest candidate (or input) layout. */
 size_t adha_measure_workspace_bytes(const adha_schema* schema, int64_t n, const adha_layout* in_layout,
@@ -468,7 +514,8 @@ int adha_tune_export(char* buf, size_t len, size_t* needed);
 int adha_tune_import(const char* text);
 
 /* One kernel launch seen by the profiler.  kind: 0 remap, 1 section, 2 section
- * backward, 3 batched remap; op: the section's adha_op (0 for remaps); bytes:
+ * backward, 3 batched remap, 4 fused run; op: the section's adha_op (0 for
+ * remaps; the number of sections for a fused run); bytes:
  * the algorithmic bytes the launch had to move (data bytes of the moved or
  * accessed fields, not padding or untouched fields); ms: its duration between
  * two CUDA events recorded around it on its stream. */

@@ -7,7 +7,8 @@ this package.  It shares no code with the CUDA path and never imports it.
                       (plain scalar C, every float operation rounded on its own).
   * planner.py     -- affinity graph, greedy grouping (ODS), candidate set, and the
                       program layout choice (PDL) by dynamic programming and by
-                      exhaustive enumeration.
+                      exhaustive enumeration, also with combine nodes (runs of
+                      consecutive sections fused in one layout).
   * program.py     -- runs a workload's sections on field arrays, whole or for a
                       sample of records.
 
@@ -18,5 +19,8 @@ from .core import (  # noqa: F401
     build, group_layout, layout_info, remap, to_fields, from_fields, tanhf, tanh_coeffs, section,
     chain_grad, aos, soa, canon,
 )
-from .planner import affinity, ods, candidates, pdl_dp, pdl_exhaustive, program_cost  # noqa: F401
+from .planner import (  # noqa: F401
+    affinity, ods, candidates, pdl_dp, pdl_exhaustive, program_cost, pdl_dp_fused, pdl_exhaustive_fused,
+    fused_program_cost,
+)
 from .program import run_program_fields, sample_program, initial_fields  # noqa: F401

@@ -127,3 +127,86 @@ def pdl_dp(sec_cost, remap_cost, return_to_input=False):
         seq.append(m)
         prev = m
     return total, seq
+
+
+# ---------------------------------------------------------------------- PDL with combine nodes
+# Paper Section 2: the combine edge joins consecutive sections into one node of the DAG.  Here a
+# node may be a window of m consecutive sections run in one layout (fused when m >= 2) at a
+# measured cost fused_cost[(k, m)][l]; a plan is a sequence of windows (layout, length) that
+# covers the sections in order.  Ties: the smaller layout, then the longer window, window by
+# window from the first (the lexicographically smallest list of (layout, -length) pairs).
+
+def fused_program_cost(windows, sec_cost, remap_cost, fused_cost, return_to_input=False):
+    """Model cost of one plan given as [(layout, length), ...] (input layout = index L)."""
+    L = len(sec_cost[0])
+    prev, k, total = L, 0, 0
+    for l, m in windows:
+        total += remap_cost[prev][l] + (sec_cost[k][l] if m == 1 else fused_cost[(k, m)][l])
+        prev, k = l, k + m
+    if return_to_input:
+        total += remap_cost[prev][L]
+    return total
+
+
+def _compositions(S, W):
+    """Every way to cut S sections into consecutive windows of 1..W sections."""
+    if S == 0:
+        yield []
+        return
+    for m in range(1, min(W, S) + 1):
+        for rest in _compositions(S - m, W):
+            yield [m] + rest
+
+
+def _as_plan(windows, S):
+    seq, win = [], []
+    for l, m in windows:
+        seq += [l] * m
+        win += [m] + [0] * (m - 1)
+    return seq, win
+
+
+def pdl_exhaustive_fused(sec_cost, remap_cost, fused_cost, max_window, return_to_input=False):
+    """Brute force over every cut into windows and every layout per window:
+    (min cost, layout per section, window length at each window's first section and 0 inside)."""
+    S, L = len(sec_cost), len(sec_cost[0])
+    best = None
+    for cut in _compositions(S, max(1, max_window)):
+        for lays in itertools.product(range(L), repeat=len(cut)):
+            windows = list(zip(lays, cut))
+            key = (fused_program_cost(windows, sec_cost, remap_cost, fused_cost, return_to_input),
+                   [(l, -m) for l, m in windows])
+            if best is None or key < best[0]:
+                best = (key, windows)
+    seq, win = _as_plan(best[1], S)
+    return best[0][0], seq, win
+
+
+def pdl_dp_fused(sec_cost, remap_cost, fused_cost, max_window, return_to_input=False):
+    """Shortest path with combine nodes: (min cost, layout per section, window lengths).
+
+    rest[k][p] = cheapest cost of sections k..S-1 (and the final remap) when the data is in
+    layout p before section k (p = L: the input layout); the path is read forwards, taking
+    the smallest layout, then the longest window, among the choices that reach the minimum.
+    """
+    S, L = len(sec_cost), len(sec_cost[0])
+    W = max(1, max_window)
+
+    def cost(k, m, l):
+        return sec_cost[k][l] if m == 1 else fused_cost[(k, m)][l]
+
+    rest = [[0] * (L + 1) for _ in range(S + 1)]
+    for p in range(L + 1):
+        rest[S][p] = remap_cost[p][L] if return_to_input else 0
+    choices = lambda k, p: [(remap_cost[p][l] + cost(k, m, l) + rest[k + m][l], l, -m)
+                            for l in range(L) for m in range(1, min(W, S - k) + 1)]
+    for k in range(S - 1, -1, -1):
+        for p in range(L + 1):
+            rest[k][p] = min(c[0] for c in choices(k, p))
+    windows, p, k = [], L, 0
+    while k < S:
+        c, l, negm = min(choices(k, p))
+        windows.append((l, -negm))
+        p, k = l, k - negm
+    seq, win = _as_plan(windows, S)
+    return rest[0][L], seq, win

@@ -31,7 +31,7 @@ class adha_section(ctypes.Structure):
 
 class adha_plan_opts(ctypes.Structure):
     _fields_ = [("n_caps", _I32), ("caps", ctypes.POINTER(_I32)), ("max_window", _I32), ("include_aos_soa", _I32),
-                ("max_candidates", _I32), ("return_to_input", _I32)]
+                ("max_candidates", _I32), ("return_to_input", _I32), ("fuse_window", _I32)]
 
 
 class adha_layout_set(ctypes.Structure):
@@ -41,17 +41,19 @@ class adha_layout_set(ctypes.Structure):
 
 class adha_cost_table(ctypes.Structure):
     _fields_ = [("n_sections", _I32), ("n_layouts", _I32), ("section_ns", ctypes.POINTER(ctypes.c_double)),
-                ("remap_ns", ctypes.POINTER(ctypes.c_double))]
+                ("remap_ns", ctypes.POINTER(ctypes.c_double)), ("max_window", _I32),
+                ("fused_ns", ctypes.POINTER(ctypes.c_double))]
 
 
 MAX_SECTIONS = 256
 MAX_FIELDS = 64
+MAX_FUSED = 16
 
 
 class adha_plan(ctypes.Structure):
     _fields_ = [("fixed", _I32), ("n_sections", _I32), ("layout_of_section", _I32 * MAX_SECTIONS),
                 ("model_ns", ctypes.c_double), ("n_remaps", _I32), ("n_launches", _I32), ("final_layout", _I32),
-                ("final_n_groups", _I32), ("final_ptrs", _P * MAX_FIELDS)]
+                ("final_n_groups", _I32), ("final_ptrs", _P * MAX_FIELDS), ("window_len", _I32 * MAX_SECTIONS)]
 
 
 class adha_launch_record(ctypes.Structure):
@@ -82,6 +84,8 @@ SIGNATURES = {
                                   ctypes.POINTER(adha_layout), _PP, _P]),
     "adha_run_section": (ctypes.c_int, [ctypes.POINTER(adha_schema), _I64, ctypes.POINTER(adha_layout), _PP,
                                         ctypes.POINTER(adha_section), _P, _P]),
+    "adha_run_sections_fused": (ctypes.c_int, [ctypes.POINTER(adha_schema), _I64, ctypes.POINTER(adha_layout), _PP,
+                                               ctypes.POINTER(adha_section), _I32, _P]),
     "adha_section_backward": (ctypes.c_int, [ctypes.POINTER(adha_schema), _I64, ctypes.POINTER(adha_layout), _PP,
                                              _PP, ctypes.POINTER(adha_section), _P, _P]),
     "adha_device_status": (ctypes.c_int, [_P, ctypes.POINTER(_I32)]),
@@ -110,8 +114,11 @@ SIGNATURES = {
     "adha_layout_set_create": (ctypes.c_int, [_I32, _I32, ctypes.POINTER(adha_layout),
                                               ctypes.POINTER(ctypes.POINTER(adha_layout_set))]),
     "adha_cost_table_create": (ctypes.c_int, [_I32, _I32, ctypes.POINTER(ctypes.POINTER(adha_cost_table))]),
+    "adha_cost_table_create_fused": (ctypes.c_int, [_I32, _I32, _I32, ctypes.POINTER(ctypes.POINTER(adha_cost_table))]),
     "adha_pdl_solve": (ctypes.c_int, [ctypes.POINTER(adha_cost_table), _I32, ctypes.POINTER(_I32),
                                       ctypes.POINTER(ctypes.c_double)]),
+    "adha_pdl_solve_fused": (ctypes.c_int, [ctypes.POINTER(adha_cost_table), _I32, _I32, ctypes.POINTER(_I32),
+                                            ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_double)]),
     "adha_measure_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(adha_schema), _I64, ctypes.POINTER(adha_layout),
                                                        ctypes.POINTER(adha_layout_set)]),
     "adha_measure": (ctypes.c_int, [ctypes.POINTER(adha_schema), _I64, ctypes.POINTER(adha_layout), _PP,

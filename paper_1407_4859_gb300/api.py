@@ -120,6 +120,13 @@ def adha_run_section(schema, n, layout, bufs, section, save=None, stream=None):
                                        _stream_ptr(stream)), "adha_run_section")
 
 
+def adha_run_sections_fused(schema, n, layout, bufs, sections, stream=None):
+    """sections: a Sections (or list of synth.Section / adha_section) run fused in one pass."""
+    secs = sections if isinstance(sections, Sections) else Sections(sections)
+    check(_lib.load().adha_run_sections_fused(ctypes.byref(schema.c), int(n), ctypes.byref(layout.c), _ptrs(bufs),
+                                              secs.arr, len(secs), _stream_ptr(stream)), "adha_run_sections_fused")
+
+
 def adha_section_backward(schema, n, layout, state_bufs, grad_bufs, section, save, stream=None):
     check(_lib.load().adha_section_backward(ctypes.byref(schema.c), int(n), ctypes.byref(layout.c),
                                             _ptrs(state_bufs), _ptrs(grad_bufs), ctypes.byref(section),
@@ -174,13 +181,14 @@ def remap(schema, n, src_layout, src_bufs, dst_layout, stream=None):
 # ------------------------------------------------------------------ planning, measuring, running
 
 class PlanOpts:
-    """adha_plan_opts: ODS struct-size limits, window length, candidate cap, return to input."""
+    """adha_plan_opts: ODS struct-size limits, window length, candidate cap, return to input, and the
+    longest run of sections PDL may fuse (fuse_window <= 1: none)."""
 
     def __init__(self, caps=(16, 32, 64, 128, 256, 0), max_window=0, include_aos_soa=True, max_candidates=0,
-                 return_to_input=False):
+                 return_to_input=False, fuse_window=0):
         self._caps = _i32_array(list(caps))
         self.c = adha_plan_opts(len(caps), self._caps, int(max_window), int(bool(include_aos_soa)),
-                                int(max_candidates), int(bool(return_to_input)))
+                                int(max_candidates), int(bool(return_to_input)), int(fuse_window))
 
 
 class Sections:
@@ -243,7 +251,23 @@ class CostTable:
         L = t.n_layouts + 1
         return [[t.remap_ns[a * L + b] for b in range(L)] for a in range(L)]
 
-    def set(self, section_ns, remap_ns):
+    @property
+    def max_window(self):
+        return self.ptr.contents.max_window
+
+    @property
+    def fused_ns(self):
+        """{(k, m): [ns per layout]} for the runs of m >= 2 sections starting at k (inf: not fusable)."""
+        t = self.ptr.contents
+        W, L = t.max_window, t.n_layouts
+        out = {}
+        for k in range(t.n_sections):
+            for m in range(2, W + 1):
+                if k + m <= t.n_sections:
+                    out[(k, m)] = [t.fused_ns[(k * W + m - 1) * L + l] for l in range(L)]
+        return out
+
+    def set(self, section_ns, remap_ns, fused_ns=None):
         t = self.ptr.contents
         for k, row in enumerate(section_ns):
             for l, v in enumerate(row):
@@ -251,6 +275,9 @@ class CostTable:
         for a, row in enumerate(remap_ns):
             for b, v in enumerate(row):
                 t.remap_ns[a * (t.n_layouts + 1) + b] = float(v)
+        for (k, m), row in (fused_ns or {}).items():
+            for l, v in enumerate(row):
+                t.fused_ns[(k * t.max_window + m - 1) * t.n_layouts + l] = float(v)
 
     def __del__(self):
         if getattr(self, "ptr", None) is not None and _lib._lib is not None:
@@ -288,9 +315,10 @@ def adha_layout_set_create(F, layouts):
     return LayoutSet(out)
 
 
-def adha_cost_table_create(n_sections, n_layouts):
+def adha_cost_table_create(n_sections, n_layouts, max_window=0):
     out = ctypes.POINTER(adha_cost_table)()
-    check(_lib.load().adha_cost_table_create(n_sections, n_layouts, ctypes.byref(out)), "adha_cost_table_create")
+    check(_lib.load().adha_cost_table_create_fused(n_sections, n_layouts, int(max_window), ctypes.byref(out)),
+          "adha_cost_table_create_fused")
     return CostTable(out)
 
 
@@ -302,6 +330,17 @@ def adha_pdl_solve(costs, return_to_input=False):
     return tot.value, list(seq)
 
 
+def adha_pdl_solve_fused(costs, return_to_input=False, max_window=0):
+    """(total ns, layout per section, window length per section: the run length at its first section, 0 inside)."""
+    S = costs.ptr.contents.n_sections
+    seq = (ctypes.c_int32 * S)()
+    win = (ctypes.c_int32 * S)()
+    tot = ctypes.c_double(0)
+    check(_lib.load().adha_pdl_solve_fused(costs.ptr, int(bool(return_to_input)), int(max_window), seq, win,
+                                           ctypes.byref(tot)), "adha_pdl_solve_fused")
+    return tot.value, list(seq), list(win)
+
+
 def adha_measure_workspace_bytes(schema, n, in_layout, candidates):
     return _lib.load().adha_measure_workspace_bytes(ctypes.byref(schema.c), int(n), ctypes.byref(in_layout.c),
                                                     candidates.ptr)
@@ -311,15 +350,17 @@ ADHA_MEASURE_AUTOTUNE = 1
 
 
 def adha_measure(schema, n, in_layout, in_bufs, sections, candidates, reps=2, workspace=None, stream=None,
-                 autotune=False):
-    """Cost table of every section in every candidate and every remap between candidates."""
+                 autotune=False, fuse_window=0):
+    """Cost table of every section in every candidate and every remap between candidates (and, with
+    fuse_window >= 2, of every run of 2..fuse_window sections that may be fused)."""
     secs = sections if isinstance(sections, Sections) else Sections(sections)
     need = adha_measure_workspace_bytes(schema, n, in_layout, candidates)
     ws = workspace if workspace is not None else torch.empty(need, dtype=torch.uint8, device=in_bufs[0].device)
     out = ctypes.POINTER(adha_cost_table)()
     check(_lib.load().adha_measure(ctypes.byref(schema.c), int(n), ctypes.byref(in_layout.c), _ptrs(in_bufs),
                                    secs.arr, len(secs), candidates.ptr, int(reps),
-                                   ADHA_MEASURE_AUTOTUNE if autotune else 0, ws.data_ptr(), ws.numel(),
+                                   (ADHA_MEASURE_AUTOTUNE if autotune else 0) | (int(fuse_window) << 8),
+                                   ws.data_ptr(), ws.numel(),
                                    _stream_ptr(stream), ctypes.byref(out)), "adha_measure")
     return CostTable(out)
 
@@ -329,18 +370,26 @@ def adha_program_workspace_bytes(schema, n, in_layout, candidates):
                                                     candidates.ptr)
 
 
-def adha_run_program(schema, n, in_layout, in_bufs, sections, candidates, costs=None, opts=None, workspace=None,
-                     fixed=None, stream=None, plan=None):
-    """Runs the program; returns the adha_plan (layout per section, final buffers' pointers)."""
-    secs = sections if isinstance(sections, Sections) else Sections(sections)
-    opts = opts or PlanOpts()
-    if plan is None:
-        plan = adha_plan()
+def _fix_plan(plan, fixed, windows):
     plan.fixed = 0
     if fixed is not None:
         plan.fixed = 1
         for k, l in enumerate(fixed):
             plan.layout_of_section[k] = int(l)
+        for k in range(len(fixed)):
+            plan.window_len[k] = int(windows[k]) if windows is not None else 0
+
+
+def adha_run_program(schema, n, in_layout, in_bufs, sections, candidates, costs=None, opts=None, workspace=None,
+                     fixed=None, stream=None, plan=None, windows=None):
+    """Runs the program; returns the adha_plan (layout per section, fused windows, final buffers'
+    pointers).  fixed: a layout per section; windows: with fixed, the run length at each run's
+    first section and 0 inside (None: every section alone)."""
+    secs = sections if isinstance(sections, Sections) else Sections(sections)
+    opts = opts or PlanOpts()
+    if plan is None:
+        plan = adha_plan()
+    _fix_plan(plan, fixed, windows)
     check(_lib.load().adha_run_program(ctypes.byref(schema.c), int(n), ctypes.byref(in_layout.c), _ptrs(in_bufs),
                                        secs.arr, len(secs), candidates.ptr, costs.ptr if costs is not None else None,
                                        ctypes.byref(opts.c), workspace.data_ptr() if workspace is not None else None,
@@ -355,18 +404,14 @@ def adha_program_host_workspace_bytes(schema, n, in_layout, candidates, n_slices
 
 
 def adha_run_program_host(schema, n, in_layout, host_in, sections, candidates, host_out, costs=None, opts=None,
-                          workspace=None, n_slices=8, fixed=None, stream=None, plan=None):
+                          workspace=None, n_slices=8, fixed=None, stream=None, plan=None, windows=None):
     """Runs the program on host buffers (pinned CPU tensors), writing the result into host_out
     (CPU tensors in the plan's final layout); returns the adha_plan."""
     secs = sections if isinstance(sections, Sections) else Sections(sections)
     opts = opts or PlanOpts()
     if plan is None:
         plan = adha_plan()
-    plan.fixed = 0
-    if fixed is not None:
-        plan.fixed = 1
-        for k, l in enumerate(fixed):
-            plan.layout_of_section[k] = int(l)
+    _fix_plan(plan, fixed, windows)
     check(_lib.load().adha_run_program_host(ctypes.byref(schema.c), int(n), ctypes.byref(in_layout.c), _ptrs(host_in),
                                             secs.arr, len(secs), candidates.ptr,
                                             costs.ptr if costs is not None else None, ctypes.byref(opts.c),
@@ -394,7 +439,7 @@ def _view_device(ptr, nbytes):
     return torch.as_tensor(_Cuda(), device="cuda")
 
 
-KINDS = {0: "remap", 1: "section", 2: "section_backward", 3: "batched_remap"}
+KINDS = {0: "remap", 1: "section", 2: "section_backward", 3: "batched_remap", 4: "fused"}
 OP_NAMES = {v: k for k, v in OPS.items()}
 
 
@@ -407,7 +452,8 @@ def adha_profile_stop(max_records=4096):
     recs = (_lib.adha_launch_record * max_records)()
     n = ctypes.c_int32(0)
     check(_lib.load().adha_profile_stop(recs, max_records, ctypes.byref(n)), "adha_profile_stop")
-    return [dict(kind=KINDS.get(recs[k].kind, recs[k].kind), op=OP_NAMES.get(recs[k].op, recs[k].op),
+    return [dict(kind=KINDS.get(recs[k].kind, recs[k].kind),
+                 op=recs[k].op if recs[k].kind == 4 else OP_NAMES.get(recs[k].op, recs[k].op),
                  bytes=recs[k].bytes, ms=recs[k].ms) for k in range(min(n.value, max_records))]
 
 

@@ -397,7 +397,10 @@ static int cached_occupancy(int kind, size_t smem, int* blocks) {
       return 0;
     }
   }
-  const int rc = kind < 100 ? remap_occupancy(kind, smem, blocks) : section_occupancy(kind - 100, smem, blocks);
+  // kinds: < 100 remap (direct or not), 100 + op section, 200 + 10*M + vec fused run
+  const int rc = kind < 100    ? remap_occupancy(kind, smem, blocks)
+                 : kind < 200 ? section_occupancy(kind - 100, smem, blocks)
+                              : fused_occupancy((kind - 200) / 10, (kind - 200) % 10 != 0, smem, blocks);
   if (rc) return rc;
   std::lock_guard<std::mutex> lk(g_occ_mu);
   g_occ_cache[{kind, smem}] = *blocks;
@@ -534,6 +537,27 @@ static int plan_remap(const Layout& S, const void* const* src_ptrs, const Layout
 // ------------------------------------------------------------------ section planning
 static bool has(uint64_t m, int f) { return (m >> f) & 1ull; }
 
+// A section's operation and operands in the kernels' form: read and written fields grouped by
+// dtype, ascending ids within a dtype.
+void fill_secop(const Layout& L, const adha_section* s, SecOp* o) {
+  std::memset(o, 0, sizeof *o);
+  o->op = s->op;
+  for (int k = 0; k < 8; ++k) o->arg[k] = s->arg[k];
+  for (int k = 0; k < 4; ++k) o->par[k] = s->fparam[k];
+  int nr = 0, nw = 0;
+  for (int d = 0; d < 4; ++d) {
+    o->rd_off[d] = (int8_t)nr;
+    o->wr_off[d] = (int8_t)nw;
+    for (int f = 0; f < L.F; ++f) {
+      if (L.dtype[f] != d) continue;
+      if (has(s->read_mask, f)) o->rd[nr++] = (int8_t)f;
+      if (has(s->write_mask, f)) o->wr[nw++] = (int8_t)f;
+    }
+  }
+  o->rd_off[4] = (int8_t)nr;
+  o->wr_off[4] = (int8_t)nw;
+}
+
 static int check_section(const Layout& L, const adha_section* s, int64_t n, bool has_save) {
   if (!s) return fail(ADHA_EINVAL, "section is NULL");
   const int F = L.F;
@@ -630,9 +654,6 @@ static int plan_section(const Layout& L, void* const* ptrs, const adha_section* 
     a.R = R;
     a.n_chunks = n / R;
     a.F = L.F;
-    a.op = s->op;
-    a.R_mask = s->read_mask;
-    a.W_mask = s->write_mask;
     a.n_load = (int)groups.size();
     a.perm_slot = -1;
     for (int f = 0; f < L.F; ++f) {
@@ -685,13 +706,7 @@ static int plan_section(const Layout& L, void* const* ptrs, const adha_section* 
     if (R <= 32) return fail(ADHA_EINVAL, "section records too wide for a 32-record chunk");
     R /= 2;
   }
-  for (int k = 0; k < 8; ++k) a.arg[k] = s->arg[k];
-  for (int k = 0; k < 4; ++k) a.par[k] = s->fparam[k];
-  for (int f = 0; f < L.F; ++f) {
-    const int d = L.dtype[f];
-    if (has(s->read_mask, f)) a.rd[d][a.n_rd[d]++] = (int8_t)f;
-    if (has(s->write_mask, f)) a.wr[d][a.n_wr[d]++] = (int8_t)f;
-  }
+  fill_secop(L, s, &a.s);
   tanh_coefficients(a.tanh_p, a.tanh_q);
   a.perm = s->perm;
   a.save = static_cast<uint8_t*>(save);
@@ -761,6 +776,168 @@ int profiled_launch(int kind, int op, double bytes, void* stream, int (*fn)(cons
   return profiled(kind, op, bytes, stream, [&] { return fn(ctx); });
 }
 
+// ------------------------------------------------------------------ fused runs (combine)
+// A run of m consecutive sections in one pass: each section valid on its own, none with `save`,
+// every gather reading through the same permutation, and no field that a gather reads through
+// the permutation written by any section of the run (a record's sections then see exactly what
+// they would see run one after another).
+static int check_fused(const Layout& L, const adha_section* s, int m, int64_t n) {
+  if (!s) return fail(ADHA_EINVAL, "sections are NULL");
+  if (m < 1 || m > kMaxFused) return fail(ADHA_EINVAL, "a fused run holds 1..%d sections (got %d)", kMaxFused, m);
+  uint64_t written = 0, at_perm = 0;
+  const int32_t* perm = nullptr;
+  for (int k = 0; k < m; ++k) {
+    if (int rc = check_section(L, &s[k], n, false)) return rc;
+    written |= s[k].write_mask;
+    at_perm |= s[k].read_at_perm_mask;
+    if (s[k].op == ADHA_OP_GATHER) {
+      if (perm && s[k].perm != perm) return fail(ADHA_EINVAL, "the gathers of a fused run use different permutations");
+      perm = s[k].perm;
+    }
+  }
+  if (written & at_perm)
+    return fail(ADHA_EINVAL, "a section of the run writes a field that a gather of the run reads through perm");
+  if (n > 0 && perm && reinterpret_cast<uintptr_t>(perm) % 16) return fail(ADHA_EINVAL, "perm is not 16-byte aligned");
+  if (n > 0 && !perm && at_perm) return fail(ADHA_EINVAL, "gather without a permutation");
+  return 0;
+}
+
+// Whether sections s[0..m) may run fused (check_fused without leaving an error message behind).
+bool fusable_run(const Layout& L, const adha_section* s, int m) {
+  const std::string saved = t_err;
+  const int rc = check_fused(L, s, m, 1);
+  t_err = saved;
+  return rc == 0;
+}
+
+static std::string fused_key(const Layout& L, const adha_section* s, int m, int64_t n) {
+  std::string k = "F";
+  for (int j = 0; j < m; ++j) {
+    k += std::to_string(s[j].op) + ":" + std::to_string(s[j].read_mask) + ":" + std::to_string(s[j].write_mask) + ":" +
+         std::to_string(s[j].read_at_perm_mask) + ":";
+    for (int a = 0; a < 8; ++a) k += std::to_string(s[j].arg[a]) + ",";
+    k += ";";
+  }
+  return k + ":L" + layout_code(L) + size_class(n);
+}
+
+std::string fused_tuning_key(const Layout& L, const adha_section* s, int m, int64_t n) { return fused_key(L, s, m, n); }
+
+// Algorithmic bytes of a fused run: every field some section reads or writes, read once; every
+// written field written once; plus the permutation and the fields read through it.
+static double fused_bytes(const Layout& L, const adha_section* s, int m, int64_t n) {
+  uint64_t rw = 0, w = 0, p = 0;
+  bool gather = false;
+  for (int k = 0; k < m; ++k) {
+    rw |= s[k].read_mask | s[k].write_mask;
+    w |= s[k].write_mask;
+    p |= s[k].read_at_perm_mask;
+    gather = gather || s[k].op == ADHA_OP_GATHER;
+  }
+  double b = gather ? 4 : 0;
+  for (int f = 0; f < L.F; ++f) {
+    const int sz = dtype_size(L.dtype[f]);
+    b += (has(rw, f) ? sz : 0) + (has(w, f) ? sz : 0) + (has(p, f) ? sz : 0);
+  }
+  return b * (double)n;
+}
+
+struct FusedPlan {
+  FusedArgs args;
+  int grid = 0;
+  size_t smem = 0;
+};
+
+static int plan_fused(const Layout& L, void* const* ptrs, const adha_section* s, int m, int64_t n, FusedPlan* plan) {
+  FusedArgs& a = plan->args;
+  std::memset(&a, 0, sizeof a);
+  int tuned_R = t_tile_override;
+  if (!tuned_R) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(fused_key(L, s, m, n));
+    if (it != g_tune.end()) tuned_R = it->second.first;
+  }
+  uint64_t staged = 0, written = 0;
+  const int32_t* perm = nullptr;
+  for (int k = 0; k < m; ++k) {
+    staged |= s[k].read_mask | s[k].write_mask;
+    written |= s[k].write_mask;
+    if (s[k].op == ADHA_OP_GATHER) perm = s[k].perm;
+  }
+  std::vector<int> groups;
+  for (int g = 0; g < L.n_groups; ++g) {
+    bool any = false;
+    for (int f : L.groups[g]) any = any || has(staged, f);
+    if (any) groups.push_back(g);
+  }
+  int rec = perm ? 4 : 0;
+  for (int g : groups) rec += L.stride[g];
+  int R = tuned_R ? std::max(32, std::min(tuned_R, 128)) : (rec > 0 ? pick_chunk(rec, 4096, 128) : 128);
+  if (R != 32 && R != 64 && R != 128) R = R < 64 ? 32 : 64;
+  for (;;) {
+    a.n = n;
+    a.R = R;
+    a.n_chunks = n / R;
+    a.n_load = (int)groups.size();
+    a.perm_slot = -1;
+    for (int f = 0; f < L.F; ++f) {
+      const int g = L.group_of[f];
+      a.f[f].g = static_cast<uint8_t*>(ptrs[g]) + L.offset_of[f];
+      a.f[f].gs = L.stride[g];
+      a.f[f].s0 = -1;
+      a.f[f].dtype = L.dtype[f];
+    }
+    int off = 0;
+    bool vec = R >= 64;
+    for (int k = 0; k < a.n_load; ++k) {
+      const int g = groups[k];
+      a.load[k].ptr = static_cast<const uint8_t*>(ptrs[g]);
+      a.load[k].stride = L.stride[g];
+      a.load[k].start = off;
+      bool w = false;
+      for (int f : L.groups[g]) w = w || has(written, f);
+      a.writeback[k] = w ? 1 : 0;
+      for (int f : L.groups[g]) {
+        a.f[f].s0 = off + L.offset_of[f];
+        a.f[f].ss = L.stride[g];
+        a.f[f].wsm = 1;   // every write goes to the chunk buffer; written groups go back whole
+      }
+      vec = vec && L.groups[g].size() == 1;
+      off += R * L.stride[g];
+    }
+    if (perm) {
+      a.perm_slot = a.n_load;
+      a.writeback[a.n_load] = 0;
+      a.load[a.n_load].ptr = reinterpret_cast<const uint8_t*>(perm);
+      a.load[a.n_load].stride = 4;
+      a.load[a.n_load].start = off;
+      off += R * 4;
+    }
+    a.in_bytes = off;
+    a.vec = vec ? 1 : 0;
+    plan->smem = fused_smem_bytes(a);
+    if (plan->smem <= (size_t)kSmemLimit) break;
+    if (R <= 32) return fail(ADHA_EINVAL, "the fused run's records are too wide for a 32-record chunk");
+    R /= 2;
+  }
+  a.n_sec = m;
+  for (int k = 0; k < m; ++k) fill_secop(L, &s[k], &a.sec[k]);
+  tanh_coefficients(a.tanh_p, a.tanh_q);
+  a.perm = perm;
+  int blocks = 0;
+  const int M = R / 32;
+  if (int rc = cached_occupancy(200 + 10 * M + a.vec, plan->smem, &blocks)) return rc;
+  return finish_grid(a.n_chunks, blocks, &plan->grid);
+}
+
+int run_fused_layout(const Layout& L, void* const* ptrs, const adha_section* s, int m, int64_t n, void* stream) {
+  if (int rc = check_fused(L, s, m, n)) return rc;
+  if (n == 0) return 0;
+  FusedPlan plan;
+  if (int rc = plan_fused(L, ptrs, s, m, n, &plan)) return rc;
+  return profiled(4, m, fused_bytes(L, s, m, n), stream, [&] { return launch_fused(plan.args, plan.grid, plan.smem, stream); });
+}
+
 int run_section_layout(const Layout& L, void* const* ptrs, const adha_section* s, int64_t n, void* save, void* stream) {
   if (int rc = check_section(L, s, n, save != nullptr)) return rc;
   if (n == 0) return 0;
@@ -819,6 +996,18 @@ int adha_run_section(const adha_schema* schema, int64_t n, const adha_layout* la
   if (section->op == ADHA_OP_GATHER && reinterpret_cast<uintptr_t>(section->perm) % 16)
     return fail(ADHA_EINVAL, "perm is not 16-byte aligned");
   return run_section_layout(L, ptrs, section, n, save, stream);
+}
+
+int adha_run_sections_fused(const adha_schema* schema, int64_t n, const adha_layout* layout, void* const* ptrs,
+                            const adha_section* sections, int32_t n_sec, adha_stream stream) {
+  clear_error();
+  Layout L;
+  if (int rc = make_layout(schema, layout, &L, "")) return rc;
+  if (n < 0) return fail(ADHA_EINVAL, "n = %lld is negative", (long long)n);
+  if (int rc = check_fused(L, sections, n_sec, n)) return rc;
+  if (n == 0) return 0;
+  if (int rc = check_ptrs(reinterpret_cast<const void* const*>(ptrs), L.n_groups, "layout")) return rc;
+  return run_fused_layout(L, ptrs, sections, n_sec, n, stream);
 }
 
 int adha_section_backward(const adha_schema* schema, int64_t n, const adha_layout* layout, void* const* state_ptrs,

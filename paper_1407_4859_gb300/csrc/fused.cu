@@ -1,0 +1,191 @@
+// fused.cu -- a run of consecutive sections in one pass over the records (paper Section 2: the
+// combine edge of the DAG, which joins consecutive sections that share a layout into one node).
+//
+// Same warp-autonomous pipeline as sections.cu: each warp stages its chunk of R = 32*M records
+// (every group holding a field that some section of the run reads or writes, plus the
+// permutation of a gather) with 16-byte cp.async one chunk ahead, then applies the run's
+// sections in order to the chunk buffer (each section reads what the previous ones wrote there),
+// and writes every group with a written field back whole.  The result is the one of running the
+// sections one after another: each record's sections run in order, and the only cross-record
+// reads (a gather's fields at perm[i]) come from groups no section of the run writes, so they
+// read the values from before the run.  Fields are read and written once per run instead of
+// once per section.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "ptx.cuh"
+#include "section_ops.cuh"
+
+namespace adha {
+
+// per-CTA slice table at the start of shared memory: pointers, slice ends, write-back flags
+constexpr int kFusedTable = (16 * (kMaxGroups + 1) + 15) / 16 * 16;
+
+// One section on the M records of each lane of a staged chunk (r = lane + 32m), writes into the
+// chunk buffer; op is runtime (uniform over the launch).
+template <int M>
+__device__ __forceinline__ void fused_section_chunk(const FusedArgs& a, const SecOp& so, uint8_t* cur, int64_t i0,
+                                                    const int32_t* ps, int lane) {
+  switch (so.op) {
+#define ADHA_FUSED_OP(OP)                                                                                 \
+  case OP:                                                                                                \
+    _Pragma("unroll") for (int m = 0; m < M; ++m) {                                                       \
+      const int r = lane + 32 * m;                                                                        \
+      run_record<OP>(so, a.f, a.tanh_p, a.tanh_q, nullptr, StagedRec{a.f, cur, r, i0 + r}, i0 + r,       \
+                     ps ? ps[r] : 0);                                                                     \
+    }                                                                                                     \
+    break;
+    ADHA_FUSED_OP(ADHA_OP_MADD3)
+    ADHA_FUSED_OP(ADHA_OP_XORSHIFT)
+    ADHA_FUSED_OP(ADHA_OP_ADD)
+    ADHA_FUSED_OP(ADHA_OP_MIX)
+    ADHA_FUSED_OP(ADHA_OP_DRIFT)
+    ADHA_FUSED_OP(ADHA_OP_BIN)
+    ADHA_FUSED_OP(ADHA_OP_KE)
+    ADHA_FUSED_OP(ADHA_OP_FLAGS)
+    ADHA_FUSED_OP(ADHA_OP_GATHER)
+    ADHA_FUSED_OP(ADHA_OP_KICK)
+    ADHA_FUSED_OP(ADHA_OP_AXPB)
+    ADHA_FUSED_OP(ADHA_OP_MUL)
+    ADHA_FUSED_OP(ADHA_OP_TANH)
+#undef ADHA_FUSED_OP
+    default: break;
+  }
+}
+
+// One section on one record in global memory (the ragged tail).
+__device__ __forceinline__ void fused_section_record(const FusedArgs& a, const SecOp& so, int64_t i, int32_t pj) {
+  const GlobalRec rec{a.f, i};
+  switch (so.op) {
+#define ADHA_FUSED_OP(OP) \
+  case OP: run_record<OP>(so, a.f, a.tanh_p, a.tanh_q, nullptr, rec, i, pj); break;
+    ADHA_FUSED_OP(ADHA_OP_MADD3)
+    ADHA_FUSED_OP(ADHA_OP_XORSHIFT)
+    ADHA_FUSED_OP(ADHA_OP_ADD)
+    ADHA_FUSED_OP(ADHA_OP_MIX)
+    ADHA_FUSED_OP(ADHA_OP_DRIFT)
+    ADHA_FUSED_OP(ADHA_OP_BIN)
+    ADHA_FUSED_OP(ADHA_OP_KE)
+    ADHA_FUSED_OP(ADHA_OP_FLAGS)
+    ADHA_FUSED_OP(ADHA_OP_GATHER)
+    ADHA_FUSED_OP(ADHA_OP_KICK)
+    ADHA_FUSED_OP(ADHA_OP_AXPB)
+    ADHA_FUSED_OP(ADHA_OP_MUL)
+    ADHA_FUSED_OP(ADHA_OP_TANH)
+#undef ADHA_FUSED_OP
+    default: break;
+  }
+}
+
+template <int M, bool VEC>
+__global__ void __launch_bounds__(kThreads) fused_kernel(const __grid_constant__ FusedArgs a) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int n_slices = a.n_load + (a.perm_slot >= 0 ? 1 : 0);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint8_t** sp = reinterpret_cast<const uint8_t**>(smem);
+  int* send = reinterpret_cast<int*>(smem + 8 * (kMaxGroups + 1));
+  int* wback = send + (kMaxGroups + 1);
+  uint8_t* buf0 = smem + kFusedTable + (size_t)warp * 2 * a.in_bytes;
+  uint8_t* buf1 = buf0 + a.in_bytes;
+  constexpr int R = 32 * M;
+  for (int k = tid; k < n_slices; k += kThreads) {
+    sp[k] = a.load[k].ptr;
+    send[k] = a.load[k].start + R * a.load[k].stride;
+    wback[k] = a.writeback[k];
+  }
+  __syncthreads();
+
+  const int64_t W = (int64_t)gridDim.x * kWarps;
+  auto stage = [&](int64_t ch, uint8_t* buf) {
+    int g = 0, start = 0;
+    for (int p = lane * 16; p < a.in_bytes; p += 512) {
+      while (p >= send[g]) start = send[g++];
+      const int64_t stride = (send[g] - start) / R;
+      cp_async16(buf + p, sp[g] + ch * (R * stride) + (p - start));
+    }
+  };
+
+  int64_t c = (int64_t)blockIdx.x * kWarps + warp;
+  if (c < a.n_chunks) stage(c, buf0);
+  cp_async_commit();
+  for (int i = 0; c < a.n_chunks; c += W, ++i) {
+    uint8_t* cur = (i & 1) ? buf1 : buf0;
+    if (c + W < a.n_chunks) stage(c + W, (i & 1) ? buf0 : buf1);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncwarp();
+    const int64_t i0 = c * R;
+    const int32_t* ps = a.perm_slot >= 0 ? reinterpret_cast<const int32_t*>(cur + a.load[a.perm_slot].start) : nullptr;
+    for (int s = 0; s < a.n_sec; ++s) {
+      const SecOp& so = a.sec[s];
+      if (VEC && so.op == ADHA_OP_MIX) mix_chunk_vec<M, true>(so, a.f, cur, i0, lane);
+      else if (VEC && so.op == ADHA_OP_AXPB) chain_chunk_vec<ADHA_OP_AXPB, M, true>(so, a.f, a.tanh_p, a.tanh_q, nullptr, cur, i0, lane);
+      else if (VEC && so.op == ADHA_OP_MUL) chain_chunk_vec<ADHA_OP_MUL, M, true>(so, a.f, a.tanh_p, a.tanh_q, nullptr, cur, i0, lane);
+      else if (VEC && so.op == ADHA_OP_TANH) chain_chunk_vec<ADHA_OP_TANH, M, true>(so, a.f, a.tanh_p, a.tanh_q, nullptr, cur, i0, lane);
+      else fused_section_chunk<M>(a, so, cur, i0, ps, lane);
+      __syncwarp();   // the next section may map records to lanes the other way
+    }
+    // groups with written fields go back whole, 16 bytes per lane per step
+    int g = 0, start = 0;
+    for (int p = lane * 16; p < a.in_bytes; p += 512) {
+      while (p >= send[g]) start = send[g++];
+      if (wback[g]) {
+        const int64_t stride = (send[g] - start) / R;
+        *reinterpret_cast<uint4*>(const_cast<uint8_t*>(sp[g]) + c * (R * stride) + (p - start)) =
+            *reinterpret_cast<const uint4*>(cur + p);
+      }
+    }
+    __syncwarp();
+  }
+  cp_async_wait<0>();
+
+  // ragged tail: the warp whose next chunk would be n_chunks, record by record in global memory
+  const int64_t t0 = a.n_chunks * R;
+  if (c == a.n_chunks && t0 < a.n) {
+    for (int64_t i = t0 + lane; i < a.n; i += 32) {
+      const int32_t pj = a.perm_slot >= 0 ? a.perm[i] : 0;
+      for (int s = 0; s < a.n_sec; ++s) fused_section_record(a, a.sec[s], i, pj);
+    }
+  }
+}
+
+size_t fused_smem_bytes(const FusedArgs& a) { return kFusedTable + (size_t)kWarps * 2 * a.in_bytes; }
+
+template <int M, bool VEC>
+static int launch_m(const FusedArgs& a, int grid, size_t smem, void* stream) {
+  cudaError_t e = cudaFuncSetAttribute(fused_kernel<M, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(fused)");
+  fused_kernel<M, VEC><<<grid, kThreads, smem, (cudaStream_t)stream>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
+  return 0;
+}
+
+int launch_fused(const FusedArgs& a, int grid, size_t smem, void* stream) {
+  if (a.vec && a.R == 64) return launch_m<2, true>(a, grid, smem, stream);
+  if (a.vec && a.R == 128) return launch_m<4, true>(a, grid, smem, stream);
+  switch (a.R) {
+    case 32: return launch_m<1, false>(a, grid, smem, stream);
+    case 64: return launch_m<2, false>(a, grid, smem, stream);
+    default: return launch_m<4, false>(a, grid, smem, stream);
+  }
+}
+
+template <int M, bool VEC>
+static int occ_m(size_t smem, int* blocks) {
+  cudaError_t e = cudaFuncSetAttribute(fused_kernel<M, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(fused)");
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fused_kernel<M, VEC>, kThreads, smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(fused)");
+  return 0;
+}
+
+int fused_occupancy(int M, bool vec, size_t smem, int* blocks) {
+  if (vec && M == 2) return occ_m<2, true>(smem, blocks);
+  if (vec && M == 4) return occ_m<4, true>(smem, blocks);
+  if (M == 1) return occ_m<1, false>(smem, blocks);
+  if (M == 2) return occ_m<2, false>(smem, blocks);
+  return occ_m<4, false>(smem, blocks);
+}
+
+}  // namespace adha

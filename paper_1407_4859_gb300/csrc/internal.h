@@ -103,29 +103,53 @@ struct FieldRef {
   int32_t wsm;      // 1: writes go into the chunk buffer and the whole slice is written back
 };
 
+// One section's operation and operands.  Read and written fields are listed by adha_dtype,
+// ascending ids within a dtype: the fields of dtype d are rd[rd_off[d] .. rd_off[d + 1]).
+struct SecOp {
+  int32_t op;
+  int32_t arg[8];
+  float par[4];
+  int8_t rd_off[5], wr_off[5];
+  int8_t rd[kMaxFields];
+  int8_t wr[kMaxFields];
+};
+
 struct SectionArgs {
   int64_t n;
   int64_t n_chunks;
   int32_t R;
   int32_t n_load, in_bytes;
   int32_t F;
-  int32_t op;
   int32_t perm_slot;            // index of the staged perm slice (GATHER), else -1
-  uint64_t R_mask, W_mask;
   GroupRef load[kMaxGroups + 1];
   int8_t writeback[kMaxGroups + 1];   // staged slice k is written back whole after the chunk
   int32_t n_writeback;
   int32_t vec;                        // 1: every accessed group is one field wide; lane = M consecutive records
   FieldRef f[kMaxFields];
-  int32_t arg[8];
-  float par[4];
   float tanh_p[8], tanh_q[8];   // tanh polynomial coefficients (7 used each)
   const int32_t* perm;
   uint8_t* save;                // NULL or n elements of the written field's type
-  // MIX: field ids of the read set by type (ascending) and of the write set by type
-  int8_t n_rd[4], n_wr[4];      // indexed by adha_dtype
-  int8_t rd[4][kMaxFields];
-  int8_t wr[4][kMaxFields];
+  SecOp s;
+};
+
+// A run of sections executed in one pass (the paper's combine): every group holding a field that a
+// section of the run reads or writes is staged per chunk, the sections are applied in order on
+// the chunk buffer, and groups with written fields go back whole.
+constexpr int kMaxFused = ADHA_MAX_FUSED;
+struct FusedArgs {
+  int64_t n;
+  int64_t n_chunks;
+  int32_t R;
+  int32_t n_load, in_bytes;
+  int32_t perm_slot;            // index of the staged perm slice (a gather in the run), else -1
+  int32_t n_sec;
+  int32_t vec;                  // 1: every staged group is one field wide
+  GroupRef load[kMaxGroups + 1];
+  int8_t writeback[kMaxGroups + 1];
+  FieldRef f[kMaxFields];
+  float tanh_p[8], tanh_q[8];
+  const int32_t* perm;
+  SecOp sec[kMaxFused];
 };
 
 struct BackwardArgs {
@@ -146,6 +170,11 @@ int remap_layouts(const Layout& S, const void* const* src_ptrs, const Layout& D,
                   void* stream, int* launched);
 int run_section_layout(const Layout& L, void* const* ptrs, const adha_section* s, int64_t n, void* save,
                        void* stream);
+// Sections s[0..m) fused into one pass (validated here).
+int run_fused_layout(const Layout& L, void* const* ptrs, const adha_section* s, int m, int64_t n, void* stream);
+std::string fused_tuning_key(const Layout& L, const adha_section* s, int m, int64_t n);
+bool fusable_run(const Layout& L, const adha_section* s, int m);
+void fill_secop(const Layout& L, const adha_section* s, SecOp* o);
 adha_layout set_layout(const adha_layout_set* s, int l);
 // Remap launch arguments for one array (chunk_override 0 = the default chunk rule).
 int remap_plan_args(const Layout& S, const void* const* src_ptrs, const Layout& D, void* const* dst_ptrs, int64_t n,
@@ -159,6 +188,8 @@ void set_overrides(int R, int wb);
 std::string remap_tuning_key(const Layout& S, const Layout& D, int64_t n);
 void set_remap_pieces(int mode);
 int pdl_solve(const adha_cost_table* c, int return_to_input, int32_t* seq, double* total);
+int pdl_solve_fused(const adha_cost_table* c, int return_to_input, int max_window, int32_t* seq, int32_t* win,
+                    double* total);
 
 // tanh polynomial coefficients (Lambert's continued fraction cut after 25): 7 each, rounded once.
 void tanh_coefficients(float p[8], float q[8]);
@@ -168,6 +199,9 @@ int launch_remap(const RemapArgs& a, int grid, size_t smem, void* stream);
 size_t remap_smem_bytes(const RemapArgs& a);
 int launch_section(const SectionArgs& a, int grid, size_t smem, void* stream);
 size_t section_smem_bytes(const SectionArgs& a);
+int launch_fused(const FusedArgs& a, int grid, size_t smem, void* stream);
+size_t fused_smem_bytes(const FusedArgs& a);
+int fused_occupancy(int M, bool vec, size_t smem, int* blocks);
 int launch_backward(const BackwardArgs& a, void* stream);
 int remap_occupancy(int unit, size_t smem, int* blocks);
 int section_occupancy(int op, size_t smem, int* blocks);

@@ -12,6 +12,7 @@
 // sections under every limit; among equally short paths the lexicographically smallest
 // sequence of candidate indices wins.
 #include <algorithm>
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -119,6 +120,54 @@ adha_layout set_layout(const adha_layout_set* s, int l) {
 
 // Layered-DAG shortest path with lexicographic tie-break; costs are whole nanoseconds held in
 // doubles, so every sum is exact and ties compare exactly.
+// PDL with combine nodes: a plan is a sequence of windows (consecutive sections, run fused when
+// longer than one) each in one layout.  rest[k][p] = cheapest way to run sections k.. when the
+// data is in layout p (p = L: the input layout); a window [k, k+m) in layout l costs
+// remap(p -> l) + cost(k, m, l), where cost(k, 1, l) = section_ns and cost(k, m >= 2, l) =
+// fused_ns.  Ties: the smaller layout index, then the longer window, window by window from the
+// first (the lexicographically smallest sequence of (layout, -length) pairs).
+int pdl_solve_fused(const adha_cost_table* c, int return_to_input, int max_window, int32_t* seq, int32_t* win,
+                    double* total) {
+  const int S = c->n_sections, L = c->n_layouts, In = L;
+  const int W = std::max(1, std::min(max_window, std::max(1, c->max_window)));
+  auto rem = [&](int a, int b) { return c->remap_ns[(size_t)a * (L + 1) + b]; };
+  auto cost = [&](int k, int m, int l) {
+    return m == 1 ? c->section_ns[(size_t)k * L + l] : c->fused_ns[((size_t)k * c->max_window + (m - 1)) * L + l];
+  };
+  std::vector<double> rest((size_t)(S + 1) * (L + 1));
+  for (int p = 0; p <= L; ++p) rest[(size_t)S * (L + 1) + p] = return_to_input ? rem(p, In) : 0.0;
+  auto step = [&](int k, int p, int* bl, int* bm) {
+    double best = 0;
+    bool first = true;
+    for (int l = 0; l < L; ++l)
+      for (int m = std::min(W, S - k); m >= 1; --m) {
+        const double v = rem(p, l) + cost(k, m, l) + rest[(size_t)(k + m) * (L + 1) + l];
+        if (first || v < best) {
+          best = v;
+          first = false;
+          if (bl) *bl = l;
+          if (bm) *bm = m;
+        }
+      }
+    return best;
+  };
+  for (int k = S - 1; k >= 0; --k)
+    for (int p = 0; p <= L; ++p) rest[(size_t)k * (L + 1) + p] = step(k, p, nullptr, nullptr);
+  *total = rest[In];
+  int p = In;
+  for (int k = 0; k < S;) {
+    int l = 0, m = 1;
+    step(k, p, &l, &m);
+    for (int j = 0; j < m; ++j) {
+      seq[k + j] = l;
+      if (win) win[k + j] = j == 0 ? m : 0;
+    }
+    p = l;
+    k += m;
+  }
+  return 0;
+}
+
 int pdl_solve(const adha_cost_table* c, int return_to_input, int32_t* seq, double* total) {
   const int S = c->n_sections, L = c->n_layouts, In = L;
   auto sec = [&](int k, int l) { return c->section_ns[(size_t)k * L + l]; };
@@ -235,18 +284,39 @@ int adha_pdl_solve(const adha_cost_table* costs, int32_t return_to_input, int32_
   return pdl_solve(costs, return_to_input, layout_of_section, total_ns);
 }
 
-int adha_cost_table_create(int32_t n_sections, int32_t n_layouts, adha_cost_table** out) {
+int adha_pdl_solve_fused(const adha_cost_table* costs, int32_t return_to_input, int32_t max_window,
+                         int32_t* layout_of_section, int32_t* window_len, double* total_ns) {
+  clear_error();
+  if (!costs || !layout_of_section || !window_len || !total_ns) return fail(ADHA_EINVAL, "NULL argument");
+  if (costs->n_sections < 1 || costs->n_layouts < 1 || !costs->section_ns || !costs->remap_ns)
+    return fail(ADHA_EINVAL, "empty cost table");
+  if (max_window >= 2 && (costs->max_window < 2 || !costs->fused_ns))
+    return fail(ADHA_EINVAL, "the cost table holds no fused runs (max_window %d)", costs->max_window);
+  return pdl_solve_fused(costs, return_to_input, max_window, layout_of_section, window_len, total_ns);
+}
+
+int adha_cost_table_create_fused(int32_t n_sections, int32_t n_layouts, int32_t max_window, adha_cost_table** out) {
   clear_error();
   if (!out || n_sections < 1 || n_layouts < 1) return fail(ADHA_EINVAL, "bad cost table size");
+  if (max_window < 0 || max_window > ADHA_MAX_FUSED) return fail(ADHA_EINVAL, "max_window %d not in [0, %d]", max_window, ADHA_MAX_FUSED);
+  const int W = max_window >= 2 ? max_window : 0;
   const size_t ns = (size_t)n_sections * n_layouts, nr = (size_t)(n_layouts + 1) * (n_layouts + 1);
-  auto* t = static_cast<adha_cost_table*>(std::calloc(1, sizeof(adha_cost_table) + sizeof(double) * (ns + nr)));
+  const size_t nf = (size_t)n_sections * W * n_layouts;
+  auto* t = static_cast<adha_cost_table*>(std::calloc(1, sizeof(adha_cost_table) + sizeof(double) * (ns + nr + nf)));
   if (!t) return fail(ADHA_ENOMEM, "host allocation of the cost table failed");
   t->n_sections = n_sections;
   t->n_layouts = n_layouts;
   t->section_ns = reinterpret_cast<double*>(t + 1);
   t->remap_ns = t->section_ns + ns;
+  t->max_window = W;
+  t->fused_ns = W ? t->remap_ns + nr : nullptr;
+  for (size_t k = 0; k < nf; ++k) t->fused_ns[k] = HUGE_VAL;   // no fused run until measured
   *out = t;
   return 0;
+}
+
+int adha_cost_table_create(int32_t n_sections, int32_t n_layouts, adha_cost_table** out) {
+  return adha_cost_table_create_fused(n_sections, n_layouts, 0, out);
 }
 
 }  // extern "C"

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -163,8 +164,14 @@ int adha_measure(const adha_schema* schema, int64_t n, const adha_layout* in_lay
   if (!workspace || ws_bytes < 2 * m)
     return fail(ADHA_ENOMEM, "measure workspace has %zu bytes, needs %zu", ws_bytes, 2 * m);
   const int L = (int)cand.size();
+  const int W = std::min((flags >> 8) & 0xFF, std::min(n_sec, kMaxFused));
   adha_cost_table* t = nullptr;
-  if (int rc = adha_cost_table_create(n_sec, L, &t)) return rc;
+  if (int rc = adha_cost_table_create_fused(n_sec, L, W >= 2 ? W : 0, &t)) return rc;
+  // runs of 2..W consecutive sections that may be fused (whether they may does not depend on the layout)
+  std::vector<std::pair<int, int>> runs;
+  for (int k = 0; k < n_sec && W >= 2; ++k)
+    for (int m = 2; m <= W && k + m <= n_sec; ++m)
+      if (fusable_run(in, &sections[k], m)) runs.push_back({k, m});
   uint8_t* A = static_cast<uint8_t*>(workspace);
   uint8_t* B = A + m;
   std::vector<void*> in_p(in_ptrs, in_ptrs + in.n_groups), pa, pb;
@@ -233,6 +240,11 @@ int adha_measure(const adha_schema* schema, int64_t n, const adha_layout* in_lay
       }
       t->section_ns[(size_t)k * L + a] = ns;
     }
+    for (size_t r = 0; r < runs.size() && !rc; ++r) {
+      const int k = runs[r].first, m = runs[r].second;
+      rc = time_ns(timer, stream, reps, [&] { return run_fused_layout(cand[a], pa.data(), &sections[k], m, n, stream); }, &ns);
+      t->fused_ns[((size_t)k * W + (m - 1)) * L + a] = ns;
+    }
     for (int b = 0; b <= L && !rc; ++b) {
       if (b == a) continue;
       const Layout& D = b < L ? cand[b] : in;
@@ -260,6 +272,59 @@ size_t adha_program_workspace_bytes(const adha_schema* schema, int64_t n, const 
   return 3 * m;
 }
 
+}  // extern "C"
+
+namespace adha {
+
+// The plan a program runs: PDL on the cost table (with combine nodes when the options allow runs
+// of two or more sections and the table holds fused costs) unless the caller fixed it; a fixed plan
+// is validated and its model cost summed from the table (+inf for a window the table lacks).
+static int settle_plan(const adha_cost_table* costs, const adha_plan_opts* opts, int n_sec, int L, adha_plan* plan) {
+  const int back = opts ? opts->return_to_input : 0;
+  const int fw = opts ? opts->fuse_window : 0;
+  if (!plan->fixed) {
+    if (!costs) return fail(ADHA_EINVAL, "no cost table: run adha_measure first or pass a fixed plan");
+    if (fw >= 2 && costs->max_window >= 2 && costs->fused_ns)
+      return pdl_solve_fused(costs, back, fw, plan->layout_of_section, plan->window_len, &plan->model_ns);
+    for (int k = 0; k < n_sec; ++k) plan->window_len[k] = 1;
+    return pdl_solve(costs, back, plan->layout_of_section, &plan->model_ns);
+  }
+  bool any = false;
+  for (int k = 0; k < n_sec; ++k) {
+    if (plan->layout_of_section[k] < 0 || plan->layout_of_section[k] >= L)
+      return fail(ADHA_EINVAL, "fixed plan names candidate %d for section %d", plan->layout_of_section[k], k);
+    any = any || plan->window_len[k] != 0;
+  }
+  if (!any)
+    for (int k = 0; k < n_sec; ++k) plan->window_len[k] = 1;
+  for (int k = 0; k < n_sec;) {
+    const int m = plan->window_len[k];
+    if (m < 1 || m > kMaxFused || k + m > n_sec) return fail(ADHA_EINVAL, "fixed plan has a window of %d at section %d", m, k);
+    for (int j = 1; j < m; ++j)
+      if (plan->window_len[k + j] != 0 || plan->layout_of_section[k + j] != plan->layout_of_section[k])
+        return fail(ADHA_EINVAL, "fixed plan: section %d lies in the window at %d but is marked otherwise", k + j, k);
+    k += m;
+  }
+  plan->model_ns = 0;
+  if (costs) {
+    int prev = L;
+    for (int k = 0; k < n_sec;) {
+      const int l = plan->layout_of_section[k], m = plan->window_len[k];
+      double c = costs->section_ns[(size_t)k * L + l];
+      if (m > 1) c = m <= costs->max_window ? costs->fused_ns[((size_t)k * costs->max_window + (m - 1)) * L + l] : HUGE_VAL;
+      plan->model_ns += costs->remap_ns[(size_t)prev * (L + 1) + l] + c;
+      prev = l;
+      k += m;
+    }
+    if (back) plan->model_ns += costs->remap_ns[(size_t)prev * (L + 1) + L];
+  }
+  return 0;
+}
+
+}  // namespace adha
+
+extern "C" {
+
 int adha_run_program(const adha_schema* schema, int64_t n, const adha_layout* in_layout, void* const* in_ptrs,
                      const adha_section* sections, int32_t n_sec, const adha_layout_set* candidates,
                      const adha_cost_table* costs, const adha_plan_opts* opts, void* workspace, size_t ws_bytes,
@@ -275,24 +340,7 @@ int adha_run_program(const adha_schema* schema, int64_t n, const adha_layout* in
   const int back = opts ? opts->return_to_input : 0;
   if (costs && (costs->n_sections != n_sec || costs->n_layouts != L))
     return fail(ADHA_EINVAL, "cost table is %dx%d, program is %dx%d", costs->n_sections, costs->n_layouts, n_sec, L);
-  if (!plan->fixed) {
-    if (!costs) return fail(ADHA_EINVAL, "no cost table: run adha_measure first or pass a fixed plan");
-    pdl_solve(costs, back, plan->layout_of_section, &plan->model_ns);
-  } else {
-    for (int k = 0; k < n_sec; ++k)
-      if (plan->layout_of_section[k] < 0 || plan->layout_of_section[k] >= L)
-        return fail(ADHA_EINVAL, "fixed plan names candidate %d for section %d", plan->layout_of_section[k], k);
-    plan->model_ns = 0;
-    if (costs) {
-      int prev = L;
-      for (int k = 0; k < n_sec; ++k) {
-        const int l = plan->layout_of_section[k];
-        plan->model_ns += costs->remap_ns[(size_t)prev * (L + 1) + l] + costs->section_ns[(size_t)k * L + l];
-        prev = l;
-      }
-      if (back) plan->model_ns += costs->remap_ns[(size_t)prev * (L + 1) + L];
-    }
-  }
+  if (int rc = settle_plan(costs, opts, n_sec, L, plan)) return rc;
   plan->n_sections = n_sec;
   plan->n_remaps = 0;
   plan->n_launches = 0;
@@ -307,7 +355,7 @@ int adha_run_program(const adha_schema* schema, int64_t n, const adha_layout* in
   arena.size = workspace ? ws_bytes : 0;
   Layout cur = in;
   std::vector<void*> cur_p(in_ptrs, in_ptrs + in.n_groups);
-  for (int k = 0; k < n_sec; ++k) {
+  for (int k = 0; k < n_sec; k += plan->window_len[k]) {
     const int l = plan->layout_of_section[k];
     const Layout& D = cand[l];
     if (!same_layout(cur, D)) {
@@ -333,7 +381,10 @@ int adha_run_program(const adha_schema* schema, int64_t n, const adha_layout* in
       cur = D;
       cur_p = dp;
     }
-    if (int rc = run_section_layout(cur, cur_p.data(), &sections[k], n, nullptr, stream)) return rc;
+    const int m = plan->window_len[k];
+    if (int rc = m == 1 ? run_section_layout(cur, cur_p.data(), &sections[k], n, nullptr, stream)
+                        : run_fused_layout(cur, cur_p.data(), &sections[k], m, n, stream))
+      return rc;
     plan->n_launches += n > 0 ? 1 : 0;
   }
   if (back && !same_layout(cur, in)) {
@@ -433,15 +484,8 @@ int adha_run_program_host(const adha_schema* schema, int64_t n, const adha_layou
       return fail(ADHA_EINVAL, "section %d reads through a permutation: it needs every record, use one slice", k);
   const int L = (int)cand.size();
   // the plan (and with it the result's layout) is fixed before any data moves
-  if (!plan->fixed) {
-    if (!costs) return fail(ADHA_EINVAL, "no cost table: run adha_measure first or pass a fixed plan");
-    if (costs->n_sections != n_sec || costs->n_layouts != L) return fail(ADHA_EINVAL, "cost table does not match");
-    pdl_solve(costs, opts ? opts->return_to_input : 0, plan->layout_of_section, &plan->model_ns);
-  } else {
-    for (int k = 0; k < n_sec; ++k)
-      if (plan->layout_of_section[k] < 0 || plan->layout_of_section[k] >= L)
-        return fail(ADHA_EINVAL, "fixed plan names candidate %d for section %d", plan->layout_of_section[k], k);
-  }
+  if (costs && (costs->n_sections != n_sec || costs->n_layouts != L)) return fail(ADHA_EINVAL, "cost table does not match");
+  if (int rc = settle_plan(costs, opts, n_sec, L, plan)) return rc;
   const bool back = opts && opts->return_to_input;
   const Layout& out_layout = back ? in : cand[plan->layout_of_section[n_sec - 1]];
   if (!host_in || !host_out) return fail(ADHA_EINVAL, "host buffers are NULL");

@@ -1,0 +1,387 @@
+// section_ops.cuh -- per-record and per-chunk arithmetic of the section kinds, shared by the
+// single-section kernel (sections.cu) and the fused kernel (fused.cu).  A record's fields are
+// reached through a FieldRef table: in the warp's chunk buffer when staged, else in global memory.
+// Every floating operation is an explicitly rounded-to-nearest intrinsic, so no contraction can
+// change a bit.
+#pragma once
+
+#include <cstdint>
+#include <cstring>
+
+#include "internal.h"
+
+namespace adha {
+
+struct StagedRec {      // record r of a staged chunk (global record i)
+  const FieldRef* f;
+  uint8_t* stage;
+  int r;
+  int64_t i;
+  template <class V>
+  __device__ __forceinline__ V ld(int k) const {
+    const FieldRef& F = f[k];
+    if (F.s0 >= 0) return *reinterpret_cast<const V*>(stage + F.s0 + r * F.ss);
+    return *reinterpret_cast<const V*>(F.g + i * F.gs);
+  }
+  template <class V>
+  __device__ __forceinline__ void st(int k, V v) const {
+    const FieldRef& F = f[k];
+    if (F.wsm) *reinterpret_cast<V*>(stage + F.s0 + r * F.ss) = v;
+    else *reinterpret_cast<V*>(F.g + i * F.gs) = v;
+  }
+};
+
+struct GlobalRec {      // record i in global memory (ragged tail)
+  const FieldRef* f;
+  int64_t i;
+  template <class V>
+  __device__ __forceinline__ V ld(int k) const {
+    return *reinterpret_cast<const V*>(f[k].g + i * f[k].gs);
+  }
+  template <class V>
+  __device__ __forceinline__ void st(int k, V v) const {
+    *reinterpret_cast<V*>(f[k].g + i * f[k].gs) = v;
+  }
+};
+
+template <class V>
+__device__ __forceinline__ V gld(const FieldRef* f, int k, int64_t i) {
+  return __ldg(reinterpret_cast<const V*>(f[k].g + i * f[k].gs));
+}
+
+// Lambert's continued fraction for tanh cut after the partial denominator 25, as x*Q(a)/P(a) with
+// a = x*x: Horner's rule over the 7 coefficients of each polynomial, then one IEEE division.
+__device__ __forceinline__ float tanh_cf(float x, const float* P, const float* Q) {
+  if (fabsf(x) >= 9.0f) return copysignf(1.0f, x);
+  const float a = __fmul_rn(x, x);
+  float q = Q[6], p = P[6];
+#pragma unroll
+  for (int j = 5; j >= 0; --j) {
+    q = __fadd_rn(__fmul_rn(q, a), Q[j]);
+    p = __fadd_rn(__fmul_rn(p, a), P[j]);
+  }
+  return __fdiv_rn(__fmul_rn(x, q), p);
+}
+
+// MIX over the M records r = lane + 32m of a staged chunk, field-major: every field's shared
+// and global addresses are computed once for the M records.
+template <int M>
+__device__ __forceinline__ void mix_chunk(const SecOp& so, const FieldRef* fr, uint8_t* stage, int64_t i0, int lane) {
+  float s[M];
+  uint32_t h[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    s[m] = 0.0f;
+    h[m] = 0u;
+  }
+  // V value of field F for the lane's record m: from the chunk buffer if staged, else global
+#define ADHA_MIX_READ(V, LIST, BODY)                                                        \
+  for (int j = so.rd_off[LIST]; j < so.rd_off[LIST + 1]; ++j) {                            \
+    const FieldRef& F = fr[so.rd[j]];                                                       \
+    if (F.s0 >= 0) {                                                                        \
+      const uint8_t* p = stage + F.s0 + lane * F.ss;                                        \
+      _Pragma("unroll") for (int m = 0; m < M; ++m) {                                       \
+        const V v = *reinterpret_cast<const V*>(p + m * 32 * F.ss);                         \
+        BODY;                                                                               \
+      }                                                                                     \
+    } else {                                                                                \
+      const uint8_t* p = F.g + (i0 + lane) * F.gs;                                          \
+      _Pragma("unroll") for (int m = 0; m < M; ++m) {                                       \
+        const V v = *reinterpret_cast<const V*>(p + (int64_t)m * 32 * F.gs);                \
+        BODY;                                                                               \
+      }                                                                                     \
+    }                                                                                       \
+  }
+  ADHA_MIX_READ(float, ADHA_F32, s[m] = __fadd_rn(s[m], v))
+  ADHA_MIX_READ(unsigned long long, ADHA_F64, h[m] ^= (uint32_t)v ^ (uint32_t)(v >> 32))
+  ADHA_MIX_READ(uint32_t, ADHA_I32, h[m] ^= v)
+  ADHA_MIX_READ(uint16_t, ADHA_BF16, h[m] ^= (uint32_t)v)
+#undef ADHA_MIX_READ
+  float t[M];
+  uint32_t k[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    t[m] = __fadd_rn(s[m], __fmul_rn(__uint2float_rn(h[m] & 255u), 0.00390625f));
+    k[m] = (h[m] ^ __float_as_uint(t[m])) >> 3;
+  }
+  // written fields: old value from the chunk buffer if staged, else global; new value to global
+#define ADHA_MIX_WRITE(V, LIST, EXPR)                                                       \
+  for (int j = so.wr_off[LIST]; j < so.wr_off[LIST + 1]; ++j) {                            \
+    const FieldRef& F = fr[so.wr[j]];                                                       \
+    uint8_t* p = stage + F.s0 + lane * F.ss;                                                \
+    if (F.wsm) {                                                                            \
+      _Pragma("unroll") for (int m = 0; m < M; ++m) {                                       \
+        V* x = reinterpret_cast<V*>(p + m * 32 * F.ss);                                     \
+        const V old = *x;                                                                   \
+        *x = EXPR;                                                                          \
+      }                                                                                     \
+    } else {                                                                                \
+      uint8_t* q = F.g + (i0 + lane) * F.gs;                                                \
+      _Pragma("unroll") for (int m = 0; m < M; ++m) {                                       \
+        const V old = *reinterpret_cast<const V*>(p + m * 32 * F.ss);                       \
+        *reinterpret_cast<V*>(q + (int64_t)m * 32 * F.gs) = EXPR;                           \
+      }                                                                                     \
+    }                                                                                       \
+  }
+  ADHA_MIX_WRITE(float, ADHA_F32, __fadd_rn(__fmul_rn(old, 0.5f), t[m]))
+  ADHA_MIX_WRITE(double, ADHA_F64, __dadd_rn(__dmul_rn(old, 0.5), (double)t[m]))
+  ADHA_MIX_WRITE(uint32_t, ADHA_I32, old ^ k[m])
+  ADHA_MIX_WRITE(uint16_t, ADHA_BF16, (uint16_t)(old ^ (uint16_t)(k[m] & 0xFFFFu)))
+#undef ADHA_MIX_WRITE
+}
+
+// M consecutive values of one field for records lane*M .. lane*M+M-1 of a one-field slice
+// (contiguous, M*sizeof(V)-byte aligned): moved with 8- or 16-byte accesses.
+template <class V, int M>
+__device__ __forceinline__ void ld_vec(const uint8_t* p, V (&v)[M]) {
+  constexpr int B = M * (int)sizeof(V);
+  if constexpr (B % 16 == 0) {
+#pragma unroll
+    for (int k = 0; k < B / 16; ++k) {
+      const uint4 x = reinterpret_cast<const uint4*>(p)[k];
+      memcpy(reinterpret_cast<uint8_t*>(v) + 16 * k, &x, 16);
+    }
+  } else if constexpr (B == 8) {
+    const uint2 x = *reinterpret_cast<const uint2*>(p);
+    memcpy(v, &x, 8);
+  } else {
+#pragma unroll
+    for (int m = 0; m < M; ++m) v[m] = reinterpret_cast<const V*>(p)[m];
+  }
+}
+
+template <class V, int M>
+__device__ __forceinline__ void st_vec(uint8_t* p, const V (&v)[M]) {
+  constexpr int B = M * (int)sizeof(V);
+  if constexpr (B % 16 == 0) {
+#pragma unroll
+    for (int k = 0; k < B / 16; ++k) {
+      uint4 x;
+      memcpy(&x, reinterpret_cast<const uint8_t*>(v) + 16 * k, 16);
+      reinterpret_cast<uint4*>(p)[k] = x;
+    }
+  } else if constexpr (B == 8) {
+    uint2 x;
+    memcpy(&x, v, 8);
+    *reinterpret_cast<uint2*>(p) = x;
+  } else {
+#pragma unroll
+    for (int m = 0; m < M; ++m) reinterpret_cast<V*>(p)[m] = v[m];
+  }
+}
+
+// MIX when every accessed group holds one field (SoA-like): lane takes records lane*M + m, so
+// each field is one vector load from the chunk buffer and one vector store, to global memory or
+// (TO_STAGE, inside a fused run) back into the chunk buffer.
+template <int M, bool TO_STAGE = false>
+__device__ __forceinline__ void mix_chunk_vec(const SecOp& so, const FieldRef* fr, uint8_t* stage, int64_t i0,
+                                              int lane) {
+  float s[M];
+  uint32_t h[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    s[m] = 0.0f;
+    h[m] = 0u;
+  }
+  for (int j = so.rd_off[ADHA_F32]; j < so.rd_off[ADHA_F32 + 1]; ++j) {
+    float v[M];
+    ld_vec<float, M>(stage + fr[so.rd[j]].s0 + lane * M * 4, v);
+#pragma unroll
+    for (int m = 0; m < M; ++m) s[m] = __fadd_rn(s[m], v[m]);
+  }
+  for (int j = so.rd_off[ADHA_F64]; j < so.rd_off[ADHA_F64 + 1]; ++j) {
+    unsigned long long v[M];
+    ld_vec<unsigned long long, M>(stage + fr[so.rd[j]].s0 + lane * M * 8, v);
+#pragma unroll
+    for (int m = 0; m < M; ++m) h[m] ^= (uint32_t)v[m] ^ (uint32_t)(v[m] >> 32);
+  }
+  for (int j = so.rd_off[ADHA_I32]; j < so.rd_off[ADHA_I32 + 1]; ++j) {
+    uint32_t v[M];
+    ld_vec<uint32_t, M>(stage + fr[so.rd[j]].s0 + lane * M * 4, v);
+#pragma unroll
+    for (int m = 0; m < M; ++m) h[m] ^= v[m];
+  }
+  for (int j = so.rd_off[ADHA_BF16]; j < so.rd_off[ADHA_BF16 + 1]; ++j) {
+    uint16_t v[M];
+    ld_vec<uint16_t, M>(stage + fr[so.rd[j]].s0 + lane * M * 2, v);
+#pragma unroll
+    for (int m = 0; m < M; ++m) h[m] ^= (uint32_t)v[m];
+  }
+  float t[M];
+  uint32_t k[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    t[m] = __fadd_rn(s[m], __fmul_rn(__uint2float_rn(h[m] & 255u), 0.00390625f));
+    k[m] = (h[m] ^ __float_as_uint(t[m])) >> 3;
+  }
+  const int64_t r0 = i0 + (int64_t)lane * M;
+  for (int j = so.wr_off[ADHA_F32]; j < so.wr_off[ADHA_F32 + 1]; ++j) {
+    const FieldRef& F = fr[so.wr[j]];
+    float v[M];
+    ld_vec<float, M>(stage + F.s0 + lane * M * 4, v);
+#pragma unroll
+    for (int m = 0; m < M; ++m) v[m] = __fadd_rn(__fmul_rn(v[m], 0.5f), t[m]);
+    st_vec<float, M>(TO_STAGE ? stage + F.s0 + lane * M * 4 : F.g + r0 * 4, v);
+  }
+  for (int j = so.wr_off[ADHA_F64]; j < so.wr_off[ADHA_F64 + 1]; ++j) {
+    const FieldRef& F = fr[so.wr[j]];
+    double v[M];
+    ld_vec<double, M>(stage + F.s0 + lane * M * 8, v);
+#pragma unroll
+    for (int m = 0; m < M; ++m) v[m] = __dadd_rn(__dmul_rn(v[m], 0.5), (double)t[m]);
+    st_vec<double, M>(TO_STAGE ? stage + F.s0 + lane * M * 8 : F.g + r0 * 8, v);
+  }
+  for (int j = so.wr_off[ADHA_I32]; j < so.wr_off[ADHA_I32 + 1]; ++j) {
+    const FieldRef& F = fr[so.wr[j]];
+    uint32_t v[M];
+    ld_vec<uint32_t, M>(stage + F.s0 + lane * M * 4, v);
+#pragma unroll
+    for (int m = 0; m < M; ++m) v[m] ^= k[m];
+    st_vec<uint32_t, M>(TO_STAGE ? stage + F.s0 + lane * M * 4 : F.g + r0 * 4, v);
+  }
+  for (int j = so.wr_off[ADHA_BF16]; j < so.wr_off[ADHA_BF16 + 1]; ++j) {
+    const FieldRef& F = fr[so.wr[j]];
+    uint16_t v[M];
+    ld_vec<uint16_t, M>(stage + F.s0 + lane * M * 2, v);
+#pragma unroll
+    for (int m = 0; m < M; ++m) v[m] = (uint16_t)(v[m] ^ (uint16_t)(k[m] & 0xFFFFu));
+    st_vec<uint16_t, M>(TO_STAGE ? stage + F.s0 + lane * M * 2 : F.g + r0 * 2, v);
+  }
+}
+
+// AXPB, MUL, TANH under the vector mapping (x, y, z each a one-field group): lane takes records
+// lane*M + m; x, y and the old z come from the chunk buffer (the values before the section, so
+// any aliasing of x, y, z reads what the per-record rule reads), z and `save` get vector stores
+// (z into the chunk buffer when TO_STAGE).
+template <int OP, int M, bool TO_STAGE = false>
+__device__ __forceinline__ void chain_chunk_vec(const SecOp& so, const FieldRef* fr, const float* tp, const float* tq,
+                                                uint8_t* save, uint8_t* stage, int64_t i0, int lane) {
+  const int* g = so.arg;
+  const int z = OP == ADHA_OP_MUL ? g[2] : g[1];
+  const int64_t r0 = i0 + (int64_t)lane * M;
+  float x[M], v[M];
+  ld_vec<float, M>(stage + fr[g[0]].s0 + lane * M * 4, x);
+  if (save) {
+    float old[M];
+    ld_vec<float, M>(stage + fr[z].s0 + lane * M * 4, old);
+    st_vec<float, M>(save + r0 * 4, old);
+  }
+  if (OP == ADHA_OP_MUL) {
+    float y[M];
+    ld_vec<float, M>(stage + fr[g[1]].s0 + lane * M * 4, y);
+#pragma unroll
+    for (int m = 0; m < M; ++m) v[m] = __fmul_rn(x[m], y[m]);
+  } else if (OP == ADHA_OP_AXPB) {
+#pragma unroll
+    for (int m = 0; m < M; ++m) v[m] = __fadd_rn(__fmul_rn(so.par[0], x[m]), so.par[1]);
+  } else {
+#pragma unroll
+    for (int m = 0; m < M; ++m) v[m] = tanh_cf(x[m], tp, tq);
+  }
+  st_vec<float, M>(TO_STAGE ? stage + fr[z].s0 + lane * M * 4 : fr[z].g + r0 * 4, v);
+}
+
+template <int OP>
+constexpr bool kVectorOp = OP == ADHA_OP_MIX || OP == ADHA_OP_AXPB || OP == ADHA_OP_MUL || OP == ADHA_OP_TANH;
+
+// One record of one section: its fields through `rec` (staged chunk or global memory), fields read
+// through the permutation from global memory (record pj), the old z to `save` when asked.
+template <int OP, class Rec>
+__device__ __forceinline__ void run_record(const SecOp& so, const FieldRef* fr, const float* tp, const float* tq,
+                                           uint8_t* save, const Rec& rec, int64_t i, int32_t pj) {
+  const int* g = so.arg;
+  if (OP == ADHA_OP_MADD3) {
+    const float m = __fmul_rn(rec.template ld<float>(g[0]), rec.template ld<float>(g[1]));
+    rec.template st<float>(g[2], __fadd_rn(m, rec.template ld<float>(g[2])));
+  } else if (OP == ADHA_OP_XORSHIFT) {
+    const uint32_t u = rec.template ld<uint32_t>(g[0]);
+    rec.template st<uint32_t>(g[1], u ^ (u >> 3));
+  } else if (OP == ADHA_OP_ADD) {
+    rec.template st<float>(g[2], __fadd_rn(rec.template ld<float>(g[0]), rec.template ld<float>(g[1])));
+  } else if (OP == ADHA_OP_MIX) {
+    float s = 0.0f;
+    uint32_t h = 0u;
+    for (int j = so.rd_off[ADHA_F32]; j < so.rd_off[ADHA_F32 + 1]; ++j) s = __fadd_rn(s, rec.template ld<float>(so.rd[j]));
+    for (int j = so.rd_off[ADHA_F64]; j < so.rd_off[ADHA_F64 + 1]; ++j) {
+      const unsigned long long b = rec.template ld<unsigned long long>(so.rd[j]);
+      h ^= (uint32_t)b ^ (uint32_t)(b >> 32);
+    }
+    for (int j = so.rd_off[ADHA_I32]; j < so.rd_off[ADHA_I32 + 1]; ++j) h ^= rec.template ld<uint32_t>(so.rd[j]);
+    for (int j = so.rd_off[ADHA_BF16]; j < so.rd_off[ADHA_BF16 + 1]; ++j) h ^= (uint32_t)rec.template ld<uint16_t>(so.rd[j]);
+    const float t = __fadd_rn(s, __fmul_rn(__uint2float_rn(h & 255u), 0.00390625f));
+    const uint32_t k = (h ^ __float_as_uint(t)) >> 3;
+    for (int j = so.wr_off[ADHA_F32]; j < so.wr_off[ADHA_F32 + 1]; ++j) {
+      const int f = so.wr[j];
+      rec.template st<float>(f, __fadd_rn(__fmul_rn(rec.template ld<float>(f), 0.5f), t));
+    }
+    if (so.wr_off[ADHA_F64 + 1] > so.wr_off[ADHA_F64]) {
+      const double td = (double)t;
+      for (int j = so.wr_off[ADHA_F64]; j < so.wr_off[ADHA_F64 + 1]; ++j) {
+        const int f = so.wr[j];
+        rec.template st<double>(f, __dadd_rn(__dmul_rn(rec.template ld<double>(f), 0.5), td));
+      }
+    }
+    for (int j = so.wr_off[ADHA_I32]; j < so.wr_off[ADHA_I32 + 1]; ++j) {
+      const int f = so.wr[j];
+      rec.template st<uint32_t>(f, rec.template ld<uint32_t>(f) ^ k);
+    }
+    for (int j = so.wr_off[ADHA_BF16]; j < so.wr_off[ADHA_BF16 + 1]; ++j) {
+      const int f = so.wr[j];
+      rec.template st<uint16_t>(f, (uint16_t)(rec.template ld<uint16_t>(f) ^ (uint16_t)(k & 0xFFFFu)));
+    }
+  } else if (OP == ADHA_OP_DRIFT) {
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+      const float d = __fmul_rn(so.par[0], rec.template ld<float>(g[3 + ax]));
+      float q = __fadd_rn(rec.template ld<float>(g[ax]), d);
+      if (q >= 1.0f) q = __fsub_rn(q, 1.0f);
+      else if (q < 0.0f) q = __fadd_rn(q, 1.0f);
+      rec.template st<float>(g[ax], q);
+    }
+  } else if (OP == ADHA_OP_BIN) {
+    const int G = (int)so.par[0];
+    int c[3];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+      int k = __float2int_rz(__fmul_rn(rec.template ld<float>(g[ax]), so.par[0]));
+      k = k < 0 ? 0 : (k > G - 1 ? G - 1 : k);
+      c[ax] = k;
+    }
+    rec.template st<int32_t>(g[3], c[0] + G * (c[1] + G * c[2]));
+  } else if (OP == ADHA_OP_KE) {
+    const float vx = rec.template ld<float>(g[0]), vy = rec.template ld<float>(g[1]),
+                vz = rec.template ld<float>(g[2]);
+    float s = __fadd_rn(__fmul_rn(vx, vx), __fmul_rn(vy, vy));
+    s = __fadd_rn(s, __fmul_rn(vz, vz));
+    const float e = __fmul_rn(__fmul_rn(0.5f, rec.template ld<float>(g[3])), s);
+    rec.template st<double>(g[4], (double)e);
+  } else if (OP == ADHA_OP_FLAGS) {
+    const uint32_t fl = rec.template ld<uint32_t>(g[0]);
+    const uint32_t bit = rec.template ld<double>(g[1]) > (double)so.par[0] ? 1u : 0u;
+    rec.template st<uint32_t>(g[0], ((fl << 1) | bit) & 255u);
+  } else if (OP == ADHA_OP_GATHER) {
+    const int64_t j = pj;
+    const float c = __fmul_rn(so.par[0], gld<float>(fr, g[6], j));
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+      const float d = __fsub_rn(gld<float>(fr, g[3 + ax], j), 0.5f);
+      rec.template st<float>(g[ax], __fadd_rn(rec.template ld<float>(g[ax]), __fmul_rn(c, d)));
+    }
+  } else if (OP == ADHA_OP_KICK) {
+    const float c = __fmul_rn(so.par[0], rec.template ld<float>(g[3]));
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax)
+      rec.template st<float>(g[ax], __fadd_rn(rec.template ld<float>(g[ax]), __fmul_rn(c, so.par[1 + ax])));
+  } else {   // AXPB, MUL, TANH: z = op(x[, y]); the old z goes to `save` when asked
+    const int z = OP == ADHA_OP_MUL ? g[2] : g[1];
+    if (save) reinterpret_cast<float*>(save)[i] = rec.template ld<float>(z);
+    const float x = rec.template ld<float>(g[0]);
+    float v;
+    if (OP == ADHA_OP_AXPB) v = __fadd_rn(__fmul_rn(so.par[0], x), so.par[1]);
+    else if (OP == ADHA_OP_MUL) v = __fmul_rn(x, rec.template ld<float>(g[1]));
+    else v = tanh_cf(x, tp, tq);
+    rec.template st<float>(z, v);
+  }
+}
+
+}  // namespace adha

@@ -4,6 +4,7 @@ ODS is pinned by hand-worked cases (tests/golden/ods_cases.txt, two of them the
 groupings printed in Tables 2 and 3 of the paper); the DP by brute-force
 enumeration of every assignment on small programs.
 """
+import math
 import os
 import random
 
@@ -101,3 +102,48 @@ def test_dp_hand_worked():
     assert oracle.pdl_dp([[1, 1], [1, 1], [1, 1]], [[0, 0, 0]] * 3) == (3, [0, 0, 0])
     # returning to the input layout adds its remap
     assert oracle.pdl_dp([[1, 0]], [[0, 0, 7], [0, 0, 1], [0, 0, 0]], True) == (1, [1])
+
+
+def _random_fused(rng, S, L, W):
+    """Fused-run costs, some runs not fusable (inf), small integers so that ties are common."""
+    return {(k, m): [rng.choice([rng.randrange(0, 30), math.inf]) for _ in range(L)]
+            for k in range(S) for m in range(2, W + 1) if k + m <= S}
+
+
+@pytest.mark.parametrize("seed", range(80))
+def test_fused_dp_equals_exhaustive(seed):
+    rng = random.Random(500 + seed)
+    S, L, W = rng.randrange(1, 6), rng.randrange(1, 4), rng.randrange(1, 5)
+    sec, rem = _random_costs(rng, S, L)
+    fused = _random_fused(rng, S, L, W)
+    back = bool(seed % 2)
+    assert oracle.pdl_dp_fused(sec, rem, fused, W, back) == oracle.pdl_exhaustive_fused(sec, rem, fused, W, back)
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_fused_dp_without_runs_is_the_plain_dp(seed):
+    rng = random.Random(900 + seed)
+    S, L = rng.randrange(1, 7), rng.randrange(1, 5)
+    sec, rem = _random_costs(rng, S, L)
+    cost, seq, win = oracle.pdl_dp_fused(sec, rem, {}, 1, bool(seed % 2))
+    assert (cost, seq) == oracle.pdl_dp(sec, rem, bool(seed % 2)) and win == [1] * S
+
+
+def test_fused_dp_hand_worked():
+    # one layout; sections cost 10 each, fusing sections 0-1 costs 12, fusing all three 25
+    sec = [[10], [10], [10]]
+    rem = [[0, 0], [0, 0]]
+    fused = {(0, 2): [12], (1, 2): [math.inf], (0, 3): [25]}
+    assert oracle.pdl_dp_fused(sec, rem, fused, 3) == (22, [0, 0, 0], [2, 0, 1])
+    # a cheaper three-section run wins; with windows of at most 2 it cannot be used
+    fused[(0, 3)] = [21]
+    assert oracle.pdl_dp_fused(sec, rem, fused, 3) == (21, [0, 0, 0], [3, 0, 0])
+    assert oracle.pdl_dp_fused(sec, rem, fused, 2) == (22, [0, 0, 0], [2, 0, 1])
+    # equal cost: the longer window first
+    fused[(0, 3)] = [22]
+    assert oracle.pdl_dp_fused(sec, rem, fused, 3) == (22, [0, 0, 0], [3, 0, 0])
+    # two layouts: B runs the fused pair cheaply but costs a remap of 5 to enter
+    sec = [[10, 10], [10, 10]]
+    rem = [[0, 5, 0], [5, 0, 0], [0, 5, 0]]
+    fused = {(0, 2): [30, 9]}
+    assert oracle.pdl_dp_fused(sec, rem, fused, 2) == (14, [1, 1], [2, 0])

@@ -1,4 +1,5 @@
 """The library's host planner (ODS, candidates, PDL) against the oracle's, CPU only."""
+import math
 import random
 
 import numpy as np
@@ -87,3 +88,82 @@ def test_run_program_rejects_bad_fixed_plan_without_gpu(P):
     with pytest.raises(AdhaError) as e:     # neither a table nor a fixed plan
         P.adha_run_program(S, 64, P.Layout.aos(6), [256], wl.sections, cand, stream=0)
     assert e.value.code == ADHA_EINVAL and "measure" in str(e.value)
+
+
+def _fused_table(P, sec, rem, fused, W):
+    t = P.adha_cost_table_create(len(sec), len(sec[0]), max_window=W)
+    t.set(sec, rem, fused)
+    return t
+
+
+@pytest.mark.parametrize("seed", range(60))
+def test_library_fused_pdl_equals_oracle(P, seed):
+    rng = random.Random(3000 + seed)
+    S, L, W = rng.randrange(1, 6), rng.randrange(1, 4), rng.randrange(2, 5)
+    sec = [[rng.randrange(0, 30) for _ in range(L)] for _ in range(S)]
+    rem = [[0 if a == b else rng.randrange(0, 25) for b in range(L + 1)] for a in range(L + 1)]
+    fused = {(k, m): [rng.choice([rng.randrange(0, 40), math.inf]) for _ in range(L)]
+             for k in range(S) for m in range(2, W + 1) if k + m <= S}
+    back = bool(seed % 3 == 0)
+    t = _fused_table(P, sec, rem, fused, W)
+    for w in range(1, W + 1):
+        want = oracle.pdl_exhaustive_fused(sec, rem, {km: v for km, v in fused.items() if km[1] <= w}, w, back)
+        assert P.adha_pdl_solve_fused(t, back, w) == want
+    cost, seq = P.adha_pdl_solve(t, back)
+    assert P.adha_pdl_solve_fused(t, back, 1) == (cost, seq, [1] * S)
+
+
+def test_library_fused_pdl_large_matches_oracle_dp(P):
+    rng = random.Random(11)
+    S, L, W = 40, 12, 6
+    sec = [[rng.randrange(1000, 50000) for _ in range(L)] for _ in range(S)]
+    rem = [[0 if a == b else rng.randrange(0, 90000) for b in range(L + 1)] for a in range(L + 1)]
+    fused = {(k, m): [rng.randrange(1000, 40000 * m) for _ in range(L)]
+             for k in range(S) for m in range(2, W + 1) if k + m <= S}
+    assert P.adha_pdl_solve_fused(_fused_table(P, sec, rem, fused, W), False, W) == \
+        oracle.pdl_dp_fused(sec, rem, fused, W)
+
+
+def test_fused_cost_table_starts_unmeasured_and_rejects_bad_windows(P):
+    from paper_1407_4859_gb300._lib import AdhaError, ADHA_EINVAL
+    t = P.adha_cost_table_create(4, 2, max_window=3)
+    assert t.max_window == 3 and all(v == math.inf for row in t.fused_ns.values() for v in row)
+    assert sorted(t.fused_ns) == [(0, 2), (0, 3), (1, 2), (1, 3), (2, 2)]
+    for bad in (-1, 17):
+        with pytest.raises(AdhaError) as e:
+            P.adha_cost_table_create(4, 2, max_window=bad)
+        assert e.value.code == ADHA_EINVAL
+    plain = P.adha_cost_table_create(4, 2)
+    with pytest.raises(AdhaError) as e:    # no fused runs in the table
+        P.adha_pdl_solve_fused(plain, False, 2)
+    assert e.value.code == ADHA_EINVAL
+
+
+def test_run_program_rejects_bad_fixed_windows_without_gpu(P):
+    from paper_1407_4859_gb300._lib import AdhaError, ADHA_EINVAL
+    wl = synth.config1(n=64)
+    S = P.Schema(wl.dtypes)
+    cand = P.adha_layout_set_create(6, [P.Layout.aos(6), P.Layout.soa(6)])
+    for fixed, windows in [([0, 0, 0], [2, 1, 1]),      # section 1 is inside the window but marked 1
+                           ([0, 1, 1], [2, 0, 1]),      # the window's sections in two layouts
+                           ([0, 0, 0], [4, 0, 0]),      # past the last section
+                           ([0, 0, 0], [0, 1, 1])]:     # no window starts at section 0
+        with pytest.raises(AdhaError) as e:
+            P.adha_run_program(S, 64, P.Layout.aos(6), [256], wl.sections, cand, fixed=fixed, windows=windows,
+                               stream=0)
+        assert e.value.code == ADHA_EINVAL
+
+
+def test_fused_run_validation_without_gpu(P):
+    from paper_1407_4859_gb300._lib import AdhaError, ADHA_EINVAL
+    wl = synth.config3(n=64)
+    S, L = P.Schema(wl.dtypes), P.Layout.soa(12)
+    bufs = [256 * (k + 1) for k in range(12)]
+    drift, gather = wl.sections[0], wl.sections[4]
+    cases = [[],                                   # empty run
+             [wl.sections[2]] * 17,                # longer than ADHA_MAX_FUSED
+             [drift, gather]]                      # drift writes pos, which the gather reads at perm
+    for secs in cases:
+        with pytest.raises(AdhaError) as e:
+            P.adha_run_sections_fused(S, 64, L, bufs, P.Sections(secs, None) if secs else P.Sections([]), stream=0)
+        assert e.value.code == ADHA_EINVAL
