@@ -218,6 +218,8 @@ def main():
                          "particle program with a gather; batched: 256 uneven arrays remapped in one launch; "
                          "differentiable: the 2^26-record chain of 64 sections, forward + backward")
     ap.add_argument("--n-log2", type=int, default=0, help="records per GPU (default: the workload's size)")
+    ap.add_argument("--fuse-window", type=int, default=-1,
+                    help="longest run of sections the fused-plan comparison may fuse (-1: all, up to 16; 0: skip)")
     ap.add_argument("--e2e-slices", type=int, default=8,
                     help="slices of the end-to-end pipeline through host buffers (programs without a gather)")
     ap.add_argument("--cost-cache", default=None,
@@ -269,20 +271,23 @@ def main():
     cand = P.adha_plan_sections(S, secs, opts)
     L = len(cand)
     t0 = time.perf_counter()
+    fuse = min(len(wl.sections), 16) if args.fuse_window < 0 else min(args.fuse_window, 16)
+    fuse = fuse if fuse >= 2 else 0
     cache_key = {"gpu": torch.cuda.get_device_name(local), "workload": wl.name, "n": n,
-                 "candidates": [l.groups for l in cand.layouts], "csrc": csrc_hash()}
+                 "candidates": [l.groups for l in cand.layouts], "csrc": csrc_hash(), "fuse_window": fuse}
     costs = None
     if args.cost_cache and os.path.exists(args.cost_cache):
         d = json.load(open(args.cost_cache))
         if d.get("key") == cache_key:
-            costs = P.adha_cost_table_create(len(wl.sections), L)
-            costs.set(d["section_ns"], d["remap_ns"])
+            costs = P.adha_cost_table_create(len(wl.sections), L, max_window=fuse)
+            costs.set(d["section_ns"], d["remap_ns"], {(k, m): row for k, m, row in d["fused_ns"]})
             P.adha_tune_import(d.get("tuning", ""))
             log("cost table and tuning loaded from %s" % args.cost_cache)
     if costs is None:
-        costs = P.adha_measure(S, n, AOS, in_buf, secs, cand, reps=2, autotune=True)
+        costs = P.adha_measure(S, n, AOS, in_buf, secs, cand, reps=2, autotune=True, fuse_window=fuse)
         if args.cost_cache:
             json.dump({"key": cache_key, "section_ns": costs.section_ns, "remap_ns": costs.remap_ns,
+                       "fused_ns": [[k, m, row] for (k, m), row in costs.fused_ns.items()],
                        "tuning": P.adha_tune_export()}, open(args.cost_cache, "w"))
     measure_s = time.perf_counter() - t0
     log("%d candidates, cost table ready in %.1f s" % (L, measure_s))
@@ -403,6 +408,9 @@ def main():
                    "adha_over_best": round(adha_ms / min(best_ms, adha_ms), 4),
                    "speedup_vs_aos": round(t_aos / adha_ms, 3), "speedup_vs_soa": round(t_soa / adha_ms, 3),
                    "paper_context": "paper: up to 6.92x over manual (SoA) layouts, K-Means on Xeon X5660 + Tesla M2050, OpenCL"}
+        if fuse:
+            compare["fused"] = fused_comparison(P, torch, S, n, AOS, in_buf, secs, cand, costs, ws, stream, fuse,
+                                                adha_ms, t_aos, t_soa, layouts)
 
     cpu = None
     if not args.no_cpu and rank == 0:
@@ -443,6 +451,48 @@ def main():
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def fused_comparison(P, torch, S, n, AOS, in_buf, secs, cand, costs, ws, stream, fuse, adha_ms, t_aos, t_soa, layouts):
+    """The program under PDL with combine nodes (runs of up to `fuse` sections fused in one layout,
+    at their measured costs), against the plain ADHA plan and the uniform layouts."""
+    opts = P.PlanOpts(CAPS, fuse_window=fuse)
+    nsec = len(secs)
+    plan = P.adha_run_program(S, n, AOS, in_buf, secs, cand, costs=costs, opts=opts, workspace=ws, stream=stream)
+    seq = list(plan.layout_of_section[:nsec])
+    win = list(plan.window_len[:nsec])
+    model_ns = plan.model_ns
+    ts = []
+    for r in range(4):   # the solved plan, run as a fixed plan (as the other programs are timed)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if r == 3:
+            P.adha_profile_start(256)
+        a.record(stream)
+        P.adha_run_program(S, n, AOS, in_buf, secs, cand, costs=costs, opts=opts, workspace=ws, stream=stream,
+                           fixed=seq, windows=win)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if r == 3:
+            recs = P.adha_profile_stop(256)
+        if r:
+            ts.append(a.elapsed_time(b))
+    fused_ms = statistics.median(ts)
+    kern = {}
+    for r in recs:
+        g = kern.setdefault(r["kind"], [0.0, 0.0, 0])
+        g[0] += r["ms"]
+        g[1] += r["bytes"]
+        g[2] += 1
+    return {"fused_ms": round(fused_ms, 3), "fuse_window": fuse,
+            "windows": [[k, w, seq[k]] for k, w in enumerate(win) if w],
+            "window_layouts": {str(seq[k]): layouts[seq[k]].groups for k, w in enumerate(win) if w},
+            "model_ns": model_ns,
+            "speedup_vs_adha": round(adha_ms / fused_ms, 3), "speedup_vs_aos": round(t_aos / fused_ms, 3),
+            "speedup_vs_soa": round(t_soa / fused_ms, 3),
+            "kernels": {k: {"launches": v[2], "ms": round(v[0], 3), "alg_GBs": round(v[1] / (v[0] * 1e6), 1)}
+                        for k, v in kern.items()},
+            "note": "windows: [first section, sections fused, candidate]; a fused kernel's algorithmic bytes are "
+                    "the union of its sections' fields read once plus written fields written once"}
 
 
 # ---------------------------------------------------------------------------------- other workloads

@@ -871,8 +871,18 @@ static int plan_fused(const Layout& L, void* const* ptrs, const adha_section* s,
     if (any) groups.push_back(g);
   }
   int rec = perm ? 4 : 0;
-  for (int g : groups) rec += L.stride[g];
-  int R = tuned_R ? std::max(32, std::min(tuned_R, 128)) : (rec > 0 ? pick_chunk(rec, 4096, 128) : 128);
+  bool one_field = true;
+  for (int g : groups) {
+    rec += L.stride[g];
+    one_field = one_field && L.groups[g].size() == 1;
+  }
+  // default chunk: with one-field groups the longest of 128 / 64 records whose buffers leave room
+  // for two CTAs per SM (the vector mapping needs 64 or more), else about 4 KB of records
+  int R = 32;
+  if (tuned_R) R = std::max(32, std::min(tuned_R, 128));
+  else if (one_field && (size_t)kWarps * 2 * 128 * rec <= (size_t)kSmemLimit / 2 - 4096) R = 128;
+  else if (one_field && (size_t)kWarps * 2 * 64 * rec <= (size_t)kSmemLimit / 2 - 4096) R = 64;
+  else R = rec > 0 ? pick_chunk(rec, 4096, 128) : 128;
   if (R != 32 && R != 64 && R != 128) R = R < 64 ? 32 : 64;
   for (;;) {
     a.n = n;
@@ -888,7 +898,7 @@ static int plan_fused(const Layout& L, void* const* ptrs, const adha_section* s,
       a.f[f].dtype = L.dtype[f];
     }
     int off = 0;
-    bool vec = R >= 64;
+    bool vec = true;
     for (int k = 0; k < a.n_load; ++k) {
       const int g = groups[k];
       a.load[k].ptr = static_cast<const uint8_t*>(ptrs[g]);

@@ -18,20 +18,28 @@
 
 namespace adha {
 
-// per-CTA slice table at the start of shared memory: pointers, slice ends, write-back flags
-constexpr int kFusedTable = (16 * (kMaxGroups + 1) + 15) / 16 * 16;
+// per-CTA tables at the start of shared memory: the slice table (pointers, slice ends, write-back
+// flags), then copies of the field table and of the sections' operands.  The compute loops look
+// fields and operands up by runtime index once per field per chunk and section; from the
+// parameter space each such lookup is an indexed constant load, whose unit saturates long before
+// the memory system does, while shared-memory loads of one address broadcast to the warp.
+constexpr int kSliceTable = (16 * (kMaxGroups + 1) + 15) / 16 * 16;
+constexpr int kFieldTable = (int)sizeof(FieldRef) * kMaxFields;
+constexpr int kFusedTable = kSliceTable + kFieldTable + (int)sizeof(SecOp) * kMaxFused;
+static_assert(sizeof(FieldRef) % 8 == 0 && sizeof(SecOp) % 4 == 0, "tables are copied in whole words");
+
 
 // One section on the M records of each lane of a staged chunk (r = lane + 32m), writes into the
 // chunk buffer; op is runtime (uniform over the launch).
 template <int M>
-__device__ __forceinline__ void fused_section_chunk(const FusedArgs& a, const SecOp& so, uint8_t* cur, int64_t i0,
-                                                    const int32_t* ps, int lane) {
+__device__ __forceinline__ void fused_section_chunk(const FusedArgs& a, const FieldRef* fr, const SecOp& so,
+                                                    uint8_t* cur, int64_t i0, const int32_t* ps, int lane) {
   switch (so.op) {
 #define ADHA_FUSED_OP(OP)                                                                                 \
   case OP:                                                                                                \
     _Pragma("unroll") for (int m = 0; m < M; ++m) {                                                       \
       const int r = lane + 32 * m;                                                                        \
-      run_record<OP>(so, a.f, a.tanh_p, a.tanh_q, nullptr, StagedRec{a.f, cur, r, i0 + r}, i0 + r,       \
+      run_record<OP>(so, fr, a.tanh_p, a.tanh_q, nullptr, StagedRec{fr, cur, r, i0 + r}, i0 + r,         \
                      ps ? ps[r] : 0);                                                                     \
     }                                                                                                     \
     break;
@@ -54,11 +62,12 @@ __device__ __forceinline__ void fused_section_chunk(const FusedArgs& a, const Se
 }
 
 // One section on one record in global memory (the ragged tail).
-__device__ __forceinline__ void fused_section_record(const FusedArgs& a, const SecOp& so, int64_t i, int32_t pj) {
-  const GlobalRec rec{a.f, i};
+__device__ __forceinline__ void fused_section_record(const FusedArgs& a, const FieldRef* fr, const SecOp& so, int64_t i,
+                                                     int32_t pj) {
+  const GlobalRec rec{fr, i};
   switch (so.op) {
 #define ADHA_FUSED_OP(OP) \
-  case OP: run_record<OP>(so, a.f, a.tanh_p, a.tanh_q, nullptr, rec, i, pj); break;
+  case OP: run_record<OP>(so, fr, a.tanh_p, a.tanh_q, nullptr, rec, i, pj); break;
     ADHA_FUSED_OP(ADHA_OP_MADD3)
     ADHA_FUSED_OP(ADHA_OP_XORSHIFT)
     ADHA_FUSED_OP(ADHA_OP_ADD)
@@ -93,6 +102,12 @@ __global__ void __launch_bounds__(kThreads) fused_kernel(const __grid_constant__
     send[k] = a.load[k].start + R * a.load[k].stride;
     wback[k] = a.writeback[k];
   }
+  FieldRef* fr = reinterpret_cast<FieldRef*>(smem + kSliceTable);
+  SecOp* secs = reinterpret_cast<SecOp*>(smem + kSliceTable + kFieldTable);
+  for (int k = tid; k < kMaxFields * (int)(sizeof(FieldRef) / 8); k += kThreads)
+    reinterpret_cast<uint2*>(fr)[k] = reinterpret_cast<const uint2*>(a.f)[k];
+  for (int k = tid; k < a.n_sec * (int)(sizeof(SecOp) / 4); k += kThreads)
+    reinterpret_cast<uint32_t*>(secs)[k] = reinterpret_cast<const uint32_t*>(a.sec)[k];
   __syncthreads();
 
   const int64_t W = (int64_t)gridDim.x * kWarps;
@@ -117,12 +132,13 @@ __global__ void __launch_bounds__(kThreads) fused_kernel(const __grid_constant__
     const int64_t i0 = c * R;
     const int32_t* ps = a.perm_slot >= 0 ? reinterpret_cast<const int32_t*>(cur + a.load[a.perm_slot].start) : nullptr;
     for (int s = 0; s < a.n_sec; ++s) {
-      const SecOp& so = a.sec[s];
-      if (VEC && so.op == ADHA_OP_MIX) mix_chunk_vec<M, true>(so, a.f, cur, i0, lane);
-      else if (VEC && so.op == ADHA_OP_AXPB) chain_chunk_vec<ADHA_OP_AXPB, M, true>(so, a.f, a.tanh_p, a.tanh_q, nullptr, cur, i0, lane);
-      else if (VEC && so.op == ADHA_OP_MUL) chain_chunk_vec<ADHA_OP_MUL, M, true>(so, a.f, a.tanh_p, a.tanh_q, nullptr, cur, i0, lane);
-      else if (VEC && so.op == ADHA_OP_TANH) chain_chunk_vec<ADHA_OP_TANH, M, true>(so, a.f, a.tanh_p, a.tanh_q, nullptr, cur, i0, lane);
-      else fused_section_chunk<M>(a, so, cur, i0, ps, lane);
+      const SecOp& so = secs[s];
+      const int op = so.op;
+      if (VEC && op == ADHA_OP_MIX) mix_chunk_vec<M, true>(so, fr, cur, i0, lane);
+      else if (VEC && op == ADHA_OP_AXPB) chain_chunk_vec<ADHA_OP_AXPB, M, true>(so, fr, a.tanh_p, a.tanh_q, nullptr, cur, i0, lane);
+      else if (VEC && op == ADHA_OP_MUL) chain_chunk_vec<ADHA_OP_MUL, M, true>(so, fr, a.tanh_p, a.tanh_q, nullptr, cur, i0, lane);
+      else if (VEC && op == ADHA_OP_TANH) chain_chunk_vec<ADHA_OP_TANH, M, true>(so, fr, a.tanh_p, a.tanh_q, nullptr, cur, i0, lane);
+      else fused_section_chunk<M>(a, fr, so, cur, i0, ps, lane);
       __syncwarp();   // the next section may map records to lanes the other way
     }
     // groups with written fields go back whole, 16 bytes per lane per step
@@ -144,7 +160,7 @@ __global__ void __launch_bounds__(kThreads) fused_kernel(const __grid_constant__
   if (c == a.n_chunks && t0 < a.n) {
     for (int64_t i = t0 + lane; i < a.n; i += 32) {
       const int32_t pj = a.perm_slot >= 0 ? a.perm[i] : 0;
-      for (int s = 0; s < a.n_sec; ++s) fused_section_record(a, a.sec[s], i, pj);
+      for (int s = 0; s < a.n_sec; ++s) fused_section_record(a, fr, secs[s], i, pj);
     }
   }
 }
@@ -162,6 +178,7 @@ static int launch_m(const FusedArgs& a, int grid, size_t smem, void* stream) {
 }
 
 int launch_fused(const FusedArgs& a, int grid, size_t smem, void* stream) {
+  if (a.vec && a.R == 32) return launch_m<1, true>(a, grid, smem, stream);
   if (a.vec && a.R == 64) return launch_m<2, true>(a, grid, smem, stream);
   if (a.vec && a.R == 128) return launch_m<4, true>(a, grid, smem, stream);
   switch (a.R) {
@@ -181,6 +198,7 @@ static int occ_m(size_t smem, int* blocks) {
 }
 
 int fused_occupancy(int M, bool vec, size_t smem, int* blocks) {
+  if (vec && M == 1) return occ_m<1, true>(smem, blocks);
   if (vec && M == 2) return occ_m<2, true>(smem, blocks);
   if (vec && M == 4) return occ_m<4, true>(smem, blocks);
   if (M == 1) return occ_m<1, false>(smem, blocks);

@@ -19,6 +19,8 @@
 
 namespace adha {
 
+constexpr int kFusedLayouts = 8;   // candidates a fused run is timed in (its cheapest one by one)
+
 static size_t round256(size_t x) { return (x + 255) / 256 * 256; }
 
 static size_t layout_bytes(const Layout& L, int64_t n) {
@@ -240,11 +242,6 @@ int adha_measure(const adha_schema* schema, int64_t n, const adha_layout* in_lay
       }
       t->section_ns[(size_t)k * L + a] = ns;
     }
-    for (size_t r = 0; r < runs.size() && !rc; ++r) {
-      const int k = runs[r].first, m = runs[r].second;
-      rc = time_ns(timer, stream, reps, [&] { return run_fused_layout(cand[a], pa.data(), &sections[k], m, n, stream); }, &ns);
-      t->fused_ns[((size_t)k * W + (m - 1)) * L + a] = ns;
-    }
     for (int b = 0; b <= L && !rc; ++b) {
       if (b == a) continue;
       const Layout& D = b < L ? cand[b] : in;
@@ -252,6 +249,56 @@ int adha_measure(const adha_schema* schema, int64_t n, const adha_layout* in_lay
       carve_after(cand[a], pa, D, n, B, &pb);
       rc = time_remap(cand[a], pa, D, pb, b == L, &ns);
       t->remap_ns[(size_t)a * (L + 1) + b] = ns;
+    }
+  }
+  // Fused runs: each run is timed in the kFusedLayouts candidates where its sections cost least
+  // one by one (the others stay +inf); under autotuning, with every chunk size (kept in the
+  // tuning cache).  Fusing reads every field once instead of once per section, so a layout that
+  // is poor for the run's sections is poor for the run too.
+  std::vector<std::vector<int>> where(runs.size());
+  std::vector<bool> used(L, false);
+  for (size_t r = 0; r < runs.size(); ++r) {
+    const int k = runs[r].first, m = runs[r].second;
+    std::vector<std::pair<double, int>> by;
+    for (int a = 0; a < L; ++a) {
+      double sum = 0;
+      for (int j = 0; j < m; ++j) sum += t->section_ns[(size_t)(k + j) * L + a];
+      by.push_back({sum, a});
+    }
+    std::sort(by.begin(), by.end());
+    for (int j = 0; j < (int)by.size() && j < kFusedLayouts; ++j) {
+      where[r].push_back(by[j].second);
+      used[by[j].second] = true;
+    }
+  }
+  for (int a = 0; a < L && !rc; ++a) {
+    if (!used[a]) continue;
+    carve(cand[a], n, A, &pa);
+    rc = remap_layouts(in, in_p.data(), cand[a], pa.data(), n, stream, nullptr);
+    for (size_t r = 0; r < runs.size() && !rc; ++r) {
+      if (std::find(where[r].begin(), where[r].end(), a) == where[r].end()) continue;
+      const int k = runs[r].first, m = runs[r].second;
+      auto run = [&] { return run_fused_layout(cand[a], pa.data(), &sections[k], m, n, stream); };
+      double ns = 0;
+      if (flags & ADHA_MEASURE_AUTOTUNE) {
+        double best = -1;
+        int bR = 0;
+        for (int R = 32; R <= 128 && !rc; R *= 2) {
+          set_overrides(R, 0);
+          rc = time_ns(timer, stream, reps, run, &ns);
+          if (!rc && (best < 0 || ns < best)) {
+            best = ns;
+            bR = R;
+          }
+        }
+        set_overrides(0, 0);
+        if (rc) break;
+        tuning_store(fused_tuning_key(cand[a], &sections[k], m, n), bR, 0);
+        ns = best;
+      } else {
+        rc = time_ns(timer, stream, reps, run, &ns);
+      }
+      t->fused_ns[((size_t)k * W + (m - 1)) * L + a] = ns;
     }
   }
   if (!rc) {

@@ -12,6 +12,32 @@
 
 namespace adha {
 
+// Exact IEEE operations done with integer instructions where the result is plain, so that the
+// fp64 pipe (a small fraction of the fp32 rate on this GPU) only does the additions.
+// x * 0.5 rounded to nearest: for a normal x whose half is normal (biased exponent 2..2046) the
+// product is exact and is x with its exponent lowered by one; zeros, subnormals, the smallest
+// normals (whose half rounds), infinities and NaNs take the multiply.
+__device__ __forceinline__ double half_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned e = (unsigned)(b >> 52) & 0x7FFu;
+  if (e >= 2u && e <= 2046u) return __longlong_as_double((long long)(b - (1ull << 52)));
+  return __dmul_rn(x, 0.5);
+}
+
+// float -> double, exact: a normal float keeps its sign and significand (shifted into the wider
+// field) and gets its exponent rebiased from 127 to 1023; zeros, subnormals, infinities and NaNs
+// take the conversion instruction.
+__device__ __forceinline__ double widen(float t) {
+  const unsigned u = __float_as_uint(t);
+  const unsigned e = (u >> 23) & 0xFFu;
+  if (e >= 1u && e <= 254u) {
+    const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                 ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)b);
+  }
+  return (double)t;
+}
+
 struct StagedRec {      // record r of a staged chunk (global record i)
   const FieldRef* f;
   uint8_t* stage;
@@ -124,7 +150,12 @@ __device__ __forceinline__ void mix_chunk(const SecOp& so, const FieldRef* fr, u
     }                                                                                       \
   }
   ADHA_MIX_WRITE(float, ADHA_F32, __fadd_rn(__fmul_rn(old, 0.5f), t[m]))
-  ADHA_MIX_WRITE(double, ADHA_F64, __dadd_rn(__dmul_rn(old, 0.5), (double)t[m]))
+  if (so.wr_off[ADHA_F64 + 1] > so.wr_off[ADHA_F64]) {
+    double td[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) td[m] = widen(t[m]);
+    ADHA_MIX_WRITE(double, ADHA_F64, __dadd_rn(half_rn(old), td[m]))
+  }
   ADHA_MIX_WRITE(uint32_t, ADHA_I32, old ^ k[m])
   ADHA_MIX_WRITE(uint16_t, ADHA_BF16, (uint16_t)(old ^ (uint16_t)(k[m] & 0xFFFFu)))
 #undef ADHA_MIX_WRITE
@@ -223,13 +254,18 @@ __device__ __forceinline__ void mix_chunk_vec(const SecOp& so, const FieldRef* f
     for (int m = 0; m < M; ++m) v[m] = __fadd_rn(__fmul_rn(v[m], 0.5f), t[m]);
     st_vec<float, M>(TO_STAGE ? stage + F.s0 + lane * M * 4 : F.g + r0 * 4, v);
   }
-  for (int j = so.wr_off[ADHA_F64]; j < so.wr_off[ADHA_F64 + 1]; ++j) {
-    const FieldRef& F = fr[so.wr[j]];
-    double v[M];
-    ld_vec<double, M>(stage + F.s0 + lane * M * 8, v);
+  if (so.wr_off[ADHA_F64 + 1] > so.wr_off[ADHA_F64]) {
+    double td[M];
 #pragma unroll
-    for (int m = 0; m < M; ++m) v[m] = __dadd_rn(__dmul_rn(v[m], 0.5), (double)t[m]);
-    st_vec<double, M>(TO_STAGE ? stage + F.s0 + lane * M * 8 : F.g + r0 * 8, v);
+    for (int m = 0; m < M; ++m) td[m] = widen(t[m]);
+    for (int j = so.wr_off[ADHA_F64]; j < so.wr_off[ADHA_F64 + 1]; ++j) {
+      const FieldRef& F = fr[so.wr[j]];
+      double v[M];
+      ld_vec<double, M>(stage + F.s0 + lane * M * 8, v);
+#pragma unroll
+      for (int m = 0; m < M; ++m) v[m] = __dadd_rn(half_rn(v[m]), td[m]);
+      st_vec<double, M>(TO_STAGE ? stage + F.s0 + lane * M * 8 : F.g + r0 * 8, v);
+    }
   }
   for (int j = so.wr_off[ADHA_I32]; j < so.wr_off[ADHA_I32 + 1]; ++j) {
     const FieldRef& F = fr[so.wr[j]];
@@ -315,10 +351,10 @@ __device__ __forceinline__ void run_record(const SecOp& so, const FieldRef* fr, 
       rec.template st<float>(f, __fadd_rn(__fmul_rn(rec.template ld<float>(f), 0.5f), t));
     }
     if (so.wr_off[ADHA_F64 + 1] > so.wr_off[ADHA_F64]) {
-      const double td = (double)t;
+      const double td = widen(t);
       for (int j = so.wr_off[ADHA_F64]; j < so.wr_off[ADHA_F64 + 1]; ++j) {
         const int f = so.wr[j];
-        rec.template st<double>(f, __dadd_rn(__dmul_rn(rec.template ld<double>(f), 0.5), td));
+        rec.template st<double>(f, __dadd_rn(half_rn(rec.template ld<double>(f)), td));
       }
     }
     for (int j = so.wr_off[ADHA_I32]; j < so.wr_off[ADHA_I32 + 1]; ++j) {
@@ -354,7 +390,7 @@ __device__ __forceinline__ void run_record(const SecOp& so, const FieldRef* fr, 
     float s = __fadd_rn(__fmul_rn(vx, vx), __fmul_rn(vy, vy));
     s = __fadd_rn(s, __fmul_rn(vz, vz));
     const float e = __fmul_rn(__fmul_rn(0.5f, rec.template ld<float>(g[3])), s);
-    rec.template st<double>(g[4], (double)e);
+    rec.template st<double>(g[4], widen(e));
   } else if (OP == ADHA_OP_FLAGS) {
     const uint32_t fl = rec.template ld<uint32_t>(g[0]);
     const uint32_t bit = rec.template ld<double>(g[1]) > (double)so.par[0] ? 1u : 0u;

@@ -171,3 +171,66 @@ def test_chain_sections_vector_mapping(P, R, save_offset):
                 assert np.array_equal(sbuf.cpu().numpy(), fields[z])
     finally:
         P.adha_tune_override(0)
+
+
+def _special_f64(rng, n):
+    """fp64 values around every case of halving: zeros, subnormals, the smallest normals (whose half
+    rounds), exponent 2 (whose half is the smallest normal), the largest finite values, infinities."""
+    tiny = np.finfo(np.float64).tiny
+    pool = np.array([0.0, -0.0, 5e-324, -5e-324, 3 * 5e-324, tiny, -tiny, 1.5 * tiny, 2 * tiny, 3 * tiny,
+                     np.nextafter(2 * tiny, 0), 4 * tiny, 1.0, -0.75, 1e300, np.finfo(np.float64).max,
+                     -np.finfo(np.float64).max, np.inf, -np.inf], dtype=np.float64)
+    v = rng.choice(pool, n)
+    bits = rng.integers(0, 1 << 62, n, dtype=np.int64).view(np.float64)     # random finite doubles too
+    pick = rng.random(n) < 0.3
+    v[pick] = bits[pick]
+    return v
+
+
+def _special_f32(rng, n):
+    """fp32 values whose sum is zero, subnormal, the smallest normal or an ordinary number."""
+    tiny = np.finfo(np.float32).tiny
+    pool = np.array([0.0, -0.0, 1e-45, -1e-45, tiny / 2, tiny, -tiny, 2 * tiny, 0.5, -0.25], dtype=np.float32)
+    return rng.choice(pool, n).astype(np.float32)
+
+
+@pytest.mark.parametrize("groups", [[[0], [1], [2], [3], [4]], [[0, 1, 2, 3, 4]], [[2, 0], [4, 3, 1]]])
+@pytest.mark.parametrize("R", [32, 64, 128])
+def test_mix_fp64_special_values(P, groups, R):
+    """The fp64 update w*0.5 + (double)t near every special case of the exact integer shortcuts
+    (halving by the exponent, widening a normal float), each path against the oracle bit for bit."""
+    n = 4 * 128 * 152 + 19
+    rng = np.random.default_rng(R + len(groups))
+    dtypes = [synth.workloads.F32, synth.workloads.F32, synth.workloads.F64, synth.workloads.F64,
+              synth.workloads.I32]
+    i32 = (rng.integers(0, 1 << 20, n).astype(np.int64) * 256 * (rng.random(n) < 0.5)).astype(np.uint32)
+    fields = [_special_f32(rng, n), _special_f32(rng, n), _special_f64(rng, n), _special_f64(rng, n),
+              i32.view(np.int32)]
+    fs = synth.workloads._fs
+    sections = [synth.Section("mix", (), fs(0, 1, 2, 3, 4), fs(2, 3)),
+                synth.Section("mix", (), fs(0, 1, 2, 3, 4), fs(0, 2, 3, 4)),
+                synth.Section("mix", (), fs(1, 2), fs(2))]
+    S, L = P.Schema(dtypes), P.Layout(groups)
+    P.adha_tune_override(R)
+    try:
+        for sec in sections:
+            bufs = to_device(n, dtypes, groups, fields)
+            P.adha_run_section(S, n, L, bufs, P.c_section(sec))
+            torch.cuda.synchronize()
+            want = [a.copy() for a in fields]
+            oracle.section(sec, dtypes, want, None)
+            got = from_device(n, dtypes, groups, bufs)
+            for f in range(len(dtypes)):
+                assert np.array_equal(got[f].view(np.uint8), want[f].view(np.uint8)), "field %d of %r" % (f, sec.write)
+        # the same three sections fused in one pass
+        bufs = to_device(n, dtypes, groups, fields)
+        P.adha_run_sections_fused(S, n, L, bufs, P.Sections(sections))
+        torch.cuda.synchronize()
+        want = [a.copy() for a in fields]
+        for sec in sections:
+            oracle.section(sec, dtypes, want, None)
+        got = from_device(n, dtypes, groups, bufs)
+        for f in range(len(dtypes)):
+            assert np.array_equal(got[f].view(np.uint8), want[f].view(np.uint8)), "fused field %d" % f
+    finally:
+        P.adha_tune_override(0)
