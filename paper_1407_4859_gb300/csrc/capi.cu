@@ -842,6 +842,10 @@ static double fused_bytes(const Layout& L, const adha_section* s, int m, int64_t
   return b * (double)n;
 }
 
+// A fused run computes long per chunk, so by default one chunk buffer per warp (more CTAs per SM,
+// the next chunk's copy issued after the write-back) beats double buffering.
+constexpr int kFusedBuffers = 1;
+
 struct FusedPlan {
   FusedArgs args;
   int grid = 0;
@@ -851,11 +855,14 @@ struct FusedPlan {
 static int plan_fused(const Layout& L, void* const* ptrs, const adha_section* s, int m, int64_t n, FusedPlan* plan) {
   FusedArgs& a = plan->args;
   std::memset(&a, 0, sizeof a);
-  int tuned_R = t_tile_override;
-  if (!tuned_R) {
+  int tuned_R = t_tile_override, tuned_buffers = t_writeback_mode;   // the store mode knob picks the buffers here
+  if (!tuned_R && !tuned_buffers) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(fused_key(L, s, m, n));
-    if (it != g_tune.end()) tuned_R = it->second.first;
+    if (it != g_tune.end()) {
+      tuned_R = it->second.first;
+      tuned_buffers = it->second.second;
+    }
   }
   uint64_t staged = 0, written = 0;
   const int32_t* perm = nullptr;
@@ -925,6 +932,7 @@ static int plan_fused(const Layout& L, void* const* ptrs, const adha_section* s,
     }
     a.in_bytes = off;
     a.vec = vec ? 1 : 0;
+    a.buffers = tuned_buffers == 1 || tuned_buffers == 2 ? tuned_buffers : kFusedBuffers;
     plan->smem = fused_smem_bytes(a);
     if (plan->smem <= (size_t)kSmemLimit) break;
     if (R <= 32) return fail(ADHA_EINVAL, "the fused run's records are too wide for a 32-record chunk");

@@ -94,8 +94,9 @@ __global__ void __launch_bounds__(kThreads) fused_kernel(const __grid_constant__
   const uint8_t** sp = reinterpret_cast<const uint8_t**>(smem);
   int* send = reinterpret_cast<int*>(smem + 8 * (kMaxGroups + 1));
   int* wback = send + (kMaxGroups + 1);
-  uint8_t* buf0 = smem + kFusedTable + (size_t)warp * 2 * a.in_bytes;
-  uint8_t* buf1 = buf0 + a.in_bytes;
+  const int nb = a.buffers;   // 2: the next chunk is staged while one is computed; 1: one buffer
+  uint8_t* buf0 = smem + kFusedTable + (size_t)warp * nb * a.in_bytes;
+  uint8_t* buf1 = buf0 + (nb - 1) * a.in_bytes;
   constexpr int R = 32 * M;
   for (int k = tid; k < n_slices; k += kThreads) {
     sp[k] = a.load[k].ptr;
@@ -125,9 +126,13 @@ __global__ void __launch_bounds__(kThreads) fused_kernel(const __grid_constant__
   cp_async_commit();
   for (int i = 0; c < a.n_chunks; c += W, ++i) {
     uint8_t* cur = (i & 1) ? buf1 : buf0;
-    if (c + W < a.n_chunks) stage(c + W, (i & 1) ? buf0 : buf1);
-    cp_async_commit();
-    cp_async_wait<1>();
+    if (nb == 2) {
+      if (c + W < a.n_chunks) stage(c + W, (i & 1) ? buf0 : buf1);
+      cp_async_commit();
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
     __syncwarp();
     const int64_t i0 = c * R;
     const int32_t* ps = a.perm_slot >= 0 ? reinterpret_cast<const int32_t*>(cur + a.load[a.perm_slot].start) : nullptr;
@@ -152,6 +157,10 @@ __global__ void __launch_bounds__(kThreads) fused_kernel(const __grid_constant__
       }
     }
     __syncwarp();
+    if (nb == 1 && c + W < a.n_chunks) {   // one buffer: the next chunk once this one has gone back
+      stage(c + W, buf0);
+      cp_async_commit();
+    }
   }
   cp_async_wait<0>();
 
@@ -165,7 +174,7 @@ __global__ void __launch_bounds__(kThreads) fused_kernel(const __grid_constant__
   }
 }
 
-size_t fused_smem_bytes(const FusedArgs& a) { return kFusedTable + (size_t)kWarps * 2 * a.in_bytes; }
+size_t fused_smem_bytes(const FusedArgs& a) { return kFusedTable + (size_t)kWarps * a.buffers * a.in_bytes; }
 
 template <int M, bool VEC>
 static int launch_m(const FusedArgs& a, int grid, size_t smem, void* stream) {

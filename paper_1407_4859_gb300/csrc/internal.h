@@ -144,6 +144,7 @@ struct FusedArgs {
   int32_t perm_slot;            // index of the staged perm slice (a gather in the run), else -1
   int32_t n_sec;
   int32_t vec;                  // 1: every staged group is one field wide
+  int32_t buffers;              // chunk buffers per warp (1 or 2)
   GroupRef load[kMaxGroups + 1];
   int8_t writeback[kMaxGroups + 1];
   FieldRef f[kMaxFields];

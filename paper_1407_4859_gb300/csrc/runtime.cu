@@ -252,8 +252,8 @@ int adha_measure(const adha_schema* schema, int64_t n, const adha_layout* in_lay
     }
   }
   // Fused runs: each run is timed in the kFusedLayouts candidates where its sections cost least
-  // one by one (the others stay +inf); under autotuning, with every chunk size (kept in the
-  // tuning cache).  Fusing reads every field once instead of once per section, so a layout that
+  // one by one (the others stay +inf); under autotuning, with four launch shapes (records per
+  // chunk x chunk buffers, kept in the tuning cache).  Fusing reads every field once instead of once per section, so a layout that
   // is poor for the run's sections is poor for the run too.
   std::vector<std::vector<int>> where(runs.size());
   std::vector<bool> used(L, false);
@@ -281,19 +281,22 @@ int adha_measure(const adha_schema* schema, int64_t n, const adha_layout* in_lay
       auto run = [&] { return run_fused_layout(cand[a], pa.data(), &sections[k], m, n, stream); };
       double ns = 0;
       if (flags & ADHA_MEASURE_AUTOTUNE) {
+        // records per chunk x chunk buffers per warp: one buffer at 32 / 64 / 128, two at 64
+        const int shapes[4][2] = {{32, 1}, {64, 1}, {128, 1}, {64, 2}};
         double best = -1;
-        int bR = 0;
-        for (int R = 32; R <= 128 && !rc; R *= 2) {
-          set_overrides(R, 0);
+        int bR = 0, bB = 0;
+        for (int q = 0; q < 4 && !rc; ++q) {
+          set_overrides(shapes[q][0], shapes[q][1]);
           rc = time_ns(timer, stream, reps, run, &ns);
           if (!rc && (best < 0 || ns < best)) {
             best = ns;
-            bR = R;
+            bR = shapes[q][0];
+            bB = shapes[q][1];
           }
         }
         set_overrides(0, 0);
         if (rc) break;
-        tuning_store(fused_tuning_key(cand[a], &sections[k], m, n), bR, 0);
+        tuning_store(fused_tuning_key(cand[a], &sections[k], m, n), bR, bB);
         ns = best;
       } else {
         rc = time_ns(timer, stream, reps, run, &ns);

@@ -14,7 +14,6 @@
 #include "internal.h"
 #include "ptx.cuh"
 #include "section_ops.cuh"
-#include "remap_common.cuh"
 
 namespace adha {
 
@@ -30,11 +29,7 @@ __global__ void __launch_bounds__(kThreads) section_kernel(const __grid_constant
   const uint8_t** sp = reinterpret_cast<const uint8_t**>(smem);
   int* send = reinterpret_cast<int*>(smem + 8 * (kMaxGroups + 1));
   int* wback = send + (kMaxGroups + 1);
-  // piece table: where each 16-byte piece of a chunk buffer comes from (the same for every chunk
-  // up to the chunk's offset), so staging needs no search over the slices
-  const int n_pieces = a.in_bytes / 16;
-  Piece* pt = reinterpret_cast<Piece*>(smem + kSectionTable);
-  uint8_t* buf0 = smem + kSectionTable + (size_t)a.in_bytes + (size_t)warp * 2 * a.in_bytes;
+  uint8_t* buf0 = smem + kSectionTable + (size_t)warp * 2 * a.in_bytes;
   uint8_t* buf1 = buf0 + a.in_bytes;
   constexpr int R = 32 * M;
   for (int k = tid; k < n_slices; k += kThreads) {
@@ -42,17 +37,18 @@ __global__ void __launch_bounds__(kThreads) section_kernel(const __grid_constant
     send[k] = a.load[k].start + R * a.load[k].stride;
     wback[k] = a.writeback[k];
   }
-  for (int q = tid; q < n_pieces; q += kThreads) pt[q] = piece_of(q, a.load, R);
   __syncthreads();
 
   const int64_t W = (int64_t)gridDim.x * kWarps;
-  // The chunk's slices are contiguous in the buffer, so the warp walks the whole buffer in 16-byte
-  // pieces (512 bytes per step, every lane busy).
+  // The chunk's slices are contiguous in the buffer and each a multiple of 64 bytes, so the
+  // warp walks the whole buffer in 16-byte pieces (512 bytes per step, every lane busy); piece
+  // p of slice g comes from byte (ch*R*stride_g + p - start_g) of group g.
   auto stage = [&](int64_t ch, uint8_t* buf) {
-#pragma unroll 1
-    for (int q = lane; q < n_pieces; q += 32) {
-      const Piece pc = pt[q];
-      cp_async16(buf + q * 16, pc.base + ch * pc.step);
+    int g = 0, start = 0;
+    for (int p = lane * 16; p < a.in_bytes; p += 512) {
+      while (p >= send[g]) start = send[g++];
+      const int64_t stride = (send[g] - start) / R;
+      cp_async16(buf + p, sp[g] + ch * (R * stride) + (p - start));
     }
   };
 
@@ -163,7 +159,7 @@ __global__ void __launch_bounds__(kThreads) backward_kernel(const __grid_constan
   }
 }
 
-size_t section_smem_bytes(const SectionArgs& a) { return kSectionTable + (size_t)(kWarps * 2 + 1) * a.in_bytes; }
+size_t section_smem_bytes(const SectionArgs& a) { return kSectionTable + (size_t)kWarps * 2 * a.in_bytes; }
 
 template <int OP, int M, bool VEC>
 static int launch_om(const SectionArgs& a, int grid, size_t smem, void* stream) {
