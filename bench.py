@@ -467,12 +467,14 @@ def fused_comparison(P, torch, S, n, AOS, in_buf, secs, cand, costs, ws, stream,
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         if r == 3:
             P.adha_profile_start(256)
+            torch.cuda.nvtx.range_push("fused")
         a.record(stream)
         P.adha_run_program(S, n, AOS, in_buf, secs, cand, costs=costs, opts=opts, workspace=ws, stream=stream,
                            fixed=seq, windows=win)
         b.record(stream)
         torch.cuda.synchronize()
         if r == 3:
+            torch.cuda.nvtx.range_pop()
             recs = P.adha_profile_stop(256)
         if r:
             ts.append(a.elapsed_time(b))
