@@ -310,10 +310,16 @@ typedef struct {
 /* adha_measure flags. */
 #define ADHA_MEASURE_AUTOTUNE 1   /* time every section launch shape, keep the fastest for later launches */
 #define ADHA_MEASURE_FUSE(w) ((int32_t)(w) << 8)   /* also time every fusable run of 2..w sections (w <= 16) */
+#define ADHA_MEASURE_DIFFERENTIABLE 2   /* costs of a forward + backward step (see adha_measure) */
 
 /* Workspace bytes adha_measure needs: two copies of the widest candidate (or input) layout. */
 size_t adha_measure_workspace_bytes(const adha_schema* schema, int64_t n, const adha_layout* in_layout,
                                     const adha_layout_set* candidates);
+
+/* The same for given adha_measure flags: with ADHA_MEASURE_DIFFERENTIABLE, three
+ * copies plus n floats (the gradients and one section's saved values). */
+size_t adha_measure_workspace_bytes_for(const adha_schema* schema, int64_t n, const adha_layout* in_layout,
+                                        const adha_layout_set* candidates, int32_t flags);
 
 /*
  * The tuning profile of PDL (paper Section 2: execution times measured per
@@ -329,6 +335,12 @@ size_t adha_measure_workspace_bytes(const adha_schema* schema, int64_t n, const 
  * the input layout under every choice of piece tables (adha_tune_remap_pieces);
  * the fastest enters the table and the library's tuning cache, which later
  * launches of the same section (or pair of layouts), layout and size class use.
+ * With ADHA_MEASURE_DIFFERENTIABLE (fp32 schemas whose sections are all axpb,
+ * mul or tanh) the table prices a forward + backward step instead: a section
+ * costs its forward launch with the overwritten values saved plus its adjoint
+ * kernel (adha_section_backward) in that layout, and a remap edge costs the
+ * remap plus its inverse (the gradients travel back through it), so
+ * remap_ns[a][b] = remap_ns[b][a]; fused runs are not timed then.
  * Synchronizes `stream`; *out is a library-owned table (adha_free).
  */
 int adha_measure(const adha_schema* schema, int64_t n, const adha_layout* in_layout, void* const* in_ptrs,

@@ -121,6 +121,9 @@ SIGNATURES = {
                                             ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_double)]),
     "adha_measure_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(adha_schema), _I64, ctypes.POINTER(adha_layout),
                                                        ctypes.POINTER(adha_layout_set)]),
+    "adha_measure_workspace_bytes_for": (ctypes.c_size_t, [ctypes.POINTER(adha_schema), _I64,
+                                                           ctypes.POINTER(adha_layout), ctypes.POINTER(adha_layout_set),
+                                                           _I32]),
     "adha_measure": (ctypes.c_int, [ctypes.POINTER(adha_schema), _I64, ctypes.POINTER(adha_layout), _PP,
                                     ctypes.POINTER(adha_section), _I32, ctypes.POINTER(adha_layout_set), _I32, _I32,
                                     _P, ctypes.c_size_t, _P, ctypes.POINTER(ctypes.POINTER(adha_cost_table))]),

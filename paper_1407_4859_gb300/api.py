@@ -341,25 +341,28 @@ def adha_pdl_solve_fused(costs, return_to_input=False, max_window=0):
     return tot.value, list(seq), list(win)
 
 
-def adha_measure_workspace_bytes(schema, n, in_layout, candidates):
-    return _lib.load().adha_measure_workspace_bytes(ctypes.byref(schema.c), int(n), ctypes.byref(in_layout.c),
-                                                    candidates.ptr)
+def adha_measure_workspace_bytes(schema, n, in_layout, candidates, flags=0):
+    return _lib.load().adha_measure_workspace_bytes_for(ctypes.byref(schema.c), int(n), ctypes.byref(in_layout.c),
+                                                        candidates.ptr, int(flags))
 
 
 ADHA_MEASURE_AUTOTUNE = 1
+ADHA_MEASURE_DIFFERENTIABLE = 2
 
 
 def adha_measure(schema, n, in_layout, in_bufs, sections, candidates, reps=2, workspace=None, stream=None,
-                 autotune=False, fuse_window=0):
+                 autotune=False, fuse_window=0, differentiable=False):
     """Cost table of every section in every candidate and every remap between candidates (and, with
-    fuse_window >= 2, of every run of 2..fuse_window sections that may be fused)."""
+    fuse_window >= 2, of every run of 2..fuse_window sections that may be fused; with differentiable,
+    of a forward + backward step)."""
     secs = sections if isinstance(sections, Sections) else Sections(sections)
-    need = adha_measure_workspace_bytes(schema, n, in_layout, candidates)
+    flags = ((ADHA_MEASURE_AUTOTUNE if autotune else 0) | (ADHA_MEASURE_DIFFERENTIABLE if differentiable else 0)
+             | (int(fuse_window) << 8))
+    need = adha_measure_workspace_bytes(schema, n, in_layout, candidates, flags)
     ws = workspace if workspace is not None else torch.empty(need, dtype=torch.uint8, device=in_bufs[0].device)
     out = ctypes.POINTER(adha_cost_table)()
     check(_lib.load().adha_measure(ctypes.byref(schema.c), int(n), ctypes.byref(in_layout.c), _ptrs(in_bufs),
-                                   secs.arr, len(secs), candidates.ptr, int(reps),
-                                   (ADHA_MEASURE_AUTOTUNE if autotune else 0) | (int(fuse_window) << 8),
+                                   secs.arr, len(secs), candidates.ptr, int(reps), flags,
                                    ws.data_ptr(), ws.numel(),
                                    _stream_ptr(stream), ctypes.byref(out)), "adha_measure")
     return CostTable(out)

@@ -10,6 +10,7 @@ fp32, so a group's struct is k contiguous floats).  Two autograd Functions:
 * SegmentFn: runs a run of axpb / mul / tanh sections in place in one layout, saving each value a
   section overwrites; its backward walks the sections in reverse with the adjoint kernel
   (adha_section_backward), which restores the overwritten field and propagates the adjoints.
+* CopyFn: a copy of the state by the remap kernel, where the first section keeps the input layout.
 
 DifferentiableProgram strings them together for a whole program under a layout plan.  Every
 forward and backward step runs in the library's kernels; PyTorch only allocates and orders them.
@@ -20,6 +21,28 @@ forward outputs hold the input-side values once backward() has run (copy them fi
 import torch
 
 from .api import c_section, adha_remap, adha_run_section, adha_section_backward
+
+
+def _copy(schema, n, layout, groups):
+    """Fresh copies of a layout's group tensors, moved by the library's remap kernel (identical
+    groups at different addresses are copied, not aliased)."""
+    out = [torch.empty_like(g) for g in groups]
+    adha_remap(schema, n, layout, list(groups), layout, out)
+    return out
+
+
+class CopyFn(torch.autograd.Function):
+    """A copy of the state (sections then update the copy in place and leave the inputs intact);
+    its backward passes the gradients through."""
+
+    @staticmethod
+    def forward(ctx, meta, *groups):
+        schema, n, layout = meta
+        return tuple(_copy(schema, n, layout, groups))
+
+    @staticmethod
+    def backward(ctx, *grads):
+        return (None,) + grads
 
 
 def _alias_map(src, dst):
@@ -96,8 +119,11 @@ class SegmentFn(torch.autograd.Function):
     @staticmethod
     def backward(ctx, *grads):
         schema, n, layout = ctx.meta
-        g = [x.clone() if x is not None else torch.zeros((n, len(layout.groups[k])), dtype=torch.float32, device="cuda")
+        # the adjoint kernels update the gradients in place: work on copies of the incoming ones
+        g = [x.contiguous() if x is not None else torch.zeros((n, len(layout.groups[k])), dtype=torch.float32,
+                                                              device="cuda")
              for k, x in enumerate(grads)]
+        g = _copy(schema, n, layout, g)
         for cs, save in reversed(ctx.saves):
             adha_section_backward(schema, n, layout, list(ctx.state), g, cs, save)
         ctx.saves = None
@@ -137,7 +163,7 @@ class DifferentiableProgram:
                 state = self._remap(state, cur, lay)
                 cur = lay
             elif first:
-                state = [x.clone() for x in state]   # sections update in place; leave the inputs intact
+                state = list(CopyFn.apply((self.schema, self.n, cur), *state))   # leave the inputs intact
             first = False
             state = list(SegmentFn.apply((self.schema, self.n, cur, self.sections[k:j]), *state))
             k = j

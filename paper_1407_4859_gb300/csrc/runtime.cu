@@ -138,15 +138,21 @@ using namespace adha;
 
 extern "C" {
 
-size_t adha_measure_workspace_bytes(const adha_schema* schema, int64_t n, const adha_layout* in_layout,
-                                    const adha_layout_set* candidates) {
+size_t adha_measure_workspace_bytes_for(const adha_schema* schema, int64_t n, const adha_layout* in_layout,
+                                        const adha_layout_set* candidates, int32_t flags) {
   clear_error();
   Layout in;
   std::vector<Layout> cand;
   if (make_layout(schema, in_layout, &in, "input") || load_set(schema, candidates, &cand)) return 0;
   size_t m = layout_bytes(in, n);
   for (const Layout& L : cand) m = std::max(m, layout_bytes(L, n));
-  return 2 * m;
+  // differentiable: a third copy for the gradients and the saved values of one section
+  return (flags & ADHA_MEASURE_DIFFERENTIABLE) ? 3 * m + round256((size_t)n * 4) : 2 * m;
+}
+
+size_t adha_measure_workspace_bytes(const adha_schema* schema, int64_t n, const adha_layout* in_layout,
+                                    const adha_layout_set* candidates) {
+  return adha_measure_workspace_bytes_for(schema, n, in_layout, candidates, 0);
 }
 
 int adha_measure(const adha_schema* schema, int64_t n, const adha_layout* in_layout, void* const* in_ptrs,
@@ -161,12 +167,20 @@ int adha_measure(const adha_schema* schema, int64_t n, const adha_layout* in_lay
   if (!in_ptrs || !sections || n_sec < 1 || n_sec > ADHA_MAX_SECTIONS || !out)
     return fail(ADHA_EINVAL, "bad arguments to adha_measure");
   if (reps < 1) reps = 2;
+  const bool diff = (flags & ADHA_MEASURE_DIFFERENTIABLE) != 0;
+  if (diff) {
+    for (int f = 0; f < in.F; ++f)
+      if (in.dtype[f] != ADHA_F32) return fail(ADHA_EINVAL, "a differentiable program has fp32 fields (field %d is not)", f);
+    for (int k = 0; k < n_sec; ++k)
+      if (sections[k].op != ADHA_OP_AXPB && sections[k].op != ADHA_OP_MUL && sections[k].op != ADHA_OP_TANH)
+        return fail(ADHA_EINVAL, "a differentiable program has axpb, mul and tanh sections (section %d is not)", k);
+  }
   size_t m = layout_bytes(in, n);
   for (const Layout& L : cand) m = std::max(m, layout_bytes(L, n));
-  if (!workspace || ws_bytes < 2 * m)
-    return fail(ADHA_ENOMEM, "measure workspace has %zu bytes, needs %zu", ws_bytes, 2 * m);
+  const size_t need = adha_measure_workspace_bytes_for(schema, n, in_layout, candidates, flags);
+  if (!workspace || ws_bytes < need) return fail(ADHA_ENOMEM, "measure workspace has %zu bytes, needs %zu", ws_bytes, need);
   const int L = (int)cand.size();
-  const int W = std::min((flags >> 8) & 0xFF, std::min(n_sec, kMaxFused));
+  const int W = diff ? 0 : std::min((flags >> 8) & 0xFF, std::min(n_sec, kMaxFused));
   adha_cost_table* t = nullptr;
   if (int rc = adha_cost_table_create_fused(n_sec, L, W >= 2 ? W : 0, &t)) return rc;
   // runs of 2..W consecutive sections that may be fused (whether they may does not depend on the layout)
@@ -176,7 +190,9 @@ int adha_measure(const adha_schema* schema, int64_t n, const adha_layout* in_lay
       if (fusable_run(in, &sections[k], m)) runs.push_back({k, m});
   uint8_t* A = static_cast<uint8_t*>(workspace);
   uint8_t* B = A + m;
-  std::vector<void*> in_p(in_ptrs, in_ptrs + in.n_groups), pa, pb;
+  uint8_t* C = B + m;                 // differentiable: gradients in layout a
+  void* saved = C + m;                // differentiable: the values one section overwrites
+  std::vector<void*> in_p(in_ptrs, in_ptrs + in.n_groups), pa, pb, pg;
   Timer timer;
   int rc = timer.init();
   auto done = [&](int code) {
@@ -217,8 +233,11 @@ int adha_measure(const adha_schema* schema, int64_t n, const adha_layout* in_lay
     // a full private copy of the input in layout a, for the section and remap timings
     carve(cand[a], n, A, &pa);
     rc = remap_layouts(in, in_p.data(), cand[a], pa.data(), n, stream, nullptr);
+    if (diff) carve(cand[a], n, C, &pg);
     for (int k = 0; k < n_sec && !rc; ++k) {
-      auto run = [&] { return run_section_layout(cand[a], pa.data(), &sections[k], n, nullptr, stream); };
+      // a differentiable program's forward sections keep what they overwrite
+      void* save = diff ? saved : nullptr;
+      auto run = [&] { return run_section_layout(cand[a], pa.data(), &sections[k], n, save, stream); };
       if (flags & ADHA_MEASURE_AUTOTUNE) {
         // every chunk size x store mode; the fastest is kept for the executor
         double best = -1;
@@ -235,10 +254,18 @@ int adha_measure(const adha_schema* schema, int64_t n, const adha_layout* in_lay
           }
         set_overrides(0, 0);
         if (rc) break;
-        tuning_store(tuning_key(cand[a], &sections[k], n, false), bR, bW);
+        tuning_store(tuning_key(cand[a], &sections[k], n, diff), bR, bW);
         ns = best;
       } else {
         rc = time_ns(timer, stream, reps, run, &ns);
+      }
+      if (diff && !rc) {   // plus its adjoint kernel in the same layout
+        const adha_layout cl = set_layout(candidates, a);
+        double bw = 0;
+        rc = time_ns(timer, stream, reps, [&] {
+          return adha_section_backward(schema, n, &cl, pa.data(), pg.data(), &sections[k], saved, stream);
+        }, &bw);
+        ns += bw;
       }
       t->section_ns[(size_t)k * L + a] = ns;
     }
@@ -304,6 +331,13 @@ int adha_measure(const adha_schema* schema, int64_t n, const adha_layout* in_lay
       t->fused_ns[((size_t)k * W + (m - 1)) * L + a] = ns;
     }
   }
+  // differentiable: every remap of the forward pass has its inverse in the backward pass (the
+  // gradients go back through the reversed byte permutation), so an edge costs both directions
+  for (int a = 0; a <= L && diff && !rc; ++a)
+    for (int b = a + 1; b <= L; ++b) {
+      const double both = t->remap_ns[(size_t)a * (L + 1) + b] + t->remap_ns[(size_t)b * (L + 1) + a];
+      t->remap_ns[(size_t)a * (L + 1) + b] = t->remap_ns[(size_t)b * (L + 1) + a] = both;
+    }
   if (!rc) {
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) rc = cuda_fail(e, "cudaStreamSynchronize(measure)");

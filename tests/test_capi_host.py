@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
+import synth
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "adha.h")
@@ -150,3 +151,27 @@ def test_tuning_cache_text_round_trip(P):
         with pytest.raises(AdhaError):
             P.adha_tune_import(bad)
     P.adha_tune_clear()
+
+
+def test_differentiable_measure_validation(P):
+    from paper_1407_4859_gb300._lib import AdhaError, ADHA_EINVAL
+    # a mix section, and an fp64 field: neither has an adjoint kernel
+    wl = synth.config1(n=64)
+    S = P.Schema(wl.dtypes)
+    cand = P.adha_layout_set_create(6, [P.Layout.aos(6), P.Layout.soa(6)])
+    with pytest.raises(AdhaError) as e:
+        P.adha_measure(S, 64, P.Layout.aos(6), [256], wl.sections, cand, workspace=_FakeWs(), differentiable=True,
+                       stream=0)
+    assert e.value.code == ADHA_EINVAL
+    assert P.adha_measure_workspace_bytes(S, 64, P.Layout.aos(6), cand, 2) > \
+        P.adha_measure_workspace_bytes(S, 64, P.Layout.aos(6), cand)
+
+
+class _FakeWs:
+    """A stand-in workspace (never touched: validation fails first)."""
+
+    def data_ptr(self):
+        return 1 << 20
+
+    def numel(self):
+        return 1 << 30

@@ -131,3 +131,33 @@ def test_full_size_gradient_sampled(P):
         assert np.array_equal(np.ascontiguousarray(gsel[:, f]).view(np.uint32), want_g[f].view(np.uint32)), f
     for f in range(wl.F):
         assert np.array_equal(tsel[f].view(np.uint32), sf[f].view(np.uint32)), f
+
+
+def test_differentiable_measure_prices_forward_and_backward(P):
+    """ADHA_MEASURE_DIFFERENTIABLE: remap edges cost both directions (symmetric table), sections cost
+    their forward launch with saves plus the adjoint kernel (more than the forward alone), and the plan
+    PDL picks on that table trains bit for bit like the oracle."""
+    from paper_1407_4859_gb300.autograd import DifferentiableProgram
+    wl = synth.config5(n=(1 << 16) + 5, n_sections=12)
+    n, F = wl.n, wl.F
+    S, AOS = P.Schema(wl.dtypes), P.Layout.aos(F)
+    fields = oracle.initial_fields(wl)
+    x0 = _aos_tensor(wl, fields)
+    secs = P.Sections(wl.sections)
+    cand = P.adha_plan_sections(S, secs, P.PlanOpts([16, 32, 0], max_window=2, max_candidates=6))
+    fwd = P.adha_measure(S, n, AOS, [x0], secs, cand)
+    both = P.adha_measure(S, n, AOS, [x0], secs, cand, differentiable=True)
+    L = len(cand)
+    r = both.remap_ns
+    assert all(r[a][b] == r[b][a] for a in range(L + 1) for b in range(L + 1))
+    assert sum(map(sum, both.section_ns)) > sum(map(sum, fwd.section_ns))
+    _, seq = P.adha_pdl_solve(both)
+    plan = [cand.layouts[l] for l in seq]
+    x = x0.detach().requires_grad_(True)
+    lay, out = DifferentiableProgram(S, n, AOS, wl.sections, plan).forward([x])
+    _loss(lay, out, wl.loss_weights).backward()
+    torch.cuda.synchronize()
+    want_g = oracle.chain_grad(wl.sections, [a.copy() for a in fields], wl.loss_weights)
+    got = _grad_fields(wl, x.grad)
+    for f in range(F):
+        assert np.array_equal(got[f].view(np.uint32), want_g[f].view(np.uint32)), "gradient of field %d" % f
