@@ -203,7 +203,8 @@ __device__ __forceinline__ void st_vec(uint8_t* p, const V (&v)[M]) {
 
 // MIX when every accessed group holds one field (SoA-like): lane takes records lane*M + m, so
 // each field is one vector load from the chunk buffer and one vector store, to global memory or
-// (TO_STAGE, inside a fused run) back into the chunk buffer.
+// (TO_STAGE, inside a fused run) back into the chunk buffer.  The field loops are unrolled so that
+// several fields' loads are in flight before their (ordered) sums consume them.
 template <int M, bool TO_STAGE = false>
 __device__ __forceinline__ void mix_chunk_vec(const SecOp& so, const FieldRef* fr, uint8_t* stage, int64_t i0,
                                               int lane) {
@@ -214,24 +215,28 @@ __device__ __forceinline__ void mix_chunk_vec(const SecOp& so, const FieldRef* f
     s[m] = 0.0f;
     h[m] = 0u;
   }
+#pragma unroll 4
   for (int j = so.rd_off[ADHA_F32]; j < so.rd_off[ADHA_F32 + 1]; ++j) {
     float v[M];
     ld_vec<float, M>(stage + fr[so.rd[j]].s0 + lane * M * 4, v);
 #pragma unroll
     for (int m = 0; m < M; ++m) s[m] = __fadd_rn(s[m], v[m]);
   }
+#pragma unroll 4
   for (int j = so.rd_off[ADHA_F64]; j < so.rd_off[ADHA_F64 + 1]; ++j) {
     unsigned long long v[M];
     ld_vec<unsigned long long, M>(stage + fr[so.rd[j]].s0 + lane * M * 8, v);
 #pragma unroll
     for (int m = 0; m < M; ++m) h[m] ^= (uint32_t)v[m] ^ (uint32_t)(v[m] >> 32);
   }
+#pragma unroll 4
   for (int j = so.rd_off[ADHA_I32]; j < so.rd_off[ADHA_I32 + 1]; ++j) {
     uint32_t v[M];
     ld_vec<uint32_t, M>(stage + fr[so.rd[j]].s0 + lane * M * 4, v);
 #pragma unroll
     for (int m = 0; m < M; ++m) h[m] ^= v[m];
   }
+#pragma unroll 4
   for (int j = so.rd_off[ADHA_BF16]; j < so.rd_off[ADHA_BF16 + 1]; ++j) {
     uint16_t v[M];
     ld_vec<uint16_t, M>(stage + fr[so.rd[j]].s0 + lane * M * 2, v);
@@ -246,6 +251,7 @@ __device__ __forceinline__ void mix_chunk_vec(const SecOp& so, const FieldRef* f
     k[m] = (h[m] ^ __float_as_uint(t[m])) >> 3;
   }
   const int64_t r0 = i0 + (int64_t)lane * M;
+#pragma unroll 4
   for (int j = so.wr_off[ADHA_F32]; j < so.wr_off[ADHA_F32 + 1]; ++j) {
     const FieldRef& F = fr[so.wr[j]];
     float v[M];
@@ -258,7 +264,8 @@ __device__ __forceinline__ void mix_chunk_vec(const SecOp& so, const FieldRef* f
     double td[M];
 #pragma unroll
     for (int m = 0; m < M; ++m) td[m] = widen(t[m]);
-    for (int j = so.wr_off[ADHA_F64]; j < so.wr_off[ADHA_F64 + 1]; ++j) {
+  #pragma unroll 4
+  for (int j = so.wr_off[ADHA_F64]; j < so.wr_off[ADHA_F64 + 1]; ++j) {
       const FieldRef& F = fr[so.wr[j]];
       double v[M];
       ld_vec<double, M>(stage + F.s0 + lane * M * 8, v);
@@ -267,6 +274,7 @@ __device__ __forceinline__ void mix_chunk_vec(const SecOp& so, const FieldRef* f
       st_vec<double, M>(TO_STAGE ? stage + F.s0 + lane * M * 8 : F.g + r0 * 8, v);
     }
   }
+#pragma unroll 4
   for (int j = so.wr_off[ADHA_I32]; j < so.wr_off[ADHA_I32 + 1]; ++j) {
     const FieldRef& F = fr[so.wr[j]];
     uint32_t v[M];
@@ -275,6 +283,7 @@ __device__ __forceinline__ void mix_chunk_vec(const SecOp& so, const FieldRef* f
     for (int m = 0; m < M; ++m) v[m] ^= k[m];
     st_vec<uint32_t, M>(TO_STAGE ? stage + F.s0 + lane * M * 4 : F.g + r0 * 4, v);
   }
+#pragma unroll 4
   for (int j = so.wr_off[ADHA_BF16]; j < so.wr_off[ADHA_BF16 + 1]; ++j) {
     const FieldRef& F = fr[so.wr[j]];
     uint16_t v[M];
