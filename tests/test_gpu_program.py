@@ -165,3 +165,31 @@ def test_host_program_gather_needs_one_slice(P):
         P.adha_run_program_host(S, wl.n, AOS, host_in, secs, cand, host_out, workspace=ws, n_slices=2,
                                 fixed=[0] * len(wl.sections))
     assert e.value.code == ADHA_EINVAL and "permutation" in str(e.value)
+
+
+def test_program_captured_in_a_cuda_graph(P):
+    """adha_run_program allocates nothing and synchronizes nothing, so a whole program (remaps and
+    sections) can be captured once and replayed: every replay equals the oracle."""
+    wl = synth.config2(n=(1 << 16) + 7)
+    S, AOS, cand, secs = _setup(P, wl)
+    fields = oracle.initial_fields(wl)
+    want = oracle.run_program_fields(wl, [a.copy() for a in fields])
+    src = to_device(wl.n, wl.dtypes, AOS.groups, fields)
+    in_bufs = [b.clone() for b in src]
+    costs = P.adha_measure(S, wl.n, AOS, in_bufs, secs, cand)
+    ws = torch.empty(P.adha_program_workspace_bytes(S, wl.n, AOS, cand), dtype=torch.uint8, device="cuda")
+    plan = P.adha_run_program(S, wl.n, AOS, in_bufs, secs, cand, costs=costs, workspace=ws)   # fills launch caches
+    seq = list(plan.layout_of_section[:len(wl.sections)])
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.graph(g, stream=s, capture_error_mode="thread_local"):
+        plan = P.adha_run_program(S, wl.n, AOS, in_bufs, secs, cand, costs=costs, workspace=ws, fixed=seq, stream=s)
+    for _ in range(2):
+        for b, x in zip(in_bufs, src):
+            b.copy_(x)
+        g.replay()
+        torch.cuda.synchronize()
+        assert P.adha_device_status() == 0
+        lay, bufs = P.final_buffers(plan, S, wl.n, cand, AOS)
+        assert_fields_equal(from_device(wl.n, wl.dtypes, lay.groups, bufs), want, "graph replay")
