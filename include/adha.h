@@ -412,17 +412,20 @@ typedef struct {
 /* A prepared batched remap (host object). */
 typedef struct adha_batched adha_batched;
 
-#define ADHA_BATCHED_AUTOTUNE 1   /* pick each array's chunk size by timing it (synchronizes `stream`) */
+#define ADHA_BATCHED_AUTOTUNE 1   /* pick each array's launch shape by timing it (synchronizes `stream`) */
 
 /*
  * Prepares the remap of n_arrays record arrays in one persistent launch (the
  * batching form of the paper's remap, Section 2): validates every array (rules
  * of adha_remap), plans each one (chunk size, element schedule) and lays out
- * the descriptors the kernel reads.  With ADHA_BATCHED_AUTOTUNE each array's
+ * the descriptors the kernel reads.  The shared memory of a CTA is set here: the
+ * number of CTAs per SM (1 to 4) whose warp-buffer budget gives the most working
+ * warps weighted by the arrays' bytes.  With ADHA_BATCHED_AUTOTUNE each array's
  * chunk size (32..256 records) and store mode for one-field destination groups
- * (see adha_tune_remap_direct) are the fastest pair, timed with the single-array
- * kernel on the array's own buffers (their contents are overwritten with the
- * remap's result).  *out is freed with adha_batched_destroy.
+ * (see adha_tune_remap_direct) are the fastest pair, then its piece tables (see
+ * adha_tune_remap_pieces) the fastest of the four choices, timed with the
+ * single-array kernel on the array's own buffers (their contents are
+ * overwritten with the remap's result).  *out is freed with adha_batched_destroy.
  */
 int adha_batched_create(int32_t n_arrays, const adha_remap_desc* descs, int32_t flags, adha_stream stream,
                         adha_batched** out);

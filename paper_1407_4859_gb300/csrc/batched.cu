@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(kThreads) batched_kernel(const __grid_constant
               *reinterpret_cast<const uint4*>(outb + q * 16);
         }
       } else {
-        write_back<DIRECT>(tout, h.n_dst, h.R, h.out_bytes, outb, c, lane);
+        write_back<DIRECT>(tout, h.R, h.out_bytes, outb, c, lane);
       }
       __syncwarp();
     }

@@ -225,6 +225,7 @@ struct RemapPlan {
 // Chunk / pipeline override for the autotuner (0 = default rule).
 static thread_local int t_tile_override = 0;
 static thread_local int t_writeback_mode = 0;   // 0 automatic, 1 never, 2 every wide written group
+static thread_local int t_fused_buffers = 0;    // fused runs: 0 tuned or default, else chunk buffers per warp
 static thread_local int t_remap_direct = 0;     // 1: remaps store one-field destination groups directly
 static thread_local int t_remap_pieces = 0;     // 0: tuned or automatic, 1 + piece-table bits otherwise
 
@@ -273,6 +274,11 @@ void tuning_store(const std::string& key, int R, int wb) {
 void set_overrides(int R, int wb) {
   t_tile_override = R;
   t_writeback_mode = wb;
+}
+
+void set_fused_overrides(int R, int buffers) {
+  t_tile_override = R;
+  t_fused_buffers = buffers;
 }
 
 // Records per warp chunk: a multiple of 32 with about `target` bytes of the widest side.
@@ -647,8 +653,7 @@ static int plan_section(const Layout& L, void* const* ptrs, const adha_section* 
   for (int g : groups) rec += L.stride[g];
   if (s->op == ADHA_OP_GATHER) rec += 4;
   int R = tuned_R ? std::max(32, std::min(tuned_R, 128)) : (rec > 0 ? pick_chunk(rec, 4096, 128) : 128);
-  if (R != 32 && R != 64 && R != 128) R = R < 64 ? 32 : 64;
-  if (R == 96) R = 64;
+  if (R != 32 && R != 64 && R != 128) R = R < 64 ? 32 : 64;   // 96 -> 64: the kernels exist for 32, 64, 128
   for (;;) {
     a.n = n;
     a.R = R;
@@ -855,7 +860,7 @@ struct FusedPlan {
 static int plan_fused(const Layout& L, void* const* ptrs, const adha_section* s, int m, int64_t n, FusedPlan* plan) {
   FusedArgs& a = plan->args;
   std::memset(&a, 0, sizeof a);
-  int tuned_R = t_tile_override, tuned_buffers = t_writeback_mode;   // the store mode knob picks the buffers here
+  int tuned_R = t_tile_override, tuned_buffers = t_fused_buffers;
   if (!tuned_R && !tuned_buffers) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(fused_key(L, s, m, n));

@@ -186,6 +186,7 @@ int profiled_launch(int kind, int op, double bytes, void* stream, int (*fn)(cons
 std::string tuning_key(const Layout& L, const adha_section* s, int64_t n, bool save);
 void tuning_store(const std::string& key, int R, int wb);
 void set_overrides(int R, int wb);
+void set_fused_overrides(int R, int buffers);
 std::string remap_tuning_key(const Layout& S, const Layout& D, int64_t n);
 void set_remap_pieces(int mode);
 int pdl_solve(const adha_cost_table* c, int return_to_input, int32_t* seq, double* total);

@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kThreads) remap_kernel(const __grid_constant__
             *reinterpret_cast<const uint4*>(outb + q * 16);
       }
     } else {
-      write_back<DIRECT>(tout, a.n_dst, a.R, a.out_bytes, outb, c, lane);
+      write_back<DIRECT>(tout, a.R, a.out_bytes, outb, c, lane);
     }
     __syncwarp();
   }

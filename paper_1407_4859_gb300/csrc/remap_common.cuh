@@ -117,7 +117,7 @@ __device__ __forceinline__ void tail_moves(int64_t t0, int64_t n, int n_moves, c
 // 16-byte stores; the staged slices follow one another in the buffer in destination order
 // (without direct classes every destination group is staged).
 template <bool DIRECT>
-__device__ __forceinline__ void write_back(const GroupRef* dst, int n_dst, int R, int out_bytes, const uint8_t* out,
+__device__ __forceinline__ void write_back(const GroupRef* dst, int R, int out_bytes, const uint8_t* out,
                                            int64_t ch, int lane) {
   int g = 0;
   for (int p = lane * 16; p < out_bytes; p += 512) {
@@ -125,7 +125,6 @@ __device__ __forceinline__ void write_back(const GroupRef* dst, int n_dst, int R
     *reinterpret_cast<uint4*>(const_cast<uint8_t*>(dst[g].ptr) + ch * R * dst[g].stride + (p - dst[g].start)) =
         *reinterpret_cast<const uint4*>(out + p);
   }
-  (void)n_dst;
 }
 
 // Where a 16-byte piece of a chunk buffer lives in global memory: base + chunk * step.

@@ -313,7 +313,7 @@ int adha_measure(const adha_schema* schema, int64_t n, const adha_layout* in_lay
         double best = -1;
         int bR = 0, bB = 0;
         for (int q = 0; q < 4 && !rc; ++q) {
-          set_overrides(shapes[q][0], shapes[q][1]);
+          set_fused_overrides(shapes[q][0], shapes[q][1]);
           rc = time_ns(timer, stream, reps, run, &ns);
           if (!rc && (best < 0 || ns < best)) {
             best = ns;
@@ -321,7 +321,7 @@ int adha_measure(const adha_schema* schema, int64_t n, const adha_layout* in_lay
             bB = shapes[q][1];
           }
         }
-        set_overrides(0, 0);
+        set_fused_overrides(0, 0);
         if (rc) break;
         tuning_store(fused_tuning_key(cand[a], &sections[k], m, n), bR, bB);
         ns = best;
