@@ -1,0 +1,52 @@
+"""bench.py's host logic, CPU only: the byte counts behind its value and the reference arm's JSON
+line (the oracle timed on the host cores), whose keys the driver reads."""
+import json
+import os
+import subprocess
+import sys
+
+import bench
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SZ = {0: 4, 1: 8, 2: 4, 3: 2}
+
+
+def test_remap_bytes_count_only_groups_that_change():
+    wl = synth.config2(n=1000)
+    F, S = wl.F, len(wl.sections)
+    aos = [list(range(F))]
+    soa = [[f] for f in range(F)]
+    data = sum(SZ[d] for d in wl.dtypes)
+    assert bench.remap_bytes(wl, [aos] * S, aos) == 0
+    assert bench.remap_bytes(wl, [soa] * S, aos) == 2 * wl.n * data
+    # AoS -> SoA -> AoS -> SoA: three full remaps
+    assert bench.remap_bytes(wl, [soa, aos, soa] + [soa] * (S - 3), aos) == 3 * 2 * wl.n * data
+    # keeping field 0 alone and the rest together moves everything once, then only the rest
+    part = [[0], list(range(1, F))]
+    moved_rest = sum(SZ[wl.dtypes[f]] for f in range(1, F))
+    assert bench.remap_bytes(wl, [part, [[0]] + [[f] for f in range(1, F)]] + [soa] * (S - 2), aos) == \
+        2 * wl.n * data + 2 * wl.n * moved_rest
+
+
+def test_program_bytes_are_layout_independent_section_bytes():
+    wl = synth.config1(n=100)
+    # S1 reads f0, f1, f2 and writes f2; S2 reads f3, i0 and writes i1; S3 reads all six and writes f0:
+    # every touched field once (read or written) plus every written field once more
+    by_hand = 100 * ((12 + 4) + (12 + 4) + (24 + 4))
+    assert bench.program_bytes(wl) == by_hand
+
+
+def test_reference_arm_prints_the_contract_line():
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "3"],
+                         cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "GB/s" and line["value"] > 0
+    assert line["config"]["workload"] == synth.config2().name
+    cpu = line["cpu_baseline"]
+    assert cpu["kind"] == "oracle" and cpu["cores"] >= 1 and cpu["value"] == line["value"] and cpu["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    for key in ("metric", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling"):
+        assert key in line
