@@ -754,6 +754,19 @@ def differentiable_bench(args, rank, world, local, dist):
     work = sum(r["bytes"] for r in recs if r["kind"] in ("section", "section_backward")) / args.steps
     value = weak_scaling_value(world, work, args.steps, ms)
     roof, kernels = _roofline(recs, args.workload)
+    # end to end: the step's input in from pinned host memory, forward + backward, its gradient out
+    grad_host = torch.empty_like(pinned).pin_memory()
+
+    def e2e_step():
+        x0.copy_(pinned, non_blocking=True)
+        grad_host.copy_(run(plan), non_blocking=True)
+    for _ in range(2):
+        e2e_step()
+    e2e_steps = max(3, args.steps // 3)
+    e2e_ms = _timed(torch, stream, e2e_steps, e2e_step) / e2e_steps
+    e2e = {"value": round(world * work / (e2e_ms * 1e6), 1), "unit": "GB/s", "h2d_bytes_per_step": pinned.numel() * 4,
+           "d2h_bytes_per_step": grad_host.numel() * 4, "ms_per_step": round(e2e_ms, 3),
+           "api": "DifferentiableProgram forward + torch.autograd.backward (pinned host input and gradient)"}
     k2 = max(3, args.steps // 2)
     t_aos = _timed(torch, stream, k2, lambda: run([AOS] * len(wl.sections))) / k2
     t_soa = _timed(torch, stream, k2, lambda: run([P.Layout.soa(F)] * len(wl.sections))) / k2
@@ -776,7 +789,7 @@ def differentiable_bench(args, rank, world, local, dist):
                        "forward_bytes_per_step": fwd, "backward_bytes_per_step": bwd,
                        "value_definition": "section + adjoint algorithmic bytes per forward+backward step / step time",
                        "l2": "inputs larger than L2 (6.4 GB)"},
-            "gpu_launches": len(recs), "roofline": roof, "kernels": kernels, "clocks": clk,
+            "gpu_launches": len(recs), "roofline": roof, "kernels": kernels, "clocks": clk, "e2e": e2e,
             "step_ms": {"adha": round(ms / args.steps, 3), "all_aos": round(t_aos, 3), "all_soa": round(t_soa, 3)},
             "cpu_baseline": cpu}), flush=True)
     if dist:

@@ -126,7 +126,10 @@ class SegmentFn(torch.autograd.Function):
         g = _copy(schema, n, layout, g)
         for cs, save in reversed(ctx.saves):
             adha_section_backward(schema, n, layout, list(ctx.state), g, cs, save)
+        # the state tensors' grad_fn refers to ctx: drop them here, or the step's memory waits for
+        # Python's cycle collector
         ctx.saves = None
+        ctx.state = None
         return (None,) + tuple(g)
 
 
