@@ -11,9 +11,12 @@ before the timed region, like an autotuner cache.
 Prints one JSON line.  `value` is algorithmic GB/s of the program: the data bytes its sections
 must move (accessed fields only; no padding, no untouched fields) divided by the step's device
 time, so a plan pays for the remaps it adds in time.  Extra keys: program times under the ADHA layouts vs
-all-AoS, all-SoA and the best of a bounded exhaustive set; the roofline of the dominant kernel;
-the oracle timed on the host cores; the end-to-end number through the C ABI with host buffers.
+all-AoS, all-SoA and the best of a bounded exhaustive set, and under PDL with fused combine nodes;
+the roofline of the dominant kernel; the oracle timed on the host cores; the end-to-end number
+through the C ABI with host buffers.
 
+--workload particles | batched | differentiable runs the other programs (the particle program with
+a gather, 256 arrays in one batched remap, the 64-section chain forward + backward).
 --impl reference times the CPU oracle (the only reference this method has) on a bounded sample
 of the same workload and prints the same metric.
 """
