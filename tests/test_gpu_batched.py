@@ -100,3 +100,33 @@ def test_batched_empty_and_aliased_arrays(P):
     b.upload()
     b.launch()
     _check(arrays)
+
+
+def test_full_size_batched_workload_sampled(P):
+    """All 256 arrays at their full sizes (11.7 GB of AoS input) in one graph-launched batched remap;
+    every array checked against the oracle on its first, middle and last 4096 records (the remap is
+    per record, so any record range can be checked alone)."""
+    specs = synth.config4_arrays()
+    arrays, hosts = [], []
+    for k, a in enumerate(specs):
+        S = P.Schema(a["dtypes"])
+        src, dst = P.Layout(a["src"]), P.Layout(a["dst"])
+        (sst,), _ = P.adha_layout_strides(S, src)
+        dst_st, _ = P.adha_layout_strides(S, dst)
+        raw = synth.fill("RAW64", synth.key(3, 200000 + k), n=(a["n"] * sst + 7) // 8).view(np.uint8)[: a["n"] * sst]
+        hosts.append((raw, sst, dst_st))
+        arrays.append(dict(schema=S, n=a["n"], src=src, dst=dst, src_bufs=[torch.from_numpy(raw).cuda()],
+                           dst_bufs=[torch.empty(max(1, a["n"] * s), dtype=torch.uint8, device="cuda") for s in dst_st]))
+    b = P.Batched(arrays)
+    b.upload()
+    b.capture()
+    b.graph_launch()
+    torch.cuda.synchronize()
+    assert P.adha_device_status() == 0
+    for k, (a, arr, (raw, sst, dst_st)) in enumerate(zip(specs, arrays, hosts)):
+        n, m = a["n"], min(4096, a["n"])
+        for i0 in sorted({0, (n - m) // 2, n - m}):
+            want = oracle.remap(m, a["dtypes"], a["src"], [raw[i0 * sst:(i0 + m) * sst]], a["dst"])
+            for g, (buf, st) in enumerate(zip(arr["dst_bufs"], dst_st)):
+                got = buf[i0 * st:(i0 + m) * st].cpu().numpy()
+                assert np.array_equal(got, want[g]), "array %d group %d records %d.." % (k, g, i0)
