@@ -1,7 +1,7 @@
 """Differentiation through layout changes and chains of fp32 sections.
 
 State in a layout is a list of float32 tensors, one (n, k) tensor per group of k fields (all fields
-fp32, so a group's struct is k contiguous floats).  Two autograd Functions:
+fp32, so a group's struct is k contiguous floats).  Three autograd Functions:
 
 * RemapFn: moves the groups that change from one layout to another with the remap kernel; its
   backward is the inverse remap of the incoming gradients (the same byte permutation, reversed).
