@@ -1,7 +1,7 @@
 """Helpers of the GPU parity tests: move field arrays in and out of a device layout.
 
 Encoding and decoding use the oracle's remap on the host (pinned by the CPU tests), so the
-bytes the GPU starts from and the values it is judged by never come from the CUDA path.
+bytes the GPU starts from and the values it is checked against never come from the CUDA path.
 """
 import numpy as np
 import torch
