@@ -51,7 +51,7 @@ enum {
   ADHA_ENOMEM = -2,   /* workspace too small, or host allocation failed          */
   ADHA_ECUDA = -3,    /* a CUDA runtime call failed: the message has its text    */
   ADHA_ETIMEOUT = -4, /* a kernel gave up waiting for its copies (see adha_device_status) */
-  ADHA_ENOTIMPL = -5  /* not supported on this build or device                   */
+  ADHA_ENOTIMPL = -5  /* not supported by the library or the device              */
 };
 
 #define ADHA_MAX_FIELDS 64
