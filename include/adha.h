@@ -413,22 +413,31 @@ typedef struct {
 typedef struct adha_batched adha_batched;
 
 #define ADHA_BATCHED_AUTOTUNE 1   /* pick each array's launch shape by timing it (synchronizes `stream`) */
+#define ADHA_BATCHED_CTAS(k) ((int32_t)(k) << 4)   /* force k CTAs per SM (1..4) instead of the model's choice */
 
 /*
  * Prepares the remap of n_arrays record arrays in one persistent launch (the
  * batching form of the paper's remap, Section 2): validates every array (rules
  * of adha_remap), plans each one (chunk size, element schedule) and lays out
- * the descriptors the kernel reads.  The shared memory of a CTA is set here: the
- * number of CTAs per SM (1 to 4) whose warp-buffer budget gives the most working
- * warps weighted by the arrays' bytes.  With ADHA_BATCHED_AUTOTUNE each array's
- * chunk size (32..256 records) and store mode for one-field destination groups
- * (see adha_tune_remap_direct) are the fastest pair, then its piece tables (see
- * adha_tune_remap_pieces) the fastest of the four choices, timed with the
- * single-array kernel on the array's own buffers (their contents are
- * overwritten with the remap's result).  *out is freed with adha_batched_destroy.
+ * the descriptors the kernel reads.  The kernel's warps work alone: each takes
+ * work units of about 1024 records of one array by an atomic ticket (largest
+ * array first) and keeps its current array's tables in its own region of
+ * shared memory.  The region is set here: the number of CTAs per SM (1 to 4)
+ * whose regions hold every array's chunk buffers (chunks shortened to fit, down
+ * to 8 records) with the most bytes x CTAs, discounting arrays whose chunks had
+ * to shrink (ADHA_BATCHED_CTAS(k) in flags forces k).  With
+ * ADHA_BATCHED_AUTOTUNE each array's chunk size (32..256 records) and store
+ * mode for one-field destination groups (see adha_tune_remap_direct) are the
+ * fastest pair, timed with the single-array kernel on the array's own buffers
+ * (their contents are overwritten with the remap's result).  *out is freed with
+ * adha_batched_destroy.  Needs a current CUDA device (occupancy queries).
  */
 int adha_batched_create(int32_t n_arrays, const adha_remap_desc* descs, int32_t flags, adha_stream stream,
                         adha_batched** out);
+
+/* What adha_batched_create chose: CTAs per SM, shared bytes per warp, work units
+ * per launch (any output may be NULL).  Host only. */
+int adha_batched_info(const adha_batched* b, int32_t* ctas_per_sm, int32_t* warp_region_bytes, int64_t* units);
 
 /* Device workspace bytes the batched remap needs (descriptors + its work ticket). */
 size_t adha_batched_workspace_bytes(const adha_batched* b);
@@ -457,6 +466,29 @@ double adha_batched_bytes(const adha_batched* b);
 /* Frees b and its graph (NULL is ignored). */
 void adha_batched_destroy(adha_batched* b);
 
+/*
+ * Device workspace bytes adha_remap_batched needs for this batch (descriptors,
+ * element schedules and the work ticket), planned by the default rules of
+ * adha_batched_create; *bytes receives it.  Validates the batch like
+ * adha_remap_batched.  Needs the current CUDA device; host only.
+ */
+int adha_workspace_bytes(int32_t n_arrays, const adha_remap_desc* descs, size_t* bytes);
+
+/*
+ * The batched remap in one call (paper Section 2, the remap edge, applied to
+ * many record arrays at once): validates and plans the batch as
+ * adha_batched_create does without autotuning, copies the descriptors into
+ * `workspace` (device, 256-byte aligned, ws_bytes >= adha_workspace_bytes of
+ * the same batch; ADHA_ENOMEM otherwise), zeroes the work ticket and enqueues
+ * the persistent kernel on `stream`.  Rules of adha_remap per array.  The
+ * descriptors are copied from a host buffer the call frees before returning,
+ * so a stream that is being captured is rejected with ADHA_EINVAL (capture
+ * adha_batched_launch, whose workspace is uploaded beforehand, instead).
+ * Asynchronous; the workspace must not be reused until the remap is done.
+ */
+int adha_remap_batched(int32_t n_arrays, const adha_remap_desc* descs, void* workspace, size_t ws_bytes,
+                       adha_stream stream);
+
 /* Bytes of the device array that adha_remap_batched_noalloc keeps its descriptors in. */
 #define ADHA_NOALLOC_SCRATCH_BYTES (1u << 20)
 
@@ -469,12 +501,17 @@ void adha_batched_destroy(adha_batched* b);
  * library (ADHA_NOALLOC_SCRATCH_BYTES, held on every GPU that loads the library
  * until the process exits) and calls no device-allocating routine.  The caller
  * still passes every input and output buffer in `descs` (rules of adha_remap).
- * A batch whose descriptors do not fit fails with ADHA_EINVAL.  Each call
- * rewrites the descriptors and zeroes the ticket, then launches the kernel on
- * `stream` (async); all calls share the one array, so calls that overlap on the
- * GPU race and must be ordered by the caller.  The first call on a device looks
- * up the array's device address; make that first call before any stream
- * capture.  The paper has no counterpart of this entry point.
+ * A batch whose descriptors do not fit fails with ADHA_EINVAL, as does a call
+ * on a stream that is being captured (the descriptors are copied from a host
+ * buffer freed on return).  Each call rewrites the descriptors and zeroes the
+ * ticket, then launches the kernel on `stream` (async); calls from several host
+ * threads reach the GPU one whole call at a time, but all calls share the one
+ * array, so calls that overlap on the GPU (different streams, unordered) race
+ * and must be ordered by the caller.  The first call on a device looks up the
+ * array's device address and keeps it for the process; make that first call
+ * before any stream capture, and do not call again after cudaDeviceReset (the
+ * kept address does not survive it).  The paper has no counterpart of this
+ * entry point.
  */
 int adha_remap_batched_noalloc(int32_t n_arrays, const adha_remap_desc* descs, adha_stream stream);
 

@@ -465,22 +465,55 @@ def adha_profile_stop(max_records=4096):
 ADHA_BATCHED_AUTOTUNE = 1
 
 
+def remap_descs(arrays):
+    """(adha_remap_desc array, objects to keep alive) for a list of array dicts with keys schema,
+    n, src, src_bufs, dst, dst_bufs."""
+    keep = []
+    descs = (_lib.adha_remap_desc * max(1, len(arrays)))()
+    for k, a in enumerate(arrays):
+        sp, dp = _ptrs(a["src_bufs"]), _ptrs(a["dst_bufs"])
+        keep += [a["schema"], a["src"], a["dst"], sp, dp]
+        descs[k] = _lib.adha_remap_desc(ctypes.pointer(a["schema"].c), int(a["n"]), ctypes.pointer(a["src"].c),
+                                        sp, ctypes.pointer(a["dst"].c), dp)
+    return descs, keep
+
+
+def adha_workspace_bytes(arrays):
+    """Device workspace bytes adha_remap_batched needs for these arrays."""
+    descs, _keep = remap_descs(arrays)
+    out = ctypes.c_size_t(0)
+    check(_lib.load().adha_workspace_bytes(len(arrays), descs, ctypes.byref(out)), "adha_workspace_bytes")
+    return out.value
+
+
+def adha_remap_batched(arrays, workspace, stream=None):
+    """All arrays remapped in one persistent launch, descriptors placed in `workspace` (a device
+    uint8 tensor of at least adha_workspace_bytes(arrays) bytes)."""
+    descs, _keep = remap_descs(arrays)
+    check(_lib.load().adha_remap_batched(len(arrays), descs, workspace.data_ptr(), workspace.numel(),
+                                         _stream_ptr(stream)), "adha_remap_batched")
+
+
 class Batched:
     """A prepared batched remap (adha_batched_create); arrays: list of dicts with keys
-    schema (Schema), n, src (Layout), src_bufs, dst (Layout), dst_bufs."""
+    schema (Schema), n, src (Layout), src_bufs, dst (Layout), dst_bufs.  ctas: force that many
+    CTAs per SM (1..4; 0 = the library's choice)."""
 
-    def __init__(self, arrays, autotune=False, stream=None):
-        self._keep = []
-        descs = (_lib.adha_remap_desc * len(arrays))()
-        for k, a in enumerate(arrays):
-            sp, dp = _ptrs(a["src_bufs"]), _ptrs(a["dst_bufs"])
-            self._keep += [a["schema"], a["src"], a["dst"], sp, dp]
-            descs[k] = _lib.adha_remap_desc(ctypes.pointer(a["schema"].c), int(a["n"]), ctypes.pointer(a["src"].c),
-                                            sp, ctypes.pointer(a["dst"].c), dp)
+    def __init__(self, arrays, autotune=False, stream=None, ctas=0):
+        descs, self._keep = remap_descs(arrays)
         self.ptr = ctypes.c_void_p()
-        check(_lib.load().adha_batched_create(len(arrays), descs, ADHA_BATCHED_AUTOTUNE if autotune else 0,
-                                              _stream_ptr(stream), ctypes.byref(self.ptr)), "adha_batched_create")
+        flags = (ADHA_BATCHED_AUTOTUNE if autotune else 0) | (int(ctas) << 4)
+        check(_lib.load().adha_batched_create(len(arrays), descs, flags, _stream_ptr(stream), ctypes.byref(self.ptr)),
+              "adha_batched_create")
         self.workspace = None
+
+    @property
+    def info(self):
+        """(CTAs per SM, shared bytes per warp, work units per launch) the plan chose."""
+        k, r, u = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int64(0)
+        check(_lib.load().adha_batched_info(self.ptr, ctypes.byref(k), ctypes.byref(r), ctypes.byref(u)),
+              "adha_batched_info")
+        return k.value, r.value, u.value
 
     @property
     def workspace_bytes(self):

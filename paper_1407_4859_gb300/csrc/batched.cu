@@ -1,22 +1,25 @@
-// batched.cu -- many record arrays remapped in one persistent launch.
+// batched.cu -- many record arrays remapped in one persistent launch (the batching form of the
+// paper's remap edge, Section 2).
 //
-// Each array (its own schema, record count and source/destination layouts) is cut into chunks
-// of R_a records, and its chunks into work blocks (about 2048 records per working warp).  A CTA holds a
-// budget of shared memory for its warps' buffers, set when the batch is created from the number of
-// CTAs per SM (1 to 4) that gives the most working warps weighted by the arrays' bytes; an array
-// whose records are too wide for eight warps' buffers in that budget is worked on by fewer warps
-// of the CTA.  A CTA takes the next block with one atomic ticket (a 64-bit counter in the caller's
-// workspace, zeroed by a memset node before every launch), builds the block's array's element
-// schedule (and, where the array uses them, its piece tables) in shared memory when the array
-// changes, and its warps run the same double-buffered cp.async pipeline as remap.cu on the
-// block's chunks.  Blocks of small arrays and of large arrays are interleaved by the ticket
-// order, so uneven sizes balance across SMs without any waiting between CTAs.  The descriptors
-// live in the workspace; the launch (memset + kernel) can be captured in a CUDA graph.
+// Every array (its own schema, record count and source/destination layouts) is cut into chunks
+// of R_a records, and its chunks into work units of about 1024 records.  Each warp works alone:
+// it takes the next unit with one 64-bit atomic ticket (in the descriptor region, zeroed before
+// every launch), finds the unit's array by a 32-way search over the arrays' first units (one
+// ballot per level), and, when the array differs from its last one, copies that array's header,
+// group table and element schedule (built on the host when the batch is prepared) into its own
+// region of shared memory.  It then runs the double-buffered cp.async pipeline of remap.cu over
+// the unit's consecutive chunks: stage the source slices with 16-byte copies one chunk ahead,
+// assemble the destination records one move per lane per step, write them back with 16-byte
+// stores.  No warp ever waits for another: there is no block-wide barrier anywhere, so uneven
+// arrays and ragged tails cost only their own work.  Units are dealt largest array first, so
+// the small arrays' single units fill the last gaps.  The launch (memset + kernel) can be
+// captured in a CUDA graph.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstring>
 #include <mutex>
+#include <numeric>
 #include <vector>
 
 #include "internal.h"
@@ -25,137 +28,117 @@
 
 namespace adha {
 
-constexpr int kBlockRecordsPerWarp = 2048;   // a work block gives each working warp about this many records
+constexpr int kUnitRecords = 1024;   // records of one work unit (whole chunks, at least one)
+constexpr int kHeaderBytes = 128;    // a warp region starts with the header of its current array
+constexpr int kMaxBatchedCtas = 8;   // CTAs per SM tried (8 x 8 warps = 64 warps, the SM's limit)
 
 struct BatchHeader {
-  int64_t n, n_full, n_chunks, block0;
+  int64_t n, n_full, n_chunks;   // records, whole chunks, chunks counting the ragged one
+  int64_t unit0;                 // first work unit of the array
+  int64_t sched0;                // byte offset of the array's schedule in the schedule region
   int32_t R, n_src, n_dst, in_bytes, out_bytes, n_moves;
-  int32_t cls_count[6], cls_order[6];
+  int32_t cls_count[6];
   int32_t group0, move0;
-  int32_t warps;        // warps of a CTA that work on this array (the others idle for its blocks)
-  int32_t chunks_per_warp;   // chunks of one working warp in one work block
-  int32_t warp_bytes;   // shared bytes of one working warp: two input buffers and an output buffer
-  int32_t pieces;       // bit 0: stage through the piece table, bit 1: write back through it
+  int32_t chunks_per_unit;
+  int32_t sched_off, buf_off;    // offsets in a warp region: the schedule, the first chunk buffer
+  int32_t sched_bytes;
 };
-
-// Warp bytes up to which the autotuner considers chunks longer than 32 records.
-constexpr int kTuneWarpBytes = 8 * 1024;
+static_assert(sizeof(BatchHeader) <= kHeaderBytes && sizeof(BatchHeader) % 16 == 0, "header is copied in words");
+static_assert(sizeof(GroupRef) == 16, "group table is copied in 16-byte words");
 
 struct BatchParams {
   unsigned long long* ticket;
-  const BatchHeader* headers;
+  const BatchHeader* headers;    // in ticket order (largest array first); arrays with nothing to move are left out
   const GroupRef* groups;
   const Move* moves;
-  const int64_t* prefix;     // first block of each array, n_arrays + 1 entries
+  const uint8_t* sched;
+  const int64_t* prefix;         // first unit of each listed array; prefix[n_arrays] = total_units
   int32_t n_arrays;
-  int64_t total_blocks;
-  int32_t max_entries;
-  int32_t max_pieces;        // piece-table entries of the array that needs the most
+  int32_t region;                // shared bytes of one warp
+  int64_t total_units;
 };
+
+// Last array a with prefix[a] <= u: a 32-way search, one ballot per level (prefix[0] = 0 <= u,
+// so lane 0 always qualifies and the answer stays inside [lo, lo + span)).
+__device__ __forceinline__ int find_array(const int64_t* prefix, int n_arrays, int64_t u, int lane) {
+  int lo = 0, span = n_arrays;
+  while (span > 1) {
+    const int step = (span + 31) >> 5, end = lo + span;
+    const int idx = lo + lane * step;
+    const bool ok = idx < end && __ldg(prefix + idx) <= u;
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, ok);
+    lo += (31 - __clz(m)) * step;
+    span = min(step, end - lo);
+  }
+  return lo;
+}
 
 template <bool DIRECT>
 __global__ void __launch_bounds__(kThreads) batched_kernel(const __grid_constant__ BatchParams p) {
   extern __shared__ __align__(16) uint8_t smem[];
-  __shared__ BatchHeader h;
-  __shared__ unsigned long long s_blk;
-  __shared__ int s_arr;
-  GroupRef* tin = reinterpret_cast<GroupRef*>(smem);
-  GroupRef* tout = tin + kMaxGroups;
-  Move* moves = reinterpret_cast<Move*>(tout + kMaxGroups);
-  uint32_t* sched = reinterpret_cast<uint32_t*>(moves + kMaxMoves);
-  Piece* pin = reinterpret_cast<Piece*>(sched + p.max_entries);   // max_entries is a multiple of 4
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  uint8_t* wbase = reinterpret_cast<uint8_t*>(pin + p.max_pieces);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint8_t* region = smem + (size_t)warp * p.region;
+  const BatchHeader& h = *reinterpret_cast<const BatchHeader*>(region);
+  GroupRef* tin = reinterpret_cast<GroupRef*>(region + kHeaderBytes);
   int cur = -1;
-  int in_pieces = 0, out_pieces = 0;
-  Piece* pout = pin;
-
   for (;;) {
-    if (tid == 0) {
-      s_blk = atomicAdd(p.ticket, 1ull);
-      int lo = 0, hi = p.n_arrays - 1;   // last array whose first block is <= s_blk
-      const int64_t b = (int64_t)s_blk;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) / 2;
-        if (p.prefix[mid] <= b) lo = mid;
-        else hi = mid - 1;
-      }
-      s_arr = lo;
-    }
-    __syncthreads();
-    const int64_t blk = (int64_t)s_blk;
-    if (blk >= p.total_blocks) break;
-    const int arr = s_arr;
-    if (arr != cur) {
-      if (tid == 0) h = p.headers[arr];
-      __syncthreads();
-      for (int k = tid; k < h.n_src; k += kThreads) tin[k] = p.groups[h.group0 + k];
-      for (int k = tid; k < h.n_dst; k += kThreads) tout[k] = p.groups[h.group0 + h.n_src + k];
-      for (int k = tid; k < h.n_moves; k += kThreads) moves[k] = p.moves[h.move0 + k];
-      __syncthreads();
-      for (int t = tid; t < h.R * h.n_moves; t += kThreads)
-        sched[t] = schedule_entry(t, h.R, h.cls_count, h.cls_order, moves, tin, tout);
-      in_pieces = (h.pieces & 1) ? h.in_bytes / 16 : 0;
-      out_pieces = (h.pieces & 2) ? h.out_bytes / 16 : 0;
-      pout = pin + in_pieces;
-      for (int q = tid; q < in_pieces; q += kThreads) pin[q] = piece_of(q, tin, h.R);
-      for (int q = tid; q < out_pieces; q += kThreads) pout[q] = piece_of(q, tout, h.R);
-      __syncthreads();
+    unsigned long long t = 0;
+    if (lane == 0) t = atomicAdd(p.ticket, 1ull);
+    const int64_t u = (int64_t)__shfl_sync(0xFFFFFFFFu, t, 0);
+    if (u >= p.total_units) break;
+    const int arr = find_array(p.prefix, p.n_arrays, u, lane);
+    if (arr != cur) {   // the warp's tables for this array: header, groups, schedule
+      __syncwarp();
+      const uint32_t* hs = reinterpret_cast<const uint32_t*>(p.headers + arr);
+      if (lane < (int)(sizeof(BatchHeader) / 4)) reinterpret_cast<uint32_t*>(region)[lane] = __ldg(hs + lane);
+      __syncwarp();
+      const uint4* gs = reinterpret_cast<const uint4*>(p.groups + h.group0);
+      for (int k = lane; k < h.n_src + h.n_dst; k += 32) reinterpret_cast<uint4*>(tin)[k] = __ldg(gs + k);
+      const uint4* ss = reinterpret_cast<const uint4*>(p.sched + h.sched0);
+      uint4* sd = reinterpret_cast<uint4*>(region + h.sched_off);
+      for (int k = lane; k < h.sched_bytes / 16; k += 32) sd[k] = __ldg(ss + k);
+      // the zeros that padding moves read, after each input buffer
+      if (lane < 2) *reinterpret_cast<uint4*>(region + h.buf_off + lane * (h.in_bytes + kZeroTail) + h.in_bytes) =
+          make_uint4(0, 0, 0, 0);
+      __syncwarp();
       cur = arr;
     }
-    const int nw = h.warps;
-    const int64_t per_block = (int64_t)h.chunks_per_warp * nw;
-    const int64_t c_begin = (blk - h.block0) * per_block;
-    const int64_t c_end = c_begin + per_block < h.n_chunks ? c_begin + per_block : h.n_chunks;
-    uint8_t* buf0 = wbase + (size_t)warp * h.warp_bytes;
-    uint8_t* buf1 = buf0 + h.in_bytes;
-    uint8_t* outb = buf1 + h.in_bytes;
-    const int64_t full_end = c_end < h.n_full ? c_end : h.n_full;
-    const int64_t R = h.R;
-    const int in_bytes = h.in_bytes, pieces = h.pieces;
+    const GroupRef* tout = tin + h.n_src;
+    const uint32_t* sched = reinterpret_cast<const uint32_t*>(region + h.sched_off);
+    uint8_t* buf0 = region + h.buf_off;
+    uint8_t* buf1 = buf0 + h.in_bytes + kZeroTail;
+    uint8_t* outb = buf1 + h.in_bytes + kZeroTail;
+    const int R = h.R, in_bytes = h.in_bytes;
+    const int64_t c_begin = (u - h.unit0) * h.chunks_per_unit;
+    const int64_t c_end = min(c_begin + (int64_t)h.chunks_per_unit, h.n_chunks);
+    const int64_t full_end = min(c_end, h.n_full);
+    // lane l copies the 16-byte pieces l, l + 32, ... of the chunk's source slices, finding each
+    // piece's group by a search that resumes where the last piece's ended
     auto stage = [&](int64_t ch, uint8_t* buf) {
-      if (pieces & 1) {
-#pragma unroll 1
-        for (int q = lane; q < in_pieces; q += 32) {
-          const Piece pc = pin[q];
-          cp_async16(buf + q * 16, pc.base + ch * pc.step);
-        }
-      } else {
-        int g = 0;
-        for (int q = lane * 16; q < in_bytes; q += 512) {
-          while (q >= tin[g].start + (int)R * tin[g].stride) ++g;
-          cp_async16(buf + q, tin[g].ptr + ch * R * tin[g].stride + (q - tin[g].start));
-        }
+      int g = 0;
+      for (int q = lane * 16; q < in_bytes; q += 512) {
+        while (q >= tin[g].start + R * tin[g].stride) ++g;
+        cp_async16(buf + q, tin[g].ptr + ch * R * tin[g].stride + (q - tin[g].start));
       }
     };
-    int64_t c = warp < nw ? c_begin + warp : full_end;
+    int64_t c = c_begin;
     if (c < full_end) stage(c, buf0);
     cp_async_commit();
-    for (int i = 0; c < full_end; c += nw, ++i) {
+    for (int i = 0; c < full_end; ++c, ++i) {
       uint8_t* curb = (i & 1) ? buf1 : buf0;
-      if (c + nw < full_end) stage(c + nw, (i & 1) ? buf0 : buf1);
+      if (c + 1 < full_end) stage(c + 1, (i & 1) ? buf0 : buf1);
       cp_async_commit();
       cp_async_wait<1>();
       __syncwarp();
-      move_chunk<DIRECT>(sched, h.R, h.cls_count, curb, outb, tout, c * R, lane);
+      move_chunk<DIRECT>(sched, R, h.cls_count, curb, outb, tout, c * R, lane);
       __syncwarp();
-      if (pieces & 2) {
-#pragma unroll 1
-        for (int q = lane; q < out_pieces; q += 32) {
-          const Piece pc = pout[q];
-          *reinterpret_cast<uint4*>(const_cast<uint8_t*>(pc.base) + c * pc.step) =
-              *reinterpret_cast<const uint4*>(outb + q * 16);
-        }
-      } else {
-        write_back<DIRECT>(tout, h.R, h.out_bytes, outb, c, lane);
-      }
+      write_back<DIRECT>(tout, R, h.out_bytes, outb, c, lane);
       __syncwarp();
     }
     cp_async_wait<0>();
-    // the array's ragged tail chunk, by the warp it falls to
-    if (warp < nw && h.n_full < h.n_chunks && h.n_full >= c_begin && h.n_full < c_end && (h.n_full - c_begin) % nw == warp)
-      tail_moves(h.n_full * h.R, h.n, h.n_moves, h.cls_count, moves, tin, tout, lane);
-    __syncthreads();
+    // the array's ragged tail chunk (fewer than R records) lies in this unit: move by move
+    if (c_end > h.n_full) tail_moves(h.n_full * R, h.n, h.n_moves, h.cls_count, p.moves + h.move0, tin, tout, lane);
+    __syncwarp();
   }
 }
 
@@ -164,15 +147,16 @@ __global__ void __launch_bounds__(kThreads) batched_kernel(const __grid_constant
 using namespace adha;
 
 struct adha_batched {
-  int32_t n_arrays = 0;
+  int32_t n_arrays = 0;            // arrays listed for the kernel (those with bytes to move)
   std::vector<uint8_t> image;      // descriptor region as it is copied to the workspace
-  size_t off_headers = 0, off_groups = 0, off_moves = 0, off_prefix = 0;
-  int64_t total_blocks = 0;
-  int32_t max_entries = 0, max_pieces = 0, warp_budget = 0;
+  size_t off_headers = 0, off_groups = 0, off_moves = 0, off_sched = 0, off_prefix = 0;
+  int64_t total_units = 0;
+  int32_t region = 0;              // shared bytes per warp
+  int32_t ctas_per_sm = 0;
   size_t smem = 0;
   int grid = 1;
   double bytes = 0;
-  bool direct = false;          // some array stores one-field destination groups directly
+  bool direct = false;             // some array stores one-field destination groups directly
   cudaGraphExec_t graph = nullptr;
   void* graph_ws = nullptr;
 };
@@ -180,6 +164,7 @@ struct adha_batched {
 namespace adha {
 
 static size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+static int al16(int x) { return (x + 15) / 16 * 16; }
 
 static BatchParams params_for(const adha_batched* b, void* ws) {
   uint8_t* base = static_cast<uint8_t*>(ws);
@@ -188,18 +173,18 @@ static BatchParams params_for(const adha_batched* b, void* ws) {
   p.headers = reinterpret_cast<const BatchHeader*>(base + b->off_headers);
   p.groups = reinterpret_cast<const GroupRef*>(base + b->off_groups);
   p.moves = reinterpret_cast<const Move*>(base + b->off_moves);
+  p.sched = base + b->off_sched;
   p.prefix = reinterpret_cast<const int64_t*>(base + b->off_prefix);
   p.n_arrays = b->n_arrays;
-  p.total_blocks = b->total_blocks;
-  p.max_entries = b->max_entries;
-  p.max_pieces = b->max_pieces;
+  p.region = b->region;
+  p.total_units = b->total_units;
   return p;
 }
 
 static int launch_batched(const adha_batched* b, void* ws, void* stream) {
   cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(unsigned long long), (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(ticket)");
-  if (b->total_blocks == 0) return 0;
+  if (b->total_units == 0) return 0;
   auto* k = b->direct ? batched_kernel<true> : batched_kernel<false>;
   e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(batched)");
@@ -209,7 +194,8 @@ static int launch_batched(const adha_batched* b, void* ws, void* stream) {
   return 0;
 }
 
-// Default chunk of an array in the batched kernel: the single-array rule, but at least 32 records.
+// Default chunk of an array: the single-array rule (about 4 KB of the wider side), at least 32
+// records; the warp-region budget may shorten it.
 static int batch_chunk(const Layout& S, const Layout& D) {
   int src = 0, dst = 0;
   for (int g = 0; g < S.n_groups; ++g) src += S.stride[g];
@@ -219,17 +205,30 @@ static int batch_chunk(const Layout& S, const Layout& D) {
   return R;
 }
 
-// Chooses each array's chunk size, direct stores and piece tables: the default rules, or
-// (autotune) the fastest measured with the single-array remap kernel on the array's own buffers:
-// first 32..256 records x direct stores, then the four piece-table choices for the best of those.
+// Shared bytes of one warp working on an array with chunks of R records: header, group table,
+// schedule (R x moves entries of 4 bytes), two input buffers (each followed by the zeros that
+// padding moves read) and an output buffer.
+static int warp_region_bytes(const RemapArgs& a, int R) {
+  const int in_rec = a.in_bytes / a.R, out_rec = a.out_bytes / a.R;
+  return kHeaderBytes + (a.n_src + a.n_dst) * (int)sizeof(GroupRef) + al16(R * a.n_moves * 4) +
+         R * (2 * in_rec + out_rec) + 2 * kZeroTail;
+}
+
+// Chooses an array's chunk size and direct stores (autotune): the fastest of 32..256 records x
+// direct stores, timed with the single-array remap kernel on the array's own buffers (without
+// piece tables, which the batched kernel does not use).
 static int tune_chunk(const Layout& S, const void* const* sp, const Layout& D, void* const* dp, int64_t n, void* stream,
-                      int* best_R, int* best_direct, int* best_pieces) {
+                      int* best_R, int* best_direct) {
   cudaEvent_t e0, e1;
-  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return fail(ADHA_ECUDA, "cudaEventCreate");
-  auto time_ms = [&](int R, int direct, int pieces, float* ms) {
+  if (cudaEventCreate(&e0) != cudaSuccess) return fail(ADHA_ECUDA, "cudaEventCreate");
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(ADHA_ECUDA, "cudaEventCreate");
+  }
+  auto time_ms = [&](int R, int direct, float* ms) {
     adha_tune_override(R);
     adha_tune_remap_direct(direct);
-    adha_tune_remap_pieces(pieces);
+    adha_tune_remap_pieces(1);
     int rc = 0;
     for (int w = 0; w < 2 && !rc; ++w) rc = remap_layouts(S, sp, D, dp, n, stream, nullptr);
     cudaEventRecord(e0, (cudaStream_t)stream);
@@ -239,40 +238,41 @@ static int tune_chunk(const Layout& S, const void* const* sp, const Layout& D, v
     adha_tune_remap_direct(0);
     adha_tune_remap_pieces(0);
     if (rc) return rc;
-    cudaEventSynchronize(e1);
-    cudaEventElapsedTime(ms, e0, e1);
-    return 0;
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+    return e == cudaSuccess ? 0 : cuda_fail(e, "timing a batched array");
   };
   float best = -1, ms = 0;
   int rc = 0;
-  // 32..256 records (shorter chunks only add per-chunk work); longer ones only while a warp's
-  // buffers stay small enough for a CTA's eight warps
   for (int trial = 0; trial < 8 && !rc; ++trial) {
     const int R = 32 << (trial >> 1), direct = trial & 1;
     RemapArgs a;
     bool empty = false;
     rc = remap_plan_args(S, sp, D, dp, n, R, direct, &a, &empty);
     if (rc || empty) break;
-    if (2 * a.in_bytes + a.out_bytes > kTuneWarpBytes && R > 32) continue;
-    rc = time_ms(R, direct, 0, &ms);
+    if (a.R != R) continue;   // too wide for this chunk in the single-array kernel
+    rc = time_ms(R, direct, &ms);
     if (!rc && (best < 0 || ms < best)) {
       best = ms;
       *best_R = R;
       *best_direct = direct;
-      *best_pieces = a.pieces;
-    }
-  }
-  for (int m = 1; m <= 4 && !rc && best >= 0; ++m) {
-    rc = time_ms(*best_R, *best_direct, m, &ms);
-    if (!rc && ms < best) {
-      best = ms;
-      *best_pieces = m - 1;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return rc;
 }
+
+struct ArrayPlan {
+  Layout S, D;
+  int64_t n = 0;
+  const void* const* sp = nullptr;
+  void* const* dp = nullptr;
+  int R0 = 0, direct = 0;   // preferred chunk, direct stores
+  bool empty = true;
+  double moved = 0;         // algorithmic bytes of the array
+  RemapArgs a;              // at R0
+};
 
 }  // namespace adha
 
@@ -282,152 +282,187 @@ int adha_batched_create(int32_t n_arrays, const adha_remap_desc* descs, int32_t 
                         adha_batched** out) {
   clear_error();
   if (!out || !descs || n_arrays < 1) return fail(ADHA_EINVAL, "bad batched arguments");
-  auto* b = new (std::nothrow) adha_batched();
-  if (!b) return fail(ADHA_ENOMEM, "host allocation failed");
-  std::vector<BatchHeader> headers;
-  std::vector<GroupRef> groups;
-  std::vector<Move> moves;
-  std::vector<double> moved_bytes;   // per array, for the choice of CTAs per SM
-  int max_pieces = 0, max_warp = 0;
+  const int forced_ctas = (flags >> 4) & 15;
+  if (forced_ctas > kMaxBatchedCtas) return fail(ADHA_EINVAL, "ADHA_BATCHED_CTAS(%d) is not in 1..%d", forced_ctas, kMaxBatchedCtas);
+  std::vector<ArrayPlan> plans(n_arrays);
   for (int k = 0; k < n_arrays; ++k) {
     const adha_remap_desc& d = descs[k];
-    Layout S, D;
-    int rc = make_layout(d.schema, d.src, &S, "source");
-    if (!rc) rc = make_layout(d.schema, d.dst, &D, "destination");
+    ArrayPlan& ap = plans[k];
+    int rc = make_layout(d.schema, d.src, &ap.S, "source");
+    if (!rc) rc = make_layout(d.schema, d.dst, &ap.D, "destination");
     if (!rc && d.n < 0) rc = fail(ADHA_EINVAL, "array %d has n = %lld", k, (long long)d.n);
     if (!rc && d.n > 0) {
-      for (int g = 0; g < S.n_groups && !rc; ++g)
+      for (int g = 0; g < ap.S.n_groups && !rc; ++g)
         if (!d.src_ptrs || !d.src_ptrs[g] || reinterpret_cast<uintptr_t>(d.src_ptrs[g]) % 16)
           rc = fail(ADHA_EINVAL, "array %d source buffer %d is NULL or misaligned", k, g);
-      for (int g = 0; g < D.n_groups && !rc; ++g)
+      for (int g = 0; g < ap.D.n_groups && !rc; ++g)
         if (!d.dst_ptrs || !d.dst_ptrs[g] || reinterpret_cast<uintptr_t>(d.dst_ptrs[g]) % 16)
           rc = fail(ADHA_EINVAL, "array %d destination buffer %d is NULL or misaligned", k, g);
     }
-    int R = 0, direct = 0, pieces = -1;
-    if (!rc && d.n > 0 && (flags & ADHA_BATCHED_AUTOTUNE))
-      rc = tune_chunk(S, d.src_ptrs, D, d.dst_ptrs, d.n, stream, &R, &direct, &pieces);
-    RemapArgs a;
-    bool empty = true;
-    if (!rc && d.n > 0) rc = remap_plan_args(S, d.src_ptrs, D, d.dst_ptrs, d.n, R ? R : batch_chunk(S, D), direct, &a, &empty);
-    if (rc) {
-      delete b;
-      return rc;
-    }
-    BatchHeader h;
-    std::memset(&h, 0, sizeof h);
-    double moved = 0;
-    if (!empty) {
-      h.n = a.n;
-      h.R = a.R;
-      h.n_full = a.n_chunks;
-      h.n_chunks = a.n_chunks + (a.n % a.R ? 1 : 0);
-      h.n_src = a.n_src;
-      h.n_dst = a.n_dst;
-      h.in_bytes = a.in_bytes;
-      h.out_bytes = a.out_bytes;
-      h.n_moves = a.n_moves;
-      for (int c = 0; c < 6; ++c) {
-        h.cls_count[c] = a.cls_count[c];
-        h.cls_order[c] = a.cls_order[c];
-      }
-      h.pieces = pieces >= 0 ? pieces : a.pieces;
-      b->direct = b->direct || (a.cls_count[0] + a.cls_count[1] + a.cls_count[2] > 0);
-      h.group0 = (int32_t)groups.size();
-      h.move0 = (int32_t)moves.size();
-      h.warp_bytes = 2 * a.in_bytes + a.out_bytes;
-      max_warp = std::max(max_warp, h.warp_bytes);
-      max_pieces = std::max(max_pieces, ((h.pieces & 1) ? a.in_bytes / 16 : 0) + ((h.pieces & 2) ? a.out_bytes / 16 : 0));
-      for (int g = 0; g < a.n_src; ++g) groups.push_back(a.src[g]);
-      for (int g = 0; g < a.n_dst; ++g) groups.push_back(a.dst[g]);
-      moves.insert(moves.end(), a.move, a.move + a.n_moves);
-      h.chunks_per_warp = std::max(1, kBlockRecordsPerWarp / h.R);
-      b->max_entries = std::max(b->max_entries, a.R * a.n_moves);
-      for (int g = 0; g < D.n_groups; ++g) {
+    if (rc) return rc;
+    ap.n = d.n;
+    ap.sp = d.src_ptrs;
+    ap.dp = d.dst_ptrs;
+    if (d.n == 0) continue;
+    int R = 0, direct = 0;
+    if (flags & ADHA_BATCHED_AUTOTUNE) rc = tune_chunk(ap.S, d.src_ptrs, ap.D, d.dst_ptrs, d.n, stream, &R, &direct);
+    if (!rc) rc = remap_plan_args(ap.S, d.src_ptrs, ap.D, d.dst_ptrs, d.n, R ? R : batch_chunk(ap.S, ap.D), direct, &ap.a,
+                                  &ap.empty);
+    if (rc) return rc;
+    ap.R0 = ap.a.R;
+    ap.direct = direct;
+    if (!ap.empty)
+      for (int g = 0; g < ap.D.n_groups; ++g) {
         bool alias = false;
-        for (int j = 0; j < S.n_groups; ++j) alias = alias || (same_group(D, g, S, j) && d.dst_ptrs[g] == d.src_ptrs[j]);
+        for (int j = 0; j < ap.S.n_groups; ++j)
+          alias = alias || (same_group(ap.D, g, ap.S, j) && d.dst_ptrs[g] == d.src_ptrs[j]);
         if (!alias)
-          for (int f : D.groups[g]) moved += dtype_size(D.dtype[f]);
+          for (int f : ap.D.groups[g]) ap.moved += 2.0 * dtype_size(ap.D.dtype[f]) * (double)d.n;
       }
-      b->bytes += 2.0 * moved * (double)d.n;
-    }
-    moved_bytes.push_back(2.0 * moved * (double)d.n);
-    headers.push_back(h);
   }
-  b->max_entries = (b->max_entries + 3) / 4 * 4;
-  b->max_pieces = max_pieces;
 
-  // CTAs per SM: 1..4, each with the shared memory left by the others; the warp-buffer budget is
-  // what remains after the tables.  The choice maximises the working warps per SM weighted by
-  // each array's bytes (an array gets as many warps of a CTA as its buffers fit, at most 8).
+  // CTAs per SM (1..4) and the shared region of a warp: every array must fit its chunk buffers
+  // and tables in one region, shortening its chunk (down to 8 records) where it must.  The choice
+  // maximises the arrays' bytes x CTAs per SM, discounted where an array's chunk had to shrink
+  // below min(its preferred chunk, 32) records.
   int sms = 0, dev = 0, sm_smem = 0, reserved = 0, optin = 0;
-  if (int rc = sm_count(&sms)) {
-    delete b;
-    return rc;
-  }
+  if (int rc = sm_count(&sms)) return rc;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  auto* kern = b->direct ? batched_kernel<true> : batched_kernel<false>;
+  bool direct_any = false;
+  for (const ArrayPlan& ap : plans) direct_any = direct_any || (!ap.empty && ap.a.cls_count[0] + ap.a.cls_count[1] + ap.a.cls_count[2] > 0);
+  auto* kern = direct_any ? batched_kernel<true> : batched_kernel<false>;
   cudaFuncAttributes fa;
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
-  if (e != cudaSuccess) {
-    delete b;
-    return cuda_fail(e, "device attributes for the batched kernel");
-  }
-  const size_t fixed = (size_t)2 * kMaxGroups * sizeof(GroupRef) + kMaxMoves * sizeof(Move) +
-                       (size_t)b->max_entries * 4 + (size_t)max_pieces * sizeof(Piece);
+  if (e != cudaSuccess) return cuda_fail(e, "device attributes for the batched kernel");
+  auto fit_R = [&](const ArrayPlan& ap, int region) {
+    int R = ap.R0;
+    while (R > 8 && warp_region_bytes(ap.a, R) > region) R = std::max(8, R / 2 / 8 * 8);
+    return warp_region_bytes(ap.a, R) <= region ? R : 0;
+  };
+  // CTAs per SM that the kernel's registers allow at all
+  int reg_ctas = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&reg_ctas, kern, kThreads, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "batched occupancy (registers)");
+  const int max_k = std::max(1, std::min(kMaxBatchedCtas, reg_ctas));
+  if (forced_ctas > max_k)
+    return fail(ADHA_EINVAL, "ADHA_BATCHED_CTAS(%d): the kernel's registers allow at most %d CTAs per SM", forced_ctas, max_k);
   double best_score = -1;
-  for (int k = 1; k <= 4; ++k) {
-    const int64_t dyn = std::min<int64_t>(optin, (int64_t)sm_smem / k - reserved - (int64_t)fa.sharedSizeBytes) / 16 * 16;
-    const int64_t budget = dyn - (int64_t)fixed;
-    if (budget < std::max(max_warp, 1)) continue;
+  int best_k = 0, best_region = 0;
+  for (int k = 1; k <= max_k; ++k) {
+    if (forced_ctas && k != forced_ctas) continue;
+    const int64_t dyn = std::min<int64_t>(optin, (int64_t)sm_smem / k - reserved - (int64_t)fa.sharedSizeBytes);
+    const int region = (int)(dyn / kWarps / 16 * 16);
     double score = 0;
-    for (size_t a = 0; a < headers.size(); ++a)
-      if (headers[a].warp_bytes > 0)
-        score += moved_bytes[a] * k * std::min<int64_t>(kWarps, budget / headers[a].warp_bytes);
-    if (score > best_score) {
+    bool ok = region > kHeaderBytes;
+    for (const ArrayPlan& ap : plans) {
+      if (ap.empty || !ok) continue;
+      const int R = fit_R(ap, region);
+      if (!R) {
+        ok = false;
+        continue;
+      }
+      const int want = std::min(ap.R0, 32);
+      score += ap.moved * k * std::min(1.0, (double)R / want);
+    }
+    if (ok && score > best_score) {
       best_score = score;
-      b->warp_budget = (int32_t)budget;
+      best_k = k;
+      best_region = region;
     }
   }
-  if (best_score < 0) {
-    const size_t need = fixed + (size_t)max_warp;
-    delete b;
-    return fail(ADHA_ENOTIMPL, "batched remap needs %zu bytes of shared memory per CTA (limit %d): an array is too wide",
-                need, optin);
-  }
+  if (best_k == 0)
+    return fail(ADHA_ENOTIMPL, "batched remap: an array's records are too wide for the shared memory of one warp");
+
+  // the arrays' final plans, in ticket order (largest first), and the descriptor image
+  std::vector<int> order;
+  for (int k = 0; k < n_arrays; ++k)
+    if (!plans[k].empty) order.push_back(k);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return plans[x].moved > plans[y].moved; });
+  std::vector<BatchHeader> headers;
+  std::vector<GroupRef> groups;
+  std::vector<Move> moves;
+  std::vector<uint32_t> sched;
   std::vector<int64_t> prefix;
-  int64_t blocks = 0;
-  for (BatchHeader& h : headers) {
-    h.block0 = blocks;
-    prefix.push_back(blocks);
-    if (h.warp_bytes == 0) continue;
-    h.warps = (int32_t)std::max(1, std::min(kWarps, b->warp_budget / h.warp_bytes));
-    const int64_t per_block = (int64_t)h.chunks_per_warp * h.warps;
-    blocks += (h.n_chunks + per_block - 1) / per_block;
+  int64_t units = 0;
+  double bytes = 0;
+  bool direct = false;
+  for (int k : order) {
+    ArrayPlan& ap = plans[k];
+    const int R = fit_R(ap, best_region);
+    RemapArgs& a = ap.a;
+    if (R != a.R) {
+      bool empty = false;
+      if (int rc = remap_plan_args(ap.S, ap.sp, ap.D, ap.dp, ap.n, R, ap.direct, &a, &empty)) return rc;
+      if (a.R != R) return fail(ADHA_ENOTIMPL, "batched remap: array %d cannot use %d-record chunks", k, R);
+    }
+    BatchHeader h;
+    std::memset(&h, 0, sizeof h);
+    h.n = a.n;
+    h.R = a.R;
+    h.n_full = a.n_chunks;
+    h.n_chunks = a.n_chunks + (a.n % a.R ? 1 : 0);
+    h.n_src = a.n_src;
+    h.n_dst = a.n_dst;
+    h.in_bytes = a.in_bytes;
+    h.out_bytes = a.out_bytes;
+    h.n_moves = a.n_moves;
+    for (int c = 0; c < kMoveClasses; ++c) h.cls_count[c] = a.cls_count[c];
+    h.group0 = (int32_t)groups.size();
+    h.move0 = (int32_t)moves.size();
+    h.chunks_per_unit = std::max(1, kUnitRecords / a.R);
+    h.sched_bytes = al16(a.R * a.n_moves * 4);
+    h.sched_off = kHeaderBytes + (a.n_src + a.n_dst) * (int)sizeof(GroupRef);
+    h.buf_off = h.sched_off + h.sched_bytes;
+    h.sched0 = (int64_t)sched.size() * 4;
+    h.unit0 = units;
+    prefix.push_back(units);
+    units += (h.n_chunks + h.chunks_per_unit - 1) / h.chunks_per_unit;
+    for (int g = 0; g < a.n_src; ++g) groups.push_back(a.src[g]);
+    for (int g = 0; g < a.n_dst; ++g) groups.push_back(a.dst[g]);
+    moves.insert(moves.end(), a.move, a.move + a.n_moves);
+    const size_t s0 = sched.size();
+    sched.resize(s0 + h.sched_bytes / 4, 0u);
+    for (int t = 0; t < a.R * a.n_moves; ++t)
+      sched[s0 + t] = schedule_entry(t, a.R, a.cls_count, a.cls_order, a.move, a.src, a.dst, a.in_bytes);
+    direct = direct || (a.cls_count[0] + a.cls_count[1] + a.cls_count[2] > 0);
+    bytes += ap.moved;
+    headers.push_back(h);
   }
-  prefix.push_back(blocks);
-  b->n_arrays = n_arrays;
-  b->total_blocks = blocks;
+  prefix.push_back(units);
+
+  auto* b = new (std::nothrow) adha_batched();
+  if (!b) return fail(ADHA_ENOMEM, "host allocation failed");
+  b->n_arrays = (int32_t)headers.size();
+  b->total_units = units;
+  b->bytes = bytes;
+  b->direct = direct;
+  b->region = best_region;
+  b->ctas_per_sm = best_k;
   b->off_headers = al256(sizeof(unsigned long long));
-  b->off_groups = b->off_headers + al256(headers.size() * sizeof(BatchHeader));
+  b->off_groups = b->off_headers + al256(std::max<size_t>(1, headers.size()) * sizeof(BatchHeader));
   b->off_moves = b->off_groups + al256(std::max<size_t>(1, groups.size()) * sizeof(GroupRef));
-  b->off_prefix = b->off_moves + al256(std::max<size_t>(1, moves.size()) * sizeof(Move));
+  b->off_sched = b->off_moves + al256(std::max<size_t>(1, moves.size()) * sizeof(Move));
+  b->off_prefix = b->off_sched + al256(std::max<size_t>(1, sched.size()) * 4);
   b->image.assign(b->off_prefix + al256(prefix.size() * sizeof(int64_t)), 0);
-  std::memcpy(b->image.data() + b->off_headers, headers.data(), headers.size() * sizeof(BatchHeader));
+  if (!headers.empty()) std::memcpy(b->image.data() + b->off_headers, headers.data(), headers.size() * sizeof(BatchHeader));
   if (!groups.empty()) std::memcpy(b->image.data() + b->off_groups, groups.data(), groups.size() * sizeof(GroupRef));
   if (!moves.empty()) std::memcpy(b->image.data() + b->off_moves, moves.data(), moves.size() * sizeof(Move));
+  if (!sched.empty()) std::memcpy(b->image.data() + b->off_sched, sched.data(), sched.size() * 4);
   std::memcpy(b->image.data() + b->off_prefix, prefix.data(), prefix.size() * sizeof(int64_t));
-  b->smem = fixed + (size_t)b->warp_budget;
+  b->smem = (size_t)kWarps * best_region;
   int per_sm = 0;
-  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, b->smem);
+  auto* k2 = b->direct ? batched_kernel<true> : batched_kernel<false>;
+  e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k2, kThreads, b->smem);
   if (e != cudaSuccess) {
     delete b;
     return cuda_fail(e, "batched occupancy");
   }
-  b->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * std::max(1, per_sm), blocks));
+  const int64_t want_ctas = (units + kWarps - 1) / kWarps;
+  b->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * std::max(1, per_sm), want_ctas));
   *out = b;
   return 0;
 }
@@ -468,7 +503,6 @@ int adha_batched_graph(adha_batched* b, void* workspace, adha_stream stream) {
   // Capture on a private stream (the legacy default stream cannot be captured); the graph is
   // later launched on the caller's stream.  `stream` is synchronized first so that the capture
   // does not race with work already queued there.
-  (void)stream;
   cudaStream_t s = nullptr;
   cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
@@ -515,6 +549,73 @@ void adha_batched_destroy(adha_batched* b) {
 
 double adha_batched_bytes(const adha_batched* b) { return b ? b->bytes : 0.0; }
 
+int adha_batched_info(const adha_batched* b, int32_t* ctas_per_sm, int32_t* warp_region_bytes, int64_t* units) {
+  clear_error();
+  if (!b) return fail(ADHA_EINVAL, "NULL batched plan");
+  if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
+  if (warp_region_bytes) *warp_region_bytes = b->region;
+  if (units) *units = b->total_units;
+  return 0;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// One-call batched remap: plan, descriptors into the caller's workspace, launch.
+
+namespace adha {
+
+// The descriptor image is copied from pageable host memory that is freed when the call returns:
+// safe for a plain enqueue (the copy is staged before cudaMemcpyAsync returns), not for a
+// capture, which would record a copy node reading freed memory on every replay.
+static int reject_capture(void* stream) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  const cudaError_t e = cudaStreamIsCapturing((cudaStream_t)stream, &st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamIsCapturing");
+  if (st != cudaStreamCaptureStatusNone)
+    return fail(ADHA_EINVAL, "the stream is being captured: this call copies its descriptors from a host buffer "
+                             "it frees on return (capture adha_batched_launch instead)");
+  return 0;
+}
+
+}  // namespace adha
+
+extern "C" {
+
+int adha_workspace_bytes(int32_t n_arrays, const adha_remap_desc* descs, size_t* bytes) {
+  clear_error();
+  if (!bytes) return fail(ADHA_EINVAL, "bytes is NULL");
+  adha_batched* b = nullptr;
+  if (int rc = adha_batched_create(n_arrays, descs, 0, nullptr, &b)) return rc;
+  *bytes = b->image.size();
+  adha_batched_destroy(b);
+  return 0;
+}
+
+int adha_remap_batched(int32_t n_arrays, const adha_remap_desc* descs, void* workspace, size_t ws_bytes,
+                       adha_stream stream) {
+  clear_error();
+  if (!workspace) return fail(ADHA_EINVAL, "workspace is NULL");
+  if (reinterpret_cast<uintptr_t>(workspace) % 256) return fail(ADHA_EINVAL, "workspace is not 256-byte aligned");
+  if (int rc = reject_capture(stream)) return rc;
+  adha_batched* b = nullptr;
+  if (int rc = adha_batched_create(n_arrays, descs, 0, stream, &b)) return rc;
+  if (ws_bytes < b->image.size()) {
+    const size_t need = b->image.size();
+    adha_batched_destroy(b);
+    return fail(ADHA_ENOMEM, "workspace has %zu bytes, the batch needs %zu (adha_workspace_bytes)", ws_bytes, need);
+  }
+  cudaError_t e = cudaMemcpyAsync(workspace, b->image.data(), b->image.size(), cudaMemcpyHostToDevice, (cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    adha_batched_destroy(b);
+    return cuda_fail(e, "copy of the batched descriptors into the workspace");
+  }
+  const std::pair<const adha_batched*, std::pair<void*, void*>> ctx{b, {workspace, stream}};
+  const int rc = profiled_launch(3, 3, b->bytes, stream, batched_fn, &ctx);
+  adha_batched_destroy(b);
+  return rc;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------------------------
@@ -536,13 +637,13 @@ static std::mutex g_noalloc_mu;
 static void* g_noalloc_ptr[256];
 
 // Device address of the scratch array on the current device, looked up once per device (the
-// host-side name of a __device__ array is only a stand-in, not a device address).
+// host-side name of a __device__ array is only a stand-in, not a device address).  The caller
+// holds g_noalloc_mu.
 static int noalloc_scratch(void** ptr) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   if (dev < 0 || dev >= 256) return fail(ADHA_ENOTIMPL, "device ordinal %d out of range", dev);
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
   if (!g_noalloc_ptr[dev]) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
@@ -557,8 +658,7 @@ static int noalloc_scratch(void** ptr) {
 
 extern "C" int adha_remap_batched_noalloc(int32_t n_arrays, const adha_remap_desc* descs, adha_stream stream) {
   clear_error();
-  void* scratch = nullptr;
-  if (int rc = noalloc_scratch(&scratch)) return rc;
+  if (int rc = reject_capture(stream)) return rc;
   adha_batched* b = nullptr;
   if (int rc = adha_batched_create(n_arrays, descs, 0, stream, &b)) return rc;
   const size_t need = b->image.size();
@@ -567,14 +667,22 @@ extern "C" int adha_remap_batched_noalloc(int32_t n_arrays, const adha_remap_des
     return fail(ADHA_EINVAL, "this batch needs %zu bytes of descriptors; the allocation-free entry point holds at most %u",
                 need, (unsigned)ADHA_NOALLOC_SCRATCH_BYTES);
   }
-  // Pageable source: the call returns once the bytes are staged, so the host image can go.
-  cudaError_t e = cudaMemcpyAsync(scratch, b->image.data(), need, cudaMemcpyHostToDevice, (cudaStream_t)stream);
-  if (e != cudaSuccess) {
-    adha_batched_destroy(b);
-    return cuda_fail(e, "copy of the batched descriptors into the scratch array");
+  int rc = 0;
+  {
+    // one thread's copy, ticket reset and kernel reach the stream before another thread's
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    void* scratch = nullptr;
+    rc = noalloc_scratch(&scratch);
+    if (!rc) {
+      // pageable source: the bytes are staged before the call returns, so the host image can go
+      const cudaError_t e = cudaMemcpyAsync(scratch, b->image.data(), need, cudaMemcpyHostToDevice, (cudaStream_t)stream);
+      if (e != cudaSuccess) rc = cuda_fail(e, "copy of the batched descriptors into the scratch array");
+    }
+    if (!rc) {
+      const std::pair<const adha_batched*, std::pair<void*, void*>> ctx{b, {scratch, stream}};
+      rc = profiled_launch(3, 2, b->bytes, stream, batched_fn, &ctx);
+    }
   }
-  const std::pair<const adha_batched*, std::pair<void*, void*>> ctx{b, {scratch, stream}};
-  const int rc = profiled_launch(3, 2, b->bytes, stream, batched_fn, &ctx);
   adha_batched_destroy(b);
   return rc;
 }

@@ -619,6 +619,8 @@ static int check_section(const Layout& L, const adha_section* s, int64_t n, bool
   return 0;
 }
 
+int check_section_layout(const Layout& L, const adha_section* s, int64_t n) { return check_section(L, s, n, false); }
+
 struct SectionPlan {
   SectionArgs args;
   size_t smem = 0;
@@ -1151,11 +1153,28 @@ int adha_tune_import(const char* text) {
     p = eol ? eol + 1 : p + line.size();
     if (line.empty()) continue;
     const size_t t1 = line.find('\t'), t2 = line.find('\t', t1 == std::string::npos ? 0 : t1 + 1);
-    if (t1 == std::string::npos || t2 == std::string::npos) return fail(ADHA_EINVAL, "bad tuning line: %s", line.c_str());
-    const int R = std::atoi(line.c_str() + t1 + 1), wb = std::atoi(line.c_str() + t2 + 1);
-    const bool remap = line[0] == 'M';
-    if (remap ? (R != 0 || wb < 0 || wb > 3) : (R < 0 || R > 128 || R % 32 || wb < 0 || wb > 2))
-      return fail(ADHA_EINVAL, "bad tuning values: %s", line.c_str());
+    if (t1 == std::string::npos || t2 == std::string::npos || t1 < 2 || line.find('\t', t2 + 1) != std::string::npos)
+      return fail(ADHA_EINVAL, "bad tuning line (want key<TAB>records<TAB>mode): %s", line.c_str());
+    const char kind = line[0];
+    if (kind != 'S' && kind != 'M' && kind != 'F') return fail(ADHA_EINVAL, "bad tuning key kind '%c': %s", kind, line.c_str());
+    // both values whole decimal numbers, nothing else on the line
+    auto number = [&](size_t from, size_t to, int* v) {
+      if (to <= from || to - from > 6) return false;
+      int x = 0;
+      for (size_t q = from; q < to; ++q) {
+        if (line[q] < '0' || line[q] > '9') return false;
+        x = 10 * x + (line[q] - '0');
+      }
+      *v = x;
+      return true;
+    };
+    int R = 0, wb = 0;
+    if (!number(t1 + 1, t2, &R) || !number(t2 + 1, line.size(), &wb))
+      return fail(ADHA_EINVAL, "bad tuning values (not whole numbers): %s", line.c_str());
+    const bool bad = kind == 'M'   ? (R != 0 || wb > 3)
+                     : kind == 'F' ? (R % 32 || R > 128 || wb > 2)
+                                   : (R % 32 || R > 128 || wb > 2);
+    if (bad) return fail(ADHA_EINVAL, "bad tuning values: %s", line.c_str());
     parsed[line.substr(0, t1)] = {R, wb};
   }
   std::lock_guard<std::mutex> lk(g_tune_mu);

@@ -175,6 +175,8 @@ int run_section_layout(const Layout& L, void* const* ptrs, const adha_section* s
 int run_fused_layout(const Layout& L, void* const* ptrs, const adha_section* s, int m, int64_t n, void* stream);
 std::string fused_tuning_key(const Layout& L, const adha_section* s, int m, int64_t n);
 bool fusable_run(const Layout& L, const adha_section* s, int m);
+// ADHA_EINVAL (message set) unless section s may run on n records stored in L.
+int check_section_layout(const Layout& L, const adha_section* s, int64_t n);
 void fill_secop(const Layout& L, const adha_section* s, SecOp* o);
 adha_layout set_layout(const adha_layout_set* s, int l);
 // Remap launch arguments for one array (chunk_override 0 = the default chunk rule).
@@ -189,6 +191,8 @@ void set_overrides(int R, int wb);
 void set_fused_overrides(int R, int buffers);
 std::string remap_tuning_key(const Layout& S, const Layout& D, int64_t n);
 void set_remap_pieces(int mode);
+// ADHA_EINVAL unless every entry of the table is >= 0 or +inf (+inf: not measured or not allowed).
+int check_costs(const adha_cost_table* c);
 int pdl_solve(const adha_cost_table* c, int return_to_input, int32_t* seq, double* total);
 int pdl_solve_fused(const adha_cost_table* c, int return_to_input, int max_window, int32_t* seq, int32_t* win,
                     double* total);

@@ -126,8 +126,27 @@ adha_layout set_layout(const adha_layout_set* s, int l) {
 // remap(p -> l) + cost(k, m, l), where cost(k, 1, l) = section_ns and cost(k, m >= 2, l) =
 // fused_ns.  Ties: the smaller layout index, then the longer window, window by window from the
 // first (the lexicographically smallest sequence of (layout, -length) pairs).
+int check_costs(const adha_cost_table* c) {
+  const size_t L = (size_t)c->n_layouts, S = (size_t)c->n_sections;
+  auto bad = [](double v) { return std::isnan(v) || v < 0; };
+  for (size_t k = 0; k < S * L; ++k)
+    if (bad(c->section_ns[k]))
+      return fail(ADHA_EINVAL, "cost table: section_ns[%zu][%zu] = %g (costs must be >= 0 or +inf)", k / L, k % L,
+                  c->section_ns[k]);
+  for (size_t k = 0; k < (L + 1) * (L + 1); ++k)
+    if (bad(c->remap_ns[k]))
+      return fail(ADHA_EINVAL, "cost table: remap_ns[%zu][%zu] = %g (costs must be >= 0 or +inf)", k / (L + 1),
+                  k % (L + 1), c->remap_ns[k]);
+  if (c->max_window >= 2 && c->fused_ns)
+    for (size_t k = 0; k < S * (size_t)c->max_window * L; ++k)
+      if (bad(c->fused_ns[k]))
+        return fail(ADHA_EINVAL, "cost table: fused_ns entry %zu = %g (costs must be >= 0 or +inf)", k, c->fused_ns[k]);
+  return 0;
+}
+
 int pdl_solve_fused(const adha_cost_table* c, int return_to_input, int max_window, int32_t* seq, int32_t* win,
                     double* total) {
+  if (int rc = check_costs(c)) return rc;
   const int S = c->n_sections, L = c->n_layouts, In = L;
   const int W = std::max(1, std::min(max_window, std::max(1, c->max_window)));
   auto rem = [&](int a, int b) { return c->remap_ns[(size_t)a * (L + 1) + b]; };
@@ -165,10 +184,12 @@ int pdl_solve_fused(const adha_cost_table* c, int return_to_input, int max_windo
     p = l;
     k += m;
   }
+  if (std::isinf(*total)) return fail(ADHA_EINVAL, "cost table: every plan has an infinite cost");
   return 0;
 }
 
 int pdl_solve(const adha_cost_table* c, int return_to_input, int32_t* seq, double* total) {
+  if (int rc = check_costs(c)) return rc;
   const int S = c->n_sections, L = c->n_layouts, In = L;
   auto sec = [&](int k, int l) { return c->section_ns[(size_t)k * L + l]; };
   auto rem = [&](int a, int b) { return c->remap_ns[(size_t)a * (L + 1) + b]; };
@@ -198,6 +219,7 @@ int pdl_solve(const adha_cost_table* c, int return_to_input, int32_t* seq, doubl
     seq[k] = arg;
     prev = arg;
   }
+  if (std::isinf(*total)) return fail(ADHA_EINVAL, "cost table: every plan has an infinite cost");
   return 0;
 }
 

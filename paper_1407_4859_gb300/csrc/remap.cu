@@ -7,8 +7,8 @@
 //      16-byte cp.async (coalesced: lane l moves bytes 16l, 16l+512, ...), one chunk ahead of
 //      the one it works on (double buffering);
 //   2. it moves every field of every destination record, one move per lane per step: a move is
-//      one field (8, 4 or 2 bytes, whole) or an aligned piece of zero padding, taken from a
-//      schedule table built once per CTA.  Moves into one-field destination groups are stored
+//      one field (8, 4 or 2 bytes, whole) or an aligned piece of zero padding (read from 16 zero
+//      bytes after the chunk buffer), taken from a schedule table built once per CTA.  Moves into one-field destination groups are stored
 //      straight to global memory (consecutive lanes on consecutive records, so the stores are
 //      coalesced); moves into wider groups are assembled in a second buffer.  This is the tile
 //      transpose between the source and destination record strides; the host picks, per move
@@ -42,16 +42,17 @@ __global__ void __launch_bounds__(kThreads) remap_kernel(const __grid_constant__
   uint32_t* sched = reinterpret_cast<uint32_t*>(tout + a.n_dst);
   uint8_t* wbase = reinterpret_cast<uint8_t*>(sched) + align16(n_entries * 4);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  uint8_t* buf0 = wbase + (size_t)warp * (2 * a.in_bytes + a.out_bytes);
-  uint8_t* buf1 = buf0 + a.in_bytes;
-  uint8_t* outb = buf1 + a.in_bytes;
+  uint8_t* buf0 = wbase + (size_t)warp * (2 * (a.in_bytes + kZeroTail) + a.out_bytes);
+  uint8_t* buf1 = buf0 + a.in_bytes + kZeroTail;
+  uint8_t* outb = buf1 + a.in_bytes + kZeroTail;
+  if (lane < 2) *reinterpret_cast<uint4*>((lane ? buf1 : buf0) + a.in_bytes) = make_uint4(0, 0, 0, 0);
 
   for (int q = tid; q < in_pieces; q += kThreads) pin[q] = piece_of(q, a.src, a.R);
   for (int q = tid; q < out_pieces; q += kThreads) pout[q] = piece_of(q, a.dst, a.R);
   for (int k = tid; k < a.n_src; k += kThreads) tin[k] = a.src[k];
   for (int k = tid; k < a.n_dst; k += kThreads) tout[k] = a.dst[k];
   for (int t = tid; t < n_entries; t += kThreads)
-    sched[t] = schedule_entry(t, a.R, a.cls_count, a.cls_order, a.move, a.src, a.dst);
+    sched[t] = schedule_entry(t, a.R, a.cls_count, a.cls_order, a.move, a.src, a.dst, a.in_bytes);
   __syncthreads();
 
   const int64_t W = (int64_t)gridDim.x * kWarps;
@@ -108,7 +109,7 @@ size_t remap_smem_bytes(const RemapArgs& a) {
   auto al = [](size_t x) { return (x + 15) / 16 * 16; };
   const size_t pieces = ((a.pieces & 1) ? a.in_bytes / 16 : 0) + ((a.pieces & 2) ? a.out_bytes / 16 : 0);
   return pieces * sizeof(Piece) + (size_t)(a.n_src + a.n_dst) * sizeof(GroupRef) + al((size_t)a.R * a.n_moves * 4) +
-         (size_t)kWarps * (2 * (size_t)a.in_bytes + a.out_bytes);
+         (size_t)kWarps * (2 * ((size_t)a.in_bytes + kZeroTail) + a.out_bytes);
 }
 
 template <bool DIRECT>

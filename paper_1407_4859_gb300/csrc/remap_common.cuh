@@ -34,44 +34,65 @@ constexpr int kMoveClasses = 6;
 __host__ __device__ __forceinline__ int class_width(int c) { return 8 >> (c % 3); }
 
 // Schedule entry t of a chunk (R records, n_moves moves sorted into the six classes):
-// source byte in the chunk buffer (0xFFFF for padding) | destination << 16, where the
-// destination is (group << 10 | record) for direct classes and the output-buffer byte otherwise.
-__device__ __forceinline__ uint32_t schedule_entry(int t, int R, const int32_t* cls_count, const int32_t* cls_order,
-                                                   const Move* moves, const GroupRef* src, const GroupRef* dst) {
+// source byte in the chunk buffer | destination << 16, where the destination is
+// (group << 10 | record) for direct classes and the output-buffer byte otherwise.  A padding move
+// reads pad_src: the 16 zero bytes that follow every input chunk buffer, so that the move loops
+// need no test.
+__host__ __device__ __forceinline__ uint32_t schedule_entry(int t, int R, const int32_t* cls_count, const int32_t* cls_order,
+                                                            const Move* moves, const GroupRef* src, const GroupRef* dst,
+                                                            int pad_src) {
   int c = 0, first = 0;
   while (t >= R * (first + cls_count[c])) first += cls_count[c++];
   const int u = t - R * first, cnt = cls_count[c];
   int r, k;
   schedule_pair(u, R, cnt, cls_order[c], &r, &k);
   const Move m = moves[first + k];
-  const uint32_t s = m.src_group < 0 ? 0xFFFFu : (uint32_t)(src[m.src_group].start + r * src[m.src_group].stride + m.src_off);
+  const uint32_t s = m.src_group < 0 ? (uint32_t)pad_src
+                                     : (uint32_t)(src[m.src_group].start + r * src[m.src_group].stride + m.src_off);
   const uint32_t d = c < 3 ? (((uint32_t)m.dst_group << 10) | (uint32_t)r)
                            : (uint32_t)(dst[m.dst_group].start + r * dst[m.dst_group].stride + m.dst_off);
   return s | (d << 16);
 }
 
+// Bytes of zeros after each input chunk buffer (the source of padding moves).
+constexpr int kZeroTail = 16;
+
+// The moves of one class into the output buffer, four per lane per round: the four schedule
+// entries, then the four source values, then the four stores, so that one round's shared-memory
+// loads are in flight together (the buffers do not overlap).
 template <typename V>
-__device__ __forceinline__ void move_class_staged(const uint32_t* sched, int begin, int end, const uint8_t* in,
-                                                  uint8_t* out, int lane) {
-#pragma unroll 4
-  for (int t = begin + lane; t < end; t += 32) {
+__device__ __forceinline__ void move_class_staged(const uint32_t* __restrict__ sched, int begin, int end,
+                                                  const uint8_t* __restrict__ in, uint8_t* __restrict__ out, int lane) {
+  int t = begin + lane;
+  for (; t + 96 < end; t += 128) {
+    const uint32_t p0 = sched[t], p1 = sched[t + 32], p2 = sched[t + 64], p3 = sched[t + 96];
+    const V v0 = *reinterpret_cast<const V*>(in + (p0 & 0xFFFFu));
+    const V v1 = *reinterpret_cast<const V*>(in + (p1 & 0xFFFFu));
+    const V v2 = *reinterpret_cast<const V*>(in + (p2 & 0xFFFFu));
+    const V v3 = *reinterpret_cast<const V*>(in + (p3 & 0xFFFFu));
+    *reinterpret_cast<V*>(out + (p0 >> 16)) = v0;
+    *reinterpret_cast<V*>(out + (p1 >> 16)) = v1;
+    *reinterpret_cast<V*>(out + (p2 >> 16)) = v2;
+    *reinterpret_cast<V*>(out + (p3 >> 16)) = v3;
+  }
+  for (; t < end; t += 32) {
     const uint32_t p = sched[t];
-    const uint32_t s = p & 0xFFFFu;
-    *reinterpret_cast<V*>(out + (p >> 16)) = s != 0xFFFFu ? *reinterpret_cast<const V*>(in + s) : V(0);
+    *reinterpret_cast<V*>(out + (p >> 16)) = *reinterpret_cast<const V*>(in + (p & 0xFFFFu));
   }
 }
 
 // Moves into one-field destination groups go straight to global memory: record rec0 + r.
 template <typename V>
-__device__ __forceinline__ void move_class_direct(const uint32_t* sched, int begin, int end, const uint8_t* in,
-                                                  const GroupRef* dst, int64_t rec0, int lane) {
+__device__ __forceinline__ void move_class_direct(const uint32_t* __restrict__ sched, int begin, int end,
+                                                  const uint8_t* __restrict__ in, const GroupRef* dst, int64_t rec0,
+                                                  int lane) {
 #pragma unroll 4
   for (int t = begin + lane; t < end; t += 32) {
     const uint32_t p = sched[t];
-    const uint32_t s = p & 0xFFFFu, d = p >> 16;
+    const uint32_t d = p >> 16;
     const GroupRef& g = dst[d >> 10];
     *reinterpret_cast<V*>(const_cast<uint8_t*>(g.ptr) + (rec0 + (int64_t)(d & 1023u)) * g.stride) =
-        s != 0xFFFFu ? *reinterpret_cast<const V*>(in + s) : V(0);
+        *reinterpret_cast<const V*>(in + (p & 0xFFFFu));
   }
 }
 

@@ -391,6 +391,7 @@ static int settle_plan(const adha_cost_table* costs, const adha_plan_opts* opts,
   }
   plan->model_ns = 0;
   if (costs) {
+    if (int rc = check_costs(costs)) return rc;
     int prev = L;
     for (int k = 0; k < n_sec;) {
       const int l = plan->layout_of_section[k], m = plan->window_len[k];
@@ -433,6 +434,41 @@ int adha_run_program(const adha_schema* schema, int64_t n, const adha_layout* in
     for (int g = 0; g < in.n_groups; ++g)
       if (!in_ptrs[g] || reinterpret_cast<uintptr_t>(in_ptrs[g]) % 16)
         return fail(ADHA_EINVAL, "input buffer %d is NULL or not 16-byte aligned", g);
+  }
+  // every section must be valid in its layout, and the workspace must hold every group the plan
+  // places there, before anything is launched: a dry run of the placements below
+  {
+    Arena dry;
+    dry.base = static_cast<uint8_t*>(workspace);
+    dry.size = workspace ? ws_bytes : 0;
+    Layout c = in;
+    std::vector<void*> cp(in.n_groups, nullptr);
+    for (int g = 0; g < in.n_groups; ++g) cp[g] = in_ptrs ? in_ptrs[g] : nullptr;
+    for (int k = 0; k < n_sec; k += plan->window_len[k]) {
+      const Layout& D = cand[plan->layout_of_section[k]];
+      if (!same_layout(c, D)) {
+        std::vector<void*> dp(D.n_groups, nullptr);
+        std::vector<bool> kept(c.n_groups, false);
+        for (int g = 0; g < D.n_groups; ++g) {
+          for (int j = 0; j < c.n_groups; ++j)
+            if (same_group(D, g, c, j)) {
+              dp[g] = cp[j];
+              kept[j] = true;
+            }
+          if (!dp[g] && !(dp[g] = dry.alloc((size_t)n * D.stride[g])))
+            return fail(ADHA_ENOMEM, "program workspace of %zu bytes is too small for the plan", ws_bytes);
+        }
+        for (int j = 0; j < c.n_groups; ++j)
+          if (!kept[j] && cp[j] && dry.owns(cp[j])) dry.release(cp[j]);
+        c = D;
+        cp = dp;
+      }
+      const int m = plan->window_len[k];
+      if (m > 1 && !fusable_run(D, &sections[k], m))
+        return fail(ADHA_EINVAL, "sections %d..%d may not run fused", k, k + m - 1);
+      for (int j = 0; j < m; ++j)
+        if (int rc = check_section_layout(D, &sections[k + j], n)) return rc;
+    }
   }
   Arena arena;
   arena.base = static_cast<uint8_t*>(workspace);

@@ -130,3 +130,69 @@ def test_full_size_batched_workload_sampled(P):
             for g, (buf, st) in enumerate(zip(arr["dst_bufs"], dst_st)):
                 got = buf[i0 * st:(i0 + m) * st].cpu().numpy()
                 assert np.array_equal(got, want[g]), "array %d group %d records %d.." % (k, g, i0)
+
+
+def _wide_specs(seed, count):
+    """Arrays up to 32 fields of any dtype (records up to 256 bytes), so that short CTA regions
+    force shorter chunks."""
+    rng = np.random.default_rng(seed)
+    specs = []
+    for _ in range(count):
+        F = int(rng.integers(1, 33))
+        dtypes = [int(x) for x in rng.integers(0, 4, F)]
+        n = int(rng.choice([0, 1, 9, 31, 64, 257, 4099, 100003]))
+        specs.append((n, dtypes, random_layout(rng, F), random_layout(rng, F)))
+    return specs
+
+
+@pytest.mark.parametrize("ctas", [1, 2, 3, 4])
+def test_batched_forced_ctas_per_sm(P, ctas):
+    """Every CTA count (and so every warp-region size, with chunks shortened to fit) gives the
+    oracle's bytes, on wide mixed-dtype records with ragged tails."""
+    arrays = _arrays(P, _wide_specs(20 + ctas, 24), 4)
+    b = P.Batched(arrays, ctas=ctas)
+    k, region, units = b.info
+    assert k == ctas and region > 0
+    b.upload()
+    b.launch()
+    _check(arrays)
+
+
+def test_one_call_batched_remap_matches_oracle(P):
+    """adha_remap_batched (plan + descriptors into the caller's workspace + launch in one call) on
+    uneven mixed-dtype arrays, twice in a row on one workspace, against the oracle."""
+    from paper_1407_4859_gb300._lib import AdhaError, ADHA_ENOMEM
+    batches = [_arrays(P, _wide_specs(seed, 30), seed) for seed in (31, 32)]
+    needs = [P.adha_workspace_bytes(arrays) for arrays in batches]
+    ws = torch.empty(max(needs), dtype=torch.uint8, device="cuda")
+    with pytest.raises(AdhaError) as e:   # too small: rejected before anything is enqueued
+        P.adha_remap_batched(batches[0], ws[: needs[0] - 256])
+    assert e.value.code == ADHA_ENOMEM
+    _check_untouched(batches[0])
+    for arrays in batches:
+        P.adha_remap_batched(arrays, ws)
+        _check(arrays)
+
+
+def _check_untouched(arrays):
+    torch.cuda.synchronize()
+    for a in arrays:
+        for d in a["dst_bufs"]:
+            assert bool((d == 0xAB).all())
+
+
+def test_one_call_batched_remap_rejects_capture(P):
+    """The one-call entry point copies its descriptors from a host buffer it frees on return, so a
+    capturing stream is refused (nothing is recorded; the capture stays valid)."""
+    from paper_1407_4859_gb300._lib import AdhaError, ADHA_EINVAL
+    arrays = _arrays(P, _wide_specs(40, 4), 40)
+    ws = torch.empty(P.adha_workspace_bytes(arrays), dtype=torch.uint8, device="cuda")
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            with pytest.raises(AdhaError) as e:
+                P.adha_remap_batched(arrays, ws, stream=side)
+    assert e.value.code == ADHA_EINVAL and "captured" in str(e.value)
+    _check_untouched(arrays)
