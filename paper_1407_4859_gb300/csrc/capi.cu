@@ -562,6 +562,12 @@ void fill_secop(const Layout& L, const adha_section* s, SecOp* o) {
   }
   o->rd_off[4] = (int8_t)nr;
   o->wr_off[4] = (int8_t)nw;
+  for (int k = 0; k < kMaxFields; ++k) o->rd_s0[k] = o->wr_s0[k] = -1;
+}
+
+void fill_secop_offsets(SecOp* o, const FieldRef* f) {
+  for (int j = 0; j < o->rd_off[4]; ++j) o->rd_s0[j] = (int16_t)f[o->rd[j]].s0;
+  for (int j = 0; j < o->wr_off[4]; ++j) o->wr_s0[j] = (int16_t)f[o->wr[j]].s0;
 }
 
 static int check_section(const Layout& L, const adha_section* s, int64_t n, bool has_save) {
@@ -714,6 +720,7 @@ static int plan_section(const Layout& L, void* const* ptrs, const adha_section* 
     R /= 2;
   }
   fill_secop(L, s, &a.s);
+  fill_secop_offsets(&a.s, a.f);
   tanh_coefficients(a.tanh_p, a.tanh_q);
   a.perm = s->perm;
   a.save = static_cast<uint8_t*>(save);
@@ -894,8 +901,8 @@ static int plan_fused(const Layout& L, void* const* ptrs, const adha_section* s,
   // for two CTAs per SM (the vector mapping needs 64 or more), else about 4 KB of records
   int R = 32;
   if (tuned_R) R = std::max(32, std::min(tuned_R, 128));
-  else if (one_field && (size_t)kWarps * 2 * 128 * rec <= (size_t)kSmemLimit / 2 - 4096) R = 128;
-  else if (one_field && (size_t)kWarps * 2 * 64 * rec <= (size_t)kSmemLimit / 2 - 4096) R = 64;
+  else if (one_field && (size_t)kWarps * 2 * 128 * rec <= (size_t)kSmemLimit / 2 - 8192) R = 128;
+  else if (one_field && (size_t)kWarps * 2 * 64 * rec <= (size_t)kSmemLimit / 2 - 8192) R = 64;
   else R = rec > 0 ? pick_chunk(rec, 4096, 128) : 128;
   if (R != 32 && R != 64 && R != 128) R = R < 64 ? 32 : 64;
   for (;;) {
@@ -940,13 +947,17 @@ static int plan_fused(const Layout& L, void* const* ptrs, const adha_section* s,
     a.in_bytes = off;
     a.vec = vec ? 1 : 0;
     a.buffers = tuned_buffers == 1 || tuned_buffers == 2 ? tuned_buffers : kFusedBuffers;
+    a.n_sec = m;
     plan->smem = fused_smem_bytes(a);
     if (plan->smem <= (size_t)kSmemLimit) break;
     if (R <= 32) return fail(ADHA_EINVAL, "the fused run's records are too wide for a 32-record chunk");
     R /= 2;
   }
   a.n_sec = m;
-  for (int k = 0; k < m; ++k) fill_secop(L, &s[k], &a.sec[k]);
+  for (int k = 0; k < m; ++k) {
+    fill_secop(L, &s[k], &a.sec[k]);
+    fill_secop_offsets(&a.sec[k], a.f);
+  }
   tanh_coefficients(a.tanh_p, a.tanh_q);
   a.perm = perm;
   int blocks = 0;

@@ -25,8 +25,12 @@ namespace adha {
 // the memory system does, while shared-memory loads of one address broadcast to the warp.
 constexpr int kSliceTable = (16 * (kMaxGroups + 1) + 15) / 16 * 16;
 constexpr int kFieldTable = (int)sizeof(FieldRef) * kMaxFields;
-constexpr int kFusedTable = kSliceTable + kFieldTable + (int)sizeof(SecOp) * kMaxFused;
 static_assert(sizeof(FieldRef) % 8 == 0 && sizeof(SecOp) % 4 == 0, "tables are copied in whole words");
+
+// Bytes of the tables for a run of n_sec sections (the chunk buffers follow, 16-byte aligned).
+__host__ __device__ constexpr int fused_table_bytes(int n_sec) {
+  return kSliceTable + kFieldTable + ((int)sizeof(SecOp) * n_sec + 15) / 16 * 16;
+}
 
 
 // One section on the M records of each lane of a staged chunk (r = lane + 32m), writes into the
@@ -95,7 +99,7 @@ __global__ void __launch_bounds__(kThreads) fused_kernel(const __grid_constant__
   int* send = reinterpret_cast<int*>(smem + 8 * (kMaxGroups + 1));
   int* wback = send + (kMaxGroups + 1);
   const int nb = a.buffers;   // 2: the next chunk is staged while one is computed; 1: one buffer
-  uint8_t* buf0 = smem + kFusedTable + (size_t)warp * nb * a.in_bytes;
+  uint8_t* buf0 = smem + fused_table_bytes(a.n_sec) + (size_t)warp * nb * a.in_bytes;
   uint8_t* buf1 = buf0 + (nb - 1) * a.in_bytes;
   constexpr int R = 32 * M;
   for (int k = tid; k < n_slices; k += kThreads) {
@@ -174,7 +178,9 @@ __global__ void __launch_bounds__(kThreads) fused_kernel(const __grid_constant__
   }
 }
 
-size_t fused_smem_bytes(const FusedArgs& a) { return kFusedTable + (size_t)kWarps * a.buffers * a.in_bytes; }
+size_t fused_smem_bytes(const FusedArgs& a) {
+  return fused_table_bytes(a.n_sec) + (size_t)kWarps * a.buffers * a.in_bytes;
+}
 
 template <int M, bool VEC>
 static int launch_m(const FusedArgs& a, int grid, size_t smem, void* stream) {

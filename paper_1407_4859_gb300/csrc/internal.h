@@ -112,6 +112,8 @@ struct SecOp {
   int8_t rd_off[5], wr_off[5];
   int8_t rd[kMaxFields];
   int8_t wr[kMaxFields];
+  int16_t rd_s0[kMaxFields];   // chunk-buffer offset (FieldRef::s0) of each listed field, -1 if not staged
+  int16_t wr_s0[kMaxFields];
 };
 
 struct SectionArgs {
@@ -178,6 +180,8 @@ bool fusable_run(const Layout& L, const adha_section* s, int m);
 // ADHA_EINVAL (message set) unless section s may run on n records stored in L.
 int check_section_layout(const Layout& L, const adha_section* s, int64_t n);
 void fill_secop(const Layout& L, const adha_section* s, SecOp* o);
+// Copies the chunk-buffer offsets of the section's listed fields from the field table.
+void fill_secop_offsets(SecOp* o, const FieldRef* f);
 adha_layout set_layout(const adha_layout_set* s, int l);
 // Remap launch arguments for one array (chunk_override 0 = the default chunk rule).
 int remap_plan_args(const Layout& S, const void* const* src_ptrs, const Layout& D, void* const* dst_ptrs, int64_t n,

@@ -12,31 +12,74 @@
 
 namespace adha {
 
-// Exact IEEE operations done with integer instructions where the result is plain, so that the
-// fp64 pipe (a small fraction of the fp32 rate on this GPU) only does the additions.
-// x * 0.5 rounded to nearest: for a normal x whose half is normal (biased exponent 2..2046) the
-// product is exact and is x with its exponent lowered by one; zeros, subnormals, the smallest
-// normals (whose half rounds), infinities and NaNs take the multiply.
-__device__ __forceinline__ double half_rn(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned e = (unsigned)(b >> 52) & 0x7FFu;
-  if (e >= 2u && e <= 2046u) return __longlong_as_double((long long)(b - (1ull << 52)));
-  return __dmul_rn(x, 0.5);
+// Exact IEEE operations done with integer instructions, so that the fp64 pipe (a small fraction
+// of the fp32 rate on this GPU) only does the additions.  Every case is a select between integer
+// results: a branch to the fp64 instruction for the rare inputs would be turned into a select by
+// the compiler too, and then the fp64 instruction would run for every value.
+
+// The common cases of the two below, taken for a whole warp when every lane's values qualify
+// (one vote per field): a normal double whose half is normal, and a normal float.
+__device__ __forceinline__ bool half_is_plain(double x) {
+  return ((unsigned)((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FFu) - 2u <= 2044u;
+}
+__device__ __forceinline__ double half_plain(double x) {
+  return __longlong_as_double(__double_as_longlong(x) - (1ll << 52));
+}
+// (a zero is plain too: a section that reads no fp32 field has t = 0 for one record in 256)
+__device__ __forceinline__ bool widen_is_plain(float t) {
+  const unsigned u = __float_as_uint(t);
+  return ((u >> 23) & 0xFFu) - 1u <= 253u || (u & 0x7FFFFFFFu) == 0u;
+}
+__device__ __forceinline__ double widen_plain(float t) {
+  const unsigned u = __float_as_uint(t);
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned long long normal = sign | ((unsigned long long)(((u >> 23) & 0xFFu) + 896u) << 52) |
+                                    ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)((u & 0x7FFFFFFFu) ? normal : sign));
 }
 
-// float -> double, exact: a normal float keeps its sign and significand (shifted into the wider
-// field) and gets its exponent rebiased from 127 to 1023; zeros, subnormals, infinities and NaNs
-// take the conversion instruction.
-__device__ __forceinline__ double widen(float t) {
-  const unsigned u = __float_as_uint(t);
-  const unsigned e = (u >> 23) & 0xFFu;
-  if (e >= 1u && e <= 254u) {
-    const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
-                                 ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
-    return __longlong_as_double((long long)b);
-  }
-  return (double)t;
+// x * 0.5 rounded to nearest.  A normal x whose half is normal (biased exponent 2..2046): the
+// exponent lowered by one.  Exponent 0 or 1 (zeros, subnormals, the smallest normals): the half is
+// subnormal, its significand the full significand q of x (with the implicit bit for exponent 1)
+// halved with ties to even (q odd is exactly a tie); a carry into the exponent field gives the
+// smallest normal, as it should.  Infinities and NaNs are returned unchanged.
+__device__ __forceinline__ double half_rn_int(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned e = (unsigned)(b >> 52) & 0x7FFu;
+  const unsigned long long q = (b & 0xFFFFFFFFFFFFFull) | (e ? (1ull << 52) : 0ull);
+  const unsigned long long h = (q >> 1) + (q & (q >> 1) & 1ull);
+  const unsigned long long small = (b & (1ull << 63)) | h;
+  const unsigned long long big = e == 0x7FFu ? b : b - (1ull << 52);
+  return __longlong_as_double((long long)(e <= 1u ? small : big));
 }
+
+// float -> double, exact.  Normal: sign and significand kept (the significand shifted into the
+// wider field), exponent rebiased from 127 to 1023.  Zero: the sign alone.  Subnormal m * 2^-149
+// (m < 2^23): normal in double, its leading bit p = 31 - clz(m) becomes the implicit one, exponent
+// p - 149.  Infinity: exponent all ones; NaN: its payload shifted likewise, made quiet.
+__device__ __forceinline__ double widen_int(float t) {
+  const unsigned u = __float_as_uint(t);
+  const unsigned e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned long long mm = (unsigned long long)m << 29;
+  const unsigned long long normal = sign | ((unsigned long long)(e + 896u) << 52) | mm;
+  const unsigned long long special = sign | (0x7FFull << 52) | mm | (m ? (1ull << 51) : 0ull);
+  const int p = 31 - __clz((int)(m | 1u));
+  const unsigned long long sub = sign | ((unsigned long long)(p + 874) << 52) |
+                                 (((unsigned long long)m << (52 - p)) & 0xFFFFFFFFFFFFFull);
+  const unsigned long long zero_or_sub = m ? sub : sign;
+  return __longlong_as_double((long long)(e == 0u ? zero_or_sub : (e == 0xFFu ? special : normal)));
+}
+
+// The same two with the IEEE instruction for the rare inputs: the compiler turns the choice into
+// a select, so the fp64 multiply (or the conversion) runs for every value next to the integer
+// result.  That costs fp64-pipe time but few registers and instructions, the better trade in
+// the memory-bound single-section kernels; fused runs, which compute long per chunk, take the
+// integer forms above behind a warp vote.
+__device__ __forceinline__ double half_rn(double x) {
+  return half_is_plain(x) ? half_plain(x) : __dmul_rn(x, 0.5);
+}
+__device__ __forceinline__ double widen(float t) { return widen_is_plain(t) ? widen_plain(t) : (double)t; }
 
 struct StagedRec {      // record r of a staged chunk (global record i)
   const FieldRef* f;
@@ -215,31 +258,37 @@ __device__ __forceinline__ void mix_chunk_vec(const SecOp& so, const FieldRef* f
     s[m] = 0.0f;
     h[m] = 0u;
   }
+  // the lane's M records of a field of size b start at stage + s0 + lane*M*b
+#define RD_S0(j) (TO_STAGE ? (int)so.rd_s0[j] : fr[so.rd[j]].s0)
+#define WR_S0(j) (TO_STAGE ? (int)so.wr_s0[j] : fr[so.wr[j]].s0)
+#define b2 (stage + lane * M * 2)
+#define b4 (stage + lane * M * 4)
+#define b8 (stage + lane * M * 8)
 #pragma unroll 4
   for (int j = so.rd_off[ADHA_F32]; j < so.rd_off[ADHA_F32 + 1]; ++j) {
     float v[M];
-    ld_vec<float, M>(stage + fr[so.rd[j]].s0 + lane * M * 4, v);
+    ld_vec<float, M>(b4 + RD_S0(j), v);
 #pragma unroll
     for (int m = 0; m < M; ++m) s[m] = __fadd_rn(s[m], v[m]);
   }
 #pragma unroll 4
   for (int j = so.rd_off[ADHA_F64]; j < so.rd_off[ADHA_F64 + 1]; ++j) {
     unsigned long long v[M];
-    ld_vec<unsigned long long, M>(stage + fr[so.rd[j]].s0 + lane * M * 8, v);
+    ld_vec<unsigned long long, M>(b8 + RD_S0(j), v);
 #pragma unroll
     for (int m = 0; m < M; ++m) h[m] ^= (uint32_t)v[m] ^ (uint32_t)(v[m] >> 32);
   }
 #pragma unroll 4
   for (int j = so.rd_off[ADHA_I32]; j < so.rd_off[ADHA_I32 + 1]; ++j) {
     uint32_t v[M];
-    ld_vec<uint32_t, M>(stage + fr[so.rd[j]].s0 + lane * M * 4, v);
+    ld_vec<uint32_t, M>(b4 + RD_S0(j), v);
 #pragma unroll
     for (int m = 0; m < M; ++m) h[m] ^= v[m];
   }
 #pragma unroll 4
   for (int j = so.rd_off[ADHA_BF16]; j < so.rd_off[ADHA_BF16 + 1]; ++j) {
     uint16_t v[M];
-    ld_vec<uint16_t, M>(stage + fr[so.rd[j]].s0 + lane * M * 2, v);
+    ld_vec<uint16_t, M>(b2 + RD_S0(j), v);
 #pragma unroll
     for (int m = 0; m < M; ++m) h[m] ^= (uint32_t)v[m];
   }
@@ -253,45 +302,72 @@ __device__ __forceinline__ void mix_chunk_vec(const SecOp& so, const FieldRef* f
   const int64_t r0 = i0 + (int64_t)lane * M;
 #pragma unroll 4
   for (int j = so.wr_off[ADHA_F32]; j < so.wr_off[ADHA_F32 + 1]; ++j) {
-    const FieldRef& F = fr[so.wr[j]];
     float v[M];
-    ld_vec<float, M>(stage + F.s0 + lane * M * 4, v);
+    ld_vec<float, M>(b4 + WR_S0(j), v);
 #pragma unroll
     for (int m = 0; m < M; ++m) v[m] = __fadd_rn(__fmul_rn(v[m], 0.5f), t[m]);
-    st_vec<float, M>(TO_STAGE ? stage + F.s0 + lane * M * 4 : F.g + r0 * 4, v);
+    st_vec<float, M>(TO_STAGE ? b4 + WR_S0(j) : fr[so.wr[j]].g + r0 * 4, v);
   }
   if (so.wr_off[ADHA_F64 + 1] > so.wr_off[ADHA_F64]) {
     double td[M];
+    if constexpr (TO_STAGE) {   // fused run: no fp64 instruction but the additions (see half_rn_int)
+      bool plain = true;
 #pragma unroll
-    for (int m = 0; m < M; ++m) td[m] = widen(t[m]);
-  #pragma unroll 4
-  for (int j = so.wr_off[ADHA_F64]; j < so.wr_off[ADHA_F64 + 1]; ++j) {
-      const FieldRef& F = fr[so.wr[j]];
+      for (int m = 0; m < M; ++m) plain = plain && widen_is_plain(t[m]);
+      if (__all_sync(0xFFFFFFFFu, plain)) {
+#pragma unroll
+        for (int m = 0; m < M; ++m) td[m] = widen_plain(t[m]);
+      } else {
+#pragma unroll
+        for (int m = 0; m < M; ++m) td[m] = widen_int(t[m]);
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < M; ++m) td[m] = widen(t[m]);
+    }
+#pragma unroll 4
+    for (int j = so.wr_off[ADHA_F64]; j < so.wr_off[ADHA_F64 + 1]; ++j) {
       double v[M];
-      ld_vec<double, M>(stage + F.s0 + lane * M * 8, v);
+      ld_vec<double, M>(b8 + WR_S0(j), v);
+      if constexpr (TO_STAGE) {
+        bool ok = true;
 #pragma unroll
-      for (int m = 0; m < M; ++m) v[m] = __dadd_rn(half_rn(v[m]), td[m]);
-      st_vec<double, M>(TO_STAGE ? stage + F.s0 + lane * M * 8 : F.g + r0 * 8, v);
+        for (int m = 0; m < M; ++m) ok = ok && half_is_plain(v[m]);
+        if (__all_sync(0xFFFFFFFFu, ok)) {
+#pragma unroll
+          for (int m = 0; m < M; ++m) v[m] = __dadd_rn(half_plain(v[m]), td[m]);
+        } else {
+#pragma unroll
+          for (int m = 0; m < M; ++m) v[m] = __dadd_rn(half_rn_int(v[m]), td[m]);
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < M; ++m) v[m] = __dadd_rn(half_rn(v[m]), td[m]);
+      }
+      st_vec<double, M>(TO_STAGE ? b8 + WR_S0(j) : fr[so.wr[j]].g + r0 * 8, v);
     }
   }
 #pragma unroll 4
   for (int j = so.wr_off[ADHA_I32]; j < so.wr_off[ADHA_I32 + 1]; ++j) {
-    const FieldRef& F = fr[so.wr[j]];
     uint32_t v[M];
-    ld_vec<uint32_t, M>(stage + F.s0 + lane * M * 4, v);
+    ld_vec<uint32_t, M>(b4 + WR_S0(j), v);
 #pragma unroll
     for (int m = 0; m < M; ++m) v[m] ^= k[m];
-    st_vec<uint32_t, M>(TO_STAGE ? stage + F.s0 + lane * M * 4 : F.g + r0 * 4, v);
+    st_vec<uint32_t, M>(TO_STAGE ? b4 + WR_S0(j) : fr[so.wr[j]].g + r0 * 4, v);
   }
 #pragma unroll 4
   for (int j = so.wr_off[ADHA_BF16]; j < so.wr_off[ADHA_BF16 + 1]; ++j) {
-    const FieldRef& F = fr[so.wr[j]];
     uint16_t v[M];
-    ld_vec<uint16_t, M>(stage + F.s0 + lane * M * 2, v);
+    ld_vec<uint16_t, M>(b2 + WR_S0(j), v);
 #pragma unroll
     for (int m = 0; m < M; ++m) v[m] = (uint16_t)(v[m] ^ (uint16_t)(k[m] & 0xFFFFu));
-    st_vec<uint16_t, M>(TO_STAGE ? stage + F.s0 + lane * M * 2 : F.g + r0 * 2, v);
+    st_vec<uint16_t, M>(TO_STAGE ? b2 + WR_S0(j) : fr[so.wr[j]].g + r0 * 2, v);
   }
+#undef b2
+#undef b4
+#undef b8
+#undef RD_S0
+#undef WR_S0
 }
 
 // AXPB, MUL, TANH under the vector mapping (x, y, z each a one-field group): lane takes records
