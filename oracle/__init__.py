@@ -3,8 +3,10 @@
 Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may import
 this package.  It shares no code with the CUDA path and never imports it.
 
-  * adha_oracle.c  -- layouts, scalar remap, sections, project tanh, chain gradient
-                      (plain scalar C, every float operation rounded on its own).
+  * adha_oracle.c  -- layouts, scalar remap, sections (including the K-Means-shaped
+                      nearest-centroid assignment and fixed-point cluster sums), project
+                      tanh, chain gradient (plain scalar C, every float operation rounded
+                      on its own).
   * planner.py     -- affinity graph, greedy grouping (ODS), candidate set, and the
                       program layout choice (PDL) by dynamic programming and by
                       exhaustive enumeration, also with combine nodes (runs of
@@ -17,7 +19,7 @@ Heterogeneous Architectures", PACT 2014, Section 2 and Tables 2-4.
 """
 from .core import (  # noqa: F401
     build, group_layout, layout_info, remap, to_fields, from_fields, tanhf, tanh_coeffs, section,
-    chain_grad, aos, soa, canon,
+    chain_grad, aos, soa, canon, kmeans_assign, kmeans_reduce, kmeans_features,
 )
 from .planner import (  # noqa: F401
     affinity, ods, candidates, pdl_dp, pdl_exhaustive, program_cost, pdl_dp_fused, pdl_exhaustive_fused,

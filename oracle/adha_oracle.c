@@ -319,6 +319,72 @@ int oracle_section(int op, const int* a, const float* p, uint64_t R, uint64_t W,
   return 0;
 }
 
+/* ------------------------------------------- K-Means-shaped sections */
+
+/*
+ * The paper's second benchmark (Section 3, Table 1, Table 3) is K-Means: a
+ * data-parallel section over all features, then a section that reduces over
+ * all records.  Its two sections, as this build defines them (the paper gives
+ * no formulas):
+ *   features x_0..x_{d-1}: the fp32 fields feat[0..d) (ascending ids);
+ *   membership m: the int32 field mf; K clusters; centroid c[k][j] = cent[k*d + j].
+ *
+ * assign:  per record, D_k = sum over j ascending of (x_j - c[k][j])^2, starting
+ *          from +0, the subtraction, the square and the addition each rounded to
+ *          nearest in fp32; m = the smallest k whose D_k is smallest (scanning k
+ *          upwards, a later k wins only when strictly smaller).
+ */
+int oracle_kmeans_assign(int d, const int* feat, int mf, int K, const float* cent, void** fa, int64_t n) {
+  if (d < 1 || K < 1) return -1;
+  for (int64_t i = 0; i < n; ++i) {
+    int best = 0;
+    float best_d = 0.0f;
+    for (int k = 0; k < K; ++k) {
+      float D = 0.0f;
+      for (int j = 0; j < d; ++j) {
+        float diff = F32(feat[j])[i] - cent[k * d + j];
+        float sq = diff * diff;
+        D = D + sq;
+      }
+      if (k == 0 || D < best_d) {
+        best_d = D;
+        best = k;
+      }
+    }
+    I32(mf)[i] = best;
+  }
+  return 0;
+}
+
+/* Fixed-point value of a feature for the reduction: x * 2^23 rounded to the
+ * nearest integer, ties to even; 2^31 - 1 or -2^31 beyond the int32 range; 0 for
+ * NaN.  The synthetic features lie on the grid of 2^-23, where this is exact. */
+static int64_t fixq(float x) {
+  float y = x * 8388608.0f;
+  if (y != y) return 0;
+  if (y >= 2147483648.0f) return 2147483647;
+  if (y < -2147483648.0f) return -2147483648LL;
+  return (int64_t)nearbyintf(y);
+}
+
+/*
+ * reduce:  out[k*(d+1)] = the number of records with m = k, and
+ *          out[k*(d+1) + 1 + j] = the sum of fixq(x_j) over those records, for
+ *          0 <= k < K; records with m outside [0, K) are left out.  The sums are
+ *          integers, so they do not depend on the order of the records.
+ */
+int oracle_kmeans_reduce(int d, const int* feat, int mf, int K, void** fa, int64_t n, int64_t* out) {
+  if (d < 1 || K < 1) return -1;
+  for (int64_t k = 0; k < (int64_t)K * (d + 1); ++k) out[k] = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    int32_t m = I32(mf)[i];
+    if (m < 0 || m >= K) continue;
+    out[(int64_t)m * (d + 1)] += 1;
+    for (int j = 0; j < d; ++j) out[(int64_t)m * (d + 1) + 1 + j] += fixq(F32(feat[j])[i]);
+  }
+  return 0;
+}
+
 /* ------------------------------------------------------- differentiation */
 
 /*

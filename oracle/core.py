@@ -15,7 +15,7 @@ _lib = None
 SIZE = {0: 4, 1: 8, 2: 4, 3: 2}
 NP = {0: np.float32, 1: np.float64, 2: np.int32, 3: np.uint16}
 OPS = dict(madd3=1, xorshift=2, add=3, mix=4, drift=5, bin=6, ke=7, flags=8, gather=9, kick=10,
-           axpb=11, mul=12, tanh=13)
+           axpb=11, mul=12, tanh=13, assign=14, reduce=15)
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -47,6 +47,8 @@ def _get():
             lib.oracle_tanh_coeffs.argtypes = [_P, _P]
             lib.oracle_section.argtypes = [_I, _P, _P, ctypes.c_uint64, ctypes.c_uint64, _I, _P, _P, _I64, _P]
             lib.oracle_chain_grad.argtypes = [_I, _P, _P, _P, _I, _P, _P, _P, _I64]
+            lib.oracle_kmeans_assign.argtypes = [_I, _P, _I, _I, _P, _P, _I64]
+            lib.oracle_kmeans_reduce.argtypes = [_I, _P, _I, _I, _P, _I64, _P]
             _lib = lib
     return _lib
 
@@ -150,8 +152,42 @@ def _mask(s):
     return m
 
 
+def kmeans_features(sec, dtypes):
+    """(feature field ids ascending, membership field, K) of an assign or reduce section: the
+    features are its fp32 read fields; args = (membership field, K)."""
+    feats = sorted(f for f in sec.read if dtypes[f] == 0)
+    return feats, int(sec.args[0]), int(sec.args[1])
+
+
+def kmeans_assign(sec, dtypes, fields):
+    """The assign section in place (membership field written); centroids from sec.table, K x d."""
+    feats, mf, K = kmeans_features(sec, dtypes)
+    n = fields[0].shape[0]
+    cent = np.ascontiguousarray(np.asarray(sec.table, dtype=np.float32))
+    assert cent.size == K * len(feats)
+    rc = _get().oracle_kmeans_assign(len(feats), _i32(feats).ctypes.data, mf, K, cent.ctypes.data, _ptrs(fields), n)
+    if rc != 0:
+        raise ValueError("bad assign section")
+
+
+def kmeans_reduce(sec, dtypes, fields):
+    """The reduce section: int64 array of K rows [count, fixed-point sum of each feature]."""
+    feats, mf, K = kmeans_features(sec, dtypes)
+    n = fields[0].shape[0]
+    out = np.zeros((K, len(feats) + 1), dtype=np.int64)
+    rc = _get().oracle_kmeans_reduce(len(feats), _i32(feats).ctypes.data, mf, K, _ptrs(fields), n, out.ctypes.data)
+    if rc != 0:
+        raise ValueError("bad reduce section")
+    return out
+
+
 def section(sec, dtypes, fields, perm=None):
-    """Run one section (a synth.Section) in place on field arrays (list of numpy arrays)."""
+    """Run one section (a synth.Section) in place on field arrays (list of numpy arrays); a reduce
+    section returns its sums (kmeans_reduce) and changes no field."""
+    if sec.op == "assign":
+        return kmeans_assign(sec, dtypes, fields)
+    if sec.op == "reduce":
+        return kmeans_reduce(sec, dtypes, fields)
     n = fields[0].shape[0]
     args = _i32(list(sec.args) + [0] * (8 - len(sec.args)))
     par = np.ascontiguousarray(np.asarray(list(sec.params) + [0.0] * (4 - len(sec.params)), dtype=np.float32))

@@ -20,7 +20,7 @@ DTYPE_NAME = {F32: "f32", F64: "f64", I32: "i32", BF16: "bf16"}
 
 # Section op names; the numeric codes are the library's adha_op values.
 OPS = dict(madd3=1, xorshift=2, add=3, mix=4, drift=5, bin=6, ke=7, flags=8, gather=9, kick=10,
-           axpb=11, mul=12, tanh=13)
+           axpb=11, mul=12, tanh=13, assign=14, reduce=15)
 
 DT = 2.0 ** -7           # time step of the particle sections (a power of two: dt*v is exact)
 
@@ -40,6 +40,7 @@ class Section:
     write: frozenset = frozenset()
     read_at_perm: frozenset = frozenset()
     params: Tuple[float, ...] = ()
+    table: Tuple[float, ...] = ()        # constants beyond params (assign: K x d centroids)
 
     @property
     def touched(self):
@@ -166,6 +167,43 @@ def config5(n=1 << 26, n_sections=64):
     return Workload("config5_differentiable_n%d" % n, n, flds, seed, secs, loss_weights=c)
 
 
+def kmeans(n=8388608, n_features=32, k=5, seed=6):
+    """K-Means-shaped program (the paper's second benchmark, Table 1: 8388608 inputs, 32 fields,
+    2 sections): 32 fp32 features U[-1,1) and an int32 membership field (zero at start);
+    section 1 assigns every record to its nearest of k seeded centroids (U[-1,1) fp32),
+    section 2 reduces every feature into per-cluster fixed-point sums and counts."""
+    flds = [Field("x%d" % j, F32, "F32_PM1") for j in range(n_features)] + [Field("member", I32, "ZERO32")]
+    M = n_features
+    feats = frozenset(range(n_features))
+    kc = gen.key(seed, 5000)
+    cent = tuple(float(np.float32(2.0 * gen.unit(kc, i) - 1.0)) for i in range(k * n_features))
+    assign = Section("assign", (M, k), feats, _fs(M), table=cent)
+    reduce = Section("reduce", (M, k), feats | _fs(M), frozenset())
+    return Workload("kmeans_n%d_f%d_k%d" % (n, n_features, k), n, flds, seed, [assign, reduce])
+
+
+def medical(n=256 ** 3, seed=7):
+    """Medical-image-registration-shaped program (the paper's first benchmark, Table 1 and Table 2:
+    a 256^3 volume, 7 sections over the fields V1..V3, U1..U3, S, T, interpT).  Sections 1-3 move
+    the vector fields together (a gather of T and U at a displaced record, a kick by S, a drift of
+    U by V), sections 4-7 are elementwise updates of the scalar fields.  Values: V N(0,1), U U[0,1),
+    S, T and interpT U[-1,1); the displaced record is a seeded random permutation."""
+    flds = [Field("V1", F32, "F32_NORMAL"), Field("V2", F32, "F32_NORMAL"), Field("V3", F32, "F32_NORMAL"),
+            Field("U1", F32, "F32_01"), Field("U2", F32, "F32_01"), Field("U3", F32, "F32_01"),
+            Field("S", F32, "F32_PM1"), Field("T", F32, "F32_PM1"), Field("interpT", F32, "F32_PM1")]
+    V1, V2, V3, U1, U2, U3, S, T, IT = range(9)
+    gather = Section("gather", (V1, V2, V3, U1, U2, U3, T), _fs(V1, V2, V3), _fs(V1, V2, V3),
+                     _fs(U1, U2, U3, T), params=(DT,))
+    kick = Section("kick", (V1, V2, V3, S), _fs(V1, V2, V3, S), _fs(V1, V2, V3), params=(DT, 0.25, -0.125, 0.0625))
+    drift = Section("drift", (U1, U2, U3, V1, V2, V3), _fs(U1, U2, U3, V1, V2, V3), _fs(U1, U2, U3), params=(DT,))
+    interp = Section("axpb", (T, IT), _fs(T), _fs(IT), params=(0.75, 0.125))
+    scale = Section("mul", (T, IT, S), _fs(T, IT), _fs(S))
+    update = Section("madd3", (U1, V1, T), _fs(U1, V1, T), _fs(T))
+    squash = Section("tanh", (S, IT), _fs(S), _fs(IT))
+    secs = [gather, kick, drift, interp, scale, update, squash]
+    return Workload("medical_n%d" % n, n, flds, seed, secs, has_perm=True)
+
+
 def config4_arrays(seed=3, n_arrays=256, n_scale=1.0):
     """256 record arrays: N log-uniform in [2^10, 2^22), F uniform in [4,32], dtypes uniform per field,
     source AoS in declared order, target a random set partition (shuffle, cut into groups of 1..8).
@@ -207,4 +245,5 @@ def tiny_workload(seed, F_max=8, n=37, n_sections=4):
 
 
 def workload(name, **kw):
-    return {"config1": config1, "config2": config2, "config3": config3, "config5": config5}[name](**kw)
+    return {"config1": config1, "config2": config2, "config3": config3, "config5": config5, "kmeans": kmeans,
+            "medical": medical}[name](**kw)
