@@ -102,11 +102,29 @@ typedef struct {
  *                               with P, Q its exact integer polynomials rounded
  *                               once to fp32 and evaluated by Horner's rule;
  *                               copysign(1, x) for |x| >= 9
+ * The two K-Means-shaped sections (the paper's second benchmark, Section 3):
+ * features x_0..x_{d-1} are the fp32 fields of read_mask in ascending id order,
+ * arg[0] = the int32 membership field m, arg[1] = K (1..8 clusters):
+ *   ASSIGN  (m, K; aux = K*d fp32 centroids c[k][j] = aux[k*d + j], device):
+ *                               D_k = sum over j ascending of (x_j - c[k][j])^2
+ *                               from +0 (fp32, each operation rounded);
+ *                               m = the smallest k with the smallest D_k.
+ *                               read_mask: features only (d >= 1); write_mask: m
+ *   REDUCE  (m, K; aux = K*(d+1) int64 outputs, device, 8-byte aligned):
+ *                               aux[k*(d+1)] = number of records with m = k,
+ *                               aux[k*(d+1) + 1 + j] = sum over them of q(x_j),
+ *                               q(x) = x * 2^23 rounded to the nearest integer
+ *                               (ties to even), 2^31 - 1 / -2^31 beyond int32,
+ *                               0 for NaN; records with m outside [0, K) are left
+ *                               out.  Integer sums: the result is the same in any
+ *                               record order.  aux is overwritten (the library
+ *                               zeroes it first).  read_mask: features and m
+ *                               (1 <= d <= 32); write_mask: none.  Not fusable.
  */
 typedef enum {
   ADHA_OP_MADD3 = 1, ADHA_OP_XORSHIFT = 2, ADHA_OP_ADD = 3, ADHA_OP_MIX = 4, ADHA_OP_DRIFT = 5,
   ADHA_OP_BIN = 6, ADHA_OP_KE = 7, ADHA_OP_FLAGS = 8, ADHA_OP_GATHER = 9, ADHA_OP_KICK = 10,
-  ADHA_OP_AXPB = 11, ADHA_OP_MUL = 12, ADHA_OP_TANH = 13
+  ADHA_OP_AXPB = 11, ADHA_OP_MUL = 12, ADHA_OP_TANH = 13, ADHA_OP_ASSIGN = 14, ADHA_OP_REDUCE = 15
 } adha_op;
 
 /*
@@ -117,6 +135,8 @@ typedef enum {
  * not use (they still shape the affinity graph and what a section loads).
  * perm: device pointer to n int32 record ids in [0,n) (GATHER only, else NULL);
  * fields read through perm must not be written by the same section.
+ * aux: device pointer to the op's table (ASSIGN: centroids, read) or result
+ * (REDUCE: sums, written); NULL for the other ops.
  */
 typedef struct {
   int32_t op;
@@ -126,6 +146,7 @@ typedef struct {
   uint64_t write_mask;
   uint64_t read_at_perm_mask;
   const int32_t* perm;
+  void* aux;
 } adha_section;
 
 /* ---------------------------------------------------------------- layouts */
@@ -382,8 +403,8 @@ size_t adha_program_host_workspace_bytes(const adha_schema* schema, int64_t n, c
  * buffer sets), so copies in both directions and kernels overlap.  The plan is solved once (or taken as fixed) before any data
  * moves; the result is written in the plan's final layout (the last section's
  * candidate, or in_layout with opts->return_to_input), host_out[g] holding
- * n * stride(g) bytes.  Sections that read through a permutation need every
- * record: with one of those n_slices must be 1.  The workspace (device,
+ * n * stride(g) bytes.  Sections that read through a permutation or reduce over
+ * all records need every record: with one of those n_slices must be 1.  The workspace (device,
  * adha_program_host_workspace_bytes) must not be used by anything else until
  * the work is done.  Asynchronous with respect to `stream`: the pipelines wait
  * for work queued on `stream` before they start, and `stream` waits for them

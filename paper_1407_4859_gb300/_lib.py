@@ -8,7 +8,7 @@ LIB_PATH = os.path.join(HERE, "libadha.so")
 ADHA_OK, ADHA_EINVAL, ADHA_ENOMEM, ADHA_ECUDA, ADHA_ETIMEOUT, ADHA_ENOTIMPL = 0, -1, -2, -3, -4, -5
 CODES = {-1: "ADHA_EINVAL", -2: "ADHA_ENOMEM", -3: "ADHA_ECUDA", -4: "ADHA_ETIMEOUT", -5: "ADHA_ENOTIMPL"}
 OPS = dict(madd3=1, xorshift=2, add=3, mix=4, drift=5, bin=6, ke=7, flags=8, gather=9, kick=10,
-           axpb=11, mul=12, tanh=13)
+           axpb=11, mul=12, tanh=13, assign=14, reduce=15)
 
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
@@ -26,7 +26,7 @@ class adha_layout(ctypes.Structure):
 
 class adha_section(ctypes.Structure):
     _fields_ = [("op", _I32), ("arg", _I32 * 8), ("fparam", ctypes.c_float * 4), ("read_mask", ctypes.c_uint64),
-                ("write_mask", ctypes.c_uint64), ("read_at_perm_mask", ctypes.c_uint64), ("perm", _P)]
+                ("write_mask", ctypes.c_uint64), ("read_at_perm_mask", ctypes.c_uint64), ("perm", _P), ("aux", _P)]
 
 
 class adha_plan_opts(ctypes.Structure):

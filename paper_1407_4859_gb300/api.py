@@ -93,8 +93,9 @@ def alloc_layout(schema, layout, n, device="cuda"):
     return [torch.empty(n * s, dtype=torch.uint8, device=device) for s in strides]
 
 
-def c_section(sec, perm=None):
-    """adha_section from a synth.Section (perm: device int32 tensor for gather sections)."""
+def c_section(sec, perm=None, aux=None):
+    """adha_section from a synth.Section (perm: device int32 tensor for gather sections; aux: device
+    tensor with an assign section's centroids or for a reduce section's sums)."""
     s = adha_section()
     s.op = OPS[sec.op]
     for k, a in enumerate(sec.args):
@@ -105,6 +106,7 @@ def c_section(sec, perm=None):
     s.write_mask = sum(1 << f for f in sec.write)
     s.read_at_perm_mask = sum(1 << f for f in sec.read_at_perm)
     s.perm = perm.data_ptr() if (perm is not None and sec.op == "gather") else None
+    s.aux = aux.data_ptr() if aux is not None else None
     return s
 
 
@@ -192,14 +194,28 @@ class PlanOpts:
 
 
 class Sections:
-    """A contiguous adha_section array (keeps the perm tensors it points to alive)."""
+    """A contiguous adha_section array (keeps the tensors it points to alive).  An assign section's
+    centroids (its synth table) are uploaded to the device; a reduce section gets an int64 device
+    tensor of K rows x (features + 1) for its result, in self.outputs[k] (unless aux[k] is given)."""
 
-    def __init__(self, secs, perm=None):
+    def __init__(self, secs, perm=None, aux=None):
         self.src = list(secs)
         self.perm = perm
+        self.aux = dict(aux or {})
+        self.outputs = {}
         self.arr = (adha_section * len(self.src))()
         for k, s in enumerate(self.src):
-            self.arr[k] = c_section(s, perm) if not isinstance(s, adha_section) else s
+            if isinstance(s, adha_section):
+                self.arr[k] = s
+                continue
+            if k not in self.aux and torch.cuda.is_available():
+                if s.op == "assign":
+                    self.aux[k] = torch.tensor(s.table, dtype=torch.float32, device="cuda")
+                elif s.op == "reduce":
+                    self.aux[k] = torch.zeros((int(s.args[1]), len(s.read)), dtype=torch.int64, device="cuda")
+            if s.op == "reduce" and k in self.aux:
+                self.outputs[k] = self.aux[k]
+            self.arr[k] = c_section(s, perm, self.aux.get(k))
 
     def __len__(self):
         return len(self.src)

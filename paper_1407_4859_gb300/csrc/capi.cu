@@ -563,6 +563,7 @@ void fill_secop(const Layout& L, const adha_section* s, SecOp* o) {
   o->rd_off[4] = (int8_t)nr;
   o->wr_off[4] = (int8_t)nw;
   for (int k = 0; k < kMaxFields; ++k) o->rd_s0[k] = o->wr_s0[k] = -1;
+  o->aux = s->aux;
 }
 
 void fill_secop_offsets(SecOp* o, const FieldRef* f) {
@@ -581,6 +582,28 @@ static int check_section(const Layout& L, const adha_section* s, int64_t n, bool
     int dt[8];
     char role[8];   // 'r' read, 'w' written, 'b' both, 'p' read at perm
   };
+  if (s->op == ADHA_OP_ASSIGN || s->op == ADHA_OP_REDUCE) {
+    const bool assign = s->op == ADHA_OP_ASSIGN;
+    const int m = s->arg[0], K = s->arg[1];
+    if (m < 0 || m >= F || L.dtype[m] != ADHA_I32)
+      return fail(ADHA_EINVAL, "op %d: membership field %d must be an int32 field", s->op, m);
+    if (K < 1 || K > kMaxClusters) return fail(ADHA_EINVAL, "op %d: K = %d not in [1, %d]", s->op, K, kMaxClusters);
+    const uint64_t feats = s->read_mask & ~(1ull << m);
+    for (int f = 0; f < F; ++f)
+      if (has(feats, f) && L.dtype[f] != ADHA_F32) return fail(ADHA_EINVAL, "op %d: feature field %d is not fp32", s->op, f);
+    const int d = __builtin_popcountll(feats);
+    if (d < 1 || (!assign && d > kMaxReduceFeatures))
+      return fail(ADHA_EINVAL, "op %d: %d feature fields (1..%d)", s->op, d, assign ? F : kMaxReduceFeatures);
+    if (assign && (s->write_mask != (1ull << m) || has(s->read_mask, m)))
+      return fail(ADHA_EINVAL, "assign section: write_mask must be the membership field alone, which it does not read");
+    if (!assign && (s->write_mask || !has(s->read_mask, m)))
+      return fail(ADHA_EINVAL, "reduce section: reads the membership field and writes no field");
+    if (s->read_at_perm_mask) return fail(ADHA_EINVAL, "only gather sections read through perm");
+    if (n > 0 && (!s->aux || reinterpret_cast<uintptr_t>(s->aux) % (assign ? 4 : 8)))
+      return fail(ADHA_EINVAL, "op %d: aux is NULL or misaligned", s->op);
+    if (has_save) return fail(ADHA_EINVAL, "save is only defined for axpb, mul and tanh sections");
+    return 0;
+  }
   Need need{};
   switch (s->op) {
     case ADHA_OP_MADD3: need = {3, {ADHA_F32, ADHA_F32, ADHA_F32}, {'r', 'r', 'b'}}; break;
@@ -662,6 +685,7 @@ static int plan_section(const Layout& L, void* const* ptrs, const adha_section* 
   if (s->op == ADHA_OP_GATHER) rec += 4;
   int R = tuned_R ? std::max(32, std::min(tuned_R, 128)) : (rec > 0 ? pick_chunk(rec, 4096, 128) : 128);
   if (R != 32 && R != 64 && R != 128) R = R < 64 ? 32 : 64;   // 96 -> 64: the kernels exist for 32, 64, 128
+  fill_secop(L, s, &a.s);   // before the shared-memory size, which depends on the op
   for (;;) {
     a.n = n;
     a.R = R;
@@ -719,7 +743,6 @@ static int plan_section(const Layout& L, void* const* ptrs, const adha_section* 
     if (R <= 32) return fail(ADHA_EINVAL, "section records too wide for a 32-record chunk");
     R /= 2;
   }
-  fill_secop(L, s, &a.s);
   fill_secop_offsets(&a.s, a.f);
   tanh_coefficients(a.tanh_p, a.tanh_q);
   a.perm = s->perm;
@@ -811,6 +834,8 @@ static int check_fused(const Layout& L, const adha_section* s, int m, int64_t n)
   }
   if (written & at_perm)
     return fail(ADHA_EINVAL, "a section of the run writes a field that a gather of the run reads through perm");
+  for (int k = 0; k < m; ++k)
+    if (s[k].op == ADHA_OP_REDUCE) return fail(ADHA_EINVAL, "a reduce section does not run in a fused run");
   if (n > 0 && perm && reinterpret_cast<uintptr_t>(perm) % 16) return fail(ADHA_EINVAL, "perm is not 16-byte aligned");
   if (n > 0 && !perm && at_perm) return fail(ADHA_EINVAL, "gather without a permutation");
   return 0;

@@ -60,6 +60,7 @@ __device__ __forceinline__ void fused_section_chunk(const FusedArgs& a, const Fi
     ADHA_FUSED_OP(ADHA_OP_AXPB)
     ADHA_FUSED_OP(ADHA_OP_MUL)
     ADHA_FUSED_OP(ADHA_OP_TANH)
+    ADHA_FUSED_OP(ADHA_OP_ASSIGN)
 #undef ADHA_FUSED_OP
     default: break;
   }
@@ -85,6 +86,7 @@ __device__ __forceinline__ void fused_section_record(const FusedArgs& a, const F
     ADHA_FUSED_OP(ADHA_OP_AXPB)
     ADHA_FUSED_OP(ADHA_OP_MUL)
     ADHA_FUSED_OP(ADHA_OP_TANH)
+    ADHA_FUSED_OP(ADHA_OP_ASSIGN)
 #undef ADHA_FUSED_OP
     default: break;
   }

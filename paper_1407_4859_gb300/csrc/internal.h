@@ -114,7 +114,11 @@ struct SecOp {
   int8_t wr[kMaxFields];
   int16_t rd_s0[kMaxFields];   // chunk-buffer offset (FieldRef::s0) of each listed field, -1 if not staged
   int16_t wr_s0[kMaxFields];
+  const void* aux;             // ASSIGN: centroids; REDUCE: the int64 sums
 };
+
+constexpr int kMaxClusters = 8;   // K of the ASSIGN and REDUCE sections
+constexpr int kMaxReduceFeatures = 32;
 
 struct SectionArgs {
   int64_t n;

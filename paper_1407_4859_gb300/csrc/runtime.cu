@@ -600,8 +600,9 @@ int adha_run_program_host(const adha_schema* schema, int64_t n, const adha_layou
   if (!plan || !sections || n_sec < 1 || n_sec > ADHA_MAX_SECTIONS || n < 0 || n_slices < 1)
     return fail(ADHA_EINVAL, "bad host-program arguments");
   for (int k = 0; k < n_sec; ++k)
-    if (sections[k].read_at_perm_mask && n_slices > 1)
-      return fail(ADHA_EINVAL, "section %d reads through a permutation: it needs every record, use one slice", k);
+    if ((sections[k].read_at_perm_mask || sections[k].op == ADHA_OP_REDUCE) && n_slices > 1)
+      return fail(ADHA_EINVAL, "section %d reads through a permutation or reduces over all records: it needs every "
+                               "record, use one slice", k);
   const int L = (int)cand.size();
   // the plan (and with it the result's layout) is fixed before any data moves
   if (costs && (costs->n_sections != n_sec || costs->n_layouts != L)) return fail(ADHA_EINVAL, "cost table does not match");

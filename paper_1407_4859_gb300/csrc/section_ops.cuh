@@ -493,6 +493,31 @@ __device__ __forceinline__ void run_record(const SecOp& so, const FieldRef* fr, 
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax)
       rec.template st<float>(g[ax], __fadd_rn(rec.template ld<float>(g[ax]), __fmul_rn(c, so.par[1 + ax])));
+  } else if (OP == ADHA_OP_ASSIGN) {
+    // D_k summed over the features in ascending order, all K distances side by side
+    const int K = so.arg[1], j0 = so.rd_off[ADHA_F32], d = so.rd_off[ADHA_F32 + 1] - j0;
+    const float* cent = static_cast<const float*>(so.aux);
+    float D[kMaxClusters];
+#pragma unroll
+    for (int k = 0; k < kMaxClusters; ++k) D[k] = 0.0f;
+    for (int j = 0; j < d; ++j) {
+      const float x = rec.template ld<float>(so.rd[j0 + j]);
+#pragma unroll
+      for (int k = 0; k < kMaxClusters; ++k)
+        if (k < K) {
+          const float df = __fsub_rn(x, __ldg(cent + k * d + j));
+          D[k] = __fadd_rn(D[k], __fmul_rn(df, df));
+        }
+    }
+    int best = 0;
+    float bd = D[0];
+#pragma unroll
+    for (int k = 1; k < kMaxClusters; ++k)
+      if (k < K && D[k] < bd) {
+        bd = D[k];
+        best = k;
+      }
+    rec.template st<int32_t>(g[0], best);
   } else {   // AXPB, MUL, TANH: z = op(x[, y]); the old z goes to `save` when asked
     const int z = OP == ADHA_OP_MUL ? g[2] : g[1];
     if (save) reinterpret_cast<float*>(save)[i] = rec.template ld<float>(z);
@@ -502,6 +527,72 @@ __device__ __forceinline__ void run_record(const SecOp& so, const FieldRef* fr, 
     else if (OP == ADHA_OP_MUL) v = __fmul_rn(x, rec.template ld<float>(g[1]));
     else v = tanh_cf(x, tp, tq);
     rec.template st<float>(z, v);
+  }
+}
+
+// Fixed-point value of a REDUCE feature: x * 2^23 (exact) rounded to the nearest integer, ties to
+// even; 2^31 - 1 or -2^31 beyond the int32 range; 0 for NaN (the limits are tested explicitly, so
+// no hardware saturation rule is relied on).
+__device__ __forceinline__ long long fixq(float x) {
+  const float y = __fmul_rn(x, 8388608.0f);
+  if (y != y) return 0;
+  if (y >= 2147483648.0f) return 2147483647ll;
+  if (y < -2147483648.0f) return -2147483648ll;
+  return (long long)__float2int_rn(y);
+}
+
+// REDUCE over the R = 32*M records of a staged chunk.  Counts: lane = record, one ballot per
+// cluster.  Sums: lane j = feature j, its column of the warp's K x 32 accumulators (int64, shared
+// memory) updated record by record; a one-field feature slice is walked starting at the lane's
+// own record so that the lanes' loads fall on different banks.  Integer sums: any order gives
+// the same result.
+template <int M>
+__device__ __forceinline__ void reduce_chunk(const SecOp& so, const FieldRef* fr, const uint8_t* stage, int lane,
+                                             long long* acc, unsigned long long* cnt) {
+  constexpr int R = 32 * M;
+  const int K = so.arg[1];
+  const FieldRef& Fm = fr[so.arg[0]];
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const int mm = *reinterpret_cast<const int32_t*>(stage + Fm.s0 + (lane + 32 * m) * Fm.ss);
+#pragma unroll
+    for (int k = 0; k < kMaxClusters; ++k)
+      if (k < K) cnt[k] += (unsigned long long)__popc(__ballot_sync(0xFFFFFFFFu, mm == k));
+  }
+  const int j0 = so.rd_off[ADHA_F32], d = so.rd_off[ADHA_F32 + 1] - j0;
+  if (lane < d) {
+    const FieldRef& Fx = fr[so.rd[j0 + lane]];
+    const int sx = Fx.s0, ssx = Fx.ss, sm = Fm.s0, ssm = Fm.ss;
+    const int skew = ssx == 4 ? lane : 0;
+    long long* col = acc + lane;
+#pragma unroll 4
+    for (int q = 0; q < R; ++q) {
+      const int r = (q + skew) & (R - 1);
+      const int mm = *reinterpret_cast<const int32_t*>(stage + sm + r * ssm);
+      const long long v = fixq(*reinterpret_cast<const float*>(stage + sx + r * ssx));
+      if ((unsigned)mm < (unsigned)K) col[mm * 32] += v;
+    }
+  }
+}
+
+// REDUCE over records [t0, n) read from global memory (the ragged tail): lane j = feature j;
+// lane 0 also counts.
+__device__ __forceinline__ void reduce_tail(const SecOp& so, const FieldRef* fr, int64_t t0, int64_t n, int lane,
+                                            long long* acc, unsigned long long* cnt) {
+  const int K = so.arg[1];
+  const FieldRef& Fm = fr[so.arg[0]];
+  const int j0 = so.rd_off[ADHA_F32], d = so.rd_off[ADHA_F32 + 1] - j0;
+  for (int64_t i = t0; i < n; ++i) {
+    const int mm = *reinterpret_cast<const int32_t*>(Fm.g + i * Fm.gs);
+    if ((unsigned)mm >= (unsigned)K) continue;
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < kMaxClusters; ++k) cnt[k] += k == mm ? 1ull : 0ull;
+    }
+    if (lane < d) {
+      const FieldRef& Fx = fr[so.rd[j0 + lane]];
+      acc[mm * 32 + lane] += fixq(*reinterpret_cast<const float*>(Fx.g + i * Fx.gs));
+    }
   }
 }
 

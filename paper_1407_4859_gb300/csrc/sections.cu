@@ -32,6 +32,16 @@ __global__ void __launch_bounds__(kThreads) section_kernel(const __grid_constant
   uint8_t* buf0 = smem + kSectionTable + (size_t)warp * 2 * a.in_bytes;
   uint8_t* buf1 = buf0 + a.in_bytes;
   constexpr int R = 32 * M;
+  // REDUCE: the warp's K x 32 int64 sums after the chunk buffers, its counts in registers
+  long long* acc = nullptr;
+  unsigned long long cnt[OP == ADHA_OP_REDUCE ? kMaxClusters : 1];
+  if constexpr (OP == ADHA_OP_REDUCE) {
+    acc = reinterpret_cast<long long*>(smem + kSectionTable + (size_t)kWarps * 2 * a.in_bytes) +
+          (size_t)warp * kMaxClusters * 32;
+    for (int k = lane; k < kMaxClusters * 32; k += 32) acc[k] = 0;
+#pragma unroll
+    for (int k = 0; k < kMaxClusters; ++k) cnt[k] = 0;
+  }
   for (int k = tid; k < n_slices; k += kThreads) {
     sp[k] = a.load[k].ptr;
     send[k] = a.load[k].start + R * a.load[k].stride;
@@ -62,7 +72,9 @@ __global__ void __launch_bounds__(kThreads) section_kernel(const __grid_constant
     cp_async_wait<1>();
     __syncwarp();
     const int64_t i0 = c * R;
-    if (OP == ADHA_OP_MIX && VEC) {
+    if constexpr (OP == ADHA_OP_REDUCE) {
+      reduce_chunk<M>(a.s, a.f, cur, lane, acc, cnt);
+    } else if (OP == ADHA_OP_MIX && VEC) {
       mix_chunk_vec<M>(a.s, a.f, cur, i0, lane);
     } else if (VEC) {
       chain_chunk_vec<OP, M>(a.s, a.f, a.tanh_p, a.tanh_q, a.save, cur, i0, lane);
@@ -94,9 +106,23 @@ __global__ void __launch_bounds__(kThreads) section_kernel(const __grid_constant
 
   // ragged tail: the warp whose next chunk would be n_chunks
   const int64_t t0 = a.n_chunks * R;
-  if (c == a.n_chunks && t0 < a.n) {
-    for (int64_t i = t0 + lane; i < a.n; i += 32)
-      run_record<OP>(a.s, a.f, a.tanh_p, a.tanh_q, a.save, GlobalRec{a.f, i}, i, a.perm_slot >= 0 ? a.perm[i] : 0);
+  if constexpr (OP == ADHA_OP_REDUCE) {
+    if (c == a.n_chunks && t0 < a.n) reduce_tail(a.s, a.f, t0, a.n, lane, acc, cnt);
+    // every warp adds its sums and counts into the result (zeroed before the launch)
+    __syncwarp();
+    const int K = a.s.arg[1], d = a.s.rd_off[ADHA_F32 + 1] - a.s.rd_off[ADHA_F32];
+    unsigned long long* out = static_cast<unsigned long long*>(const_cast<void*>(a.s.aux));
+#pragma unroll
+    for (int k = 0; k < kMaxClusters; ++k)
+      if (k < K) {
+        if (lane < d) atomicAdd(out + (size_t)k * (d + 1) + 1 + lane, (unsigned long long)acc[k * 32 + lane]);
+        if (lane == 0) atomicAdd(out + (size_t)k * (d + 1), cnt[k]);
+      }
+  } else {
+    if (c == a.n_chunks && t0 < a.n) {
+      for (int64_t i = t0 + lane; i < a.n; i += 32)
+        run_record<OP>(a.s, a.f, a.tanh_p, a.tanh_q, a.save, GlobalRec{a.f, i}, i, a.perm_slot >= 0 ? a.perm[i] : 0);
+    }
   }
 }
 
@@ -159,12 +185,20 @@ __global__ void __launch_bounds__(kThreads) backward_kernel(const __grid_constan
   }
 }
 
-size_t section_smem_bytes(const SectionArgs& a) { return kSectionTable + (size_t)kWarps * 2 * a.in_bytes; }
+size_t section_smem_bytes(const SectionArgs& a) {
+  const size_t acc = a.s.op == ADHA_OP_REDUCE ? (size_t)kWarps * kMaxClusters * 32 * 8 : 0;
+  return kSectionTable + (size_t)kWarps * 2 * a.in_bytes + acc;
+}
 
 template <int OP, int M, bool VEC>
 static int launch_om(const SectionArgs& a, int grid, size_t smem, void* stream) {
   cudaError_t e = cudaFuncSetAttribute(section_kernel<OP, M, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(section)");
+  if (OP == ADHA_OP_REDUCE) {   // the sums are added into a zeroed result
+    const int K = a.s.arg[1], d = a.s.rd_off[ADHA_F32 + 1] - a.s.rd_off[ADHA_F32];
+    e = cudaMemsetAsync(const_cast<void*>(a.s.aux), 0, (size_t)K * (d + 1) * 8, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(reduce result)");
+  }
   section_kernel<OP, M, VEC><<<grid, kThreads, smem, (cudaStream_t)stream>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "section kernel launch");
@@ -196,7 +230,7 @@ static int occ_op(size_t smem, int* blocks) {
 #define ADHA_FOR_EACH_OP(X)                                                                              \
   X(ADHA_OP_MADD3) X(ADHA_OP_XORSHIFT) X(ADHA_OP_ADD) X(ADHA_OP_MIX) X(ADHA_OP_DRIFT) X(ADHA_OP_BIN)     \
   X(ADHA_OP_KE) X(ADHA_OP_FLAGS) X(ADHA_OP_GATHER) X(ADHA_OP_KICK) X(ADHA_OP_AXPB) X(ADHA_OP_MUL)        \
-  X(ADHA_OP_TANH)
+  X(ADHA_OP_TANH) X(ADHA_OP_ASSIGN) X(ADHA_OP_REDUCE)
 
 int launch_section(const SectionArgs& a, int grid, size_t smem, void* stream) {
   switch (a.s.op) {

@@ -1,0 +1,204 @@
+"""GPU parity of the paper-shaped programs: the K-Means-shaped sections (nearest-centroid assign,
+fixed-point per-cluster reduce) and whole K-Means- and Medical-shaped programs, bit-exact against
+the oracle in AoS, SoA and random groupings, ragged sizes, every chunk size, and at full size."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_util import to_device, from_device, assert_fields_equal, random_layout
+
+pytestmark = pytest.mark.gpu
+CAPS = [16, 32, 64, 128, 256, 0]
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_1407_4859_gb300 import build
+    build.build()
+    import paper_1407_4859_gb300 as P
+    return P
+
+
+def _layouts(F, seed):
+    rng = np.random.default_rng(seed)
+    return [oracle.aos(F), oracle.soa(F), random_layout(rng, F)]
+
+
+def _special_features(rng, n):
+    """Grid values mostly, plus values that exercise the fixed-point rounding and saturation."""
+    x = (rng.integers(-(1 << 23), 1 << 23, n) * 2.0 ** -23).astype(np.float32)
+    pool = np.array([np.nan, np.inf, -np.inf, 3e38, -3e38, 2.0 ** -24, 1.5 * 2.0 ** -23, 2.5 * 2.0 ** -23,
+                     256.0, -256.0, 1e-40], dtype=np.float32)
+    pick = rng.random(n) < 0.05
+    x[pick] = rng.choice(pool, int(pick.sum()))
+    return x
+
+
+@pytest.mark.parametrize("chunk", [0, 32, 64, 128])
+@pytest.mark.parametrize("n", [1, 31, 4099, 70001])
+def test_assign_and_reduce_sections(P, chunk, n):
+    wl = synth.kmeans(n=n, n_features=12, k=7)
+    d = 12
+    rng = np.random.default_rng(n + chunk)
+    base = oracle.initial_fields(wl)
+    base[d] = base[d].view(np.int32)
+    S = P.Schema(wl.dtypes)
+    assign, reduce = wl.sections
+    for groups in _layouts(wl.F, n):
+        # assign: membership bit-exact
+        fields = [a.copy() for a in base]
+        bufs = to_device(n, wl.dtypes, groups, fields)
+        secs = P.Sections([assign])
+        P.adha_tune_override(chunk)
+        try:
+            P.adha_run_section(S, n, P.Layout(groups), bufs, secs.arr[0])
+            torch.cuda.synchronize()
+        finally:
+            P.adha_tune_override(0)
+        want = [a.copy() for a in base]
+        oracle.section(assign, wl.dtypes, want)
+        assert_fields_equal(from_device(n, wl.dtypes, groups, bufs), want, "assign in %r" % (groups,))
+        # reduce: memberships anywhere in [-1, K], features with special values
+        fields = [_special_features(rng, n) for _ in range(d)] + [rng.integers(-1, 8, n).astype(np.int32)]
+        bufs = to_device(n, wl.dtypes, groups, fields)
+        rs = P.Sections([reduce])
+        P.adha_tune_override(chunk)
+        try:
+            P.adha_run_section(S, n, P.Layout(groups), bufs, rs.arr[0])
+            torch.cuda.synchronize()
+        finally:
+            P.adha_tune_override(0)
+        want = oracle.section(reduce, wl.dtypes, [a.copy() for a in fields])
+        assert np.array_equal(rs.outputs[0].cpu().numpy(), want), "reduce in %r" % (groups,)
+        # and the fields are untouched
+        assert_fields_equal(from_device(n, wl.dtypes, groups, bufs), fields, "reduce left the fields")
+
+
+def test_reduce_twice_overwrites(P):
+    """The result is the sums of the last run, not an accumulation across runs."""
+    wl = synth.kmeans(n=5000, n_features=4, k=3)
+    f = oracle.initial_fields(wl)
+    f[4] = (np.arange(5000) % 3).astype(np.int32)
+    S, L = P.Schema(wl.dtypes), P.Layout.soa(5)
+    bufs = to_device(5000, wl.dtypes, L.groups, f)
+    rs = P.Sections([wl.sections[1]])
+    for _ in range(2):
+        P.adha_run_section(S, 5000, L, bufs, rs.arr[0])
+    torch.cuda.synchronize()
+    assert np.array_equal(rs.outputs[0].cpu().numpy(), oracle.section(wl.sections[1], wl.dtypes, f))
+
+
+def test_assign_fused_with_elementwise_sections(P):
+    """assign inside a fused run (after sections that change the features) equals the oracle's
+    sections one after another."""
+    wl = synth.kmeans(n=20011, n_features=8, k=5)
+    fs = frozenset
+    pre = [synth.Section("axpb", (0, 1), fs({0}), fs({1}), params=(0.5, 0.25)),
+           synth.Section("mul", (2, 3, 4), fs({2, 3}), fs({4}))]
+    run = pre + [wl.sections[0]]
+    base = oracle.initial_fields(wl)
+    base[8] = base[8].view(np.int32)
+    S = P.Schema(wl.dtypes)
+    for groups in _layouts(wl.F, 5):
+        bufs = to_device(wl.n, wl.dtypes, groups, base)
+        P.adha_run_sections_fused(S, wl.n, P.Layout(groups), bufs, P.Sections(run))
+        torch.cuda.synchronize()
+        want = [a.copy() for a in base]
+        for s in run:
+            oracle.section(s, wl.dtypes, want)
+        assert_fields_equal(from_device(wl.n, wl.dtypes, groups, bufs), want, "fused in %r" % (groups,))
+
+
+def _program(P, wl, n_check=None):
+    """The workload through adha_run_program: ODS candidates, measured costs, PDL; returns
+    (final fields, reduce outputs, plan)."""
+    n = wl.n
+    S = P.Schema(wl.dtypes)
+    AOS = P.Layout.aos(wl.F)
+    fields = oracle.initial_fields(wl)
+    perm = wl.perm() if wl.has_perm else None
+    bufs = to_device(n, wl.dtypes, AOS.groups, fields)
+    dperm = torch.from_numpy(perm).cuda() if perm is not None else None
+    secs = P.Sections(wl.sections, dperm)
+    cand = P.adha_plan_sections(S, secs, P.PlanOpts(CAPS))
+    costs = P.adha_measure(S, n, AOS, bufs, secs, cand, reps=1)
+    ws = torch.empty(P.adha_program_workspace_bytes(S, n, AOS, cand), dtype=torch.uint8, device="cuda")
+    plan = P.adha_run_program(S, n, AOS, bufs, secs, cand, costs=costs, workspace=ws)
+    torch.cuda.synchronize()
+    lay, out = P.final_buffers(plan, S, n, cand, AOS)
+    got = from_device(n, wl.dtypes, lay.groups, out)
+    return got, {k: v.cpu().numpy() for k, v in secs.outputs.items()}, plan, fields, perm
+
+
+def test_kmeans_program_matches_oracle(P):
+    wl = synth.kmeans(n=(1 << 16) + 13)
+    got, outs, plan, fields, _ = _program(P, wl)
+    want = [a.copy() for a in fields]
+    want[32] = want[32].view(np.int32)
+    oracle.section(wl.sections[0], wl.dtypes, want)
+    red = oracle.section(wl.sections[1], wl.dtypes, want)
+    assert_fields_equal(got, want, "kmeans program")
+    assert np.array_equal(outs[1], red)
+
+
+def test_medical_program_matches_oracle(P):
+    wl = synth.medical(n=(1 << 16) + 7)
+    got, _, plan, fields, perm = _program(P, wl)
+    want = [a.copy() for a in fields]
+    oracle.run_program_fields(wl, want, perm)
+    assert_fields_equal(got, want, "medical program")
+
+
+def test_full_size_kmeans_sections(P):
+    """8388608 records of 32 features: the whole membership field and the reduce result against
+    the oracle over every record, in SoA (the plan's layout) and AoS."""
+    wl = synth.kmeans()
+    n = wl.n
+    base = oracle.initial_fields(wl)
+    base[32] = base[32].view(np.int32)
+    want = [a.copy() for a in base]
+    oracle.section(wl.sections[0], wl.dtypes, want)
+    red = oracle.section(wl.sections[1], wl.dtypes, want)
+    S = P.Schema(wl.dtypes)
+    for groups in (oracle.soa(33), oracle.aos(33)):
+        bufs = to_device(n, wl.dtypes, groups, base)
+        secs = P.Sections(wl.sections)
+        for k in range(2):
+            P.adha_run_section(S, n, P.Layout(groups), bufs, secs.arr[k])
+        torch.cuda.synchronize()
+        got = from_device(n, wl.dtypes, groups, bufs)
+        assert np.array_equal(got[32], want[32]), "membership in %s" % ("SoA" if len(groups) > 1 else "AoS")
+        assert np.array_equal(secs.outputs[1].cpu().numpy(), red)
+
+
+def test_full_size_medical_program_sampled(P):
+    """256^3 records through the program (ODS + measured PDL); 4096 sampled records against the
+    oracle's per-record evaluation (closed under the gather's permutation)."""
+    wl = synth.medical()
+    n = wl.n
+    S = P.Schema(wl.dtypes)
+    AOS = P.Layout.aos(wl.F)
+    perm = wl.perm()
+    fields = oracle.initial_fields(wl)
+    bufs = to_device(n, wl.dtypes, AOS.groups, fields)
+    del fields
+    dperm = torch.from_numpy(perm).cuda()
+    secs = P.Sections(wl.sections, dperm)
+    cand = P.adha_plan_sections(S, secs, P.PlanOpts(CAPS))
+    costs = P.adha_measure(S, n, AOS, bufs, secs, cand, reps=1)
+    ws = torch.empty(P.adha_program_workspace_bytes(S, n, AOS, cand), dtype=torch.uint8, device="cuda")
+    plan = P.adha_run_program(S, n, AOS, bufs, secs, cand, costs=costs, workspace=ws)
+    torch.cuda.synchronize()
+    lay, out = P.final_buffers(plan, S, n, cand, AOS)
+    rng = np.random.default_rng(9)
+    sample = np.unique(np.concatenate([[0, n - 1], rng.integers(0, n, 4094)]))
+    want = oracle.sample_program(wl, sample, perm)
+    strides, _, _ = oracle.layout_info(wl.dtypes, lay.groups)
+    rows = []
+    for o, st in zip(out, strides):
+        idx = torch.from_numpy((sample[:, None] * st + np.arange(st)[None, :]).reshape(-1)).cuda()
+        rows.append(o.view(-1)[idx].cpu().numpy())
+    got = oracle.to_fields(len(sample), wl.dtypes, lay.groups, rows)
+    assert_fields_equal(got, want, "medical sampled")

@@ -157,3 +157,49 @@ def test_bad_section_in_a_later_window_fails_before_launch(P):
         with pytest.raises(AdhaError) as e:
             P.adha_run_program(S, 64, P.Layout.aos(6), [4096], secs, cand, fixed=fixed, workspace=ws, stream=0)
         assert e.value.code == EINVAL and "dtype" in str(e.value)
+
+
+def test_kmeans_sections_validated_before_launch(P):
+    """The assign and reduce sections' rules (fp32 features, an int32 membership field, 1 <= K <= 8,
+    at most 32 features for reduce, reduce writes no field, aux present and aligned, reduce never
+    fused) are checked on the host."""
+    AdhaError, EINVAL, _ = _codes()
+    F = 6
+    dtypes = [0, 0, 0, 0, 2, 2]
+    S, L = P.Schema(dtypes), P.Layout.soa(F)
+    bufs = [4096 * (k + 1) for k in range(F)]
+    fs = frozenset
+    Sec = synth.Section
+    aux8 = 1 << 20
+    bad = [Sec("assign", (4, 3), fs({0, 1, 2}), fs({5})),            # writes a field other than m
+           Sec("assign", (0, 3), fs({1, 2}), fs({0})),               # membership not int32
+           Sec("assign", (4, 9), fs({0, 1}), fs({4})),               # K too large
+           Sec("assign", (4, 2), fs({0, 5}), fs({4})),               # an int32 feature
+           Sec("reduce", (4, 2), fs({0, 1}), fs()),                  # does not read m
+           Sec("reduce", (4, 2), fs({0, 1, 4}), fs({1})),            # writes a field
+           Sec("reduce", (4, 0), fs({0, 1, 4}), fs())]               # K = 0
+    for sec in bad:
+        c = P.c_section(sec)
+        c.aux = aux8
+        with pytest.raises(AdhaError) as e:
+            P.adha_run_section(S, 64, L, bufs, c, stream=0)
+        assert e.value.code == EINVAL, sec
+    ok = Sec("reduce", (4, 2), fs({0, 1, 4}), fs())
+    c = P.c_section(ok)                                               # aux NULL
+    with pytest.raises(AdhaError) as e:
+        P.adha_run_section(S, 64, L, bufs, c, stream=0)
+    assert e.value.code == EINVAL and "aux" in str(e.value)
+    c.aux = aux8 + 4                                                  # not 8-byte aligned
+    with pytest.raises(AdhaError) as e:
+        P.adha_run_section(S, 64, L, bufs, c, stream=0)
+    assert e.value.code == EINVAL and "aux" in str(e.value)
+    c.aux = aux8
+    with pytest.raises(AdhaError) as e:                               # never fused, even alone
+        P.adha_run_sections_fused(S, 64, L, bufs, P.Sections([c]), stream=0)
+    assert e.value.code == EINVAL and "fused" in str(e.value)
+    wide = P.Schema([0] * 33 + [2])
+    c = P.c_section(Sec("reduce", (33, 2), fs(range(34)), fs()))
+    c.aux = aux8
+    with pytest.raises(AdhaError) as e:                               # 33 features for reduce
+        P.adha_run_section(wide, 64, P.Layout.soa(34), [4096 * (k + 1) for k in range(34)], c, stream=0)
+    assert e.value.code == EINVAL
