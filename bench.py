@@ -1,7 +1,7 @@
 #!/usr/bin/env python3
 """Benchmark of the ADHA hot path on GB300: the layout-stress program (2^24 records of 16
 fields: 8 fp32, 4 fp64, 4 int32 = 80 B in AoS; 8 sections with Bernoulli(0.3) read/write sets
-plus one section over every field).
+plus one section over every field) is the headline line.
 
 One step = one pass of the path over one batch: candidate layouts by ODS (affinity graph +
 greedy grouping, host), PDL on the measured cost table (host), then the chosen chain of remap
@@ -10,15 +10,18 @@ before the timed region, like an autotuner cache.
 
 Prints one JSON line.  `value` is algorithmic GB/s of the program: the data bytes its sections
 must move (accessed fields only; no padding, no untouched fields) divided by the step's device
-time, so a plan pays for the remaps it adds in time.  Extra keys: program times under the ADHA layouts vs
-all-AoS, all-SoA and the best of a bounded exhaustive set, and under PDL with fused combine nodes;
-the roofline of the dominant kernel; the oracle timed on the host cores; the end-to-end number
-through the C ABI with host buffers.
+time, so a plan pays for the remaps it adds in time.  Extra keys: program times under the ADHA
+layouts vs all-AoS, all-SoA and the best of the exhaustive set (every {AoS,SoA} assignment, every
+uniform single-layout program and the 32 plans of lowest model cost), and under PDL with fused
+combine nodes; the roofline of the dominant kernel; the oracle timed on the host cores (all of
+them, and one thread); the end-to-end number through the C ABI with host buffers; the random
+gather probe's rate (the gather section's own roofline); and `workloads`, a measured line for
+each other program: particles (2^25 records with a gather), batched (256 arrays in one batched
+remap), differentiable (2^26 x 24 fp32, 64 sections forward + backward: the largest), kmeans
+(8388608 x 32 features, assign + reduce) and medical (256^3 x 9 fields, 7 sections).
 
---workload particles | batched | differentiable runs the other programs (the particle program with
-a gather, 256 arrays in one batched remap, the 64-section chain forward + backward).
---impl reference times the CPU oracle (the only reference this method has) on a bounded sample
-of the same workload and prints the same metric.
+--workload NAME prints that workload's line alone.  --impl reference times the CPU oracle (the
+only reference this method has) on a bounded sample of the headline workload.
 """
 import argparse
 import hashlib
@@ -36,6 +39,8 @@ if ROOT not in sys.path:
 CAPS = [16, 32, 64, 128, 256, 0]
 METRIC = "remap and section HBM GB/s vs ~8 TB/s; program time ADHA-layout vs AoS/SoA/exhaustive"
 FALLBACK_HBM_GBS = 6800.0
+PAPER_CONTEXT = "paper: up to 6.92x over manual (SoA) layouts, K-Means on Xeon X5660 + Tesla M2050, OpenCL"
+WORKLOADS = ["stress", "particles", "batched", "differentiable", "kmeans", "medical"]
 
 
 def log(*a):
@@ -117,6 +122,43 @@ def traffic_for(workload, kernel_key):
     return None if ent is None else ent.get("dram_bytes_per_launch")
 
 
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def top_plans(section_ns, remap_ns, k_best=32):
+    """The k_best layout sequences of lowest model cost (section costs + remap costs on the cost
+    table, input layout = index L), by a k-best dynamic program over the layered DAG."""
+    import numpy as np
+    sec = np.asarray(section_ns, dtype=np.float64)
+    rem = np.asarray(remap_ns, dtype=np.float64)
+    S, L = sec.shape
+    K = k_best
+    cost = np.full((L, K), np.inf)
+    cost[:, 0] = sec[S - 1]
+    backs = [None] * S
+    for k in range(S - 2, -1, -1):
+        flat = (rem[:L, :L, None] + cost[None, :, :]).reshape(L, L * K)
+        idx = np.argsort(flat, axis=1, kind="stable")[:, :K]
+        cost = np.take_along_axis(flat, idx, axis=1) + sec[k][:, None]
+        backs[k] = idx
+    start = (rem[L, :L, None] + cost).reshape(-1)
+    plans = []
+    for o in np.argsort(start, kind="stable")[:K]:
+        if not np.isfinite(start[o]):
+            break
+        l, r = divmod(int(o), K)
+        seq = [l]
+        for k in range(S - 1):
+            l, r = divmod(int(backs[k][l, r]), K)
+            seq.append(l)
+        plans.append((float(start[o]), seq))
+    return plans
+
+
 class Clocks:
     """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
 
@@ -151,14 +193,15 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-# ---------------------------------------------------------------------------------- reference arm
+# ---------------------------------------------------------------------------------- CPU oracle
 
 _AOS_CACHE = {}
 
 
-def oracle_program_seconds(wl, plan_layouts, n_sample):
+def oracle_program_seconds(wl, plan_layouts, n_sample, threads=1):
     """The oracle computing the same transformation on the first n_sample records: decode the
-    AoS input, run every section, encode the result in the plan's final layout."""
+    AoS input, run every section, encode the result in the plan's final layout (split over
+    `threads` host threads by record range; the per-record code is the same)."""
     import numpy as np
     import oracle
     small = wl.with_n(n_sample)
@@ -167,12 +210,33 @@ def oracle_program_seconds(wl, plan_layouts, n_sample):
         fields = oracle.initial_fields(small)
         _AOS_CACHE[key] = oracle.from_fields(n_sample, wl.dtypes, oracle.aos(wl.F), fields)
     aos = _AOS_CACHE[key]
+    perm = small.perm() if small.has_perm else None
     t0 = time.perf_counter()
-    f = oracle.to_fields(n_sample, wl.dtypes, oracle.aos(wl.F), aos)
-    f = [np.ascontiguousarray(a) for a in f]
-    oracle.run_program_fields(small, f, small.perm() if small.has_perm else None)
-    oracle.from_fields(n_sample, wl.dtypes, plan_layouts[-1], f)
+    soa = oracle.remap_threads(n_sample, wl.dtypes, oracle.aos(wl.F), aos, oracle.soa(wl.F), threads=threads)
+    f = [soa[k].view(oracle.core.NP[wl.dtypes[k]]) for k in range(wl.F)]
+    for s in small.sections:
+        oracle.section_threads(s, wl.dtypes, f, perm, threads=threads)
+    oracle.remap_threads(n_sample, wl.dtypes, oracle.soa(wl.F), [np.ascontiguousarray(a).view(np.uint8) for a in f],
+                         plan_layouts[-1], threads=threads)
     return time.perf_counter() - t0
+
+
+def cpu_baseline(wl, plan_layouts, n_sample, budget_s=10.0):
+    """The oracle on the first n_sample records, on every host core and on one, in GB/s of the
+    program's algorithmic bytes."""
+    cores = host_cores()
+    b = program_bytes(wl.with_n(n_sample))
+    out = {}
+    for threads in (cores, 1):
+        t_tot, reps = 0.0, 0
+        while reps < 3 and (reps == 0 or t_tot < budget_s):
+            t_tot += oracle_program_seconds(wl, plan_layouts, n_sample, threads)
+            reps += 1
+        out[threads] = (round(b * reps / t_tot / 1e9, 3), reps)
+    return {"value": out[cores][0], "unit": "GB/s", "cores": cores, "kind": "oracle", "threads_1": out[1][0],
+            "sample": "first %d of %d records x %d runs: AoS decode, %d sections, encode in the ADHA final layout; "
+                      "record ranges over %d host threads (threads_1: one thread)"
+                      % (n_sample, wl.n, out[cores][1], len(wl.sections), cores)}
 
 
 def run_reference(args):
@@ -181,128 +245,147 @@ def run_reference(args):
         return 0
     import synth
     wl = synth.config2()
-    n_sample = 1 << 18
+    n_sample = 1 << 20
+    cores = host_cores()
     aos = [list(range(wl.F))]
     layouts = [aos] * len(wl.sections)          # the oracle's own representation does not change layout
     small = wl.with_n(n_sample)
     bytes_per = program_bytes(small)
     for _ in range(args.warmup):
-        oracle_program_seconds(wl, layouts, n_sample)
-    secs = [oracle_program_seconds(wl, layouts, n_sample) for _ in range(args.steps)]
+        oracle_program_seconds(wl, layouts, n_sample, cores)
+    secs = [oracle_program_seconds(wl, layouts, n_sample, cores) for _ in range(args.steps)]
     total = sum(secs)
     value = bytes_per * args.steps / total / 1e9
+    sample = "first 2^20 of 2^24 records per step, all 9 sections + AoS decode / encode, record ranges over %d " \
+             "host threads" % cores
     line = {
         "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000 * total / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64+i32",
         "data": "synthetic (seeded SplitMix64)",
         "config": {"workload": wl.name, "n_records_per_step": n_sample,
-                   "note": "CPU oracle (plain scalar C, one thread) on the first 2^18 records of the 2^24-record batch"},
-        "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                         "sample": "first 2^18 of 2^24 records per step, all 9 sections + AoS decode / encode"},
+                   "note": "CPU oracle (plain scalar C) on the first 2^20 records of the 2^24-record batch"},
+        "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
-# ---------------------------------------------------------------------------------- device arm
+# ---------------------------------------------------------------------------------- device helpers
 
-def main():
-    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=10)
-    ap.add_argument("--impl", default="adha", choices=["adha", "reference"])
-    ap.add_argument("--no-compare", action="store_true", help="skip the AoS/SoA/exhaustive program comparison")
-    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle timing")
-    ap.add_argument("--workload", default="stress", choices=["stress", "particles", "batched", "differentiable"],
-                    help="stress: the 2^24-record layout-stress program (the headline); particles: the 2^25-record "
-                         "particle program with a gather; batched: 256 uneven arrays remapped in one launch; "
-                         "differentiable: the 2^26-record chain of 64 sections, forward + backward")
-    ap.add_argument("--n-log2", type=int, default=0, help="records per GPU (default: the workload's size)")
-    ap.add_argument("--fuse-window", type=int, default=-1,
-                    help="longest run of sections the fused-plan comparison may fuse (-1: all, up to 16; 0: skip)")
-    ap.add_argument("--e2e-slices", type=int, default=8,
-                    help="slices of the end-to-end pipeline through host buffers (programs without a gather)")
-    ap.add_argument("--cost-cache", default=None,
-                    help="JSON file holding the measured cost table: loaded when it matches the GPU, workload and "
-                         "candidates, written after measuring otherwise")
-    args = ap.parse_args()
-    if args.warmup < 3:
-        ap.error("--warmup must be at least 3")
-    if args.impl == "reference":
-        return run_reference(args)
+def _timed(torch, stream, steps, fn):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
 
-    rank, world, local = env_rank()
+
+def _group_kernels(recs):
+    groups = {}
+    for r in recs:
+        key = r["kind"] if r["kind"] != "section" else "section_%s" % r["op"]
+        g = groups.setdefault(key, [0.0, 0.0, 0])
+        g[0] += r["ms"]
+        g[1] += r["bytes"]
+        g[2] += 1
+    return groups
+
+
+def _roofline(recs, workload):
+    """Roofline of the dominant kernel (largest share of the recorded launches): its algorithmic
+    bytes over its event time, against the measured copy peak."""
+    groups = _group_kernels(recs)
+    dom = max(groups, key=lambda k: groups[k][0])
+    peak, src = measured_peaks()
+    achieved = groups[dom][1] / (groups[dom][0] * 1e6)
+    total = sum(v[0] for v in groups.values())
+    name = {"remap": "remap_kernel", "batched_remap": "batched_kernel", "fused": "fused_kernel",
+            "section_backward": "backward_kernel"}.get(dom, "section_kernel<%s>" % dom.replace("section_", ""))
+    roof = {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1), "peak": peak,
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback",
+            "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic_for(workload, dom),
+            "launches": groups[dom][2], "share": round(groups[dom][0] / max(1e-9, total), 3)}
+    kernels = {k: {"launches": v[2], "ms": round(v[0], 3), "alg_GBs": round(v[1] / (v[0] * 1e6), 1)}
+               for k, v in sorted(groups.items(), key=lambda kv: -kv[1][0])}
+    return roof, kernels
+
+
+def pack_aos(P, wl):
+    """The workload's seeded values as AoS record bytes (the library's struct rule for offsets,
+    zero padding), packed with a numpy structured array."""
     import numpy as np
-    import torch
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    import synth
-    from paper_1407_4859_gb300 import build
-    build.build()
-    import paper_1407_4859_gb300 as P
+    S = P.Schema(wl.dtypes)
+    (stride,), off = P.adha_layout_strides(S, P.Layout.aos(wl.F))
+    np_t = {0: np.float32, 1: np.float64, 2: np.int32, 3: np.uint16}
+    dt = np.dtype({"names": ["f%d" % f for f in range(wl.F)], "formats": [np_t[d] for d in wl.dtypes],
+                   "offsets": off, "itemsize": stride})
+    rec = np.zeros(wl.n, dtype=dt)
+    for f in range(wl.F):
+        v = wl.values(f)
+        rec["f%d" % f] = v.view(np_t[wl.dtypes[f]])
+        del v
+    return rec.view(np.uint8).reshape(-1)
 
-    if args.workload == "batched":
-        return batched_bench(args, rank, world, local, dist)
-    if args.workload == "differentiable":
-        return differentiable_bench(args, rank, world, local, dist)
-    if args.workload == "particles":
-        wl = synth.config3(n=1 << (args.n_log2 or 25))
-    else:
-        wl = synth.config2(n=1 << (args.n_log2 or 24))
+
+# ---------------------------------------------------------------------------------- programs
+
+def program_run(P, torch, wl, args, tag, world=1, dist=None, local=0, autotune=True, fuse=0, compare=True,
+                cpu=True, steps=None, warmup=None, reps=2, cache=None):
+    """One program workload: ODS candidates, measured cost table, the timed PDL program, its
+    roofline, end-to-end run from host buffers, and the comparison with AoS, SoA and the
+    exhaustive set.  Returns the JSON dict of the workload (contract keys included)."""
+    import numpy as np
+    steps = steps or args.steps
+    warmup = warmup or args.warmup
     n = wl.n
     S = P.Schema(wl.dtypes)
     AOS = P.Layout.aos(wl.F)
     perm_dev = torch.from_numpy(wl.perm()).cuda() if wl.has_perm else None
     secs = P.Sections(wl.sections, perm_dev)
     t0 = time.perf_counter()
-    host_aos = None
-    fields = [wl.values(f) for f in range(wl.F)]
-    import oracle  # encoding the seeded input as AoS bytes on the host (test infrastructure, not timed)
-    host_aos = oracle.from_fields(n, wl.dtypes, AOS.groups, fields)[0]
-    del fields
-    pinned = torch.from_numpy(host_aos).pin_memory()
+    pinned = torch.from_numpy(pack_aos(P, wl)).pin_memory()
     in_buf = [pinned.cuda()]
-    log("inputs ready in %.1f s" % (time.perf_counter() - t0))
-
+    log("%s: inputs ready in %.1f s" % (tag, time.perf_counter() - t0))
     opts = P.PlanOpts(CAPS, max_window=0)
     cand = P.adha_plan_sections(S, secs, opts)
     L = len(cand)
     t0 = time.perf_counter()
-    fuse = min(len(wl.sections), 16) if args.fuse_window < 0 else min(args.fuse_window, 16)
-    fuse = fuse if fuse >= 2 else 0
     cache_key = {"gpu": torch.cuda.get_device_name(local), "workload": wl.name, "n": n,
-                 "candidates": [l.groups for l in cand.layouts], "csrc": csrc_hash(), "fuse_window": fuse}
+                 "candidates": [l.groups for l in cand.layouts], "csrc": csrc_hash(), "fuse_window": fuse,
+                 "autotune": autotune, "reps": reps}
     costs = None
-    if args.cost_cache and os.path.exists(args.cost_cache):
-        d = json.load(open(args.cost_cache))
-        if d.get("key") == cache_key:
+    if cache and os.path.exists(cache):
+        d = json.load(open(cache)).get(wl.name)
+        if d and d.get("key") == cache_key:
             costs = P.adha_cost_table_create(len(wl.sections), L, max_window=fuse)
             costs.set(d["section_ns"], d["remap_ns"], {(k, m): row for k, m, row in d["fused_ns"]})
             P.adha_tune_import(d.get("tuning", ""))
-            log("cost table and tuning loaded from %s" % args.cost_cache)
+            log("%s: cost table and tuning loaded from %s" % (tag, cache))
     if costs is None:
-        costs = P.adha_measure(S, n, AOS, in_buf, secs, cand, reps=2, autotune=True, fuse_window=fuse)
-        if args.cost_cache:
-            json.dump({"key": cache_key, "section_ns": costs.section_ns, "remap_ns": costs.remap_ns,
-                       "fused_ns": [[k, m, row] for (k, m), row in costs.fused_ns.items()],
-                       "tuning": P.adha_tune_export()}, open(args.cost_cache, "w"))
+        costs = P.adha_measure(S, n, AOS, in_buf, secs, cand, reps=reps, autotune=autotune, fuse_window=fuse)
+        if cache:
+            allc = json.load(open(cache)) if os.path.exists(cache) else {}
+            allc[wl.name] = {"key": cache_key, "section_ns": costs.section_ns, "remap_ns": costs.remap_ns,
+                             "fused_ns": [[k, m, row] for (k, m), row in costs.fused_ns.items()],
+                             "tuning": P.adha_tune_export()}
+            json.dump(allc, open(cache, "w"))
     measure_s = time.perf_counter() - t0
-    log("%d candidates, cost table ready in %.1f s" % (L, measure_s))
+    log("%s: %d candidates, cost table ready in %.1f s" % (tag, L, measure_s))
     ws = torch.empty(P.adha_program_workspace_bytes(S, n, AOS, cand), dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
     def step():
         c = P.adha_plan_sections(S, secs, opts)          # ODS candidates (host)
-        return P.adha_run_program(S, n, AOS, in_buf, secs, c, costs=costs, workspace=ws, stream=stream), c
+        return P.adha_run_program(S, n, AOS, in_buf, secs, c, costs=costs, workspace=ws, stream=stream)
 
-    for _ in range(args.warmup):
-        plan, _ = step()
+    plan = None
+    for _ in range(warmup):
+        plan = step()
     layouts = cand.layouts
     seq = list(plan.layout_of_section[:len(wl.sections)])
     plan_layouts = [layouts[l].groups for l in seq]
@@ -315,75 +398,58 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    P.adha_profile_start(64 * args.steps)
+    P.adha_profile_start(64 * steps)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.nvtx.range_push("timed")
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
-    recs = P.adha_profile_stop(64 * args.steps)
+    recs = P.adha_profile_stop(64 * steps)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = reduce_max_ms(dist, e0.elapsed_time(e1))
-    value = weak_scaling_value(world, bytes_per_step, args.steps, ms)
+    value = weak_scaling_value(world, bytes_per_step, steps, ms)
+    roofline, per_kernel = _roofline(recs, tag)
 
-    # roofline of the dominant kernel (largest share of the timed region)
-    groups = {}
-    for r in recs:
-        key = r["kind"] if r["kind"] != "section" else "section_%s" % r["op"]
-        g = groups.setdefault(key, [0.0, 0.0, 0])
-        g[0] += r["ms"]
-        g[1] += r["bytes"]
-        g[2] += 1
-    dom = max(groups, key=lambda k: groups[k][0])
-    peak, peak_src = measured_peaks()
-    achieved = groups[dom][1] / (groups[dom][0] * 1e6)
-    kernel_name = {"remap": "remap_kernel"}.get(dom, "section_kernel<%s>" % dom.replace("section_", ""))
-    traffic = traffic_for(args.workload, dom)
-    roofline = {"bound": "hbm", "kernel": kernel_name, "achieved": round(achieved, 1), "peak": peak,
-                "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
-                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-                "launches": groups[dom][2], "share": round(groups[dom][0] / max(1e-9, sum(v[0] for v in groups.values())), 3)}
-    per_kernel = {k: {"launches": v[2], "ms": round(v[0], 3), "alg_GBs": round(v[1] / (v[0] * 1e6), 1)}
-                  for k, v in sorted(groups.items(), key=lambda kv: -kv[1][0])}
-
-    # end to end through the C ABI with host buffers: adha_run_program_host cuts the batch into
-    # slices that flow through two streams (upload, program, download overlap); the timed region
-    # holds every host->device copy of the step's input and device->host copy of its result
+    # end to end through the C ABI with host buffers (pinned in, pinned out, copies inside)
     lay_final = layouts[seq[-1]]
     strides, _ = P.adha_layout_strides(S, lay_final)
     host_out = [torch.empty(n * s, dtype=torch.uint8).pin_memory() for s in strides]
-    n_slices = 1 if wl.has_perm else args.e2e_slices
+    one_slice = wl.has_perm or any(s.op == "reduce" for s in wl.sections)
+    n_slices = 1 if one_slice else args.e2e_slices
     ws_host = torch.empty(P.adha_program_host_workspace_bytes(S, n, AOS, cand, n_slices), dtype=torch.uint8,
                           device="cuda")
-    e2e_steps = max(3, min(20, args.steps // 10))
+    outs_host = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in secs.outputs.items()}
 
     def e2e_step():
         P.adha_run_program_host(S, n, AOS, [pinned], secs, cand, host_out, costs=costs, workspace=ws_host,
                                 n_slices=n_slices, stream=stream)
+        for k, v in secs.outputs.items():   # a reduce section's result comes back too
+            outs_host[k].copy_(v, non_blocking=True)
     for _ in range(3):   # the first passes through freshly pinned host pages run slow
         e2e_step()
+    e2e_steps = max(3, min(20, steps // 10))
     e2e_ms = _timed(torch, stream, e2e_steps, e2e_step) / e2e_steps
     del ws_host
+    d2h = int(sum(h.numel() for h in host_out)) + int(sum(v.numel() * v.element_size() for v in outs_host.values()))
     e2e = {"value": round(world * bytes_per_step / (e2e_ms * 1e6), 1), "unit": "GB/s",
-           "h2d_bytes_per_step": int(pinned.numel()), "d2h_bytes_per_step": int(sum(h.numel() for h in host_out)),
-           "ms_per_step": round(e2e_ms, 3), "slices": n_slices,
-           "api": "adha_run_program_host (pinned host buffers in and out)"}
+           "h2d_bytes_per_step": int(pinned.numel()), "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3),
+           "slices": n_slices, "api": "adha_run_program_host (pinned host buffers in and out)"}
 
-    # program time: ADHA vs all-AoS vs all-SoA vs a bounded exhaustive set
-    compare = None
-    if not args.no_compare and rank == 0:
-        def prog_ms(fixed, reps=3):
+    compare_d = None
+    if compare:
+        def prog_ms(fixed, reps_=3):
             ts = []
-            for r in range(reps + 1):
+            for r in range(reps_ + 1):
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record(stream)
-                P.adha_run_program(S, n, AOS, in_buf, secs, cand, costs=costs, fixed=fixed, workspace=ws, stream=stream)
+                P.adha_run_program(S, n, AOS, in_buf, secs, cand, costs=costs, fixed=fixed, workspace=ws,
+                                   stream=stream)
                 b.record(stream)
                 torch.cuda.synchronize()
                 if r:
@@ -396,64 +462,59 @@ def main():
         t_soa = prog_ms([i_soa] * nsec)
         import itertools
         tried = {}
-        for assign in itertools.product([i_aos, i_soa], repeat=nsec):
-            tried[assign] = prog_ms(list(assign), reps=1)
+        n_mix = 0
+        if nsec <= 10:
+            for assign in itertools.product([i_aos, i_soa], repeat=nsec):
+                tried[assign] = prog_ms(list(assign), reps_=1)
+            n_mix = 2 ** nsec
         for l in range(L):
-            tried[(l,) * nsec] = prog_ms([l] * nsec, reps=1)
+            tried[(l,) * nsec] = prog_ms([l] * nsec, reps_=1)
+        tops = top_plans(costs.section_ns, costs.remap_ns, 32)
+        for _, p in tops:
+            if tuple(p) not in tried:
+                tried[tuple(p)] = prog_ms(list(p), reps_=1)
         best_assign = min(tried, key=tried.get)
         best_ms = prog_ms(list(best_assign))
         uniform_best = min(range(L), key=lambda l: tried[(l,) * nsec])
-        compare = {"adha_ms": round(adha_ms, 3), "all_aos_ms": round(t_aos, 3), "all_soa_ms": round(t_soa, 3),
-                   "exhaustive_best_ms": round(min(best_ms, adha_ms), 3),
-                   "exhaustive_set": "bounded: all %d {AoS,SoA}^%d assignments + %d uniform single-layout programs "
-                                     "+ the ADHA plan (full %d^%d enumeration infeasible)" % (2 ** nsec, nsec, L, L, nsec),
-                   "exhaustive_best_plan": list(best_assign), "best_uniform_layout": layouts[uniform_best].groups,
-                   "adha_over_best": round(adha_ms / min(best_ms, adha_ms), 4),
-                   "speedup_vs_aos": round(t_aos / adha_ms, 3), "speedup_vs_soa": round(t_soa / adha_ms, 3),
-                   "paper_context": "paper: up to 6.92x over manual (SoA) layouts, K-Means on Xeon X5660 + Tesla M2050, OpenCL"}
+        best = min(best_ms, adha_ms)
+        compare_d = {"adha_ms": round(adha_ms, 3), "all_aos_ms": round(t_aos, 3), "all_soa_ms": round(t_soa, 3),
+                     "exhaustive_best_ms": round(best, 3),
+                     "exhaustive_set": "%s%d uniform single-layout programs + the %d plans of lowest model cost + "
+                                       "the ADHA plan (%d programs; the full %d^%d enumeration is infeasible)"
+                                       % ("all %d {AoS,SoA}^%d assignments + " % (n_mix, nsec) if n_mix else "",
+                                          L, len(tops), len(tried), L, nsec),
+                     "exhaustive_best_plan": list(best_assign), "best_uniform_layout": layouts[uniform_best].groups,
+                     "adha_over_best": round(adha_ms / best, 4),
+                     "speedup_vs_aos": round(t_aos / adha_ms, 3), "speedup_vs_soa": round(t_soa / adha_ms, 3),
+                     "paper_context": PAPER_CONTEXT}
         if fuse:
-            compare["fused"] = fused_comparison(P, torch, S, n, AOS, in_buf, secs, cand, costs, ws, stream, fuse,
-                                                adha_ms, t_aos, t_soa, layouts)
+            compare_d["fused"] = fused_comparison(P, torch, S, n, AOS, in_buf, secs, cand, costs, ws, stream, fuse,
+                                                  adha_ms, t_aos, t_soa, layouts)
 
-    cpu = None
-    if not args.no_cpu and rank == 0:
-        n_sample = min(n, 1 << 22)
-        small = wl.with_n(n_sample)
-        b_small = program_bytes(small)
-        t_tot, reps = 0.0, 0
-        while reps < 3 and (reps == 0 or t_tot < 10.0):
-            t_tot += oracle_program_seconds(wl, plan_layouts, n_sample)
-            reps += 1
-        cpu = {"value": round(b_small * reps / t_tot / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
-               "sample": "first 2^22 of %d records x %d runs: AoS decode, %d sections, encode in the ADHA final layout"
-                         % (n, reps, len(wl.sections))}
-
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64+i32",
-            "data": "synthetic (seeded SplitMix64, values as the workload states)",
-            "config": {"workload": wl.name, "records": n,
-                       "fields": ("8 f32 + 4 f64 + 4 i32 (80 B AoS)" if args.workload == "stress"
-                                  else "pos, vel, mass, charge f32; id, cell, flags i32; energy f64 (56 B AoS)"),
-                       "sections": len(wl.sections), "candidates": L, "plan": seq,
-                       "plan_layouts": plan_layouts, "remaps_per_step": plan.n_remaps,
-                       "l2": "inputs larger than L2 (%.2f GB per AoS copy vs 129 MB)" % (pinned.numel() / 1e9),
-                       "parallelism": "one independent batch per GPU" if world > 1 else "single GPU",
-                       "measure_s": round(measure_s, 2), "program_bytes_per_step": bytes_per_step,
-                       "remap_bytes_per_step": remap_bytes_per_step,
-                       "value_definition": "program section bytes per step / step device time; remaps the plan "
-                                           "adds cost time but are not counted as work",
-                       "step_GBs_incl_remaps": round(world * (bytes_per_step + remap_bytes_per_step) * args.steps
-                                                     / (ms * 1e6), 1)},
-            "gpu_launches": len(recs), "roofline": roofline, "kernels": per_kernel, "clocks": clk,
-            "e2e": e2e, "cpu_baseline": cpu, "program_ms": compare,
-        }
-        print(json.dumps(line), flush=True)
-    if dist:
-        dist.destroy_process_group()
-    return 0
+    cpu_d = cpu_baseline(wl, plan_layouts, min(n, 1 << 22)) if cpu else None
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": steps,
+        "warmup": warmup, "ms_per_step": round(ms / steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "+".join(sorted({{0: "f32", 1: "f64", 2: "i32", 3: "bf16"}[d] for d in wl.dtypes})),
+        "data": "synthetic (seeded SplitMix64, values as the workload states)",
+        "config": {"workload": wl.name, "records": n, "fields": wl.F,
+                   "record_bytes_aos": int(pinned.numel() // max(1, n)), "sections": len(wl.sections),
+                   "candidates": L, "plan": seq, "plan_layouts": plan_layouts, "remaps_per_step": plan.n_remaps,
+                   "l2": "inputs larger than L2 (%.2f GB per AoS copy vs 129 MB)" % (pinned.numel() / 1e9),
+                   "parallelism": "one independent batch per GPU" if world > 1 else "single GPU",
+                   "measure_s": round(measure_s, 2), "program_bytes_per_step": bytes_per_step,
+                   "remap_bytes_per_step": remap_bytes_per_step,
+                   "value_definition": "program section bytes per step / step device time; remaps the plan "
+                                       "adds cost time but are not counted as work",
+                   "step_GBs_incl_remaps": round(world * (bytes_per_step + remap_bytes_per_step) * steps
+                                                 / (ms * 1e6), 1)},
+        "gpu_launches": len(recs), "roofline": roofline, "kernels": per_kernel, "clocks": clk,
+        "e2e": e2e, "cpu_baseline": cpu_d, "program_ms": compare_d,
+    }
+    del in_buf, ws, pinned
+    torch.cuda.empty_cache()
+    return line
 
 
 def fused_comparison(P, torch, S, n, AOS, in_buf, secs, cand, costs, ws, stream, fuse, adha_ms, t_aos, t_soa, layouts):
@@ -466,6 +527,7 @@ def fused_comparison(P, torch, S, n, AOS, in_buf, secs, cand, costs, ws, stream,
     win = list(plan.window_len[:nsec])
     model_ns = plan.model_ns
     ts = []
+    recs = []
     for r in range(4):   # the solved plan, run as a fixed plan (as the other programs are timed)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         if r == 3:
@@ -500,49 +562,38 @@ def fused_comparison(P, torch, S, n, AOS, in_buf, secs, cand, costs, ws, stream,
                     "the union of its sections' fields read once plus written fields written once"}
 
 
-# ---------------------------------------------------------------------------------- other workloads
-
-def _timed(torch, stream, steps, fn):
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(steps):
-        fn()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    return e0.elapsed_time(e1)
-
-
-def _roofline(recs, workload):
-    groups = {}
-    for r in recs:
-        key = r["kind"] if r["kind"] != "section" else "section_%s" % r["op"]
-        g = groups.setdefault(key, [0.0, 0.0, 0])
-        g[0] += r["ms"]
-        g[1] += r["bytes"]
-        g[2] += 1
-    dom = max(groups, key=lambda k: groups[k][0])
-    peak, src = measured_peaks()
-    achieved = groups[dom][1] / (groups[dom][0] * 1e6)
-    total = sum(v[0] for v in groups.values())
-    roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
-            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback",
-            "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic_for(workload, dom),
-            "launches": groups[dom][2], "share": round(groups[dom][0] / max(1e-9, total), 3)}
-    kernels = {k: {"launches": v[2], "ms": round(v[0], 3), "alg_GBs": round(v[1] / (v[0] * 1e6), 1)}
-               for k, v in sorted(groups.items(), key=lambda kv: -kv[1][0])}
-    return roof, kernels
+def gather_probe_run(P, torch, wl, reps=10):
+    """The random-access roofline of the gather section: 16-byte structs read at the workload's
+    permutation (2^25 records) and written in order, GB/s of 4 + 16 + 16 bytes per record."""
+    import numpy as np
+    n = wl.n
+    perm = torch.from_numpy(wl.perm()).cuda()
+    table = torch.randint(0, 255, (n * 16,), dtype=torch.uint8, device="cuda")
+    out = torch.empty_like(table)
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        P.adha_gather_probe(table, perm, out, 16)
+    ms = _timed(torch, stream, reps, lambda: P.adha_gather_probe(table, perm, out, 16)) / reps
+    ok = bool(torch.equal(out.view(n, 16)[:4096], table.view(n, 16)[perm[:4096].long()]))
+    res = {"GBs": round(n * 36 / (ms * 1e6), 1), "ms": round(ms, 4), "records": n, "rec_bytes": 16,
+           "ns_per_record": round(ms * 1e6 / n, 4), "checked": ok,
+           "definition": "out[i] = table[perm[i]], 16-byte structs, perm read and out written in order; "
+                         "4 + 16 + 16 algorithmic bytes per record"}
+    del table, out, perm
+    return res
 
 
-def batched_bench(args, rank, world, local, dist):
+# ---------------------------------------------------------------------------------- batched remap
+
+def batched_run(P, torch, args, world=1, dist=None, local=0, steps=None, warmup=None, cpu=True):
     """256 record arrays (N log-uniform in [2^10, 2^22), F in [4, 32], mixed dtypes) remapped
     AoS -> their own random groupings: one graph-captured persistent launch per step, against one
     adha_remap launch per array."""
     import numpy as np
-    import torch
     import synth
     import oracle
-    import paper_1407_4859_gb300 as P
+    steps = steps or args.steps
+    warmup = warmup or args.warmup
     stream = torch.cuda.current_stream()
     specs = synth.config4_arrays(n_scale=2.0 ** ((args.n_log2 or 22) - 22))
     t0 = time.perf_counter()
@@ -577,35 +628,43 @@ def batched_bench(args, rank, world, local, dist):
             oo += al(d)
         arrays.append(dict(schema=S, n=a["n"], src=src, dst=dst, src_bufs=src_bufs, dst_bufs=dst_bufs))
     dev_in_all.copy_(host_in_all)
-    log("batched inputs ready in %.1f s" % (time.perf_counter() - t0))
+    log("batched: inputs ready in %.1f s" % (time.perf_counter() - t0))
     t0 = time.perf_counter()
-    b = P.Batched(arrays, autotune=True)
+    b = P.Batched(arrays)
     b.upload()
     b.capture()
-    tune_s = time.perf_counter() - t0
+    plan_s = time.perf_counter() - t0
+    ctas, region, units = b.info
     bytes_per = b.bytes
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         b.graph_launch()
     clocks = Clocks(local)
     clocks.start()
     if dist:
         dist.barrier()
-    P.adha_profile_start(4 * args.steps + 16)
+    P.adha_profile_start(4 * steps + 16)
     torch.cuda.nvtx.range_push("timed")
-    ms = _timed(torch, stream, args.steps, b.graph_launch)
+    ms = _timed(torch, stream, steps, b.graph_launch)
     torch.cuda.nvtx.range_pop()
-    recs = P.adha_profile_stop(4 * args.steps + 16)
+    recs = P.adha_profile_stop(4 * steps + 16)
     clk = clocks.stop()
     ms = reduce_max_ms(dist, ms)
-    value = weak_scaling_value(world, bytes_per, args.steps, ms)
-    roof, kernels = _roofline(recs, args.workload)
+    value = weak_scaling_value(world, bytes_per, steps, ms)
+    roof, kernels = _roofline(recs, "batched")
+
+    # the one-call entry point (plan + descriptors + launch per call)
+    ws1 = torch.empty(P.adha_workspace_bytes(arrays), dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        P.adha_remap_batched(arrays, ws1)
+    k2 = max(3, steps // 10)
+    one_call_ms = _timed(torch, stream, k2, lambda: P.adha_remap_batched(arrays, ws1)) / k2
+    del ws1
 
     def per_array():
         for a in arrays:
             P.adha_remap(a["schema"], a["n"], a["src"], a["src_bufs"], a["dst"], a["dst_bufs"], stream=stream)
     for _ in range(3):
         per_array()
-    k2 = max(3, args.steps // 10)
     per_ms = _timed(torch, stream, k2, per_array) / k2
     g = torch.cuda.CUDAGraph()
     side = torch.cuda.Stream()
@@ -636,12 +695,11 @@ def batched_bench(args, rank, world, local, dist):
         if hi > lo:
             i0, o0 = in_ends[lo - 1] if lo else (0, 0)
             i1, o1 = in_ends[hi - 1]
-            bq = P.Batched(arrays[lo:hi], autotune=True)
+            bq = P.Batched(arrays[lo:hi])
             bq.upload()
             bq.capture()
             quarters.append((bq, slice(i0, i1), slice(o0, o1), torch.cuda.Stream()))
         lo = hi
-    e2e_steps = 3
 
     def e2e_step():
         for bq, si, so, st in quarters:
@@ -654,56 +712,60 @@ def batched_bench(args, rank, world, local, dist):
             stream.wait_stream(st)
     for _ in range(3):
         e2e_step()
-    e2e_ms = _timed(torch, stream, e2e_steps, e2e_step) / e2e_steps
+    e2e_ms = _timed(torch, stream, 3, e2e_step) / 3
     h2d = host_in_all.numel()
     d2h = host_out_all.numel()
-    cpu = None
-    if not args.no_cpu and rank == 0:
+    cpu_d = None
+    if cpu:
+        cores = host_cores()
         t_tot, moved = 0.0, 0.0
         for a, h in list(zip(specs, host_in))[:64]:
             ns = min(a["n"], 1 << 16)
-            S = a["dtypes"]
-            (sst,), _ = P.adha_layout_strides(P.Schema(S), P.Layout(a["src"]))
+            (sst,), _ = P.adha_layout_strides(P.Schema(a["dtypes"]), P.Layout(a["src"]))
             src_bytes = h[: ns * sst].numpy()
             t1 = time.perf_counter()
-            oracle.remap(ns, S, a["src"], [src_bytes], a["dst"])
+            oracle.remap_threads(ns, a["dtypes"], a["src"], [src_bytes], a["dst"], threads=cores)
             t_tot += time.perf_counter() - t1
-            moved += 2 * ns * sum(SZ[d] for d in S)
-        cpu = {"value": round(moved / t_tot / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
-               "sample": "first min(N, 2^16) records of the first 64 arrays, scalar oracle remap"}
-    if rank == 0:
-        print(json.dumps({
-            "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "bytes (f32/f64/i32/bf16 fields)",
-            "data": "synthetic (seeded SplitMix64 bytes)",
-            "config": {"workload": "config4_batched_remap_256_arrays", "arrays": len(arrays),
-                       "records": int(sum(a["n"] for a in arrays)), "moved_bytes_per_step": bytes_per,
-                       "l2": "inputs larger than L2 (%.1f GB)" % (h2d / 1e9), "autotune_and_capture_s": round(tune_s, 2),
-                       "value_definition": "2 x data bytes of all moved fields of all arrays / step time"},
-            "gpu_launches": len(recs), "roofline": roof, "kernels": kernels, "clocks": clk,
-            "per_array_launches": {"ms_per_step": round(per_ms, 4), "GBs": round(bytes_per / (per_ms * 1e6), 1),
-                                   "graph_of_256_launches_ms": round(graph_ms, 4),
-                                   "graph_of_256_launches_GBs": round(bytes_per / (graph_ms * 1e6), 1)},
-            "e2e": {"value": round(world * bytes_per / (e2e_ms * 1e6), 1), "unit": "GB/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3),
-                    "api": "%d batched remaps (adha_batched_graph_launch) on their own streams, pinned host "
-                           "blocks in and out" % len(quarters)},
-            "cpu_baseline": cpu}), flush=True)
-    if dist:
-        dist.destroy_process_group()
-    return 0
+            moved += 2 * ns * sum(SZ[d] for d in a["dtypes"])
+        cpu_d = {"value": round(moved / t_tot / 1e9, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
+                 "sample": "first min(N, 2^16) records of the first 64 arrays, scalar oracle remap over %d host "
+                           "threads" % cores}
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": steps,
+        "warmup": warmup, "ms_per_step": round(ms / steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bytes (f32/f64/i32/bf16 fields)",
+        "data": "synthetic (seeded SplitMix64 bytes)",
+        "config": {"workload": "config4_batched_remap_256_arrays", "arrays": len(arrays),
+                   "records": int(sum(a["n"] for a in arrays)), "moved_bytes_per_step": bytes_per,
+                   "l2": "inputs larger than L2 (%.1f GB)" % (h2d / 1e9), "plan_and_capture_s": round(plan_s, 2),
+                   "ctas_per_sm": ctas, "warp_region_bytes": region, "work_units": units,
+                   "value_definition": "2 x data bytes of all moved fields of all arrays / step time"},
+        "gpu_launches": len(recs), "roofline": roof, "kernels": kernels, "clocks": clk,
+        "one_call_ms": round(one_call_ms, 4), "one_call_GBs": round(bytes_per / (one_call_ms * 1e6), 1),
+        "per_array_launches": {"ms_per_step": round(per_ms, 4), "GBs": round(bytes_per / (per_ms * 1e6), 1),
+                               "graph_of_256_launches_ms": round(graph_ms, 4),
+                               "graph_of_256_launches_GBs": round(bytes_per / (graph_ms * 1e6), 1)},
+        "e2e": {"value": round(world * bytes_per / (e2e_ms * 1e6), 1), "unit": "GB/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3),
+                "api": "%d batched remaps (adha_batched_graph_launch) on their own streams, pinned host "
+                       "blocks in and out" % len(quarters)},
+        "cpu_baseline": cpu_d}
+    del dev_in_all, dev_out_all, arrays, quarters, b
+    torch.cuda.empty_cache()
+    return line
 
 
-def differentiable_bench(args, rank, world, local, dist):
+# ---------------------------------------------------------------------------------- differentiable
+
+def differentiable_run(P, torch, args, world=1, dist=None, local=0, steps=None, warmup=None, cpu=True):
     """The 2^26-record chain of 64 fp32 sections: forward (remaps + in-place sections with saves)
     and backward (inverse remaps + adjoint kernels) under the PDL plan, against all-AoS / all-SoA."""
     import numpy as np
-    import torch
     import synth
     import oracle
-    import paper_1407_4859_gb300 as P
     from paper_1407_4859_gb300.autograd import DifferentiableProgram
+    steps = steps or args.steps
+    warmup = warmup or args.warmup
     wl = synth.config5(n=1 << (args.n_log2 or 26))
     n, F = wl.n, wl.F
     S = P.Schema(wl.dtypes)
@@ -716,7 +778,7 @@ def differentiable_bench(args, rank, world, local, dist):
     pinned = torch.from_numpy(host).pin_memory()
     del host
     x0 = pinned.cuda()
-    log("inputs ready in %.1f s" % (time.perf_counter() - t0))
+    log("differentiable: inputs ready in %.1f s" % (time.perf_counter() - t0))
     secs = P.Sections(wl.sections)
     cand = P.adha_plan_sections(S, secs, P.PlanOpts(CAPS, max_window=2, max_candidates=16))
     t0 = time.perf_counter()
@@ -738,25 +800,25 @@ def differentiable_bench(args, rank, world, local, dist):
         return x.grad
 
     plan = [layouts[l] for l in seq]
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         run(plan)
     clocks = Clocks(local)
     clocks.start()
     if dist:
         dist.barrier()
-    P.adha_profile_start(512 * args.steps + 64)
+    P.adha_profile_start(512 * steps + 64)
     torch.cuda.nvtx.range_push("timed")
-    ms = _timed(torch, stream, args.steps, lambda: run(plan))
+    ms = _timed(torch, stream, steps, lambda: run(plan))
     torch.cuda.nvtx.range_pop()
-    recs = P.adha_profile_stop(512 * args.steps + 64)
+    recs = P.adha_profile_stop(512 * steps + 64)
     clk = clocks.stop()
     ms = reduce_max_ms(dist, ms)
-    fwd = sum(r["bytes"] for r in recs if r["kind"] in ("section", "remap")) / args.steps
-    bwd = sum(r["bytes"] for r in recs if r["kind"] == "section_backward") / args.steps
+    fwd = sum(r["bytes"] for r in recs if r["kind"] in ("section", "remap")) / steps
+    bwd = sum(r["bytes"] for r in recs if r["kind"] == "section_backward") / steps
     # program work only (sections and their adjoints), like the stress bench's value
-    work = sum(r["bytes"] for r in recs if r["kind"] in ("section", "section_backward")) / args.steps
-    value = weak_scaling_value(world, work, args.steps, ms)
-    roof, kernels = _roofline(recs, args.workload)
+    work = sum(r["bytes"] for r in recs if r["kind"] in ("section", "section_backward")) / steps
+    value = weak_scaling_value(world, work, steps, ms)
+    roof, kernels = _roofline(recs, "differentiable")
     # end to end: the step's input in from pinned host memory, forward + backward, its gradient out
     grad_host = torch.empty_like(pinned).pin_memory()
 
@@ -765,36 +827,170 @@ def differentiable_bench(args, rank, world, local, dist):
         grad_host.copy_(run(plan), non_blocking=True)
     for _ in range(2):
         e2e_step()
-    e2e_steps = max(3, args.steps // 3)
+    e2e_steps = max(3, steps // 3)
     e2e_ms = _timed(torch, stream, e2e_steps, e2e_step) / e2e_steps
     e2e = {"value": round(world * work / (e2e_ms * 1e6), 1), "unit": "GB/s", "h2d_bytes_per_step": pinned.numel() * 4,
            "d2h_bytes_per_step": grad_host.numel() * 4, "ms_per_step": round(e2e_ms, 3),
            "api": "DifferentiableProgram forward + torch.autograd.backward (pinned host input and gradient)"}
-    k2 = max(3, args.steps // 2)
-    t_aos = _timed(torch, stream, k2, lambda: run([AOS] * len(wl.sections))) / k2
+    k2 = max(3, steps // 2)
     t_soa = _timed(torch, stream, k2, lambda: run([P.Layout.soa(F)] * len(wl.sections))) / k2
-    cpu = None
-    if not args.no_cpu and rank == 0:
+    t_aos = _timed(torch, stream, 3, lambda: run([AOS] * len(wl.sections))) / 3
+    uni = {}
+    for l in range(min(len(layouts), 16)):
+        uni[l] = _timed(torch, stream, 2, lambda: run([layouts[l]] * len(wl.sections))) / 2
+    best_l = min(uni, key=uni.get)
+    cpu_d = None
+    if cpu:
+        cores = host_cores()
         ns = 1 << 18
         st = [wl.values(f, n=ns) for f in range(F)]
         t1 = time.perf_counter()
         oracle.chain_grad(wl.sections, st, wl.loss_weights)
         dt = time.perf_counter() - t1
-        cpu = {"value": round(work * ns / n / dt / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
-               "sample": "first 2^18 of 2^26 records: forward + reverse pass per record"}
+        cpu_d = {"value": round(work * ns / n / dt / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                 "sample": "first 2^18 of 2^26 records: forward + reverse pass per record, one thread (the chain "
+                           "gradient is not split by record range)"}
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": steps,
+        "warmup": warmup, "ms_per_step": round(ms / steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded N(0,1))",
+        "config": {"workload": wl.name, "records": n, "fields": "24 f32 (96 B AoS)", "sections": len(wl.sections),
+                   "candidates": len(cand), "plan": seq, "measure_s": round(measure_s, 1),
+                   "forward_bytes_per_step": fwd, "backward_bytes_per_step": bwd,
+                   "value_definition": "section + adjoint algorithmic bytes per forward+backward step / step time",
+                   "l2": "inputs larger than L2 (6.4 GB)"},
+        "gpu_launches": len(recs), "roofline": roof, "kernels": kernels, "clocks": clk, "e2e": e2e,
+        "step_ms": {"adha": round(ms / steps, 3), "all_aos": round(t_aos, 3), "all_soa": round(t_soa, 3),
+                    "best_uniform": round(uni[best_l], 3), "best_uniform_layout": layouts[best_l].groups,
+                    "bounded_exhaustive": "every uniform single-layout program of the %d candidates" % len(uni)},
+        "cpu_baseline": cpu_d}
+    del x0, pinned, grad_host
+    torch.cuda.empty_cache()
+    return line
+
+
+# ---------------------------------------------------------------------------------- main
+
+def _compact(line):
+    """The workload line without the bulky plan details (for the headline's `workloads` key)."""
+    out = {k: v for k, v in line.items() if k not in ("metric", "data", "higher_is_better", "scaling",
+                                                      "vs_baseline", "n_gpus")}
+    cfg = dict(out.get("config", {}))
+    cfg.pop("plan_layouts", None)
+    out["config"] = cfg
+    if out.get("program_ms") and "exhaustive_best_plan" in out["program_ms"]:
+        out["program_ms"] = dict(out["program_ms"])
+        out["program_ms"].pop("best_uniform_layout", None)
+    return out
+
+
+def run_workload(name, P, torch, args, world, dist, local, sub=False):
+    import synth
+    steps = min(args.steps, 20) if sub else args.steps
+    warmup = args.warmup
+    if name == "stress":
+        fuse = min(9, 16) if args.fuse_window < 0 else min(args.fuse_window, 16)
+        fuse = fuse if fuse >= 2 else 0
+        return program_run(P, torch, synth.config2(n=1 << (args.n_log2 or 24)), args, "stress", world, dist, local,
+                           autotune=True, fuse=fuse, cpu=not args.no_cpu, compare=not args.no_compare,
+                           cache=args.cost_cache)
+    if name == "particles":
+        return program_run(P, torch, synth.config3(n=1 << (args.n_log2 or 25)), args, "particles", world, dist, local,
+                           autotune=not sub, fuse=0 if sub else 10, cpu=not args.no_cpu, steps=steps, warmup=warmup,
+                           reps=1 if sub else 2, cache=args.cost_cache)
+    if name == "kmeans":
+        return program_run(P, torch, synth.kmeans(n=args.n_log2 and (1 << args.n_log2) or 8388608), args, "kmeans",
+                           world, dist, local, autotune=not sub, fuse=0, cpu=not args.no_cpu, steps=steps,
+                           warmup=warmup, reps=1 if sub else 2, cache=args.cost_cache)
+    if name == "medical":
+        return program_run(P, torch, synth.medical(n=args.n_log2 and (1 << args.n_log2) or 256 ** 3), args, "medical",
+                           world, dist, local, autotune=not sub, fuse=0 if sub else 7, cpu=not args.no_cpu,
+                           steps=steps, warmup=warmup, reps=1 if sub else 2, cache=args.cost_cache)
+    if name == "batched":
+        return batched_run(P, torch, args, world, dist, local, steps=steps, warmup=warmup, cpu=not args.no_cpu)
+    if name == "differentiable":
+        return differentiable_run(P, torch, args, world, dist, local, steps=min(steps, 10) if sub else steps,
+                                  warmup=warmup, cpu=not args.no_cpu)
+    raise ValueError(name)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="adha", choices=["adha", "reference"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the AoS/SoA/exhaustive program comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle timing")
+    ap.add_argument("--no-workloads", action="store_true", help="headline line only (no other workloads)")
+    ap.add_argument("--workload", default=None, choices=WORKLOADS,
+                    help="print this workload's line alone (default: the stress headline with every other "
+                         "workload under `workloads`)")
+    ap.add_argument("--n-log2", type=int, default=0, help="records per GPU (default: the workload's size)")
+    ap.add_argument("--fuse-window", type=int, default=-1,
+                    help="longest run of sections the fused-plan comparison may fuse (-1: all, up to 16; 0: skip)")
+    ap.add_argument("--e2e-slices", type=int, default=8,
+                    help="slices of the end-to-end pipeline through host buffers (programs without a gather)")
+    ap.add_argument("--cost-cache", default=None,
+                    help="JSON file holding measured cost tables: loaded when they match the GPU, workload and "
+                         "candidates, written after measuring otherwise")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    rank, world, local = env_rank()
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1407_4859_gb300 import build
+    build.build()
+    import paper_1407_4859_gb300 as P
+
+    if args.workload:
+        line = run_workload(args.workload, P, torch, args, world, dist, local)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    import synth
+    line = run_workload("stress", P, torch, args, world, dist, local)
+    if world == 1 and not args.no_workloads:
+        t0 = time.perf_counter()
+        try:
+            line["gather_random"] = gather_probe_run(P, torch, synth.config3(n=1 << 25))
+        except Exception as e:   # a measurement aid: report its failure, keep the headline
+            line["gather_random"] = {"error": repr(e)[:300]}
+        subs = {}
+        for name in ["particles", "batched", "differentiable", "kmeans", "medical"]:
+            t1 = time.perf_counter()
+            try:
+                subs[name] = _compact(run_workload(name, P, torch, args, world, dist, local, sub=True))
+            except Exception as e:
+                subs[name] = {"error": repr(e)[:300]}
+            subs[name]["wall_s"] = round(time.perf_counter() - t1, 1)
+            log("%s done in %.1f s" % (name, subs[name]["wall_s"]))
+        g = line.get("gather_random", {})
+        part = subs.get("particles", {})
+        gk = part.get("kernels", {}).get("section_gather")
+        if gk and g.get("ns_per_record"):
+            n_part = part["config"]["records"]
+            ns = gk["ms"] * 1e6 / (gk["launches"] * n_part)
+            part["gather_vs_probe"] = {"gather_ns_per_record": round(ns, 4),
+                                       "probe_ns_per_record": g["ns_per_record"],
+                                       "frac": round(g["ns_per_record"] / ns, 4),
+                                       "note": "time per record of the probe (random 16-byte reads, sequential "
+                                               "index and output) over that of the gather section"}
+        line["workloads"] = subs
+        line["workloads_wall_s"] = round(time.perf_counter() - t0, 1)
     if rank == 0:
-        print(json.dumps({
-            "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded N(0,1))",
-            "config": {"workload": wl.name, "records": n, "fields": "24 f32 (96 B AoS)", "sections": len(wl.sections),
-                       "candidates": len(cand), "plan": seq, "measure_s": round(measure_s, 1),
-                       "forward_bytes_per_step": fwd, "backward_bytes_per_step": bwd,
-                       "value_definition": "section + adjoint algorithmic bytes per forward+backward step / step time",
-                       "l2": "inputs larger than L2 (6.4 GB)"},
-            "gpu_launches": len(recs), "roofline": roof, "kernels": kernels, "clocks": clk, "e2e": e2e,
-            "step_ms": {"adha": round(ms / args.steps, 3), "all_aos": round(t_aos, 3), "all_soa": round(t_soa, 3)},
-            "cpu_baseline": cpu}), flush=True)
+        print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0

@@ -586,9 +586,22 @@ int adha_tune_export(char* buf, size_t len, size_t* needed);
 /* Adds the entries of a text made by adha_tune_export to the cache.  Host only. */
 int adha_tune_import(const char* text);
 
+/*
+ * Random-access read microbenchmark, the roofline of the gather section (whose
+ * reads land on permuted records, where a copy's bandwidth does not apply):
+ * out[i] = table[perm[i]] for i in [0, n), elements of rec_bytes (4, 8 or 16)
+ * bytes; perm holds n int32 indices into table (device), out n elements
+ * (device, not overlapping table).  The permutation is read and out written in
+ * order.  Algorithmic bytes per element: 4 + 2 * rec_bytes.  Async on `stream`.
+ * A measuring tool: the paper has no counterpart.
+ */
+int adha_gather_probe(const void* table, const int32_t* perm, void* out, int64_t n, int32_t rec_bytes,
+                      adha_stream stream);
+
 /* One kernel launch seen by the profiler.  kind: 0 remap, 1 section, 2 section
- * backward, 3 batched remap, 4 fused run; op: the section's adha_op (0 for
- * remaps; the number of sections for a fused run); bytes:
+ * backward, 3 batched remap, 4 fused run, 5 gather probe; op: the section's
+ * adha_op (0 for remaps; the number of sections for a fused run; the element
+ * bytes for the probe); bytes:
  * the algorithmic bytes the launch had to move (data bytes of the moved or
  * accessed fields, not padding or untouched fields); ms: its duration between
  * two CUDA events recorded around it on its stream. */

@@ -19,7 +19,8 @@ Heterogeneous Architectures", PACT 2014, Section 2 and Tables 2-4.
 """
 from .core import (  # noqa: F401
     build, group_layout, layout_info, remap, to_fields, from_fields, tanhf, tanh_coeffs, section,
-    chain_grad, aos, soa, canon, kmeans_assign, kmeans_reduce, kmeans_features,
+    chain_grad, aos, soa, canon, kmeans_assign, kmeans_reduce, kmeans_features, section_threads,
+    remap_threads,
 )
 from .planner import (  # noqa: F401
     affinity, ods, candidates, pdl_dp, pdl_exhaustive, program_cost, pdl_dp_fused, pdl_exhaustive_fused,

@@ -246,9 +246,20 @@ static void sec_mix(int F, const int* dtypes, void** fa, uint64_t R, uint64_t W,
  * The gather reads at perm[i] only fields it never writes, so the loop order
  * does not matter.  Returns 0, or -1 for an unknown op.
  */
+int oracle_section_range(int op, const int* a, const float* p, uint64_t R, uint64_t W, int F, const int* dtypes,
+                         void** fa, int64_t i0, int64_t i1, const int32_t* perm);
+
 int oracle_section(int op, const int* a, const float* p, uint64_t R, uint64_t W, int F, const int* dtypes,
                    void** fa, int64_t n, const int32_t* perm) {
-  for (int64_t i = 0; i < n; ++i) {
+  return oracle_section_range(op, a, p, R, W, F, dtypes, fa, 0, n, perm);
+}
+
+/* The same on records [i0, i1) of the field arrays (so that disjoint ranges can run side by
+ * side: a record's result depends on its own fields, and a gather's reads at perm[i] on fields
+ * no section writes in that section). */
+int oracle_section_range(int op, const int* a, const float* p, uint64_t R, uint64_t W, int F, const int* dtypes,
+                         void** fa, int64_t i0, int64_t i1, const int32_t* perm) {
+  for (int64_t i = i0; i < i1; ++i) {
     switch (op) {
       case OP_MADD3: { float m = F32(a[0])[i] * F32(a[1])[i]; F32(a[2])[i] = m + F32(a[2])[i]; break; }
       case OP_XORSHIFT: { uint32_t u = (uint32_t)I32(a[0])[i]; I32(a[1])[i] = (int32_t)(u ^ (u >> 3)); break; }
@@ -334,9 +345,17 @@ int oracle_section(int op, const int* a, const float* p, uint64_t R, uint64_t W,
  *          nearest in fp32; m = the smallest k whose D_k is smallest (scanning k
  *          upwards, a later k wins only when strictly smaller).
  */
+int oracle_kmeans_assign_range(int d, const int* feat, int mf, int K, const float* cent, void** fa, int64_t i0,
+                               int64_t i1);
+
 int oracle_kmeans_assign(int d, const int* feat, int mf, int K, const float* cent, void** fa, int64_t n) {
+  return oracle_kmeans_assign_range(d, feat, mf, K, cent, fa, 0, n);
+}
+
+int oracle_kmeans_assign_range(int d, const int* feat, int mf, int K, const float* cent, void** fa, int64_t i0,
+                               int64_t i1) {
   if (d < 1 || K < 1) return -1;
-  for (int64_t i = 0; i < n; ++i) {
+  for (int64_t i = i0; i < i1; ++i) {
     int best = 0;
     float best_d = 0.0f;
     for (int k = 0; k < K; ++k) {
@@ -373,10 +392,19 @@ static int64_t fixq(float x) {
  *          0 <= k < K; records with m outside [0, K) are left out.  The sums are
  *          integers, so they do not depend on the order of the records.
  */
+int oracle_kmeans_reduce_range(int d, const int* feat, int mf, int K, void** fa, int64_t i0, int64_t i1,
+                               int64_t* out);
+
 int oracle_kmeans_reduce(int d, const int* feat, int mf, int K, void** fa, int64_t n, int64_t* out) {
+  return oracle_kmeans_reduce_range(d, feat, mf, K, fa, 0, n, out);
+}
+
+/* The sums over records [i0, i1) alone (integer partial sums of ranges add up exactly). */
+int oracle_kmeans_reduce_range(int d, const int* feat, int mf, int K, void** fa, int64_t i0, int64_t i1,
+                               int64_t* out) {
   if (d < 1 || K < 1) return -1;
   for (int64_t k = 0; k < (int64_t)K * (d + 1); ++k) out[k] = 0;
-  for (int64_t i = 0; i < n; ++i) {
+  for (int64_t i = i0; i < i1; ++i) {
     int32_t m = I32(mf)[i];
     if (m < 0 || m >= K) continue;
     out[(int64_t)m * (d + 1)] += 1;

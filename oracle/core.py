@@ -49,6 +49,10 @@ def _get():
             lib.oracle_chain_grad.argtypes = [_I, _P, _P, _P, _I, _P, _P, _P, _I64]
             lib.oracle_kmeans_assign.argtypes = [_I, _P, _I, _I, _P, _P, _I64]
             lib.oracle_kmeans_reduce.argtypes = [_I, _P, _I, _I, _P, _I64, _P]
+            lib.oracle_section_range.argtypes = [_I, _P, _P, ctypes.c_uint64, ctypes.c_uint64, _I, _P, _P, _I64,
+                                                 _I64, _P]
+            lib.oracle_kmeans_assign_range.argtypes = [_I, _P, _I, _I, _P, _P, _I64, _I64]
+            lib.oracle_kmeans_reduce_range.argtypes = [_I, _P, _I, _I, _P, _I64, _I64, _P]
             _lib = lib
     return _lib
 
@@ -226,3 +230,74 @@ def chain_grad(sections, fields, c):
     if rc != 0:
         raise ValueError("chain_grad failed")
     return grads
+
+
+def _ranges(n, threads):
+    step = (n + threads - 1) // max(1, threads)
+    return [(i0, min(n, i0 + step)) for i0 in range(0, n, max(1, step))]
+
+
+def section_threads(sec, dtypes, fields, perm=None, threads=1):
+    """section() split over `threads` host threads by record range (the per-record code is the
+    same, so the result is bit-identical; ctypes releases the interpreter lock during each call).
+    A reduce section's partial sums of the ranges are added (exact: integers)."""
+    from concurrent.futures import ThreadPoolExecutor
+    n = fields[0].shape[0]
+    for a in fields:
+        assert a.flags.c_contiguous and a.shape[0] == n
+    fa = _ptrs(fields)
+    dt = _i32(dtypes)
+    lib = _get()
+    if sec.op in ("assign", "reduce"):
+        feats, mf, K = kmeans_features(sec, dtypes)
+        fe = _i32(feats)
+        if sec.op == "assign":
+            cent = np.ascontiguousarray(np.asarray(sec.table, dtype=np.float32))
+            work = lambda r: lib.oracle_kmeans_assign_range(len(feats), fe.ctypes.data, mf, K, cent.ctypes.data, fa,
+                                                            r[0], r[1])
+        else:
+            parts = []
+
+            def work(r):
+                out = np.zeros((K, len(feats) + 1), dtype=np.int64)
+                rc = lib.oracle_kmeans_reduce_range(len(feats), fe.ctypes.data, mf, K, fa, r[0], r[1], out.ctypes.data)
+                parts.append(out)
+                return rc
+    else:
+        args = _i32(list(sec.args) + [0] * (8 - len(sec.args)))
+        par = np.ascontiguousarray(np.asarray(list(sec.params) + [0.0] * (4 - len(sec.params)), dtype=np.float32))
+        pp = np.ascontiguousarray(perm, dtype=np.int32).ctypes.data if sec.op == "gather" else None
+        work = lambda r: lib.oracle_section_range(OPS[sec.op], args.ctypes.data, par.ctypes.data, _mask(sec.read),
+                                                  _mask(sec.write), len(dtypes), dt.ctypes.data, fa, r[0], r[1], pp)
+    with ThreadPoolExecutor(max_workers=max(1, threads)) as ex:
+        rcs = list(ex.map(work, _ranges(n, threads)))
+    if any(rcs):
+        raise ValueError("oracle section %r failed" % sec.op)
+    if sec.op == "reduce":
+        return sum(parts) if parts else np.zeros((kmeans_features(sec, dtypes)[2], 1), dtype=np.int64)
+    return None
+
+
+def remap_threads(n, dtypes, src_groups, src_bufs, dst_groups, threads=1):
+    """remap() split over host threads by record range (each range a slice of every buffer)."""
+    from concurrent.futures import ThreadPoolExecutor
+    s_stride, _, _ = layout_info(dtypes, src_groups)
+    d_stride, _, _ = layout_info(dtypes, dst_groups)
+    dst = [np.empty(n * st, dtype=np.uint8) for st in d_stride]
+    srcb = [np.ascontiguousarray(b).view(np.uint8).reshape(-1) for b in src_bufs]
+    F = len(dtypes)
+    sl, sf = _i32([len(g) for g in src_groups]), _i32([f for g in src_groups for f in g])
+    dl, df = _i32([len(g) for g in dst_groups]), _i32([f for g in dst_groups for f in g])
+    dt = _i32(dtypes)
+    lib = _get()
+
+    def work(r):
+        i0, i1 = r
+        sp = _ptrs([b[i0 * st:i1 * st] for b, st in zip(srcb, s_stride)])
+        dp = _ptrs([b[i0 * st:i1 * st] for b, st in zip(dst, d_stride)])
+        return lib.oracle_remap(i1 - i0, F, dt.ctypes.data, len(src_groups), sl.ctypes.data, sf.ctypes.data, sp,
+                                len(dst_groups), dl.ctypes.data, df.ctypes.data, dp)
+    with ThreadPoolExecutor(max_workers=max(1, threads)) as ex:
+        if any(ex.map(work, _ranges(n, threads))):
+            raise ValueError("bad layout")
+    return dst

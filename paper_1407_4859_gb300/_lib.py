@@ -102,6 +102,7 @@ SIGNATURES = {
     "adha_remap_batched": (ctypes.c_int, [_I32, ctypes.POINTER(adha_remap_desc), _P, ctypes.c_size_t, _P]),
     "adha_workspace_bytes": (ctypes.c_int, [_I32, ctypes.POINTER(adha_remap_desc), ctypes.POINTER(ctypes.c_size_t)]),
     "adha_batched_info": (ctypes.c_int, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I64)]),
+    "adha_gather_probe": (ctypes.c_int, [_P, _P, _P, _I64, _I32, _P]),
     "adha_tune_writeback": (ctypes.c_int, [_I32]),
     "adha_tune_remap_direct": (ctypes.c_int, [_I32]),
     "adha_tune_remap_pieces": (ctypes.c_int, [_I32]),

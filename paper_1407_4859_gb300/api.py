@@ -458,7 +458,14 @@ def _view_device(ptr, nbytes):
     return torch.as_tensor(_Cuda(), device="cuda")
 
 
-KINDS = {0: "remap", 1: "section", 2: "section_backward", 3: "batched_remap", 4: "fused"}
+KINDS = {0: "remap", 1: "section", 2: "section_backward", 3: "batched_remap", 4: "fused", 5: "gather_probe"}
+
+
+def adha_gather_probe(table, perm, out, rec_bytes=16, stream=None):
+    """out[i] = table[perm[i]] for every i (device tensors; elements of rec_bytes bytes)."""
+    n = perm.numel()
+    check(_lib.load().adha_gather_probe(table.data_ptr(), perm.data_ptr(), out.data_ptr(), int(n), int(rec_bytes),
+                                        _stream_ptr(stream)), "adha_gather_probe")
 OP_NAMES = {v: k for k, v in OPS.items()}
 
 
@@ -472,7 +479,7 @@ def adha_profile_stop(max_records=4096):
     n = ctypes.c_int32(0)
     check(_lib.load().adha_profile_stop(recs, max_records, ctypes.byref(n)), "adha_profile_stop")
     return [dict(kind=KINDS.get(recs[k].kind, recs[k].kind),
-                 op=recs[k].op if recs[k].kind == 4 else OP_NAMES.get(recs[k].op, recs[k].op),
+                 op=recs[k].op if recs[k].kind in (4, 5) else OP_NAMES.get(recs[k].op, recs[k].op),
                  bytes=recs[k].bytes, ms=recs[k].ms) for k in range(min(n.value, max_records))]
 
 

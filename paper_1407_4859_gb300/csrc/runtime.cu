@@ -306,6 +306,9 @@ int adha_measure(const adha_schema* schema, int64_t n, const adha_layout* in_lay
       if (std::find(where[r].begin(), where[r].end(), a) == where[r].end()) continue;
       const int k = runs[r].first, m = runs[r].second;
       auto run = [&] { return run_fused_layout(cand[a], pa.data(), &sections[k], m, n, stream); };
+      // each timing starts from the input's values: repeated runs of a window can drive them to
+      // infinities, and fused runs take slower exact paths for such values
+      auto fresh = [&] { return remap_layouts(in, in_p.data(), cand[a], pa.data(), n, stream, nullptr); };
       double ns = 0;
       if (flags & ADHA_MEASURE_AUTOTUNE) {
         // records per chunk x chunk buffers per warp: one buffer at 32 / 64 / 128, two at 64
@@ -314,7 +317,8 @@ int adha_measure(const adha_schema* schema, int64_t n, const adha_layout* in_lay
         int bR = 0, bB = 0;
         for (int q = 0; q < 4 && !rc; ++q) {
           set_fused_overrides(shapes[q][0], shapes[q][1]);
-          rc = time_ns(timer, stream, reps, run, &ns);
+          rc = fresh();
+          if (!rc) rc = time_ns(timer, stream, reps, run, &ns);
           if (!rc && (best < 0 || ns < best)) {
             best = ns;
             bR = shapes[q][0];
@@ -326,7 +330,8 @@ int adha_measure(const adha_schema* schema, int64_t n, const adha_layout* in_lay
         tuning_store(fused_tuning_key(cand[a], &sections[k], m, n), bR, bB);
         ns = best;
       } else {
-        rc = time_ns(timer, stream, reps, run, &ns);
+        rc = fresh();
+        if (!rc) rc = time_ns(timer, stream, reps, run, &ns);
       }
       t->fused_ns[((size_t)k * W + (m - 1)) * L + a] = ns;
     }

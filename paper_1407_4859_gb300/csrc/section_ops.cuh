@@ -531,46 +531,126 @@ __device__ __forceinline__ void run_record(const SecOp& so, const FieldRef* fr, 
 }
 
 // Fixed-point value of a REDUCE feature: x * 2^23 (exact) rounded to the nearest integer, ties to
-// even; 2^31 - 1 or -2^31 beyond the int32 range; 0 for NaN (the limits are tested explicitly, so
-// no hardware saturation rule is relied on).
+// even; 2^31 - 1 or -2^31 beyond the int32 range; 0 for NaN.  That is the float-to-int32
+// conversion PTX defines (cvt.rni.s32.f32: the result clamped to the range, NaN to 0), so one
+// conversion instruction does it.
 __device__ __forceinline__ long long fixq(float x) {
-  const float y = __fmul_rn(x, 8388608.0f);
-  if (y != y) return 0;
-  if (y >= 2147483648.0f) return 2147483647ll;
-  if (y < -2147483648.0f) return -2147483648ll;
-  return (long long)__float2int_rn(y);
+  return (long long)__float2int_rn(__fmul_rn(x, 8388608.0f));
+}
+
+// ASSIGN over the M records of each lane of a staged chunk (r = lane + 32m), for K clusters:
+// feature by feature, its chunk offsets are looked up once for the lane's M records and its K
+// centroid coordinates come from the CTA's transposed copy (cT[j*8 + k], two 16-byte broadcast
+// loads); the K x M distances are carried in registers (the per-record rule, in the same order).
+template <int M, int K>
+__device__ __forceinline__ void assign_chunk_k(const SecOp& so, const FieldRef* fr, uint8_t* stage, int64_t i0,
+                                               int lane, const float* cT) {
+  const int j0 = so.rd_off[ADHA_F32], d = so.rd_off[ADHA_F32 + 1] - j0;
+  float D[K][M];
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int m = 0; m < M; ++m) D[k][m] = 0.0f;
+  for (int j = 0; j < d; ++j) {
+    const FieldRef& F = fr[so.rd[j0 + j]];
+    const uint8_t* p = stage + F.s0 + lane * F.ss;
+    const int step = 32 * F.ss;
+    float x[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) x[m] = *reinterpret_cast<const float*>(p + m * step);
+    const float4 c0 = *reinterpret_cast<const float4*>(cT + j * kMaxClusters);
+    const float4 c1 = *reinterpret_cast<const float4*>(cT + j * kMaxClusters + 4);
+    const float c[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        const float df = __fsub_rn(x[m], c[k]);
+        D[k][m] = __fadd_rn(D[k][m], __fmul_rn(df, df));
+      }
+  }
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    int best = 0;
+    float bd = D[0][m];
+#pragma unroll
+    for (int k = 1; k < K; ++k)
+      if (D[k][m] < bd) {
+        bd = D[k][m];
+        best = k;
+      }
+    const int r = lane + 32 * m;
+    StagedRec{fr, stage, r, i0 + r}.template st<int32_t>(so.arg[0], best);
+  }
+}
+
+template <int M>
+__device__ __forceinline__ void assign_chunk(const SecOp& so, const FieldRef* fr, uint8_t* stage, int64_t i0, int lane,
+                                             const float* cT) {
+  switch (so.arg[1]) {   // K, uniform over the launch
+    case 1: assign_chunk_k<M, 1>(so, fr, stage, i0, lane, cT); break;
+    case 2: assign_chunk_k<M, 2>(so, fr, stage, i0, lane, cT); break;
+    case 3: assign_chunk_k<M, 3>(so, fr, stage, i0, lane, cT); break;
+    case 4: assign_chunk_k<M, 4>(so, fr, stage, i0, lane, cT); break;
+    case 5: assign_chunk_k<M, 5>(so, fr, stage, i0, lane, cT); break;
+    case 6: assign_chunk_k<M, 6>(so, fr, stage, i0, lane, cT); break;
+    case 7: assign_chunk_k<M, 7>(so, fr, stage, i0, lane, cT); break;
+    default: assign_chunk_k<M, 8>(so, fr, stage, i0, lane, cT); break;
+  }
+}
+
+// Where a REDUCE lane finds its feature (lane j = feature j, if j < d) and the membership in a
+// staged chunk; looked up once per kernel, since the lanes index the field table differently.
+struct ReduceLane {
+  int d, K;
+  int sx, ssx, sm, ssm;   // chunk-buffer offset and stride of the lane's feature and of the membership
+  int skew;               // one-field feature slice: the lane starts at its own record (spread banks)
+};
+
+__device__ __forceinline__ ReduceLane reduce_lane(const SecOp& so, const FieldRef* fr, int lane) {
+  ReduceLane q;
+  const int j0 = so.rd_off[ADHA_F32];
+  q.d = so.rd_off[ADHA_F32 + 1] - j0;
+  q.K = so.arg[1];
+  const FieldRef& Fm = fr[so.arg[0]];
+  q.sm = Fm.s0;
+  q.ssm = Fm.ss;
+  q.sx = q.ssx = 0;
+  if (lane < q.d) {
+    const FieldRef& Fx = fr[so.rd[j0 + lane]];
+    q.sx = Fx.s0;
+    q.ssx = Fx.ss;
+  }
+  q.skew = q.ssx == 4 ? lane : 0;
+  return q;
 }
 
 // REDUCE over the R = 32*M records of a staged chunk.  Counts: lane = record, one ballot per
 // cluster.  Sums: lane j = feature j, its column of the warp's K x 32 accumulators (int64, shared
-// memory) updated record by record; a one-field feature slice is walked starting at the lane's
-// own record so that the lanes' loads fall on different banks.  Integer sums: any order gives
-// the same result.
+// memory) updated record by record.  Integer sums: any order gives the same result.
 template <int M>
-__device__ __forceinline__ void reduce_chunk(const SecOp& so, const FieldRef* fr, const uint8_t* stage, int lane,
-                                             long long* acc, unsigned long long* cnt) {
+__device__ __forceinline__ void reduce_chunk(const ReduceLane& q, const uint8_t* stage, int lane, long long* acc,
+                                             unsigned long long* cnt) {
   constexpr int R = 32 * M;
-  const int K = so.arg[1];
-  const FieldRef& Fm = fr[so.arg[0]];
 #pragma unroll
   for (int m = 0; m < M; ++m) {
-    const int mm = *reinterpret_cast<const int32_t*>(stage + Fm.s0 + (lane + 32 * m) * Fm.ss);
+    const int mm = *reinterpret_cast<const int32_t*>(stage + q.sm + (lane + 32 * m) * q.ssm);
 #pragma unroll
     for (int k = 0; k < kMaxClusters; ++k)
-      if (k < K) cnt[k] += (unsigned long long)__popc(__ballot_sync(0xFFFFFFFFu, mm == k));
+      if (k < q.K) cnt[k] += (unsigned long long)__popc(__ballot_sync(0xFFFFFFFFu, mm == k));
   }
-  const int j0 = so.rd_off[ADHA_F32], d = so.rd_off[ADHA_F32 + 1] - j0;
-  if (lane < d) {
-    const FieldRef& Fx = fr[so.rd[j0 + lane]];
-    const int sx = Fx.s0, ssx = Fx.ss, sm = Fm.s0, ssm = Fm.ss;
-    const int skew = ssx == 4 ? lane : 0;
+  if (lane < q.d) {
     long long* col = acc + lane;
+    const uint8_t* pm = stage + q.sm;
+    const uint8_t* px = stage + q.sx;
 #pragma unroll 4
-    for (int q = 0; q < R; ++q) {
-      const int r = (q + skew) & (R - 1);
-      const int mm = *reinterpret_cast<const int32_t*>(stage + sm + r * ssm);
-      const long long v = fixq(*reinterpret_cast<const float*>(stage + sx + r * ssx));
-      if ((unsigned)mm < (unsigned)K) col[mm * 32] += v;
+    for (int i = 0; i < R; ++i) {
+      const int r = (i + q.skew) & (R - 1);
+      const int mm = *reinterpret_cast<const int32_t*>(pm + r * q.ssm);
+      const long long v = fixq(*reinterpret_cast<const float*>(px + r * q.ssx));
+      // a membership outside [0, K) goes to the scratch row kMaxClusters, never read back
+      const int row = (unsigned)mm < (unsigned)q.K ? mm : kMaxClusters;
+      col[row * 32] += v;
     }
   }
 }

@@ -35,10 +35,12 @@ __global__ void __launch_bounds__(kThreads) section_kernel(const __grid_constant
   // REDUCE: the warp's K x 32 int64 sums after the chunk buffers, its counts in registers
   long long* acc = nullptr;
   unsigned long long cnt[OP == ADHA_OP_REDUCE ? kMaxClusters : 1];
+  ReduceLane rq{};
   if constexpr (OP == ADHA_OP_REDUCE) {
+    rq = reduce_lane(a.s, a.f, lane);
     acc = reinterpret_cast<long long*>(smem + kSectionTable + (size_t)kWarps * 2 * a.in_bytes) +
-          (size_t)warp * kMaxClusters * 32;
-    for (int k = lane; k < kMaxClusters * 32; k += 32) acc[k] = 0;
+          (size_t)warp * (kMaxClusters + 1) * 32;
+    for (int k = lane; k < (kMaxClusters + 1) * 32; k += 32) acc[k] = 0;
 #pragma unroll
     for (int k = 0; k < kMaxClusters; ++k) cnt[k] = 0;
   }
@@ -46,6 +48,17 @@ __global__ void __launch_bounds__(kThreads) section_kernel(const __grid_constant
     sp[k] = a.load[k].ptr;
     send[k] = a.load[k].start + R * a.load[k].stride;
     wback[k] = a.writeback[k];
+  }
+  // ASSIGN: the centroids, transposed (cT[j*8 + k]; zero for k >= K), after the chunk buffers
+  float* cT = nullptr;
+  if constexpr (OP == ADHA_OP_ASSIGN) {
+    cT = reinterpret_cast<float*>(smem + kSectionTable + (size_t)kWarps * 2 * a.in_bytes);
+    const int K = a.s.arg[1], d = a.s.rd_off[ADHA_F32 + 1] - a.s.rd_off[ADHA_F32];
+    const float* cent = static_cast<const float*>(a.s.aux);
+    for (int t = tid; t < d * kMaxClusters; t += kThreads) {
+      const int j = t / kMaxClusters, k = t - j * kMaxClusters;
+      cT[t] = k < K ? __ldg(cent + k * d + j) : 0.0f;
+    }
   }
   __syncthreads();
 
@@ -73,7 +86,9 @@ __global__ void __launch_bounds__(kThreads) section_kernel(const __grid_constant
     __syncwarp();
     const int64_t i0 = c * R;
     if constexpr (OP == ADHA_OP_REDUCE) {
-      reduce_chunk<M>(a.s, a.f, cur, lane, acc, cnt);
+      reduce_chunk<M>(rq, cur, lane, acc, cnt);
+    } else if constexpr (OP == ADHA_OP_ASSIGN) {
+      assign_chunk<M>(a.s, a.f, cur, i0, lane, cT);
     } else if (OP == ADHA_OP_MIX && VEC) {
       mix_chunk_vec<M>(a.s, a.f, cur, i0, lane);
     } else if (VEC) {
@@ -186,8 +201,9 @@ __global__ void __launch_bounds__(kThreads) backward_kernel(const __grid_constan
 }
 
 size_t section_smem_bytes(const SectionArgs& a) {
-  const size_t acc = a.s.op == ADHA_OP_REDUCE ? (size_t)kWarps * kMaxClusters * 32 * 8 : 0;
-  return kSectionTable + (size_t)kWarps * 2 * a.in_bytes + acc;
+  const size_t acc = a.s.op == ADHA_OP_REDUCE ? (size_t)kWarps * (kMaxClusters + 1) * 32 * 8 : 0;   // + scratch row
+  const size_t cent = a.s.op == ADHA_OP_ASSIGN ? (size_t)kMaxFields * kMaxClusters * 4 : 0;
+  return kSectionTable + (size_t)kWarps * 2 * a.in_bytes + acc + cent;
 }
 
 template <int OP, int M, bool VEC>

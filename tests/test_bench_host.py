@@ -50,3 +50,27 @@ def test_reference_arm_prints_the_contract_line():
                            "d2h_bytes_per_step": 0}
     for key in ("metric", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling"):
         assert key in line
+
+
+def test_top_plans_are_the_cheapest_by_model_cost():
+    """bench.top_plans (the exhaustive set's plans of lowest model cost) against enumeration of
+    every layout sequence on random small cost tables: the same costs, each plan's cost correct."""
+    import itertools
+    import random
+    for seed in range(20):
+        rng = random.Random(seed)
+        S, L, K = rng.randrange(1, 5), rng.randrange(1, 5), rng.randrange(1, 12)
+        sec = [[rng.randrange(0, 30) for _ in range(L)] for _ in range(S)]
+        rem = [[0 if a == b else rng.randrange(0, 25) for b in range(L + 1)] for a in range(L + 1)]
+
+        def cost(seq):
+            c, prev = 0, L
+            for k, l in enumerate(seq):
+                c += rem[prev][l] + sec[k][l]
+                prev = l
+            return c
+        every = sorted(cost(s) for s in itertools.product(range(L), repeat=S))
+        got = bench.top_plans(sec, rem, K)
+        assert [c for c, _ in got] == every[:K]
+        assert all(cost(seq) == c for c, seq in got)
+        assert len({tuple(seq) for _, seq in got}) == len(got)
