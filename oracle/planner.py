@@ -210,3 +210,172 @@ def pdl_dp_fused(sec_cost, remap_cost, fused_cost, max_window, return_to_input=F
         p, k = l, k - negm
     seq, win = _as_plan(windows, S)
     return rest[0][L], seq, win
+
+
+# ---------------------------------------------------------------------- PDL over a structured CFG
+# Paper Section 2: PDL builds a rooted DAG from the program's structured control-flow graph
+# (SCFG) and takes a shortest path through it.  The paper gives no cost rule for branches and
+# loops; the reading here: a program is a tree of regions
+#   ("sec", k)                       section k of the cost table,
+#   ("seq", [regions])               regions one after another (an empty one changes nothing),
+#   ("branch", [regions], [w])       one of the regions runs, region b with probability w[b]
+#                                    (the w sum to 1); the branches meet again at a merge point,
+#   ("loop", region, T)              the region runs T >= 1 times (a loop tested at its end),
+# (regions are lists or tuples, each a distinct object: plans are keyed by the region's identity)
+# and a plan gives a layout to every section, to every merge point and to every loop header
+# (the layout the data is in whenever an iteration starts); layout index L is the input layout,
+# which merge points and headers may also keep.  The cost is the expected time: every section
+# and every remap on the way weighted by how often it runs; a branch's path pays the remap from
+# its last layout to the merge point's; an iteration starts with the remap into the header's
+# layout (from the entry layout the first time, from the body's last layout after that).
+
+INF = float("inf")
+
+
+def scfg_nodes(tree):
+    """The regions of a tree in preorder: [(kind, payload)], children before their next sibling."""
+    out = []
+
+    def walk(t):
+        out.append(t)
+        if t[0] == "seq":
+            for c in t[1]:
+                walk(c)
+        elif t[0] == "branch":
+            for c in t[1]:
+                walk(c)
+        elif t[0] == "loop":
+            walk(t[1])
+    walk(tree)
+    return out
+
+
+def scfg_expected_cost(tree, layout, sec_cost, remap_cost, return_to_input=False):
+    """Expected cost of a plan: `layout` maps id(region) -> layout of that section / merge point /
+    loop header.  Evaluated by following the regions with their execution weights."""
+    L = len(sec_cost[0])
+
+    def run(t, cur):                  # (expected cost, layout afterwards)
+        kind = t[0]
+        if kind == "sec":
+            l = layout[id(t)]
+            return remap_cost[cur][l] + sec_cost[t[1]][l], l
+        if kind == "seq":
+            total = 0
+            for c in t[1]:
+                cost, cur = run(c, cur)
+                total += cost
+            return total, cur
+        if kind == "branch":
+            m = layout[id(t)]
+            total = 0
+            for c, w in zip(t[1], t[2]):
+                cost, out = run(c, cur)
+                total += w * (cost + remap_cost[out][m])
+            return total, m
+        f = layout[id(t)]             # loop header
+        body, T = t[1], t[2]
+        cost, out = run(body, f)
+        return remap_cost[cur][f] + T * cost + (T - 1) * remap_cost[out][f], out
+
+    total, out = run(tree, L)
+    if return_to_input:
+        total += remap_cost[out][L]
+    return total
+
+
+def pdl_scfg_exhaustive(tree, sec_cost, remap_cost, return_to_input=False):
+    """Brute force over every layout of every section (0..L-1), merge point and loop header
+    (0..L): the least expected cost."""
+    L = len(sec_cost[0])
+    nodes = [t for t in scfg_nodes(tree) if t[0] in ("sec", "branch", "loop")]
+    choices = [range(L) if t[0] == "sec" else range(L + 1) for t in nodes]
+    best = None
+    for assign in itertools.product(*choices):
+        cost = scfg_expected_cost(tree, {id(t): l for t, l in zip(nodes, assign)}, sec_cost, remap_cost,
+                                  return_to_input)
+        if best is None or cost < best:
+            best = cost
+    return best
+
+
+def _minplus(A, B):
+    n, m, k = len(A), len(B[0]), len(B)
+    return [[min(A[i][q] + B[q][j] for q in range(k)) for j in range(m)] for i in range(n)]
+
+
+def pdl_scfg_dp(tree, sec_cost, remap_cost, return_to_input=False):
+    """Shortest expected path over the SCFG by dynamic programming on the region tree: every
+    region gets a matrix C[p][q] = least expected cost of running it entered in layout p and
+    left in layout q (0..L, L = input layout).  A section: the remap into its layout plus its
+    cost; a sequence: the min-plus product of its regions' matrices; a branch: for a merge
+    layout q, the sum over branches of w_b * min over the branch's last layout (its matrix plus
+    the remap to q); a loop with header f: remap into f, T times the body from f, T - 1 remaps
+    from the body's last layout back to f, the least over f.  Returns (least expected cost,
+    {id(region): layout}) for one best plan."""
+    L = len(sec_cost[0])
+    N = L + 1
+    rem = remap_cost
+    memo = {}
+
+    def mat(t):
+        key = id(t)
+        if key in memo:
+            return memo[key]
+        kind = t[0]
+        if kind == "sec":
+            k = t[1]
+            C = [[rem[p][q] + sec_cost[k][q] if q < L else INF for q in range(N)] for p in range(N)]
+        elif kind == "seq":
+            C = [[0 if p == q else INF for q in range(N)] for p in range(N)]
+            for c in t[1]:
+                C = _minplus(C, mat(c))
+        elif kind == "branch":
+            C = [[0.0] * N for _ in range(N)]
+            for c, w in zip(t[1], t[2]):
+                B = mat(c)
+                for p in range(N):
+                    for q in range(N):
+                        C[p][q] += w * min(B[p][r] + rem[r][q] for r in range(N))
+        else:
+            B, T = mat(t[1]), t[2]
+            C = [[min(rem[p][f] + T * B[f][e] + (T - 1) * rem[e][f] for f in range(N)) for e in range(N)]
+                 for p in range(N)]
+        memo[key] = C
+        return C
+
+    plan = {}
+
+    def pick(t, p, q):   # record the choices of one best path through t entered in p, left in q
+        kind = t[0]
+        if kind == "sec":
+            plan[id(t)] = q
+        elif kind == "seq":
+            cs = t[1]
+            # prefix products, then walk back choosing each intermediate layout
+            pref = [[[0 if a == b else INF for b in range(N)] for a in range(N)]]
+            for c in cs:
+                pref.append(_minplus(pref[-1], mat(c)))
+            cur = q
+            for i in range(len(cs), 0, -1):
+                M = mat(cs[i - 1])
+                prev = min(range(N), key=lambda r: pref[i - 1][p][r] + M[r][cur])
+                pick(cs[i - 1], prev, cur)
+                cur = prev
+        elif kind == "branch":
+            plan[id(t)] = q
+            for c in t[1]:
+                B = mat(c)
+                r = min(range(N), key=lambda r: B[p][r] + rem[r][q])
+                pick(c, p, r)
+        else:
+            B, T = mat(t[1]), t[2]
+            f = min(range(N), key=lambda f: rem[p][f] + T * B[f][q] + (T - 1) * rem[q][f])
+            plan[id(t)] = f
+            pick(t[1], f, q)
+
+    C = mat(tree)
+    ends = [C[L][q] + (rem[q][L] if return_to_input else 0) for q in range(N)]
+    q = min(range(N), key=lambda q: ends[q])
+    pick(tree, L, q)
+    return ends[q], plan
