@@ -311,6 +311,43 @@ int adha_pdl_solve(const adha_cost_table* costs, int32_t return_to_input, int32_
 int adha_pdl_solve_fused(const adha_cost_table* costs, int32_t return_to_input, int32_t max_window,
                          int32_t* layout_of_section, int32_t* window_len, double* total_ns);
 
+/*
+ * PDL over a structured control-flow graph (paper Section 2: the rooted DAG is
+ * built from the program's SCFG).  The program is a tree of regions, one node
+ * each, children given by index:
+ *   ADHA_SCFG_SECTION  section `section` (a row of the cost table)
+ *   ADHA_SCFG_SEQ      its children in order (none: nothing runs)
+ *   ADHA_SCFG_BRANCH   one child runs, child b with probability weights[b]
+ *                      (>= 0, summing to 1); the children meet at a merge point
+ *   ADHA_SCFG_LOOP     its one child runs `trips` >= 1 times (tested at its end)
+ * A plan gives a layout to every section (a candidate, 0..n_layouts-1), to every
+ * merge point and to every loop header (a candidate, or n_layouts = the input
+ * layout: the layout the data is in when the branches meet / an iteration
+ * starts).  Its cost is the expected time: every section and remap weighted by
+ * how often it runs; each branch pays the remap from its last layout to the
+ * merge point's; each iteration starts with the remap into the header's layout
+ * (from the loop's entry layout the first time, from the body's last layout
+ * after that).  The least expected cost is found by a dynamic program over the
+ * tree (a matrix of costs entered in layout p and left in layout q per region:
+ * min-plus products for sequences, weighted sums for branches, the best header
+ * for loops); ties go to the smaller layout index.  Writes layout_of_node[i]
+ * (-1 for SEQ nodes) and the expected cost.  Every node must be reached from
+ * `root` exactly once (a tree) and n_nodes <= 4096; EINVAL otherwise.  Host only.
+ */
+enum { ADHA_SCFG_SECTION = 0, ADHA_SCFG_SEQ = 1, ADHA_SCFG_BRANCH = 2, ADHA_SCFG_LOOP = 3 };
+
+typedef struct {
+  int32_t kind;
+  int32_t section;            /* SECTION: row of the cost table                          */
+  int32_t n_children;         /* SEQ: >= 0; BRANCH: >= 1; LOOP: 1; SECTION: 0          */
+  const int32_t* children;    /* node indices (host)                                     */
+  const double* weights;      /* BRANCH: n_children probabilities (host)                 */
+  double trips;               /* LOOP: expected iterations, >= 1                          */
+} adha_scfg_node;
+
+int adha_pdl_solve_scfg(const adha_cost_table* costs, int32_t n_nodes, const adha_scfg_node* nodes, int32_t root,
+                        int32_t return_to_input, int32_t* layout_of_node, double* total_ns);
+
 /* ----------------------------------------------------------- measure and run */
 
 /* A program's layout plan and where its result ended up. */

@@ -65,6 +65,11 @@ class adha_remap_desc(ctypes.Structure):
                 ("src_ptrs", _PP), ("dst", ctypes.POINTER(adha_layout)), ("dst_ptrs", _PP)]
 
 
+class adha_scfg_node(ctypes.Structure):
+    _fields_ = [("kind", _I32), ("section", _I32), ("n_children", _I32), ("children", ctypes.POINTER(_I32)),
+                ("weights", ctypes.POINTER(ctypes.c_double)), ("trips", ctypes.c_double)]
+
+
 class AdhaError(RuntimeError):
     def __init__(self, code, fn, msg):
         super().__init__("%s failed with %s: %s" % (fn, CODES.get(code, code), msg))
@@ -103,6 +108,8 @@ SIGNATURES = {
     "adha_workspace_bytes": (ctypes.c_int, [_I32, ctypes.POINTER(adha_remap_desc), ctypes.POINTER(ctypes.c_size_t)]),
     "adha_batched_info": (ctypes.c_int, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I64)]),
     "adha_gather_probe": (ctypes.c_int, [_P, _P, _P, _I64, _I32, _P]),
+    "adha_pdl_solve_scfg": (ctypes.c_int, [ctypes.POINTER(adha_cost_table), _I32, ctypes.POINTER(adha_scfg_node), _I32,
+                                           _I32, ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_double)]),
     "adha_tune_writeback": (ctypes.c_int, [_I32]),
     "adha_tune_remap_direct": (ctypes.c_int, [_I32]),
     "adha_tune_remap_pieces": (ctypes.c_int, [_I32]),

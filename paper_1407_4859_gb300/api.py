@@ -357,6 +357,38 @@ def adha_pdl_solve_fused(costs, return_to_input=False, max_window=0):
     return tot.value, list(seq), list(win)
 
 
+SCFG_KINDS = {"sec": 0, "seq": 1, "branch": 2, "loop": 3}
+
+
+def adha_pdl_solve_scfg(costs, tree, return_to_input=False):
+    """PDL over a region tree of nested lists: ["sec", k], ["seq", [regions]],
+    ["branch", [regions], [weights]], ["loop", region, trips].  Returns (expected cost,
+    {id(region): layout}) with a layout for every section, merge point and loop header."""
+    order = []
+
+    def walk(t):
+        order.append(t)
+        kids = t[1] if t[0] in ("seq", "branch") else ([t[1]] if t[0] == "loop" else [])
+        for c in kids:
+            walk(c)
+    walk(tree)
+    index = {id(t): i for i, t in enumerate(order)}
+    keep = []
+    nodes = (_lib.adha_scfg_node * len(order))()
+    for i, t in enumerate(order):
+        kids = t[1] if t[0] in ("seq", "branch") else ([t[1]] if t[0] == "loop" else [])
+        ch = _i32_array([index[id(c)] for c in kids])
+        w = (ctypes.c_double * max(1, len(kids)))(*(t[2] if t[0] == "branch" else []))
+        keep += [ch, w]
+        nodes[i] = _lib.adha_scfg_node(SCFG_KINDS[t[0]], int(t[1]) if t[0] == "sec" else 0, len(kids), ch, w,
+                                       float(t[2]) if t[0] == "loop" else 0.0)
+    lay = (ctypes.c_int32 * len(order))()
+    tot = ctypes.c_double(0)
+    check(_lib.load().adha_pdl_solve_scfg(costs.ptr, len(order), nodes, 0, int(bool(return_to_input)), lay,
+                                          ctypes.byref(tot)), "adha_pdl_solve_scfg")
+    return tot.value, {id(t): lay[i] for i, t in enumerate(order) if t[0] != "seq"}
+
+
 def adha_measure_workspace_bytes(schema, n, in_layout, candidates, flags=0):
     return _lib.load().adha_measure_workspace_bytes_for(ctypes.byref(schema.c), int(n), ctypes.byref(in_layout.c),
                                                         candidates.ptr, int(flags))

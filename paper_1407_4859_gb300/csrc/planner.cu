@@ -223,11 +223,210 @@ int pdl_solve(const adha_cost_table* c, int return_to_input, int32_t* seq, doubl
   return 0;
 }
 
+// PDL over a structured control-flow graph: a cost matrix C[p][q] (N = L + 1 states, state L the
+// input layout) per region of the tree, entered in layout p and left in layout q; then one best
+// plan read back from the root with the choices of smallest index among equal costs.
+struct ScfgSolver {
+  const adha_cost_table* c;
+  const adha_scfg_node* nodes;
+  int L, N;
+  std::vector<std::vector<double>> mat;   // per node, N x N
+  std::vector<int32_t>* out;
+
+  double rem(int a, int b) const { return c->remap_ns[(size_t)a * N + b]; }
+  double sec(int k, int l) const { return c->section_ns[(size_t)k * L + l]; }
+
+  std::vector<double> identity() const {
+    std::vector<double> I((size_t)N * N, HUGE_VAL);
+    for (int p = 0; p < N; ++p) I[(size_t)p * N + p] = 0;
+    return I;
+  }
+  std::vector<double> minplus(const std::vector<double>& A, const std::vector<double>& B) const {
+    std::vector<double> C((size_t)N * N, HUGE_VAL);
+    for (int p = 0; p < N; ++p)
+      for (int q = 0; q < N; ++q) {
+        const double a = A[(size_t)p * N + q];
+        if (a == HUGE_VAL) continue;
+        for (int r = 0; r < N; ++r) {
+          const double v = a + B[(size_t)q * N + r];
+          if (v < C[(size_t)p * N + r]) C[(size_t)p * N + r] = v;
+        }
+      }
+    return C;
+  }
+
+  void build(int i) {   // children first
+    const adha_scfg_node& nd = nodes[i];
+    for (int j = 0; j < nd.n_children; ++j) build(nd.children[j]);
+    std::vector<double> C((size_t)N * N, HUGE_VAL);
+    if (nd.kind == ADHA_SCFG_SECTION) {
+      for (int p = 0; p < N; ++p)
+        for (int q = 0; q < L; ++q) C[(size_t)p * N + q] = rem(p, q) + sec(nd.section, q);
+    } else if (nd.kind == ADHA_SCFG_SEQ) {
+      C = identity();
+      for (int j = 0; j < nd.n_children; ++j) C = minplus(C, mat[nd.children[j]]);
+    } else if (nd.kind == ADHA_SCFG_BRANCH) {
+      std::fill(C.begin(), C.end(), 0.0);
+      for (int j = 0; j < nd.n_children; ++j) {
+        const std::vector<double>& B = mat[nd.children[j]];
+        const double w = nd.weights[j];
+        for (int p = 0; p < N; ++p)
+          for (int q = 0; q < N; ++q) {
+            double best = HUGE_VAL;
+            for (int r = 0; r < N; ++r) best = std::min(best, B[(size_t)p * N + r] + rem(r, q));
+            C[(size_t)p * N + q] += w * best;
+          }
+      }
+    } else {   // loop
+      const std::vector<double>& B = mat[nd.children[0]];
+      const double T = nd.trips;
+      for (int p = 0; p < N; ++p)
+        for (int e = 0; e < N; ++e) {
+          double best = HUGE_VAL;
+          for (int f = 0; f < N; ++f) best = std::min(best, rem(p, f) + T * B[(size_t)f * N + e] + (T - 1) * rem(e, f));
+          C[(size_t)p * N + e] = best;
+        }
+    }
+    mat[i] = std::move(C);
+  }
+
+  void pick(int i, int p, int q) {
+    const adha_scfg_node& nd = nodes[i];
+    if (nd.kind == ADHA_SCFG_SECTION) {
+      (*out)[i] = q;
+    } else if (nd.kind == ADHA_SCFG_SEQ) {
+      (*out)[i] = -1;
+      std::vector<std::vector<double>> pref(1, identity());
+      for (int j = 0; j < nd.n_children; ++j) pref.push_back(minplus(pref.back(), mat[nd.children[j]]));
+      int cur = q;
+      for (int j = nd.n_children; j >= 1; --j) {
+        const std::vector<double>& M = mat[nd.children[j - 1]];
+        int arg = 0;
+        double best = HUGE_VAL;
+        for (int r = 0; r < N; ++r) {
+          const double v = pref[j - 1][(size_t)p * N + r] + M[(size_t)r * N + cur];
+          if (v < best) {
+            best = v;
+            arg = r;
+          }
+        }
+        pick(nd.children[j - 1], arg, cur);
+        cur = arg;
+      }
+    } else if (nd.kind == ADHA_SCFG_BRANCH) {
+      (*out)[i] = q;
+      for (int j = 0; j < nd.n_children; ++j) {
+        const std::vector<double>& B = mat[nd.children[j]];
+        int arg = 0;
+        double best = HUGE_VAL;
+        for (int r = 0; r < N; ++r) {
+          const double v = B[(size_t)p * N + r] + rem(r, q);
+          if (v < best) {
+            best = v;
+            arg = r;
+          }
+        }
+        pick(nd.children[j], p, arg);
+      }
+    } else {
+      const std::vector<double>& B = mat[nd.children[0]];
+      const double T = nd.trips;
+      int arg = 0;
+      double best = HUGE_VAL;
+      for (int f = 0; f < N; ++f) {
+        const double v = rem(p, f) + T * B[(size_t)f * N + q] + (T - 1) * rem(q, f);
+        if (v < best) {
+          best = v;
+          arg = f;
+        }
+      }
+      (*out)[i] = arg;
+      pick(nd.children[0], arg, q);
+    }
+  }
+};
+
 }  // namespace adha
 
 using namespace adha;
 
 extern "C" {
+
+int adha_pdl_solve_scfg(const adha_cost_table* costs, int32_t n_nodes, const adha_scfg_node* nodes, int32_t root,
+                        int32_t return_to_input, int32_t* layout_of_node, double* total_ns) {
+  clear_error();
+  if (!costs || !nodes || !layout_of_node || !total_ns) return fail(ADHA_EINVAL, "NULL argument");
+  if (costs->n_sections < 1 || costs->n_layouts < 1 || !costs->section_ns || !costs->remap_ns)
+    return fail(ADHA_EINVAL, "empty cost table");
+  if (n_nodes < 1 || n_nodes > 4096) return fail(ADHA_EINVAL, "n_nodes = %d not in [1, 4096]", n_nodes);
+  if (root < 0 || root >= n_nodes) return fail(ADHA_EINVAL, "root %d is not a node", root);
+  if (int rc = check_costs(costs)) return rc;
+  // the nodes must form a tree below root, each reached once
+  std::vector<int> seen(n_nodes, 0), stack{root};
+  int reached = 0;
+  while (!stack.empty()) {
+    const int i = stack.back();
+    stack.pop_back();
+    if (seen[i]++) return fail(ADHA_EINVAL, "node %d is reached twice (the regions must form a tree)", i);
+    ++reached;
+    const adha_scfg_node& nd = nodes[i];
+    if (nd.n_children < 0 || (nd.n_children > 0 && !nd.children)) return fail(ADHA_EINVAL, "node %d: bad children", i);
+    switch (nd.kind) {
+      case ADHA_SCFG_SECTION:
+        if (nd.n_children != 0) return fail(ADHA_EINVAL, "section node %d has children", i);
+        if (nd.section < 0 || nd.section >= costs->n_sections)
+          return fail(ADHA_EINVAL, "node %d names section %d (the table has %d)", i, nd.section, costs->n_sections);
+        break;
+      case ADHA_SCFG_SEQ: break;
+      case ADHA_SCFG_BRANCH: {
+        if (nd.n_children < 1 || !nd.weights) return fail(ADHA_EINVAL, "branch node %d needs children and weights", i);
+        double sum = 0;
+        for (int j = 0; j < nd.n_children; ++j) {
+          if (!(nd.weights[j] >= 0) || std::isinf(nd.weights[j]))
+            return fail(ADHA_EINVAL, "branch node %d: weight %g", i, nd.weights[j]);
+          sum += nd.weights[j];
+        }
+        if (std::fabs(sum - 1.0) > 1e-9) return fail(ADHA_EINVAL, "branch node %d: weights sum to %.12g, not 1", i, sum);
+        break;
+      }
+      case ADHA_SCFG_LOOP:
+        if (nd.n_children != 1) return fail(ADHA_EINVAL, "loop node %d has %d children (needs its body)", i, nd.n_children);
+        if (!(nd.trips >= 1) || std::isinf(nd.trips)) return fail(ADHA_EINVAL, "loop node %d: trips = %g", i, nd.trips);
+        break;
+      default: return fail(ADHA_EINVAL, "node %d has kind %d", i, nd.kind);
+    }
+    for (int j = 0; j < nd.n_children; ++j) {
+      const int ch = nd.children[j];
+      if (ch < 0 || ch >= n_nodes) return fail(ADHA_EINVAL, "node %d: child %d is not a node", i, ch);
+      stack.push_back(ch);
+    }
+  }
+  std::vector<int32_t> out(n_nodes, -1);
+  ScfgSolver sv;
+  sv.c = costs;
+  sv.nodes = nodes;
+  sv.L = costs->n_layouts;
+  sv.N = sv.L + 1;
+  sv.mat.assign(n_nodes, {});
+  sv.out = &out;
+  sv.build(root);
+  const std::vector<double>& C = sv.mat[root];
+  int arg = 0;
+  double best = HUGE_VAL;
+  for (int q = 0; q < sv.N; ++q) {
+    const double v = C[(size_t)sv.L * sv.N + q] + (return_to_input ? sv.rem(q, sv.L) : 0.0);
+    if (v < best) {
+      best = v;
+      arg = q;
+    }
+  }
+  if (std::isinf(best)) return fail(ADHA_EINVAL, "cost table: every plan has an infinite cost");
+  sv.pick(root, sv.L, arg);
+  for (int i = 0; i < n_nodes; ++i) layout_of_node[i] = out[i];
+  *total_ns = best;
+  return 0;
+}
+
 
 int adha_ods(const adha_schema* schema, const adha_section* sections, int32_t n_sec, int32_t cap_bytes,
              int32_t* n_groups, int32_t* group_len, int32_t* fields) {

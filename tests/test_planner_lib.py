@@ -167,3 +167,54 @@ def test_fused_run_validation_without_gpu(P):
         with pytest.raises(AdhaError) as e:
             P.adha_run_sections_fused(S, 64, L, bufs, P.Sections(secs, None) if secs else P.Sections([]), stream=0)
         assert e.value.code == ADHA_EINVAL
+
+
+def _scfg_table(P, sec, rem):
+    t = P.adha_cost_table_create(len(sec), len(sec[0]))
+    t.set(sec, rem)
+    return t
+
+
+@pytest.mark.parametrize("seed", range(60))
+def test_library_scfg_pdl_equals_oracle(P, seed):
+    """adha_pdl_solve_scfg on random region trees (branches, loops, empty branches): the oracle's
+    DP cost (itself equal to brute force), and a plan whose expected cost, evaluated by the oracle,
+    is that cost; with the same tie rule the plan is the oracle's."""
+    from test_oracle_scfg import _random_tree
+    rng = random.Random(7000 + seed)
+    S, L = rng.randrange(1, 6), rng.randrange(1, 5)
+    sec = [[rng.randrange(0, 300) for _ in range(L)] for _ in range(S)]
+    rem = [[0 if a == b else rng.randrange(0, 250) for b in range(L + 1)] for a in range(L + 1)]
+    tree = _random_tree(rng, S)
+    back = seed % 3 == 0
+    want, oplan = oracle.pdl_scfg_dp(tree, sec, rem, back)
+    got, plan = P.adha_pdl_solve_scfg(_scfg_table(P, sec, rem), tree, back)
+    assert got == want
+    assert oracle.scfg_expected_cost(tree, plan, sec, rem, back) == got
+    assert plan == oplan
+
+
+def test_library_scfg_large_matches_oracle(P):
+    from test_oracle_scfg import _random_tree
+    rng = random.Random(99)
+    S, L = 12, 24
+    sec = [[rng.randrange(1000, 50000) for _ in range(L)] for _ in range(S)]
+    rem = [[0 if a == b else rng.randrange(0, 90000) for b in range(L + 1)] for a in range(L + 1)]
+    tree = _random_tree(rng, S)
+    want, oplan = oracle.pdl_scfg_dp(tree, sec, rem)
+    got, plan = P.adha_pdl_solve_scfg(_scfg_table(P, sec, rem), tree)
+    assert got == want and plan == oplan
+
+
+def test_library_scfg_rejects_bad_trees(P):
+    from paper_1407_4859_gb300._lib import AdhaError, ADHA_EINVAL
+    t = _scfg_table(P, [[1, 2], [3, 4]], [[0, 1, 1], [1, 0, 1], [1, 1, 0]])
+    shared = ["sec", 0]
+    for tree in (["sec", 5],                                    # no such section
+                 ["branch", [["sec", 0], ["sec", 1]], [0.5, 0.25]],  # weights do not sum to 1
+                 ["branch", [["sec", 0]], [-0.0 - 1.0]],           # negative weight
+                 ["loop", ["sec", 0], 0.5],                        # fewer than one trip
+                 ["seq", [shared, shared]]):                       # one region reached twice
+        with pytest.raises(AdhaError) as e:
+            P.adha_pdl_solve_scfg(t, tree)
+        assert e.value.code == ADHA_EINVAL, tree
