@@ -443,9 +443,17 @@ def program_run(P, torch, wl, args, tag, world=1, dist=None, local=0, autotune=T
 
     compare_d = None
     if compare:
+        # a plan whose first layout is the input's runs in place on the input buffers: every
+        # compared run starts again from the batch's values (restored outside the timed events)
+        pristine = in_buf[0].clone()
+
+        def restore():
+            in_buf[0].copy_(pristine)
+
         def prog_ms(fixed, reps_=3):
             ts = []
             for r in range(reps_ + 1):
+                restore()
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record(stream)
                 P.adha_run_program(S, n, AOS, in_buf, secs, cand, costs=costs, fixed=fixed, workspace=ws,
@@ -489,7 +497,9 @@ def program_run(P, torch, wl, args, tag, world=1, dist=None, local=0, autotune=T
                      "paper_context": PAPER_CONTEXT}
         if fuse:
             compare_d["fused"] = fused_comparison(P, torch, S, n, AOS, in_buf, secs, cand, costs, ws, stream, fuse,
-                                                  adha_ms, t_aos, t_soa, layouts)
+                                                  adha_ms, t_aos, t_soa, layouts, restore)
+        restore()
+        del pristine
 
     cpu_d = cpu_baseline(wl, plan_layouts, min(n, 1 << 22)) if cpu else None
     line = {
@@ -517,11 +527,13 @@ def program_run(P, torch, wl, args, tag, world=1, dist=None, local=0, autotune=T
     return line
 
 
-def fused_comparison(P, torch, S, n, AOS, in_buf, secs, cand, costs, ws, stream, fuse, adha_ms, t_aos, t_soa, layouts):
+def fused_comparison(P, torch, S, n, AOS, in_buf, secs, cand, costs, ws, stream, fuse, adha_ms, t_aos, t_soa, layouts,
+                     restore):
     """The program under PDL with combine nodes (runs of up to `fuse` sections fused in one layout,
     at their measured costs), against the plain ADHA plan and the uniform layouts."""
     opts = P.PlanOpts(CAPS, fuse_window=fuse)
     nsec = len(secs)
+    restore()
     plan = P.adha_run_program(S, n, AOS, in_buf, secs, cand, costs=costs, opts=opts, workspace=ws, stream=stream)
     seq = list(plan.layout_of_section[:nsec])
     win = list(plan.window_len[:nsec])
@@ -529,6 +541,7 @@ def fused_comparison(P, torch, S, n, AOS, in_buf, secs, cand, costs, ws, stream,
     ts = []
     recs = []
     for r in range(4):   # the solved plan, run as a fixed plan (as the other programs are timed)
+        restore()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         if r == 3:
             P.adha_profile_start(256)

@@ -564,6 +564,17 @@ void fill_secop(const Layout& L, const adha_section* s, SecOp* o) {
   o->wr_off[4] = (int8_t)nw;
   for (int k = 0; k < kMaxFields; ++k) o->rd_s0[k] = o->wr_s0[k] = -1;
   o->aux = s->aux;
+  // a gather whose fields read through perm fill one 16-byte struct reads them with one load
+  o->gvec = 0;
+  if (s->op == ADHA_OP_GATHER) {
+    const int g = L.group_of[s->arg[3]];
+    bool one = L.stride[g] == 16;
+    for (int k = 3; k < 7 && one; ++k) one = L.group_of[s->arg[k]] == g;
+    if (one) {
+      o->gvec = 1;
+      for (int k = 0; k < 4; ++k) o->gidx[k] = (int8_t)(L.offset_of[s->arg[3 + k]] / 4);
+    }
+  }
 }
 
 void fill_secop_offsets(SecOp* o, const FieldRef* f) {

@@ -115,6 +115,8 @@ struct SecOp {
   int16_t rd_s0[kMaxFields];   // chunk-buffer offset (FieldRef::s0) of each listed field, -1 if not staged
   int16_t wr_s0[kMaxFields];
   const void* aux;             // ASSIGN: centroids; REDUCE: the int64 sums
+  int8_t gvec;                 // GATHER: px, py, pz, q share one 16-byte struct (one 16-byte load at perm[i])
+  int8_t gidx[4];              // GATHER with gvec: the word of px, py, pz, q in that struct
 };
 
 constexpr int kMaxClusters = 8;   // K of the ASSIGN and REDUCE sections

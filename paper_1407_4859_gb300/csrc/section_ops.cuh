@@ -482,10 +482,23 @@ __device__ __forceinline__ void run_record(const SecOp& so, const FieldRef* fr, 
     rec.template st<uint32_t>(g[0], ((fl << 1) | bit) & 255u);
   } else if (OP == ADHA_OP_GATHER) {
     const int64_t j = pj;
-    const float c = __fmul_rn(so.par[0], gld<float>(fr, g[6], j));
+    float pv[4];   // px, py, pz, q of record j
+    if (so.gvec) {   // all four in one 16-byte struct: one load
+      const uint8_t* base = fr[g[3]].g - 4 * so.gidx[0];
+      const uint4 w = __ldg(reinterpret_cast<const uint4*>(base + j * 16));
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const int q = so.gidx[a];
+        pv[a] = __uint_as_float(q == 0 ? w.x : q == 1 ? w.y : q == 2 ? w.z : w.w);
+      }
+    } else {
+#pragma unroll
+      for (int a = 0; a < 4; ++a) pv[a] = gld<float>(fr, g[3 + a], j);
+    }
+    const float c = __fmul_rn(so.par[0], pv[3]);
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
-      const float d = __fsub_rn(gld<float>(fr, g[3 + ax], j), 0.5f);
+      const float d = __fsub_rn(pv[ax], 0.5f);
       rec.template st<float>(g[ax], __fadd_rn(rec.template ld<float>(g[ax]), __fmul_rn(c, d)));
     }
   } else if (OP == ADHA_OP_KICK) {

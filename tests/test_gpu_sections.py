@@ -234,3 +234,26 @@ def test_mix_fp64_special_values(P, groups, R):
             assert np.array_equal(got[f].view(np.uint8), want[f].view(np.uint8)), "fused field %d" % f
     finally:
         P.adha_tune_override(0)
+
+
+@pytest.mark.parametrize("order", [[0, 1, 2, 7], [7, 2, 0, 1], [1, 7, 0, 2]])
+@pytest.mark.parametrize("n", [1, 33, 70001])
+def test_gather_reads_one_struct_through_perm(P, order, n):
+    """The gather whose four fields read at perm[i] (pos xyz, charge) fill one 16-byte struct loads
+    them with one 16-byte load, in any order within the struct; bit-exact against the oracle, in
+    the fused kernel too."""
+    wl = synth.config3(n=n)
+    perm = wl.perm()
+    rest = [f for f in range(12) if f not in order]
+    for groups in ([order] + [[f] for f in rest], [order, rest]):
+        _check_section(P, wl, wl.sections[4], groups, perm)
+        fields = oracle.initial_fields(wl)
+        bufs = to_device(n, wl.dtypes, groups, fields)
+        run = [wl.sections[4], wl.sections[5]]       # gather then kick, fused
+        P.adha_run_sections_fused(P.Schema(wl.dtypes), n, P.Layout(groups), bufs,
+                                  P.Sections(run, torch.from_numpy(perm).cuda()))
+        torch.cuda.synchronize()
+        want = [a.copy() for a in fields]
+        for s in run:
+            oracle.section(s, wl.dtypes, want, perm)
+        assert_fields_equal(from_device(n, wl.dtypes, groups, bufs), want, "fused gather in %r" % (groups,))
