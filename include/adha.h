@@ -50,7 +50,7 @@ enum {
   ADHA_EINVAL = -1,   /* bad argument: the message names it                      */
   ADHA_ENOMEM = -2,   /* workspace too small, or host allocation failed          */
   ADHA_ECUDA = -3,    /* a CUDA runtime call failed: the message has its text    */
-  ADHA_ETIMEOUT = -4, /* a kernel gave up waiting for its copies (see adha_device_status) */
+  ADHA_ETIMEOUT = -4, /* reserved for a bounded wait that ran out; no kernel here waits on anything */
   ADHA_ENOTIMPL = -5  /* not supported by the library or the device              */
 };
 
@@ -657,13 +657,6 @@ int adha_profile_start(int32_t max_records);
 /* Stops recording, waits for the recorded launches and copies up to
  * max_records of them to out; *n_records = how many were recorded. */
 int adha_profile_stop(adha_launch_record* out, int32_t max_records, int32_t* n_records);
-
-/*
- * Reads and clears the device status word that kernels set when a bounded
- * wait for their own copies ran out (then they stop early and their output is
- * incomplete).  Synchronizes `stream`.  *status = 0 when nothing happened.
- */
-int adha_device_status(adha_stream stream, int32_t* status);
 
 /* Thread-local message of the last failing call on this thread ("" if none). */
 const char* adha_last_error(void);

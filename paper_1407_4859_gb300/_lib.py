@@ -93,7 +93,6 @@ SIGNATURES = {
                                                ctypes.POINTER(adha_section), _I32, _P]),
     "adha_section_backward": (ctypes.c_int, [ctypes.POINTER(adha_schema), _I64, ctypes.POINTER(adha_layout), _PP,
                                              _PP, ctypes.POINTER(adha_section), _P, _P]),
-    "adha_device_status": (ctypes.c_int, [_P, ctypes.POINTER(_I32)]),
     "adha_tune_override": (ctypes.c_int, [_I32]),
     "adha_batched_create": (ctypes.c_int, [_I32, ctypes.POINTER(adha_remap_desc), _I32, _P, ctypes.POINTER(_P)]),
     "adha_batched_workspace_bytes": (ctypes.c_size_t, [_P]),

@@ -167,12 +167,6 @@ def adha_tune_import(text):
     check(_lib.load().adha_tune_import(text.encode()), "adha_tune_import")
 
 
-def adha_device_status(stream=None):
-    v = ctypes.c_int32(0)
-    check(_lib.load().adha_device_status(_stream_ptr(stream), ctypes.byref(v)), "adha_device_status")
-    return v.value
-
-
 def remap(schema, n, src_layout, src_bufs, dst_layout, stream=None):
     """Remap into freshly allocated buffers of dst_layout; returns them."""
     dst = alloc_layout(schema, dst_layout, n, device=src_bufs[0].device)

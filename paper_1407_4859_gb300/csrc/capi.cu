@@ -35,30 +35,13 @@ void clear_error() { t_err.clear(); }
 
 // ------------------------------------------------------------------ device state
 // Status word set by kernels whose bounded waits ran out (one per device, module memory).
-__device__ int g_status_word;
-
 static std::mutex g_mu;
-static int* g_status_ptr[256];
 static int g_sms[256];
 
 static int current_device(int* dev) {
   cudaError_t e = cudaGetDevice(dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   if (*dev < 0 || *dev >= 256) return fail(ADHA_ENOTIMPL, "device ordinal %d out of range", *dev);
-  return 0;
-}
-
-int status_word(int** ptr) {
-  int dev;
-  if (int rc = current_device(&dev)) return rc;
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_status_ptr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_status_word);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(status)");
-    g_status_ptr[dev] = static_cast<int*>(p);
-  }
-  *ptr = g_status_ptr[dev];
   return 0;
 }
 
@@ -1247,22 +1230,6 @@ int adha_tune_writeback(int32_t mode) {
   clear_error();
   if (mode < 0 || mode > 2) return fail(ADHA_EINVAL, "writeback mode %d not in [0, 2]", mode);
   t_writeback_mode = mode;
-  return 0;
-}
-
-int adha_device_status(adha_stream stream, int32_t* status) {
-  clear_error();
-  if (!status) return fail(ADHA_EINVAL, "status is NULL");
-  int* word = nullptr;
-  if (int rc = status_word(&word)) return rc;
-  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
-  int v = 0;
-  e = cudaMemcpy(&v, word, sizeof v, cudaMemcpyDeviceToHost);
-  if (e != cudaSuccess) return cuda_fail(e, "read status word");
-  e = cudaMemset(word, 0, sizeof v);
-  if (e != cudaSuccess) return cuda_fail(e, "clear status word");
-  *status = v;
   return 0;
 }
 

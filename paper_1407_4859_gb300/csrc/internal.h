@@ -47,8 +47,6 @@ int make_layout(const adha_schema* schema, const adha_layout* layout, Layout* ou
 int check_schema(const adha_schema* schema);
 bool same_group(const Layout& a, int ga, const Layout& b, int gb);
 
-// Device address of the library's status word on the current device (set up on first use).
-int status_word(int** ptr);
 int sm_count(int* count);
 
 // ------------------------------------------------------------------ kernel argument blocks

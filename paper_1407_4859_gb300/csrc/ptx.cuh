@@ -1,93 +1,14 @@
-// ptx.cuh -- inline PTX for the staged kernels: 16-byte cp.async copies, and mbarriers with bulk
-// (TMA, non-tensor) copies.
-//
-// Bulk copies move a contiguous slice with one instruction; the transaction count lands on an
-// mbarrier whose phase the consumers wait for.  Every mbarrier wait is bounded: after
-// kWaitBudget clock cycles the caller stops and reports ADHA_ETIMEOUT through the status word
-// instead of spinning forever.
+// ptx.cuh -- inline PTX for the staged kernels: 16-byte cp.async copies from global to shared
+// memory, completion tracked per thread in commit groups (nothing waits on another thread).
 #pragma once
 
 #include <cstdint>
 
 namespace adha {
 
-constexpr long long kWaitBudget = 4000000000LL;   // ~2 s at 2 GHz
-
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Waits for phase `parity` of `bar` to complete; false if the budget ran out first.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > kWaitBudget) return false;
-  }
-  return true;
-}
-
-// Bulk copy global -> shared; completion is counted on `bar` (bytes, 16-byte aligned, multiple of 16).
-__device__ __forceinline__ void bulk_load(void* sdst, const void* gsrc, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_addr(sdst)),
-      "l"(gsrc), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
-
-// Bulk copy shared -> global in the current bulk group.
-__device__ __forceinline__ void bulk_store(void* gdst, const void* ssrc, uint32_t bytes) {
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(smem_addr(ssrc)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-
-// Wait until at most N committed bulk groups still read shared memory.
-template <int N>
-__device__ __forceinline__ void bulk_wait_read() {
-  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
-}
-
-// Wait until at most N committed bulk groups are incomplete (writes performed).
-template <int N>
-__device__ __forceinline__ void bulk_wait_all() {
-  asm volatile("cp.async.bulk.wait_group %0;" ::"n"(N) : "memory");
-}
-
-// Orders this thread's generic-proxy shared-memory writes before later async-proxy (bulk) reads.
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(status, 0, code); }
 
 // 16-byte asynchronous copy global -> shared (LDGSTS), completion tracked per thread in groups.
 __device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {

@@ -122,7 +122,6 @@ def test_full_size_batched_workload_sampled(P):
     b.capture()
     b.graph_launch()
     torch.cuda.synchronize()
-    assert P.adha_device_status() == 0
     for k, (a, arr, (raw, sst, dst_st)) in enumerate(zip(specs, arrays, hosts)):
         n, m = a["n"], min(4096, a["n"])
         for i0 in sorted({0, (n - m) // 2, n - m}):

@@ -190,6 +190,5 @@ def test_program_captured_in_a_cuda_graph(P):
             b.copy_(x)
         g.replay()
         torch.cuda.synchronize()
-        assert P.adha_device_status() == 0
         lay, bufs = P.final_buffers(plan, S, wl.n, cand, AOS)
         assert_fields_equal(from_device(wl.n, wl.dtypes, lay.groups, bufs), want, "graph replay")

@@ -35,7 +35,6 @@ def _check_section(P, wl, sec, groups, perm=None, save=False):
         sbuf = torch.empty(n, dtype=torch.float32, device="cuda")
     P.adha_run_section(P.Schema(wl.dtypes), n, P.Layout(groups), bufs, P.c_section(sec, dperm), save=sbuf)
     torch.cuda.synchronize()
-    assert P.adha_device_status() == 0
     want = [a.copy() for a in fields]
     oracle.section(sec, wl.dtypes, want, perm)
     assert_fields_equal(from_device(n, wl.dtypes, groups, bufs), want, "%s in %r" % (sec.op, groups))
@@ -162,7 +161,6 @@ def test_chain_sections_vector_mapping(P, R, save_offset):
                 sbuf = base[save_offset:save_offset + n]
             P.adha_run_section(S, n, L, bufs, P.c_section(sec), save=sbuf)
             torch.cuda.synchronize()
-            assert P.adha_device_status() == 0
             want = [a.copy() for a in fields]
             oracle.section(sec, wl.dtypes, want, None)
             assert_fields_equal(from_device(n, wl.dtypes, groups, bufs), want, "%s %r R=%d" % (sec.op, sec.args, R))

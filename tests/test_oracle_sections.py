@@ -241,8 +241,10 @@ def test_chain_grad_matches_central_differences():
         an = g[f].astype(np.float64)
         scale = np.maximum(1.0, np.abs(fd))
         err = np.abs(fd - an) / scale
-        # kinks: none (smooth ops); fp32 forward vs fp64 differences stay far below 1e-2
-        assert np.quantile(err, 0.999) < 1e-2, (f, float(err.max()))
+        # every record, no quantile: the ops are smooth (no kinks), the fp32 gradient's rounding over
+        # at most 64 sections is a few 1e-6 relative at worst, the central difference's truncation
+        # (h^2 |f'''| / 6 with h = 1e-4) far below that; a dropped term or a wrong sign is O(1)
+        assert err.max() < 1e-5, (f, float(err.max()))
         checked += 1
     assert checked == wl.F
     # the fp32 forward state also agrees with the fp64 forward to fp32 accuracy
