@@ -10,8 +10,9 @@ this package.  It shares no code with the CUDA path and never imports it.
   * planner.py     -- affinity graph, greedy grouping (ODS), candidate set, and the
                       program layout choice (PDL) by dynamic programming and by
                       exhaustive enumeration, also with combine nodes (runs of
-                      consecutive sections fused in one layout) and over a structured
-                      control-flow graph (branches and loops, expected cost).
+                      consecutive sections fused in one layout), over a structured
+                      control-flow graph (branches and loops, expected cost) and with the
+                      device as a second dimension (transfer-inclusive edges).
   * program.py     -- runs a workload's sections on field arrays, whole or for a
                       sample of records.
 
@@ -25,6 +26,7 @@ from .core import (  # noqa: F401
 )
 from .planner import (  # noqa: F401
     affinity, ods, candidates, pdl_dp, pdl_exhaustive, program_cost, pdl_dp_fused, pdl_exhaustive_fused,
-    fused_program_cost, pdl_scfg_dp, pdl_scfg_exhaustive, scfg_expected_cost,
+    fused_program_cost, pdl_scfg_dp, pdl_scfg_exhaustive, scfg_expected_cost, pdl_devices_dp,
+    pdl_devices_exhaustive, device_program_cost,
 )
 from .program import run_program_fields, sample_program, initial_fields  # noqa: F401

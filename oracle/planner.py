@@ -379,3 +379,66 @@ def pdl_scfg_dp(tree, sec_cost, remap_cost, return_to_input=False):
     q = min(range(N), key=lambda q: ends[q])
     pick(tree, L, q)
     return ends[q], plan
+
+
+# ---------------------------------------------------------------------- PDL with a device dimension
+# Paper Section 2 and Table 4: PDL maps every section to a device as well as a layout (Medical:
+# CPU-ODS(1-3) remap GPU-ODS(4-7)).  The reading here: D devices, each with its own cost table
+# (section times and remap times between layouts on that device, input layout = index L) and a
+# transfer time xfer[a][b][l] for moving data in layout l from device a to device b (l = L: the
+# input layout).  A plan gives each section a (layout, device); between consecutive sections on
+# one device the edge is that device's remap; across devices it is the cheaper of remapping on
+# the source then moving the result, or moving the data then remapping on the destination.  The
+# input starts in layout L on input_device; return_to_input adds the way back to it.
+
+def device_edge(rem, xfer, a, la, b, lb):
+    """Cost of going from layout la on device a to layout lb on device b."""
+    if a == b:
+        return rem[a][la][lb]
+    return min(rem[a][la][lb] + xfer[a][b][lb], xfer[a][b][la] + rem[b][la][lb])
+
+
+def device_program_cost(plan, sec, rem, xfer, input_device, return_to_input=False):
+    """Model cost of a plan [(layout, device), ...]; sec[d][k][l], rem[d][a][b], xfer[a][b][l]."""
+    L = len(sec[0][0])
+    cur = (L, input_device)
+    total = 0
+    for k, (l, d) in enumerate(plan):
+        total += device_edge(rem, xfer, cur[1], cur[0], d, l) + sec[d][k][l]
+        cur = (l, d)
+    if return_to_input:
+        total += device_edge(rem, xfer, cur[1], cur[0], input_device, L)
+    return total
+
+
+def pdl_devices_exhaustive(sec, rem, xfer, input_device, return_to_input=False):
+    """Brute force over every (layout, device) per section: (least cost, smallest such plan)."""
+    D, S, L = len(sec), len(sec[0]), len(sec[0][0])
+    states = [(l, d) for d in range(D) for l in range(L)]
+    return min((device_program_cost(list(p), sec, rem, xfer, input_device, return_to_input), list(p))
+               for p in itertools.product(states, repeat=S))
+
+
+def pdl_devices_dp(sec, rem, xfer, input_device, return_to_input=False):
+    """The layered-DAG shortest path over (layout, device) states (state index d*L + l), ties to
+    the smaller state index: (least cost, [(layout, device)] per section)."""
+    D, S, L = len(sec), len(sec[0]), len(sec[0][0])
+    states = [(l, d) for d in range(D) for l in range(L)]
+    n = len(states)
+    edge = lambda x, y: device_edge(rem, xfer, x[1], x[0], y[1], y[0])
+    start = (L, input_device)
+    rest = [[0] * n for _ in range(S)]
+    for i, (l, d) in enumerate(states):
+        rest[S - 1][i] = sec[d][S - 1][l] + (edge((l, d), start) if return_to_input else 0)
+    for k in range(S - 2, -1, -1):
+        for i, (l, d) in enumerate(states):
+            rest[k][i] = sec[d][k][l] + min(edge((l, d), states[j]) + rest[k + 1][j] for j in range(n))
+    plan, prev, total = [], start, None
+    for k in range(S):
+        vals = [edge(prev, states[j]) + rest[k][j] for j in range(n)]
+        j = vals.index(min(vals))
+        if k == 0:
+            total = vals[j]
+        plan.append(states[j])
+        prev = states[j]
+    return total, plan

@@ -147,3 +147,38 @@ def test_fused_dp_hand_worked():
     rem = [[0, 5, 0], [5, 0, 0], [0, 5, 0]]
     fused = {(0, 2): [30, 9]}
     assert oracle.pdl_dp_fused(sec, rem, fused, 2) == (14, [1, 1], [2, 0])
+
+
+def _device_tables(rng, D, S, L):
+    sec = [[[rng.randrange(0, 40) for _ in range(L)] for _ in range(S)] for _ in range(D)]
+    rem = [[[0 if a == b else rng.randrange(0, 20) for b in range(L + 1)] for a in range(L + 1)] for _ in range(D)]
+    xfer = [[[0 if a == b else rng.randrange(5, 60) for _ in range(L + 1)] for b in range(D)] for a in range(D)]
+    return sec, rem, xfer
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_device_dp_equals_brute_force(seed):
+    """PDL with the device dimension (paper Table 4: sections mapped to CPU or GPU): the DP over
+    (layout, device) states equals enumeration of every plan, cost and tie rule."""
+    import random
+    rng = random.Random(seed)
+    D, S, L = rng.randrange(1, 4), rng.randrange(1, 4), rng.randrange(1, 4)
+    sec, rem, xfer = _device_tables(rng, D, S, L)
+    dev = rng.randrange(D)
+    back = seed % 2 == 0
+    cost, plan = oracle.pdl_devices_exhaustive(sec, rem, xfer, dev, back)
+    assert oracle.pdl_devices_dp(sec, rem, xfer, dev, back) == (cost, [tuple(p) for p in plan])
+
+
+def test_device_plan_hand_worked():
+    """Table 4's shape: three sections cheap on device 1, then three cheap on device 0, the input on
+    device 0 in layout L.  Moving costs 10 each way, section costs 1 on the cheap device and 8
+    otherwise: the plan moves once to device 1 and once back (10 + 3 + 10 + 3 = 26) instead of
+    staying on device 0 (3 * 8 + 3 = 27)."""
+    L = 1
+    sec = [[[8]] * 3 + [[1]] * 3, [[1]] * 3 + [[8]] * 3]
+    rem = [[[0, 0], [0, 0]], [[0, 0], [0, 0]]]
+    xfer = [[[0, 0], [10, 10]], [[10, 10], [0, 0]]]
+    cost, plan = oracle.pdl_devices_dp(sec, rem, xfer, 0)
+    assert cost == 26 and [d for _, d in plan] == [1, 1, 1, 0, 0, 0]
+    assert oracle.device_program_cost([(0, 0)] * 6, sec, rem, xfer, 0) == 27
