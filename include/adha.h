@@ -348,6 +348,27 @@ typedef struct {
 int adha_pdl_solve_scfg(const adha_cost_table* costs, int32_t n_nodes, const adha_scfg_node* nodes, int32_t root,
                         int32_t return_to_input, int32_t* layout_of_node, double* total_ns);
 
+/*
+ * PDL with the device as a second dimension (paper Section 2 and Table 4: the
+ * tuning profile covers every device, and the plan maps each section to a
+ * device as well as a layout, e.g. CPU-ODS(1-3) remap GPU-ODS(4-7)).  costs[d]
+ * is device d's table (same sections and candidates on every device; remap_ns
+ * between layouts on that device, index n_layouts = the input layout);
+ * transfer_ns[(a*n_devices + b)*(n_layouts+1) + l] is the time to move the data,
+ * in layout l (n_layouts: the input layout), from device a to device b.  A plan
+ * gives each section a (layout, device); consecutive sections on one device pay
+ * that device's remap, across devices the cheaper of remapping on the source and
+ * then moving, or moving and then remapping on the destination.  The input is
+ * in the input layout on input_device (also where return_to_input goes back
+ * to).  Shortest path over the (layout, device) states, state index
+ * device*n_layouts + layout, ties to the smaller index.  The library runs
+ * sections on its GPU only: this call plans; costs for other devices come from
+ * the caller.  1 <= n_devices <= 8.  Host only.
+ */
+int adha_pdl_solve_devices(int32_t n_devices, const adha_cost_table* const* costs, const double* transfer_ns,
+                           int32_t input_device, int32_t return_to_input, int32_t* layout_of_section,
+                           int32_t* device_of_section, double* total_ns);
+
 /* ----------------------------------------------------------- measure and run */
 
 /* A program's layout plan and where its result ended up. */

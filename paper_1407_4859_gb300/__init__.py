@@ -12,5 +12,5 @@ from .api import (  # noqa: F401
     adha_cost_table_create, adha_pdl_solve, adha_pdl_solve_fused, adha_measure_workspace_bytes, adha_measure,
     adha_program_workspace_bytes, adha_run_program, final_buffers, adha_profile_start, adha_profile_stop, Batched,
     adha_program_host_workspace_bytes, adha_run_program_host, adha_workspace_bytes, adha_remap_batched,
-    remap_descs, adha_gather_probe, adha_pdl_solve_scfg,
+    remap_descs, adha_gather_probe, adha_pdl_solve_scfg, adha_pdl_solve_devices,
 )

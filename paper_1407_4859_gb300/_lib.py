@@ -107,6 +107,9 @@ SIGNATURES = {
     "adha_workspace_bytes": (ctypes.c_int, [_I32, ctypes.POINTER(adha_remap_desc), ctypes.POINTER(ctypes.c_size_t)]),
     "adha_batched_info": (ctypes.c_int, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I64)]),
     "adha_gather_probe": (ctypes.c_int, [_P, _P, _P, _I64, _I32, _P]),
+    "adha_pdl_solve_devices": (ctypes.c_int, [_I32, ctypes.POINTER(ctypes.POINTER(adha_cost_table)),
+                                              ctypes.POINTER(ctypes.c_double), _I32, _I32, ctypes.POINTER(_I32),
+                                              ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_double)]),
     "adha_pdl_solve_scfg": (ctypes.c_int, [ctypes.POINTER(adha_cost_table), _I32, ctypes.POINTER(adha_scfg_node), _I32,
                                            _I32, ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_double)]),
     "adha_tune_writeback": (ctypes.c_int, [_I32]),

@@ -351,6 +351,22 @@ def adha_pdl_solve_fused(costs, return_to_input=False, max_window=0):
     return tot.value, list(seq), list(win)
 
 
+def adha_pdl_solve_devices(tables, transfer_ns, input_device=0, return_to_input=False):
+    """PDL over (layout, device): tables = one CostTable per device, transfer_ns[a][b][l] the time to
+    move layout l (l = n_layouts: the input layout) from device a to device b.  Returns (total ns,
+    [(layout, device)] per section)."""
+    D = len(tables)
+    S, L = tables[0].ptr.contents.n_sections, tables[0].ptr.contents.n_layouts
+    arr = (ctypes.POINTER(adha_cost_table) * D)(*[t.ptr for t in tables])
+    flat = [float(transfer_ns[a][b][l]) for a in range(D) for b in range(D) for l in range(L + 1)]
+    xf = (ctypes.c_double * len(flat))(*flat)
+    lay, dev = (ctypes.c_int32 * S)(), (ctypes.c_int32 * S)()
+    tot = ctypes.c_double(0)
+    check(_lib.load().adha_pdl_solve_devices(D, arr, xf, int(input_device), int(bool(return_to_input)), lay, dev,
+                                             ctypes.byref(tot)), "adha_pdl_solve_devices")
+    return tot.value, [(lay[k], dev[k]) for k in range(S)]
+
+
 SCFG_KINDS = {"sec": 0, "seq": 1, "branch": 2, "loop": 3}
 
 

@@ -352,6 +352,56 @@ using namespace adha;
 
 extern "C" {
 
+int adha_pdl_solve_devices(int32_t n_devices, const adha_cost_table* const* costs, const double* transfer_ns,
+                           int32_t input_device, int32_t return_to_input, int32_t* layout_of_section,
+                           int32_t* device_of_section, double* total_ns) {
+  clear_error();
+  if (n_devices < 1 || n_devices > 8) return fail(ADHA_EINVAL, "n_devices = %d not in [1, 8]", n_devices);
+  if (!costs || !transfer_ns || !layout_of_section || !device_of_section || !total_ns)
+    return fail(ADHA_EINVAL, "NULL argument");
+  if (input_device < 0 || input_device >= n_devices) return fail(ADHA_EINVAL, "input_device %d", input_device);
+  const int D = n_devices;
+  for (int d = 0; d < D; ++d) {
+    if (!costs[d] || costs[d]->n_sections < 1 || costs[d]->n_layouts < 1 || !costs[d]->section_ns || !costs[d]->remap_ns)
+      return fail(ADHA_EINVAL, "device %d: empty cost table", d);
+    if (costs[d]->n_sections != costs[0]->n_sections || costs[d]->n_layouts != costs[0]->n_layouts)
+      return fail(ADHA_EINVAL, "device %d: the tables differ in size", d);
+    if (int rc = check_costs(costs[d])) return rc;
+  }
+  const int S = costs[0]->n_sections, L = costs[0]->n_layouts;
+  for (size_t k = 0; k < (size_t)D * D * (L + 1); ++k)
+    if (std::isnan(transfer_ns[k]) || transfer_ns[k] < 0)
+      return fail(ADHA_EINVAL, "transfer_ns entry %zu = %g (must be >= 0 or +inf)", k, transfer_ns[k]);
+  auto rem = [&](int d, int a, int b) { return costs[d]->remap_ns[(size_t)a * (L + 1) + b]; };
+  auto xfer = [&](int a, int b, int l) { return transfer_ns[((size_t)a * D + b) * (L + 1) + l]; };
+  auto edge = [&](int a, int la, int b, int lb) {
+    if (a == b) return rem(a, la, lb);
+    return std::min(rem(a, la, lb) + xfer(a, b, lb), xfer(a, b, la) + rem(b, la, lb));
+  };
+  // the plain PDL on the expanded table: state d*L + l, input state D*L
+  const int LL = D * L;
+  adha_cost_table* t = nullptr;
+  if (int rc = adha_cost_table_create(S, LL, &t)) return rc;
+  for (int k = 0; k < S; ++k)
+    for (int d = 0; d < D; ++d)
+      for (int l = 0; l < L; ++l) t->section_ns[(size_t)k * LL + d * L + l] = costs[d]->section_ns[(size_t)k * L + l];
+  for (int x = 0; x <= LL; ++x)
+    for (int y = 0; y <= LL; ++y) {
+      const int a = x < LL ? x / L : input_device, la = x < LL ? x % L : L;
+      const int b = y < LL ? y / L : input_device, lb = y < LL ? y % L : L;
+      t->remap_ns[(size_t)x * (LL + 1) + y] = x == y ? 0.0 : edge(a, la, b, lb);
+    }
+  std::vector<int32_t> seq(S);
+  const int rc = pdl_solve(t, return_to_input, seq.data(), total_ns);
+  std::free(t);
+  if (rc) return rc;
+  for (int k = 0; k < S; ++k) {
+    layout_of_section[k] = seq[k] % L;
+    device_of_section[k] = seq[k] / L;
+  }
+  return 0;
+}
+
 int adha_pdl_solve_scfg(const adha_cost_table* costs, int32_t n_nodes, const adha_scfg_node* nodes, int32_t root,
                         int32_t return_to_input, int32_t* layout_of_node, double* total_ns) {
   clear_error();

@@ -218,3 +218,30 @@ def test_library_scfg_rejects_bad_trees(P):
         with pytest.raises(AdhaError) as e:
             P.adha_pdl_solve_scfg(t, tree)
         assert e.value.code == ADHA_EINVAL, tree
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_library_device_pdl_equals_oracle(P, seed):
+    from test_oracle_planner import _device_tables
+    rng = random.Random(9100 + seed)
+    D, S, L = rng.randrange(1, 4), rng.randrange(1, 5), rng.randrange(1, 4)
+    sec, rem, xfer = _device_tables(rng, D, S, L)
+    dev = rng.randrange(D)
+    back = seed % 2 == 1
+    tables = [_table(P, sec[d], rem[d]) for d in range(D)]
+    want = oracle.pdl_devices_dp(sec, rem, xfer, dev, back)
+    got = P.adha_pdl_solve_devices(tables, xfer, dev, back)
+    assert got == (want[0], [tuple(p) for p in want[1]])
+
+
+def test_library_device_pdl_rejects_bad_inputs(P):
+    from paper_1407_4859_gb300._lib import AdhaError, ADHA_EINVAL
+    a = _table(P, [[1, 2]], [[0, 1, 1], [1, 0, 1], [1, 1, 0]])
+    b = _table(P, [[1, 2], [3, 4]], [[0, 1, 1], [1, 0, 1], [1, 1, 0]])
+    ok = [[[0] * 3, [5] * 3], [[5] * 3, [0] * 3]]
+    for tables, xf, dev in (([a, b], ok, 0),                                  # tables of different sizes
+                            ([a, a], [[[0] * 3, [-1, 5, 5]], [[5] * 3, [0] * 3]], 0),   # negative transfer
+                            ([a, a], ok, 2)):                                  # no such input device
+        with pytest.raises(AdhaError) as e:
+            P.adha_pdl_solve_devices(tables, xf, dev)
+        assert e.value.code == ADHA_EINVAL
