@@ -639,10 +639,13 @@ __device__ __forceinline__ ReduceLane reduce_lane(const SecOp& so, const FieldRe
 }
 
 // REDUCE over the R = 32*M records of a staged chunk.  Counts: lane = record, one ballot per
-// cluster.  Sums: lane j = feature j, its column of the warp's K x 32 accumulators (int64, shared
-// memory) updated record by record.  Integer sums: any order gives the same result.
+// cluster.  Sums: lane j = feature j, its column of the warp's two (K+1) x 32 accumulator tables
+// (int64, shared memory): even records into the first, odd into the second, so that two
+// read-add-write chains are in flight (the tables never alias).  Integer sums: any order gives the
+// same result.
 template <int M>
-__device__ __forceinline__ void reduce_chunk(const ReduceLane& q, const uint8_t* stage, int lane, long long* acc,
+__device__ __forceinline__ void reduce_chunk(const ReduceLane& q, const uint8_t* stage, int lane,
+                                             long long* __restrict__ acc, long long* __restrict__ acc2,
                                              unsigned long long* cnt) {
   constexpr int R = 32 * M;
 #pragma unroll
@@ -653,17 +656,22 @@ __device__ __forceinline__ void reduce_chunk(const ReduceLane& q, const uint8_t*
       if (k < q.K) cnt[k] += (unsigned long long)__popc(__ballot_sync(0xFFFFFFFFu, mm == k));
   }
   if (lane < q.d) {
-    long long* col = acc + lane;
+    long long* __restrict__ col = acc + lane;
+    long long* __restrict__ col2 = acc2 + lane;
     const uint8_t* pm = stage + q.sm;
     const uint8_t* px = stage + q.sx;
-#pragma unroll 4
-    for (int i = 0; i < R; ++i) {
-      const int r = (i + q.skew) & (R - 1);
-      const int mm = *reinterpret_cast<const int32_t*>(pm + r * q.ssm);
-      const long long v = fixq(*reinterpret_cast<const float*>(px + r * q.ssx));
+#pragma unroll 2
+    for (int i = 0; i < R; i += 2) {
+      const int r0 = (i + q.skew) & (R - 1), r1 = (i + 1 + q.skew) & (R - 1);
+      const int m0 = *reinterpret_cast<const int32_t*>(pm + r0 * q.ssm);
+      const int m1 = *reinterpret_cast<const int32_t*>(pm + r1 * q.ssm);
+      const long long v0 = fixq(*reinterpret_cast<const float*>(px + r0 * q.ssx));
+      const long long v1 = fixq(*reinterpret_cast<const float*>(px + r1 * q.ssx));
       // a membership outside [0, K) goes to the scratch row kMaxClusters, never read back
-      const int row = (unsigned)mm < (unsigned)q.K ? mm : kMaxClusters;
-      col[row * 32] += v;
+      const int row0 = (unsigned)m0 < (unsigned)q.K ? m0 : kMaxClusters;
+      const int row1 = (unsigned)m1 < (unsigned)q.K ? m1 : kMaxClusters;
+      col[row0 * 32] += v0;
+      col2[row1 * 32] += v1;
     }
   }
 }

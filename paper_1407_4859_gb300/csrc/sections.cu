@@ -39,8 +39,8 @@ __global__ void __launch_bounds__(kThreads) section_kernel(const __grid_constant
   if constexpr (OP == ADHA_OP_REDUCE) {
     rq = reduce_lane(a.s, a.f, lane);
     acc = reinterpret_cast<long long*>(smem + kSectionTable + (size_t)kWarps * 2 * a.in_bytes) +
-          (size_t)warp * (kMaxClusters + 1) * 32;
-    for (int k = lane; k < (kMaxClusters + 1) * 32; k += 32) acc[k] = 0;
+          (size_t)warp * 2 * (kMaxClusters + 1) * 32;
+    for (int k = lane; k < 2 * (kMaxClusters + 1) * 32; k += 32) acc[k] = 0;
 #pragma unroll
     for (int k = 0; k < kMaxClusters; ++k) cnt[k] = 0;
   }
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(kThreads) section_kernel(const __grid_constant
     __syncwarp();
     const int64_t i0 = c * R;
     if constexpr (OP == ADHA_OP_REDUCE) {
-      reduce_chunk<M>(rq, cur, lane, acc, cnt);
+      reduce_chunk<M>(rq, cur, lane, acc, acc + (kMaxClusters + 1) * 32, cnt);
     } else if constexpr (OP == ADHA_OP_ASSIGN) {
       assign_chunk<M>(a.s, a.f, cur, i0, lane, cT);
     } else if (OP == ADHA_OP_MIX && VEC) {
@@ -130,7 +130,9 @@ __global__ void __launch_bounds__(kThreads) section_kernel(const __grid_constant
 #pragma unroll
     for (int k = 0; k < kMaxClusters; ++k)
       if (k < K) {
-        if (lane < d) atomicAdd(out + (size_t)k * (d + 1) + 1 + lane, (unsigned long long)acc[k * 32 + lane]);
+        if (lane < d)
+          atomicAdd(out + (size_t)k * (d + 1) + 1 + lane,
+                    (unsigned long long)(acc[k * 32 + lane] + acc[(kMaxClusters + 1 + k) * 32 + lane]));
         if (lane == 0) atomicAdd(out + (size_t)k * (d + 1), cnt[k]);
       }
   } else {
@@ -201,7 +203,8 @@ __global__ void __launch_bounds__(kThreads) backward_kernel(const __grid_constan
 }
 
 size_t section_smem_bytes(const SectionArgs& a) {
-  const size_t acc = a.s.op == ADHA_OP_REDUCE ? (size_t)kWarps * (kMaxClusters + 1) * 32 * 8 : 0;   // + scratch row
+  // REDUCE: two (K+1) x 32 int64 tables per warp (even and odd records; row K is scratch)
+  const size_t acc = a.s.op == ADHA_OP_REDUCE ? (size_t)kWarps * 2 * (kMaxClusters + 1) * 32 * 8 : 0;
   const size_t cent = a.s.op == ADHA_OP_ASSIGN ? (size_t)kMaxFields * kMaxClusters * 4 : 0;
   return kSectionTable + (size_t)kWarps * 2 * a.in_bytes + acc + cent;
 }
