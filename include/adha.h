@@ -612,6 +612,15 @@ int adha_tune_override(int32_t chunk_records);
 int adha_tune_writeback(int32_t mode);
 
 /*
+ * Chunk buffers per warp of section kernels launched later by the calling
+ * thread: 0 = as tuned (adha_measure with ADHA_MEASURE_AUTOTUNE), else 2;
+ * 2 = the next chunk is staged while one is computed; 1 = one buffer (half the
+ * shared memory, so more CTAs per SM; the next chunk is staged after this one).
+ * Every choice computes the same bytes.  Host only; EINVAL for another value.
+ */
+int adha_tune_section_buffers(int32_t buffers);
+
+/*
  * How remaps launched later by the calling thread store one-field destination
  * groups: 0 = through the warp's output buffer with 16-byte stores (default),
  * 1 = straight from the move loop to global memory (less shared memory, more

@@ -113,6 +113,7 @@ SIGNATURES = {
     "adha_pdl_solve_scfg": (ctypes.c_int, [ctypes.POINTER(adha_cost_table), _I32, ctypes.POINTER(adha_scfg_node), _I32,
                                            _I32, ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_double)]),
     "adha_tune_writeback": (ctypes.c_int, [_I32]),
+    "adha_tune_section_buffers": (ctypes.c_int, [_I32]),
     "adha_tune_remap_direct": (ctypes.c_int, [_I32]),
     "adha_tune_remap_pieces": (ctypes.c_int, [_I32]),
     "adha_tune_clear": (ctypes.c_int, []),

@@ -143,6 +143,10 @@ def adha_tune_writeback(mode=0):
     check(_lib.load().adha_tune_writeback(int(mode)), "adha_tune_writeback")
 
 
+def adha_tune_section_buffers(buffers=0):
+    check(_lib.load().adha_tune_section_buffers(int(buffers)), "adha_tune_section_buffers")
+
+
 def adha_tune_remap_direct(mode=0):
     check(_lib.load().adha_tune_remap_direct(int(mode)), "adha_tune_remap_direct")
 

@@ -208,6 +208,7 @@ struct RemapPlan {
 // Chunk / pipeline override for the autotuner (0 = default rule).
 static thread_local int t_tile_override = 0;
 static thread_local int t_writeback_mode = 0;   // 0 automatic, 1 never, 2 every wide written group
+static thread_local int t_section_buffers = 0;  // section chunk buffers per warp: 0 tuned or 2, else 1 or 2
 static thread_local int t_fused_buffers = 0;    // fused runs: 0 tuned or default, else chunk buffers per warp
 static thread_local int t_remap_direct = 0;     // 1: remaps store one-field destination groups directly
 static thread_local int t_remap_pieces = 0;     // 0: tuned or automatic, 1 + piece-table bits otherwise
@@ -254,9 +255,10 @@ void tuning_store(const std::string& key, int R, int wb) {
   g_tune[key] = {R, wb};
 }
 
-void set_overrides(int R, int wb) {
+void set_overrides(int R, int wb, int buffers) {
   t_tile_override = R;
   t_writeback_mode = wb;
+  t_section_buffers = buffers;
 }
 
 void set_fused_overrides(int R, int buffers) {
@@ -654,15 +656,17 @@ static int plan_section(const Layout& L, void* const* ptrs, const adha_section* 
                         SectionPlan* plan) {
   SectionArgs& a = plan->args;
   std::memset(&a, 0, sizeof a);
-  int tuned_R = t_tile_override, wb_mode = t_writeback_mode;
-  if (!tuned_R && !wb_mode) {
+  int tuned_R = t_tile_override, wb_mode = t_writeback_mode, buffers = t_section_buffers;
+  if (!tuned_R && !wb_mode && !buffers) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(section_key(L, s, n, save != nullptr));
-    if (it != g_tune.end()) {
+    if (it != g_tune.end()) {   // mode: store mode, + 4 for one chunk buffer per warp
       tuned_R = it->second.first;
-      wb_mode = it->second.second;
+      wb_mode = it->second.second & 3;
+      buffers = (it->second.second & 4) ? 1 : 2;
     }
   }
+  if (buffers != 1) buffers = 2;
   uint64_t staged = s->read_mask;
   if (s->op == ADHA_OP_MIX) staged |= s->write_mask;
   if (save) staged |= 1ull << (s->op == ADHA_OP_MUL ? s->arg[2] : s->arg[1]);
@@ -726,6 +730,7 @@ static int plan_section(const Layout& L, void* const* ptrs, const adha_section* 
       off += R * 4;
     }
     a.in_bytes = off;
+    a.buffers = buffers;
     // vector mapping: every staged group and every written field's group is one field wide
     // (and `save`, if any, aligned for the chunk's vector stores)
     const bool vec_op = s->op == ADHA_OP_MIX || s->op == ADHA_OP_AXPB || s->op == ADHA_OP_MUL || s->op == ADHA_OP_TANH;
@@ -1203,7 +1208,7 @@ int adha_tune_import(const char* text) {
       return fail(ADHA_EINVAL, "bad tuning values (not whole numbers): %s", line.c_str());
     const bool bad = kind == 'M'   ? (R != 0 || wb > 3)
                      : kind == 'F' ? (R % 32 || R > 128 || wb > 2)
-                                   : (R % 32 || R > 128 || wb > 2);
+                                   : (R % 32 || R > 128 || (wb & 3) > 2 || wb > 6);
     if (bad) return fail(ADHA_EINVAL, "bad tuning values: %s", line.c_str());
     parsed[line.substr(0, t1)] = {R, wb};
   }
@@ -1223,6 +1228,13 @@ int adha_tune_remap_pieces(int32_t mode) {
   clear_error();
   if (mode < 0 || mode > 4) return fail(ADHA_EINVAL, "remap piece-table mode %d not in [0, 4]", mode);
   t_remap_pieces = mode;
+  return 0;
+}
+
+int adha_tune_section_buffers(int32_t buffers) {
+  clear_error();
+  if (buffers < 0 || buffers > 2) return fail(ADHA_EINVAL, "section buffers %d not in [0, 2]", buffers);
+  t_section_buffers = buffers;
   return 0;
 }
 

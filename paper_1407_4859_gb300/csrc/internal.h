@@ -131,6 +131,7 @@ struct SectionArgs {
   int8_t writeback[kMaxGroups + 1];   // staged slice k is written back whole after the chunk
   int32_t n_writeback;
   int32_t vec;                        // 1: every accessed group is one field wide; lane = M consecutive records
+  int32_t buffers;                    // chunk buffers per warp: 2 (the next chunk staged during this one) or 1
   FieldRef f[kMaxFields];
   float tanh_p[8], tanh_q[8];   // tanh polynomial coefficients (7 used each)
   const int32_t* perm;
@@ -195,7 +196,7 @@ int profiled_launch(int kind, int op, double bytes, void* stream, int (*fn)(cons
 // Autotuning: the key of a section launch, storing its best shape, thread-local overrides.
 std::string tuning_key(const Layout& L, const adha_section* s, int64_t n, bool save);
 void tuning_store(const std::string& key, int R, int wb);
-void set_overrides(int R, int wb);
+void set_overrides(int R, int wb, int buffers = 0);
 void set_fused_overrides(int R, int buffers);
 std::string remap_tuning_key(const Layout& S, const Layout& D, int64_t n);
 void set_remap_pieces(int mode);

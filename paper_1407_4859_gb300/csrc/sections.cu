@@ -29,8 +29,9 @@ __global__ void __launch_bounds__(kThreads) section_kernel(const __grid_constant
   const uint8_t** sp = reinterpret_cast<const uint8_t**>(smem);
   int* send = reinterpret_cast<int*>(smem + 8 * (kMaxGroups + 1));
   int* wback = send + (kMaxGroups + 1);
-  uint8_t* buf0 = smem + kSectionTable + (size_t)warp * 2 * a.in_bytes;
-  uint8_t* buf1 = buf0 + a.in_bytes;
+  const int nb = a.buffers;   // 2: the next chunk is staged while one is computed; 1: one buffer
+  uint8_t* buf0 = smem + kSectionTable + (size_t)warp * nb * a.in_bytes;
+  uint8_t* buf1 = buf0 + (nb - 1) * a.in_bytes;
   constexpr int R = 32 * M;
   // REDUCE: the warp's K x 32 int64 sums after the chunk buffers, its counts in registers
   long long* acc = nullptr;
@@ -38,7 +39,7 @@ __global__ void __launch_bounds__(kThreads) section_kernel(const __grid_constant
   ReduceLane rq{};
   if constexpr (OP == ADHA_OP_REDUCE) {
     rq = reduce_lane(a.s, a.f, lane);
-    acc = reinterpret_cast<long long*>(smem + kSectionTable + (size_t)kWarps * 2 * a.in_bytes) +
+    acc = reinterpret_cast<long long*>(smem + kSectionTable + (size_t)kWarps * nb * a.in_bytes) +
           (size_t)warp * 2 * (kMaxClusters + 1) * 32;
     for (int k = lane; k < 2 * (kMaxClusters + 1) * 32; k += 32) acc[k] = 0;
 #pragma unroll
@@ -52,7 +53,7 @@ __global__ void __launch_bounds__(kThreads) section_kernel(const __grid_constant
   // ASSIGN: the centroids, transposed (cT[j*8 + k]; zero for k >= K), after the chunk buffers
   float* cT = nullptr;
   if constexpr (OP == ADHA_OP_ASSIGN) {
-    cT = reinterpret_cast<float*>(smem + kSectionTable + (size_t)kWarps * 2 * a.in_bytes);
+    cT = reinterpret_cast<float*>(smem + kSectionTable + (size_t)kWarps * nb * a.in_bytes);
     const int K = a.s.arg[1], d = a.s.rd_off[ADHA_F32 + 1] - a.s.rd_off[ADHA_F32];
     const float* cent = static_cast<const float*>(a.s.aux);
     for (int t = tid; t < d * kMaxClusters; t += kThreads) {
@@ -80,9 +81,13 @@ __global__ void __launch_bounds__(kThreads) section_kernel(const __grid_constant
   cp_async_commit();
   for (int i = 0; c < a.n_chunks; c += W, ++i) {
     uint8_t* cur = (i & 1) ? buf1 : buf0;
-    if (c + W < a.n_chunks) stage(c + W, (i & 1) ? buf0 : buf1);
-    cp_async_commit();
-    cp_async_wait<1>();
+    if (nb == 2) {
+      if (c + W < a.n_chunks) stage(c + W, (i & 1) ? buf0 : buf1);
+      cp_async_commit();
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
     __syncwarp();
     const int64_t i0 = c * R;
     if constexpr (OP == ADHA_OP_REDUCE) {
@@ -116,6 +121,10 @@ __global__ void __launch_bounds__(kThreads) section_kernel(const __grid_constant
       }
     }
     __syncwarp();
+    if (nb == 1 && c + W < a.n_chunks) {   // one buffer: the next chunk once this one is done with it
+      stage(c + W, buf0);
+      cp_async_commit();
+    }
   }
   cp_async_wait<0>();
 
@@ -206,7 +215,7 @@ size_t section_smem_bytes(const SectionArgs& a) {
   // REDUCE: two (K+1) x 32 int64 tables per warp (even and odd records; row K is scratch)
   const size_t acc = a.s.op == ADHA_OP_REDUCE ? (size_t)kWarps * 2 * (kMaxClusters + 1) * 32 * 8 : 0;
   const size_t cent = a.s.op == ADHA_OP_ASSIGN ? (size_t)kMaxFields * kMaxClusters * 4 : 0;
-  return kSectionTable + (size_t)kWarps * 2 * a.in_bytes + acc + cent;
+  return kSectionTable + (size_t)kWarps * a.buffers * a.in_bytes + acc + cent;
 }
 
 template <int OP, int M, bool VEC>

@@ -135,6 +135,19 @@ def test_tuning_cache_text_round_trip(P):
         P.adha_tune_writeback(3)
     P.adha_tune_override(0)
     P.adha_tune_writeback(0)
+    for bad in [-1, 3]:
+        with pytest.raises(AdhaError):
+            P.adha_tune_section_buffers(bad)
+    for ok in [1, 2, 0]:
+        P.adha_tune_section_buffers(ok)
+    # section entries: store mode 0..2, + 4 for one chunk buffer
+    one_buffer = "S1:7:4:0:0:0,1,2,0,0,0,0,0,:L0.0,1.0,2.0,|:n20\t64\t6\n"
+    P.adha_tune_import(one_buffer)
+    assert P.adha_tune_export() == one_buffer
+    for bad in ["S1:7:4:0:0:0,1,2,0,0,0,0,0,:L0.0,|:n20\t64\t3\n", "S1:7:4:0:0:0,1,2,0,0,0,0,0,:L0.0,|:n20\t64\t7\n"]:
+        with pytest.raises(AdhaError):
+            P.adha_tune_import(bad)
+    P.adha_tune_clear()
     for bad in [-1, 2]:
         with pytest.raises(AdhaError):
             P.adha_tune_remap_direct(bad)

@@ -202,3 +202,17 @@ def test_full_size_medical_program_sampled(P):
         rows.append(o.view(-1)[idx].cpu().numpy())
     got = oracle.to_fields(len(sample), wl.dtypes, lay.groups, rows)
     assert_fields_equal(got, want, "medical sampled")
+
+
+@pytest.mark.parametrize("rec_bytes", [4, 8, 16])
+@pytest.mark.parametrize("n", [1, 1000, 1 << 20])
+def test_gather_probe_reads_the_permuted_records(P, rec_bytes, n):
+    """The gather's roofline probe copies table[perm[i]] to out[i], element by element."""
+    import synth
+    perm = torch.from_numpy(synth.perm_i32(synth.key(11, rec_bytes), n)).cuda()
+    table = torch.randint(0, 256, (n * rec_bytes,), dtype=torch.uint8, device="cuda")
+    out = torch.zeros_like(table)
+    P.adha_gather_probe(table, perm, out, rec_bytes)
+    torch.cuda.synchronize()
+    want = table.view(n, rec_bytes)[perm.long()]
+    assert torch.equal(out.view(n, rec_bytes), want)

@@ -255,3 +255,28 @@ def test_gather_reads_one_struct_through_perm(P, order, n):
         for s in run:
             oracle.section(s, wl.dtypes, want, perm)
         assert_fields_equal(from_device(n, wl.dtypes, groups, bufs), want, "fused gather in %r" % (groups,))
+
+
+@pytest.mark.parametrize("buffers", [1, 2])
+@pytest.mark.parametrize("R", [32, 128])
+@pytest.mark.parametrize("wb", [1, 2])
+def test_sections_chunk_buffers(P, buffers, R, wb):
+    """One chunk buffer per warp (the next chunk staged after this one is written back) and two
+    (staged during it) give the oracle's bytes for every stress, particle and K-Means section, at
+    either store mode, with a ragged tail."""
+    P.adha_tune_override(R)
+    P.adha_tune_writeback(wb)
+    P.adha_tune_section_buffers(buffers)
+    try:
+        wl = synth.config2(n=3 * 128 * 152 + 45)
+        for k, sec in enumerate(wl.sections):
+            for groups in _layouts(wl.F, 40 + k)[:3]:
+                _check_section(P, wl, sec, groups)
+        wl = synth.config3(n=2 * 128 * 152 + 7)
+        perm = wl.perm()
+        for k, sec in enumerate(wl.sections):
+            _check_section(P, wl, sec, _layouts(wl.F, 60 + k)[2], perm)
+    finally:
+        P.adha_tune_section_buffers(0)
+        P.adha_tune_writeback(0)
+        P.adha_tune_override(0)

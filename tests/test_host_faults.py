@@ -203,3 +203,14 @@ def test_kmeans_sections_validated_before_launch(P):
     with pytest.raises(AdhaError) as e:                               # 33 features for reduce
         P.adha_run_section(wide, 64, P.Layout.soa(34), [4096 * (k + 1) for k in range(34)], c, stream=0)
     assert e.value.code == EINVAL
+
+
+def test_gather_probe_arguments_checked_before_launch(P):
+    from paper_1407_4859_gb300 import _lib
+    AdhaError, EINVAL, _ = _codes()
+    lib = _lib.load()
+    for args in [(256, 512, 768, 10, 3), (256, 512, 768, -1, 16), (0, 512, 768, 10, 16), (264, 512, 768, 10, 16),
+                 (256, 514, 768, 10, 16)]:
+        rc = lib.adha_gather_probe(args[0], args[1], args[2], args[3], args[4], None)
+        assert rc == EINVAL, args
+    assert lib.adha_gather_probe(None, None, None, 0, 16, None) == 0     # nothing to do
