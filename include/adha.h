@@ -36,8 +36,10 @@
 #ifndef ADHA_H_
 #define ADHA_H_
 
+#ifndef __CUDACC_RTC__   /* the run-time compiler of fused windows provides these types itself */
 #include <stddef.h>
 #include <stdint.h>
+#endif
 
 #ifdef __cplusplus
 extern "C" {
@@ -619,6 +621,57 @@ int adha_tune_writeback(int32_t mode);
  * Every choice computes the same bytes.  Host only; EINVAL for another value.
  */
 int adha_tune_section_buffers(int32_t buffers);
+
+/*
+ * Fused runs specialised at run time (paper Section 2, the combine edge: one
+ * pass over the records for a run of sections).  The library's fused kernel
+ * looks fields and operands up in tables at run time; a specialised run is the
+ * same pipeline compiled for this one run (chunk shape, slice offsets, field
+ * types and section operands as constants, each record's fields in registers
+ * across the run's sections) with the CUDA run-time compiler for sm_103a,
+ * loaded once and cached for the process.  Both compute the same bytes.
+ *
+ * adha_tune_fused_jit: how fused runs launched later by the calling thread
+ * choose: 0 = as tuned (adha_measure with ADHA_MEASURE_AUTOTUNE times both and
+ * keeps the faster), 1 = always the library's kernel, 2 = always specialised
+ * (a run that cannot be, e.g. one with an ASSIGN section, then fails with
+ * ADHA_ENOTIMPL and the reason).  A run first met while its stream is being
+ * captured is not compiled then: it takes the library's kernel (mode 0) or
+ * fails with ADHA_ENOTIMPL (mode 2).  Compiling takes a fraction of a second
+ * per run; adha_measure compiles the runs it times in parallel host threads.
+ * EINVAL for another mode.
+ *
+ * adha_jit_available: 1 if the run-time compiler (libnvrtc) could be loaded,
+ * else 0 with the reason as the error message.
+ *
+ * adha_jit_log: the last compile's log (the compiler's messages and the
+ * register and shared-memory report of the kernel), NUL-terminated into
+ * buf[0..cap) when buf is not NULL; *len (if not NULL) gets its full length.
+ */
+int adha_tune_fused_jit(int32_t mode);
+
+/*
+ * Chunk buffers per warp of fused runs launched later by the calling thread:
+ * 0 = as tuned, else one (the default); 1 or 2.  Host only; EINVAL otherwise.
+ */
+int adha_tune_fused_buffers(int32_t buffers);
+
+/*
+ * The specialised kernel of the fused run sections[0..n_sec) on n records in
+ * `layout` (validated like adha_run_sections_fused; chunk_records 0 = the
+ * library's rule, else 32, 64 or 128; buffers 0 = the default, else 1 or 2):
+ * its CUDA source (NUL-terminated into src[0..cap) when src is not NULL; *len,
+ * if not NULL, gets the full length, also on failure after planning), compiled
+ * for sm_103a (no device needed) and, when load != 0, loaded into the process's
+ * cache so that later launches of the run (mode 2, or as tuned) skip the
+ * compile.  ADHA_ENOTIMPL if the run cannot be specialised or the run-time
+ * compiler is missing; ADHA_ECUDA with the compiler's log if it fails.
+ */
+int adha_fused_jit_build(const adha_schema* schema, int64_t n, const adha_layout* layout, const adha_section* sections,
+                         int32_t n_sec, int32_t chunk_records, int32_t buffers, int32_t load, char* src, size_t cap,
+                         size_t* len);
+int adha_jit_available(void);
+int adha_jit_log(char* buf, size_t cap, size_t* len);
 
 /*
  * How remaps launched later by the calling thread store one-field destination

@@ -114,6 +114,13 @@ SIGNATURES = {
                                            _I32, ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_double)]),
     "adha_tune_writeback": (ctypes.c_int, [_I32]),
     "adha_tune_section_buffers": (ctypes.c_int, [_I32]),
+    "adha_tune_fused_jit": (ctypes.c_int, [_I32]),
+    "adha_tune_fused_buffers": (ctypes.c_int, [_I32]),
+    "adha_fused_jit_build": (ctypes.c_int, [ctypes.POINTER(adha_schema), _I64, ctypes.POINTER(adha_layout),
+                                            ctypes.POINTER(adha_section), _I32, _I32, _I32, _I32, ctypes.c_char_p,
+                                            ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+    "adha_jit_available": (ctypes.c_int, []),
+    "adha_jit_log": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     "adha_tune_remap_direct": (ctypes.c_int, [_I32]),
     "adha_tune_remap_pieces": (ctypes.c_int, [_I32]),
     "adha_tune_clear": (ctypes.c_int, []),

@@ -147,6 +147,40 @@ def adha_tune_section_buffers(buffers=0):
     check(_lib.load().adha_tune_section_buffers(int(buffers)), "adha_tune_section_buffers")
 
 
+def adha_tune_fused_jit(mode=0):
+    check(_lib.load().adha_tune_fused_jit(int(mode)), "adha_tune_fused_jit")
+
+
+def adha_tune_fused_buffers(buffers=0):
+    check(_lib.load().adha_tune_fused_buffers(int(buffers)), "adha_tune_fused_buffers")
+
+
+def adha_fused_jit_build(schema, n, layout, sections, chunk_records=0, buffers=0, load=False):
+    """The specialised kernel's CUDA source for the fused run `sections` (compiled; loaded into the
+    process's cache when `load`, which needs the GPU)."""
+    secs = sections if isinstance(sections, Sections) else Sections(sections)
+    cap = 1 << 20
+    buf = ctypes.create_string_buffer(cap)
+    n_src = ctypes.c_size_t(0)
+    check(_lib.load().adha_fused_jit_build(ctypes.byref(schema.c), int(n), ctypes.byref(layout.c), secs.arr, len(secs),
+                                           int(chunk_records), int(buffers), int(bool(load)), buf, cap,
+                                           ctypes.byref(n_src)), "adha_fused_jit_build")
+    assert n_src.value < cap, "source longer than the buffer"
+    return buf.value.decode()
+
+
+def adha_jit_available():
+    return bool(_lib.load().adha_jit_available())
+
+
+def adha_jit_log():
+    n = ctypes.c_size_t(0)
+    check(_lib.load().adha_jit_log(None, 0, ctypes.byref(n)), "adha_jit_log")
+    buf = ctypes.create_string_buffer(n.value + 1)
+    check(_lib.load().adha_jit_log(buf, n.value + 1, None), "adha_jit_log")
+    return buf.value.decode(errors="replace")
+
+
 def adha_tune_remap_direct(mode=0):
     check(_lib.load().adha_tune_remap_direct(int(mode)), "adha_tune_remap_direct")
 

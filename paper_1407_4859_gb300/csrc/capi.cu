@@ -210,6 +210,7 @@ static thread_local int t_tile_override = 0;
 static thread_local int t_writeback_mode = 0;   // 0 automatic, 1 never, 2 every wide written group
 static thread_local int t_section_buffers = 0;  // section chunk buffers per warp: 0 tuned or 2, else 1 or 2
 static thread_local int t_fused_buffers = 0;    // fused runs: 0 tuned or default, else chunk buffers per warp
+static thread_local int t_fused_jit = 0;        // fused runs: 0 as tuned, 1 library kernel, 2 specialised at run time
 static thread_local int t_remap_direct = 0;     // 1: remaps store one-field destination groups directly
 static thread_local int t_remap_pieces = 0;     // 0: tuned or automatic, 1 + piece-table bits otherwise
 
@@ -888,20 +889,26 @@ struct FusedPlan {
   FusedArgs args;
   int grid = 0;
   size_t smem = 0;
+  const void* jit = nullptr;   // the run's specialised kernel, or NULL for the library's fused kernel
 };
 
-static int plan_fused(const Layout& L, void* const* ptrs, const adha_section* s, int m, int64_t n, FusedPlan* plan) {
+// launchable = false: the arguments only (no kernel looked up, no device queried).
+static int plan_fused(const Layout& L, void* const* ptrs, const adha_section* s, int m, int64_t n, void* stream,
+                      FusedPlan* plan, bool launchable = true) {
   FusedArgs& a = plan->args;
   std::memset(&a, 0, sizeof a);
   int tuned_R = t_tile_override, tuned_buffers = t_fused_buffers;
+  bool tuned_jit = false;
   if (!tuned_R && !tuned_buffers) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(fused_key(L, s, m, n));
-    if (it != g_tune.end()) {
+    if (it != g_tune.end()) {   // buffers, + 4 for the run specialised at run time
       tuned_R = it->second.first;
-      tuned_buffers = it->second.second;
+      tuned_buffers = it->second.second & 3;
+      tuned_jit = (it->second.second & 4) != 0;
     }
   }
+  const bool want_jit = t_fused_jit == 2 || (t_fused_jit == 0 && tuned_jit);
   uint64_t staged = 0, written = 0;
   const int32_t* perm = nullptr;
   for (int k = 0; k < m; ++k) {
@@ -984,7 +991,24 @@ static int plan_fused(const Layout& L, void* const* ptrs, const adha_section* s,
   }
   tanh_coefficients(a.tanh_p, a.tanh_q);
   a.perm = perm;
+  if (!launchable) return 0;
   int blocks = 0;
+  if (want_jit) {
+    // compiled here unless the stream is being captured (loading a module is no stream work)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) != cudaSuccess) cs = cudaStreamCaptureStatusNone;
+    std::string why;
+    const void* fn = nullptr;
+    const int rc = jit_kernel(a, L.F, a.buffers, cs == cudaStreamCaptureStatusNone, &fn, &why);
+    if (rc == 0) {
+      plan->jit = fn;
+      plan->smem = jit_smem_bytes(a);
+      if (int e = jit_occupancy(fn, plan->smem, &blocks)) return e;
+      return finish_grid(a.n_chunks, blocks, &plan->grid);
+    }
+    if (t_fused_jit == 2) return rc;   // asked for explicitly: report why not
+    clear_error();                     // else the library's fused kernel
+  }
   const int M = R / 32;
   if (int rc = cached_occupancy(200 + 10 * M + a.vec, plan->smem, &blocks)) return rc;
   return finish_grid(a.n_chunks, blocks, &plan->grid);
@@ -994,8 +1018,44 @@ int run_fused_layout(const Layout& L, void* const* ptrs, const adha_section* s, 
   if (int rc = check_fused(L, s, m, n)) return rc;
   if (n == 0) return 0;
   FusedPlan plan;
-  if (int rc = plan_fused(L, ptrs, s, m, n, &plan)) return rc;
-  return profiled(4, m, fused_bytes(L, s, m, n), stream, [&] { return launch_fused(plan.args, plan.grid, plan.smem, stream); });
+  if (int rc = plan_fused(L, ptrs, s, m, n, stream, &plan)) return rc;
+  return profiled(4, m, fused_bytes(L, s, m, n), stream, [&] {
+    return plan.jit ? launch_fused_jit(plan.jit, plan.args, plan.grid, plan.smem, stream)
+                    : launch_fused(plan.args, plan.grid, plan.smem, stream);
+  });
+}
+
+// The launch arguments of a fused run with chunk shape (chunk, buffers), planned on stand-in group
+// addresses (planning reads no memory; the specialised source holds no address).
+int fused_jit_args(const Layout& L, const adha_section* s, int m, int64_t n, int chunk, int buffers, FusedArgs* out) {
+  if (int rc = check_fused(L, s, m, n)) return rc;
+  if (n == 0) return fail(ADHA_EINVAL, "n = 0: nothing to specialise");
+  std::vector<void*> fake(L.n_groups, reinterpret_cast<void*>((uintptr_t)1 << 40));
+  const int saved_R = t_tile_override, saved_B = t_fused_buffers, saved_J = t_fused_jit;
+  t_tile_override = chunk;
+  t_fused_buffers = buffers;
+  t_fused_jit = 1;
+  FusedPlan plan;
+  const int rc = plan_fused(L, fake.data(), s, m, n, nullptr, &plan, false);
+  t_tile_override = saved_R;
+  t_fused_buffers = saved_B;
+  t_fused_jit = saved_J;
+  if (rc == 0) *out = plan.args;
+  return rc;
+}
+
+void set_fused_jit(int mode) { t_fused_jit = mode; }
+
+// The fused run's specialised source, compiled (and loaded into the process's cache when `load`).
+int fused_jit_build(const Layout& L, const adha_section* s, int m, int64_t n, int chunk, int buffers, int load,
+                    std::string* src) {
+  FusedArgs a;
+  if (int rc = fused_jit_args(L, s, m, n, chunk, buffers, &a)) return rc;
+  std::string why;
+  if (!jit_source(a, L.F, a.buffers, src, &why)) return fail(ADHA_ENOTIMPL, "fused run not specialised: %s", why.c_str());
+  if (!load) return jit_compile_only(*src);
+  const void* fn = nullptr;
+  return jit_kernel(a, L.F, a.buffers, true, &fn, &why);
 }
 
 int run_section_layout(const Layout& L, void* const* ptrs, const adha_section* s, int64_t n, void* save, void* stream) {
@@ -1068,6 +1128,27 @@ int adha_run_sections_fused(const adha_schema* schema, int64_t n, const adha_lay
   if (n == 0) return 0;
   if (int rc = check_ptrs(reinterpret_cast<const void* const*>(ptrs), L.n_groups, "layout")) return rc;
   return run_fused_layout(L, ptrs, sections, n_sec, n, stream);
+}
+
+int adha_fused_jit_build(const adha_schema* schema, int64_t n, const adha_layout* layout, const adha_section* sections,
+                         int32_t n_sec, int32_t chunk_records, int32_t buffers, int32_t load, char* src, size_t cap,
+                         size_t* len) {
+  clear_error();
+  Layout L;
+  if (int rc = make_layout(schema, layout, &L, "")) return rc;
+  if (n < 0) return fail(ADHA_EINVAL, "n = %lld is negative", (long long)n);
+  if (chunk_records != 0 && chunk_records != 32 && chunk_records != 64 && chunk_records != 128)
+    return fail(ADHA_EINVAL, "chunk_records %d is not 0, 32, 64 or 128", chunk_records);
+  if (buffers < 0 || buffers > 2) return fail(ADHA_EINVAL, "buffers %d not in [0, 2]", buffers);
+  std::string text;
+  const int rc = fused_jit_build(L, sections, n_sec, n, chunk_records, buffers, load, &text);
+  if (len) *len = text.size();
+  if (src && cap) {
+    const size_t k = std::min(cap - 1, text.size());
+    std::memcpy(src, text.data(), k);
+    src[k] = '\0';
+  }
+  return rc;
 }
 
 int adha_section_backward(const adha_schema* schema, int64_t n, const adha_layout* layout, void* const* state_ptrs,
@@ -1207,7 +1288,7 @@ int adha_tune_import(const char* text) {
     if (!number(t1 + 1, t2, &R) || !number(t2 + 1, line.size(), &wb))
       return fail(ADHA_EINVAL, "bad tuning values (not whole numbers): %s", line.c_str());
     const bool bad = kind == 'M'   ? (R != 0 || wb > 3)
-                     : kind == 'F' ? (R % 32 || R > 128 || wb > 2)
+                     : kind == 'F' ? (R % 32 || R > 128 || (wb & 3) > 2 || wb > 6)
                                    : (R % 32 || R > 128 || (wb & 3) > 2 || wb > 6);
     if (bad) return fail(ADHA_EINVAL, "bad tuning values: %s", line.c_str());
     parsed[line.substr(0, t1)] = {R, wb};
@@ -1235,6 +1316,40 @@ int adha_tune_section_buffers(int32_t buffers) {
   clear_error();
   if (buffers < 0 || buffers > 2) return fail(ADHA_EINVAL, "section buffers %d not in [0, 2]", buffers);
   t_section_buffers = buffers;
+  return 0;
+}
+
+int adha_tune_fused_buffers(int32_t buffers) {
+  clear_error();
+  if (buffers < 0 || buffers > 2) return fail(ADHA_EINVAL, "fused buffers %d not in [0, 2]", buffers);
+  t_fused_buffers = buffers;
+  return 0;
+}
+
+int adha_tune_fused_jit(int32_t mode) {
+  clear_error();
+  if (mode < 0 || mode > 2) return fail(ADHA_EINVAL, "fused run mode %d not in [0, 2]", mode);
+  t_fused_jit = mode;
+  return 0;
+}
+
+int adha_jit_available(void) {
+  clear_error();
+  std::string why;
+  if (jit_available(&why)) return 1;
+  fail(ADHA_ENOTIMPL, "%s", why.c_str());
+  return 0;
+}
+
+int adha_jit_log(char* buf, size_t cap, size_t* len) {
+  clear_error();
+  const std::string log = jit_last_log();
+  if (len) *len = log.size();
+  if (buf && cap) {
+    const size_t k = std::min(cap - 1, log.size());
+    std::memcpy(buf, log.data(), k);
+    buf[k] = '\0';
+  }
   return 0;
 }
 

@@ -10,15 +10,12 @@
 #include <string>
 #include <vector>
 
-#include "../../include/adha.h"
+#include "device_types.h"
 
 namespace adha {
 
-constexpr int kMaxFields = ADHA_MAX_FIELDS;
-constexpr int kMaxGroups = ADHA_MAX_FIELDS;
 constexpr int kMaxMoves = 256;         // moves (fields + padding pieces) over all built destination records
 constexpr int kMaxStride = 4095;       // bytes per struct
-constexpr int kThreads = 256;          // threads per CTA of the staged kernels (8 warps)
 constexpr int kSmemLimit = 227 * 1024; // dynamic shared memory one CTA may use
 
 inline int dtype_size(int d) { return d == ADHA_F64 ? 8 : (d == ADHA_BF16 ? 2 : 4); }
@@ -50,15 +47,7 @@ bool same_group(const Layout& a, int ga, const Layout& b, int gb);
 int sm_count(int* count);
 
 // ------------------------------------------------------------------ kernel argument blocks
-// Both staged kernels work per warp: a warp copies R consecutive records of every group it needs
-// ("a chunk", R a multiple of 32) into its own shared buffer with 16-byte cp.async, double
-// buffered, then works on the chunk.  Inside a buffer the groups' slices follow one another in
-// the listed order; slice k starts at byte start[k] (16-byte aligned) and holds R*stride[k] bytes.
-struct GroupRef {
-  const uint8_t* ptr;     // group buffer
-  int32_t stride;         // struct size
-  int32_t start;          // slice offset within a chunk buffer
-};
+// (GroupRef, FieldRef, SecOp and FusedArgs are in device_types.h.)
 
 // One field of a destination record (or one aligned zero piece of its padding) and where its
 // bytes come from.  Moves are 8, 4 or 2 bytes wide: a field moves whole, whatever the other
@@ -92,34 +81,6 @@ struct RemapArgs {
   Move move[kMaxMoves];
 };
 
-struct FieldRef {
-  uint8_t* g;       // global address of the field in record 0
-  int32_t gs;       // global stride (the group's struct size)
-  int32_t s0;       // byte offset within a chunk buffer of the field in chunk record 0, -1 if not staged
-  int32_t ss;       // stride within the chunk buffer
-  int32_t dtype;
-  int32_t wsm;      // 1: writes go into the chunk buffer and the whole slice is written back
-};
-
-// One section's operation and operands.  Read and written fields are listed by adha_dtype,
-// ascending ids within a dtype: the fields of dtype d are rd[rd_off[d] .. rd_off[d + 1]).
-struct SecOp {
-  int32_t op;
-  int32_t arg[8];
-  float par[4];
-  int8_t rd_off[5], wr_off[5];
-  int8_t rd[kMaxFields];
-  int8_t wr[kMaxFields];
-  int16_t rd_s0[kMaxFields];   // chunk-buffer offset (FieldRef::s0) of each listed field, -1 if not staged
-  int16_t wr_s0[kMaxFields];
-  const void* aux;             // ASSIGN: centroids; REDUCE: the int64 sums
-  int8_t gvec;                 // GATHER: px, py, pz, q share one 16-byte struct (one 16-byte load at perm[i])
-  int8_t gidx[4];              // GATHER with gvec: the word of px, py, pz, q in that struct
-};
-
-constexpr int kMaxClusters = 8;   // K of the ASSIGN and REDUCE sections
-constexpr int kMaxReduceFeatures = 32;
-
 struct SectionArgs {
   int64_t n;
   int64_t n_chunks;
@@ -137,27 +98,6 @@ struct SectionArgs {
   const int32_t* perm;
   uint8_t* save;                // NULL or n elements of the written field's type
   SecOp s;
-};
-
-// A run of sections executed in one pass (the paper's combine): every group holding a field that a
-// section of the run reads or writes is staged per chunk, the sections are applied in order on
-// the chunk buffer, and groups with written fields go back whole.
-constexpr int kMaxFused = ADHA_MAX_FUSED;
-struct FusedArgs {
-  int64_t n;
-  int64_t n_chunks;
-  int32_t R;
-  int32_t n_load, in_bytes;
-  int32_t perm_slot;            // index of the staged perm slice (a gather in the run), else -1
-  int32_t n_sec;
-  int32_t vec;                  // 1: every staged group is one field wide
-  int32_t buffers;              // chunk buffers per warp (1 or 2)
-  GroupRef load[kMaxGroups + 1];
-  int8_t writeback[kMaxGroups + 1];
-  FieldRef f[kMaxFields];
-  float tanh_p[8], tanh_q[8];
-  const int32_t* perm;
-  SecOp sec[kMaxFused];
 };
 
 struct BackwardArgs {
@@ -198,6 +138,8 @@ std::string tuning_key(const Layout& L, const adha_section* s, int64_t n, bool s
 void tuning_store(const std::string& key, int R, int wb);
 void set_overrides(int R, int wb, int buffers = 0);
 void set_fused_overrides(int R, int buffers);
+void set_fused_jit(int mode);   // 0 as tuned, 1 library kernel, 2 specialised
+int fused_jit_args(const Layout& L, const adha_section* s, int m, int64_t n, int chunk, int buffers, FusedArgs* out);
 std::string remap_tuning_key(const Layout& S, const Layout& D, int64_t n);
 void set_remap_pieces(int mode);
 // ADHA_EINVAL unless every entry of the table is >= 0 or +inf (+inf: not measured or not allowed).
@@ -215,11 +157,21 @@ size_t remap_smem_bytes(const RemapArgs& a);
 int launch_section(const SectionArgs& a, int grid, size_t smem, void* stream);
 size_t section_smem_bytes(const SectionArgs& a);
 int launch_fused(const FusedArgs& a, int grid, size_t smem, void* stream);
+// Fused runs specialised at run time (jit.cu): the kernel of run `a` (F fields; compiled and
+// loaded here when `compile`, else only found in the cache), its occupancy and launch.
+bool jit_available(std::string* why);
+int jit_kernel(const FusedArgs& a, int F, int buffers, bool compile, const void** fn, std::string* why);
+int jit_prepare(const std::vector<FusedArgs>& runs, const std::vector<int>& F, const std::vector<int>& buffers);
+int jit_occupancy(const void* fn, size_t smem, int* blocks);
+int launch_fused_jit(const void* fn, const FusedArgs& a, int grid, size_t smem, void* stream);
+size_t jit_smem_bytes(const FusedArgs& a);
+bool jit_source(const FusedArgs& a, int F, int buffers, std::string* src, std::string* why);
+int jit_compile_only(const std::string& src);   // compile, no device needed, nothing loaded
+std::string jit_last_log();
 size_t fused_smem_bytes(const FusedArgs& a);
 int fused_occupancy(int M, bool vec, size_t smem, int* blocks);
 int launch_backward(const BackwardArgs& a, void* stream);
 int remap_occupancy(int unit, size_t smem, int* blocks);
 int section_occupancy(int op, size_t smem, int* blocks);
-constexpr int kWarps = kThreads / 32;
 
 }  // namespace adha

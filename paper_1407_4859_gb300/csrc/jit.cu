@@ -1,0 +1,393 @@
+// jit.cu -- fused runs specialised at run time (see fused_jit.cuh for the kernel skeleton).
+//
+// For a planned fused run (FusedArgs: chunk shape, slices, field table, sections) this file writes
+// the run's description W as CUDA source, compiles it with the skeleton for sm_103a with the
+// CUDA run-time compiler (NVRTC, loaded on first use), loads the binary and keeps the kernel in a
+// process-wide cache keyed by the source text.  The source holds no pointer and no record count:
+// one kernel serves every launch of the same run on the same layout and chunk shape.  Floating
+// point flags are the library's own (no contraction, IEEE division and square root, no flush to
+// zero), so a specialised run computes the bytes of the library's fused kernel.
+#include <cuda_runtime.h>
+#include <dlfcn.h>
+#include <nvrtc.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "internal.h"
+
+namespace adha {
+
+// Headers the skeleton includes, embedded at build time (generated source).
+extern const int kJitHeaderCount;
+extern const char* const kJitHeaderNames[];
+extern const char* const kJitHeaderText[];
+
+namespace {
+
+struct Nvrtc {
+  bool tried = false, ok = false;
+  std::string why;
+  nvrtcResult (*create)(nvrtcProgram*, const char*, const char*, int, const char* const*, const char* const*);
+  nvrtcResult (*compile)(nvrtcProgram, int, const char* const*);
+  nvrtcResult (*log_size)(nvrtcProgram, size_t*);
+  nvrtcResult (*log)(nvrtcProgram, char*);
+  nvrtcResult (*cubin_size)(nvrtcProgram, size_t*);
+  nvrtcResult (*cubin)(nvrtcProgram, char*);
+  nvrtcResult (*destroy)(nvrtcProgram*);
+};
+
+std::mutex g_nvrtc_mu;
+Nvrtc g_nvrtc;
+
+#ifndef ADHA_CUDA_LIBDIR
+#define ADHA_CUDA_LIBDIR ""
+#endif
+
+const Nvrtc* nvrtc() {
+  std::lock_guard<std::mutex> lk(g_nvrtc_mu);
+  Nvrtc& n = g_nvrtc;
+  if (n.tried) return n.ok ? &n : nullptr;
+  n.tried = true;
+  const std::string dir = ADHA_CUDA_LIBDIR;
+  const std::string names[] = {"libnvrtc.so.13", "libnvrtc.so", dir.empty() ? "" : dir + "/libnvrtc.so.13"};
+  void* h = nullptr;
+  for (const std::string& nm : names)
+    if (!nm.empty() && (h = dlopen(nm.c_str(), RTLD_NOW | RTLD_LOCAL))) break;
+  if (!h) {
+    n.why = "the CUDA run-time compiler (libnvrtc.so.13) could not be loaded";
+    return nullptr;
+  }
+  bool all = true;
+  auto sym = [&](const char* s) {
+    void* p = dlsym(h, s);
+    all = all && p;
+    return p;
+  };
+  n.create = reinterpret_cast<decltype(n.create)>(sym("nvrtcCreateProgram"));
+  n.compile = reinterpret_cast<decltype(n.compile)>(sym("nvrtcCompileProgram"));
+  n.log_size = reinterpret_cast<decltype(n.log_size)>(sym("nvrtcGetProgramLogSize"));
+  n.log = reinterpret_cast<decltype(n.log)>(sym("nvrtcGetProgramLog"));
+  n.cubin_size = reinterpret_cast<decltype(n.cubin_size)>(sym("nvrtcGetCUBINSize"));
+  n.cubin = reinterpret_cast<decltype(n.cubin)>(sym("nvrtcGetCUBIN"));
+  n.destroy = reinterpret_cast<decltype(n.destroy)>(sym("nvrtcDestroyProgram"));
+  if (!all) {
+    n.why = "libnvrtc lacks an entry point the library needs";
+    return nullptr;
+  }
+  n.ok = true;
+  return &n;
+}
+
+struct Kernel {
+  cudaLibrary_t lib = nullptr;
+  cudaKernel_t fn = nullptr;
+  size_t occ_smem = 0;   // shared memory the cached occupancy was computed for
+  int occ_blocks = 0;
+};
+
+std::mutex g_cache_mu;
+std::map<std::string, Kernel>* g_cache = new std::map<std::string, Kernel>();   // never freed: kernels live as long as the process
+std::mutex g_log_mu;
+std::string g_last_log;
+
+const char* ctype_of(int dtype) {
+  return dtype == ADHA_F64 ? "unsigned long long" : (dtype == ADHA_BF16 ? "uint16_t" : "uint32_t");
+}
+
+// Fields a section reaches through its record accessor (besides the listed read / written
+// fields, which cover them when the section is valid); -1 ends the list.
+void op_fields(const SecOp& s, int out[8]) {
+  int k = 0;
+  auto add = [&](int a) { out[k++] = s.arg[a]; };
+  switch (s.op) {
+    case ADHA_OP_MADD3: case ADHA_OP_ADD: case ADHA_OP_MUL: add(0); add(1); add(2); break;
+    case ADHA_OP_XORSHIFT: case ADHA_OP_FLAGS: case ADHA_OP_AXPB: case ADHA_OP_TANH: add(0); add(1); break;
+    case ADHA_OP_DRIFT: for (int a = 0; a < 6; ++a) add(a); break;
+    case ADHA_OP_BIN: case ADHA_OP_KICK: for (int a = 0; a < 4; ++a) add(a); break;
+    case ADHA_OP_KE: for (int a = 0; a < 5; ++a) add(a); break;
+    case ADHA_OP_GATHER: add(0); add(1); add(2); break;
+    default: break;
+  }
+  out[k] = -1;
+}
+
+bool op_supported(int op) {
+  switch (op) {
+    case ADHA_OP_MADD3: case ADHA_OP_XORSHIFT: case ADHA_OP_ADD: case ADHA_OP_MIX: case ADHA_OP_DRIFT:
+    case ADHA_OP_BIN: case ADHA_OP_KE: case ADHA_OP_FLAGS: case ADHA_OP_GATHER: case ADHA_OP_KICK:
+    case ADHA_OP_AXPB: case ADHA_OP_MUL: case ADHA_OP_TANH:
+      return true;
+    default:
+      return false;   // ASSIGN reads its centroid table through a pointer; REDUCE never fuses
+  }
+}
+
+void emit_ints(std::string& o, const int8_t* v, int n) {
+  o += "{";
+  for (int k = 0; k < n; ++k) o += (k ? "," : "") + std::to_string(v[k]);
+  o += "}";
+}
+
+// A float as an exact hexadecimal literal.
+std::string float_literal(float x) {
+  char b[64];
+  std::snprintf(b, sizeof b, "%af", (double)x);
+  return b;
+}
+
+}  // namespace
+
+bool jit_available(std::string* why) {
+  const Nvrtc* n = nvrtc();
+  if (!n && why) *why = g_nvrtc.why;
+  return n != nullptr;
+}
+
+// The source of the specialised kernel for run `a` (F fields) with `buffers` chunk buffers per
+// warp; false (with the reason) when the run cannot be specialised.
+bool jit_source(const FusedArgs& a, int F, int buffers, std::string* src, std::string* why) {
+  if (a.R != 32 && a.R != 64 && a.R != 128) return *why = "chunk size", false;
+  uint64_t used = 0, written = 0;
+  for (int s = 0; s < a.n_sec; ++s) {
+    const SecOp& so = a.sec[s];
+    if (!op_supported(so.op)) return *why = "op " + std::to_string(so.op) + " is not specialised", false;
+    for (int k = 0; k < 4; ++k)
+      if (!std::isfinite(so.par[k])) return *why = "a non-finite section parameter", false;
+    for (int j = 0; j < so.rd_off[4]; ++j) used |= 1ull << so.rd[j];
+    for (int j = 0; j < so.wr_off[4]; ++j) used |= 1ull << so.wr[j], written |= 1ull << so.wr[j];
+  }
+  for (int s = 0; s < a.n_sec; ++s) {
+    int fs[8];
+    op_fields(a.sec[s], fs);
+    for (int k = 0; fs[k] >= 0; ++k)
+      if (fs[k] >= F || !((used >> fs[k]) & 1)) return *why = "an operand outside the section's masks", false;
+  }
+  for (int f = 0; f < F; ++f)
+    if (((used >> f) & 1) && a.f[f].s0 < 0) return *why = "an accessed field is not staged", false;
+
+  const int n_slices = a.n_load + (a.perm_slot >= 0 ? 1 : 0);
+  std::string o;
+  o.reserve(16384);
+  o += "#include \"fused_jit.cuh\"\nnamespace adha {\n@OPS@struct W {\n";
+  o += "  static constexpr int M = " + std::to_string(a.R / 32) + ", kBuffers = " + std::to_string(buffers) +
+       ", kInBytes = " + std::to_string(a.in_bytes) + ", kPermStart = " +
+       std::to_string(a.perm_slot >= 0 ? a.load[a.perm_slot].start : -1) + ";\n";
+  o += "  __device__ static __forceinline__ void stage(const FusedArgs& a, int64_t ch, uint8_t* buf, int lane) {\n";
+  for (int g = 0; g < n_slices; ++g)
+    o += "    ADHA_JIT_STAGE(" + std::to_string(g) + ", " + std::to_string(a.R * a.load[g].stride) + ", " +
+         std::to_string(a.load[g].start) + ")\n";
+  o += "  }\n  __device__ static __forceinline__ void writeback(const FusedArgs& a, int64_t ch, const uint8_t* buf, int lane) {\n";
+  for (int g = 0; g < a.n_load; ++g)
+    if (a.writeback[g])
+      o += "    ADHA_JIT_WRITEBACK(" + std::to_string(g) + ", " + std::to_string(a.R * a.load[g].stride) + ", " +
+           std::to_string(a.load[g].start) + ")\n";
+  o += "  }\n  struct Rec {\n";
+  for (int f = 0; f < F; ++f)
+    if ((used >> f) & 1) o += std::string("    mutable ") + ctype_of(a.f[f].dtype) + " v" + std::to_string(f) + ";\n";
+  o += "    template <class V>\n    __device__ __forceinline__ V ld(int k) const {\n      switch (k) {\n";
+  for (int f = 0; f < F; ++f)
+    if ((used >> f) & 1) o += "        case " + std::to_string(f) + ": return jit_as<V>(v" + std::to_string(f) + ");\n";
+  o += "        default: return V();\n      }\n    }\n";
+  o += "    template <class V>\n    __device__ __forceinline__ void st(int k, V v) const {\n      switch (k) {\n";
+  for (int f = 0; f < F; ++f)
+    if ((written >> f) & 1)
+      o += "        case " + std::to_string(f) + ": v" + std::to_string(f) + " = jit_bits<" + ctype_of(a.f[f].dtype) +
+           ">(v); break;\n";
+  o += "        default: break;\n      }\n    }\n";
+  o += "    __device__ __forceinline__ void load(const uint8_t* b, int r) {\n";
+  for (int f = 0; f < F; ++f)
+    if ((used >> f) & 1)
+      o += "      v" + std::to_string(f) + " = *reinterpret_cast<const " + ctype_of(a.f[f].dtype) + "*>(b + " +
+           std::to_string(a.f[f].s0) + " + r * " + std::to_string(a.f[f].ss) + ");\n";
+  o += "    }\n    __device__ __forceinline__ void store(uint8_t* b, int r) const {\n";
+  for (int f = 0; f < F; ++f)
+    if ((written >> f) & 1)
+      o += "      *reinterpret_cast<" + std::string(ctype_of(a.f[f].dtype)) + "*>(b + " + std::to_string(a.f[f].s0) +
+           " + r * " + std::to_string(a.f[f].ss) + ") = v" + std::to_string(f) + ";\n";
+  o += "    }\n  };\n";
+  // the sections' operands: constant globals, so that every load from them folds to its value
+  std::string ops;
+  for (int s = 0; s < a.n_sec; ++s) {
+    const SecOp& so = a.sec[s];
+    ops += "__device__ constexpr SecOp kSec" + std::to_string(s) + " = {" + std::to_string(so.op) + ", {";
+    for (int k = 0; k < 8; ++k) ops += (k ? "," : "") + std::to_string(so.arg[k]);
+    ops += "}, {";
+    for (int k = 0; k < 4; ++k) ops += (k ? "," : "") + float_literal(so.par[k]);
+    ops += "}, ";
+    emit_ints(ops, so.rd_off, 5);
+    ops += ", ";
+    emit_ints(ops, so.wr_off, 5);
+    ops += ", ";
+    emit_ints(ops, so.rd, so.rd_off[4] > 0 ? so.rd_off[4] : 1);
+    ops += ", ";
+    emit_ints(ops, so.wr, so.wr_off[4] > 0 ? so.wr_off[4] : 1);
+    ops += ", {}, {}, nullptr, " + std::to_string(so.gvec) + ", ";
+    emit_ints(ops, so.gidx, 4);
+    ops += "};\n";
+  }
+  o += "  template <bool VOTE, class Rec>\n  __device__ static __forceinline__ void apply(const FusedArgs& a, const FieldRef* fr, "
+       "const Rec& x, int64_t i, int32_t pj) {\n";
+  for (int s = 0; s < a.n_sec; ++s)
+    o += "    run_record<" + std::to_string(a.sec[s].op) + ", VOTE>(kSec" + std::to_string(s) +
+         ", fr, a.tanh_p, a.tanh_q, nullptr, x, i, pj);\n";
+  o += "  }\n};\n}  // namespace adha\n\n";
+  o.replace(o.find("@OPS@"), 5, ops);
+  o += "extern \"C\" __global__ void __launch_bounds__(adha::kThreads) adha_fused_window(const __grid_constant__ "
+       "adha::FusedArgs a) {\n  adha::fused_window<adha::W>(a);\n}\n";
+  *src = std::move(o);
+  return true;
+}
+
+// Compiles `src` for sm_103a into `bin` (no device needed); the log is kept for adha_jit_log.
+static int compile_cubin(const std::string& src, std::vector<char>* bin) {
+  const Nvrtc* nv = nvrtc();
+  if (!nv) return fail(ADHA_ENOTIMPL, "%s", g_nvrtc.why.c_str());
+  nvrtcProgram prog = nullptr;
+  if (nv->create(&prog, src.c_str(), "adha_fused_window.cu", kJitHeaderCount, kJitHeaderText, kJitHeaderNames) !=
+      NVRTC_SUCCESS)
+    return fail(ADHA_ECUDA, "nvrtcCreateProgram failed");
+  const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "--fmad=false", "-ftz=false", "-prec-div=true",
+                        "-prec-sqrt=true", "-default-device", "--ptxas-options=-v"};
+  const nvrtcResult cr = nv->compile(prog, (int)(sizeof opts / sizeof opts[0]), opts);
+  size_t ls = 0;
+  nv->log_size(prog, &ls);
+  std::string log(ls, '\0');
+  if (ls) nv->log(prog, &log[0]);
+  {
+    std::lock_guard<std::mutex> lk(g_log_mu);
+    g_last_log = log;
+  }
+  if (cr != NVRTC_SUCCESS) {
+    nv->destroy(&prog);
+    return fail(ADHA_ECUDA, "run-time compile of a fused run failed: %.400s", log.c_str());
+  }
+  size_t cs = 0;
+  nv->cubin_size(prog, &cs);
+  bin->resize(cs);
+  nv->cubin(prog, bin->data());
+  nv->destroy(&prog);
+  return 0;
+}
+
+// Compiles and loads `src` (or finds it in the cache).
+static int jit_load(const std::string& src, Kernel* out) {
+  {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto it = g_cache->find(src);
+    if (it != g_cache->end()) {
+      *out = it->second;
+      return 0;
+    }
+  }
+  std::vector<char> bin;
+  if (int rc = compile_cubin(src, &bin)) return rc;
+  Kernel k;
+  cudaError_t e = cudaLibraryLoadData(&k.lib, bin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaLibraryLoadData(fused run)");
+  e = cudaLibraryGetKernel(&k.fn, k.lib, "adha_fused_window");
+  if (e != cudaSuccess) return cuda_fail(e, "cudaLibraryGetKernel(fused run)");
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  auto ins = g_cache->emplace(src, k);
+  if (!ins.second) cudaLibraryUnload(k.lib);   // another thread compiled the same run meanwhile
+  *out = ins.first->second;
+  return 0;
+}
+
+int jit_kernel(const FusedArgs& a, int F, int buffers, bool compile, const void** fn, std::string* why) {
+  std::string src;
+  if (!jit_source(a, F, buffers, &src, why)) return fail(ADHA_ENOTIMPL, "fused run not specialised: %s", why->c_str());
+  if (!compile) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto it = g_cache->find(src);
+    if (it == g_cache->end()) {
+      *why = "not compiled yet";
+      return fail(ADHA_ENOTIMPL, "fused run not compiled yet");
+    }
+    *fn = reinterpret_cast<const void*>(it->second.fn);
+    return 0;
+  }
+  Kernel k;
+  if (int rc = jit_load(src, &k)) return rc;
+  *fn = reinterpret_cast<const void*>(k.fn);
+  return 0;
+}
+
+int jit_prepare(const std::vector<FusedArgs>& runs, const std::vector<int>& F, const std::vector<int>& buffers) {
+  std::vector<std::string> srcs;
+  for (size_t r = 0; r < runs.size(); ++r) {
+    std::string s, why;
+    if (jit_source(runs[r], F[r], buffers[r], &s, &why)) srcs.push_back(std::move(s));
+  }
+  if (srcs.empty()) return 0;
+  if (!nvrtc()) return fail(ADHA_ENOTIMPL, "%s", g_nvrtc.why.c_str());
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned hw = std::thread::hardware_concurrency();
+  const size_t T = std::min<size_t>(srcs.size(), std::max(1u, std::min(hw, 32u)));
+  std::vector<int> rcs(T, 0);
+  std::vector<std::thread> th;
+  for (size_t t = 0; t < T; ++t)
+    th.emplace_back([&, t] {
+      cudaSetDevice(dev);
+      for (size_t i = t; i < srcs.size(); i += T) {
+        Kernel k;
+        if (int rc = jit_load(srcs[i], &k)) rcs[t] = rc;
+      }
+    });
+  for (auto& x : th) x.join();
+  for (int rc : rcs)
+    if (rc) return fail(rc, "run-time compile of a fused run failed");
+  return 0;
+}
+
+int jit_occupancy(const void* fn, size_t smem, int* blocks) {
+  {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    for (auto& kv : *g_cache)
+      if (reinterpret_cast<const void*>(kv.second.fn) == fn && kv.second.occ_smem == smem && kv.second.occ_blocks) {
+        *blocks = kv.second.occ_blocks;
+        return 0;
+      }
+  }
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(fused run)");
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fn, kThreads, smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(fused run)");
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  for (auto& kv : *g_cache)
+    if (reinterpret_cast<const void*>(kv.second.fn) == fn) {
+      kv.second.occ_smem = smem;
+      kv.second.occ_blocks = *blocks;
+    }
+  return 0;
+}
+
+int launch_fused_jit(const void* fn, const FusedArgs& a, int grid, size_t smem, void* stream) {
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(fused run)");
+  void* args[] = {const_cast<FusedArgs*>(&a)};
+  e = cudaLaunchKernel(fn, dim3(grid), dim3(kThreads), args, smem, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "specialised fused run launch");
+  return 0;
+}
+
+int jit_compile_only(const std::string& src) {
+  std::vector<char> bin;
+  return compile_cubin(src, &bin);
+}
+
+size_t jit_smem_bytes(const FusedArgs& a) { return (size_t)kWarps * a.buffers * a.in_bytes; }
+
+std::string jit_last_log() {
+  std::lock_guard<std::mutex> lk(g_log_mu);
+  return g_last_log;
+}
+
+}  // namespace adha

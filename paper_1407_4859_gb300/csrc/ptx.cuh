@@ -2,7 +2,9 @@
 // memory, completion tracked per thread in commit groups (nothing waits on another thread).
 #pragma once
 
+#ifndef __CUDACC_RTC__
 #include <cstdint>
+#endif
 
 namespace adha {
 

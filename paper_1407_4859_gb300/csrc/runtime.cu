@@ -339,6 +339,63 @@ int adha_measure(const adha_schema* schema, int64_t n, const adha_layout* in_lay
       t->fused_ns[((size_t)k * W + (m - 1)) * L + a] = ns;
     }
   }
+  // Specialised runs (autotuning, when the run-time compiler can be loaded): each run in the two
+  // candidates where its sections cost least one by one, under three chunk shapes.  All are
+  // compiled first, in parallel host threads, then timed like the library's kernel; a faster one
+  // replaces the entry, and its tuning says "specialised".  A run that cannot be specialised, or
+  // a compile that fails, keeps the library kernel's time.
+  if ((flags & ADHA_MEASURE_AUTOTUNE) && !rc && !runs.empty() && jit_available(nullptr)) {
+    const int shapes[3][2] = {{32, 2}, {64, 1}, {64, 2}};
+    constexpr int kJitLayouts = 2;
+    std::vector<FusedArgs> jargs;
+    std::vector<int> jF, jB;
+    std::vector<bool> jit_layout(L, false);
+    for (size_t r = 0; r < runs.size(); ++r)
+      for (int j = 0; j < (int)where[r].size() && j < kJitLayouts; ++j) {
+        const int a = where[r][j];
+        for (int q = 0; q < 3; ++q) {
+          FusedArgs x;
+          if (fused_jit_args(cand[a], &sections[runs[r].first], runs[r].second, n, shapes[q][0], shapes[q][1], &x))
+            continue;
+          jargs.push_back(x);
+          jF.push_back(cand[a].F);
+          jB.push_back(x.buffers);
+          jit_layout[a] = true;
+        }
+      }
+    if (jit_prepare(jargs, jF, jB)) clear_error();
+    for (int a = 0; a < L && !rc; ++a) {
+      if (!jit_layout[a]) continue;
+      carve(cand[a], n, A, &pa);
+      rc = remap_layouts(in, in_p.data(), cand[a], pa.data(), n, stream, nullptr);
+      for (size_t r = 0; r < runs.size() && !rc; ++r) {
+        const auto top = std::find(where[r].begin(), where[r].end(), a);
+        if (top == where[r].end() || top - where[r].begin() >= kJitLayouts) continue;
+        const int k = runs[r].first, m = runs[r].second;
+        double& entry = t->fused_ns[((size_t)k * W + (m - 1)) * L + a];
+        auto run = [&] { return run_fused_layout(cand[a], pa.data(), &sections[k], m, n, stream); };
+        auto fresh = [&] { return remap_layouts(in, in_p.data(), cand[a], pa.data(), n, stream, nullptr); };
+        for (int q = 0; q < 3 && !rc; ++q) {
+          set_fused_overrides(shapes[q][0], shapes[q][1]);
+          set_fused_jit(2);
+          double ns = 0;
+          rc = fresh();
+          int e = rc ? rc : time_ns(timer, stream, reps, run, &ns);
+          set_fused_jit(0);
+          set_fused_overrides(0, 0);
+          if (e == ADHA_ENOTIMPL) {   // not specialised (or not compiled): the library kernel's time stands
+            clear_error();
+            continue;
+          }
+          rc = e;
+          if (!rc && ns < entry) {
+            entry = ns;
+            tuning_store(fused_tuning_key(cand[a], &sections[k], m, n), shapes[q][0], shapes[q][1] + 4);
+          }
+        }
+      }
+    }
+  }
   // differentiable: every remap of the forward pass has its inverse in the backward pass (the
   // gradients go back through the reversed byte permutation), so an edge costs both directions
   for (int a = 0; a <= L && diff && !rc; ++a)

@@ -5,10 +5,20 @@
 // change a bit.
 #pragma once
 
+#ifndef __CUDACC_RTC__
 #include <cstdint>
 #include <cstring>
+#endif
 
-#include "internal.h"
+#include "device_types.h"
+
+// Loops over a section's listed fields: unrolled in windows specialised at run time (constant
+// bounds), left to the compiler's own choice in the library's kernels (bounds known at run time).
+#ifdef __CUDACC_RTC__
+#define ADHA_FIELD_LOOP _Pragma("unroll")
+#else
+#define ADHA_FIELD_LOOP
+#endif
 
 namespace adha {
 
@@ -80,6 +90,14 @@ __device__ __forceinline__ double half_rn(double x) {
   return half_is_plain(x) ? half_plain(x) : __dmul_rn(x, 0.5);
 }
 __device__ __forceinline__ double widen(float t) { return widen_is_plain(t) ? widen_plain(t) : (double)t; }
+
+// The integer forms behind one warp vote per value, for code whose 32 lanes run it together.
+__device__ __forceinline__ double half_vote(double x) {
+  return __all_sync(0xFFFFFFFFu, half_is_plain(x)) ? half_plain(x) : half_rn_int(x);
+}
+__device__ __forceinline__ double widen_vote(float t) {
+  return __all_sync(0xFFFFFFFFu, widen_is_plain(t)) ? widen_plain(t) : widen_int(t);
+}
 
 struct StagedRec {      // record r of a staged chunk (global record i)
   const FieldRef* f;
@@ -405,9 +423,13 @@ __device__ __forceinline__ void chain_chunk_vec(const SecOp& so, const FieldRef*
 template <int OP>
 constexpr bool kVectorOp = OP == ADHA_OP_MIX || OP == ADHA_OP_AXPB || OP == ADHA_OP_MUL || OP == ADHA_OP_TANH;
 
-// One record of one section: its fields through `rec` (staged chunk or global memory), fields read
-// through the permutation from global memory (record pj), the old z to `save` when asked.
-template <int OP, class Rec>
+// One record of one section: its fields through `rec` (staged chunk, global memory, or registers
+// in a specialised window), fields read through the permutation from global memory (record pj),
+// the old z to `save` when asked.  VOTE: the fp64 halving and widening take the integer forms
+// behind a warp vote (every lane of the warp must run the call).  The field loops are unrolled
+// where their bounds are compile-time constants (specialised windows), so that every field index
+// folds to a constant there.
+template <int OP, bool VOTE = false, class Rec>
 __device__ __forceinline__ void run_record(const SecOp& so, const FieldRef* fr, const float* tp, const float* tq,
                                            uint8_t* save, const Rec& rec, int64_t i, int32_t pj) {
   const int* g = so.arg;
@@ -422,30 +444,39 @@ __device__ __forceinline__ void run_record(const SecOp& so, const FieldRef* fr, 
   } else if (OP == ADHA_OP_MIX) {
     float s = 0.0f;
     uint32_t h = 0u;
+ADHA_FIELD_LOOP
     for (int j = so.rd_off[ADHA_F32]; j < so.rd_off[ADHA_F32 + 1]; ++j) s = __fadd_rn(s, rec.template ld<float>(so.rd[j]));
+ADHA_FIELD_LOOP
     for (int j = so.rd_off[ADHA_F64]; j < so.rd_off[ADHA_F64 + 1]; ++j) {
       const unsigned long long b = rec.template ld<unsigned long long>(so.rd[j]);
       h ^= (uint32_t)b ^ (uint32_t)(b >> 32);
     }
+ADHA_FIELD_LOOP
     for (int j = so.rd_off[ADHA_I32]; j < so.rd_off[ADHA_I32 + 1]; ++j) h ^= rec.template ld<uint32_t>(so.rd[j]);
+ADHA_FIELD_LOOP
     for (int j = so.rd_off[ADHA_BF16]; j < so.rd_off[ADHA_BF16 + 1]; ++j) h ^= (uint32_t)rec.template ld<uint16_t>(so.rd[j]);
     const float t = __fadd_rn(s, __fmul_rn(__uint2float_rn(h & 255u), 0.00390625f));
     const uint32_t k = (h ^ __float_as_uint(t)) >> 3;
+ADHA_FIELD_LOOP
     for (int j = so.wr_off[ADHA_F32]; j < so.wr_off[ADHA_F32 + 1]; ++j) {
       const int f = so.wr[j];
       rec.template st<float>(f, __fadd_rn(__fmul_rn(rec.template ld<float>(f), 0.5f), t));
     }
     if (so.wr_off[ADHA_F64 + 1] > so.wr_off[ADHA_F64]) {
-      const double td = widen(t);
+      const double td = VOTE ? widen_vote(t) : widen(t);
+ADHA_FIELD_LOOP
       for (int j = so.wr_off[ADHA_F64]; j < so.wr_off[ADHA_F64 + 1]; ++j) {
         const int f = so.wr[j];
-        rec.template st<double>(f, __dadd_rn(half_rn(rec.template ld<double>(f)), td));
+        const double x = rec.template ld<double>(f);
+        rec.template st<double>(f, __dadd_rn(VOTE ? half_vote(x) : half_rn(x), td));
       }
     }
+ADHA_FIELD_LOOP
     for (int j = so.wr_off[ADHA_I32]; j < so.wr_off[ADHA_I32 + 1]; ++j) {
       const int f = so.wr[j];
       rec.template st<uint32_t>(f, rec.template ld<uint32_t>(f) ^ k);
     }
+ADHA_FIELD_LOOP
     for (int j = so.wr_off[ADHA_BF16]; j < so.wr_off[ADHA_BF16 + 1]; ++j) {
       const int f = so.wr[j];
       rec.template st<uint16_t>(f, (uint16_t)(rec.template ld<uint16_t>(f) ^ (uint16_t)(k & 0xFFFFu)));
@@ -475,7 +506,7 @@ __device__ __forceinline__ void run_record(const SecOp& so, const FieldRef* fr, 
     float s = __fadd_rn(__fmul_rn(vx, vx), __fmul_rn(vy, vy));
     s = __fadd_rn(s, __fmul_rn(vz, vz));
     const float e = __fmul_rn(__fmul_rn(0.5f, rec.template ld<float>(g[3])), s);
-    rec.template st<double>(g[4], widen(e));
+    rec.template st<double>(g[4], VOTE ? widen_vote(e) : widen(e));
   } else if (OP == ADHA_OP_FLAGS) {
     const uint32_t fl = rec.template ld<uint32_t>(g[0]);
     const uint32_t bit = rec.template ld<double>(g[1]) > (double)so.par[0] ? 1u : 0u;

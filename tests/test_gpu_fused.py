@@ -206,3 +206,80 @@ def test_fused_profile_records(P):
     written = set().union(*[s.write for s in wl.sections[:3]])
     sz = {0: 4, 1: 8, 2: 4, 3: 2}
     assert recs[0]["bytes"] == wl.n * (sum(sz[wl.dtypes[f]] for f in touched) + sum(sz[wl.dtypes[f]] for f in written))
+
+
+def _check_specialised(P, wl, run, groups, perm=None, chunk=0, buffers=0):
+    P.adha_tune_fused_jit(2)
+    P.adha_tune_fused_buffers(buffers)
+    try:
+        _check_run(P, wl, run, groups, perm, chunk)
+    finally:
+        P.adha_tune_fused_buffers(0)
+        P.adha_tune_fused_jit(0)
+
+
+@pytest.mark.parametrize("buffers", [1, 2])
+@pytest.mark.parametrize("chunk", [0, 64, 128])
+@pytest.mark.parametrize("start,m", [(0, 9), (3, 5), (7, 2), (4, 1)])
+def test_stress_runs_specialised(P, buffers, chunk, start, m):
+    """Runs specialised at run time (operands, offsets and field types compiled in, fields in
+    registers) give the oracle's bytes in AoS, SoA and a random layout, with a ragged tail."""
+    wl = synth.config2(n=50021)
+    for groups in _layouts(wl.F, 10 * start + m):
+        _check_specialised(P, wl, wl.sections[start:start + m], groups, chunk=chunk, buffers=buffers)
+
+
+@pytest.mark.parametrize("chunk", [0, 32, 128])
+def test_particle_runs_specialised(P, chunk):
+    """Every fusable particle run of 2..4 sections (gathers through the staged permutation, the
+    16-byte gather load, drift's wrap, bin's clamps, fp32 KE widened to fp64) specialised."""
+    wl = synth.config3(n=60013)
+    perm = wl.perm()
+    runs = [wl.sections[k:k + m] for m in range(2, 5) for k in range(len(wl.sections) - m + 1)]
+    runs = [r for r in runs if _fusable(r)]
+    rng = np.random.default_rng(100 + chunk)
+    for groups in [random_layout(rng, wl.F), oracle.aos(wl.F), oracle.soa(wl.F)]:
+        for run in runs[::2]:
+            _check_specialised(P, wl, run, groups, perm, chunk=chunk, buffers=1 + chunk % 2)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_tiny_chain_and_bf16_runs_specialised(P, seed):
+    """madd3 / xorshift / add, the chain ops (axpb, mul, tanh, aliased operands included) and a
+    bf16 field in mix, specialised."""
+    for n in [1, 33, 4099]:
+        wl = synth.config1(n=n)
+        for groups in _layouts(wl.F, n + seed):
+            _check_specialised(P, wl, wl.sections, groups, chunk=[0, 32, 64, 128][seed])
+    wl = synth.config5(n=30011, n_sections=16)
+    k = random.Random(seed).randrange(0, 8)
+    for groups in _layouts(wl.F, 70 + seed):
+        _check_specialised(P, wl, wl.sections[k:k + 8], groups, chunk=[0, 64, 128, 32][seed])
+    wl = synth.tiny_workload(seed, F_max=12, n=9001, n_sections=6)
+    flds = list(wl.fields)
+    flds[0] = synth.Field("b", synth.workloads.BF16, "RAW16")
+    wl.fields = flds
+    for groups in _layouts(wl.F, 40 + seed):
+        _check_specialised(P, wl, wl.sections, groups, chunk=[0, 64, 128, 32][seed], buffers=1 + seed % 2)
+
+
+def test_specialised_run_refuses_assign(P):
+    """ASSIGN reads its centroid table through a pointer and is not specialised: asked for
+    explicitly, the run fails with ADHA_ENOTIMPL and launches nothing; as tuned, it takes the
+    library's fused kernel."""
+    from paper_1407_4859_gb300._lib import AdhaError, ADHA_ENOTIMPL
+    wl = synth.kmeans(n=4099, n_features=8, k=3)
+    fields = oracle.initial_fields(wl)
+    groups = oracle.soa(wl.F)
+    S, L = P.Schema(wl.dtypes), P.Layout(groups)
+    bufs = to_device(wl.n, wl.dtypes, groups, fields)
+    secs = P.Sections([wl.sections[0]])
+    P.adha_tune_fused_jit(2)
+    try:
+        with pytest.raises(AdhaError) as e:
+            P.adha_run_sections_fused(S, wl.n, L, bufs, secs)
+        assert e.value.code == ADHA_ENOTIMPL and "not specialised" in str(e.value)
+    finally:
+        P.adha_tune_fused_jit(0)
+    torch.cuda.synchronize()
+    assert_fields_equal(from_device(wl.n, wl.dtypes, groups, bufs), fields, "nothing launched")
