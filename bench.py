@@ -288,7 +288,8 @@ def _timed(torch, stream, steps, fn):
 def _group_kernels(recs):
     groups = {}
     for r in recs:
-        key = r["kind"] if r["kind"] != "section" else "section_%s" % r["op"]
+        key = ("section_%s" % r["op"] if r["kind"] == "section" else
+               "specialised_%s" % r["op"] if r["kind"] == "section_specialised" else r["kind"])
         g = groups.setdefault(key, [0.0, 0.0, 0])
         g[0] += r["ms"]
         g[1] += r["bytes"]
@@ -305,7 +306,10 @@ def _roofline(recs, workload):
     achieved = groups[dom][1] / (groups[dom][0] * 1e6)
     total = sum(v[0] for v in groups.values())
     name = {"remap": "remap_kernel", "batched_remap": "batched_kernel", "fused": "fused_kernel",
-            "section_backward": "backward_kernel"}.get(dom, "section_kernel<%s>" % dom.replace("section_", ""))
+            "section_backward": "backward_kernel"}.get(dom)
+    if name is None:
+        name = ("adha_fused_window (%s section, specialised)" % dom[len("specialised_"):]
+                if dom.startswith("specialised_") else "section_kernel<%s>" % dom.replace("section_", ""))
     roof = {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1), "peak": peak,
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback",
             "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic_for(workload, dom),

@@ -651,6 +651,17 @@ int adha_tune_section_buffers(int32_t buffers);
 int adha_tune_fused_jit(int32_t mode);
 
 /*
+ * How sections launched later by the calling thread (adha_run_section and the
+ * executor; not those with a save buffer) choose their kernel: 0 = as tuned
+ * (adha_measure with ADHA_MEASURE_AUTOTUNE also times each section as a
+ * one-section run specialised at run time, in the layouts where the library's
+ * kernel does best, and keeps the faster), 1 = always the library's section
+ * kernel, 2 = specialised wherever the section can be (else the library's
+ * kernel).  Both compute the same bytes.  EINVAL for another mode.
+ */
+int adha_tune_section_jit(int32_t mode);
+
+/*
  * Chunk buffers per warp of fused runs launched later by the calling thread:
  * 0 = as tuned, else one (the default); 1 or 2.  Host only; EINVAL otherwise.
  */
@@ -719,7 +730,8 @@ int adha_gather_probe(const void* table, const int32_t* perm, void* out, int64_t
                       adha_stream stream);
 
 /* One kernel launch seen by the profiler.  kind: 0 remap, 1 section, 2 section
- * backward, 3 batched remap, 4 fused run, 5 gather probe; op: the section's
+ * backward, 3 batched remap, 4 fused run, 5 gather probe, 6 section run as a
+ * one-section run specialised at run time; op: the section's
  * adha_op (0 for remaps; the number of sections for a fused run; the element
  * bytes for the probe); bytes:
  * the algorithmic bytes the launch had to move (data bytes of the moved or

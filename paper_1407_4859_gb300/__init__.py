@@ -6,7 +6,7 @@ it does not load the library; the first call does, and raises if the library has
 """
 from .api import (  # noqa: F401
     Schema, Layout, alloc_layout, c_section, adha_version, adha_layout_strides, adha_remap, adha_run_section,
-    adha_run_sections_fused, adha_section_backward, adha_tune_override, adha_tune_writeback, adha_tune_section_buffers, adha_tune_fused_jit, adha_tune_fused_buffers, adha_fused_jit_build, adha_jit_available, adha_jit_log,
+    adha_run_sections_fused, adha_section_backward, adha_tune_override, adha_tune_writeback, adha_tune_section_buffers, adha_tune_fused_jit, adha_tune_fused_buffers, adha_tune_section_jit, adha_fused_jit_build, adha_jit_available, adha_jit_log,
     adha_tune_remap_direct, adha_tune_remap_pieces, adha_tune_clear, adha_tune_export, adha_tune_import, remap,
     PlanOpts, Sections, LayoutSet, CostTable, adha_ods, adha_plan_sections, adha_layout_set_create,
     adha_cost_table_create, adha_pdl_solve, adha_pdl_solve_fused, adha_measure_workspace_bytes, adha_measure,

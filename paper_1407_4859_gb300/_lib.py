@@ -116,6 +116,7 @@ SIGNATURES = {
     "adha_tune_section_buffers": (ctypes.c_int, [_I32]),
     "adha_tune_fused_jit": (ctypes.c_int, [_I32]),
     "adha_tune_fused_buffers": (ctypes.c_int, [_I32]),
+    "adha_tune_section_jit": (ctypes.c_int, [_I32]),
     "adha_fused_jit_build": (ctypes.c_int, [ctypes.POINTER(adha_schema), _I64, ctypes.POINTER(adha_layout),
                                             ctypes.POINTER(adha_section), _I32, _I32, _I32, _I32, ctypes.c_char_p,
                                             ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),

@@ -151,6 +151,10 @@ def adha_tune_fused_jit(mode=0):
     check(_lib.load().adha_tune_fused_jit(int(mode)), "adha_tune_fused_jit")
 
 
+def adha_tune_section_jit(mode=0):
+    check(_lib.load().adha_tune_section_jit(int(mode)), "adha_tune_section_jit")
+
+
 def adha_tune_fused_buffers(buffers=0):
     check(_lib.load().adha_tune_fused_buffers(int(buffers)), "adha_tune_fused_buffers")
 
@@ -538,7 +542,8 @@ def _view_device(ptr, nbytes):
     return torch.as_tensor(_Cuda(), device="cuda")
 
 
-KINDS = {0: "remap", 1: "section", 2: "section_backward", 3: "batched_remap", 4: "fused", 5: "gather_probe"}
+KINDS = {0: "remap", 1: "section", 2: "section_backward", 3: "batched_remap", 4: "fused", 5: "gather_probe",
+         6: "section_specialised"}
 
 
 def adha_gather_probe(table, perm, out, rec_bytes=16, stream=None):

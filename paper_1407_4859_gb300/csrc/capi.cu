@@ -211,6 +211,7 @@ static thread_local int t_writeback_mode = 0;   // 0 automatic, 1 never, 2 every
 static thread_local int t_section_buffers = 0;  // section chunk buffers per warp: 0 tuned or 2, else 1 or 2
 static thread_local int t_fused_buffers = 0;    // fused runs: 0 tuned or default, else chunk buffers per warp
 static thread_local int t_fused_jit = 0;        // fused runs: 0 as tuned, 1 library kernel, 2 specialised at run time
+static thread_local int t_section_jit = 0;      // sections: 0 as tuned, 1 library kernel, 2 specialised where possible
 static thread_local int t_remap_direct = 0;     // 1: remaps store one-field destination groups directly
 static thread_local int t_remap_pieces = 0;     // 0: tuned or automatic, 1 + piece-table bits otherwise
 
@@ -661,7 +662,7 @@ static int plan_section(const Layout& L, void* const* ptrs, const adha_section* 
   if (!tuned_R && !wb_mode && !buffers) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(section_key(L, s, n, save != nullptr));
-    if (it != g_tune.end()) {   // mode: store mode, + 4 for one chunk buffer per warp
+    if (it != g_tune.end() && !(it->second.second & 8)) {   // mode: store mode, + 4 for one chunk buffer per warp
       tuned_R = it->second.first;
       wb_mode = it->second.second & 3;
       buffers = (it->second.second & 4) ? 1 : 2;
@@ -1058,9 +1059,54 @@ int fused_jit_build(const Layout& L, const adha_section* s, int m, int64_t n, in
   return jit_kernel(a, L.F, a.buffers, true, &fn, &why);
 }
 
+// A section run as a one-section run specialised at run time, chunk shape (R, buffers); ENOTIMPL
+// (nothing launched) where it cannot be, or is not compiled and the stream is being captured.
+static int run_section_specialised(const Layout& L, void* const* ptrs, const adha_section* s, int64_t n, int R,
+                                   int buffers, void* stream) {
+  if (check_fused(L, s, 1, n)) {
+    clear_error();
+    return fail(ADHA_ENOTIMPL, "section not specialised");
+  }
+  const int saved_R = t_tile_override, saved_B = t_fused_buffers, saved_J = t_fused_jit;
+  t_tile_override = R;
+  t_fused_buffers = buffers;
+  t_fused_jit = 2;
+  FusedPlan plan;
+  int rc = plan_fused(L, ptrs, s, 1, n, stream, &plan);
+  t_tile_override = saved_R;
+  t_fused_buffers = saved_B;
+  t_fused_jit = saved_J;
+  if (rc) return rc;
+  return profiled(6, s->op, section_bytes(L, s, n, false), stream,
+                  [&] { return launch_fused_jit(plan.jit, plan.args, plan.grid, plan.smem, stream); });
+}
+
+int run_section_specialised_shape(const Layout& L, void* const* ptrs, const adha_section* s, int64_t n, int R,
+                                  int buffers, void* stream) {
+  return run_section_specialised(L, ptrs, s, n, R, buffers, stream);
+}
+
 int run_section_layout(const Layout& L, void* const* ptrs, const adha_section* s, int64_t n, void* save, void* stream) {
   if (int rc = check_section(L, s, n, save != nullptr)) return rc;
   if (n == 0) return 0;
+  // tuned (or asked) to run specialised: a one-section run compiled for this section and layout
+  if (!save && t_section_jit != 1 && !t_tile_override && !t_writeback_mode && !t_section_buffers) {
+    int R = 0, mode = 0;
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune.find(section_key(L, s, n, false));
+      if (it != g_tune.end()) {
+        R = it->second.first;
+        mode = it->second.second;
+      }
+    }
+    if ((mode & 8) || t_section_jit == 2) {
+      const int rc = run_section_specialised(L, ptrs, s, n, (mode & 8) ? R : 0, (mode & 8) ? ((mode & 4) ? 1 : 2) : 0,
+                                             stream);
+      if (rc != ADHA_ENOTIMPL) return rc;
+      clear_error();   // not specialised: the library's section kernel
+    }
+  }
   SectionPlan plan;
   if (int rc = plan_section(L, ptrs, s, n, save, &plan)) return rc;
   return profiled(1, s->op, section_bytes(L, s, n, save != nullptr), stream,
@@ -1289,7 +1335,7 @@ int adha_tune_import(const char* text) {
       return fail(ADHA_EINVAL, "bad tuning values (not whole numbers): %s", line.c_str());
     const bool bad = kind == 'M'   ? (R != 0 || wb > 3)
                      : kind == 'F' ? (R % 32 || R > 128 || (wb & 3) > 2 || wb > 6)
-                                   : (R % 32 || R > 128 || (wb & 3) > 2 || wb > 6);
+                                   : (R % 32 || R > 128 || (wb & 3) > 2 || wb > 14);
     if (bad) return fail(ADHA_EINVAL, "bad tuning values: %s", line.c_str());
     parsed[line.substr(0, t1)] = {R, wb};
   }
@@ -1316,6 +1362,13 @@ int adha_tune_section_buffers(int32_t buffers) {
   clear_error();
   if (buffers < 0 || buffers > 2) return fail(ADHA_EINVAL, "section buffers %d not in [0, 2]", buffers);
   t_section_buffers = buffers;
+  return 0;
+}
+
+int adha_tune_section_jit(int32_t mode) {
+  clear_error();
+  if (mode < 0 || mode > 2) return fail(ADHA_EINVAL, "section mode %d not in [0, 2]", mode);
+  t_section_jit = mode;
   return 0;
 }
 

@@ -139,6 +139,10 @@ void tuning_store(const std::string& key, int R, int wb);
 void set_overrides(int R, int wb, int buffers = 0);
 void set_fused_overrides(int R, int buffers);
 void set_fused_jit(int mode);   // 0 as tuned, 1 library kernel, 2 specialised
+// One section as a one-section run specialised at run time with chunk shape (R, buffers), profiled
+// as a section; ADHA_ENOTIMPL (nothing launched) where it cannot be.
+int run_section_specialised_shape(const Layout& L, void* const* ptrs, const adha_section* s, int64_t n, int R,
+                                  int buffers, void* stream);
 int fused_jit_args(const Layout& L, const adha_section* s, int m, int64_t n, int chunk, int buffers, FusedArgs* out);
 std::string remap_tuning_key(const Layout& S, const Layout& D, int64_t n);
 void set_remap_pieces(int mode);

@@ -281,6 +281,69 @@ int adha_measure(const adha_schema* schema, int64_t n, const adha_layout* in_lay
       t->remap_ns[(size_t)a * (L + 1) + b] = ns;
     }
   }
+  // Specialised sections (autotuning, not differentiable, when the run-time compiler can be
+  // loaded): each section also as a one-section run compiled for it, in the kJitSectionLayouts
+  // candidates where the library's kernel did best, under six chunk shapes (32 / 64 / 128 records x
+  // one or two buffers).  All are compiled first, in parallel host threads; a faster time
+  // replaces the entry and its tuning says "specialised" (mode + 8).
+  if ((flags & ADHA_MEASURE_AUTOTUNE) && !diff && !rc && jit_available(nullptr)) {
+    constexpr int kJitSectionLayouts = 3;
+    const int shapes[6][2] = {{32, 1}, {32, 2}, {64, 1}, {64, 2}, {128, 1}, {128, 2}};
+    std::vector<std::vector<int>> top(n_sec);
+    std::vector<bool> any(L, false);
+    std::vector<FusedArgs> jargs;
+    std::vector<int> jF, jB;
+    for (int k = 0; k < n_sec; ++k) {
+      std::vector<std::pair<double, int>> by;
+      for (int a = 0; a < L; ++a) by.push_back({t->section_ns[(size_t)k * L + a], a});
+      std::sort(by.begin(), by.end());
+      for (int j = 0; j < (int)by.size() && j < kJitSectionLayouts; ++j) {
+        const int a = by[j].second;
+        bool ok = false;
+        for (int q = 0; q < 6; ++q) {
+          FusedArgs x;
+          if (fused_jit_args(cand[a], &sections[k], 1, n, shapes[q][0], shapes[q][1], &x)) {
+            clear_error();
+            continue;
+          }
+          jargs.push_back(x);
+          jF.push_back(cand[a].F);
+          jB.push_back(x.buffers);
+          ok = true;
+        }
+        if (ok) {
+          top[k].push_back(a);
+          any[a] = true;
+        }
+      }
+    }
+    if (jit_prepare(jargs, jF, jB)) clear_error();
+    for (int a = 0; a < L && !rc; ++a) {
+      if (!any[a]) continue;
+      carve(cand[a], n, A, &pa);
+      rc = remap_layouts(in, in_p.data(), cand[a], pa.data(), n, stream, nullptr);
+      for (int k = 0; k < n_sec && !rc; ++k) {
+        if (std::find(top[k].begin(), top[k].end(), a) == top[k].end()) continue;
+        double& entry = t->section_ns[(size_t)k * L + a];
+        for (int q = 0; q < 6 && !rc; ++q) {
+          double ns = 0;
+          const int R = shapes[q][0], nb = shapes[q][1];
+          const int e = time_ns(timer, stream, reps, [&] {
+            return run_section_specialised_shape(cand[a], pa.data(), &sections[k], n, R, nb, stream);
+          }, &ns);
+          if (e == ADHA_ENOTIMPL) {
+            clear_error();
+            continue;
+          }
+          rc = e;
+          if (!rc && ns < entry) {
+            entry = ns;
+            tuning_store(tuning_key(cand[a], &sections[k], n, false), R, 8 + (nb == 1 ? 4 : 0));
+          }
+        }
+      }
+    }
+  }
   // Fused runs: each run is timed in the kFusedLayouts candidates where its sections cost least
   // one by one (the others stay +inf); under autotuning, with four launch shapes (records per
   // chunk x chunk buffers, kept in the tuning cache).  Fusing reads every field once instead of once per section, so a layout that

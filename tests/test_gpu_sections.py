@@ -280,3 +280,45 @@ def test_sections_chunk_buffers(P, buffers, R, wb):
         P.adha_tune_section_buffers(0)
         P.adha_tune_writeback(0)
         P.adha_tune_override(0)
+
+
+
+@pytest.mark.parametrize("k", range(9))
+def test_stress_sections_specialised(P, k):
+    """Each stress section as a one-section run specialised at run time (the executor's choice
+    when tuning finds it faster) gives the oracle's bytes in four layouts; the profiler sees it."""
+    wl = synth.config2(n=3 * 128 * 152 + 45)
+    P.adha_tune_section_jit(2)
+    try:
+        for groups in _layouts(wl.F, 80 + k):
+            P.adha_profile_start()
+            _check_section(P, wl, wl.sections[k], groups)
+            recs = P.adha_profile_stop()
+            assert [r["kind"] for r in recs] == ["section_specialised"] and recs[0]["op"] == "mix"
+    finally:
+        P.adha_tune_section_jit(0)
+
+
+def test_other_sections_specialised(P):
+    """Particle (gather through perm included), medical-chain and tiny-program sections
+    specialised; a section with a save buffer keeps the library kernel."""
+    P.adha_tune_section_jit(2)
+    try:
+        wl = synth.config3(n=2 * 128 * 152 + 7)
+        perm = wl.perm()
+        for k, sec in enumerate(wl.sections):
+            _check_section(P, wl, sec, _layouts(wl.F, 90 + k)[k % 4], perm)
+        wl = synth.medical(n=70001)
+        perm = wl.perm()
+        for k, sec in enumerate(wl.sections):
+            _check_section(P, wl, sec, _layouts(wl.F, 95 + k)[k % 4], perm)
+        for n in [1, 33, 4099]:
+            wl = synth.config1(n=n)
+            for k, sec in enumerate(wl.sections):
+                _check_section(P, wl, sec, _layouts(wl.F, n + k)[k % 4])
+        wl = synth.config5(n=30011, n_sections=4)
+        P.adha_profile_start()
+        _check_section(P, wl, wl.sections[0], oracle.soa(wl.F), save=True)
+        assert [r["kind"] for r in P.adha_profile_stop()] == ["section"]
+    finally:
+        P.adha_tune_section_jit(0)
