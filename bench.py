@@ -913,15 +913,15 @@ def run_workload(name, P, torch, args, world, dist, local, sub=False):
                            cache=args.cost_cache)
     if name == "particles":
         return program_run(P, torch, synth.config3(n=1 << (args.n_log2 or 25)), args, "particles", world, dist, local,
-                           autotune=not sub, fuse=0 if sub else 10, cpu=not args.no_cpu, steps=steps, warmup=warmup,
+                           autotune=True, fuse=0 if sub else 10, cpu=not args.no_cpu, steps=steps, warmup=warmup,
                            reps=1 if sub else 2, cache=args.cost_cache)
     if name == "kmeans":
         return program_run(P, torch, synth.kmeans(n=args.n_log2 and (1 << args.n_log2) or 8388608), args, "kmeans",
-                           world, dist, local, autotune=not sub, fuse=0, cpu=not args.no_cpu, steps=steps,
+                           world, dist, local, autotune=True, fuse=0, cpu=not args.no_cpu, steps=steps,
                            warmup=warmup, reps=1 if sub else 2, cache=args.cost_cache)
     if name == "medical":
         return program_run(P, torch, synth.medical(n=args.n_log2 and (1 << args.n_log2) or 256 ** 3), args, "medical",
-                           world, dist, local, autotune=not sub, fuse=0 if sub else 7, cpu=not args.no_cpu,
+                           world, dist, local, autotune=True, fuse=0 if sub else 7, cpu=not args.no_cpu,
                            steps=steps, warmup=warmup, reps=1 if sub else 2, cache=args.cost_cache)
     if name == "batched":
         return batched_run(P, torch, args, world, dist, local, steps=steps, warmup=warmup, cpu=not args.no_cpu)

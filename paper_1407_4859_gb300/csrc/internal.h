@@ -17,6 +17,8 @@ namespace adha {
 constexpr int kMaxMoves = 256;         // moves (fields + padding pieces) over all built destination records
 constexpr int kMaxStride = 4095;       // bytes per struct
 constexpr int kSmemLimit = 227 * 1024; // dynamic shared memory one CTA may use
+constexpr size_t kSmemPerSM = 228 * 1024;       // shared memory of one SM
+constexpr size_t kSmemReservedPerCTA = 1024;    // taken by the system from it for every resident CTA
 
 inline int dtype_size(int d) { return d == ADHA_F64 ? 8 : (d == ADHA_BF16 ? 2 : 4); }
 

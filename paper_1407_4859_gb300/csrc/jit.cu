@@ -11,6 +11,7 @@
 #include <dlfcn.h>
 #include <nvrtc.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -239,8 +240,13 @@ bool jit_source(const FusedArgs& a, int F, int buffers, std::string* src, std::s
          ", fr, a.tanh_p, a.tanh_q, nullptr, x, i, pj);\n";
   o += "  }\n};\n}  // namespace adha\n\n";
   o.replace(o.find("@OPS@"), 5, ops);
-  o += "extern \"C\" __global__ void __launch_bounds__(adha::kThreads) adha_fused_window(const __grid_constant__ "
-       "adha::FusedArgs a) {\n  adha::fused_window<adha::W>(a);\n}\n";
+  // as many CTAs per SM as the chunk buffers leave room for, up to three: registers are capped to
+  // match (80 a thread at three), so that registers do not become the tighter limit
+  const size_t smem = (size_t)kWarps * buffers * a.in_bytes;
+  const int by_smem = (int)(kSmemPerSM / (smem + kSmemReservedPerCTA));
+  const int min_blocks = std::max(1, std::min(3, by_smem));
+  o += "extern \"C\" __global__ void __launch_bounds__(adha::kThreads, " + std::to_string(min_blocks) +
+       ") adha_fused_window(const __grid_constant__ adha::FusedArgs a) {\n  adha::fused_window<adha::W>(a);\n}\n";
   *src = std::move(o);
   return true;
 }
