@@ -283,12 +283,20 @@ int adha_measure(const adha_schema* schema, int64_t n, const adha_layout* in_lay
   }
   // Specialised sections (autotuning, not differentiable, when the run-time compiler can be
   // loaded): each section also as a one-section run compiled for it, in the kJitSectionLayouts
-  // candidates where the library's kernel did best, under six chunk shapes (32 / 64 / 128 records x
-  // one or two buffers).  All are compiled first, in parallel host threads; a faster time
-  // replaces the entry and its tuning says "specialised" (mode + 8).
+  // candidates where the library's kernel did best and in the one that PDL on the table so far
+  // picks for it (a plan keeps a layout across sections to save remaps, so that one is often
+  // none of the three), under six chunk shapes (32 / 64 / 128 records x one or two buffers).  All
+  // are compiled first, in parallel host threads; a faster time replaces the entry and its tuning
+  // says "specialised" (mode + 8).
   if ((flags & ADHA_MEASURE_AUTOTUNE) && !diff && !rc && jit_available(nullptr)) {
     constexpr int kJitSectionLayouts = 3;
     const int shapes[6][2] = {{32, 1}, {32, 2}, {64, 1}, {64, 2}, {128, 1}, {128, 2}};
+    std::vector<int32_t> pre(n_sec, -1);
+    double pre_total = 0;
+    if (pdl_solve(t, 0, pre.data(), &pre_total)) {
+      clear_error();
+      std::fill(pre.begin(), pre.end(), -1);
+    }
     std::vector<std::vector<int>> top(n_sec);
     std::vector<bool> any(L, false);
     std::vector<FusedArgs> jargs;
@@ -297,8 +305,10 @@ int adha_measure(const adha_schema* schema, int64_t n, const adha_layout* in_lay
       std::vector<std::pair<double, int>> by;
       for (int a = 0; a < L; ++a) by.push_back({t->section_ns[(size_t)k * L + a], a});
       std::sort(by.begin(), by.end());
-      for (int j = 0; j < (int)by.size() && j < kJitSectionLayouts; ++j) {
-        const int a = by[j].second;
+      std::vector<int> pick;
+      for (int j = 0; j < (int)by.size() && j < kJitSectionLayouts; ++j) pick.push_back(by[j].second);
+      if (pre[k] >= 0 && pre[k] < L && std::find(pick.begin(), pick.end(), pre[k]) == pick.end()) pick.push_back(pre[k]);
+      for (const int a : pick) {
         bool ok = false;
         for (int q = 0; q < 6; ++q) {
           FusedArgs x;
