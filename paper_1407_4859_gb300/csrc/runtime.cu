@@ -709,35 +709,6 @@ static int host_pipe(HostPipe** out) {
 
 static int64_t slice_records(int64_t n, int n_slices) { return (n + n_slices - 1) / n_slices; }
 
-// The slices (first record, records) of a batch of n records cut for n_slices buffer sets of ns
-// records: with four or more slices the first two and the last two are a quarter and a half of ns
-// (multiples of 1024 records), so that the upload before the first kernel and the download after
-// the last one, which nothing overlaps, are short; the slices between are ns records, the last of
-// them what remains.  Every slice fits a buffer set.
-static std::vector<std::pair<int64_t, int64_t>> slice_schedule(int64_t n, int n_slices) {
-  const int64_t ns = slice_records(n, n_slices);
-  std::vector<std::pair<int64_t, int64_t>> out;
-  const int64_t q = ns / 4 / 1024 * 1024, h = ns / 2 / 1024 * 1024;
-  if (n_slices >= 4 && q > 0 && 2 * (q + h) < n) {
-    std::vector<int64_t> sizes = {q, h};
-    int64_t mid = n - 2 * (q + h);
-    while (mid > 0) {
-      sizes.push_back(std::min(ns, mid));
-      mid -= sizes.back();
-    }
-    sizes.push_back(h);
-    sizes.push_back(q);
-    int64_t i0 = 0;
-    for (int64_t c : sizes) {
-      out.push_back({i0, c});
-      i0 += c;
-    }
-    return out;
-  }
-  for (int64_t i0 = 0; i0 < n; i0 += ns) out.push_back({i0, std::min(ns, n - i0)});
-  return out;
-}
-
 // The groups of one slice between host and device: one cudaMemcpy2DAsync per run of consecutive
 // groups with equal bytes that lie back to back on the host (the groups of one pinned block, one
 // after another) and equally spaced on the device (the program allocates its group buffers one
@@ -831,10 +802,9 @@ int adha_run_program_host(const adha_schema* schema, int64_t n, const adha_layou
   for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(ss[k], pipe->start, 0);
   if (e != cudaSuccess) return cuda_fail(e, "pipeline start");
   adha_plan slice_plan;
-  const std::vector<std::pair<int64_t, int64_t>> cuts = slice_schedule(n, n_slices);
-  for (size_t k = 0; k < cuts.size(); ++k) {
+  for (int64_t k = 0, i0 = 0; i0 < n; ++k, i0 += ns) {
     const int b = (int)(k % kPipeSets);
-    const int64_t i0 = cuts[k].first, cnt = cuts[k].second;
+    const int64_t cnt = std::min(ns, n - i0);
     uint8_t* base = static_cast<uint8_t*>(workspace) + b * set_b;
     std::vector<void*> dev_in;
     carve(in, ns, base, &dev_in);
