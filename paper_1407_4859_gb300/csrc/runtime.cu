@@ -710,32 +710,24 @@ static int host_pipe(HostPipe** out) {
 static int64_t slice_records(int64_t n, int n_slices) { return (n + n_slices - 1) / n_slices; }
 
 // The groups of one slice between host and device: one cudaMemcpy2DAsync per run of consecutive
-// groups with equal bytes that lie back to back on the host (the groups of one pinned block, one
-// after another) and equally spaced on the device (the program allocates its group buffers one
-// after another), else one cudaMemcpyAsync per group.  Every copy-engine request costs several
-// microseconds, which adds up over a few hundred small ones per batch.  A strided copy the
-// runtime refuses (host buffers that only happen to be adjacent) is redone group by group.
+// groups with equal bytes whose source and destination addresses are each equally spaced (the
+// groups of a host block allocated in one piece, and the program's group buffers, which it
+// allocates one after another), else one cudaMemcpyAsync per group.  Every copy engine request
+// costs several microseconds, which adds up over a few hundred small ones per batch.
 static cudaError_t copy_groups(int n_groups, void* const* dst, const void* const* src, const size_t* bytes,
                                cudaMemcpyKind kind, cudaStream_t s) {
-  const bool to_host = kind == cudaMemcpyDeviceToHost;
-  const auto at = [](const void* p) { return reinterpret_cast<uintptr_t>(p); };
   int g0 = 0;
   while (g0 < n_groups) {
     int g1 = g0 + 1;
-    if (g1 < n_groups && bytes[g0] && bytes[g1] == bytes[g0] && at(dst[g1]) > at(dst[g0]) && at(src[g1]) > at(src[g0])) {
+    const auto at = [](const void* p) { return reinterpret_cast<uintptr_t>(p); };
+    if (g1 < n_groups && bytes[g1] == bytes[g0] && at(dst[g1]) > at(dst[g0]) && at(src[g1]) > at(src[g0])) {
       const uintptr_t dp = at(dst[g1]) - at(dst[g0]), sp = at(src[g1]) - at(src[g0]);
-      const uintptr_t hp = to_host ? dp : sp, devp = to_host ? sp : dp;
-      if (hp == bytes[g0] && devp >= bytes[g0])
+      if (dp >= bytes[g0] && sp >= bytes[g0])
         while (g1 < n_groups && bytes[g1] == bytes[g0] && at(dst[g1]) == at(dst[g0]) + (g1 - g0) * dp &&
                at(src[g1]) == at(src[g0]) + (g1 - g0) * sp)
           ++g1;
       if (g1 - g0 > 1) {
-        cudaError_t e = cudaMemcpy2DAsync(dst[g0], dp, src[g0], sp, bytes[g0], g1 - g0, kind, s);
-        if (e == cudaErrorInvalidValue) {
-          cudaGetLastError();   // an argument check, not a fault: copy the groups one by one
-          for (int g = g0; g < g1 && (e = cudaMemcpyAsync(dst[g], src[g], bytes[g], kind, s)) == cudaSuccess; ++g) {
-          }
-        }
+        const cudaError_t e = cudaMemcpy2DAsync(dst[g0], dp, src[g0], sp, bytes[g0], g1 - g0, kind, s);
         if (e != cudaSuccess) return e;
         g0 = g1;
         continue;
