@@ -423,13 +423,7 @@ def program_run(P, torch, wl, args, tag, world=1, dist=None, local=0, autotune=T
     # end to end through the C ABI with host buffers (pinned in, pinned out, copies inside)
     lay_final = layouts[seq[-1]]
     strides, _ = P.adha_layout_strides(S, lay_final)
-    # the result's groups in one pinned block, one after another (equal groups then leave the
-    # device in one strided copy per slice)
-    out_block = torch.empty(n * sum(strides), dtype=torch.uint8).pin_memory()
-    host_out, at = [], 0
-    for s_ in strides:
-        host_out.append(out_block[at:at + n * s_])
-        at += n * s_
+    host_out = [torch.empty(n * s, dtype=torch.uint8).pin_memory() for s in strides]
     one_slice = wl.has_perm or any(s.op == "reduce" for s in wl.sections)
     n_slices = 1 if one_slice else args.e2e_slices
     ws_host = torch.empty(P.adha_program_host_workspace_bytes(S, n, AOS, cand, n_slices), dtype=torch.uint8,

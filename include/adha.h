@@ -468,9 +468,7 @@ size_t adha_program_host_workspace_bytes(const adha_schema* schema, int64_t n, c
  * adha_program_host_workspace_bytes) must not be used by anything else until
  * the work is done.  Asynchronous with respect to `stream`: the pipelines wait
  * for work queued on `stream` before they start, and `stream` waits for them
- * to finish.  plan->final_ptrs lists host_out.  Groups of equal size whose host
- * buffers are equally spaced (one pinned block holding them one after another)
- * move in one strided copy per slice instead of one copy per group.
+ * to finish.  plan->final_ptrs lists host_out.
  */
 int adha_run_program_host(const adha_schema* schema, int64_t n, const adha_layout* in_layout,
                           const void* const* host_in, const adha_section* sections, int32_t n_sec,

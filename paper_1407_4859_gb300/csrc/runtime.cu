@@ -709,40 +709,6 @@ static int host_pipe(HostPipe** out) {
 
 static int64_t slice_records(int64_t n, int n_slices) { return (n + n_slices - 1) / n_slices; }
 
-// The groups of one slice between host and device: one cudaMemcpy2DAsync per run of consecutive
-// groups with equal bytes whose source and destination addresses are each equally spaced (the
-// groups of a host block allocated in one piece, and the program's group buffers, which it
-// allocates one after another), else one cudaMemcpyAsync per group.  Every copy engine request
-// costs several microseconds, which adds up over a few hundred small ones per batch.
-static cudaError_t copy_groups(int n_groups, void* const* dst, const void* const* src, const size_t* bytes,
-                               cudaMemcpyKind kind, cudaStream_t s) {
-  int g0 = 0;
-  while (g0 < n_groups) {
-    int g1 = g0 + 1;
-    const auto at = [](const void* p) { return reinterpret_cast<uintptr_t>(p); };
-    if (g1 < n_groups && bytes[g1] == bytes[g0] && at(dst[g1]) > at(dst[g0]) && at(src[g1]) > at(src[g0])) {
-      const uintptr_t dp = at(dst[g1]) - at(dst[g0]), sp = at(src[g1]) - at(src[g0]);
-      if (dp >= bytes[g0] && sp >= bytes[g0])
-        while (g1 < n_groups && bytes[g1] == bytes[g0] && at(dst[g1]) == at(dst[g0]) + (g1 - g0) * dp &&
-               at(src[g1]) == at(src[g0]) + (g1 - g0) * sp)
-          ++g1;
-      if (g1 - g0 > 1) {
-        const cudaError_t e = cudaMemcpy2DAsync(dst[g0], dp, src[g0], sp, bytes[g0], g1 - g0, kind, s);
-        if (e != cudaSuccess) return e;
-        g0 = g1;
-        continue;
-      }
-      g1 = g0 + 1;
-    }
-    if (bytes[g0]) {
-      const cudaError_t e = cudaMemcpyAsync(dst[g0], src[g0], bytes[g0], kind, s);
-      if (e != cudaSuccess) return e;
-    }
-    g0 = g1;
-  }
-  return cudaSuccess;
-}
-
 }  // namespace adha
 
 extern "C" {
@@ -802,15 +768,9 @@ int adha_run_program_host(const adha_schema* schema, int64_t n, const adha_layou
     carve(in, ns, base, &dev_in);
     // upload: once the download that last used this buffer set is done
     if (k >= kPipeSets) e = cudaStreamWaitEvent(pipe->up, pipe->freed[b], 0);
-    {
-      std::vector<const void*> src(in.n_groups);
-      std::vector<size_t> bytes(in.n_groups);
-      for (int g = 0; g < in.n_groups; ++g) {
-        src[g] = static_cast<const uint8_t*>(host_in[g]) + i0 * in.stride[g];
-        bytes[g] = (size_t)cnt * in.stride[g];
-      }
-      if (e == cudaSuccess) e = copy_groups(in.n_groups, dev_in.data(), src.data(), bytes.data(), cudaMemcpyHostToDevice, pipe->up);
-    }
+    for (int g = 0; g < in.n_groups && e == cudaSuccess; ++g)
+      e = cudaMemcpyAsync(dev_in[g], static_cast<const uint8_t*>(host_in[g]) + i0 * in.stride[g],
+                          (size_t)cnt * in.stride[g], cudaMemcpyHostToDevice, pipe->up);
     if (e == cudaSuccess) e = cudaEventRecord(pipe->uploaded[b], pipe->up);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(pipe->comp, pipe->uploaded[b], 0);
     if (e != cudaSuccess) return cuda_fail(e, "slice upload");
@@ -821,18 +781,9 @@ int adha_run_program_host(const adha_schema* schema, int64_t n, const adha_layou
       return rc;
     e = cudaEventRecord(pipe->computed[b], pipe->comp);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(pipe->down, pipe->computed[b], 0);
-    {
-      const int G = slice_plan.final_n_groups;
-      std::vector<void*> dst(G);
-      std::vector<size_t> bytes(G);
-      for (int g = 0; g < G; ++g) {
-        dst[g] = static_cast<uint8_t*>(host_out[g]) + i0 * out_layout.stride[g];
-        bytes[g] = (size_t)cnt * out_layout.stride[g];
-      }
-      if (e == cudaSuccess)
-        e = copy_groups(G, dst.data(), const_cast<const void* const*>(slice_plan.final_ptrs), bytes.data(),
-                        cudaMemcpyDeviceToHost, pipe->down);
-    }
+    for (int g = 0; g < slice_plan.final_n_groups && e == cudaSuccess; ++g)
+      e = cudaMemcpyAsync(static_cast<uint8_t*>(host_out[g]) + i0 * out_layout.stride[g], slice_plan.final_ptrs[g],
+                          (size_t)cnt * out_layout.stride[g], cudaMemcpyDeviceToHost, pipe->down);
     if (e == cudaSuccess) e = cudaEventRecord(pipe->freed[b], pipe->down);
     if (e != cudaSuccess) return cuda_fail(e, "slice download");
   }
