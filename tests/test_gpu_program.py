@@ -129,28 +129,48 @@ def test_full_size_program_sampled(P, make):
         assert np.array_equal(got.view(np.uint8), np.ascontiguousarray(want[f]).view(np.uint8)), "field %d" % f
 
 
+def _pinned_groups(sizes, block):
+    """Pinned host buffers of the given sizes: separate, or views of one block one after another."""
+    if not block:
+        return [torch.zeros(s, dtype=torch.uint8).pin_memory() for s in sizes]
+    whole = torch.zeros(sum(sizes), dtype=torch.uint8).pin_memory()
+    out, at = [], 0
+    for s in sizes:
+        out.append(whole[at:at + s])
+        at += s
+    return out
+
+
+@pytest.mark.parametrize("block", [False, True])
+@pytest.mark.parametrize("in_soa", [False, True])
 @pytest.mark.parametrize("slices", [1, 3, 8])
-def test_host_program_pipeline(P, slices):
-    """adha_run_program_host: host buffers in, host buffers out, slices pipelined on two streams."""
+def test_host_program_pipeline(P, slices, in_soa, block):
+    """adha_run_program_host: host buffers in, host buffers out, slices pipelined on two streams;
+    AoS or SoA input, host groups separate or views of one block."""
     wl = synth.config2(n=200003)
     n = wl.n
     S, AOS, cand, secs = _setup(P, wl)
+    IN = P.Layout.soa(wl.F) if in_soa else AOS
     fields = oracle.initial_fields(wl)
     want = oracle.run_program_fields(wl, [a.copy() for a in fields])
-    host_in = [torch.from_numpy(b).pin_memory() for b in oracle.from_fields(n, wl.dtypes, AOS.groups, fields)]
-    costs = P.adha_measure(S, n, AOS, [h.cuda() for h in host_in], secs, cand)
+    packed = oracle.from_fields(n, wl.dtypes, IN.groups, fields)
+    host_in = _pinned_groups([b.size for b in packed], block)
+    for h, b in zip(host_in, packed):
+        h.copy_(torch.from_numpy(b))
+    costs = P.adha_measure(S, n, IN, [h.cuda() for h in host_in], secs, cand)
     _, seq = P.adha_pdl_solve(costs)
     out_layout = cand.layouts[seq[-1]]
     strides, _ = P.adha_layout_strides(S, out_layout)
-    host_out = [torch.zeros(n * s, dtype=torch.uint8).pin_memory() for s in strides]
-    ws = torch.empty(P.adha_program_host_workspace_bytes(S, n, AOS, cand, slices), dtype=torch.uint8, device="cuda")
-    plan = P.adha_run_program_host(S, n, AOS, host_in, secs, cand, host_out, costs=costs, workspace=ws, n_slices=slices)
+    host_out = _pinned_groups([n * s for s in strides], block)
+    ws = torch.empty(P.adha_program_host_workspace_bytes(S, n, IN, cand, slices), dtype=torch.uint8, device="cuda")
+    plan = P.adha_run_program_host(S, n, IN, host_in, secs, cand, host_out, costs=costs, workspace=ws, n_slices=slices)
     torch.cuda.synchronize()
     assert list(plan.layout_of_section[:len(wl.sections)]) == seq
     assert_fields_equal(oracle.to_fields(n, wl.dtypes, out_layout.groups, [h.numpy() for h in host_out]), want,
                         "host program, %d slices" % slices)
     # the inputs are host data: untouched
-    assert np.array_equal(host_in[0].numpy(), oracle.from_fields(n, wl.dtypes, AOS.groups, fields)[0])
+    for h, b in zip(host_in, packed):
+        assert np.array_equal(h.numpy(), b)
 
 
 def test_host_program_gather_needs_one_slice(P):
