@@ -424,7 +424,7 @@ def program_run(P, torch, wl, args, tag, world=1, dist=None, local=0, autotune=T
     lay_final = layouts[seq[-1]]
     strides, _ = P.adha_layout_strides(S, lay_final)
     host_out = [torch.empty(n * s, dtype=torch.uint8).pin_memory() for s in strides]
-    one_slice = wl.has_perm or any(s.op == "reduce" for s in wl.sections)
+    one_slice = wl.has_perm   # a gather reads other records; a reduce adds slice by slice
     n_slices = 1 if one_slice else args.e2e_slices
     ws_host = torch.empty(P.adha_program_host_workspace_bytes(S, n, AOS, cand, n_slices), dtype=torch.uint8,
                           device="cuda")

@@ -463,8 +463,10 @@ size_t adha_program_host_workspace_bytes(const adha_schema* schema, int64_t n, c
  * buffer sets), so copies in both directions and kernels overlap.  The plan is solved once (or taken as fixed) before any data
  * moves; the result is written in the plan's final layout (the last section's
  * candidate, or in_layout with opts->return_to_input), host_out[g] holding
- * n * stride(g) bytes.  Sections that read through a permutation or reduce over
- * all records need every record: with one of those n_slices must be 1.  The workspace (device,
+ * n * stride(g) bytes.  Sections that read through a permutation need every
+ * record: with one of those n_slices must be 1.  A REDUCE section's result is
+ * zeroed once and every slice adds its records' sums into it (exact integer
+ * sums, so the total is the one of a single pass).  The workspace (device,
  * adha_program_host_workspace_bytes) must not be used by anything else until
  * the work is done.  Asynchronous with respect to `stream`: the pipelines wait
  * for work queued on `stream` before they start, and `stream` waits for them

@@ -212,6 +212,7 @@ static thread_local int t_section_buffers = 0;  // section chunk buffers per war
 static thread_local int t_fused_buffers = 0;    // fused runs: 0 tuned or default, else chunk buffers per warp
 static thread_local int t_fused_jit = 0;        // fused runs: 0 as tuned, 1 library kernel, 2 specialised at run time
 static thread_local int t_section_jit = 0;      // sections: 0 as tuned, 1 library kernel, 2 specialised where possible
+static thread_local bool t_reduce_accumulate = false;   // REDUCE adds into its result (host pipeline slices)
 static thread_local int t_remap_direct = 0;     // 1: remaps store one-field destination groups directly
 static thread_local int t_remap_pieces = 0;     // 0: tuned or automatic, 1 + piece-table bits otherwise
 
@@ -733,6 +734,7 @@ static int plan_section(const Layout& L, void* const* ptrs, const adha_section* 
     }
     a.in_bytes = off;
     a.buffers = buffers;
+    a.accumulate = t_reduce_accumulate ? 1 : 0;
     // vector mapping: every staged group and every written field's group is one field wide
     // (and `save`, if any, aligned for the chunk's vector stores)
     const bool vec_op = s->op == ADHA_OP_MIX || s->op == ADHA_OP_AXPB || s->op == ADHA_OP_MUL || s->op == ADHA_OP_TANH;
@@ -1046,6 +1048,7 @@ int fused_jit_args(const Layout& L, const adha_section* s, int m, int64_t n, int
 }
 
 void set_fused_jit(int mode) { t_fused_jit = mode; }
+void set_reduce_accumulate(bool on) { t_reduce_accumulate = on; }
 
 // The fused run's specialised source, compiled (and loaded into the process's cache when `load`).
 int fused_jit_build(const Layout& L, const adha_section* s, int m, int64_t n, int chunk, int buffers, int load,

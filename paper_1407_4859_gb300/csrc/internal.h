@@ -95,6 +95,7 @@ struct SectionArgs {
   int32_t n_writeback;
   int32_t vec;                        // 1: every accessed group is one field wide; lane = M consecutive records
   int32_t buffers;                    // chunk buffers per warp: 2 (the next chunk staged during this one) or 1
+  int32_t accumulate;                 // REDUCE: add into the result as it is (else it is zeroed first)
   FieldRef f[kMaxFields];
   float tanh_p[8], tanh_q[8];   // tanh polynomial coefficients (7 used each)
   const int32_t* perm;
@@ -141,6 +142,9 @@ void tuning_store(const std::string& key, int R, int wb);
 void set_overrides(int R, int wb, int buffers = 0);
 void set_fused_overrides(int R, int buffers);
 void set_fused_jit(int mode);   // 0 as tuned, 1 library kernel, 2 specialised
+// REDUCE sections launched later by the calling thread add into their result instead of zeroing it
+// first (the host pipeline zeroes it once and reduces slice by slice).
+void set_reduce_accumulate(bool on);
 // One section as a one-section run specialised at run time with chunk shape (R, buffers), profiled
 // as a section; ADHA_ENOTIMPL (nothing launched) where it cannot be.
 int run_section_specialised_shape(const Layout& L, void* const* ptrs, const adha_section* s, int64_t n, int R,

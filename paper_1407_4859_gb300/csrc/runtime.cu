@@ -738,9 +738,8 @@ int adha_run_program_host(const adha_schema* schema, int64_t n, const adha_layou
   if (!plan || !sections || n_sec < 1 || n_sec > ADHA_MAX_SECTIONS || n < 0 || n_slices < 1)
     return fail(ADHA_EINVAL, "bad host-program arguments");
   for (int k = 0; k < n_sec; ++k)
-    if ((sections[k].read_at_perm_mask || sections[k].op == ADHA_OP_REDUCE) && n_slices > 1)
-      return fail(ADHA_EINVAL, "section %d reads through a permutation or reduces over all records: it needs every "
-                               "record, use one slice", k);
+    if (sections[k].read_at_perm_mask && n_slices > 1)
+      return fail(ADHA_EINVAL, "section %d reads through a permutation: it needs every record, use one slice", k);
   const int L = (int)cand.size();
   // the plan (and with it the result's layout) is fixed before any data moves
   if (costs && (costs->n_sections != n_sec || costs->n_layouts != L)) return fail(ADHA_EINVAL, "cost table does not match");
@@ -759,6 +758,24 @@ int adha_run_program_host(const adha_schema* schema, int64_t n, const adha_layou
   cudaStream_t ss[3] = {pipe->up, pipe->comp, pipe->down};
   for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(ss[k], pipe->start, 0);
   if (e != cudaSuccess) return cuda_fail(e, "pipeline start");
+  // a REDUCE's result is zeroed once and every slice adds its records' sums into it (integer
+  // sums: the total does not depend on how the records are cut)
+  bool any_reduce = false;
+  for (int k = 0; k < n_sec && e == cudaSuccess; ++k)
+    if (sections[k].op == ADHA_OP_REDUCE) {
+      any_reduce = true;
+      const int K = sections[k].arg[1];
+      int d = 0;
+      for (int f = 0; f < in.F; ++f)
+        d += f != sections[k].arg[0] && ((sections[k].read_mask >> f) & 1) ? 1 : 0;
+      if (sections[k].aux) e = cudaMemsetAsync(const_cast<void*>(sections[k].aux), 0, (size_t)K * (d + 1) * 8, pipe->comp);
+    }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(reduce result)");
+  struct Accumulate {   // REDUCE adds into its result during the slices, on this thread only
+    bool on;
+    explicit Accumulate(bool o) : on(o) { if (on) set_reduce_accumulate(true); }
+    ~Accumulate() { if (on) set_reduce_accumulate(false); }
+  } accumulate(any_reduce);
   adha_plan slice_plan;
   for (int64_t k = 0, i0 = 0; i0 < n; ++k, i0 += ns) {
     const int b = (int)(k % kPipeSets);

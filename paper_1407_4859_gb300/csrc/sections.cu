@@ -222,7 +222,7 @@ template <int OP, int M, bool VEC>
 static int launch_om(const SectionArgs& a, int grid, size_t smem, void* stream) {
   cudaError_t e = cudaFuncSetAttribute(section_kernel<OP, M, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(section)");
-  if (OP == ADHA_OP_REDUCE) {   // the sums are added into a zeroed result
+  if (OP == ADHA_OP_REDUCE && !a.accumulate) {   // the sums are added into a zeroed result
     const int K = a.s.arg[1], d = a.s.rd_off[ADHA_F32 + 1] - a.s.rd_off[ADHA_F32];
     e = cudaMemsetAsync(const_cast<void*>(a.s.aux), 0, (size_t)K * (d + 1) * 8, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(reduce result)");

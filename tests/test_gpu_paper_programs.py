@@ -216,3 +216,34 @@ def test_gather_probe_reads_the_permuted_records(P, rec_bytes, n):
     torch.cuda.synchronize()
     want = table.view(n, rec_bytes)[perm.long()]
     assert torch.equal(out.view(n, rec_bytes), want)
+
+
+@pytest.mark.parametrize("slices", [1, 3, 8])
+def test_kmeans_host_pipeline_reduces_slice_by_slice(P, slices):
+    """adha_run_program_host on the K-Means program: the reduce's result is zeroed once and every
+    slice adds its sums (exact integers), so any slice count gives the oracle's sums and counts;
+    two calls in a row give the same (the second does not add to the first)."""
+    wl = synth.kmeans(n=(1 << 17) + 29)
+    n = wl.n
+    S = P.Schema(wl.dtypes)
+    AOS = P.Layout.aos(wl.F)
+    fields = oracle.initial_fields(wl)
+    host_in = [torch.from_numpy(b).pin_memory() for b in oracle.from_fields(n, wl.dtypes, AOS.groups, fields)]
+    secs = P.Sections(wl.sections)
+    cand = P.adha_plan_sections(S, secs, P.PlanOpts(CAPS))
+    costs = P.adha_measure(S, n, AOS, [h.cuda() for h in host_in], secs, cand, reps=1)
+    _, seq = P.adha_pdl_solve(costs)
+    out_layout = cand.layouts[seq[-1]]
+    strides, _ = P.adha_layout_strides(S, out_layout)
+    host_out = [torch.zeros(n * s, dtype=torch.uint8).pin_memory() for s in strides]
+    ws = torch.empty(P.adha_program_host_workspace_bytes(S, n, AOS, cand, slices), dtype=torch.uint8, device="cuda")
+    want = [a.copy() for a in fields]
+    want[32] = want[32].view(np.int32)
+    oracle.section(wl.sections[0], wl.dtypes, want)
+    red = oracle.section(wl.sections[1], wl.dtypes, want)
+    for _ in range(2):
+        P.adha_run_program_host(S, n, AOS, host_in, secs, cand, host_out, costs=costs, workspace=ws, n_slices=slices)
+        torch.cuda.synchronize()
+        assert np.array_equal(secs.outputs[1].cpu().numpy(), red), "%d slices" % slices
+    got = oracle.to_fields(n, wl.dtypes, out_layout.groups, [h.numpy() for h in host_out])
+    assert_fields_equal(got, want, "kmeans host program, %d slices" % slices)
