@@ -9,7 +9,7 @@ import torch
 
 import oracle
 import synth
-from gpu_util import to_device, from_device, assert_fields_equal
+from gpu_util import to_device, from_device, assert_fields_equal, random_layout
 
 pytestmark = pytest.mark.gpu
 CAPS = [16, 32, 64, 128, 256, 0]
@@ -212,3 +212,53 @@ def test_program_captured_in_a_cuda_graph(P):
         torch.cuda.synchronize()
         lay, bufs = P.final_buffers(plan, S, wl.n, cand, AOS)
         assert_fields_equal(from_device(wl.n, wl.dtypes, lay.groups, bufs), want, "graph replay")
+
+
+def test_specialised_kernels_in_a_cuda_graph(P):
+    """Sections specialised at run time can be captured and replayed once compiled (a first eager
+    run compiles them); one met first during a capture is not compiled there: a section takes the
+    library's kernel, a fused run asked to be specialised fails with ADHA_ENOTIMPL and launches
+    nothing.  Every replay equals the oracle."""
+    from paper_1407_4859_gb300._lib import AdhaError, ADHA_ENOTIMPL
+    wl = synth.config2(n=(1 << 16) + 7)
+    S = P.Schema(wl.dtypes)
+    rng = np.random.default_rng(2024)
+    fields = oracle.initial_fields(wl)
+    for groups, warm in [(oracle.soa(wl.F), True), (random_layout(rng, wl.F), False)]:
+        L = P.Layout(groups)
+        src = to_device(wl.n, wl.dtypes, groups, fields)
+        bufs = [b.clone() for b in src]
+        P.adha_tune_section_jit(2)
+        try:
+            if warm:
+                for sec in wl.sections:
+                    P.adha_run_section(S, wl.n, L, bufs, P.c_section(sec))
+                torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            s = torch.cuda.Stream()
+            with torch.cuda.graph(g, stream=s, capture_error_mode="thread_local"):
+                for sec in wl.sections:
+                    P.adha_run_section(S, wl.n, L, bufs, P.c_section(sec), stream=s)
+        finally:
+            P.adha_tune_section_jit(0)
+        want = oracle.run_program_fields(wl, [a.copy() for a in fields])
+        for _ in range(2):
+            for b, x in zip(bufs, src):
+                b.copy_(x)
+            g.replay()
+            torch.cuda.synchronize()
+            assert_fields_equal(from_device(wl.n, wl.dtypes, groups, bufs), want, "replay in %r" % (groups,))
+    groups = random_layout(rng, wl.F)
+    bufs = to_device(wl.n, wl.dtypes, groups, fields)
+    P.adha_tune_fused_jit(2)
+    try:
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        with pytest.raises(AdhaError) as e:
+            with torch.cuda.graph(g, stream=s, capture_error_mode="thread_local"):
+                P.adha_run_sections_fused(S, wl.n, P.Layout(groups), bufs, P.Sections(wl.sections[:4]), stream=s)
+        assert e.value.code == ADHA_ENOTIMPL
+    finally:
+        P.adha_tune_fused_jit(0)
+    torch.cuda.synchronize()
+    assert_fields_equal(from_device(wl.n, wl.dtypes, groups, bufs), fields, "nothing launched")
