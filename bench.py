@@ -109,17 +109,40 @@ def csrc_hash():
     return h.hexdigest()[:16]
 
 
+# The device sources each kernel family is compiled from (a traffic record holds while they hash
+# the same; host planning picks launch shapes by timing, so it is not part of the key).
+KERNEL_SOURCES = {
+    "specialised": ["jit.cu", "fused_jit.cuh", "section_ops.cuh", "device_types.h", "ptx.cuh"],
+    "section": ["sections.cu", "section_ops.cuh", "device_types.h", "ptx.cuh"],
+    "section_backward": ["sections.cu", "section_ops.cuh", "device_types.h"],
+    "remap": ["remap.cu", "remap_common.cuh", "internal.h", "ptx.cuh"],
+    "batched_remap": ["batched.cu", "remap_common.cuh", "internal.h", "ptx.cuh"],
+    "fused": ["fused.cu", "section_ops.cuh", "device_types.h", "ptx.cuh"],
+}
+
+
+def kernel_sources_hash(kernel_key):
+    """Hash of the device sources of the kernel a launch-profiler key names (e.g. specialised_mix,
+    section_gather, remap, batched_remap, section_backward, fused)."""
+    fam = kernel_key if kernel_key in KERNEL_SOURCES else kernel_key.split("_")[0]
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1407_4859_gb300", "csrc")
+    for f in KERNEL_SOURCES.get(fam, []):
+        h.update(f.encode() + b"\0" + open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def traffic_for(workload, kernel_key):
     """DRAM bytes per launch of one kernel in one bench workload, from the committed ncu summary,
-    if the kernel sources have not changed since it was taken."""
+    if the kernel's device sources have not changed since it was taken."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    if d.get("csrc_hash") != csrc_hash():
-        return None
     ent = d.get("workloads", {}).get(workload, {}).get(kernel_key)
-    return None if ent is None else ent.get("dram_bytes_per_launch")
+    if ent is None or ent.get("sources_hash") != kernel_sources_hash(kernel_key):
+        return None
+    return ent.get("dram_bytes_per_launch")
 
 
 def host_cores():
@@ -917,7 +940,7 @@ def run_workload(name, P, torch, args, world, dist, local, sub=False):
                            reps=1 if sub else 2, cache=args.cost_cache)
     if name == "kmeans":
         return program_run(P, torch, synth.kmeans(n=args.n_log2 and (1 << args.n_log2) or 8388608), args, "kmeans",
-                           world, dist, local, autotune=True, fuse=0, cpu=not args.no_cpu, steps=steps,
+                           world, dist, local, autotune=True, fuse=2, cpu=not args.no_cpu, steps=steps,
                            warmup=warmup, reps=1 if sub else 2, cache=args.cost_cache)
     if name == "medical":
         return program_run(P, torch, synth.medical(n=args.n_log2 and (1 << args.n_log2) or 256 ** 3), args, "medical",

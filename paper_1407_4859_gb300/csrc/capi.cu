@@ -391,10 +391,11 @@ static int cached_occupancy(int kind, size_t smem, int* blocks) {
       return 0;
     }
   }
-  // kinds: < 100 remap (direct or not), 100 + op section, 200 + 10*M + vec fused run
+  // kinds: < 100 remap (direct or not), 100 + op section, 200 + 10*M + vec + 2*km fused run
   const int rc = kind < 100    ? remap_occupancy(kind, smem, blocks)
                  : kind < 200 ? section_occupancy(kind - 100, smem, blocks)
-                              : fused_occupancy((kind - 200) / 10, (kind - 200) % 10 != 0, smem, blocks);
+                              : fused_occupancy((kind - 200) / 10, ((kind - 200) % 10) & 1, ((kind - 200) % 10) >> 1,
+                                                smem, blocks);
   if (rc) return rc;
   std::lock_guard<std::mutex> lk(g_occ_mu);
   g_occ_cache[{kind, smem}] = *blocks;
@@ -570,6 +571,15 @@ void fill_secop_offsets(SecOp* o, const FieldRef* f) {
   for (int j = 0; j < o->wr_off[4]; ++j) o->wr_s0[j] = (int16_t)f[o->wr[j]].s0;
 }
 
+// A REDUCE sums cluster by cluster ("walk") when none of its features is a one-field slice: the
+// lanes then read one record's features from one struct, consecutive words.
+static bool reduce_walks(const Layout& L, const adha_section* s) {
+  if (s->op != ADHA_OP_REDUCE) return false;
+  for (int f = 0; f < L.F; ++f)
+    if (f != s->arg[0] && has(s->read_mask, f) && L.groups[L.group_of[f]].size() == 1) return false;
+  return true;
+}
+
 static int check_section(const Layout& L, const adha_section* s, int64_t n, bool has_save) {
   if (!s) return fail(ADHA_EINVAL, "section is NULL");
   const int F = L.F;
@@ -735,6 +745,7 @@ static int plan_section(const Layout& L, void* const* ptrs, const adha_section* 
     a.in_bytes = off;
     a.buffers = buffers;
     a.accumulate = t_reduce_accumulate ? 1 : 0;
+    a.reduce_walk = reduce_walks(L, s) ? 1 : 0;
     // vector mapping: every staged group and every written field's group is one field wide
     // (and `save`, if any, aligned for the chunk's vector stores)
     const bool vec_op = s->op == ADHA_OP_MIX || s->op == ADHA_OP_AXPB || s->op == ADHA_OP_MUL || s->op == ADHA_OP_TANH;
@@ -837,8 +848,9 @@ static int check_fused(const Layout& L, const adha_section* s, int m, int64_t n)
   }
   if (written & at_perm)
     return fail(ADHA_EINVAL, "a section of the run writes a field that a gather of the run reads through perm");
-  for (int k = 0; k < m; ++k)
-    if (s[k].op == ADHA_OP_REDUCE) return fail(ADHA_EINVAL, "a reduce section does not run in a fused run");
+  int reduces = 0;
+  for (int k = 0; k < m; ++k) reduces += s[k].op == ADHA_OP_REDUCE ? 1 : 0;
+  if (reduces > 1) return fail(ADHA_EINVAL, "a fused run holds at most one reduce section (got %d)", reduces);
   if (n > 0 && perm && reinterpret_cast<uintptr_t>(perm) % 16) return fail(ADHA_EINVAL, "perm is not 16-byte aligned");
   if (n > 0 && !perm && at_perm) return fail(ADHA_EINVAL, "gather without a permutation");
   return 0;
@@ -914,10 +926,13 @@ static int plan_fused(const Layout& L, void* const* ptrs, const adha_section* s,
   const bool want_jit = t_fused_jit == 2 || (t_fused_jit == 0 && tuned_jit);
   uint64_t staged = 0, written = 0;
   const int32_t* perm = nullptr;
+  int reduce_sec = -1, assign_sec = -1;
   for (int k = 0; k < m; ++k) {
     staged |= s[k].read_mask | s[k].write_mask;
     written |= s[k].write_mask;
     if (s[k].op == ADHA_OP_GATHER) perm = s[k].perm;
+    if (s[k].op == ADHA_OP_REDUCE) reduce_sec = k;
+    if (s[k].op == ADHA_OP_ASSIGN && assign_sec < 0) assign_sec = k;
   }
   std::vector<int> groups;
   for (int g = 0; g < L.n_groups; ++g) {
@@ -982,6 +997,10 @@ static int plan_fused(const Layout& L, void* const* ptrs, const adha_section* s,
     a.vec = vec ? 1 : 0;
     a.buffers = tuned_buffers == 1 || tuned_buffers == 2 ? tuned_buffers : kFusedBuffers;
     a.n_sec = m;
+    a.reduce_sec = reduce_sec;
+    a.assign_sec = assign_sec;
+    a.accumulate = t_reduce_accumulate ? 1 : 0;
+    a.reduce_walk = reduce_sec >= 0 && reduce_walks(L, &s[reduce_sec]) ? 1 : 0;
     plan->smem = fused_smem_bytes(a);
     if (plan->smem <= (size_t)kSmemLimit) break;
     if (R <= 32) return fail(ADHA_EINVAL, "the fused run's records are too wide for a 32-record chunk");
@@ -1013,7 +1032,7 @@ static int plan_fused(const Layout& L, void* const* ptrs, const adha_section* s,
     clear_error();                     // else the library's fused kernel
   }
   const int M = R / 32;
-  if (int rc = cached_occupancy(200 + 10 * M + a.vec, plan->smem, &blocks)) return rc;
+  if (int rc = cached_occupancy(200 + 10 * M + a.vec + 2 * (fused_is_km(a) ? 1 : 0), plan->smem, &blocks)) return rc;
   return finish_grid(a.n_chunks, blocks, &plan->grid);
 }
 

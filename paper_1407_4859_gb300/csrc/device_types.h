@@ -79,6 +79,10 @@ struct FusedArgs {
   int32_t n_sec;
   int32_t vec;                  // 1: every staged group is one field wide
   int32_t buffers;              // chunk buffers per warp (1 or 2)
+  int32_t reduce_sec;           // index of the run's REDUCE section (at most one), else -1
+  int32_t assign_sec;           // index of the run's first ASSIGN section (centroids staged per CTA), else -1
+  int32_t accumulate;           // REDUCE: add into the result as it is (else it is zeroed before the launch)
+  int32_t reduce_walk;          // REDUCE: no feature in a one-field slice (sums cluster by cluster)
   GroupRef load[kMaxGroups + 1];
   int8_t writeback[kMaxGroups + 1];
   FieldRef f[kMaxFields];

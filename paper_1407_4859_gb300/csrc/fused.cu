@@ -32,6 +32,11 @@ __host__ __device__ constexpr int fused_table_bytes(int n_sec) {
   return kSliceTable + kFieldTable + ((int)sizeof(SecOp) * n_sec + 15) / 16 * 16;
 }
 
+// After the chunk buffers: a REDUCE's two sum tables per warp (unless it walks) and its record
+// lists (see reduce_chunk_any), then an ASSIGN's centroid pair table.
+constexpr size_t kCentroidBytes = (size_t)kCentroidPairBytes;
+static_assert(kReduceTableBytes % 16 == 0 && kReduceListBytes % 16 == 0, "the centroid table stays 16-byte aligned");
+
 
 // One section on the M records of each lane of a staged chunk (r = lane + 32m), writes into the
 // chunk buffer; op is runtime (uniform over the launch).
@@ -92,7 +97,10 @@ __device__ __forceinline__ void fused_section_record(const FusedArgs& a, const F
   }
 }
 
-template <int M, bool VEC>
+// KM: the run holds a K-Means-shaped section (assign or reduce), whose per-chunk code and
+// tables are compiled into a kernel of their own, so that the registers they need do not lower
+// the occupancy of every other fused run.
+template <int M, bool VEC, bool KM>
 __global__ void __launch_bounds__(kThreads) fused_kernel(const __grid_constant__ FusedArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int n_slices = a.n_load + (a.perm_slot >= 0 ? 1 : 0);
@@ -115,7 +123,30 @@ __global__ void __launch_bounds__(kThreads) fused_kernel(const __grid_constant__
     reinterpret_cast<uint2*>(fr)[k] = reinterpret_cast<const uint2*>(a.f)[k];
   for (int k = tid; k < a.n_sec * (int)(sizeof(SecOp) / 4); k += kThreads)
     reinterpret_cast<uint32_t*>(secs)[k] = reinterpret_cast<const uint32_t*>(a.sec)[k];
+  uint8_t* extra = smem + fused_table_bytes(a.n_sec) + (size_t)kWarps * nb * a.in_bytes;
+  long long* acc = nullptr;   // REDUCE: this warp's sum tables (or register sums) and record list;
+  int* idx = nullptr;         // its counts, one cluster per lane
+  unsigned long long cnt_lane = 0;
+  long long sum[KM ? kMaxClusters : 1];
+  if (KM && a.reduce_sec >= 0) {
+    if (!a.reduce_walk) {
+      acc = reinterpret_cast<long long*>(extra) + (size_t)warp * 2 * (kMaxClusters + 1) * 32;
+      for (int k = lane; k < 2 * (kMaxClusters + 1) * 32; k += 32) acc[k] = 0;
+      extra += kReduceTableBytes;
+    }
+    idx = reinterpret_cast<int*>(extra) + warp * 32;
+    extra += kReduceListBytes;
+#pragma unroll
+    for (int k = 0; k < (KM ? kMaxClusters : 1); ++k) sum[k] = 0;
+  }
+  float* cT = nullptr;
+  if (KM && a.assign_sec >= 0) {
+    cT = reinterpret_cast<float*>(extra);
+    fill_centroid_pairs(a.sec[a.assign_sec], a.f, cT, tid, kThreads);
+  }
   __syncthreads();
+  ReduceLane rq{};
+  if (KM && a.reduce_sec >= 0) rq = reduce_lane(secs[a.reduce_sec], fr, lane, a.reduce_walk != 0);
 
   const int64_t W = (int64_t)gridDim.x * kWarps;
   auto stage = [&](int64_t ch, uint8_t* buf) {
@@ -145,7 +176,15 @@ __global__ void __launch_bounds__(kThreads) fused_kernel(const __grid_constant__
     for (int s = 0; s < a.n_sec; ++s) {
       const SecOp& so = secs[s];
       const int op = so.op;
-      if (VEC && op == ADHA_OP_MIX) mix_chunk_vec<M, true>(so, fr, cur, i0, lane);
+      if constexpr (KM) {
+        if (s == a.reduce_sec) {
+          reduce_chunk_any<M, true>(rq, cur, lane, acc, acc + (kMaxClusters + 1) * 32, idx, sum, &cnt_lane);
+          __syncwarp();
+          continue;
+        }
+      }
+      if (KM && s == a.assign_sec) assign_chunk<M>(so, fr, cur, i0, lane, cT);
+      else if (VEC && op == ADHA_OP_MIX) mix_chunk_vec<M, true>(so, fr, cur, i0, lane);
       else if (VEC && op == ADHA_OP_AXPB) chain_chunk_vec<ADHA_OP_AXPB, M, true>(so, fr, a.tanh_p, a.tanh_q, nullptr, cur, i0, lane);
       else if (VEC && op == ADHA_OP_MUL) chain_chunk_vec<ADHA_OP_MUL, M, true>(so, fr, a.tanh_p, a.tanh_q, nullptr, cur, i0, lane);
       else if (VEC && op == ADHA_OP_TANH) chain_chunk_vec<ADHA_OP_TANH, M, true>(so, fr, a.tanh_p, a.tanh_q, nullptr, cur, i0, lane);
@@ -173,54 +212,90 @@ __global__ void __launch_bounds__(kThreads) fused_kernel(const __grid_constant__
   // ragged tail: the warp whose next chunk would be n_chunks, record by record in global memory
   const int64_t t0 = a.n_chunks * R;
   if (c == a.n_chunks && t0 < a.n) {
-    for (int64_t i = t0 + lane; i < a.n; i += 32) {
-      const int32_t pj = a.perm_slot >= 0 ? a.perm[i] : 0;
-      for (int s = 0; s < a.n_sec; ++s) fused_section_record(a, fr, secs[s], i, pj);
+    if (!KM || a.reduce_sec < 0) {
+      for (int64_t i = t0 + lane; i < a.n; i += 32) {
+        const int32_t pj = a.perm_slot >= 0 ? a.perm[i] : 0;
+        for (int s = 0; s < a.n_sec; ++s) fused_section_record(a, fr, secs[s], i, pj);
+      }
+    } else {   // section by section over the tail's records: the reduce reads every lane's records
+      for (int s = 0; s < a.n_sec; ++s) {
+        __syncwarp();
+        if (s == a.reduce_sec) {
+          if constexpr (KM) reduce_tail<true>(rq, secs[s], fr, t0, a.n, lane, acc, sum, &cnt_lane);
+        } else {
+          for (int64_t i = t0 + lane; i < a.n; i += 32)
+            fused_section_record(a, fr, secs[s], i, a.perm_slot >= 0 ? a.perm[i] : 0);
+        }
+      }
+    }
+  }
+  if constexpr (KM) {
+    if (a.reduce_sec >= 0) {   // every warp adds its sums and counts into the result
+      __syncwarp();
+      reduce_flush<true>(rq, secs[a.reduce_sec], lane, acc, sum, &cnt_lane);
     }
   }
 }
 
 size_t fused_smem_bytes(const FusedArgs& a) {
-  return fused_table_bytes(a.n_sec) + (size_t)kWarps * a.buffers * a.in_bytes;
+  return fused_table_bytes(a.n_sec) + (size_t)kWarps * a.buffers * a.in_bytes +
+         (a.reduce_sec >= 0 ? (a.reduce_walk ? 0 : kReduceTableBytes) + kReduceListBytes : 0) +
+         (a.assign_sec >= 0 ? kCentroidBytes : 0);
 }
 
-template <int M, bool VEC>
+template <int M, bool VEC, bool KM>
 static int launch_m(const FusedArgs& a, int grid, size_t smem, void* stream) {
-  cudaError_t e = cudaFuncSetAttribute(fused_kernel<M, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(fused_kernel<M, VEC, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(fused)");
-  fused_kernel<M, VEC><<<grid, kThreads, smem, (cudaStream_t)stream>>>(a);
+  if (a.reduce_sec >= 0 && !a.accumulate) {   // the sums are added into a zeroed result
+    const SecOp& so = a.sec[a.reduce_sec];
+    const int K = so.arg[1], d = so.rd_off[ADHA_F32 + 1] - so.rd_off[ADHA_F32];
+    e = cudaMemsetAsync(const_cast<void*>(so.aux), 0, (size_t)K * (d + 1) * 8, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(reduce result)");
+  }
+  fused_kernel<M, VEC, KM><<<grid, kThreads, smem, (cudaStream_t)stream>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
   return 0;
 }
 
-int launch_fused(const FusedArgs& a, int grid, size_t smem, void* stream) {
-  if (a.vec && a.R == 32) return launch_m<1, true>(a, grid, smem, stream);
-  if (a.vec && a.R == 64) return launch_m<2, true>(a, grid, smem, stream);
-  if (a.vec && a.R == 128) return launch_m<4, true>(a, grid, smem, stream);
+template <bool KM>
+static int launch_km(const FusedArgs& a, int grid, size_t smem, void* stream) {
+  if (a.vec && a.R == 32) return launch_m<1, true, KM>(a, grid, smem, stream);
+  if (a.vec && a.R == 64) return launch_m<2, true, KM>(a, grid, smem, stream);
+  if (a.vec && a.R == 128) return launch_m<4, true, KM>(a, grid, smem, stream);
   switch (a.R) {
-    case 32: return launch_m<1, false>(a, grid, smem, stream);
-    case 64: return launch_m<2, false>(a, grid, smem, stream);
-    default: return launch_m<4, false>(a, grid, smem, stream);
+    case 32: return launch_m<1, false, KM>(a, grid, smem, stream);
+    case 64: return launch_m<2, false, KM>(a, grid, smem, stream);
+    default: return launch_m<4, false, KM>(a, grid, smem, stream);
   }
 }
 
-template <int M, bool VEC>
+int launch_fused(const FusedArgs& a, int grid, size_t smem, void* stream) {
+  return fused_is_km(a) ? launch_km<true>(a, grid, smem, stream) : launch_km<false>(a, grid, smem, stream);
+}
+
+template <int M, bool VEC, bool KM>
 static int occ_m(size_t smem, int* blocks) {
-  cudaError_t e = cudaFuncSetAttribute(fused_kernel<M, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(fused_kernel<M, VEC, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(fused)");
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fused_kernel<M, VEC>, kThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fused_kernel<M, VEC, KM>, kThreads, smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(fused)");
   return 0;
 }
 
-int fused_occupancy(int M, bool vec, size_t smem, int* blocks) {
-  if (vec && M == 1) return occ_m<1, true>(smem, blocks);
-  if (vec && M == 2) return occ_m<2, true>(smem, blocks);
-  if (vec && M == 4) return occ_m<4, true>(smem, blocks);
-  if (M == 1) return occ_m<1, false>(smem, blocks);
-  if (M == 2) return occ_m<2, false>(smem, blocks);
-  return occ_m<4, false>(smem, blocks);
+template <bool KM>
+static int occ_km(int M, bool vec, size_t smem, int* blocks) {
+  if (vec && M == 1) return occ_m<1, true, KM>(smem, blocks);
+  if (vec && M == 2) return occ_m<2, true, KM>(smem, blocks);
+  if (vec && M == 4) return occ_m<4, true, KM>(smem, blocks);
+  if (M == 1) return occ_m<1, false, KM>(smem, blocks);
+  if (M == 2) return occ_m<2, false, KM>(smem, blocks);
+  return occ_m<4, false, KM>(smem, blocks);
+}
+
+int fused_occupancy(int M, bool vec, bool km, size_t smem, int* blocks) {
+  return km ? occ_km<true>(M, vec, smem, blocks) : occ_km<false>(M, vec, smem, blocks);
 }
 
 }  // namespace adha

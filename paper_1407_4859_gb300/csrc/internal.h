@@ -96,6 +96,7 @@ struct SectionArgs {
   int32_t vec;                        // 1: every accessed group is one field wide; lane = M consecutive records
   int32_t buffers;                    // chunk buffers per warp: 2 (the next chunk staged during this one) or 1
   int32_t accumulate;                 // REDUCE: add into the result as it is (else it is zeroed first)
+  int32_t reduce_walk;                // REDUCE: no feature in a one-field slice (sums cluster by cluster)
   FieldRef f[kMaxFields];
   float tanh_p[8], tanh_q[8];   // tanh polynomial coefficients (7 used each)
   const int32_t* perm;
@@ -179,7 +180,9 @@ bool jit_source(const FusedArgs& a, int F, int buffers, std::string* src, std::s
 int jit_compile_only(const std::string& src);   // compile, no device needed, nothing loaded
 std::string jit_last_log();
 size_t fused_smem_bytes(const FusedArgs& a);
-int fused_occupancy(int M, bool vec, size_t smem, int* blocks);
+int fused_occupancy(int M, bool vec, bool km, size_t smem, int* blocks);
+// Whether a fused run holds an assign or a reduce section (they have a kernel of their own).
+inline bool fused_is_km(const FusedArgs& a) { return a.reduce_sec >= 0 || a.assign_sec >= 0; }
 int launch_backward(const BackwardArgs& a, void* stream);
 int remap_occupancy(int unit, size_t smem, int* blocks);
 int section_occupancy(int op, size_t smem, int* blocks);

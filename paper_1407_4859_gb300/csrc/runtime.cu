@@ -240,12 +240,14 @@ int adha_measure(const adha_schema* schema, int64_t n, const adha_layout* in_lay
       auto run = [&] { return run_section_layout(cand[a], pa.data(), &sections[k], n, save, stream); };
       if (flags & ADHA_MEASURE_AUTOTUNE) {
         // every chunk size x store mode with two chunk buffers per warp, and 64 or 128 records
-        // with one (twice the resident warps; at 32 records one buffer hides too little); the
-        // fastest is kept for the executor, one buffer as store mode + 4
+        // with one (twice the resident warps; at 32 records one buffer hides too little, except
+        // for the assign and reduce sections, whose long compute per chunk wants the most warps);
+        // the fastest is kept for the executor, one buffer as store mode + 4
         double best = -1;
         int bR = 0, bW = 0;
+        const bool long_compute = sections[k].op == ADHA_OP_ASSIGN || sections[k].op == ADHA_OP_REDUCE;
         for (int nb = 2; nb >= 1 && !rc; --nb)
-          for (int R = nb == 2 ? 32 : 64; R <= 128 && !rc; R *= 2)
+          for (int R = nb == 2 || long_compute ? 32 : 64; R <= 128 && !rc; R *= 2)
             for (int wb = 1; wb <= 2 && !rc; ++wb) {
               set_overrides(R, wb, nb);
               rc = time_ns(timer, stream, reps, run, &ns);

@@ -11,6 +11,7 @@
 #endif
 
 #include "device_types.h"
+#include "ptx.cuh"
 
 // Loops over a section's listed fields: unrolled in windows specialised at run time (constant
 // bounds), left to the compiler's own choice in the library's kernels (bounds known at run time).
@@ -582,49 +583,95 @@ __device__ __forceinline__ long long fixq(float x) {
   return (long long)__float2int_rn(__fmul_rn(x, 8388608.0f));
 }
 
+// ASSIGN's centroid table in shared memory, one per CTA: for feature j and cluster k the pair
+// (c[k][j], c[k][j]) at cP[2*(j*8 + k)] (zero for k >= K), so one 16-byte load gives two
+// clusters' pairs and a pair meets two records' values in one packed instruction.
+// After the pairs, each feature's chunk-buffer offset and stride (int2), so that the per-chunk loop
+// reads them with one broadcast shared load instead of indexed loads from the parameter space.
+constexpr int kCentroidPairBytes = kMaxFields * kMaxClusters * 8 + kMaxFields * 8;
+
+__device__ __forceinline__ void fill_centroid_pairs(const SecOp& so, const FieldRef* fr, float* cP, int tid,
+                                                    int nthreads) {
+  const int j0 = so.rd_off[ADHA_F32], K = so.arg[1], d = so.rd_off[ADHA_F32 + 1] - j0;
+  const float* cent = static_cast<const float*>(so.aux);
+  for (int t = tid; t < d * kMaxClusters; t += nthreads) {
+    const int j = t / kMaxClusters, k = t - j * kMaxClusters;
+    const float v = k < K ? __ldg(cent + k * d + j) : 0.0f;
+    cP[2 * t] = v;
+    cP[2 * t + 1] = v;
+  }
+  int2* off = reinterpret_cast<int2*>(cP + 2 * kMaxFields * kMaxClusters);
+  for (int j = tid; j < d; j += nthreads) {
+    const FieldRef& F = fr[so.rd[j0 + j]];
+    off[j] = make_int2(F.s0, F.ss);
+  }
+}
+
 // ASSIGN over the M records of each lane of a staged chunk (r = lane + 32m), for K clusters:
 // feature by feature, its chunk offsets are looked up once for the lane's M records and its K
-// centroid coordinates come from the CTA's transposed copy (cT[j*8 + k], two 16-byte broadcast
-// loads); the K x M distances are carried in registers (the per-record rule, in the same order).
+// centroid coordinates come from the CTA's pair table; the K x M distances are carried in
+// registers, records paired (m, m + 1) in packed fp32 instructions when M is even.  Each half
+// is the per-record rule itself: D_k = ((+0 + sq_0) + sq_1) + ..., sq_j = (x_j - c_kj)^2, every
+// operation rounded to nearest on its own, features in ascending order.
 template <int M, int K>
 __device__ __forceinline__ void assign_chunk_k(const SecOp& so, const FieldRef* fr, uint8_t* stage, int64_t i0,
-                                               int lane, const float* cT) {
-  const int j0 = so.rd_off[ADHA_F32], d = so.rd_off[ADHA_F32 + 1] - j0;
-  float D[K][M];
+                                               int lane, const float* cP) {
+  const int d = so.rd_off[ADHA_F32 + 1] - so.rd_off[ADHA_F32];
+  constexpr int H = (M + 1) / 2;   // register pairs per cluster
+  unsigned long long D[K][H];
 #pragma unroll
   for (int k = 0; k < K; ++k)
 #pragma unroll
-    for (int m = 0; m < M; ++m) D[k][m] = 0.0f;
+    for (int h = 0; h < H; ++h) D[k][h] = 0ull;   // +0.0f in both halves
+  const int2* off = reinterpret_cast<const int2*>(cP + 2 * kMaxFields * kMaxClusters);
   for (int j = 0; j < d; ++j) {
-    const FieldRef& F = fr[so.rd[j0 + j]];
-    const uint8_t* p = stage + F.s0 + lane * F.ss;
-    const int step = 32 * F.ss;
-    float x[M];
+    const int2 F = off[j];   // chunk-buffer offset and stride of feature j
+    const uint8_t* p = stage + F.x + lane * F.y;
+    const int step = 32 * F.y;
+    unsigned long long x2[H];
 #pragma unroll
-    for (int m = 0; m < M; ++m) x[m] = *reinterpret_cast<const float*>(p + m * step);
-    const float4 c0 = *reinterpret_cast<const float4*>(cT + j * kMaxClusters);
-    const float4 c1 = *reinterpret_cast<const float4*>(cT + j * kMaxClusters + 4);
-    const float c[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+    for (int h = 0; h < H; ++h) {
+      const float lo = *reinterpret_cast<const float*>(p + (2 * h) * step);
+      const float hi = 2 * h + 1 < M ? *reinterpret_cast<const float*>(p + (2 * h + 1) * step) : 0.0f;
+      x2[h] = f2_pack(lo, hi);
+    }
+    const ulonglong2* cp = reinterpret_cast<const ulonglong2*>(cP + 2 * j * kMaxClusters);
+    unsigned long long c2[K + 1];
+#pragma unroll
+    for (int k = 0; k < K; k += 2) {
+      const ulonglong2 v = cp[k / 2];
+      c2[k] = v.x;
+      c2[k + 1] = v.y;
+    }
 #pragma unroll
     for (int k = 0; k < K; ++k)
 #pragma unroll
-      for (int m = 0; m < M; ++m) {
-        const float df = __fsub_rn(x[m], c[k]);
-        D[k][m] = __fadd_rn(D[k][m], __fmul_rn(df, df));
+      for (int h = 0; h < H; ++h) {
+        const unsigned long long df = f2_sub_rn(x2[h], c2[k]);
+        D[k][h] = f2_add_rn(D[k][h], f2_mul_rn(df, df));
       }
   }
 #pragma unroll
-  for (int m = 0; m < M; ++m) {
-    int best = 0;
-    float bd = D[0][m];
+  for (int h = 0; h < H; ++h) {
+    float Dl[K], Dh[K];
 #pragma unroll
-    for (int k = 1; k < K; ++k)
-      if (D[k][m] < bd) {
-        bd = D[k][m];
-        best = k;
-      }
-    const int r = lane + 32 * m;
-    StagedRec{fr, stage, r, i0 + r}.template st<int32_t>(so.arg[0], best);
+    for (int k = 0; k < K; ++k) f2_unpack(D[k][h], &Dl[k], &Dh[k]);
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int m = 2 * h + e;
+      if (m >= M) break;
+      const float* Dm = e ? Dh : Dl;
+      int best = 0;
+      float bd = Dm[0];
+#pragma unroll
+      for (int k = 1; k < K; ++k)
+        if (Dm[k] < bd) {
+          bd = Dm[k];
+          best = k;
+        }
+      const int r = lane + 32 * m;
+      StagedRec{fr, stage, r, i0 + r}.template st<int32_t>(so.arg[0], best);
+    }
   }
 }
 
@@ -649,9 +696,17 @@ struct ReduceLane {
   int d, K;
   int sx, ssx, sm, ssm;   // chunk-buffer offset and stride of the lane's feature and of the membership
   int skew;               // one-field feature slice: the lane starts at its own record (spread banks)
+  bool walk;              // sum cluster by cluster into registers (see reduce_chunk_any)
 };
 
-__device__ __forceinline__ ReduceLane reduce_lane(const SecOp& so, const FieldRef* fr, int lane) {
+// Shared memory of a REDUCE per CTA: the two sum tables of every warp (when it does not walk) and
+// every warp's 32-entry record list.
+constexpr size_t kReduceTableBytes = (size_t)kWarps * 2 * (kMaxClusters + 1) * 32 * 8;
+constexpr size_t kReduceListBytes = (size_t)kWarps * 32 * 4;
+
+// walk: every feature lies in a slice wider than one field (decided on the host, which sizes the
+// shared tables only for the other way).
+__device__ __forceinline__ ReduceLane reduce_lane(const SecOp& so, const FieldRef* fr, int lane, bool walk) {
   ReduceLane q;
   const int j0 = so.rd_off[ADHA_F32];
   q.d = so.rd_off[ADHA_F32 + 1] - j0;
@@ -666,26 +721,97 @@ __device__ __forceinline__ ReduceLane reduce_lane(const SecOp& so, const FieldRe
     q.ssx = Fx.ss;
   }
   q.skew = q.ssx == 4 ? lane : 0;
+  q.walk = walk;
   return q;
 }
 
-// REDUCE over the R = 32*M records of a staged chunk.  Counts: lane = record, one ballot per
-// cluster.  Sums: lane j = feature j, its column of the warp's two (K+1) x 32 accumulator tables
-// (int64, shared memory): even records into the first, odd into the second, so that two
-// read-add-write chains are in flight (the tables never alias).  Integer sums: any order gives the
-// same result.
 template <int M>
-__device__ __forceinline__ void reduce_chunk(const ReduceLane& q, const uint8_t* stage, int lane,
-                                             long long* __restrict__ acc, long long* __restrict__ acc2,
-                                             unsigned long long* cnt) {
-  constexpr int R = 32 * M;
+__device__ __forceinline__ void reduce_sums(const ReduceLane& q, const uint8_t* stage, int lane,
+                                            long long* __restrict__ acc, long long* __restrict__ acc2);
+
+// REDUCE over the R = 32*M records of a staged chunk.  Counts: lane = record, one ballot per
+// cluster (LANECOUNT: lane k keeps cluster k's count, one register; else every lane keeps all K).
+// Sums, lane j = feature j, integer sums (any order gives the same result):
+// * walk (every feature in a slice wider than one field, e.g. AoS): for each group of 32 records
+//   the warp lists the records cluster by cluster (a counting sort by ballots into the warp's
+//   32-entry list `idx`), then, cluster by cluster, all lanes read the same listed record
+//   (consecutive words of a struct) four records at a time, adding into the register sums
+//   sum[k]: no shared-memory accumulator and no chain through memory;
+// * else (one-field slices, where the lanes reading one record would all hit one bank): each
+//   lane starts at its own record and adds every record into its row of two (K+1) x 32 tables in
+//   shared memory, even records into the first and odd into the second, so that two
+//   read-add-write chains are in flight (row K takes memberships outside [0, K)).
+template <int M, bool LANECOUNT>
+__device__ __forceinline__ void reduce_chunk_any(const ReduceLane& q, const uint8_t* stage, int lane,
+                                                 long long* __restrict__ acc, long long* __restrict__ acc2,
+                                                 int* __restrict__ idx, long long (&sum)[kMaxClusters],
+                                                 unsigned long long* cnt) {
+  if (q.walk) {
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      const int mm = *reinterpret_cast<const int32_t*>(stage + q.sm + (lane + 32 * m) * q.ssm);
+      unsigned b[kMaxClusters];
+      int start = 0;
+#pragma unroll
+      for (int k = 0; k < kMaxClusters; ++k) {
+        b[k] = k < q.K ? __ballot_sync(0xFFFFFFFFu, mm == k) : 0u;
+        const int c = __popc(b[k]);
+        if (LANECOUNT) {
+          if (lane == k) *cnt += (unsigned long long)c;
+        } else {
+          cnt[k] += (unsigned long long)c;
+        }
+        if (k < q.K && mm == k) idx[start + __popc(b[k] & lt)] = lane;
+        start += c;
+      }
+      __syncwarp();
+      if (lane < q.d) {
+        const uint8_t* px = stage + q.sx + 32 * m * q.ssx;
+        int e = 0;
+#pragma unroll
+        for (int k = 0; k < kMaxClusters; ++k) {
+          int t = e;
+          e += __popc(b[k]);
+          long long s = 0;
+          for (; t + 4 <= e; t += 4) {
+            const int r0 = idx[t], r1 = idx[t + 1], r2 = idx[t + 2], r3 = idx[t + 3];
+            const float x0 = *reinterpret_cast<const float*>(px + r0 * q.ssx);
+            const float x1 = *reinterpret_cast<const float*>(px + r1 * q.ssx);
+            const float x2 = *reinterpret_cast<const float*>(px + r2 * q.ssx);
+            const float x3 = *reinterpret_cast<const float*>(px + r3 * q.ssx);
+            s += (fixq(x0) + fixq(x1)) + (fixq(x2) + fixq(x3));
+          }
+          for (; t < e; ++t) s += fixq(*reinterpret_cast<const float*>(px + idx[t] * q.ssx));
+          sum[k] += s;
+        }
+      }
+      __syncwarp();   // the list is rewritten for the next 32 records
+    }
+    return;
+  }
 #pragma unroll
   for (int m = 0; m < M; ++m) {
     const int mm = *reinterpret_cast<const int32_t*>(stage + q.sm + (lane + 32 * m) * q.ssm);
 #pragma unroll
     for (int k = 0; k < kMaxClusters; ++k)
-      if (k < q.K) cnt[k] += (unsigned long long)__popc(__ballot_sync(0xFFFFFFFFu, mm == k));
+      if (k < q.K) {
+        const unsigned b = __ballot_sync(0xFFFFFFFFu, mm == k);
+        if (LANECOUNT) {
+          if (lane == k) *cnt += (unsigned long long)__popc(b);
+        } else {
+          cnt[k] += (unsigned long long)__popc(b);
+        }
+      }
   }
+  reduce_sums<M>(q, stage, lane, acc, acc2);
+}
+
+
+template <int M>
+__device__ __forceinline__ void reduce_sums(const ReduceLane& q, const uint8_t* stage, int lane,
+                                            long long* __restrict__ acc, long long* __restrict__ acc2) {
+  constexpr int R = 32 * M;
   if (lane < q.d) {
     long long* __restrict__ col = acc + lane;
     long long* __restrict__ col2 = acc2 + lane;
@@ -708,24 +834,53 @@ __device__ __forceinline__ void reduce_chunk(const ReduceLane& q, const uint8_t*
 }
 
 // REDUCE over records [t0, n) read from global memory (the ragged tail): lane j = feature j;
-// lane 0 also counts.
-__device__ __forceinline__ void reduce_tail(const SecOp& so, const FieldRef* fr, int64_t t0, int64_t n, int lane,
-                                            long long* acc, unsigned long long* cnt) {
-  const int K = so.arg[1];
+// counts in lane 0 (all K) or, LANECOUNT, lane k for cluster k; sums into the register sums
+// (walk) or row mm of the first shared table.
+template <bool LANECOUNT>
+__device__ __forceinline__ void reduce_tail(const ReduceLane& q, const SecOp& so, const FieldRef* fr, int64_t t0,
+                                            int64_t n, int lane, long long* acc, long long (&sum)[kMaxClusters],
+                                            unsigned long long* cnt) {
   const FieldRef& Fm = fr[so.arg[0]];
-  const int j0 = so.rd_off[ADHA_F32], d = so.rd_off[ADHA_F32 + 1] - j0;
+  const int j0 = so.rd_off[ADHA_F32];
   for (int64_t i = t0; i < n; ++i) {
     const int mm = *reinterpret_cast<const int32_t*>(Fm.g + i * Fm.gs);
-    if ((unsigned)mm >= (unsigned)K) continue;
-    if (lane == 0) {
+    if ((unsigned)mm >= (unsigned)q.K) continue;
+    if (LANECOUNT) {
+      if (lane == mm) *cnt += 1ull;
+    } else if (lane == 0) {
 #pragma unroll
       for (int k = 0; k < kMaxClusters; ++k) cnt[k] += k == mm ? 1ull : 0ull;
     }
-    if (lane < d) {
+    if (lane < q.d) {
       const FieldRef& Fx = fr[so.rd[j0 + lane]];
-      acc[mm * 32 + lane] += fixq(*reinterpret_cast<const float*>(Fx.g + i * Fx.gs));
+      const long long v = fixq(*reinterpret_cast<const float*>(Fx.g + i * Fx.gs));
+      if (q.walk) {
+#pragma unroll
+        for (int k = 0; k < kMaxClusters; ++k) sum[k] += k == mm ? v : 0ll;
+      } else {
+        acc[mm * 32 + lane] += v;
+      }
     }
   }
+}
+
+// The warp's sums and counts added into the result (K rows of [count, d sums], zeroed before
+// the launch unless the caller accumulates).
+template <bool LANECOUNT>
+__device__ __forceinline__ void reduce_flush(const ReduceLane& q, const SecOp& so, int lane, const long long* acc,
+                                             const long long (&sum)[kMaxClusters], const unsigned long long* cnt) {
+  unsigned long long* out = static_cast<unsigned long long*>(const_cast<void*>(so.aux));
+  const int d = q.d;
+#pragma unroll
+  for (int k = 0; k < kMaxClusters; ++k)
+    if (k < q.K) {
+      if (lane < d) {
+        const long long v = q.walk ? sum[k] : acc[k * 32 + lane] + acc[(kMaxClusters + 1 + k) * 32 + lane];
+        atomicAdd(out + (size_t)k * (d + 1) + 1 + lane, (unsigned long long)v);
+      }
+      if (!LANECOUNT && lane == 0) atomicAdd(out + (size_t)k * (d + 1), cnt[k]);
+    }
+  if (LANECOUNT && lane < q.K) atomicAdd(out + (size_t)lane * (d + 1), *cnt);
 }
 
 }  // namespace adha

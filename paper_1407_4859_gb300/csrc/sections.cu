@@ -33,33 +33,35 @@ __global__ void __launch_bounds__(kThreads) section_kernel(const __grid_constant
   uint8_t* buf0 = smem + kSectionTable + (size_t)warp * nb * a.in_bytes;
   uint8_t* buf1 = buf0 + (nb - 1) * a.in_bytes;
   constexpr int R = 32 * M;
-  // REDUCE: the warp's K x 32 int64 sums after the chunk buffers, its counts in registers
+  // REDUCE: counts and (walk) sums in registers; after the chunk buffers the warp's two sum
+  // tables (not walk) and its 32-entry record list (walk)
   long long* acc = nullptr;
-  unsigned long long cnt[OP == ADHA_OP_REDUCE ? kMaxClusters : 1];
+  int* idx = nullptr;
+  unsigned long long cnt = 0;   // REDUCE: lane k counts cluster k
+  long long sum[kMaxClusters];
   ReduceLane rq{};
   if constexpr (OP == ADHA_OP_REDUCE) {
-    rq = reduce_lane(a.s, a.f, lane);
-    acc = reinterpret_cast<long long*>(smem + kSectionTable + (size_t)kWarps * nb * a.in_bytes) +
-          (size_t)warp * 2 * (kMaxClusters + 1) * 32;
-    for (int k = lane; k < 2 * (kMaxClusters + 1) * 32; k += 32) acc[k] = 0;
+    rq = reduce_lane(a.s, a.f, lane, a.reduce_walk != 0);
+    uint8_t* extra = smem + kSectionTable + (size_t)kWarps * nb * a.in_bytes;
+    if (!rq.walk) {
+      acc = reinterpret_cast<long long*>(extra) + (size_t)warp * 2 * (kMaxClusters + 1) * 32;
+      for (int k = lane; k < 2 * (kMaxClusters + 1) * 32; k += 32) acc[k] = 0;
+      extra += kReduceTableBytes;
+    }
+    idx = reinterpret_cast<int*>(extra) + warp * 32;
 #pragma unroll
-    for (int k = 0; k < kMaxClusters; ++k) cnt[k] = 0;
+    for (int k = 0; k < kMaxClusters; ++k) sum[k] = 0;
   }
   for (int k = tid; k < n_slices; k += kThreads) {
     sp[k] = a.load[k].ptr;
     send[k] = a.load[k].start + R * a.load[k].stride;
     wback[k] = a.writeback[k];
   }
-  // ASSIGN: the centroids, transposed (cT[j*8 + k]; zero for k >= K), after the chunk buffers
+  // ASSIGN: the centroid pair table after the chunk buffers
   float* cT = nullptr;
   if constexpr (OP == ADHA_OP_ASSIGN) {
     cT = reinterpret_cast<float*>(smem + kSectionTable + (size_t)kWarps * nb * a.in_bytes);
-    const int K = a.s.arg[1], d = a.s.rd_off[ADHA_F32 + 1] - a.s.rd_off[ADHA_F32];
-    const float* cent = static_cast<const float*>(a.s.aux);
-    for (int t = tid; t < d * kMaxClusters; t += kThreads) {
-      const int j = t / kMaxClusters, k = t - j * kMaxClusters;
-      cT[t] = k < K ? __ldg(cent + k * d + j) : 0.0f;
-    }
+    fill_centroid_pairs(a.s, a.f, cT, tid, kThreads);
   }
   __syncthreads();
 
@@ -91,7 +93,7 @@ __global__ void __launch_bounds__(kThreads) section_kernel(const __grid_constant
     __syncwarp();
     const int64_t i0 = c * R;
     if constexpr (OP == ADHA_OP_REDUCE) {
-      reduce_chunk<M>(rq, cur, lane, acc, acc + (kMaxClusters + 1) * 32, cnt);
+      reduce_chunk_any<M, true>(rq, cur, lane, acc, acc + (kMaxClusters + 1) * 32, idx, sum, &cnt);
     } else if constexpr (OP == ADHA_OP_ASSIGN) {
       assign_chunk<M>(a.s, a.f, cur, i0, lane, cT);
     } else if (OP == ADHA_OP_MIX && VEC) {
@@ -131,19 +133,10 @@ __global__ void __launch_bounds__(kThreads) section_kernel(const __grid_constant
   // ragged tail: the warp whose next chunk would be n_chunks
   const int64_t t0 = a.n_chunks * R;
   if constexpr (OP == ADHA_OP_REDUCE) {
-    if (c == a.n_chunks && t0 < a.n) reduce_tail(a.s, a.f, t0, a.n, lane, acc, cnt);
+    if (c == a.n_chunks && t0 < a.n) reduce_tail<true>(rq, a.s, a.f, t0, a.n, lane, acc, sum, &cnt);
     // every warp adds its sums and counts into the result (zeroed before the launch)
     __syncwarp();
-    const int K = a.s.arg[1], d = a.s.rd_off[ADHA_F32 + 1] - a.s.rd_off[ADHA_F32];
-    unsigned long long* out = static_cast<unsigned long long*>(const_cast<void*>(a.s.aux));
-#pragma unroll
-    for (int k = 0; k < kMaxClusters; ++k)
-      if (k < K) {
-        if (lane < d)
-          atomicAdd(out + (size_t)k * (d + 1) + 1 + lane,
-                    (unsigned long long)(acc[k * 32 + lane] + acc[(kMaxClusters + 1 + k) * 32 + lane]));
-        if (lane == 0) atomicAdd(out + (size_t)k * (d + 1), cnt[k]);
-      }
+    reduce_flush<true>(rq, a.s, lane, acc, sum, &cnt);
   } else {
     if (c == a.n_chunks && t0 < a.n) {
       for (int64_t i = t0 + lane; i < a.n; i += 32)
@@ -212,9 +205,9 @@ __global__ void __launch_bounds__(kThreads) backward_kernel(const __grid_constan
 }
 
 size_t section_smem_bytes(const SectionArgs& a) {
-  // REDUCE: two (K+1) x 32 int64 tables per warp (even and odd records; row K is scratch)
-  const size_t acc = a.s.op == ADHA_OP_REDUCE ? (size_t)kWarps * 2 * (kMaxClusters + 1) * 32 * 8 : 0;
-  const size_t cent = a.s.op == ADHA_OP_ASSIGN ? (size_t)kMaxFields * kMaxClusters * 4 : 0;
+  // REDUCE: two (K+1) x 32 int64 tables per warp unless it walks, and a 32-entry list per warp
+  const size_t acc = a.s.op == ADHA_OP_REDUCE ? (a.reduce_walk ? 0 : kReduceTableBytes) + kReduceListBytes : 0;
+  const size_t cent = a.s.op == ADHA_OP_ASSIGN ? (size_t)kCentroidPairBytes : 0;
   return kSectionTable + (size_t)kWarps * a.buffers * a.in_bytes + acc + cent;
 }
 

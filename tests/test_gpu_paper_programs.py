@@ -247,3 +247,148 @@ def test_kmeans_host_pipeline_reduces_slice_by_slice(P, slices):
         assert np.array_equal(secs.outputs[1].cpu().numpy(), red), "%d slices" % slices
     got = oracle.to_fields(n, wl.dtypes, out_layout.groups, [h.numpy() for h in host_out])
     assert_fields_equal(got, want, "kmeans host program, %d slices" % slices)
+
+
+@pytest.mark.parametrize("chunk", [0, 32, 64, 128])
+@pytest.mark.parametrize("n", [31, 4099, 70001])
+def test_assign_and_reduce_fused(P, chunk, n):
+    """The K-Means pair as one fused run (the paper's combine edge over both sections): the
+    membership the assign writes into the chunk buffer is what the reduce sums by, and the result
+    equals the oracle's two sections one after another, in AoS, SoA and a random grouping, ragged
+    tails included; features carry special values (NaN, infinities, out-of-range magnitudes)."""
+    wl = synth.kmeans(n=n, n_features=12, k=7)
+    d = 12
+    rng = np.random.default_rng(100 + n + chunk)
+    S = P.Schema(wl.dtypes)
+    for groups in _layouts(wl.F, n + 1):
+        fields = [_special_features(rng, n) for _ in range(d)] + [rng.integers(-1, 8, n).astype(np.int32)]
+        bufs = to_device(n, wl.dtypes, groups, fields)
+        secs = P.Sections(wl.sections)
+        P.adha_tune_override(chunk)
+        try:
+            P.adha_run_sections_fused(S, n, P.Layout(groups), bufs, secs)
+            torch.cuda.synchronize()
+        finally:
+            P.adha_tune_override(0)
+        want = [a.copy() for a in fields]
+        oracle.section(wl.sections[0], wl.dtypes, want)
+        red = oracle.section(wl.sections[1], wl.dtypes, want)
+        assert_fields_equal(from_device(n, wl.dtypes, groups, bufs), want, "fused assign in %r" % (groups,))
+        assert np.array_equal(secs.outputs[1].cpu().numpy(), red), "fused reduce in %r" % (groups,)
+
+
+@pytest.mark.parametrize("n", [1, 77, 65600])
+def test_reduce_inside_a_fused_run_sees_its_position(P, n):
+    """A reduce between two sections of a fused run sums the features as the earlier section left
+    them and not as the later one rewrites them; memberships anywhere in [-1, K]; run twice, the
+    result is the last run's sums.  The elementwise sections' inputs are grid values (the bits of a
+    NaN that arithmetic produces are not fixed across processors); the reduce also reads special
+    values in the features no section computes."""
+    fs = frozenset
+    wl = synth.kmeans(n=n, n_features=6, k=4)
+    d = 6
+    pre = synth.Section("axpb", (0, 1), fs({0}), fs({1}), params=(0.5, 0.25))     # feature 1 from feature 0
+    post = synth.Section("mul", (2, 3, 4), fs({2, 3}), fs({4}))                  # feature 4 rewritten after
+    run = [pre, wl.sections[1], post]
+    rng = np.random.default_rng(n)
+    S = P.Schema(wl.dtypes)
+    for groups in _layouts(wl.F, n + 7):
+        fields = [_special_features(rng, n) for _ in range(d)] + [rng.integers(-1, 5, n).astype(np.int32)]
+        for f in (0, 2, 3):
+            fields[f] = (rng.integers(-(1 << 23), 1 << 23, n) * 2.0 ** -23).astype(np.float32)
+        bufs = to_device(n, wl.dtypes, groups, fields)
+        secs = P.Sections(run)
+        for _ in range(2):
+            P.adha_run_sections_fused(S, n, P.Layout(groups), bufs, secs)
+            torch.cuda.synchronize()
+        want = [a.copy() for a in fields]
+        for rep in range(2):
+            red = None
+            for s in run:
+                r = oracle.section(s, wl.dtypes, want)
+                if s.op == "reduce":
+                    red = r
+        assert_fields_equal(from_device(n, wl.dtypes, groups, bufs), want, "fused run in %r" % (groups,))
+        assert np.array_equal(secs.outputs[1].cpu().numpy(), red), "reduce at its position in %r" % (groups,)
+
+
+def test_kmeans_program_with_combine_nodes(P):
+    """The K-Means program under PDL with combine nodes (measured fused costs): the result equals
+    the oracle's, whether or not PDL fuses the pair; through the host pipeline too (8 slices, the
+    fused reduce adding into a result zeroed once)."""
+    wl = synth.kmeans(n=(1 << 17) + 29)
+    n = wl.n
+    S = P.Schema(wl.dtypes)
+    AOS = P.Layout.aos(wl.F)
+    fields = oracle.initial_fields(wl)
+    bufs = to_device(n, wl.dtypes, AOS.groups, fields)
+    secs = P.Sections(wl.sections)
+    cand = P.adha_plan_sections(S, secs, P.PlanOpts(CAPS))
+    costs = P.adha_measure(S, n, AOS, bufs, secs, cand, reps=1, fuse_window=2)
+    opts = P.PlanOpts(CAPS, fuse_window=2)
+    want = [a.copy() for a in fields]
+    want[32] = want[32].view(np.int32)
+    oracle.section(wl.sections[0], wl.dtypes, want)
+    red = oracle.section(wl.sections[1], wl.dtypes, want)
+    ws = torch.empty(P.adha_program_workspace_bytes(S, n, AOS, cand), dtype=torch.uint8, device="cuda")
+    for fixed_windows in (None, [2, 0]):
+        bufs = to_device(n, wl.dtypes, AOS.groups, fields)
+        if fixed_windows is None:
+            plan = P.adha_run_program(S, n, AOS, bufs, secs, cand, costs=costs, opts=opts, workspace=ws)
+        else:   # the pair fused in AoS, whatever the costs say
+            plan = P.adha_run_program(S, n, AOS, bufs, secs, cand, costs=costs, opts=opts, workspace=ws,
+                                      fixed=[0, 0], windows=fixed_windows)
+        torch.cuda.synchronize()
+        lay, out = P.final_buffers(plan, S, n, cand, AOS)
+        assert_fields_equal(from_device(n, wl.dtypes, lay.groups, out), want, "kmeans, windows %r" % (fixed_windows,))
+        assert np.array_equal(secs.outputs[1].cpu().numpy(), red)
+    host_in = [torch.from_numpy(b).pin_memory() for b in oracle.from_fields(n, wl.dtypes, AOS.groups, fields)]
+    strides, _ = P.adha_layout_strides(S, AOS)
+    host_out = [torch.zeros(n * s, dtype=torch.uint8).pin_memory() for s in strides]
+    hws = torch.empty(P.adha_program_host_workspace_bytes(S, n, AOS, cand, 8), dtype=torch.uint8, device="cuda")
+    for _ in range(2):
+        P.adha_run_program_host(S, n, AOS, host_in, secs, cand, host_out, costs=costs, opts=opts, workspace=hws,
+                                n_slices=8, fixed=[0, 0], windows=[2, 0])
+        torch.cuda.synchronize()
+        assert np.array_equal(secs.outputs[1].cpu().numpy(), red), "host pipeline, fused pair"
+    got = oracle.to_fields(n, wl.dtypes, AOS.groups, [h.numpy() for h in host_out])
+    assert_fields_equal(got, want, "kmeans host program, fused pair")
+
+
+@pytest.mark.parametrize("chunk", [32, 64, 128])
+def test_assign_with_subnormal_distances(P, chunk):
+    """Features and centroids near 1e-20, so that squared differences and their sums are subnormal
+    fp32 values (and some underflow to zero): the distances, compared in pairs of records per
+    packed instruction, must keep every subnormal bit (no flush to zero) to match the oracle's
+    membership, alone and fused with the reduce; K = 1..8 (every specialised cluster count)."""
+    import dataclasses
+    n, d = 9001, 6
+    rng = np.random.default_rng(chunk)
+    for K in range(1, 9):
+        wl = synth.kmeans(n=n, n_features=d, k=K)
+        table = tuple(float(np.float32(v * 1e-20)) for v in wl.sections[0].table)
+        assign = dataclasses.replace(wl.sections[0], table=table)
+        run = [assign, wl.sections[1]]
+        fields = [(rng.standard_normal(n) * 1e-20).astype(np.float32) for _ in range(d)] + [np.zeros(n, np.int32)]
+        want = [a.copy() for a in fields]
+        oracle.section(assign, wl.dtypes, want)
+        red = oracle.section(wl.sections[1], wl.dtypes, want)
+        assert K == 1 or len(set(want[d].tolist())) > 1, "memberships should differ"
+        S = P.Schema(wl.dtypes)
+        for groups in (oracle.aos(d + 1), oracle.soa(d + 1)):
+            for fused in (False, True):
+                bufs = to_device(n, wl.dtypes, groups, fields)
+                secs = P.Sections(run)
+                P.adha_tune_override(chunk)
+                try:
+                    if fused:
+                        P.adha_run_sections_fused(S, n, P.Layout(groups), bufs, secs)
+                    else:
+                        P.adha_run_section(S, n, P.Layout(groups), bufs, secs.arr[0])
+                        P.adha_run_section(S, n, P.Layout(groups), bufs, secs.arr[1])
+                    torch.cuda.synchronize()
+                finally:
+                    P.adha_tune_override(0)
+                got = from_device(n, wl.dtypes, groups, bufs)
+                assert np.array_equal(got[d], want[d]), "K=%d fused=%s %r" % (K, fused, groups)
+                assert np.array_equal(secs.outputs[1].cpu().numpy(), red), "K=%d fused=%s" % (K, fused)

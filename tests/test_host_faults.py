@@ -161,8 +161,8 @@ def test_bad_section_in_a_later_window_fails_before_launch(P):
 
 def test_kmeans_sections_validated_before_launch(P):
     """The assign and reduce sections' rules (fp32 features, an int32 membership field, 1 <= K <= 8,
-    at most 32 features for reduce, reduce writes no field, aux present and aligned, reduce never
-    fused) are checked on the host."""
+    at most 32 features for reduce, reduce writes no field, aux present and aligned, at most one
+    reduce in a fused run) are checked on the host."""
     AdhaError, EINVAL, _ = _codes()
     F = 6
     dtypes = [0, 0, 0, 0, 2, 2]
@@ -194,9 +194,12 @@ def test_kmeans_sections_validated_before_launch(P):
         P.adha_run_section(S, 64, L, bufs, c, stream=0)
     assert e.value.code == EINVAL and "aux" in str(e.value)
     c.aux = aux8
-    with pytest.raises(AdhaError) as e:                               # never fused, even alone
-        P.adha_run_sections_fused(S, 64, L, bufs, P.Sections([c]), stream=0)
-    assert e.value.code == EINVAL and "fused" in str(e.value)
+    two = P.Sections([ok, ok])
+    for k in range(2):
+        two.arr[k].aux = aux8
+    with pytest.raises(AdhaError) as e:                               # two reduces in one fused run
+        P.adha_run_sections_fused(S, 64, L, bufs, two, stream=0)
+    assert e.value.code == EINVAL and "one reduce" in str(e.value)
     wide = P.Schema([0] * 33 + [2])
     c = P.c_section(Sec("reduce", (33, 2), fs(range(34)), fs()))
     c.aux = aux8
