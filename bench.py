@@ -836,7 +836,10 @@ def differentiable_run(P, torch, args, world=1, dist=None, local=0, steps=None, 
         key = tuple(tuple(g) for g in lay.groups)
         if key not in seeds:
             seeds[key] = [c[torch.tensor(g, device="cuda")].expand(n, len(g)).contiguous() for g in lay.groups]
-        torch.autograd.backward(out, seeds[key])
+        # backward on this thread (not autograd's device thread), so that its adjoint launches fall
+        # inside this thread's NVTX ranges like the forward launches
+        with torch.autograd.set_multithreading_enabled(False):
+            torch.autograd.backward(out, seeds[key])
         return x.grad
 
     plan = [layouts[l] for l in seq]

@@ -74,3 +74,25 @@ def test_top_plans_are_the_cheapest_by_model_cost():
         assert [c for c, _ in got] == every[:K]
         assert all(cost(seq) == c for c, seq in got)
         assert len({tuple(seq) for _, seq in got}) == len(got)
+
+
+def test_traffic_records_hold_only_while_their_kernel_sources_are_unchanged(tmp_path, monkeypatch):
+    """A committed DRAM-traffic record is reported while the kernel family's device sources hash to
+    the recorded value, and not once any of those files changes."""
+    fam = bench.KERNEL_SOURCES["remap"]
+    rec = {"workloads": {"stress": {"remap": {"dram_bytes_per_launch": 123, "sources_hash": bench.kernel_sources_hash("remap")}}}}
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "traffic.json").write_text(json.dumps(rec))
+    csrc = tmp_path / "paper_1407_4859_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    real = os.path.join(ROOT, "paper_1407_4859_gb300", "csrc")
+    for f in os.listdir(real):
+        (csrc / f).write_bytes(open(os.path.join(real, f), "rb").read())
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.traffic_for("stress", "remap") == 123
+    assert bench.traffic_for("stress", "specialised_mix") is None          # no record
+    (csrc / fam[0]).write_bytes((csrc / fam[0]).read_bytes() + b"\n// changed\n")
+    assert bench.traffic_for("stress", "remap") is None
+    # a family that does not include the changed file keeps its hash
+    assert fam[0] not in bench.KERNEL_SOURCES["specialised"]
