@@ -885,14 +885,16 @@ def differentiable_run(P, torch, args, world=1, dist=None, local=0, steps=None, 
     cpu_d = None
     if cpu:
         cores = host_cores()
-        ns = 1 << 18
-        st = [wl.values(f, n=ns) for f in range(F)]
-        t1 = time.perf_counter()
-        oracle.chain_grad(wl.sections, st, wl.loss_weights)
-        dt = time.perf_counter() - t1
-        cpu_d = {"value": round(work * ns / n / dt / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                 "sample": "first 2^18 of 2^26 records: forward + reverse pass per record, one thread (the chain "
-                           "gradient is not split by record range)"}
+        rates = {}
+        for threads, ns in ((1, 1 << 18), (cores, 1 << 21)):
+            st = [np.ascontiguousarray(wl.values(f, n=ns), dtype=np.float32) for f in range(F)]
+            t1 = time.perf_counter()
+            oracle.chain_grad_threads(wl.sections, st, wl.loss_weights, threads=threads)
+            rates[threads] = work * ns / n / (time.perf_counter() - t1) / 1e9
+        cpu_d = {"value": round(rates[cores], 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
+                 "threads_1": round(rates[1], 3),
+                 "sample": "first 2^21 of 2^26 records over %d host threads by record range (threads_1: first "
+                           "2^18 on one thread): forward + reverse pass per record" % cores}
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": steps,
         "warmup": warmup, "ms_per_step": round(ms / steps, 3), "higher_is_better": True,

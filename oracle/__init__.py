@@ -21,7 +21,7 @@ Heterogeneous Architectures", PACT 2014, Section 2 and Tables 2-4.
 """
 from .core import (  # noqa: F401
     build, group_layout, layout_info, remap, to_fields, from_fields, tanhf, tanh_coeffs, section,
-    chain_grad, aos, soa, canon, kmeans_assign, kmeans_reduce, kmeans_features, section_threads,
+    chain_grad, chain_grad_threads, aos, soa, canon, kmeans_assign, kmeans_reduce, kmeans_features, section_threads,
     remap_threads,
 )
 from .planner import (  # noqa: F401

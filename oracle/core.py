@@ -232,6 +232,37 @@ def chain_grad(sections, fields, c):
     return grads
 
 
+def chain_grad_threads(sections, fields, c, threads=1):
+    """chain_grad() split over `threads` host threads by record range: every record's forward and
+    reverse pass is independent of the others, so each range runs the same per-record code on
+    slices of the arrays (bit-identical to one call; ctypes releases the interpreter lock)."""
+    from concurrent.futures import ThreadPoolExecutor
+    n = fields[0].shape[0]
+    for a in fields:
+        assert a.flags.c_contiguous and a.shape[0] == n and a.dtype == np.float32
+    F = len(fields)
+    ops = _i32([OPS[s.op] for s in sections])
+    args, par = [], []
+    for s in sections:
+        args += [s.args[0], s.args[1], s.args[2]] if s.op == "mul" else [s.args[0], 0, s.args[1]]
+        par += list(s.params) if s.op == "axpb" else [0.0, 0.0]
+    args = _i32(args)
+    par = np.ascontiguousarray(np.asarray(par, dtype=np.float32))
+    cc = np.ascontiguousarray(np.asarray(c, dtype=np.float32))
+    grads = [np.empty(n, dtype=np.float32) for _ in range(F)]
+    lib = _get()
+
+    def work(r):
+        i0, i1 = r
+        return lib.oracle_chain_grad(len(sections), ops.ctypes.data, args.ctypes.data, par.ctypes.data, F,
+                                     _ptrs([a[i0:i1] for a in fields]), cc.ctypes.data,
+                                     _ptrs([g[i0:i1] for g in grads]), i1 - i0)
+    with ThreadPoolExecutor(max_workers=max(1, threads)) as ex:
+        if any(ex.map(work, _ranges(n, threads))):
+            raise ValueError("chain_grad failed")
+    return grads
+
+
 def _ranges(n, threads):
     step = (n + threads - 1) // max(1, threads)
     return [(i0, min(n, i0 + step)) for i0 in range(0, n, max(1, step))]

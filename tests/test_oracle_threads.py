@@ -45,3 +45,14 @@ def test_threaded_remap_equals_one_call(threads):
     one = oracle.remap(wl.n, wl.dtypes, oracle.aos(16), aos, groups)
     many = oracle.remap_threads(wl.n, wl.dtypes, oracle.aos(16), aos, groups, threads=threads)
     assert all(np.array_equal(x, y) for x, y in zip(one, many))
+
+
+@pytest.mark.parametrize("threads", [2, 6])
+def test_threaded_chain_gradient_equals_one_call(threads):
+    wl = synth.config5(n=5003)
+    a = [x.copy() for x in oracle.initial_fields(wl)]
+    b = [x.copy() for x in a]
+    ga = oracle.chain_grad(wl.sections, a, wl.loss_weights)
+    gb = oracle.chain_grad_threads(wl.sections, b, wl.loss_weights, threads=threads)
+    for x, y in zip(a + ga, b + gb):
+        assert np.array_equal(x.view(np.uint8), y.view(np.uint8))
