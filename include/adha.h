@@ -496,7 +496,8 @@ typedef struct {
 typedef struct adha_batched adha_batched;
 
 #define ADHA_BATCHED_AUTOTUNE 1   /* pick each array's launch shape by timing it (synchronizes `stream`) */
-#define ADHA_BATCHED_CTAS(k) ((int32_t)(k) << 4)   /* force k CTAs per SM (1..4) instead of the model's choice */
+#define ADHA_BATCHED_TWO_BUFFERS 2   /* two input chunk buffers per warp (the next chunk staged during the moves) */
+#define ADHA_BATCHED_CTAS(k) ((int32_t)(k) << 4)   /* force k CTAs per SM (1..8) instead of the model's choice */
 
 /*
  * Prepares the remap of n_arrays record arrays in one persistent launch (the
@@ -505,10 +506,14 @@ typedef struct adha_batched adha_batched;
  * the descriptors the kernel reads.  The kernel's warps work alone: each takes
  * work units of about 1024 records of one array by an atomic ticket (largest
  * array first) and keeps its current array's tables in its own region of
- * shared memory.  The region is set here: the number of CTAs per SM (1 to 4)
- * whose regions hold every array's chunk buffers (chunks shortened to fit, down
- * to 8 records) with the most bytes x CTAs, discounting arrays whose chunks had
- * to shrink (ADHA_BATCHED_CTAS(k) in flags forces k).  With
+ * shared memory.  The region is set here: the number of CTAs per SM (1 to 8,
+ * as registers allow) whose regions hold every array's chunk buffers (chunks
+ * shortened to fit, down to 8 records) with the most bytes x CTAs, discounting
+ * arrays whose chunks had to shrink (ADHA_BATCHED_CTAS(k) in flags forces k).
+ * A warp has one input chunk buffer and stages its next chunk once the moves
+ * have read the current one (longer chunks in the same shared memory, measured
+ * faster on the 256-array workload); ADHA_BATCHED_TWO_BUFFERS gives it two, the
+ * next chunk staged while the current one is moved.  With
  * ADHA_BATCHED_AUTOTUNE each array's chunk size (32..256 records) and store
  * mode for one-field destination groups (see adha_tune_remap_direct) are the
  * fastest pair, timed with the single-array kernel on the array's own buffers

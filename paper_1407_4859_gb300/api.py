@@ -571,6 +571,7 @@ def adha_profile_stop(max_records=4096):
 # ------------------------------------------------------------------ batched remap
 
 ADHA_BATCHED_AUTOTUNE = 1
+ADHA_BATCHED_TWO_BUFFERS = 2
 
 
 def remap_descs(arrays):
@@ -605,12 +606,13 @@ def adha_remap_batched(arrays, workspace, stream=None):
 class Batched:
     """A prepared batched remap (adha_batched_create); arrays: list of dicts with keys
     schema (Schema), n, src (Layout), src_bufs, dst (Layout), dst_bufs.  ctas: force that many
-    CTAs per SM (1..4; 0 = the library's choice)."""
+    CTAs per SM (1..8; 0 = the library's choice); buffers: input chunk buffers per warp (1 or 2)."""
 
-    def __init__(self, arrays, autotune=False, stream=None, ctas=0):
+    def __init__(self, arrays, autotune=False, stream=None, ctas=0, buffers=1):
         descs, self._keep = remap_descs(arrays)
         self.ptr = ctypes.c_void_p()
-        flags = (ADHA_BATCHED_AUTOTUNE if autotune else 0) | (int(ctas) << 4)
+        flags = ((ADHA_BATCHED_AUTOTUNE if autotune else 0) | (ADHA_BATCHED_TWO_BUFFERS if buffers == 2 else 0)
+                 | (int(ctas) << 4))
         check(_lib.load().adha_batched_create(len(arrays), descs, flags, _stream_ptr(stream), ctypes.byref(self.ptr)),
               "adha_batched_create")
         self.workspace = None

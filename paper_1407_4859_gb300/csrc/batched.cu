@@ -7,10 +7,12 @@
 // every launch), finds the unit's array by a 32-way search over the arrays' first units (one
 // ballot per level), and, when the array differs from its last one, copies that array's header,
 // group table and element schedule (built on the host when the batch is prepared) into its own
-// region of shared memory.  It then runs the double-buffered cp.async pipeline of remap.cu over
-// the unit's consecutive chunks: stage the source slices with 16-byte copies one chunk ahead,
-// assemble the destination records one move per lane per step, write them back with 16-byte
-// stores.  No warp ever waits for another: there is no block-wide barrier anywhere, so uneven
+// region of shared memory.  It then runs the cp.async pipeline of remap.cu over the unit's
+// consecutive chunks: stage the source slices with 16-byte copies, assemble the destination
+// records one move per lane per step, write them back with 16-byte stores.  With one input
+// buffer per warp (the default) the next chunk is staged as soon as the moves have read the
+// current one, so its copy overlaps the write-back, and the shared memory saved goes to longer
+// chunks; with two, the next chunk is staged before the current one is moved.  No warp ever waits for another: there is no block-wide barrier anywhere, so uneven
 // arrays and ragged tails cost only their own work.  Units are dealt largest array first, so
 // the small arrays' single units fill the last gaps.  The launch (memset + kernel) can be
 // captured in a CUDA graph.
@@ -55,6 +57,7 @@ struct BatchParams {
   const int64_t* prefix;         // first unit of each listed array; prefix[n_arrays] = total_units
   int32_t n_arrays;
   int32_t region;                // shared bytes of one warp
+  int32_t buffers;               // input chunk buffers per warp: 2 (the next chunk staged during this one) or 1
   int64_t total_units;
 };
 
@@ -98,16 +101,17 @@ __global__ void __launch_bounds__(kThreads) batched_kernel(const __grid_constant
       uint4* sd = reinterpret_cast<uint4*>(region + h.sched_off);
       for (int k = lane; k < h.sched_bytes / 16; k += 32) sd[k] = __ldg(ss + k);
       // the zeros that padding moves read, after each input buffer
-      if (lane < 2) *reinterpret_cast<uint4*>(region + h.buf_off + lane * (h.in_bytes + kZeroTail) + h.in_bytes) =
-          make_uint4(0, 0, 0, 0);
+      if (lane < p.buffers)
+        *reinterpret_cast<uint4*>(region + h.buf_off + lane * (h.in_bytes + kZeroTail) + h.in_bytes) = make_uint4(0, 0, 0, 0);
       __syncwarp();
       cur = arr;
     }
     const GroupRef* tout = tin + h.n_src;
     const uint32_t* sched = reinterpret_cast<const uint32_t*>(region + h.sched_off);
     uint8_t* buf0 = region + h.buf_off;
-    uint8_t* buf1 = buf0 + h.in_bytes + kZeroTail;
-    uint8_t* outb = buf1 + h.in_bytes + kZeroTail;
+    const int nb = p.buffers;
+    uint8_t* buf1 = buf0 + (nb - 1) * (h.in_bytes + kZeroTail);
+    uint8_t* outb = buf0 + nb * (h.in_bytes + kZeroTail);
     const int R = h.R, in_bytes = h.in_bytes;
     const int64_t c_begin = (u - h.unit0) * h.chunks_per_unit;
     const int64_t c_end = min(c_begin + (int64_t)h.chunks_per_unit, h.n_chunks);
@@ -126,12 +130,20 @@ __global__ void __launch_bounds__(kThreads) batched_kernel(const __grid_constant
     cp_async_commit();
     for (int i = 0; c < full_end; ++c, ++i) {
       uint8_t* curb = (i & 1) ? buf1 : buf0;
-      if (c + 1 < full_end) stage(c + 1, (i & 1) ? buf0 : buf1);
-      cp_async_commit();
-      cp_async_wait<1>();
+      if (nb == 2) {
+        if (c + 1 < full_end) stage(c + 1, (i & 1) ? buf0 : buf1);
+        cp_async_commit();
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
       __syncwarp();
       move_chunk<DIRECT>(sched, R, h.cls_count, curb, outb, tout, c * R, lane);
       __syncwarp();
+      if (nb == 1 && c + 1 < full_end) {   // one buffer: the next chunk once the moves have read this one
+        stage(c + 1, buf0);
+        cp_async_commit();
+      }
       write_back<DIRECT>(tout, R, h.out_bytes, outb, c, lane);
       __syncwarp();
     }
@@ -157,6 +169,7 @@ struct adha_batched {
   int grid = 1;
   double bytes = 0;
   bool direct = false;             // some array stores one-field destination groups directly
+  int32_t buffers = 1;             // input chunk buffers per warp
   cudaGraphExec_t graph = nullptr;
   void* graph_ws = nullptr;
 };
@@ -177,6 +190,7 @@ static BatchParams params_for(const adha_batched* b, void* ws) {
   p.prefix = reinterpret_cast<const int64_t*>(base + b->off_prefix);
   p.n_arrays = b->n_arrays;
   p.region = b->region;
+  p.buffers = b->buffers;
   p.total_units = b->total_units;
   return p;
 }
@@ -206,12 +220,12 @@ static int batch_chunk(const Layout& S, const Layout& D) {
 }
 
 // Shared bytes of one warp working on an array with chunks of R records: header, group table,
-// schedule (R x moves entries of 4 bytes), two input buffers (each followed by the zeros that
+// schedule (R x moves entries of 4 bytes), nb input buffers (each followed by the zeros that
 // padding moves read) and an output buffer.
-static int warp_region_bytes(const RemapArgs& a, int R) {
+static int warp_region_bytes(const RemapArgs& a, int R, int nb) {
   const int in_rec = a.in_bytes / a.R, out_rec = a.out_bytes / a.R;
   return kHeaderBytes + (a.n_src + a.n_dst) * (int)sizeof(GroupRef) + al16(R * a.n_moves * 4) +
-         R * (2 * in_rec + out_rec) + 2 * kZeroTail;
+         R * (nb * in_rec + out_rec) + nb * kZeroTail;
 }
 
 // Chooses an array's chunk size and direct stores (autotune): the fastest of 32..256 records x
@@ -283,6 +297,7 @@ int adha_batched_create(int32_t n_arrays, const adha_remap_desc* descs, int32_t 
   clear_error();
   if (!out || !descs || n_arrays < 1) return fail(ADHA_EINVAL, "bad batched arguments");
   const int forced_ctas = (flags >> 4) & 15;
+  const int nb = (flags & ADHA_BATCHED_TWO_BUFFERS) ? 2 : 1;
   if (forced_ctas > kMaxBatchedCtas) return fail(ADHA_EINVAL, "ADHA_BATCHED_CTAS(%d) is not in 1..%d", forced_ctas, kMaxBatchedCtas);
   std::vector<ArrayPlan> plans(n_arrays);
   for (int k = 0; k < n_arrays; ++k) {
@@ -339,8 +354,8 @@ int adha_batched_create(int32_t n_arrays, const adha_remap_desc* descs, int32_t 
   if (e != cudaSuccess) return cuda_fail(e, "device attributes for the batched kernel");
   auto fit_R = [&](const ArrayPlan& ap, int region) {
     int R = ap.R0;
-    while (R > 8 && warp_region_bytes(ap.a, R) > region) R = std::max(8, R / 2 / 8 * 8);
-    return warp_region_bytes(ap.a, R) <= region ? R : 0;
+    while (R > 8 && warp_region_bytes(ap.a, R, nb) > region) R = std::max(8, R / 2 / 8 * 8);
+    return warp_region_bytes(ap.a, R, nb) <= region ? R : 0;
   };
   // CTAs per SM that the kernel's registers allow at all
   int reg_ctas = 0;
@@ -441,6 +456,7 @@ int adha_batched_create(int32_t n_arrays, const adha_remap_desc* descs, int32_t 
   b->direct = direct;
   b->region = best_region;
   b->ctas_per_sm = best_k;
+  b->buffers = nb;
   b->off_headers = al256(sizeof(unsigned long long));
   b->off_groups = b->off_headers + al256(std::max<size_t>(1, headers.size()) * sizeof(BatchHeader));
   b->off_moves = b->off_groups + al256(std::max<size_t>(1, groups.size()) * sizeof(GroupRef));

@@ -55,11 +55,11 @@ def _random_specs(seed, count, n_choices):
     return specs
 
 
-@pytest.mark.parametrize("autotune", [False, True])
-def test_batched_random_arrays(P, autotune):
+@pytest.mark.parametrize("autotune,buffers", [(False, 1), (True, 1), (False, 2), (True, 2)])
+def test_batched_random_arrays(P, autotune, buffers):
     specs = _random_specs(5, 40, [1, 7, 32, 33, 1000, 4097, 70001, 300000])
     arrays = _arrays(P, specs, 1)
-    b = P.Batched(arrays, autotune=autotune)
+    b = P.Batched(arrays, autotune=autotune, buffers=buffers)
     if autotune:   # autotuning ran the arrays' remaps already: reset the outputs
         for a in arrays:
             for d in a["dst_bufs"]:
@@ -144,12 +144,13 @@ def _wide_specs(seed, count):
     return specs
 
 
+@pytest.mark.parametrize("buffers", [1, 2])
 @pytest.mark.parametrize("ctas", [1, 2, 3, 4])
-def test_batched_forced_ctas_per_sm(P, ctas):
+def test_batched_forced_ctas_per_sm(P, ctas, buffers):
     """Every CTA count (and so every warp-region size, with chunks shortened to fit) gives the
     oracle's bytes, on wide mixed-dtype records with ragged tails."""
     arrays = _arrays(P, _wide_specs(20 + ctas, 24), 4)
-    b = P.Batched(arrays, ctas=ctas)
+    b = P.Batched(arrays, ctas=ctas, buffers=buffers)
     k, region, units = b.info
     assert k == ctas and region > 0
     b.upload()
