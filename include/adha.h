@@ -413,7 +413,7 @@ size_t adha_measure_workspace_bytes_for(const adha_schema* schema, int64_t n, co
  * leaves that group in place, as the executor does.  With ADHA_MEASURE_AUTOTUNE
  * in flags each section is timed under every launch shape (records per chunk
  * 32, 64, 128 x field-wise or whole-group stores), and each remap from or to
- * the input layout under every choice of piece tables (adha_tune_remap_pieces);
+ * the input layout under every choice of piece tables and chunk buffers (adha_tune_remap_pieces);
  * the fastest enters the table and the library's tuning cache, which later
  * launches of the same section (or pair of layouts), layout and size class use.
  * With ADHA_MEASURE_DIFFERENTIABLE (fp32 schemas whose sections are all axpb,
@@ -701,13 +701,15 @@ int adha_tune_remap_direct(int32_t mode);
 
 /*
  * How remaps launched later by the calling thread find where each 16-byte piece
- * of a chunk buffer lives in global memory: through a per-block table of the
- * pieces, or by a search over the groups.  0 = as tuned for the pair of layouts
- * (adha_measure with ADHA_MEASURE_AUTOTUNE), else automatic (the table for a
- * buffer whose slices average under 256 bytes); 1..4 = forced, with bits
- * mode - 1: bit 0 = stage the source buffer through the table, bit 1 = write the
- * destination buffer back through it.  Every mode moves the same bytes.  Host
- * only; EINVAL for another mode.
+ * of a chunk buffer lives in global memory (through a per-block table of the
+ * pieces, or by a search over the groups) and how many input chunk buffers a
+ * warp has.  0 = as tuned for the pair of layouts (adha_measure with
+ * ADHA_MEASURE_AUTOTUNE), else automatic (the table for a buffer whose slices
+ * average under 256 bytes; two buffers); 1..8 = forced, with bits mode - 1:
+ * bit 0 = stage the source buffer through the table, bit 1 = write the
+ * destination buffer back through it, bit 2 = one input buffer (the next chunk
+ * staged once the moves have read the current one) instead of two.  Every mode
+ * moves the same bytes.  Host only; EINVAL for another mode.
  */
 int adha_tune_remap_pieces(int32_t mode);
 

@@ -214,10 +214,10 @@ static thread_local int t_fused_jit = 0;        // fused runs: 0 as tuned, 1 lib
 static thread_local int t_section_jit = 0;      // sections: 0 as tuned, 1 library kernel, 2 specialised where possible
 static thread_local bool t_reduce_accumulate = false;   // REDUCE adds into its result (host pipeline slices)
 static thread_local int t_remap_direct = 0;     // 1: remaps store one-field destination groups directly
-static thread_local int t_remap_pieces = 0;     // 0: tuned or automatic, 1 + piece-table bits otherwise
+static thread_local int t_remap_pieces = 0;     // 0: tuned or automatic, 1 + (piece-table bits | 4 for one buffer) otherwise
 
 // Autotuned launch shapes: section key -> (records per chunk, writeback mode); remap key ->
-// (0, piece-table bits).
+// (0, piece-table bits | 4 for one chunk buffer).
 static std::mutex g_tune_mu;
 static std::map<std::string, std::pair<int, int>> g_tune;
 
@@ -510,8 +510,12 @@ static int plan_remap(const Layout& S, const void* const* src_ptrs, const Layout
     for (int k = 0; k < a.n_dst; ++k) staged_dst += a.dst[k].start >= 0;
     const bool narrow_in = a.in_bytes < 256 * a.n_src, narrow_out = staged_dst > 0 && a.out_bytes < 256 * staged_dst;
     a.pieces = (narrow_in ? 1 : 0) | (narrow_out ? 2 : 0);
-    if (t_remap_pieces) a.pieces = t_remap_pieces - 1;
-    else if (tuned_pieces >= 0) a.pieces = tuned_pieces;
+    a.buffers = 2;
+    const int mode = t_remap_pieces ? t_remap_pieces - 1 : tuned_pieces;
+    if (mode >= 0) {
+      a.pieces = mode & 3;
+      a.buffers = (mode & 4) ? 1 : 2;
+    }
     a.n_moves = (int)moves.size();
     for (int c = 0; c < kMoveClasses; ++c) a.cls_count[c] = 0;
     for (size_t k = 0; k < idx.size(); ++k) {
@@ -1355,7 +1359,7 @@ int adha_tune_import(const char* text) {
     int R = 0, wb = 0;
     if (!number(t1 + 1, t2, &R) || !number(t2 + 1, line.size(), &wb))
       return fail(ADHA_EINVAL, "bad tuning values (not whole numbers): %s", line.c_str());
-    const bool bad = kind == 'M'   ? (R != 0 || wb > 3)
+    const bool bad = kind == 'M'   ? (R != 0 || wb > 7)
                      : kind == 'F' ? (R % 32 || R > 128 || (wb & 3) > 2 || wb > 6)
                                    : (R % 32 || R > 128 || (wb & 3) > 2 || wb > 14);
     if (bad) return fail(ADHA_EINVAL, "bad tuning values: %s", line.c_str());
@@ -1375,7 +1379,7 @@ int adha_tune_remap_direct(int32_t mode) {
 
 int adha_tune_remap_pieces(int32_t mode) {
   clear_error();
-  if (mode < 0 || mode > 4) return fail(ADHA_EINVAL, "remap piece-table mode %d not in [0, 4]", mode);
+  if (mode < 0 || mode > 8) return fail(ADHA_EINVAL, "remap piece-table mode %d not in [0, 8]", mode);
   t_remap_pieces = mode;
   return 0;
 }

@@ -78,6 +78,7 @@ struct RemapArgs {
   int32_t cls_count[6];   // moves per class, in that order in `move`
   int32_t cls_order[6];   // per class: schedule order (see schedule_pair)
   int32_t pieces;         // bit 0: stage through the per-CTA piece table, bit 1: write back through it
+  int32_t buffers;        // input chunk buffers per warp: 2 (the next chunk staged during the moves) or 1
   GroupRef src[kMaxGroups];
   GroupRef dst[kMaxGroups];
   Move move[kMaxMoves];

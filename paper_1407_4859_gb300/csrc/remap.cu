@@ -4,8 +4,9 @@
 // Every warp works alone on chunks of R consecutive records (R a multiple of 32), so the main
 // loop has no block-wide barrier:
 //   1. the warp copies the chunk's slice of every source group into its own shared buffer with
-//      16-byte cp.async (coalesced: lane l moves bytes 16l, 16l+512, ...), one chunk ahead of
-//      the one it works on (double buffering);
+//      16-byte cp.async (coalesced: lane l moves bytes 16l, 16l+512, ...): one chunk ahead of
+//      the one it works on (two buffers), or, with one buffer, as soon as the moves have read
+//      the current chunk (half the input buffers' shared memory, so more warps per SM);
 //   2. it moves every field of every destination record, one move per lane per step: a move is
 //      one field (8, 4 or 2 bytes, whole) or an aligned piece of zero padding (read from 16 zero
 //      bytes after the chunk buffer), taken from a schedule table built once per CTA.  Moves into one-field destination groups are stored
@@ -42,10 +43,11 @@ __global__ void __launch_bounds__(kThreads) remap_kernel(const __grid_constant__
   uint32_t* sched = reinterpret_cast<uint32_t*>(tout + a.n_dst);
   uint8_t* wbase = reinterpret_cast<uint8_t*>(sched) + align16(n_entries * 4);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  uint8_t* buf0 = wbase + (size_t)warp * (2 * (a.in_bytes + kZeroTail) + a.out_bytes);
-  uint8_t* buf1 = buf0 + a.in_bytes + kZeroTail;
-  uint8_t* outb = buf1 + a.in_bytes + kZeroTail;
-  if (lane < 2) *reinterpret_cast<uint4*>((lane ? buf1 : buf0) + a.in_bytes) = make_uint4(0, 0, 0, 0);
+  const int nb = a.buffers;
+  uint8_t* buf0 = wbase + (size_t)warp * (nb * (a.in_bytes + kZeroTail) + a.out_bytes);
+  uint8_t* buf1 = buf0 + (nb - 1) * (a.in_bytes + kZeroTail);
+  uint8_t* outb = buf0 + nb * (a.in_bytes + kZeroTail);
+  if (lane < nb) *reinterpret_cast<uint4*>((lane ? buf1 : buf0) + a.in_bytes) = make_uint4(0, 0, 0, 0);
 
   for (int q = tid; q < in_pieces; q += kThreads) pin[q] = piece_of(q, a.src, a.R);
   for (int q = tid; q < out_pieces; q += kThreads) pout[q] = piece_of(q, a.dst, a.R);
@@ -80,12 +82,20 @@ __global__ void __launch_bounds__(kThreads) remap_kernel(const __grid_constant__
   cp_async_commit();
   for (int i = 0; c < a.n_chunks; c += W, ++i) {
     uint8_t* cur = (i & 1) ? buf1 : buf0;
-    if (c + W < a.n_chunks) stage(c + W, (i & 1) ? buf0 : buf1);
-    cp_async_commit();
-    cp_async_wait<1>();
+    if (nb == 2) {
+      if (c + W < a.n_chunks) stage(c + W, (i & 1) ? buf0 : buf1);
+      cp_async_commit();
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
     __syncwarp();
     move_chunk<DIRECT>(sched, a.R, a.cls_count, cur, outb, tout, c * R, lane);
     __syncwarp();
+    if (nb == 1 && c + W < a.n_chunks) {   // one buffer: the next chunk once the moves have read this one
+      stage(c + W, buf0);
+      cp_async_commit();
+    }
     if (a.pieces & 2) {
 #pragma unroll 1
       for (int q = lane; q < out_pieces; q += 32) {
@@ -109,7 +119,7 @@ size_t remap_smem_bytes(const RemapArgs& a) {
   auto al = [](size_t x) { return (x + 15) / 16 * 16; };
   const size_t pieces = ((a.pieces & 1) ? a.in_bytes / 16 : 0) + ((a.pieces & 2) ? a.out_bytes / 16 : 0);
   return pieces * sizeof(Piece) + (size_t)(a.n_src + a.n_dst) * sizeof(GroupRef) + al((size_t)a.R * a.n_moves * 4) +
-         (size_t)kWarps * (2 * ((size_t)a.in_bytes + kZeroTail) + a.out_bytes);
+         (size_t)kWarps * ((size_t)a.buffers * ((size_t)a.in_bytes + kZeroTail) + a.out_bytes);
 }
 
 template <bool DIRECT>

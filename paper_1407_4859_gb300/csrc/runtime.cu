@@ -209,7 +209,7 @@ int adha_measure(const adha_schema* schema, int64_t n, const adha_layout* in_lay
     if (!tune || !(flags & ADHA_MEASURE_AUTOTUNE)) return time_ns(timer, stream, reps, run, ns);
     double best = -1, t = 0;
     int bits = 0;
-    for (int m = 1; m <= 4; ++m) {
+    for (int m = 1; m <= 8; ++m) {   // piece tables x one or two chunk buffers per warp
       set_remap_pieces(m);
       const int e = time_ns(timer, stream, reps, run, &t);
       set_remap_pieces(0);

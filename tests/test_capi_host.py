@@ -151,16 +151,16 @@ def test_tuning_cache_text_round_trip(P):
     for bad in [-1, 2]:
         with pytest.raises(AdhaError):
             P.adha_tune_remap_direct(bad)
-    for bad in [-1, 5]:
+    for bad in [-1, 9]:
         with pytest.raises(AdhaError):
             P.adha_tune_remap_pieces(bad)
-    for ok in [4, 3, 2, 1, 0]:
+    for ok in [8, 7, 5, 4, 3, 2, 1, 0]:
         P.adha_tune_remap_pieces(ok)
-    # remap entries: records 0, piece-table bits 0..3
-    remap = "M0.0,1.0,|>0.0,|1.0,|:n20\t0\t3\n"
+    # remap entries: records 0, piece-table bits 0..3 (+ 4: one chunk buffer)
+    remap = "M0.0,1.0,|>0.0,|1.0,|:n20\t0\t7\n"
     P.adha_tune_import(remap)
     assert P.adha_tune_export() == remap
-    for bad in ["M0.0,|>0.0,|:n3\t32\t1\n", "M0.0,|>0.0,|:n3\t0\t4\n"]:
+    for bad in ["M0.0,|>0.0,|:n3\t32\t1\n", "M0.0,|>0.0,|:n3\t0\t8\n"]:
         with pytest.raises(AdhaError):
             P.adha_tune_import(bad)
     P.adha_tune_clear()

@@ -33,7 +33,7 @@ def _check_remap(P, n, dtypes, src, dst, fields):
 
 @pytest.mark.parametrize("seed", range(24))
 @pytest.mark.parametrize("n", [1, 17, 1000, 4099])
-@pytest.mark.parametrize("direct,pieces", [(0, 0), (1, 0), (0, 2), (1, 1)])
+@pytest.mark.parametrize("direct,pieces", [(0, 0), (1, 0), (0, 2), (1, 1), (0, 5), (1, 8)])
 def test_random_layouts(P, seed, n, direct, pieces):
     rng = np.random.default_rng(1000 + seed)
     F = int(rng.integers(1, 24))
@@ -48,7 +48,7 @@ def test_random_layouts(P, seed, n, direct, pieces):
 
 
 @pytest.mark.parametrize("n", [33, 4099, 100003])
-@pytest.mark.parametrize("pieces", [0, 1, 2])
+@pytest.mark.parametrize("pieces", [0, 1, 2, 5, 8])
 @pytest.mark.parametrize("chunk", [0, 8, 64])
 def test_aos_soa_many_narrow_fields(P, n, pieces, chunk):
     """24 fp32 fields: 24 slices of 4 * chunk bytes per buffer, the case the piece tables are for."""
