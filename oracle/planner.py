@@ -29,13 +29,18 @@ from .core import group_layout, aos, soa, canon
 
 
 def affinity(sections, F):
-    """Edge weights {(a, b): w}, a < b: sections whose accessed fields include both a and b."""
+    """Edge weights {(a, b): w}, a < b: the number of record accesses, over the window's sections,
+    that reach both a and b.  A section accesses its record i (the fields it reads or writes)
+    and, if it gathers, the record perm[i] (the fields it reads through the permutation): two
+    accesses, each adding one to every pair of its fields; a field read at i and a field read at
+    perm[i] are not accessed together."""
     w = {}
     for s in sections:
-        t = sorted(s.touched)
-        for i in range(len(t)):
-            for j in range(i + 1, len(t)):
-                w[(t[i], t[j])] = w.get((t[i], t[j]), 0) + 1
+        for acc in (s.read | s.write, s.read_at_perm):
+            t = sorted(acc)
+            for i in range(len(t)):
+                for j in range(i + 1, len(t)):
+                    w[(t[i], t[j])] = w.get((t[i], t[j]), 0) + 1
     return w
 
 

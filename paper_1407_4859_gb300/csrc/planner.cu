@@ -1,6 +1,7 @@
 // planner.cu -- host side of ADHA's two levels (paper Section 2):
 //   ODS: an affinity graph over the fields a run of sections accesses, edge weight = the number
-//        of sections accessing both fields; greedy clustering of fields into structures under a
+//        of record accesses reaching both fields (a section accesses record i, and record
+//        perm[i] if it gathers); greedy clustering of fields into structures under a
 //        struct-size limit ("determined based on the underlying architecture");
 //   PDL: one layout per section for the whole program: the shortest path through the layered
 //        DAG input -> section 1 -> ... -> section S whose nodes are (section, candidate layout),
@@ -24,7 +25,6 @@ namespace adha {
 
 using Groups = std::vector<std::vector<int>>;
 
-static uint64_t touched(const adha_section& s) { return s.read_mask | s.write_mask | s.read_at_perm_mask; }
 
 // Canonical order: fields ascending inside a group, groups by their first field.
 static Groups canonical(Groups g) {
@@ -34,15 +34,15 @@ static Groups canonical(Groups g) {
 }
 
 Groups ods_groups(int F, const int* dtype, const adha_section* secs, int n_sec, int cap) {
-  // affinity weights
+  // affinity weights: each record access of each section (its record i: the fields it reads or
+  // writes; record perm[i]: the fields it reads through the permutation) adds one to every pair
   std::vector<int> w(F * F, 0);
-  for (int k = 0; k < n_sec; ++k) {
-    const uint64_t m = touched(secs[k]);
-    for (int a = 0; a < F; ++a)
-      if ((m >> a) & 1ull)
-        for (int b = a + 1; b < F; ++b)
-          if ((m >> b) & 1ull) ++w[a * F + b];
-  }
+  for (int k = 0; k < n_sec; ++k)
+    for (const uint64_t m : {secs[k].read_mask | secs[k].write_mask, secs[k].read_at_perm_mask})
+      for (int a = 0; a < F; ++a)
+        if ((m >> a) & 1ull)
+          for (int b = a + 1; b < F; ++b)
+            if ((m >> b) & 1ull) ++w[a * F + b];
   struct Edge { int w, a, b; };
   std::vector<Edge> edges;
   for (int a = 0; a < F; ++a)
@@ -82,7 +82,7 @@ static int validate_sections(int F, const adha_section* secs, int n_sec) {
   if (!secs) return fail(ADHA_EINVAL, "sections are NULL");
   const uint64_t all = F == 64 ? ~0ull : ((1ull << F) - 1);
   for (int k = 0; k < n_sec; ++k)
-    if (touched(secs[k]) & ~all) return fail(ADHA_EINVAL, "section %d names fields beyond %d", k, F);
+    if ((secs[k].read_mask | secs[k].write_mask | secs[k].read_at_perm_mask) & ~all) return fail(ADHA_EINVAL, "section %d names fields beyond %d", k, F);
   return 0;
 }
 

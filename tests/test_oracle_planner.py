@@ -57,11 +57,28 @@ def test_ods_golden(dtypes, sections, cap, want):
 
 
 def test_affinity_counts_common_occurrences():
+    """Hand-worked: the mix section accesses {0,1,2} in one record (three pairs); the gather
+    accesses {1} at record i (no pair) and {2,3} at record perm[i] (one pair; 1 and 2 are never in
+    one access, so (1,2) gets nothing from it); the last section touches one field."""
     secs = [Section("mix", (), frozenset([0, 1, 2]), frozenset([0])),
             Section("gather", (), frozenset([1]), frozenset([1]), frozenset([2, 3])),
             Section("mix", (), frozenset([3]), frozenset([3]))]
     w = oracle.affinity(secs, 4)
-    assert w == {(0, 1): 1, (0, 2): 1, (1, 2): 2, (1, 3): 1, (2, 3): 1}
+    assert w == {(0, 1): 1, (0, 2): 1, (1, 2): 1, (2, 3): 1}
+    # a field read both at i and at perm[i] is in both accesses: (1,2) from record i, (2,3) from perm[i]
+    g2 = [Section("gather", (), frozenset([1, 2]), frozenset([1]), frozenset([2, 3]))]
+    assert oracle.affinity(g2, 4) == {(1, 2): 1, (2, 3): 1}
+
+
+def test_ods_packs_the_fields_a_gather_reads_through_the_permutation():
+    """The Medical-shaped gather (writes V1..V3 at i, reads U1..U3 and T at perm[i]): under a
+    16-byte limit ODS keeps the permuted reads in one 16-byte struct and the V fields in another,
+    the grouping that lets the gather fetch each permuted record with one 16-byte load."""
+    import synth
+    wl = synth.medical(n=64)
+    gather = wl.sections[0]
+    assert gather.op == "gather"
+    assert oracle.ods([gather], wl.dtypes, 16) == [[0, 1, 2], [3, 4, 5, 7], [6], [8]]
 
 
 def test_untouched_fields_stay_alone_and_no_cap_gives_one_cluster():

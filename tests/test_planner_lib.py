@@ -35,8 +35,25 @@ def test_library_ods_random(P, seed):
         assert P.adha_ods(P.Schema(wl.dtypes), secs, cap).groups == oracle.ods(secs, wl.dtypes, cap)
 
 
+@pytest.mark.parametrize("seed", range(30))
+def test_library_ods_random_with_permuted_reads(P, seed):
+    """Windows holding gather-like sections (fields read at record i, written at i, read at
+    perm[i]): the library's affinity counts the two record accesses apart, as the oracle's does."""
+    rng = np.random.default_rng(500 + seed)
+    F = int(rng.integers(3, 20))
+    dtypes = [int(x) for x in rng.integers(0, 4, F)]
+    secs = []
+    for _ in range(int(rng.integers(1, 4))):
+        rd = frozenset(int(f) for f in np.nonzero(rng.random(F) < 0.3)[0])
+        wr = frozenset(f for f in rd if rng.random() < 0.5)
+        pr = frozenset(int(f) for f in np.nonzero(rng.random(F) < 0.3)[0]) - wr
+        secs.append(synth.Section("gather", (), rd | wr, wr, pr))
+    for cap in [0, 8, 12, 16, 24, 40]:
+        assert P.adha_ods(P.Schema(dtypes), secs, cap).groups == oracle.ods(secs, dtypes, cap)
+
+
 @pytest.mark.parametrize("make,window", [(synth.config1, 0), (synth.config2, 0), (synth.config3, 4),
-                                         (synth.config5, 3)])
+                                         (synth.config5, 3), (synth.medical, 3)])
 def test_library_candidates_match_oracle(P, make, window):
     wl = make(n=16)
     lib = P.adha_plan_sections(P.Schema(wl.dtypes), wl.sections, P.PlanOpts(CAPS, max_window=window))
