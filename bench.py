@@ -602,6 +602,20 @@ def fused_comparison(P, torch, S, n, AOS, in_buf, secs, cand, costs, ws, stream,
                     "the union of its sections' fields read once plus written fields written once"}
 
 
+def _gather_vs_probe(sub, probe):
+    """The workload's gather section (library or specialised kernel) against the random-gather
+    probe run on the same number of records: time per record of the probe over the gather's."""
+    ks = sub.get("kernels", {})
+    gk = ks.get("section_gather") or ks.get("specialised_gather")
+    if not gk or not probe.get("ns_per_record"):
+        return
+    ns = gk["ms"] * 1e6 / (gk["launches"] * sub["config"]["records"])
+    sub["gather_vs_probe"] = {"gather_ns_per_record": round(ns, 4), "probe_ns_per_record": probe["ns_per_record"],
+                              "probe_records": probe["records"], "frac": round(probe["ns_per_record"] / ns, 4),
+                              "note": "time per record of the probe (random 16-byte reads, sequential index and "
+                                      "output) over that of the gather section"}
+
+
 def gather_probe_run(P, torch, wl, reps=10):
     """The random-access roofline of the gather section: 16-byte structs read at the workload's
     permutation (2^25 records) and written in order, GB/s of 4 + 16 + 16 bytes per record."""
@@ -1021,17 +1035,12 @@ def main():
                 subs[name] = {"error": repr(e)[:300]}
             subs[name]["wall_s"] = round(time.perf_counter() - t1, 1)
             log("%s done in %.1f s" % (name, subs[name]["wall_s"]))
-        g = line.get("gather_random", {})
-        part = subs.get("particles", {})
-        gk = part.get("kernels", {}).get("section_gather")
-        if gk and g.get("ns_per_record"):
-            n_part = part["config"]["records"]
-            ns = gk["ms"] * 1e6 / (gk["launches"] * n_part)
-            part["gather_vs_probe"] = {"gather_ns_per_record": round(ns, 4),
-                                       "probe_ns_per_record": g["ns_per_record"],
-                                       "frac": round(g["ns_per_record"] / ns, 4),
-                                       "note": "time per record of the probe (random 16-byte reads, sequential "
-                                               "index and output) over that of the gather section"}
+        _gather_vs_probe(subs.get("particles", {}), line.get("gather_random", {}))
+        if "error" not in subs.get("medical", {"error": 1}):
+            try:   # the probe at the Medical program's size and permutation
+                _gather_vs_probe(subs["medical"], gather_probe_run(P, torch, synth.medical()))
+            except Exception as e:
+                subs["medical"]["gather_vs_probe"] = {"error": repr(e)[:300]}
         line["workloads"] = subs
         line["workloads_wall_s"] = round(time.perf_counter() - t0, 1)
     if rank == 0:

@@ -96,3 +96,18 @@ def test_traffic_records_hold_only_while_their_kernel_sources_are_unchanged(tmp_
     assert bench.traffic_for("stress", "remap") is None
     # a family that does not include the changed file keeps its hash
     assert fam[0] not in bench.KERNEL_SOURCES["specialised"]
+
+
+def test_gather_vs_probe_reads_either_gather_kernel():
+    """The gather's time per record comes from whichever kernel ran it (library or specialised),
+    over the workload's records, and is set against the probe's time per record."""
+    probe = {"ns_per_record": 0.02, "records": 1000}
+    for key in ("section_gather", "specialised_gather"):
+        sub = {"kernels": {key: {"ms": 0.1, "launches": 4}, "remap": {"ms": 9.0, "launches": 4}},
+               "config": {"records": 1000000}}
+        bench._gather_vs_probe(sub, probe)
+        g = sub["gather_vs_probe"]
+        assert abs(g["gather_ns_per_record"] - 0.025) < 1e-9 and abs(g["frac"] - 0.8) < 1e-9
+    sub = {"kernels": {"remap": {"ms": 1.0, "launches": 1}}, "config": {"records": 10}}
+    bench._gather_vs_probe(sub, probe)
+    assert "gather_vs_probe" not in sub
