@@ -190,8 +190,11 @@ int adha_run_section(const adha_schema* schema, int64_t n, const adha_layout* la
  * written fields are written back whole.  The result equals running the
  * sections one after another with adha_run_section.  Requirements (EINVAL
  * otherwise): 1 <= n_sec <= ADHA_MAX_FUSED, each section valid alone, all
- * gathers of the run use the same perm, and no section of the run writes a
- * field that a gather of the run reads through perm.  Async on `stream`.
+ * gathers of the run use the same perm, no section of the run writes a field
+ * that a gather of the run reads through perm, and at most one REDUCE section.
+ * A REDUCE in the run sums every record as the run's earlier sections left it
+ * (its result is zeroed before the launch, as adha_run_section does).  Async on
+ * `stream`.
  */
 int adha_run_sections_fused(const adha_schema* schema, int64_t n, const adha_layout* layout, void* const* ptrs,
                             const adha_section* sections, int32_t n_sec, adha_stream stream);
