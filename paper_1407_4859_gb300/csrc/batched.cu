@@ -354,7 +354,10 @@ int adha_batched_create(int32_t n_arrays, const adha_remap_desc* descs, int32_t 
   if (e != cudaSuccess) return cuda_fail(e, "device attributes for the batched kernel");
   auto fit_R = [&](const ArrayPlan& ap, int region) {
     int R = ap.R0;
-    while (R > 8 && warp_region_bytes(ap.a, R, nb) > region) R = std::max(8, R / 2 / 8 * 8);
+    // the longest chunk (at most the preferred one) whose tables and buffers fit the region: in
+    // steps of 32 records while at least 32 (whole 32-record blocks keep the skewed schedule
+    // orders), then of 8
+    while (R > 8 && warp_region_bytes(ap.a, R, nb) > region) R -= R > 32 ? 32 : 8;
     return warp_region_bytes(ap.a, R, nb) <= region ? R : 0;
   };
   // CTAs per SM that the kernel's registers allow at all
