@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(kThreads) fused_kernel(const __grid_constant__
       const int op = so.op;
       if constexpr (KM) {
         if (s == a.reduce_sec) {
-          reduce_chunk_any<M, true>(rq, cur, lane, acc, acc + (kMaxClusters + 1) * 32, idx, sum, &cnt_lane);
+          reduce_chunk_any<M>(rq, cur, lane, acc, acc + (kMaxClusters + 1) * 32, idx, sum, &cnt_lane);
           __syncwarp();
           continue;
         }
@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(kThreads) fused_kernel(const __grid_constant__
       for (int s = 0; s < a.n_sec; ++s) {
         __syncwarp();
         if (s == a.reduce_sec) {
-          if constexpr (KM) reduce_tail<true>(rq, secs[s], fr, t0, a.n, lane, acc, sum, &cnt_lane);
+          if constexpr (KM) reduce_tail(rq, secs[s], fr, t0, a.n, lane, acc, sum, &cnt_lane);
         } else {
           for (int64_t i = t0 + lane; i < a.n; i += 32)
             fused_section_record(a, fr, secs[s], i, a.perm_slot >= 0 ? a.perm[i] : 0);
@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(kThreads) fused_kernel(const __grid_constant__
   if constexpr (KM) {
     if (a.reduce_sec >= 0) {   // every warp adds its sums and counts into the result
       __syncwarp();
-      reduce_flush<true>(rq, secs[a.reduce_sec], lane, acc, sum, &cnt_lane);
+      reduce_flush(rq, secs[a.reduce_sec], lane, acc, sum, &cnt_lane);
     }
   }
 }

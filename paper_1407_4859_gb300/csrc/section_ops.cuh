@@ -730,7 +730,7 @@ __device__ __forceinline__ void reduce_sums(const ReduceLane& q, const uint8_t* 
                                             long long* __restrict__ acc, long long* __restrict__ acc2);
 
 // REDUCE over the R = 32*M records of a staged chunk.  Counts: lane = record, one ballot per
-// cluster (LANECOUNT: lane k keeps cluster k's count, one register; else every lane keeps all K).
+// cluster, lane k keeping cluster k's count (one register).
 // Sums, lane j = feature j, integer sums (any order gives the same result):
 // * walk (every feature in a slice wider than one field, e.g. AoS): for each group of 32 records
 //   the warp lists the records cluster by cluster (a counting sort by ballots into the warp's
@@ -741,7 +741,7 @@ __device__ __forceinline__ void reduce_sums(const ReduceLane& q, const uint8_t* 
 //   lane starts at its own record and adds every record into its row of two (K+1) x 32 tables in
 //   shared memory, even records into the first and odd into the second, so that two
 //   read-add-write chains are in flight (row K takes memberships outside [0, K)).
-template <int M, bool LANECOUNT>
+template <int M>
 __device__ __forceinline__ void reduce_chunk_any(const ReduceLane& q, const uint8_t* stage, int lane,
                                                  long long* __restrict__ acc, long long* __restrict__ acc2,
                                                  int* __restrict__ idx, long long (&sum)[kMaxClusters],
@@ -757,11 +757,7 @@ __device__ __forceinline__ void reduce_chunk_any(const ReduceLane& q, const uint
       for (int k = 0; k < kMaxClusters; ++k) {
         b[k] = k < q.K ? __ballot_sync(0xFFFFFFFFu, mm == k) : 0u;
         const int c = __popc(b[k]);
-        if (LANECOUNT) {
-          if (lane == k) *cnt += (unsigned long long)c;
-        } else {
-          cnt[k] += (unsigned long long)c;
-        }
+        if (lane == k) *cnt += (unsigned long long)c;
         if (k < q.K && mm == k) idx[start + __popc(b[k] & lt)] = lane;
         start += c;
       }
@@ -797,11 +793,7 @@ __device__ __forceinline__ void reduce_chunk_any(const ReduceLane& q, const uint
     for (int k = 0; k < kMaxClusters; ++k)
       if (k < q.K) {
         const unsigned b = __ballot_sync(0xFFFFFFFFu, mm == k);
-        if (LANECOUNT) {
-          if (lane == k) *cnt += (unsigned long long)__popc(b);
-        } else {
-          cnt[k] += (unsigned long long)__popc(b);
-        }
+        if (lane == k) *cnt += (unsigned long long)__popc(b);
       }
   }
   reduce_sums<M>(q, stage, lane, acc, acc2);
@@ -833,10 +825,8 @@ __device__ __forceinline__ void reduce_sums(const ReduceLane& q, const uint8_t* 
   }
 }
 
-// REDUCE over records [t0, n) read from global memory (the ragged tail): lane j = feature j;
-// counts in lane 0 (all K) or, LANECOUNT, lane k for cluster k; sums into the register sums
-// (walk) or row mm of the first shared table.
-template <bool LANECOUNT>
+// REDUCE over records [t0, n) read from global memory (the ragged tail): lane j = feature j,
+// lane k counts cluster k; sums into the register sums (walk) or row mm of the first shared table.
 __device__ __forceinline__ void reduce_tail(const ReduceLane& q, const SecOp& so, const FieldRef* fr, int64_t t0,
                                             int64_t n, int lane, long long* acc, long long (&sum)[kMaxClusters],
                                             unsigned long long* cnt) {
@@ -845,12 +835,7 @@ __device__ __forceinline__ void reduce_tail(const ReduceLane& q, const SecOp& so
   for (int64_t i = t0; i < n; ++i) {
     const int mm = *reinterpret_cast<const int32_t*>(Fm.g + i * Fm.gs);
     if ((unsigned)mm >= (unsigned)q.K) continue;
-    if (LANECOUNT) {
-      if (lane == mm) *cnt += 1ull;
-    } else if (lane == 0) {
-#pragma unroll
-      for (int k = 0; k < kMaxClusters; ++k) cnt[k] += k == mm ? 1ull : 0ull;
-    }
+    if (lane == mm) *cnt += 1ull;
     if (lane < q.d) {
       const FieldRef& Fx = fr[so.rd[j0 + lane]];
       const long long v = fixq(*reinterpret_cast<const float*>(Fx.g + i * Fx.gs));
@@ -866,7 +851,6 @@ __device__ __forceinline__ void reduce_tail(const ReduceLane& q, const SecOp& so
 
 // The warp's sums and counts added into the result (K rows of [count, d sums], zeroed before
 // the launch unless the caller accumulates).
-template <bool LANECOUNT>
 __device__ __forceinline__ void reduce_flush(const ReduceLane& q, const SecOp& so, int lane, const long long* acc,
                                              const long long (&sum)[kMaxClusters], const unsigned long long* cnt) {
   unsigned long long* out = static_cast<unsigned long long*>(const_cast<void*>(so.aux));
@@ -878,9 +862,8 @@ __device__ __forceinline__ void reduce_flush(const ReduceLane& q, const SecOp& s
         const long long v = q.walk ? sum[k] : acc[k * 32 + lane] + acc[(kMaxClusters + 1 + k) * 32 + lane];
         atomicAdd(out + (size_t)k * (d + 1) + 1 + lane, (unsigned long long)v);
       }
-      if (!LANECOUNT && lane == 0) atomicAdd(out + (size_t)k * (d + 1), cnt[k]);
     }
-  if (LANECOUNT && lane < q.K) atomicAdd(out + (size_t)lane * (d + 1), *cnt);
+  if (lane < q.K) atomicAdd(out + (size_t)lane * (d + 1), *cnt);
 }
 
 }  // namespace adha

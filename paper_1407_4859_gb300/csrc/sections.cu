@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kThreads) section_kernel(const __grid_constant
     __syncwarp();
     const int64_t i0 = c * R;
     if constexpr (OP == ADHA_OP_REDUCE) {
-      reduce_chunk_any<M, true>(rq, cur, lane, acc, acc + (kMaxClusters + 1) * 32, idx, sum, &cnt);
+      reduce_chunk_any<M>(rq, cur, lane, acc, acc + (kMaxClusters + 1) * 32, idx, sum, &cnt);
     } else if constexpr (OP == ADHA_OP_ASSIGN) {
       assign_chunk<M>(a.s, a.f, cur, i0, lane, cT);
     } else if (OP == ADHA_OP_MIX && VEC) {
@@ -133,10 +133,10 @@ __global__ void __launch_bounds__(kThreads) section_kernel(const __grid_constant
   // ragged tail: the warp whose next chunk would be n_chunks
   const int64_t t0 = a.n_chunks * R;
   if constexpr (OP == ADHA_OP_REDUCE) {
-    if (c == a.n_chunks && t0 < a.n) reduce_tail<true>(rq, a.s, a.f, t0, a.n, lane, acc, sum, &cnt);
+    if (c == a.n_chunks && t0 < a.n) reduce_tail(rq, a.s, a.f, t0, a.n, lane, acc, sum, &cnt);
     // every warp adds its sums and counts into the result (zeroed before the launch)
     __syncwarp();
-    reduce_flush<true>(rq, a.s, lane, acc, sum, &cnt);
+    reduce_flush(rq, a.s, lane, acc, sum, &cnt);
   } else {
     if (c == a.n_chunks && t0 < a.n) {
       for (int64_t i = t0 + lane; i < a.n; i += 32)
