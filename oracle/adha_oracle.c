@@ -335,7 +335,7 @@ int oracle_section_range(int op, const int* a, const float* p, uint64_t R, uint6
 /*
  * The paper's second benchmark (Section 3, Table 1, Table 3) is K-Means: a
  * data-parallel section over all features, then a section that reduces over
- * all records.  Its two sections, as this build defines them (the paper gives
+ * all records.  Its two sections, as this library defines them (the paper gives
  * no formulas):
  *   features x_0..x_{d-1}: the fp32 fields feat[0..d) (ascending ids);
  *   membership m: the int32 field mf; K clusters; centroid c[k][j] = cent[k*d + j].
