@@ -1,5 +1,5 @@
 """bench.py's host logic, CPU only: the byte counts behind its value and the reference arm's JSON
-line (the oracle timed on the host cores), whose keys the driver reads."""
+line (the oracle timed on the host cores), whose keys the benchmark contract fixes."""
 import json
 import os
 import subprocess
