@@ -958,6 +958,7 @@ static int plan_fused(const Layout& L, void* const* ptrs, const adha_section* s,
   else if (one_field && (size_t)kWarps * 2 * 64 * rec <= (size_t)kSmemLimit / 2 - 8192) R = 64;
   else R = rec > 0 ? pick_chunk(rec, 4096, 128) : 128;
   if (R != 32 && R != 64 && R != 128) R = R < 64 ? 32 : 64;
+  if ((reduce_sec >= 0 || assign_sec >= 0) && R > 64) R = 64;   // the assign / reduce kernels stop at 64
   for (;;) {
     a.n = n;
     a.R = R;

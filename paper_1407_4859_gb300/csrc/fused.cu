@@ -259,15 +259,24 @@ static int launch_m(const FusedArgs& a, int grid, size_t smem, void* stream) {
   return 0;
 }
 
+// Runs with an assign or a reduce take the record-by-record mapping whatever the layout (the vector
+// mapping only speeds up the mix and chain sections) and at most 64 records per chunk: each such
+// kernel carries the assign's per-K specialisations, so only two are built.
 template <bool KM>
 static int launch_km(const FusedArgs& a, int grid, size_t smem, void* stream) {
-  if (a.vec && a.R == 32) return launch_m<1, true, KM>(a, grid, smem, stream);
-  if (a.vec && a.R == 64) return launch_m<2, true, KM>(a, grid, smem, stream);
-  if (a.vec && a.R == 128) return launch_m<4, true, KM>(a, grid, smem, stream);
-  switch (a.R) {
-    case 32: return launch_m<1, false, KM>(a, grid, smem, stream);
-    case 64: return launch_m<2, false, KM>(a, grid, smem, stream);
-    default: return launch_m<4, false, KM>(a, grid, smem, stream);
+  if constexpr (!KM) {
+    if (a.vec && a.R == 32) return launch_m<1, true, false>(a, grid, smem, stream);
+    if (a.vec && a.R == 64) return launch_m<2, true, false>(a, grid, smem, stream);
+    if (a.vec && a.R == 128) return launch_m<4, true, false>(a, grid, smem, stream);
+  }
+  if constexpr (KM) {   // such runs are planned with at most 64 records per chunk
+    return a.R == 32 ? launch_m<1, false, true>(a, grid, smem, stream) : launch_m<2, false, true>(a, grid, smem, stream);
+  } else {
+    switch (a.R) {
+      case 32: return launch_m<1, false, false>(a, grid, smem, stream);
+      case 64: return launch_m<2, false, false>(a, grid, smem, stream);
+      default: return launch_m<4, false, false>(a, grid, smem, stream);
+    }
   }
 }
 
@@ -286,12 +295,18 @@ static int occ_m(size_t smem, int* blocks) {
 
 template <bool KM>
 static int occ_km(int M, bool vec, size_t smem, int* blocks) {
-  if (vec && M == 1) return occ_m<1, true, KM>(smem, blocks);
-  if (vec && M == 2) return occ_m<2, true, KM>(smem, blocks);
-  if (vec && M == 4) return occ_m<4, true, KM>(smem, blocks);
-  if (M == 1) return occ_m<1, false, KM>(smem, blocks);
-  if (M == 2) return occ_m<2, false, KM>(smem, blocks);
-  return occ_m<4, false, KM>(smem, blocks);
+  if constexpr (!KM) {
+    if (vec && M == 1) return occ_m<1, true, false>(smem, blocks);
+    if (vec && M == 2) return occ_m<2, true, false>(smem, blocks);
+    if (vec && M == 4) return occ_m<4, true, false>(smem, blocks);
+  }
+  if constexpr (KM) {
+    return M == 1 ? occ_m<1, false, true>(smem, blocks) : occ_m<2, false, true>(smem, blocks);
+  } else {
+    if (M == 1) return occ_m<1, false, false>(smem, blocks);
+    if (M == 2) return occ_m<2, false, false>(smem, blocks);
+    return occ_m<4, false, false>(smem, blocks);
+  }
 }
 
 int fused_occupancy(int M, bool vec, bool km, size_t smem, int* blocks) {
