@@ -217,7 +217,7 @@ static thread_local int t_remap_direct = 0;     // 1: remaps store one-field des
 static thread_local int t_remap_pieces = 0;     // 0: tuned or automatic, 1 + (piece-table bits | 4 for one buffer) otherwise
 
 // Autotuned launch shapes: section key -> (records per chunk, writeback mode); remap key ->
-// (0, piece-table bits | 4 for one chunk buffer).
+// (records per chunk, 0 for the size rule; piece-table bits | 4 for one chunk buffer).
 static std::mutex g_tune_mu;
 static std::map<std::string, std::pair<int, int>> g_tune;
 
@@ -471,13 +471,19 @@ static int plan_remap(const Layout& S, const void* const* src_ptrs, const Layout
   int src_rec = 0, dst_rec = 0;
   for (int j : need) src_rec += S.stride[j];
   for (int d : build) dst_rec += D.stride[d];
-  int R = t_tile_override ? t_tile_override : pick_remap_chunk(std::max(src_rec, dst_rec));
-  int tuned_pieces = -1;
-  if (!t_remap_pieces) {
+  int tuned_pieces = -1, tuned_R = 0;
+  if (!t_remap_pieces || !t_tile_override) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(remap_key(S, D, n));
-    if (it != g_tune.end()) tuned_pieces = it->second.second;
+    if (it != g_tune.end()) {
+      tuned_R = it->second.first;
+      tuned_pieces = it->second.second;
+    }
   }
+  // records per chunk: forced, else tuned, else about 4 KB of the wider side (the loop below
+  // shortens it while the buffers do not fit)
+  int R = t_tile_override ? t_tile_override : tuned_R > 0 ? tuned_R : pick_remap_chunk(std::max(src_rec, dst_rec));
+  if (t_remap_pieces) tuned_pieces = -1;
   for (;;) {
     a.n = n;
     a.R = R;
@@ -1360,7 +1366,7 @@ int adha_tune_import(const char* text) {
     int R = 0, wb = 0;
     if (!number(t1 + 1, t2, &R) || !number(t2 + 1, line.size(), &wb))
       return fail(ADHA_EINVAL, "bad tuning values (not whole numbers): %s", line.c_str());
-    const bool bad = kind == 'M'   ? (R != 0 || wb > 7)
+    const bool bad = kind == 'M'   ? (R % 8 || R < 0 || R > 1024 || wb > 7)
                      : kind == 'F' ? (R % 32 || R > 128 || (wb & 3) > 2 || wb > 6)
                                    : (R % 32 || R > 128 || (wb & 3) > 2 || wb > 14);
     if (bad) return fail(ADHA_EINVAL, "bad tuning values: %s", line.c_str());

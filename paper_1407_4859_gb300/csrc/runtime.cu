@@ -208,7 +208,7 @@ int adha_measure(const adha_schema* schema, int64_t n, const adha_layout* in_lay
     auto run = [&] { return remap_layouts(S, sp.data(), D, const_cast<void**>(dp.data()), n, stream, nullptr); };
     if (!tune || !(flags & ADHA_MEASURE_AUTOTUNE)) return time_ns(timer, stream, reps, run, ns);
     double best = -1, t = 0;
-    int bits = 0;
+    int bits = 0, bestR = 0;
     for (int m = 1; m <= 8; ++m) {   // piece tables x one or two chunk buffers per warp
       set_remap_pieces(m);
       const int e = time_ns(timer, stream, reps, run, &t);
@@ -219,7 +219,21 @@ int adha_measure(const adha_schema* schema, int64_t n, const adha_layout* in_lay
         bits = m - 1;
       }
     }
-    tuning_store(remap_tuning_key(S, D, n), 0, bits);
+    // then the chunk: records per chunk from 24 to 128 with the best of the above (the size rule
+    // gives 16 records for 80-byte records, where the per-chunk work dominates)
+    for (const int R : {24, 32, 48, 64, 96, 128}) {
+      set_remap_pieces(bits + 1);
+      set_overrides(R, 0, 0);
+      const int e = time_ns(timer, stream, reps, run, &t);
+      set_overrides(0, 0, 0);
+      set_remap_pieces(0);
+      if (e) return e;
+      if (t < best) {
+        best = t;
+        bestR = R;
+      }
+    }
+    tuning_store(remap_tuning_key(S, D, n), bestR, bits);
     *ns = best;
     return 0;
   };

@@ -156,11 +156,12 @@ def test_tuning_cache_text_round_trip(P):
             P.adha_tune_remap_pieces(bad)
     for ok in [8, 7, 5, 4, 3, 2, 1, 0]:
         P.adha_tune_remap_pieces(ok)
-    # remap entries: records 0, piece-table bits 0..3 (+ 4: one chunk buffer)
+    # remap entries: records per chunk (0: the size rule), piece-table bits 0..3 (+ 4: one chunk buffer)
     remap = "M0.0,1.0,|>0.0,|1.0,|:n20\t0\t7\n"
     P.adha_tune_import(remap)
     assert P.adha_tune_export() == remap
-    for bad in ["M0.0,|>0.0,|:n3\t32\t1\n", "M0.0,|>0.0,|:n3\t0\t8\n"]:
+    P.adha_tune_import("M0.0,|>0.0,|:n3\t24\t5\n")                # records per chunk: a multiple of 8
+    for bad in ["M0.0,|>0.0,|:n3\t12\t1\n", "M0.0,|>0.0,|:n3\t2048\t1\n", "M0.0,|>0.0,|:n3\t0\t8\n"]:
         with pytest.raises(AdhaError):
             P.adha_tune_import(bad)
     P.adha_tune_clear()
