@@ -416,7 +416,8 @@ size_t adha_measure_workspace_bytes_for(const adha_schema* schema, int64_t n, co
  * leaves that group in place, as the executor does.  With ADHA_MEASURE_AUTOTUNE
  * in flags each section is timed under every launch shape (records per chunk
  * 32, 64, 128 x field-wise or whole-group stores), and each remap from or to
- * the input layout under every choice of piece tables and chunk buffers (adha_tune_remap_pieces);
+ * the input layout under every choice of piece tables and chunk buffers (adha_tune_remap_pieces),
+ * then under chunks of 24 to 128 records with the best of those choices;
  * the fastest enters the table and the library's tuning cache, which later
  * launches of the same section (or pair of layouts), layout and size class use.
  * With ADHA_MEASURE_DIFFERENTIABLE (fp32 schemas whose sections are all axpb,
